@@ -1,0 +1,135 @@
+"""Seeded synthetic inputs for the A-DOT workloads.
+
+This module only lays out initial data and random states (shapes, sizes and
+value ranges of the paper's tests and of the benchmark configurations). It
+holds none of the scheme's arithmetic, and both the CUDA path and the oracle
+take its arrays as plain inputs.
+
+Conventions: a state is three float64 arrays (h, q, z) on uniform cells of
+[x_min, x_max], cell centres x_i = x_min + (i + 1/2) dx. q = h u.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+G = 9.81
+XI_P04 = 1.0 / (1.0 - 0.4)  # porosity p = 0.4
+
+# boundary kinds (same meaning on both sides of the boundary; values below)
+BC_TRANSMISSIVE, BC_PERIODIC, BC_INFLOW_Q, BC_OUTFLOW_H, BC_INFLOW_QZ = range(5)
+
+
+@dataclass
+class Problem:
+    name: str
+    n: int
+    x_min: float
+    x_max: float
+    cfl: float
+    t_end: float
+    Ag: float
+    xi: float
+    h: np.ndarray
+    q: np.ndarray
+    z: np.ndarray
+    bc_left: int = BC_TRANSMISSIVE
+    bc_right: int = BC_TRANSMISSIVE
+    bcl: tuple = (0.0, 0.0, 0.0)
+    bcr: tuple = (0.0, 0.0, 0.0)
+    g: float = G
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def dx(self) -> float:
+        return (self.x_max - self.x_min) / self.n
+
+
+def cell_centres(n: int, x_min: float, x_max: float) -> np.ndarray:
+    dx = (x_max - x_min) / n
+    return x_min + (np.arange(n, dtype=np.float64) + 0.5) * dx
+
+
+def riemann(n: int, x_min: float, x_max: float, x0: float, WL, WR) -> tuple:
+    """Piecewise-constant data: cells with centre <= x0 take WL=(h,q,z), others WR."""
+    x = cell_centres(n, x_min, x_max)
+    left = x <= x0
+    out = []
+    for k in range(3):
+        out.append(np.where(left, WL[k], WR[k]).astype(np.float64))
+    return tuple(out)
+
+
+def movable_bed_riemann(n: int = 200) -> Problem:
+    """Movable-bed Riemann problem on [0, 10] m, discontinuity at 5 m:
+    left h=2.0, u=0.25, z=0; right h=1.0, u=0.2, z=0.5; Grass A_g=0.01,
+    p=0.4, CFL 0.9, t_end 1 s, transmissive ends."""
+    h, q, z = riemann(n, 0.0, 10.0, 5.0, (2.0, 0.5, 0.0), (1.0, 0.2, 0.5))
+    return Problem("movable_bed_riemann", n, 0.0, 10.0, 0.9, 1.0, 0.01, XI_P04, h, q, z)
+
+
+def smooth_periodic(n: int) -> Problem:
+    """Smooth periodic problem on [0, 1] m: h = 1 + 0.1 sin 2 pi x,
+    u = 0.3 + 0.05 cos 2 pi x, z = 0.1 sin 2 pi x at cell centres; Grass
+    A_g = 0.005, p = 0.4, CFL 0.8, t_end 0.5 s."""
+    x = cell_centres(n, 0.0, 1.0)
+    h = 1.0 + 0.1 * np.sin(2 * np.pi * x)
+    u = 0.3 + 0.05 * np.cos(2 * np.pi * x)
+    z = 0.1 * np.sin(2 * np.pi * x)
+    return Problem("smooth_periodic", n, 0.0, 1.0, 0.8, 0.5, 0.005, XI_P04, h, h * u, z,
+                   BC_PERIODIC, BC_PERIODIC)
+
+
+def gaussian_bump(n: int, Ag: float = 0.001) -> Problem:
+    """Flow over a Gaussian bump z = 0.2 exp(-(x-5)^2) on [0, 10] m with
+    h + z = 0.4, q = 0.6; inflow q = 0.6, outflow h = 0.33."""
+    x = cell_centres(n, 0.0, 10.0)
+    z = 0.2 * np.exp(-(x - 5.0) ** 2)
+    h = 0.4 - z
+    q = np.full(n, 0.6)
+    return Problem("gaussian_bump", n, 0.0, 10.0, 0.9, 10.0, Ag, XI_P04, h, q, z,
+                   BC_INFLOW_Q, BC_OUTFLOW_H, (0.6, 0.0, 0.0), (0.33, 0.0, 0.0))
+
+
+def lake_at_rest(n: int, seed: int = 7, level: float = 1.0) -> Problem:
+    """Still water over a rough bed: z on multiples of 2^-10 in [0, 0.5],
+    h = level - z, q = 0, transmissive ends."""
+    rng = np.random.default_rng(seed)
+    z = rng.integers(0, 512, size=n).astype(np.float64) / 1024.0
+    h = level - z
+    return Problem("lake_at_rest", n, 0.0, 1.0, 0.9, 1.0, 0.01, XI_P04, h, np.zeros(n), z)
+
+
+def dam_break(n: int, hL=2.0, hR=1.0, uL=0.0, uR=0.0) -> Problem:
+    """Flat-bed fixed-bed dam break on [0, 10] m at 5 m (A_g = 0)."""
+    h, q, z = riemann(n, 0.0, 10.0, 5.0, (hL, hL * uL, 0.0), (hR, hR * uR, 0.0))
+    return Problem("dam_break", n, 0.0, 10.0, 0.9, 0.5, 0.0, 1.0, h, q, z)
+
+
+def random_edges(n: int, seed: int, h_range=(0.05, 5.0), fr_range=(-3.0, 3.0),
+                 dz_scale=0.3, rel_jump=0.5, g: float = G):
+    """Random edge pairs (WL, WR) as [3, n] float64 arrays.
+
+    Left states: h ~ U(h_range), Froude ~ U(fr_range), z ~ U(-0.5, 0.5).
+    Right states: left state times (1 + U(-rel_jump, rel_jump)) for h and q,
+    z + U(-dz_scale, dz_scale).
+    """
+    rng = np.random.default_rng(seed)
+    hL = rng.uniform(*h_range, size=n)
+    frL = rng.uniform(*fr_range, size=n)
+    qL = frL * np.sqrt(g * hL) * hL
+    zL = rng.uniform(-0.5, 0.5, size=n)
+    hR = hL * (1.0 + rng.uniform(-rel_jump, rel_jump, size=n))
+    qR = qL * (1.0 + rng.uniform(-rel_jump, rel_jump, size=n)) + 0.01 * rng.standard_normal(n)
+    zR = zL + rng.uniform(-dz_scale, dz_scale, size=n)
+    return np.stack([hL, qL, zL]), np.stack([hR, qR, zR])
+
+
+def random_states(n: int, seed: int, h_range=(0.05, 5.0), fr_range=(-3.0, 3.0),
+                  g: float = G):
+    """Random single states (h, q) with h ~ U(h_range) and Froude ~ U(fr_range)."""
+    rng = np.random.default_rng(seed)
+    h = rng.uniform(*h_range, size=n)
+    fr = rng.uniform(*fr_range, size=n)
+    return h, fr * np.sqrt(g * h) * h
