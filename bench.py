@@ -1,0 +1,309 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the A-DOT time step on one GB300 (or N replicas).
+
+Workload: the smooth periodic problem on [0, 1] m (h = 1 + 0.1 sin 2 pi x,
+u = 0.3 + 0.05 cos 2 pi x, z = 0.1 sin 2 pi x; Grass A_g = 0.005, p = 0.4,
+CFL 0.8) at N = 1e7 cells, float32 arithmetic with a float-float state. One
+step = one time step over all cells (edge fluctuations, update, CFL maximum),
+replayed from a CUDA graph. Metric: cell-updates/s = N * steps / seconds.
+
+Prints one JSON line (rank 0). --impl reference times the FP64 CPU oracle on
+the host cores instead (one step = one oracle time step on a bounded sample of
+the same workload).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/s at N=1e7 (A-DOT FP32 vs surrogate) at L1 err vs FP64 oracle"
+UNIT = "cell-updates/s"
+# FP32 flops per cell-update of the fused step kernel (FMA = 2): three
+# Gauss-Legendre nodes of the edge fluctuation, the float-float update and the
+# CFL spectral radius of the new state. Derivation and the ncu cross-check of
+# this count are in the design notes.
+FLOPS_PER_CELL_UPDATE = 1240.0
+BYTES_PER_CELL_UPDATE = 48.0  # float-float state: 3 x 8 B read + 3 x 8 B written
+
+
+def measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2400)
+    ap.add_argument("--warmup", type=int, default=96)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=float, default=1e7)
+    ap.add_argument("--block", type=int, default=256)
+    ap.add_argument("--cpu-steps", type=int, default=3,
+                    help="oracle steps on the full workload for cpu_baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--accuracy-steps", type=int, default=96,
+                    help="steps of the FP32-vs-FP64 increment check (0 = skip)")
+    return ap.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return None, 0, 1, 0
+    import torch
+    import torch.distributed as dist
+    rank = int(os.environ["RANK"])
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    backend = "nccl" if torch.cuda.is_available() else "gloo"
+    if torch.cuda.is_available():
+        torch.cuda.set_device(local)
+    dist.init_process_group(backend)
+    return dist, rank, ws, local
+
+
+def oracle_throughput(n: int, steps: int, threads: int | None = None):
+    """The FP64 oracle (as it stands) on the smooth periodic workload with n
+    cells for `steps` time steps on the host cores. Returns (cell-updates/s,
+    seconds, threads)."""
+    import oracle as O
+    from paper_1912_04791_gb300 import workloads as W
+    O.build()
+    if threads:
+        O.set_num_threads(threads)
+    P = W.smooth_periodic(n)
+    cfg = O.make_cfg(P.n, P.x_min, P.x_max, P.cfl, O.grass(P.Ag, xi=P.xi), P.bc_left, P.bc_right)
+    t0 = time.perf_counter()
+    O.run(cfg, P.h, P.q, P.z, max_steps=steps)
+    dt = time.perf_counter() - t0
+    return n * steps / dt, dt, O.num_threads()
+
+
+def run_reference(args, rank, ws):
+    """Reference arm: the FP64 CPU oracle, each step one oracle time step on a
+    sample of the workload sized so that warmup + steps end within ~3 min."""
+    if rank != 0:
+        return
+    import oracle as O
+    from paper_1912_04791_gb300 import workloads as W
+    O.build()
+    n_full = int(args.n)
+    # calibrate the per-cell cost on a small grid
+    rate, _, thr = oracle_throughput(100_000, 2)
+    budget = 150.0  # seconds for warmup + timed steps
+    n_s = int(min(n_full, max(1000, budget * rate / max(1, args.steps + args.warmup))))
+    P = W.smooth_periodic(n_s)
+    cfg = O.make_cfg(P.n, P.x_min, P.x_max, P.cfl, O.grass(P.Ag, xi=P.xi), P.bc_left, P.bc_right)
+    h, q, z, *_ = O.run(cfg, P.h, P.q, P.z, max_steps=args.warmup)
+    t0 = time.perf_counter()
+    O.run(cfg, h, q, z, max_steps=args.steps)
+    sec = time.perf_counter() - t0
+    value = n_s * args.steps / sec
+    sample = f"{n_s} cells of the N={n_full} smooth periodic workload (same initial data), one oracle time step per step"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"smooth_periodic N={n_full} (oracle sample)", "n_cells": n_s},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": thr, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    dist, rank, ws, local = dist_init()
+    if args.impl == "reference":
+        run_reference(args, rank, ws)
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    import torch
+
+    from paper_1912_04791_gb300 import adot
+    from paper_1912_04791_gb300 import build as B
+    from paper_1912_04791_gb300 import workloads as W
+
+    if rank == 0:
+        B.build()
+    if dist:
+        dist.barrier()
+    B.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n = int(args.n)
+    P = W.smooth_periodic(n)
+    stream = torch.cuda.Stream(device=dev)
+    cfg = adot.config_for(P, adot.FP32, block_threads=args.block, device=local)
+    solver = adot.Solver(cfg, stream=stream)
+    solver.set_state(P.h, P.q, P.z)
+
+    # warm-up
+    adot.adot_step(solver.ctx, args.warmup)
+
+    # timed region: K graph-replayed steps, CUDA events on the launching stream
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    adot.adot_enqueue_steps(solver.ctx, args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1)
+    t_sim, steps_done, dt_last = adot.adot_query(solver.ctx)  # raises on a device error
+    if dist:
+        tt = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    value = ws * n * args.steps / (ms * 1e-3)
+    per_launch_s = ms * 1e-3 / args.steps
+
+    # end to end through the public API with pinned host buffers:
+    # set_state (H2D) + K steps + get_state (D2H)
+    e2e = None
+    if not args.no_e2e:
+        hin = [torch.from_numpy(a).pin_memory() for a in (P.h, P.q, P.z)]
+        hout = [torch.empty(n, dtype=torch.float64).pin_memory() for _ in range(3)]
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        adot.adot_set_state(solver.ctx, *hin)
+        adot.adot_enqueue_steps(solver.ctx, args.steps)
+        adot.adot_get_state(solver.ctx, *hout)
+        sec = time.perf_counter() - t0
+        if dist:
+            tt = torch.tensor([sec], dtype=torch.float64, device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            sec = float(tt.item())
+        e2e = {"value": ws * n * args.steps / sec, "unit": UNIT,
+               "h2d_bytes_per_step": 3 * 8 * n / args.steps,
+               "d2h_bytes_per_step": 3 * 8 * n / args.steps,
+               "note": f"per call: set_state of 3x{n} float64 from pinned host, {args.steps} steps, get_state to pinned host"}
+
+    # accuracy: FP32 increment vs the GPU FP64 path over the same steps
+    accuracy = None
+    if args.accuracy_steps > 0 and rank == 0:
+        K = args.accuracy_steps
+        with adot.Solver(adot.config_for(P, adot.FP64, device=local), stream=stream) as s64:
+            s64.set_state(P.h, P.q, P.z)
+            s64.step(K)
+            ref = s64.get_state()
+        solver.set_state(P.h, P.q, P.z)
+        solver.step(K)
+        got = solver.get_state()
+        accuracy = {"steps": K, "reference": "GPU FP64 path (parity-tested against the oracle)"}
+        for name, a, b, a0 in zip("hqz", got, ref, (P.h, P.q, P.z)):
+            accuracy[f"l1_rel_increment_{name}"] = float(np.abs((a - a0) - (b - a0)).sum()
+                                                         / np.abs(b - a0).sum())
+            accuracy[f"l1_rel_state_{name}"] = float(np.abs(a - b).sum() / np.abs(b).sum())
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        rate, sec, thr = oracle_throughput(n, args.cpu_steps)
+        cpu = {"value": rate, "unit": UNIT, "cores": thr, "kind": "oracle",
+               "sample": f"{args.cpu_steps} oracle time steps of the full N={n} workload ({sec:.1f} s)"}
+
+    solver.close()
+    if rank == 0:
+        f_peak = 152 * 128 * 2 * (2070e6) / 1e12  # FP32 FMA peak at the maximum SM clock, TFLOP/s
+        achieved = FLOPS_PER_CELL_UPDATE * n / per_launch_s / 1e12
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"smooth_periodic N={n} (A-DOT FP32, float-float state)",
+                       "n_cells": n, "domain": "[0,1] m periodic", "Ag": P.Ag, "xi": P.xi,
+                       "cfl": P.cfl, "block_threads": args.block, "steps_per_graph": 48,
+                       "l2": "inputs larger than L2 (2 x 240 MB state buffers, no flush)",
+                       "parallelism": "replicas" if ws > 1 else "single"},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": f_peak, "unit": "TFLOP/s",
+                         "frac": achieved / f_peak, "traffic": None,
+                         "kernel": "k_step<float,GRASS,256>",
+                         "peak_source": "152 SM x 128 FP32 lanes x 2 x 2070 MHz (derived)",
+                         "hbm_achieved_gbs": BYTES_PER_CELL_UPDATE * n / per_launch_s / 1e9,
+                         "hbm_peak_gbs": measured_peaks().get("hbm_gbs", 6800.0)},
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps, "clocks": clocks,
+            "accuracy": accuracy, "sim_time_after_timed_steps": t_sim,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,158 @@
+/*
+ * adot.h - C ABI of the GB300 (sm_103a) A-DOT library.
+ *
+ * A-DOT is the Dumbser-Osher-Toro (DOT) path-conservative scheme for the 1D
+ * de Saint Venant-Exner system with the flux-matrix eigenstructure computed
+ * analytically (Carraro, Valiani & Caleffi, arXiv 1912.04791, Sec. 3.3).
+ * The state is W = [h, q, z] (depth, unit discharge, bed elevation) on n
+ * uniform cells of [x_min, x_max]; Eq. scheme (S = 0) advances it by
+ *     W_i <- W_i - dt/dx (D-_{i+1/2} + D+_{i-1/2}),
+ * with the DOT fluctuations of Eq. DOTjumpN (3-point Gauss-Legendre rule on
+ * the segment path of Eq. path) and |A| = R|Lambda|R^-1 (Eq. asbA) from the
+ * trigonometric roots of Eq. lambda and the vectors of Eq. RR / RR-1.
+ *
+ * Conventions for every entry point:
+ *  - Pointers are plain host or device addresses; arrays are float64.
+ *    A [3][n] array holds row 0 = h, row 1 = q, row 2 = z, each contiguous.
+ *  - `on_device` = 1: the pointers are device addresses on the context's
+ *    device (e.g. torch CUDA tensors' data_ptr()); 0: host addresses. The
+ *    library copies in and out; it never keeps a caller pointer after the call.
+ *  - The library allocates and owns all device state (state buffers, control
+ *    block, scratch, CUDA graphs) from adot_create until adot_destroy.
+ *  - Every call returns an adot_status and never throws. A device-side error
+ *    (non-finite value, h <= 0, non-hyperbolic state) is recorded in a sticky
+ *    device status word and returned by the next synchronising call; the
+ *    context stays valid so that adot_get_state can still read the state.
+ *  - Work is ordered on the CUDA stream given at creation (NULL: a stream the
+ *    library creates). A context is not thread-safe.
+ *  - There is no CPU fallback: without a usable CUDA device adot_create fails
+ *    with ADOT_E_CUDA.
+ */
+#ifndef ADOT_H
+#define ADOT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  ADOT_OK = 0,
+  ADOT_E_INVALID_ARG = 1,       /* bad pointer, size, config value or call order */
+  ADOT_E_NONPOSITIVE_DEPTH = 2, /* a cell reached h <= 0 */
+  ADOT_E_NONFINITE = 3,         /* NaN or Inf in the state or the time step */
+  ADOT_E_NONHYPERBOLIC = 4,     /* |k2 / sqrt(4 k1^3)| > 1 + 1e-6 at some state (Eq. parameters) */
+  ADOT_E_CUDA = 5,              /* a CUDA runtime call failed */
+  ADOT_E_TIMEOUT = 6,           /* a bounded device-side wait ran out */
+  ADOT_E_UNSUPPORTED = 7        /* valid request this build does not implement */
+} adot_status;
+
+/* Sediment transport closure (Sec. 2). */
+typedef enum {
+  ADOT_LAW_GRASS = 0, /* q_s = A_g u^3 (Eq. Grass) */
+  ADOT_LAW_MPM = 1    /* q_s = sign(u) 8 (theta-0.047)_+^1.5 sqrt(g (s-1) d50^3), Eq. MPM,
+                         theta = n^2 u^2 / ((s-1) d50 h^(1/3)) (Eq. Shields, Manning s_f) */
+} adot_law_kind;
+
+/* Arithmetic of the state and the fluctuations. */
+typedef enum {
+  ADOT_FP64 = 0, /* everything in float64 */
+  ADOT_FP32 = 1  /* state as float-float (two float32 per value, updated with TwoSum);
+                    fluctuations in float32; the cubic-root solve and |A| dW of a node
+                    redone in float64 when 1 - arg^2 < 1e-4 (near-coalescent roots) */
+} adot_precision;
+
+/* Boundary kinds. A ghost cell outside each end supplies the edge state. */
+typedef enum {
+  ADOT_BC_TRANSMISSIVE = 0, /* ghost = adjacent cell (zero jump, zero fluctuation) */
+  ADOT_BC_PERIODIC = 1,     /* both ends: the domain wraps */
+  ADOT_BC_INFLOW_Q = 2,     /* ghost q = value[0]; h, z copied */
+  ADOT_BC_OUTFLOW_H = 3,    /* ghost h = value[0]; q, z copied */
+  ADOT_BC_INFLOW_QZ = 4     /* ghost q = value[0], z = value[1] - value[2] * t; h copied */
+} adot_bc;
+
+typedef struct {
+  int32_t kind;     /* adot_law_kind */
+  double g;         /* gravitational acceleration [m/s^2] */
+  double xi;        /* 1 / (1 - p), p = bed porosity (Eq. SV-Ex3) */
+  double Ag;        /* Grass coefficient [s^2/m] */
+  double s_rel;     /* MPM: relative grain density */
+  double d50;       /* MPM: median grain size [m] */
+  double manning_n; /* MPM: Manning coefficient [s/m^(1/3)] */
+} adot_law;
+
+typedef struct {
+  int64_t n_cells;          /* >= 1 */
+  double x_min, x_max;      /* domain, x_max > x_min */
+  double cfl;               /* dt = cfl * dx / max_i max(|l1|, |l3|)(W_i), 0 < cfl <= 1 */
+  adot_law law;
+  int32_t precision;        /* adot_precision */
+  int32_t bc_left, bc_right;
+  double bc_left_value[3], bc_right_value[3];
+  int32_t block_threads;    /* threads per block of the step kernel; 0 = tuned default */
+  int32_t steps_per_graph;  /* time steps captured per CUDA graph; 0 = default (48) */
+  int32_t device;           /* CUDA device ordinal; -1 = the calling thread's current device */
+} adot_config;
+
+typedef struct adot_ctx adot_ctx;
+
+/* Creates a context: validates cfg (ADOT_E_INVALID_ARG on a bad value; both ends
+ * must be periodic or neither), makes cfg->device current (unless -1), allocates
+ * the device state and control block on it and binds `cuda_stream` (a cudaStream_t, or NULL). The
+ * state is zero until adot_set_state. *out receives the context or NULL. */
+adot_status adot_create(const adot_config* cfg, void* cuda_stream, adot_ctx** out);
+
+/* Frees everything the context owns. Accepts NULL. */
+void adot_destroy(adot_ctx* ctx);
+
+/* Copies the state in (n_cells float64 values each), resets time to t0 and the
+ * step counter to 0, and computes the first time step's CFL maximum.
+ * ADOT_E_NONPOSITIVE_DEPTH / ADOT_E_NONFINITE if the state is not admissible. */
+adot_status adot_set_state(adot_ctx* ctx, const double* h, const double* q, const double* z,
+                           int on_device, double t0);
+
+/* Copies the current state out (float-float states are summed to float64). */
+adot_status adot_get_state(adot_ctx* ctx, double* h, double* q, double* z, int on_device);
+
+/* Advances n_steps >= 0 time steps (Eq. scheme) with no end time, then waits
+ * for the stream and reports the time and the last step's dt (either pointer
+ * may be NULL) and the first device-side error. */
+adot_status adot_step(adot_ctx* ctx, int64_t n_steps, double* t_out, double* dt_last_out);
+
+/* Enqueues n_steps steps on the stream and returns without waiting (errors
+ * surface at the next synchronising call: adot_step, adot_run_to, adot_query). */
+adot_status adot_enqueue_steps(adot_ctx* ctx, int64_t n_steps);
+
+/* Advances until the time reaches t_end (the last step is shortened to land on
+ * it exactly). *steps_out (may be NULL) receives the steps taken by this call. */
+adot_status adot_run_to(adot_ctx* ctx, double t_end, int64_t* steps_out);
+
+/* Waits for the stream; reports time, total steps since adot_set_state and the
+ * last dt (NULL pointers are skipped) and the first device-side error. */
+adot_status adot_query(adot_ctx* ctx, double* t_out, int64_t* steps_out, double* dt_last_out);
+
+/* DOT fluctuations of n independent edges (Eq. DOTjumpN, G = 3, segment path),
+ * in the context's law and precision. WL, WR: [3][n] left and right states;
+ * Dminus, Dplus: [3][n] outputs. rho_max_out (may be NULL): the largest
+ * max(|l1|, |l3|) met at any quadrature node. n = 0 is valid and writes nothing.
+ * In ADOT_FP32 the inputs are first rounded to float-float, as the state is. */
+adot_status adot_fluctuations(adot_ctx* ctx, const double* WL, const double* WR, int64_t n,
+                              double* Dminus, double* Dplus, double* rho_max_out,
+                              int on_device);
+
+/* Sums over the cells of h, q and z (float64, fixed-order tree: the result is
+ * bit-reproducible). Multiply by dx for the integrals. */
+adot_status adot_conserved_sums(adot_ctx* ctx, double sums_out[3]);
+
+/* Name of a status code (static string). */
+const char* adot_status_string(adot_status s);
+
+/* Library version string (static). */
+const char* adot_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ADOT_H */

@@ -1,0 +1,268 @@
+"""Thin ctypes binding of libadot.so (the C ABI of include/adot.h).
+
+Functions carry the C names and only marshal arguments: numpy arrays are
+passed as host pointers (on_device=0), torch CUDA tensors as device pointers
+(on_device=1); every step of the computation runs in the library's CUDA
+kernels. Loading fails loudly when the library has not been built: there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libadot.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "adot.h")
+
+OK, E_INVALID_ARG, E_NONPOSITIVE_DEPTH, E_NONFINITE, E_NONHYPERBOLIC, E_CUDA, E_TIMEOUT, \
+    E_UNSUPPORTED = range(8)
+LAW_GRASS, LAW_MPM = 0, 1
+FP64, FP32 = 0, 1
+BC_TRANSMISSIVE, BC_PERIODIC, BC_INFLOW_Q, BC_OUTFLOW_H, BC_INFLOW_QZ = range(5)
+
+
+class AdotError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = status_string(status) if _lib is not None else str(status)
+        super().__init__(f"{where}: {msg} (status {status})")
+
+
+class Law(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("g", ctypes.c_double), ("xi", ctypes.c_double),
+                ("Ag", ctypes.c_double), ("s_rel", ctypes.c_double), ("d50", ctypes.c_double),
+                ("manning_n", ctypes.c_double)]
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("n_cells", ctypes.c_int64), ("x_min", ctypes.c_double),
+                ("x_max", ctypes.c_double), ("cfl", ctypes.c_double), ("law", Law),
+                ("precision", ctypes.c_int32), ("bc_left", ctypes.c_int32),
+                ("bc_right", ctypes.c_int32), ("bc_left_value", ctypes.c_double * 3),
+                ("bc_right_value", ctypes.c_double * 3), ("block_threads", ctypes.c_int32),
+                ("steps_per_graph", ctypes.c_int32), ("device", ctypes.c_int32)]
+
+
+_lib = None
+_P = ctypes.c_void_p
+_D = ctypes.POINTER(ctypes.c_double)
+
+
+def lib() -> ctypes.CDLL:
+    """Loads libadot.so (raises if it is missing)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is not built: call paper_1912_04791_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        i32, i64, dbl = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+        sig = {
+            "adot_create": ([ctypes.POINTER(Config), _P, ctypes.POINTER(_P)], i32),
+            "adot_destroy": ([_P], None),
+            "adot_set_state": ([_P, _P, _P, _P, i32, dbl], i32),
+            "adot_get_state": ([_P, _P, _P, _P, i32], i32),
+            "adot_step": ([_P, i64, _D, _D], i32),
+            "adot_enqueue_steps": ([_P, i64], i32),
+            "adot_run_to": ([_P, dbl, ctypes.POINTER(i64)], i32),
+            "adot_query": ([_P, _D, ctypes.POINTER(i64), _D], i32),
+            "adot_fluctuations": ([_P, _P, _P, i64, _P, _P, _D, i32], i32),
+            "adot_conserved_sums": ([_P, _D], i32),
+            "adot_status_string": ([i32], ctypes.c_char_p),
+            "adot_version": ([], ctypes.c_char_p),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def header_functions() -> list[str]:
+    """Names of the functions include/adot.h declares."""
+    with open(HEADER) as fh:
+        text = fh.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(adot_\w+)\s*\(", text)))
+
+
+def status_string(st: int) -> str:
+    return lib().adot_status_string(st).decode()
+
+
+def version() -> str:
+    return lib().adot_version().decode()
+
+
+def _check(st: int, where: str):
+    if st != OK:
+        raise AdotError(st, where)
+
+
+def _ptr(a, n=None):
+    """(address, on_device) of a float64 contiguous numpy array or torch tensor."""
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("numpy arrays must be contiguous float64")
+        if n is not None and a.size != n:
+            raise ValueError(f"expected {n} values, got {a.size}")
+        return a.ctypes.data, 0
+    import torch  # only for device memory
+    if not isinstance(a, torch.Tensor):
+        raise TypeError("expected a numpy array or a torch tensor")
+    if a.dtype != torch.float64 or not a.is_contiguous():
+        raise ValueError("tensors must be contiguous float64")
+    if n is not None and a.numel() != n:
+        raise ValueError(f"expected {n} values, got {a.numel()}")
+    return a.data_ptr(), (1 if a.is_cuda else 0)
+
+
+def make_config(n_cells, x_min, x_max, cfl, Ag, xi, precision=FP32, bc_left=BC_TRANSMISSIVE,
+                bc_right=BC_TRANSMISSIVE, bcl=(0.0, 0.0, 0.0), bcr=(0.0, 0.0, 0.0), g=9.81,
+                law=LAW_GRASS, s_rel=0.0, d50=0.0, manning_n=0.0, block_threads=0,
+                steps_per_graph=0, device=-1) -> Config:
+    c = Config()
+    c.n_cells = int(n_cells)
+    c.x_min, c.x_max, c.cfl = float(x_min), float(x_max), float(cfl)
+    c.law = Law(law, g, xi, Ag, s_rel, d50, manning_n)
+    c.precision = precision
+    c.bc_left, c.bc_right = bc_left, bc_right
+    for i in range(3):
+        c.bc_left_value[i] = float(bcl[i])
+        c.bc_right_value[i] = float(bcr[i])
+    c.block_threads = block_threads
+    c.steps_per_graph = steps_per_graph
+    c.device = device
+    return c
+
+
+def config_for(problem, precision=FP32, **kw) -> Config:
+    """Config of a workloads.Problem."""
+    return make_config(problem.n, problem.x_min, problem.x_max, problem.cfl, problem.Ag,
+                       problem.xi, precision, problem.bc_left, problem.bc_right, problem.bcl,
+                       problem.bcr, problem.g, **kw)
+
+
+def adot_create(cfg: Config, stream=None) -> int:
+    s = stream
+    if s is not None and not isinstance(s, int):
+        s = s.cuda_stream  # torch.cuda.Stream
+    out = _P()
+    _check(lib().adot_create(ctypes.byref(cfg), s, ctypes.byref(out)), "adot_create")
+    return out.value
+
+
+def adot_destroy(ctx: int) -> None:
+    lib().adot_destroy(ctx)
+
+
+def adot_set_state(ctx: int, h, q, z, t0: float = 0.0, n=None) -> None:
+    (ph, dh), (pq, dq), (pz, dz) = _ptr(h, n), _ptr(q, n), _ptr(z, n)
+    if not dh == dq == dz:
+        raise ValueError("h, q, z must all be on the host or all on the device")
+    _check(lib().adot_set_state(ctx, ph, pq, pz, dh, t0), "adot_set_state")
+
+
+def adot_get_state(ctx: int, h, q, z) -> None:
+    (ph, dh), (pq, dq), (pz, dz) = _ptr(h), _ptr(q), _ptr(z)
+    if not dh == dq == dz:
+        raise ValueError("h, q, z must all be on the host or all on the device")
+    _check(lib().adot_get_state(ctx, ph, pq, pz, dh), "adot_get_state")
+
+
+def adot_step(ctx: int, n_steps: int):
+    t, dt = ctypes.c_double(), ctypes.c_double()
+    _check(lib().adot_step(ctx, n_steps, ctypes.byref(t), ctypes.byref(dt)), "adot_step")
+    return t.value, dt.value
+
+
+def adot_enqueue_steps(ctx: int, n_steps: int) -> None:
+    _check(lib().adot_enqueue_steps(ctx, n_steps), "adot_enqueue_steps")
+
+
+def adot_run_to(ctx: int, t_end: float) -> int:
+    s = ctypes.c_int64()
+    _check(lib().adot_run_to(ctx, t_end, ctypes.byref(s)), "adot_run_to")
+    return s.value
+
+
+def adot_query(ctx: int):
+    t, dt, s = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
+    _check(lib().adot_query(ctx, ctypes.byref(t), ctypes.byref(s), ctypes.byref(dt)), "adot_query")
+    return t.value, s.value, dt.value
+
+
+def adot_fluctuations(ctx: int, WL, WR, Dm=None, Dp=None):
+    """D-/+ of the edges WL -> WR ([3, n] float64, numpy or CUDA tensors).
+    Returns (Dm, Dp, rho_max)."""
+    n = WL.shape[1]
+    if Dm is None:
+        Dm = np.empty((3, n)) if isinstance(WL, np.ndarray) else WL.new_empty((3, n))
+    if Dp is None:
+        Dp = np.empty((3, n)) if isinstance(WL, np.ndarray) else WL.new_empty((3, n))
+    (pl, d1), (pr, d2), (pm, d3), (pp, d4) = _ptr(WL), _ptr(WR), _ptr(Dm), _ptr(Dp)
+    if not d1 == d2 == d3 == d4:
+        raise ValueError("all arrays must be on the host or all on the device")
+    rho = ctypes.c_double()
+    _check(lib().adot_fluctuations(ctx, pl, pr, n, pm, pp, ctypes.byref(rho), d1),
+           "adot_fluctuations")
+    return Dm, Dp, rho.value
+
+
+def adot_conserved_sums(ctx: int) -> np.ndarray:
+    out = (ctypes.c_double * 3)()
+    _check(lib().adot_conserved_sums(ctx, out), "adot_conserved_sums")
+    return np.array(out[:])
+
+
+class Solver:
+    """Owning wrapper around one context."""
+
+    def __init__(self, cfg: Config, stream=None):
+        self.cfg = cfg
+        self.n = cfg.n_cells
+        self.ctx = adot_create(cfg, stream)
+
+    def set_state(self, h, q, z, t0=0.0):
+        adot_set_state(self.ctx, h, q, z, t0, self.n)
+
+    def get_state(self):
+        h, q, z = np.empty(self.n), np.empty(self.n), np.empty(self.n)
+        adot_get_state(self.ctx, h, q, z)
+        return h, q, z
+
+    def step(self, n):
+        return adot_step(self.ctx, n)
+
+    def run_to(self, t_end):
+        return adot_run_to(self.ctx, t_end)
+
+    def query(self):
+        return adot_query(self.ctx)
+
+    def fluctuations(self, WL, WR):
+        return adot_fluctuations(self.ctx, WL, WR)
+
+    def conserved_sums(self):
+        return adot_conserved_sums(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            adot_destroy(self.ctx)
+            self.ctx = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

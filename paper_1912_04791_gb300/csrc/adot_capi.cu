@@ -1,0 +1,440 @@
+// C-ABI runtime of the A-DOT library (declared in include/adot.h).
+//
+// A context owns two ping-pong state buffers, a device control block (time,
+// dt, step count and CFL maximum in three rotating slots plus a sticky status
+// word), host-pinned mirrors for status reads, and a CUDA graph of
+// `steps_per_graph` consecutive time-step launches. A run of steps replays the
+// graph whenever the step counter is at a multiple of 6 (the rotation period
+// of the three control slots and the two buffers) and launches single steps
+// otherwise, so the graph's fixed kernel arguments always match.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "../../include/adot.h"
+#include "adot_internal.h"
+
+using namespace adot;
+
+struct adot_ctx {
+  adot_config cfg;
+  int device;
+  int prec;  // 0 = float64, 1 = float-float
+  int law;
+  int block;
+  int steps_per_graph;
+  cudaStream_t stream;
+  bool own_stream;
+  cudaStream_t cap_stream;
+  StepParams p;
+  void* buf[2][3];  // [ping-pong][h, q, z]
+  int cur;          // buffer holding the current state
+  int phase;        // steps launched since set_state, mod 6
+  Ctl* d_ctl;
+  Ctl* h_ctl;       // pinned mirror
+  double* d_io;     // 3 * n float64 staging for conversions
+  double* d_partial;
+  double* d_sums;
+  double* h_sums;   // pinned, 3
+  double* d_fl;     // 12 * fl_cap float64 for host-pointer fluctuation calls
+  int64_t fl_cap;
+  unsigned long long* d_flrho;  // fluctuation scratch: rho bits + status
+  unsigned long long* h_flrho;  // pinned mirror (2 words)
+  cudaGraphExec_t graph;
+  bool graph_ready;
+  bool state_set;
+  double t_end_dev;  // t_end currently stored in the control block
+};
+
+namespace {
+
+
+#define CK(expr)                               \
+  do {                                         \
+    cudaError_t _e = (expr);                   \
+    if (_e != cudaSuccess) return ADOT_E_CUDA; \
+  } while (0)
+
+adot_status status_from_bits(unsigned bits) {
+  if (bits & ST_NONFINITE) return ADOT_E_NONFINITE;
+  if (bits & ST_DEPTH) return ADOT_E_NONPOSITIVE_DEPTH;
+  if (bits & ST_NONHYPERBOLIC) return ADOT_E_NONHYPERBOLIC;
+  if (bits & ST_TIMEOUT) return ADOT_E_TIMEOUT;
+  return ADOT_OK;
+}
+
+bool valid_bc(int k) { return k >= ADOT_BC_TRANSMISSIVE && k <= ADOT_BC_INFLOW_QZ; }
+
+adot_status validate(const adot_config* c) {
+  if (!c) return ADOT_E_INVALID_ARG;
+  if (c->n_cells < 1) return ADOT_E_INVALID_ARG;
+  if (!(c->x_max > c->x_min) || !isfinite(c->x_min) || !isfinite(c->x_max)) return ADOT_E_INVALID_ARG;
+  if (!(c->cfl > 0.0 && c->cfl <= 1.0)) return ADOT_E_INVALID_ARG;
+  if (!(c->law.g > 0.0) || !(c->law.xi > 0.0) || !isfinite(c->law.Ag)) return ADOT_E_INVALID_ARG;
+  if (c->law.kind == ADOT_LAW_MPM) {
+    if (!(c->law.s_rel > 1.0) || !(c->law.d50 > 0.0) || !(c->law.manning_n >= 0.0))
+      return ADOT_E_INVALID_ARG;
+  } else if (c->law.kind != ADOT_LAW_GRASS) {
+    return ADOT_E_INVALID_ARG;
+  }
+  if (c->precision != ADOT_FP64 && c->precision != ADOT_FP32) return ADOT_E_INVALID_ARG;
+  if (!valid_bc(c->bc_left) || !valid_bc(c->bc_right)) return ADOT_E_INVALID_ARG;
+  if ((c->bc_left == ADOT_BC_PERIODIC) != (c->bc_right == ADOT_BC_PERIODIC)) return ADOT_E_INVALID_ARG;
+  for (int i = 0; i < 3; ++i)
+    if (!isfinite(c->bc_left_value[i]) || !isfinite(c->bc_right_value[i])) return ADOT_E_INVALID_ARG;
+  if (c->block_threads != 0 && !step_block_supported(c->block_threads)) return ADOT_E_INVALID_ARG;
+  if (c->steps_per_graph < 0 || c->device < -1) return ADOT_E_INVALID_ARG;
+  return ADOT_OK;
+}
+
+StateF32 st32(adot_ctx* c, int which) {
+  return StateF32{(float2*)c->buf[which][0], (float2*)c->buf[which][1], (float2*)c->buf[which][2]};
+}
+StateF64 st64(adot_ctx* c, int which) {
+  return StateF64{(double*)c->buf[which][0], (double*)c->buf[which][1], (double*)c->buf[which][2]};
+}
+
+cudaError_t launch_one(adot_ctx* c, cudaStream_t s, int cur, int phase) {
+  const int slot = phase % 3;
+  if (c->prec == ADOT_FP32)
+    return launch_step_f32(c->p, c->law, c->block, st32(c, cur), st32(c, 1 - cur), slot, s);
+  return launch_step_f64(c->p, c->law, c->block, st64(c, cur), st64(c, 1 - cur), slot, s);
+}
+
+adot_status build_graph(adot_ctx* c) {
+  if (c->graph_ready) return ADOT_OK;
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t err = cudaSuccess;
+  for (int k = 0; k < c->steps_per_graph && err == cudaSuccess; ++k)
+    err = launch_one(c, c->cap_stream, k & 1, k % 6);
+  cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g);
+  if (err != cudaSuccess || e2 != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return ADOT_E_CUDA;
+  }
+  err = cudaGraphInstantiate(&c->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (err != cudaSuccess) return ADOT_E_CUDA;
+  c->graph_ready = true;
+  return ADOT_OK;
+}
+
+adot_status enqueue(adot_ctx* c, int64_t n) {
+  while (n > 0) {
+    if (c->phase == 0 && n >= c->steps_per_graph) {
+      adot_status st = build_graph(c);
+      if (st) return st;
+      CK(cudaGraphLaunch(c->graph, c->stream));
+      n -= c->steps_per_graph;  // a multiple of 6: phase and buffer unchanged
+    } else {
+      CK(launch_one(c, c->stream, c->cur, c->phase));
+      c->cur ^= 1;
+      c->phase = (c->phase + 1) % 6;
+      --n;
+    }
+  }
+  return ADOT_OK;
+}
+
+adot_status set_t_end(adot_ctx* c, double t_end) {
+  if (c->t_end_dev == t_end) return ADOT_OK;
+  // the pinned mirror is only written while the stream is idle (callers sync)
+  CK(cudaStreamSynchronize(c->stream));
+  c->h_ctl->t_end = t_end;
+  CK(cudaMemcpyAsync(&c->d_ctl->t_end, &c->h_ctl->t_end, sizeof(double), cudaMemcpyHostToDevice,
+                     c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->t_end_dev = t_end;
+  return ADOT_OK;
+}
+
+adot_status read_ctl(adot_ctx* c) {
+  CK(cudaMemcpyAsync(c->h_ctl, c->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return ADOT_OK;
+}
+
+void free_ctx(adot_ctx* c) {
+  if (!c) return;
+  if (c->graph_ready) cudaGraphExecDestroy(c->graph);
+  for (int b = 0; b < 2; ++b)
+    for (int k = 0; k < 3; ++k)
+      if (c->buf[b][k]) cudaFree(c->buf[b][k]);
+  if (c->d_ctl) cudaFree(c->d_ctl);
+  if (c->h_ctl) cudaFreeHost(c->h_ctl);
+  if (c->d_io) cudaFree(c->d_io);
+  if (c->d_partial) cudaFree(c->d_partial);
+  if (c->d_sums) cudaFree(c->d_sums);
+  if (c->h_sums) cudaFreeHost(c->h_sums);
+  if (c->d_fl) cudaFree(c->d_fl);
+  if (c->d_flrho) cudaFree(c->d_flrho);
+  if (c->h_flrho) cudaFreeHost(c->h_flrho);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  free(c);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* adot_version(void) { return "adot-gb300 0.1 (sm_103a)"; }
+
+const char* adot_status_string(adot_status s) {
+  switch (s) {
+    case ADOT_OK: return "ok";
+    case ADOT_E_INVALID_ARG: return "invalid argument";
+    case ADOT_E_NONPOSITIVE_DEPTH: return "non-positive water depth";
+    case ADOT_E_NONFINITE: return "non-finite value";
+    case ADOT_E_NONHYPERBOLIC: return "non-hyperbolic state";
+    case ADOT_E_CUDA: return "CUDA error";
+    case ADOT_E_TIMEOUT: return "device wait timed out";
+    case ADOT_E_UNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+adot_status adot_create(const adot_config* cfg, void* cuda_stream, adot_ctx** out) {
+  if (!out) return ADOT_E_INVALID_ARG;
+  *out = nullptr;
+  adot_status st = validate(cfg);
+  if (st) return st;
+  int dev = 0;
+  if (cfg->device >= 0 && cudaSetDevice(cfg->device) != cudaSuccess) return ADOT_E_CUDA;
+  if (cudaGetDevice(&dev) != cudaSuccess) return ADOT_E_CUDA;
+  adot_ctx* c = (adot_ctx*)calloc(1, sizeof(adot_ctx));
+  if (!c) return ADOT_E_CUDA;
+  c->cfg = *cfg;
+  c->device = dev;
+  c->prec = cfg->precision;
+  c->law = cfg->law.kind;
+  c->block = cfg->block_threads ? cfg->block_threads : 256;
+  int spg = cfg->steps_per_graph ? cfg->steps_per_graph : 48;
+  c->steps_per_graph = ((spg + 5) / 6) * 6;
+  c->t_end_dev = INFINITY;
+  const int64_t n = cfg->n_cells;
+
+  StepParams& p = c->p;
+  p.n = n;
+  p.dx = (cfg->x_max - cfg->x_min) / (double)n;
+  p.cfl = cfg->cfl;
+  p.periodic = (cfg->bc_left == ADOT_BC_PERIODIC) ? 1 : 0;
+  p.bc_left = cfg->bc_left;
+  p.bc_right = cfg->bc_right;
+  for (int i = 0; i < 3; ++i) {
+    p.bcl[i] = cfg->bc_left_value[i];
+    p.bcr[i] = cfg->bc_right_value[i];
+  }
+  const adot_law& L = cfg->law;
+  double K3 = 3.0 * L.xi * L.Ag;
+  double mpm_c = 0.0, mpm_scale = 0.0;
+  if (L.kind == ADOT_LAW_MPM) {
+    mpm_c = L.manning_n * L.manning_n / ((L.s_rel - 1.0) * L.d50);
+    mpm_scale = L.xi * sqrt(L.g * (L.s_rel - 1.0) * L.d50 * L.d50 * L.d50);
+  }
+  p.ld = LawT<double>{L.g, K3, mpm_c, mpm_scale};
+  p.lf = LawT<float>{(float)L.g, (float)K3, (float)mpm_c, (float)mpm_scale};
+
+  cudaError_t e = cudaSuccess;
+  if (cuda_stream) {
+    c->stream = (cudaStream_t)cuda_stream;
+  } else {
+    e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    c->own_stream = true;
+  }
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+  const size_t elem = (c->prec == ADOT_FP32) ? sizeof(float2) : sizeof(double);
+  for (int b = 0; b < 2 && e == cudaSuccess; ++b)
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaMalloc(&c->buf[b][k], elem * (size_t)n);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_ctl, sizeof(Ctl));
+  if (e == cudaSuccess) e = cudaHostAlloc((void**)&c->h_ctl, sizeof(Ctl), cudaHostAllocDefault);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_partial, sizeof(double) * 3 * sums_partial_blocks(n));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_sums, sizeof(double) * 3);
+  if (e == cudaSuccess) e = cudaHostAlloc((void**)&c->h_sums, sizeof(double) * 3, cudaHostAllocDefault);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_flrho, sizeof(unsigned long long) * 2);
+  if (e == cudaSuccess) e = cudaHostAlloc((void**)&c->h_flrho, sizeof(unsigned long long) * 2, cudaHostAllocDefault);
+  if (e == cudaSuccess && c->prec == ADOT_FP32) e = cudaMalloc((void**)&c->d_io, sizeof(double) * 3 * (size_t)n);
+  if (e == cudaSuccess) {
+    memset(c->h_ctl, 0, sizeof(Ctl));
+    c->h_ctl->t_end = INFINITY;
+    e = cudaMemcpyAsync(c->d_ctl, c->h_ctl, sizeof(Ctl), cudaMemcpyHostToDevice, c->stream);
+  }
+  for (int b = 0; b < 2 && e == cudaSuccess; ++b)
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k)
+      e = cudaMemsetAsync(c->buf[b][k], 0, elem * (size_t)n, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    free_ctx(c);
+    return ADOT_E_CUDA;
+  }
+  *out = c;
+  return ADOT_OK;
+}
+
+void adot_destroy(adot_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  free_ctx(c);
+}
+
+adot_status adot_set_state(adot_ctx* c, const double* h, const double* q, const double* z,
+                           int on_device, double t0) {
+  if (!c || !h || !q || !z || !isfinite(t0)) return ADOT_E_INVALID_ARG;
+  const int64_t n = c->p.n;
+  const size_t bytes = sizeof(double) * (size_t)n;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const double* src[3] = {h, q, z};
+  CK(cudaStreamSynchronize(c->stream));
+  for (int k = 0; k < 3; ++k) {
+    if (c->prec == ADOT_FP32) {
+      CK(cudaMemcpyAsync(c->d_io + k * n, src[k], bytes, kind, c->stream));
+      CK(launch_to_ff(c->d_io + k * n, (float2*)c->buf[0][k], n, c->stream));
+    } else {
+      CK(cudaMemcpyAsync(c->buf[0][k], src[k], bytes, kind, c->stream));
+    }
+  }
+  memset(c->h_ctl, 0, sizeof(Ctl));
+  c->h_ctl->s[0].t = t0;
+  c->h_ctl->t_end = INFINITY;
+  c->t_end_dev = INFINITY;
+  CK(cudaMemcpyAsync(c->d_ctl, c->h_ctl, sizeof(Ctl), cudaMemcpyHostToDevice, c->stream));
+  c->cur = 0;
+  c->phase = 0;
+  if (c->prec == ADOT_FP32)
+    CK(launch_rho_f32(c->p, c->law, st32(c, 0), 0, c->stream));
+  else
+    CK(launch_rho_f64(c->p, c->law, st64(c, 0), 0, c->stream));
+  adot_status st = read_ctl(c);
+  if (st) return st;
+  c->state_set = true;
+  return status_from_bits(c->h_ctl->status);
+}
+
+adot_status adot_get_state(adot_ctx* c, double* h, double* q, double* z, int on_device) {
+  if (!c || !h || !q || !z) return ADOT_E_INVALID_ARG;
+  const int64_t n = c->p.n;
+  const size_t bytes = sizeof(double) * (size_t)n;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  double* dst[3] = {h, q, z};
+  for (int k = 0; k < 3; ++k) {
+    if (c->prec == ADOT_FP32) {
+      CK(launch_from_ff((const float2*)c->buf[c->cur][k], c->d_io + k * n, n, c->stream));
+      CK(cudaMemcpyAsync(dst[k], c->d_io + k * n, bytes, kind, c->stream));
+    } else {
+      CK(cudaMemcpyAsync(dst[k], c->buf[c->cur][k], bytes, kind, c->stream));
+    }
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  return ADOT_OK;
+}
+
+adot_status adot_enqueue_steps(adot_ctx* c, int64_t n_steps) {
+  if (!c || n_steps < 0 || !c->state_set) return ADOT_E_INVALID_ARG;
+  adot_status st = set_t_end(c, INFINITY);
+  if (st) return st;
+  return enqueue(c, n_steps);
+}
+
+adot_status adot_query(adot_ctx* c, double* t_out, int64_t* steps_out, double* dt_last_out) {
+  if (!c) return ADOT_E_INVALID_ARG;
+  adot_status st = read_ctl(c);
+  if (st) return st;
+  const CtlSlot& s = c->h_ctl->s[c->phase % 3];
+  if (t_out) *t_out = s.t;
+  if (steps_out) *steps_out = s.steps;
+  if (dt_last_out) *dt_last_out = s.dt;
+  return status_from_bits(c->h_ctl->status);
+}
+
+adot_status adot_step(adot_ctx* c, int64_t n_steps, double* t_out, double* dt_last_out) {
+  adot_status st = adot_enqueue_steps(c, n_steps);
+  if (st) return st;
+  return adot_query(c, t_out, nullptr, dt_last_out);
+}
+
+adot_status adot_run_to(adot_ctx* c, double t_end, int64_t* steps_out) {
+  if (!c || !c->state_set || !isfinite(t_end)) return ADOT_E_INVALID_ARG;
+  adot_status st = read_ctl(c);
+  if (st) return st;
+  const long long steps0 = c->h_ctl->s[c->phase % 3].steps;
+  if (steps_out) *steps_out = 0;
+  if (c->h_ctl->s[c->phase % 3].t >= t_end) return status_from_bits(c->h_ctl->status);
+  st = set_t_end(c, t_end);
+  if (st) return st;
+  for (;;) {
+    // align to the graph's phase with single steps, then replay whole graphs
+    int64_t chunk = c->phase ? (6 - c->phase) : c->steps_per_graph;
+    st = enqueue(c, chunk);
+    if (st) return st;
+    st = read_ctl(c);
+    if (st) return st;
+    const CtlSlot& s = c->h_ctl->s[c->phase % 3];
+    if (steps_out) *steps_out = s.steps - steps0;
+    adot_status dev = status_from_bits(c->h_ctl->status);
+    if (dev) return dev;
+    if (!(s.t < t_end)) break;
+  }
+  return ADOT_OK;
+}
+
+adot_status adot_fluctuations(adot_ctx* c, const double* WL, const double* WR, int64_t n,
+                              double* Dminus, double* Dplus, double* rho_max_out, int on_device) {
+  if (!c || n < 0) return ADOT_E_INVALID_ARG;
+  if (n > 0 && (!WL || !WR || !Dminus || !Dplus)) return ADOT_E_INVALID_ARG;
+  if (n == 0) {
+    if (rho_max_out) *rho_max_out = 0.0;
+    return ADOT_OK;
+  }
+  const double *wl = WL, *wr = WR;
+  double *dm = Dminus, *dp = Dplus;
+  const size_t bytes = sizeof(double) * 3 * (size_t)n;
+  if (!on_device) {
+    if (c->fl_cap < n) {
+      if (c->d_fl) cudaFree(c->d_fl);
+      c->d_fl = nullptr;
+      c->fl_cap = 0;
+      CK(cudaMalloc((void**)&c->d_fl, 4 * bytes));
+      c->fl_cap = n;
+    }
+    double* base = c->d_fl;
+    CK(cudaMemcpyAsync(base, WL, bytes, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(base + 3 * n, WR, bytes, cudaMemcpyHostToDevice, c->stream));
+    wl = base;
+    wr = base + 3 * n;
+    dm = base + 6 * n;
+    dp = base + 9 * n;
+  }
+  CK(cudaMemsetAsync(c->d_flrho, 0, 2 * sizeof(unsigned long long), c->stream));
+  CK(launch_fluct(c->prec, c->law, c->p.lf, c->p.ld, wl, wr, n, dm, dp, c->d_flrho,
+                  (unsigned*)(c->d_flrho + 1), c->stream));
+  if (!on_device) {
+    CK(cudaMemcpyAsync(Dminus, dm, bytes, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(Dplus, dp, bytes, cudaMemcpyDeviceToHost, c->stream));
+  }
+  CK(cudaMemcpyAsync(c->h_flrho, c->d_flrho, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                     c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (rho_max_out) {
+    unsigned long long b = c->h_flrho[0];
+    double r;
+    memcpy(&r, &b, sizeof(r));
+    *rho_max_out = r;
+  }
+  return status_from_bits((unsigned)(c->h_flrho[1] & 0xffffffffu));
+}
+
+adot_status adot_conserved_sums(adot_ctx* c, double sums_out[3]) {
+  if (!c || !sums_out) return ADOT_E_INVALID_ARG;
+  if (c->prec == ADOT_FP32)
+    CK(launch_sums_f32(st32(c, c->cur), c->p.n, c->d_partial, c->d_sums, c->stream));
+  else
+    CK(launch_sums_f64(st64(c, c->cur), c->p.n, c->d_partial, c->d_sums, c->stream));
+  CK(cudaMemcpyAsync(c->h_sums, c->d_sums, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  for (int i = 0; i < 3; ++i) sums_out[i] = c->h_sums[i];
+  return ADOT_OK;
+}
+
+}  // extern "C"

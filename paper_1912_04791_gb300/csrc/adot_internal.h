@@ -1,0 +1,87 @@
+// Internal declarations shared by the kernel translation units and the C-ABI
+// runtime. Not part of the public interface (include/adot.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "adot_math.cuh"
+
+namespace adot {
+
+// One slot of the device control block. Step n reads slot n % 3, writes slot
+// (n+1) % 3 and clears the CFL maximum of slot (n+2) % 3, so no slot is read
+// and written by the same launch.
+struct CtlSlot {
+  double t;                     // time at the start of the step that reads the slot
+  double dt;                    // dt of the step that wrote the slot
+  long long steps;              // steps taken since the state was set
+  unsigned long long rho_bits;  // max spectral radius of the state (float bits or double bits)
+};
+
+struct Ctl {
+  CtlSlot s[3];
+  double t_end;     // steps are clipped to land on t_end; no work once t >= t_end
+  unsigned status;  // sticky ST_* bits
+  unsigned pad;
+};
+
+struct StateF32 {
+  float2* h;
+  float2* q;
+  float2* z;
+};
+
+struct StateF64 {
+  double* h;
+  double* q;
+  double* z;
+};
+
+// Parameters common to every time-step launch (fixed for a context).
+struct StepParams {
+  int64_t n;
+  double dx;
+  double cfl;
+  int periodic;
+  int bc_left, bc_right;
+  double bcl[3], bcr[3];
+  LawT<float> lf;
+  LawT<double> ld;
+  Ctl* ctl;
+};
+
+enum : int { BC_TRANSMISSIVE = 0, BC_PERIODIC = 1, BC_INFLOW_Q = 2, BC_OUTFLOW_H = 3, BC_INFLOW_QZ = 4 };
+
+// Supported block sizes of the step kernels.
+bool step_block_supported(int block);
+
+// One time step (Eq. scheme): fluctuations on every edge, update of every cell,
+// CFL maximum of the updated state. slot = step index mod 3.
+cudaError_t launch_step_f32(const StepParams& p, int law, int block, StateF32 in, StateF32 out,
+                            int slot, cudaStream_t s);
+cudaError_t launch_step_f64(const StepParams& p, int law, int block, StateF64 in, StateF64 out,
+                            int slot, cudaStream_t s);
+
+// CFL maximum of a state into ctl->s[slot].rho_bits (which must be zero), and
+// admissibility (h > 0, finite) into ctl->status.
+cudaError_t launch_rho_f32(const StepParams& p, int law, StateF32 st, int slot, cudaStream_t s);
+cudaError_t launch_rho_f64(const StepParams& p, int law, StateF64 st, int slot, cudaStream_t s);
+
+// float64 <-> float-float conversion of n values.
+cudaError_t launch_to_ff(const double* src, float2* dst, int64_t n, cudaStream_t s);
+cudaError_t launch_from_ff(const float2* src, double* dst, int64_t n, cudaStream_t s);
+
+// Stateless fluctuations of n edges; WL, WR, Dm, Dp are device [3][n] float64.
+// rho_bits (double bits) and status are device scalars updated with atomics.
+cudaError_t launch_fluct(int precision, int law, const LawT<float>& lf, const LawT<double>& ld,
+                         const double* WL, const double* WR, int64_t n, double* Dm, double* Dp,
+                         unsigned long long* rho_bits, unsigned* status, cudaStream_t s);
+
+// Fixed-order float64 sums of the three state arrays: partial has room for
+// sums_partial_blocks(n) * 3 doubles; out receives 3 doubles.
+int sums_partial_blocks(int64_t n);
+cudaError_t launch_sums_f32(StateF32 st, int64_t n, double* partial, double* out, cudaStream_t s);
+cudaError_t launch_sums_f64(StateF64 st, int64_t n, double* partial, double* out, cudaStream_t s);
+
+}  // namespace adot

@@ -1,0 +1,304 @@
+// Device math of the A-DOT scheme (arXiv 1912.04791), templated on the working
+// precision (float or double).
+//
+// One quadrature node of Eq. DOTjumpN needs, at the node state (h, q):
+//   step 1  the sediment-flux derivatives a = xi dq_s/dh, b = xi dq_s/dq
+//           (Eq. Grass / Eq. MPM with Eq. Shields);
+//   step 2  k1, k2 and phi (Eq. parameters, Eq. parameters_bis);
+//   step 3  the trigonometric roots of the characteristic polynomial
+//           (Eq. charPol, Eq. lambda);
+//   steps 4-5  |A| dW = R |Lambda| R^-1 dW (Eq. asbA, Eq. RR, Eq. RR-1).
+// Steps 4-5 are evaluated matrix-free, |A| dW = sum_i |l_i| r_i (l_i . dW),
+// which is the same product as the paper's three-matrix form applied to dW.
+// The three denominators d_i = (l_i - l_j)(l_i - l_k) share one reciprocal of
+// (l1-l2)(l1-l3)(l2-l3). The three cosines cos(phi/3 -+ pi/3), cos(phi/3) of
+// Eq. lambda come from one sincos through cos(x -+ pi/3) = C/2 +- (sqrt3/2) S.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace adot {
+
+enum : int { LAW_GRASS = 0, LAW_MPM = 1 };
+
+// Status bits recorded in the device control block.
+enum : unsigned {
+  ST_DEPTH = 1u,        // h <= 0
+  ST_NONFINITE = 2u,    // NaN / Inf
+  ST_NONHYPERBOLIC = 4u,
+  ST_TIMEOUT = 8u
+};
+
+// Closure parameters in the working precision, with the porosity factor xi
+// folded in where it multiplies.
+template <typename T>
+struct LawT {
+  T g;
+  T K3;         // Grass: 3 xi A_g, so b = K3 u^2 / h and a = -b u
+  T mpm_c;      // MPM: n^2 / ((s - 1) d50), theta = mpm_c u^2 h^(-1/3)
+  T mpm_scale;  // MPM: xi sqrt(g (s - 1) d50^3)
+};
+
+// Gap below which |A| dW switches to the Newton divided-difference form
+// (relative to c), and the zero band of a coalesced pair's slope; the same
+// reading the oracle uses for the coalescence case.
+constexpr double TAU_GAP = 1e-6;
+// Tolerance on |arg| - 1 before a node is declared non-hyperbolic.
+constexpr double TAU_HYP = 1e-6;
+// In float32 a node whose 1 - arg^2 is below this is redone in float64
+// (two roots within ~0.7 sqrt(1e-4) c of each other).
+constexpr float TAU_FP64_FALLBACK = 1e-4f;
+
+// Gauss-Legendre 3-point rule on [0, 1] (Eq. DOTjumpN with G = 3).
+constexpr double GL3_S0 = 0.1127016653792583115;  // 1/2 - sqrt(15)/10
+constexpr double GL3_S2 = 0.8872983346207416885;  // 1/2 + sqrt(15)/10
+constexpr double GL3_W0 = 5.0 / 18.0;
+constexpr double GL3_W1 = 8.0 / 18.0;
+
+__device__ __forceinline__ float d_sqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double d_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float d_rsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double d_rsqrt(double x) { return rsqrt(x); }
+__device__ __forceinline__ float d_acos(float x) { return acosf(x); }
+__device__ __forceinline__ double d_acos(double x) { return acos(x); }
+__device__ __forceinline__ void d_sincos(float x, float* s, float* c) { sincosf(x, s, c); }
+__device__ __forceinline__ void d_sincos(double x, double* s, double* c) { sincos(x, s, c); }
+__device__ __forceinline__ float d_rcbrt(float x) { return rcbrtf(x); }
+__device__ __forceinline__ double d_rcbrt(double x) { return rcbrt(x); }
+__device__ __forceinline__ float d_abs(float x) { return fabsf(x); }
+__device__ __forceinline__ double d_abs(double x) { return fabs(x); }
+__device__ __forceinline__ float d_min(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ double d_min(double a, double b) { return fmin(a, b); }
+__device__ __forceinline__ float d_max(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double d_max(double a, double b) { return fmax(a, b); }
+
+// Step 1: a = xi dq_s/dh, b = xi dq_s/dq at (h, q), given 1/h and u = q/h.
+// Grass (Eq. Grass, five-step procedure step 1): dq_s/dq = 3 A_g u^2/h and
+// dq_s/dh = -3 A_g u^3/h, i.e. b = K3 u^2/h, a = -b u.
+// MPM (Eq. MPM, Eq. Shields, Manning s_f = n^2 u^2 h^(-4/3)):
+// theta = mpm_c u^2 h^(-1/3); q_s = sign(u) 8 (theta - 0.047)^1.5 scale;
+// dtheta/dq = 2 mpm_c u h^(-4/3), dtheta/dh = -(7/3) theta / h.
+template <typename T, int LAW>
+__device__ __forceinline__ void sediment_derivs(const LawT<T>& L, T h, T q, T inv_h, T u, T& a,
+                                                T& b) {
+  if constexpr (LAW == LAW_GRASS) {
+    (void)h;
+    (void)q;
+    b = L.K3 * u * u * inv_h;
+    a = -b * u;
+  } else {
+    T r3 = d_rcbrt(h);
+    T theta = L.mpm_c * u * u * r3;
+    T ex = theta - T(0.047);
+    if (ex > T(0)) {
+      T s = L.mpm_scale * T(12) * d_sqrt(ex);  // scale * dPhi/dtheta
+      b = s * T(2) * L.mpm_c * d_abs(u) * r3 * inv_h;
+      T sg = (q > T(0)) ? T(1) : ((q < T(0)) ? T(-1) : T(0));
+      a = -s * sg * (T(7) / T(3)) * theta * inv_h;
+    } else {
+      a = T(0);
+      b = T(0);
+    }
+  }
+}
+
+// Eigen-data of A at one state.
+template <typename T>
+struct Eig {
+  T u, c, c2, inv_c2, a, b;
+  T l1, l2, l3;  // l1 <= l2 <= l3
+  T arg;         // k2 / sqrt(4 k1^3) before clamping
+};
+
+// Steps 1-3: derivatives, k1, k2, phi, and the three roots of Eq. lambda.
+template <typename T, int LAW>
+__device__ __forceinline__ void node_eig(const LawT<T>& L, T h, T q, Eig<T>& e) {
+  const T inv_h = T(1) / h;
+  const T u = q * inv_h;
+  const T c2 = L.g * h;
+  const T rc = d_rsqrt(c2);  // 1/c
+  const T c = c2 * rc;
+  const T Fr = u * rc;
+  T a, b;
+  sediment_derivs<T, LAW>(L, h, q, inv_h, u, a, b);
+  const T k1 = T(3) + Fr * Fr + T(3) * b;
+  const T k2 = Fr * (T(18) * (T(1) + b) - T(2) * Fr * Fr) + T(27) * a * rc;
+  const T rk = d_rsqrt(k1);
+  const T arg = T(0.5) * k2 * (rk * rk * rk);
+  const T argc = d_min(d_max(arg, T(-1)), T(1));
+  const T phi3 = d_acos(argc) * T(1.0 / 3.0);
+  T S, C;
+  d_sincos(phi3, &S, &C);
+  const T m = T(2.0 / 3.0) * (k1 * rk);  // (2/3) sqrt(k1)
+  const T F = T(2.0 / 3.0) * Fr;
+  const T hc = T(0.5) * C;
+  const T hs = T(0.86602540378443864676) * S;  // (sqrt 3 / 2) S
+  e.u = u;
+  e.c = c;
+  e.c2 = c2;
+  e.inv_c2 = rc * rc;
+  e.a = a;
+  e.b = b;
+  e.l1 = c * (F - m * (hc + hs));  // cos(phi/3 - pi/3) = C/2 + (sqrt3/2) S
+  e.l2 = c * (F - m * (hc - hs));  // cos(phi/3 + pi/3) = C/2 - (sqrt3/2) S
+  e.l3 = c * (F + m * C);
+  e.arg = arg;
+}
+
+// A(W) v with A from Eq. W&A_definition.
+template <typename T>
+__device__ __forceinline__ void A_times(const Eig<T>& e, T v0, T v1, T v2, T& y0, T& y1, T& y2) {
+  y0 = v1;
+  y1 = (e.c2 - e.u * e.u) * v0 + T(2) * e.u * v1 + e.c2 * v2;
+  y2 = e.a * v0 + e.b * v1;
+}
+
+// Steps 4-5 applied to dW: |A| dW = sum_i |l_i| r_i (l_i . dW) with
+// r_i = [1, l_i, (u - l_i)^2/c^2 - 1] (Eq. RR) and
+// l_i = [c^2 - u^2 + l_j l_k, 2u - l_j - l_k, c^2] / ((l_i - l_j)(l_i - l_k)) (Eq. RR-1).
+template <typename T>
+__device__ __forceinline__ void abs_A_times_eigvec(const Eig<T>& e, T dh, T dq, T dz, T& x0, T& x1,
+                                                   T& x2) {
+  const T l1 = e.l1, l2 = e.l2, l3 = e.l3;
+  const T e12 = l1 - l2, e13 = l1 - l3, e23 = l2 - l3;
+  const T invP = T(1) / (e12 * e13 * e23);
+  const T w0 = e.c2 - e.u * e.u;
+  const T tu = T(2) * e.u;
+  const T cz = e.c2 * dz;
+  const T p1 = (w0 + l2 * l3) * dh + (tu - l2 - l3) * dq + cz;
+  const T p2 = (w0 + l3 * l1) * dh + (tu - l3 - l1) * dq + cz;
+  const T p3 = (w0 + l1 * l2) * dh + (tu - l1 - l2) * dq + cz;
+  // 1/d1 = e23/P, 1/d2 = -e13/P, 1/d3 = e12/P
+  const T al1 = d_abs(l1) * p1 * (e23 * invP);
+  const T al2 = -d_abs(l2) * p2 * (e13 * invP);
+  const T al3 = d_abs(l3) * p3 * (e12 * invP);
+  const T v1 = e.u - l1, v2 = e.u - l2, v3 = e.u - l3;
+  x0 = al1 + al2 + al3;
+  x1 = al1 * l1 + al2 * l2 + al3 * l3;
+  x2 = (al1 * v1 * v1 + al2 * v2 * v2 + al3 * v3 * v3) * e.inv_c2 - x0;
+}
+
+// First divided difference of |x| with the coalescence reading: a pair closer
+// than tau is one double root m = (a+b)/2 with slope sign(m), 0 if |m| < tau.
+template <typename T>
+__device__ __forceinline__ T dd1_abs(T a, T b, T tau) {
+  if (d_abs(a - b) < tau) {
+    T m = T(0.5) * (a + b);
+    if (d_abs(m) < tau) return T(0);
+    return m > T(0) ? T(1) : T(-1);
+  }
+  if (a >= T(0) && b >= T(0)) return T(1);
+  if (a <= T(0) && b <= T(0)) return T(-1);
+  return (d_abs(a) - d_abs(b)) / (a - b);
+}
+
+// |A| dW by Newton interpolation of |x| on the spectrum:
+// |A| = f[l1] I + f[l1,l2](A - l1 I) + f[l1,l2,l3](A - l1 I)(A - l2 I).
+template <typename T>
+__device__ __forceinline__ void abs_A_times_newton(const Eig<T>& e, T dh, T dq, T dz, T& x0, T& x1,
+                                                   T& x2) {
+  const T tau = T(TAU_GAP) * e.c;
+  const T f0 = d_abs(e.l1);
+  const T f01 = dd1_abs(e.l1, e.l2, tau);
+  const T f12 = dd1_abs(e.l2, e.l3, tau);
+  const T span = e.l3 - e.l1;
+  const T f012 = (span < tau) ? T(0) : (f12 - f01) / span;
+  T y0, y1, y2;
+  A_times(e, dh, dq, dz, y0, y1, y2);
+  // v = (A - l2 I) dW; w = (A - l1 I) v
+  const T v0 = y0 - e.l2 * dh, v1 = y1 - e.l2 * dq, v2 = y2 - e.l2 * dz;
+  T w0, w1, w2;
+  A_times(e, v0, v1, v2, w0, w1, w2);
+  w0 -= e.l1 * v0;
+  w1 -= e.l1 * v1;
+  w2 -= e.l1 * v2;
+  x0 = f0 * dh + f01 * (y0 - e.l1 * dh) + f012 * w0;
+  x1 = f0 * dq + f01 * (y1 - e.l1 * dq) + f012 * w1;
+  x2 = f0 * dz + f01 * (y2 - e.l1 * dz) + f012 * w2;
+}
+
+// Full float64 node: A dW and |A| dW, with the Newton form when two roots are
+// closer than TAU_GAP * c. Sets ST_NONHYPERBOLIC when |arg| > 1 + TAU_HYP.
+template <int LAW>
+__device__ __forceinline__ void node_f64(const LawT<double>& L, double h, double q, double dh,
+                                         double dq, double dz, double y[3], double x[3],
+                                         unsigned& flags) {
+  Eig<double> e;
+  node_eig<double, LAW>(L, h, q, e);
+  if (!(d_abs(e.arg) <= 1.0 + TAU_HYP)) flags |= ST_NONHYPERBOLIC;
+  A_times(e, dh, dq, dz, y[0], y[1], y[2]);
+  const double gap = d_min(e.l2 - e.l1, e.l3 - e.l2);
+  if (gap < TAU_GAP * e.c)
+    abs_A_times_newton(e, dh, dq, dz, x[0], x[1], x[2]);
+  else
+    abs_A_times_eigvec(e, dh, dq, dz, x[0], x[1], x[2]);
+}
+
+// Float64 redo of a float32 node (kept out of line so that its registers do
+// not weigh on the float32 fast path).
+template <int LAW>
+__device__ __noinline__ void node_f64_fallback(const LawT<double>& L, float h, float q, float dh,
+                                               float dq, float dz, float* y, float* x,
+                                               unsigned* flags) {
+  double yd[3], xd[3];
+  unsigned f = 0;
+  node_f64<LAW>(L, (double)h, (double)q, (double)dh, (double)dq, (double)dz, yd, xd, f);
+  *flags |= f;
+  for (int r = 0; r < 3; ++r) {
+    y[r] = (float)yd[r];
+    x[r] = (float)xd[r];
+  }
+}
+
+// Float32 node with the float64 redo when 1 - arg^2 < TAU_FP64_FALLBACK (or
+// arg is not finite).
+template <int LAW>
+__device__ __forceinline__ void node_f32(const LawT<float>& L, const LawT<double>& Ld, float h,
+                                         float q, float dh, float dq, float dz, float y[3],
+                                         float x[3], unsigned& flags) {
+  Eig<float> e;
+  node_eig<float, LAW>(L, h, q, e);
+  const float delta = 1.0f - e.arg * e.arg;
+  if (!(delta >= TAU_FP64_FALLBACK)) {
+    node_f64_fallback<LAW>(Ld, h, q, dh, dq, dz, y, x, &flags);
+    return;
+  }
+  A_times(e, dh, dq, dz, y[0], y[1], y[2]);
+  abs_A_times_eigvec(e, dh, dq, dz, x[0], x[1], x[2]);
+}
+
+// Spectral radius max(|l1|, |l3|) at a state.
+template <typename T, int LAW>
+__device__ __forceinline__ T spectral_radius(const LawT<T>& L, T h, T q) {
+  Eig<T> e;
+  node_eig<T, LAW>(L, h, q, e);
+  return d_max(d_abs(e.l1), d_abs(e.l3));
+}
+
+// ---------------------------------------------------------------------------
+// float-float helpers (value = hi + lo, |lo| <= ulp(hi)/2)
+// ---------------------------------------------------------------------------
+
+// (hi, lo) + b with Knuth's TwoSum on hi + b, the low parts folded in, and a
+// Fast2Sum renormalisation. Uses only float32 adds (no contraction possible).
+__device__ __forceinline__ float2 ff_add(float2 a, float b) {
+  const float s = a.x + b;
+  const float bb = s - a.x;
+  const float err = (a.x - (s - bb)) + (b - bb);
+  const float lo = a.y + err;
+  const float hi = s + lo;
+  return make_float2(hi, lo - (hi - s));
+}
+
+// (a - b) of two float-float values rounded to one float.
+__device__ __forceinline__ float ff_diff(float2 a, float2 b) { return (a.x - b.x) + (a.y - b.y); }
+
+__device__ __forceinline__ float2 ff_from_double(double d) {
+  const float hi = (float)d;
+  return make_float2(hi, (float)(d - (double)hi));
+}
+
+__device__ __forceinline__ double ff_to_double(float2 a) { return (double)a.x + (double)a.y; }
+
+}  // namespace adot

@@ -1,0 +1,17 @@
+// float32 (float-float state) instantiation of the fused time-step kernel.
+#include "adot_step_impl.cuh"
+
+namespace adot {
+
+bool step_block_supported(int block) { return block == 128 || block == 256 || block == 512; }
+
+cudaError_t launch_step_f32(const StepParams& p, int law, int block, StateF32 in, StateF32 out,
+                            int slot, cudaStream_t s) {
+  return launch_step_impl<float>(p, law, block, in, out, slot, s);
+}
+
+cudaError_t launch_rho_f32(const StepParams& p, int law, StateF32 st, int slot, cudaStream_t s) {
+  return launch_rho_impl<float>(p, law, st, slot, s);
+}
+
+}  // namespace adot

@@ -1,0 +1,15 @@
+// float64 instantiation of the fused time-step kernel.
+#include "adot_step_impl.cuh"
+
+namespace adot {
+
+cudaError_t launch_step_f64(const StepParams& p, int law, int block, StateF64 in, StateF64 out,
+                            int slot, cudaStream_t s) {
+  return launch_step_impl<double>(p, law, block, in, out, slot, s);
+}
+
+cudaError_t launch_rho_f64(const StepParams& p, int law, StateF64 st, int slot, cudaStream_t s) {
+  return launch_rho_impl<double>(p, law, st, slot, s);
+}
+
+}  // namespace adot

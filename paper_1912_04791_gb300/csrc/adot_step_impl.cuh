@@ -1,0 +1,334 @@
+// Fused time-step kernel of the A-DOT scheme, shared by the float32 and
+// float64 translation units.
+//
+// Launch geometry: block b owns edges e = b*(B-1) + t, t = 0..B-1 (edge e
+// joins cells e-1 and e; edges 0..n), and updates cells e-1 for t >= 1, i.e.
+// B-1 cells per block, so one edge per block is evaluated twice and no other
+// work is repeated. Per thread:
+//   1. load cells e-1 and e (or a ghost / the periodic wrap at the ends);
+//   2. D-/+ of edge e = 1/2 sum_k w_k (A_k dW -/+ |A_k| dW) over the three
+//      Gauss-Legendre nodes of the segment path (Eq. path, Eq. DOTjumpN);
+//   3. publish D+ in shared memory; after one barrier, cell e-1 takes its own
+//      edge's D- and the left neighbour thread's D+ (Eq. scheme):
+//      W_{e-1} <- W_{e-1} - dt/dx (D-_e + D+_{e-1});
+//   4. spectral radius of the new state, block max, one 64-bit atomicMax
+//      into the control slot that the next step reads for its dt.
+// dt is formed once per block by thread 0 from the control slot:
+// dt = cfl dx / rho_max, clipped so that t lands on t_end; once t >= t_end the
+// kernel copies the state unchanged (the ping-pong buffers stay consistent).
+#pragma once
+
+#include <float.h>
+
+#include "adot_internal.h"
+
+namespace adot {
+
+template <typename R>
+struct Prec;
+
+template <>
+struct Prec<float> {
+  using S = float2;
+  using State = StateF32;
+  __device__ static __forceinline__ float diff(S a, S b) { return ff_diff(a, b); }
+  __device__ static __forceinline__ float hi(S a) { return a.x; }
+  __device__ static __forceinline__ S add(S a, float d) { return ff_add(a, d); }
+  __device__ static __forceinline__ S from_double(double d) { return ff_from_double(d); }
+  __device__ static __forceinline__ unsigned long long bits(float r) {
+    return (unsigned long long)__float_as_uint(r);
+  }
+  __device__ static __forceinline__ double from_bits(unsigned long long b) {
+    return (double)__uint_as_float((unsigned)b);
+  }
+  __device__ static __forceinline__ bool finite(S a) { return isfinite(a.x) && isfinite(a.y); }
+  template <int LAW>
+  __device__ static __forceinline__ void node(const StepParams& p, float h, float q, float dh,
+                                              float dq, float dz, float y[3], float x[3],
+                                              unsigned& flags) {
+    node_f32<LAW>(p.lf, p.ld, h, q, dh, dq, dz, y, x, flags);
+  }
+  __device__ static __forceinline__ const LawT<float>& law(const StepParams& p) { return p.lf; }
+};
+
+template <>
+struct Prec<double> {
+  using S = double;
+  using State = StateF64;
+  __device__ static __forceinline__ double diff(S a, S b) { return a - b; }
+  __device__ static __forceinline__ double hi(S a) { return a; }
+  __device__ static __forceinline__ S add(S a, double d) { return a + d; }
+  __device__ static __forceinline__ S from_double(double d) { return d; }
+  __device__ static __forceinline__ unsigned long long bits(double r) {
+    return (unsigned long long)__double_as_longlong(r);
+  }
+  __device__ static __forceinline__ double from_bits(unsigned long long b) {
+    return __longlong_as_double((long long)b);
+  }
+  __device__ static __forceinline__ bool finite(S a) { return isfinite(a); }
+  template <int LAW>
+  __device__ static __forceinline__ void node(const StepParams& p, double h, double q, double dh,
+                                              double dq, double dz, double y[3], double x[3],
+                                              unsigned& flags) {
+    node_f64<LAW>(p.ld, h, q, dh, dq, dz, y, x, flags);
+  }
+  __device__ static __forceinline__ const LawT<double>& law(const StepParams& p) { return p.ld; }
+};
+
+// Ghost state beyond one end (adj = the adjacent cell).
+template <typename R>
+__device__ __forceinline__ void ghost_state(int kind, const double v[3], double t,
+                                            const typename Prec<R>::S adj[3],
+                                            typename Prec<R>::S out[3]) {
+  out[0] = adj[0];
+  out[1] = adj[1];
+  out[2] = adj[2];
+  if (kind == BC_INFLOW_Q) {
+    out[1] = Prec<R>::from_double(v[0]);
+  } else if (kind == BC_OUTFLOW_H) {
+    out[0] = Prec<R>::from_double(v[0]);
+  } else if (kind == BC_INFLOW_QZ) {
+    out[1] = Prec<R>::from_double(v[0]);
+    out[2] = Prec<R>::from_double(v[1] - v[2] * t);
+  }
+}
+
+// States on both sides of edge e (joins cells e-1 and e), 0 <= e <= n.
+template <typename R>
+__device__ __forceinline__ void load_edge(const StepParams& p, const typename Prec<R>::State& st,
+                                          int64_t e, int slot, typename Prec<R>::S wl[3],
+                                          typename Prec<R>::S wr[3]) {
+  const int64_t n = p.n;
+  if (e > 0 && e < n) {
+    wl[0] = st.h[e - 1];
+    wl[1] = st.q[e - 1];
+    wl[2] = st.z[e - 1];
+    wr[0] = st.h[e];
+    wr[1] = st.q[e];
+    wr[2] = st.z[e];
+  } else if (p.periodic) {
+    const int64_t il = (e == 0) ? n - 1 : e - 1;
+    const int64_t ir = (e == n) ? 0 : e;
+    wl[0] = st.h[il];
+    wl[1] = st.q[il];
+    wl[2] = st.z[il];
+    wr[0] = st.h[ir];
+    wr[1] = st.q[ir];
+    wr[2] = st.z[ir];
+  } else if (e == 0) {
+    wr[0] = st.h[0];
+    wr[1] = st.q[0];
+    wr[2] = st.z[0];
+    ghost_state<R>(p.bc_left, p.bcl, p.ctl->s[slot].t, wr, wl);
+  } else {
+    wl[0] = st.h[n - 1];
+    wl[1] = st.q[n - 1];
+    wl[2] = st.z[n - 1];
+    ghost_state<R>(p.bc_right, p.bcr, p.ctl->s[slot].t, wl, wr);
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ R warp_max(R v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = d_max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// D-/+ of one edge from its two states.
+template <typename R, int LAW>
+__device__ __forceinline__ void edge_fluct(const StepParams& p, const typename Prec<R>::S wl[3],
+                                           const typename Prec<R>::S wr[3], R dm[3], R dp[3],
+                                           unsigned& flags) {
+  const R dh = Prec<R>::diff(wr[0], wl[0]);
+  const R dq = Prec<R>::diff(wr[1], wl[1]);
+  const R dz = Prec<R>::diff(wr[2], wl[2]);
+  const R h0 = Prec<R>::hi(wl[0]), q0 = Prec<R>::hi(wl[1]);
+  R ya[3] = {R(0), R(0), R(0)}, xa[3] = {R(0), R(0), R(0)};
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const R s = (k == 0) ? R(GL3_S0) : ((k == 1) ? R(0.5) : R(GL3_S2));
+    const R w = (k == 1) ? R(GL3_W1) : R(GL3_W0);
+    R y[3], x[3];
+    Prec<R>::template node<LAW>(p, h0 + s * dh, q0 + s * dq, dh, dq, dz, y, x, flags);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      ya[r] += w * y[r];
+      xa[r] += w * x[r];
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    dm[r] = R(0.5) * (ya[r] - xa[r]);
+    dp[r] = R(0.5) * (ya[r] + xa[r]);
+  }
+}
+
+template <typename R, int LAW, int B>
+__global__ void __launch_bounds__(B) k_step(const StepParams p, const typename Prec<R>::State in,
+                                            const typename Prec<R>::State out, const int slot) {
+  using S = typename Prec<R>::S;
+  __shared__ R sDp[3][B];
+  __shared__ R sRed[B / 32];
+  __shared__ R sNu;
+  __shared__ int sDone;
+
+  const int tid = threadIdx.x;
+  const int64_t n = p.n;
+  const int64_t e = (int64_t)blockIdx.x * (B - 1) + tid;
+  Ctl* ctl = p.ctl;
+
+  if (tid == 0) {
+    const CtlSlot cs = ctl->s[slot];
+    const double t_end = ctl->t_end;
+    const bool done = !(cs.t < t_end);
+    const double rho = Prec<R>::from_bits(cs.rho_bits);
+    double dt = p.cfl * p.dx / rho;
+    double tn = cs.t + dt;
+    if (tn >= t_end) {
+      dt = t_end - cs.t;
+      tn = t_end;
+    }
+    sNu = done ? R(0) : R(dt / p.dx);
+    sDone = done ? 1 : 0;
+    if (blockIdx.x == 0) {
+      CtlSlot& nx = ctl->s[(slot + 1) % 3];
+      nx.t = done ? cs.t : tn;
+      nx.dt = done ? cs.dt : dt;
+      nx.steps = cs.steps + (done ? 0 : 1);
+      if (done) nx.rho_bits = cs.rho_bits;
+      ctl->s[(slot + 2) % 3].rho_bits = 0ull;
+    }
+  }
+
+  unsigned flags = 0;
+  S wl[3];
+  R dm[3] = {R(0), R(0), R(0)}, dp[3] = {R(0), R(0), R(0)};
+  if (e <= n) {
+    S wr[3];
+    load_edge<R>(p, in, e, slot, wl, wr);
+    edge_fluct<R, LAW>(p, wl, wr, dm, dp, flags);
+  }
+  sDp[0][tid] = dp[0];
+  sDp[1][tid] = dp[1];
+  sDp[2][tid] = dp[2];
+  __syncthreads();
+
+  const R nu = sNu;
+  const bool done = sDone != 0;
+  R rho = R(0);
+  const int64_t i = e - 1;
+  if (tid >= 1 && i < n) {
+    S nh = wl[0], nq = wl[1], nz = wl[2];
+    if (!done) {
+      nh = Prec<R>::add(wl[0], -nu * (dm[0] + sDp[0][tid - 1]));
+      nq = Prec<R>::add(wl[1], -nu * (dm[1] + sDp[1][tid - 1]));
+      nz = Prec<R>::add(wl[2], -nu * (dm[2] + sDp[2][tid - 1]));
+    }
+    out.h[i] = nh;
+    out.q[i] = nq;
+    out.z[i] = nz;
+    if (!done) {
+      const R hh = Prec<R>::hi(nh);
+      if (!(hh > R(0))) flags |= ST_DEPTH;
+      if (!(Prec<R>::finite(nh) && Prec<R>::finite(nq) && Prec<R>::finite(nz))) {
+        flags |= ST_NONFINITE;
+      } else if (hh > R(0)) {
+        rho = spectral_radius<R, LAW>(Prec<R>::law(p), hh, Prec<R>::hi(nq));
+        if (!(rho <= R(3.0e38))) {
+          flags |= ST_NONFINITE;
+          rho = R(0);
+        }
+      }
+    }
+  }
+
+  rho = warp_max(rho);
+  if ((tid & 31) == 0) sRed[tid >> 5] = rho;
+  __syncthreads();
+  if (tid < 32) {
+    rho = (tid < B / 32) ? sRed[tid] : R(0);
+    rho = warp_max(rho);
+    if (tid == 0 && !done && rho > R(0))
+      atomicMax(&ctl->s[(slot + 1) % 3].rho_bits, Prec<R>::bits(rho));
+  }
+  if (flags) atomicOr(&ctl->status, flags);
+}
+
+// CFL maximum and admissibility of a state (grid-stride).
+template <typename R, int LAW>
+__global__ void __launch_bounds__(256) k_rho(const StepParams p, const typename Prec<R>::State st,
+                                             const int slot) {
+  __shared__ R sRed[8];
+  unsigned flags = 0;
+  R rho = R(0);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const auto h = st.h[i], q = st.q[i], z = st.z[i];
+    const R hh = Prec<R>::hi(h);
+    if (!(Prec<R>::finite(h) && Prec<R>::finite(q) && Prec<R>::finite(z))) {
+      flags |= ST_NONFINITE;
+      continue;
+    }
+    if (!(hh > R(0))) {
+      flags |= ST_DEPTH;
+      continue;
+    }
+    R r = spectral_radius<R, LAW>(Prec<R>::law(p), hh, Prec<R>::hi(q));
+    if (!(r <= R(3.0e38))) {
+      flags |= ST_NONFINITE;
+      continue;
+    }
+    rho = d_max(rho, r);
+  }
+  rho = warp_max(rho);
+  if ((threadIdx.x & 31) == 0) sRed[threadIdx.x >> 5] = rho;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    rho = (threadIdx.x < 8) ? sRed[threadIdx.x] : R(0);
+    rho = warp_max(rho);
+    if (threadIdx.x == 0 && rho > R(0)) atomicMax(&p.ctl->s[slot].rho_bits, Prec<R>::bits(rho));
+  }
+  if (flags) atomicOr(&p.ctl->status, flags);
+}
+
+template <typename R, int LAW>
+cudaError_t launch_step_law(const StepParams& p, int block, typename Prec<R>::State in,
+                            typename Prec<R>::State out, int slot, cudaStream_t s) {
+  // edges 0..n, B-1 new edges per block: ceil((n+1)/(B-1)) blocks
+  const int64_t cells = block - 1;
+  const int64_t g = (p.n + 1 + cells - 1) / cells;
+  if (g > 0x7fffffffLL) return cudaErrorInvalidValue;
+  switch (block) {
+    case 128: k_step<R, LAW, 128><<<(unsigned)g, 128, 0, s>>>(p, in, out, slot); break;
+    case 256: k_step<R, LAW, 256><<<(unsigned)g, 256, 0, s>>>(p, in, out, slot); break;
+    case 512: k_step<R, LAW, 512><<<(unsigned)g, 512, 0, s>>>(p, in, out, slot); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_step_impl(const StepParams& p, int law, int block, typename Prec<R>::State in,
+                             typename Prec<R>::State out, int slot, cudaStream_t s) {
+  if (law == LAW_GRASS) return launch_step_law<R, LAW_GRASS>(p, block, in, out, slot, s);
+  if (law == LAW_MPM) return launch_step_law<R, LAW_MPM>(p, block, in, out, slot, s);
+  return cudaErrorInvalidValue;
+}
+
+template <typename R>
+cudaError_t launch_rho_impl(const StepParams& p, int law, typename Prec<R>::State st, int slot,
+                            cudaStream_t s) {
+  int64_t g = (p.n + 255) / 256;
+  if (g > 152 * 32) g = 152 * 32;
+  if (g < 1) g = 1;
+  if (law == LAW_GRASS)
+    k_rho<R, LAW_GRASS><<<(unsigned)g, 256, 0, s>>>(p, st, slot);
+  else if (law == LAW_MPM)
+    k_rho<R, LAW_MPM><<<(unsigned)g, 256, 0, s>>>(p, st, slot);
+  else
+    return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+}  // namespace adot

@@ -18,3 +18,13 @@ def oracle():
     import oracle as O
     O.build()
     return O
+
+
+@pytest.fixture(scope="session")
+def gpu():
+    """Builds and loads libadot.so; the tests that use it need a GPU and fail
+    (rather than skip) when the library or the device is missing."""
+    from paper_1912_04791_gb300 import adot, build
+    build.build()
+    adot.lib()
+    return adot

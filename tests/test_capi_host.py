@@ -1,0 +1,85 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds and
+loads, exports every function include/adot.h declares, the ctypes structures
+match the C layout, and argument validation rejects bad configurations before
+any CUDA call."""
+import ctypes
+import os
+import subprocess
+
+import pytest
+
+from paper_1912_04791_gb300 import adot, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    build.build()
+    return adot.lib()
+
+
+def test_exports_every_declared_function(L):
+    names = adot.header_functions()
+    assert len(names) >= 12
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_struct_layout_matches_c(tmp_path):
+    src = tmp_path / "layout.c"
+    src.write_text(r'''
+#include <stddef.h>
+#include <stdio.h>
+#include "adot.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(adot_config), sizeof(adot_law),
+         offsetof(adot_config, law), offsetof(adot_config, precision),
+         offsetof(adot_config, bc_left_value), offsetof(adot_config, bc_right_value),
+         offsetof(adot_config, block_threads), offsetof(adot_config, device),
+         offsetof(adot_law, manning_n));
+  return 0;
+}
+''')
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True,
+                                          check=True).stdout.split()]
+    C, W = adot.Config, adot.Law
+    want = [ctypes.sizeof(C), ctypes.sizeof(W), C.law.offset, C.precision.offset,
+            C.bc_left_value.offset, C.bc_right_value.offset, C.block_threads.offset,
+            C.device.offset, W.manning_n.offset]
+    assert got == want
+
+
+def test_status_strings_and_version(L):
+    assert adot.status_string(adot.OK) == "ok"
+    assert "depth" in adot.status_string(adot.E_NONPOSITIVE_DEPTH)
+    assert adot.status_string(99) == "unknown status"
+    assert "sm_103a" in adot.version()
+
+
+@pytest.mark.parametrize("field,value", [
+    ("n_cells", 0), ("cfl", 0.0), ("cfl", 1.5), ("x_max", -1.0), ("precision", 7),
+    ("bc_left", 9), ("block_threads", 100), ("steps_per_graph", -6), ("device", -3)])
+def test_invalid_config_rejected_without_cuda(L, field, value):
+    cfg = adot.make_config(64, 0.0, 1.0, 0.8, 0.005, 5 / 3)
+    setattr(cfg, field, value)
+    out = ctypes.c_void_p()
+    st = L.adot_create(ctypes.byref(cfg), None, ctypes.byref(out))
+    assert st == adot.E_INVALID_ARG and not out.value
+
+
+def test_periodic_must_be_on_both_ends(L):
+    cfg = adot.make_config(64, 0.0, 1.0, 0.8, 0.005, 5 / 3, bc_left=adot.BC_PERIODIC)
+    out = ctypes.c_void_p()
+    assert L.adot_create(ctypes.byref(cfg), None, ctypes.byref(out)) == adot.E_INVALID_ARG
+
+
+def test_null_arguments_rejected(L):
+    out = ctypes.c_void_p()
+    assert L.adot_create(None, None, ctypes.byref(out)) == adot.E_INVALID_ARG
+    assert L.adot_step(None, 1, None, None) == adot.E_INVALID_ARG
+    assert L.adot_query(None, None, None, None) == adot.E_INVALID_ARG
+    assert L.adot_fluctuations(None, None, None, 0, None, None, None, 0) == adot.E_INVALID_ARG
+    L.adot_destroy(None)

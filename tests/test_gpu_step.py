@@ -1,0 +1,218 @@
+"""Parity of whole CUDA time-stepping runs (fused edge + update + CFL kernel,
+Eq. scheme) with the FP64 oracle, on the benchmark workloads at sizes the
+oracle finishes in seconds (several blocks plus a ragged tail), plus the
+runtime's contracts: graph replays equal single launches bit for bit, run_to
+lands on t_end, sums are reproducible, errors are reported.
+
+Tolerances. FP64: every value within 1e-12 relative to the variable's scale
+after the run (rounding-order differences only). FP32 (float-float state,
+float32 fluctuations): the increment W^K - W^0 matches the oracle's to an L1
+relative error of 1e-5, the target precision of the float32 path."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1912_04791_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+G = 9.81
+
+
+def _ocfg(P):
+    law = O.grass(P.Ag, xi=P.xi, g=P.g)
+    return O.make_cfg(P.n, P.x_min, P.x_max, P.cfl, law, P.bc_left, P.bc_right, P.bcl, P.bcr)
+
+
+def _scale(a):
+    return max(np.abs(a).max(), 1e-300)
+
+
+def _run_gpu(gpu, P, prec, steps=None, t_end=None, **kw):
+    with gpu.Solver(gpu.config_for(P, prec, **kw)) as s:
+        s.set_state(P.h, P.q, P.z)
+        if t_end is not None:
+            s.run_to(t_end)
+        else:
+            s.step(steps)
+        t, nsteps, dt = s.query()
+        h, q, z = s.get_state()
+    return h, q, z, t, nsteps, dt
+
+
+@pytest.mark.parametrize("n", [1, 2, 255, 256, 511, 1000, 2049])
+@pytest.mark.parametrize("block", [128, 256, 512])
+def test_fp64_smooth_periodic_matches_oracle(gpu, n, block):
+    P = W.smooth_periodic(n)
+    K = 60
+    ho, qo, zo, to, _, _ = O.run(_ocfg(P), P.h, P.q, P.z, max_steps=K)
+    h, q, z, t, steps, _ = _run_gpu(gpu, P, gpu.FP64, steps=K, block_threads=block)
+    assert steps == K
+    assert t == pytest.approx(to, rel=1e-13)
+    for a, b in ((h, ho), (q, qo), (z, zo)):
+        assert np.abs(a - b).max() <= 1e-12 * _scale(b)
+
+
+@pytest.mark.parametrize("n", [200, 701])
+def test_fp64_movable_bed_riemann_to_t_end(gpu, n):
+    """Movable-bed Riemann problem (transmissive ends) run to t_end = 1 s."""
+    P = W.movable_bed_riemann(n)
+    ho, qo, zo, to, so, _ = O.run(_ocfg(P), P.h, P.q, P.z, t_end=P.t_end)
+    h, q, z, t, steps, _ = _run_gpu(gpu, P, gpu.FP64, t_end=P.t_end)
+    assert t == P.t_end and steps == so
+    for a, b in ((h, ho), (q, qo), (z, zo)):
+        assert np.abs(a - b).max() <= 1e-12 * _scale(b)
+
+
+def test_fp64_inflow_outflow_boundaries(gpu):
+    """Test 2 boundary data (inflow q and time-dependent z, outflow h)."""
+    from oracle import exact as X
+    q0 = 2.0
+    qb, zb, rate, hR = X.berthon_boundary(q0)
+    n = 300
+    h0, qq0, z0 = X.berthon_cell_average(n, q0, 0.0)
+    P = W.Problem("berthon", n, 0.0, 7.0, 0.9, 10.0, 0.005, 1.0, h0, qq0, z0,
+                  W.BC_INFLOW_QZ, W.BC_OUTFLOW_H, (qb, zb, rate), (hR, 0.0, 0.0))
+    ho, qo, zo, to, so, _ = O.run(_ocfg(P), P.h, P.q, P.z, t_end=2.0)
+    h, q, z, t, steps, _ = _run_gpu(gpu, P, gpu.FP64, t_end=2.0)
+    assert t == 2.0 and steps == so
+    for a, b in ((h, ho), (q, qo), (z, zo)):
+        assert np.abs(a - b).max() <= 1e-12 * _scale(b)
+
+
+def test_fp64_gaussian_bump_inflow_outflow(gpu):
+    P = W.gaussian_bump(997)
+    ho, qo, zo, _, _, _ = O.run(_ocfg(P), P.h, P.q, P.z, max_steps=150)
+    h, q, z, _, _, _ = _run_gpu(gpu, P, gpu.FP64, steps=150)
+    for a, b in ((h, ho), (q, qo), (z, zo)):
+        assert np.abs(a - b).max() <= 1e-12 * _scale(b)
+
+
+@pytest.mark.parametrize("n", [257, 4099])
+def test_fp32_increment_matches_oracle(gpu, n):
+    P = W.smooth_periodic(n)
+    K = 200
+    ho, qo, zo, _, _, _ = O.run(_ocfg(P), P.h, P.q, P.z, max_steps=K)
+    h, q, z, _, _, _ = _run_gpu(gpu, P, gpu.FP32, steps=K)
+    for a, b, a0 in ((h, ho, P.h), (q, qo, P.q), (z, zo, P.z)):
+        inc, ref = a - a0, b - a0
+        assert np.abs(inc - ref).sum() <= 1e-5 * np.abs(ref).sum()
+
+
+def test_fp32_movable_bed_riemann_l1(gpu):
+    P = W.movable_bed_riemann(200)
+    ho, qo, zo, to, _, _ = O.run(_ocfg(P), P.h, P.q, P.z, t_end=P.t_end)
+    h, q, z, t, _, _ = _run_gpu(gpu, P, gpu.FP32, t_end=P.t_end)
+    assert t == P.t_end
+    for a, b in ((h, ho), (q, qo), (z, zo)):
+        assert np.abs(a - b).sum() <= 1e-5 * np.abs(b).sum()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_graph_replay_equals_single_launches(gpu, prec):
+    """steps_per_graph = 6 (graph replays) and a run that is never graph-aligned
+    (one step first) give bit-identical states after the same number of steps."""
+    P = W.smooth_periodic(3001)
+    a = _run_gpu(gpu, P, prec, steps=61, steps_per_graph=6)
+    with gpu.Solver(gpu.config_for(P, prec, steps_per_graph=60)) as s:
+        s.set_state(P.h, P.q, P.z)
+        for _ in range(61):
+            s.step(1)
+        b = s.get_state() + s.query()
+    for x, y in zip(a[:3], b[:3]):
+        assert np.array_equal(x, y)
+    assert a[3] == b[3] and a[4] == b[4] == 61
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_run_to_lands_on_t_end_and_stops(gpu, prec):
+    P = W.movable_bed_riemann(200)
+    with gpu.Solver(gpu.config_for(P, prec)) as s:
+        s.set_state(P.h, P.q, P.z)
+        k1 = s.run_to(0.25)
+        t, steps, _ = s.query()
+        assert t == 0.25 and steps == k1 > 0
+        assert s.run_to(0.25) == 0  # already there
+        k2 = s.run_to(0.5)
+        t, steps, _ = s.query()
+        assert t == 0.5 and steps == k1 + k2
+    if prec == 0:
+        ho, qo, zo, to, so, _ = O.run(_ocfg(P), P.h, P.q, P.z, t_end=0.25)
+        assert so == k1
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_conserved_sums(gpu, prec):
+    """Fixed-order device sums equal numpy's sums of the state, are bit-reproducible,
+    and the periodic run conserves sum h."""
+    P = W.smooth_periodic(100003)
+    with gpu.Solver(gpu.config_for(P, prec)) as s:
+        s.set_state(P.h, P.q, P.z)
+        s0 = s.conserved_sums()
+        assert np.allclose(s0, [P.h.sum(), P.q.sum(), P.z.sum()], rtol=1e-13, atol=1e-9)
+        s.step(30)
+        s1 = s.conserved_sums()
+        s2 = s.conserved_sums()
+        assert np.array_equal(s1, s2)
+        h, q, z = s.get_state()
+        assert np.allclose(s1, [h.sum(), q.sum(), z.sum()], rtol=1e-12, atol=1e-9)
+        tol = 1e-13 if prec == 0 else 1e-9
+        assert abs(s1[0] - s0[0]) <= tol * s0[0]
+
+
+def test_lake_at_rest_gpu(gpu):
+    P = W.lake_at_rest(4096)
+    for prec, qb in ((0, 1e-12), (1, 2e-5)):
+        h, q, z, _, _, _ = _run_gpu(gpu, P, prec, steps=300)
+        assert np.abs(q).max() <= qb
+        assert np.abs(h + z - 1.0).max() <= 50 * qb
+
+
+def test_bad_state_is_reported(gpu):
+    P = W.smooth_periodic(512)
+    with gpu.Solver(gpu.config_for(P, 0)) as s:
+        h = P.h.copy()
+        h[17] = -1.0
+        with pytest.raises(gpu.AdotError) as e:
+            s.set_state(h, P.q, P.z)
+        assert e.value.status == gpu.E_NONPOSITIVE_DEPTH
+        q = P.q.copy()
+        q[3] = np.nan
+        with pytest.raises(gpu.AdotError) as e:
+            s.set_state(P.h, q, P.z)
+        assert e.value.status == gpu.E_NONFINITE
+        # the context stays usable
+        s.set_state(P.h, P.q, P.z)
+        s.step(5)
+
+
+def test_dry_out_is_reported(gpu):
+    """Two streams leaving each other (u = -+3 m/s on h = 0.1 m, beyond the
+    2(c_L + c_R) dry-bed limit) drive h through zero, as in the oracle: the run
+    reports ADOT_E_NONPOSITIVE_DEPTH or ADOT_E_NONFINITE and the state can
+    still be read."""
+    P = W.dam_break(512, hL=0.1, hR=0.1, uL=-3.0, uR=3.0)
+    with pytest.raises(O.OracleError):
+        O.run(_ocfg(P), P.h, P.q, P.z, max_steps=50)
+    with gpu.Solver(gpu.config_for(P, 0)) as s:
+        s.set_state(P.h, P.q, P.z)
+        with pytest.raises(gpu.AdotError) as e:
+            s.step(400)
+        assert e.value.status in (gpu.E_NONPOSITIVE_DEPTH, gpu.E_NONFINITE)
+        h, q, z = s.get_state()
+        assert h.shape == (512,)
+
+
+def test_device_state_roundtrip(gpu):
+    torch = pytest.importorskip("torch")
+    P = W.smooth_periodic(2000)
+    ho, qo, zo, _, _, _ = O.run(_ocfg(P), P.h, P.q, P.z, max_steps=10)
+    stream = torch.cuda.current_stream()
+    with gpu.Solver(gpu.config_for(P, 0), stream=stream) as s:
+        th, tq, tz = (torch.tensor(a, device="cuda") for a in (P.h, P.q, P.z))
+        s.set_state(th, tq, tz)
+        s.step(10)
+        oh, oq, oz = (torch.empty(2000, dtype=torch.float64, device="cuda") for _ in range(3))
+        gpu.adot_get_state(s.ctx, oh, oq, oz)
+        torch.cuda.synchronize()
+        for a, b in ((oh, ho), (oq, qo), (oz, zo)):
+            assert np.abs(a.cpu().numpy() - b).max() <= 1e-12 * _scale(b)
