@@ -249,6 +249,7 @@ adot_status adot_create(const adot_config* cfg, void* cuda_stream, adot_ctx** ou
   for (int b = 0; b < 2 && e == cudaSuccess; ++b)
     for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaMalloc(&c->buf[b][k], elem * (size_t)n);
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_ctl, sizeof(Ctl));
+  p.ctl = c->d_ctl;
   if (e == cudaSuccess) e = cudaHostAlloc((void**)&c->h_ctl, sizeof(Ctl), cudaHostAllocDefault);
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_partial, sizeof(double) * 3 * sums_partial_blocks(n));
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_sums, sizeof(double) * 3);

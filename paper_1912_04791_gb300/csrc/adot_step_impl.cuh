@@ -295,6 +295,7 @@ __global__ void __launch_bounds__(256) k_rho(const StepParams p, const typename 
 template <typename R, int LAW>
 cudaError_t launch_step_law(const StepParams& p, int block, typename Prec<R>::State in,
                             typename Prec<R>::State out, int slot, cudaStream_t s) {
+  if (p.ctl == nullptr || p.n < 1) return cudaErrorInvalidValue;
   // edges 0..n, B-1 new edges per block: ceil((n+1)/(B-1)) blocks
   const int64_t cells = block - 1;
   const int64_t g = (p.n + 1 + cells - 1) / cells;
@@ -319,6 +320,7 @@ cudaError_t launch_step_impl(const StepParams& p, int law, int block, typename P
 template <typename R>
 cudaError_t launch_rho_impl(const StepParams& p, int law, typename Prec<R>::State st, int slot,
                             cudaStream_t s) {
+  if (p.ctl == nullptr || p.n < 1) return cudaErrorInvalidValue;
   int64_t g = (p.n + 255) / 256;
   if (g > 152 * 32) g = 152 * 32;
   if (g < 1) g = 1;
