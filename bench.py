@@ -51,7 +51,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=96)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=float, default=1e7)
-    ap.add_argument("--block", type=int, default=256)
+    ap.add_argument("--block", type=int, default=0, help="threads per block (0 = autotuned)")
+    ap.add_argument("--reg-cap", type=int, default=0, help="64, -1 = none, 0 = autotuned")
+    ap.add_argument("--sweep", action="store_true", help="also time every kernel variant")
     ap.add_argument("--cpu-steps", type=int, default=3,
                     help="oracle steps on the full workload for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -200,9 +202,33 @@ def main():
     n = int(args.n)
     P = W.smooth_periodic(n)
     stream = torch.cuda.Stream(device=dev)
-    cfg = adot.config_for(P, adot.FP32, block_threads=args.block, device=local)
+    cfg = adot.config_for(P, adot.FP32, block_threads=args.block, reg_cap=args.reg_cap,
+                          device=local)
     solver = adot.Solver(cfg, stream=stream)
     solver.set_state(P.h, P.q, P.z)
+    block, reg_cap = adot.adot_autotune(solver.ctx, 8)
+
+    def time_steps(s, k):
+        torch.cuda.synchronize(dev)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        adot.adot_enqueue_steps(s.ctx, k)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        adot.adot_query(s.ctx)
+        return a.elapsed_time(b)
+
+    variants = None
+    if args.sweep and rank == 0:
+        variants = {}
+        for vb, vc in [(128, 64), (128, -1), (256, 64), (256, -1), (512, 64), (512, -1)]:
+            with adot.Solver(adot.config_for(P, adot.FP32, block_threads=vb, reg_cap=vc,
+                                             device=local), stream=stream) as sv:
+                sv.set_state(P.h, P.q, P.z)
+                adot.adot_step(sv.ctx, 48)
+                ms_v = time_steps(sv, 480)
+            variants[f"{vb}x{'cap64' if vc == 64 else 'nocap'}"] = n * 480 / (ms_v * 1e-3)
 
     # warm-up
     adot.adot_step(solver.ctx, args.warmup)
@@ -261,12 +287,13 @@ def main():
         K = args.accuracy_steps
         with adot.Solver(adot.config_for(P, adot.FP64, device=local), stream=stream) as s64:
             s64.set_state(P.h, P.q, P.z)
-            s64.step(K)
+            ms64 = time_steps(s64, K)
             ref = s64.get_state()
         solver.set_state(P.h, P.q, P.z)
         solver.step(K)
         got = solver.get_state()
-        accuracy = {"steps": K, "reference": "GPU FP64 path (parity-tested against the oracle)"}
+        accuracy = {"steps": K, "reference": "GPU FP64 path (parity-tested against the oracle)",
+                    "fp64_cell_updates_per_s": n * K / (ms64 * 1e-3)}
         for name, a, b, a0 in zip("hqz", got, ref, (P.h, P.q, P.z)):
             accuracy[f"l1_rel_increment_{name}"] = float(np.abs((a - a0) - (b - a0)).sum()
                                                          / np.abs(b - a0).sum())
@@ -288,17 +315,18 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"smooth_periodic N={n} (A-DOT FP32, float-float state)",
                        "n_cells": n, "domain": "[0,1] m periodic", "Ag": P.Ag, "xi": P.xi,
-                       "cfl": P.cfl, "block_threads": args.block, "steps_per_graph": 48,
+                       "cfl": P.cfl, "block_threads": block, "reg_cap": reg_cap,
+                       "steps_per_graph": 48,
                        "l2": "inputs larger than L2 (2 x 240 MB state buffers, no flush)",
                        "parallelism": "replicas" if ws > 1 else "single"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": f_peak, "unit": "TFLOP/s",
                          "frac": achieved / f_peak, "traffic": None,
-                         "kernel": "k_step<float,GRASS,256>",
+                         "kernel": f"k_step<float,GRASS,{block},{max(reg_cap, 0)}>",
                          "peak_source": "152 SM x 128 FP32 lanes x 2 x 2070 MHz (derived)",
                          "hbm_achieved_gbs": BYTES_PER_CELL_UPDATE * n / per_launch_s / 1e9,
                          "hbm_peak_gbs": measured_peaks().get("hbm_gbs", 6800.0)},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps, "clocks": clocks,
-            "accuracy": accuracy, "sim_time_after_timed_steps": t_sim,
+            "accuracy": accuracy, "sim_time_after_timed_steps": t_sim, "variants": variants,
         }
         print(json.dumps(line), flush=True)
     if dist:

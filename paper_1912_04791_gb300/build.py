@@ -18,8 +18,10 @@ LIB_PATH = os.path.join(HERE, "libadot.so")
 
 SOURCES = ["adot_step_f32.cu", "adot_step_f64.cu", "adot_aux.cu", "adot_capi.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# -ftz / -prec-div / -prec-sqrt relax float32 only (denormals flushed, division and
+# square root to ~2 ulp); float64 arithmetic is unaffected.
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-v",
-              "--expt-relaxed-constexpr"]
+              "--expt-relaxed-constexpr", "-ftz=true", "-prec-div=false", "-prec-sqrt=false"]
 
 
 def nvcc() -> str:

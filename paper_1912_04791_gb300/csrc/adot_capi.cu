@@ -12,6 +12,10 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "../../include/adot.h"
 #include "adot_internal.h"
 
@@ -22,7 +26,8 @@ struct adot_ctx {
   int device;
   int prec;  // 0 = float64, 1 = float-float
   int law;
-  int block;
+  StepVariant var;  // step kernel variant in use
+  bool tuned;       // variant fixed by the config, the cache or adot_autotune
   int steps_per_graph;
   cudaStream_t stream;
   bool own_stream;
@@ -84,6 +89,7 @@ adot_status validate(const adot_config* c) {
   for (int i = 0; i < 3; ++i)
     if (!isfinite(c->bc_left_value[i]) || !isfinite(c->bc_right_value[i])) return ADOT_E_INVALID_ARG;
   if (c->block_threads != 0 && !step_block_supported(c->block_threads)) return ADOT_E_INVALID_ARG;
+  if (c->reg_cap != 0 && c->reg_cap != 64 && c->reg_cap != -1) return ADOT_E_INVALID_ARG;
   if (c->steps_per_graph < 0 || c->device < -1) return ADOT_E_INVALID_ARG;
   return ADOT_OK;
 }
@@ -95,15 +101,22 @@ StateF64 st64(adot_ctx* c, int which) {
   return StateF64{(double*)c->buf[which][0], (double*)c->buf[which][1], (double*)c->buf[which][2]};
 }
 
-cudaError_t launch_one(adot_ctx* c, cudaStream_t s, int cur, int phase) {
+cudaError_t launch_one_v(adot_ctx* c, StepVariant v, cudaStream_t s, int cur, int phase) {
   const int slot = phase % 3;
   if (c->prec == ADOT_FP32)
-    return launch_step_f32(c->p, c->law, c->block, st32(c, cur), st32(c, 1 - cur), slot, s);
-  return launch_step_f64(c->p, c->law, c->block, st64(c, cur), st64(c, 1 - cur), slot, s);
+    return launch_step_f32(c->p, c->law, v, st32(c, cur), st32(c, 1 - cur), slot, s);
+  return launch_step_f64(c->p, c->law, v, st64(c, cur), st64(c, 1 - cur), slot, s);
+}
+
+cudaError_t launch_one(adot_ctx* c, cudaStream_t s, int cur, int phase) {
+  return launch_one_v(c, c->var, s, cur, phase);
 }
 
 adot_status build_graph(adot_ctx* c) {
-  if (c->graph_ready) return ADOT_OK;
+  if (c->graph_ready) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph_ready = false;
+  }
   cudaGraph_t g = nullptr;
   CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
   cudaError_t err = cudaSuccess;
@@ -136,6 +149,71 @@ adot_status enqueue(adot_ctx* c, int64_t n) {
     }
   }
   return ADOT_OK;
+}
+
+// Process-wide cache of tuned variants: (device, law, precision, log2 n, filters).
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int, int, int>, StepVariant> g_tune_cache;
+
+std::tuple<int, int, int, int, int, int> tune_key(const adot_ctx* c) {
+  int lg = 0;
+  for (int64_t n = c->p.n; n > 1; n >>= 1) ++lg;
+  return std::make_tuple(c->device, c->law, c->prec, lg, c->cfg.block_threads, c->cfg.reg_cap);
+}
+
+bool candidate(const adot_config& cfg, StepVariant v) {
+  if (cfg.block_threads && v.block != cfg.block_threads) return false;
+  if (cfg.reg_cap == 64 && v.reg_cap != 64) return false;
+  if (cfg.reg_cap == -1 && v.reg_cap != 0) return false;
+  return true;
+}
+
+// Times each candidate variant on the current state: trial steps read the
+// current buffer and write the other one, with the current control slot, so
+// neither the state nor the step counter advances. The slot they write is
+// reset afterwards.
+adot_status tune(adot_ctx* c, int64_t trial) {
+  if (trial < 1) trial = 1;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return ADOT_E_CUDA;
+  }
+  float best_ms = 0.0f;
+  StepVariant best = c->var;
+  bool have = false;
+  cudaError_t err = cudaSuccess;
+  for (int i = 0; i < kNumStepVariants && err == cudaSuccess; ++i) {
+    const StepVariant v = kStepVariants[i];
+    if (!candidate(c->cfg, v)) continue;
+    for (int k = 0; k < 2 && err == cudaSuccess; ++k) err = launch_one_v(c, v, c->stream, c->cur, c->phase);
+    if (err == cudaSuccess) err = cudaEventRecord(e0, c->stream);
+    for (int64_t k = 0; k < trial && err == cudaSuccess; ++k)
+      err = launch_one_v(c, v, c->stream, c->cur, c->phase);
+    if (err == cudaSuccess) err = cudaEventRecord(e1, c->stream);
+    if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+    if (err == cudaSuccess && (!have || ms < best_ms)) {
+      best_ms = ms;
+      best = v;
+      have = true;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (err != cudaSuccess) return ADOT_E_CUDA;
+  CK(cudaMemsetAsync(&c->d_ctl->s[(c->phase + 1) % 3].rho_bits, 0, sizeof(unsigned long long),
+                     c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->var = best;
+  c->tuned = true;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[tune_key(c)] = best;
+  }
+  return build_graph(c);
 }
 
 adot_status set_t_end(adot_ctx* c, double t_end) {
@@ -210,7 +288,13 @@ adot_status adot_create(const adot_config* cfg, void* cuda_stream, adot_ctx** ou
   c->device = dev;
   c->prec = cfg->precision;
   c->law = cfg->law.kind;
-  c->block = cfg->block_threads ? cfg->block_threads : 256;
+  c->var = StepVariant{cfg->block_threads ? cfg->block_threads : 256,
+                       cfg->reg_cap == 64 ? 64 : 0};
+  {
+    int n_cand = 0;
+    for (int i = 0; i < kNumStepVariants; ++i) n_cand += candidate(*cfg, kStepVariants[i]) ? 1 : 0;
+    c->tuned = (n_cand <= 1);
+  }
   int spg = cfg->steps_per_graph ? cfg->steps_per_graph : 48;
   c->steps_per_graph = ((spg + 5) / 6) * 6;
   c->t_end_dev = INFINITY;
@@ -266,7 +350,7 @@ adot_status adot_create(const adot_config* cfg, void* cuda_stream, adot_ctx** ou
     for (int k = 0; k < 3 && e == cudaSuccess; ++k)
       e = cudaMemsetAsync(c->buf[b][k], 0, elem * (size_t)n, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-  if (e != cudaSuccess) {
+  if (e != cudaSuccess || build_graph(c) != ADOT_OK) {
     free_ctx(c);
     return ADOT_E_CUDA;
   }
@@ -310,7 +394,25 @@ adot_status adot_set_state(adot_ctx* c, const double* h, const double* q, const 
   adot_status st = read_ctl(c);
   if (st) return st;
   c->state_set = true;
-  return status_from_bits(c->h_ctl->status);
+  st = status_from_bits(c->h_ctl->status);
+  if (st) return st;
+  if (!c->tuned) {
+    bool cached = false;
+    {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      auto it = g_tune_cache.find(tune_key(c));
+      if (it != g_tune_cache.end()) {
+        c->var = it->second;
+        cached = true;
+      }
+    }
+    if (cached) {
+      c->tuned = true;
+      return build_graph(c);
+    }
+    return tune(c, 8);
+  }
+  return ADOT_OK;
 }
 
 adot_status adot_get_state(adot_ctx* c, double* h, double* q, double* z, int on_device) {
@@ -424,6 +526,16 @@ adot_status adot_fluctuations(adot_ctx* c, const double* WL, const double* WR, i
     *rho_max_out = r;
   }
   return status_from_bits((unsigned)(c->h_flrho[1] & 0xffffffffu));
+}
+
+adot_status adot_autotune(adot_ctx* c, int64_t trial_steps, int32_t* block_out,
+                          int32_t* reg_cap_out) {
+  if (!c || !c->state_set || trial_steps < 1) return ADOT_E_INVALID_ARG;
+  adot_status st = tune(c, trial_steps);
+  if (st) return st;
+  if (block_out) *block_out = c->var.block;
+  if (reg_cap_out) *reg_cap_out = c->var.reg_cap ? c->var.reg_cap : -1;
+  return ADOT_OK;
 }
 
 adot_status adot_conserved_sums(adot_ctx* c, double sums_out[3]) {

@@ -53,14 +53,26 @@ struct StepParams {
 
 enum : int { BC_TRANSMISSIVE = 0, BC_PERIODIC = 1, BC_INFLOW_Q = 2, BC_OUTFLOW_H = 3, BC_INFLOW_QZ = 4 };
 
-// Supported block sizes of the step kernels.
+// A compiled variant of the step kernel: threads per block and the register
+// cap per thread (0 = none) given to the register allocator.
+struct StepVariant {
+  int block;
+  int reg_cap;
+};
+
+// The compiled variants, in the order the autotuner tries them.
+constexpr int kNumStepVariants = 6;
+constexpr StepVariant kStepVariants[kNumStepVariants] = {
+    {256, 0}, {256, 64}, {128, 0}, {128, 64}, {512, 0}, {512, 64}};
+
 bool step_block_supported(int block);
+bool step_variant_supported(StepVariant v);
 
 // One time step (Eq. scheme): fluctuations on every edge, update of every cell,
 // CFL maximum of the updated state. slot = step index mod 3.
-cudaError_t launch_step_f32(const StepParams& p, int law, int block, StateF32 in, StateF32 out,
+cudaError_t launch_step_f32(const StepParams& p, int law, StepVariant v, StateF32 in, StateF32 out,
                             int slot, cudaStream_t s);
-cudaError_t launch_step_f64(const StepParams& p, int law, int block, StateF64 in, StateF64 out,
+cudaError_t launch_step_f64(const StepParams& p, int law, StepVariant v, StateF64 in, StateF64 out,
                             int slot, cudaStream_t s);
 
 // CFL maximum of a state into ctl->s[slot].rho_bits (which must be zero), and

@@ -109,10 +109,18 @@ struct Eig {
   T u, c, c2, inv_c2, a, b;
   T l1, l2, l3;  // l1 <= l2 <= l3
   T arg;         // k2 / sqrt(4 k1^3) before clamping
+  int ks;        // index (1..3) of the root of smallest magnitude
 };
 
+__device__ __forceinline__ float d_fdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double d_fdiv(double a, double b) { return a / b; }
+
 // Steps 1-3: derivatives, k1, k2, phi, and the three roots of Eq. lambda.
-template <typename T, int LAW>
+// The root of smallest magnitude comes out of Eq. lambda as a difference of
+// two O(c) terms; with ACCURATE it is recomputed from the product of the
+// roots, l1 l2 l3 = c^2 a (the constant term of Eq. charPol times c^3), so
+// that it keeps full relative precision.
+template <typename T, int LAW, bool ACCURATE = true>
 __device__ __forceinline__ void node_eig(const LawT<T>& L, T h, T q, Eig<T>& e) {
   const T inv_h = T(1) / h;
   const T u = q * inv_h;
@@ -134,15 +142,39 @@ __device__ __forceinline__ void node_eig(const LawT<T>& L, T h, T q, Eig<T>& e) 
   const T F = T(2.0 / 3.0) * Fr;
   const T hc = T(0.5) * C;
   const T hs = T(0.86602540378443864676) * S;  // (sqrt 3 / 2) S
+  T l1 = c * (F - m * (hc + hs));  // cos(phi/3 - pi/3) = C/2 + (sqrt3/2) S
+  T l2 = c * (F - m * (hc - hs));  // cos(phi/3 + pi/3) = C/2 - (sqrt3/2) S
+  T l3 = c * (F + m * C);
+  e.ks = 0;
+  if (ACCURATE) {
+    // The quotient is never less accurate than the trigonometric value; it is
+    // skipped only when the other two roots' product is zero (a double root
+    // at 0, e.g. a fixed bed exactly at |Fr| = 1).
+    const T m1 = d_abs(l1), m2 = d_abs(l2), m3 = d_abs(l3);
+    const T ca = c2 * a;
+    if (m1 <= m2 && m1 <= m3) {
+      const T pr = l2 * l3;
+      if (pr != T(0)) l1 = ca / pr;
+      e.ks = 1;
+    } else if (m2 <= m3) {
+      const T pr = l1 * l3;
+      if (pr != T(0)) l2 = ca / pr;
+      e.ks = 2;
+    } else {
+      const T pr = l1 * l2;
+      if (pr != T(0)) l3 = ca / pr;
+      e.ks = 3;
+    }
+  }
   e.u = u;
   e.c = c;
   e.c2 = c2;
   e.inv_c2 = rc * rc;
   e.a = a;
   e.b = b;
-  e.l1 = c * (F - m * (hc + hs));  // cos(phi/3 - pi/3) = C/2 + (sqrt3/2) S
-  e.l2 = c * (F - m * (hc - hs));  // cos(phi/3 + pi/3) = C/2 - (sqrt3/2) S
-  e.l3 = c * (F + m * C);
+  e.l1 = l1;
+  e.l2 = l2;
+  e.l3 = l3;
   e.arg = arg;
 }
 
@@ -157,26 +189,43 @@ __device__ __forceinline__ void A_times(const Eig<T>& e, T v0, T v1, T v2, T& y0
 // Steps 4-5 applied to dW: |A| dW = sum_i |l_i| r_i (l_i . dW) with
 // r_i = [1, l_i, (u - l_i)^2/c^2 - 1] (Eq. RR) and
 // l_i = [c^2 - u^2 + l_j l_k, 2u - l_j - l_k, c^2] / ((l_i - l_j)(l_i - l_k)) (Eq. RR-1).
+// The entries are evaluated through identities of the roots of Eq. charPol,
+// l^3 - 2u l^2 - (c^2 - u^2 + c^2 b) l - c^2 a = 0, which avoid cancelling
+// O(c) terms: 2u - l_j - l_k = l_i (sum of roots), c^2 - u^2 + l_j l_k =
+// l_i (l_i - 2u) - c^2 b (sum of pair products), and for the two roots of
+// larger magnitude (u - l_i)^2/c^2 - 1 = b + a / l_i.
 template <typename T>
 __device__ __forceinline__ void abs_A_times_eigvec(const Eig<T>& e, T dh, T dq, T dz, T& x0, T& x1,
                                                    T& x2) {
   const T l1 = e.l1, l2 = e.l2, l3 = e.l3;
   const T e12 = l1 - l2, e13 = l1 - l3, e23 = l2 - l3;
   const T invP = T(1) / (e12 * e13 * e23);
-  const T w0 = e.c2 - e.u * e.u;
   const T tu = T(2) * e.u;
+  const T cb = e.c2 * e.b;
   const T cz = e.c2 * dz;
-  const T p1 = (w0 + l2 * l3) * dh + (tu - l2 - l3) * dq + cz;
-  const T p2 = (w0 + l3 * l1) * dh + (tu - l3 - l1) * dq + cz;
-  const T p3 = (w0 + l1 * l2) * dh + (tu - l1 - l2) * dq + cz;
+  const T p1 = (l1 * (l1 - tu) - cb) * dh + l1 * dq + cz;
+  const T p2 = (l2 * (l2 - tu) - cb) * dh + l2 * dq + cz;
+  const T p3 = (l3 * (l3 - tu) - cb) * dh + l3 * dq + cz;
   // 1/d1 = e23/P, 1/d2 = -e13/P, 1/d3 = e12/P
   const T al1 = d_abs(l1) * p1 * (e23 * invP);
   const T al2 = -d_abs(l2) * p2 * (e13 * invP);
   const T al3 = d_abs(l3) * p3 * (e12 * invP);
+  // third entries of r_i; the root of smallest magnitude takes the direct form
   const T v1 = e.u - l1, v2 = e.u - l2, v3 = e.u - l3;
+  T r1 = e.b + d_fdiv(e.a, l1);
+  T r2 = e.b + d_fdiv(e.a, l2);
+  T r3 = e.b + d_fdiv(e.a, l3);
+  if (e.ks == 1) r1 = v1 * v1 * e.inv_c2 - T(1);
+  if (e.ks == 2) r2 = v2 * v2 * e.inv_c2 - T(1);
+  if (e.ks == 3) r3 = v3 * v3 * e.inv_c2 - T(1);
+  if (e.ks == 0) {
+    r1 = v1 * v1 * e.inv_c2 - T(1);
+    r2 = v2 * v2 * e.inv_c2 - T(1);
+    r3 = v3 * v3 * e.inv_c2 - T(1);
+  }
   x0 = al1 + al2 + al3;
   x1 = al1 * l1 + al2 * l2 + al3 * l3;
-  x2 = (al1 * v1 * v1 + al2 * v2 * v2 + al3 * v3 * v3) * e.inv_c2 - x0;
+  x2 = al1 * r1 + al2 * r2 + al3 * r3;
 }
 
 // First divided difference of |x| with the coalescence reading: a pair closer
@@ -268,11 +317,12 @@ __device__ __forceinline__ void node_f32(const LawT<float>& L, const LawT<double
   abs_A_times_eigvec(e, dh, dq, dz, x[0], x[1], x[2]);
 }
 
-// Spectral radius max(|l1|, |l3|) at a state.
+// Spectral radius max(|l1|, |l3|) at a state (the extreme roots need no
+// small-root correction).
 template <typename T, int LAW>
 __device__ __forceinline__ T spectral_radius(const LawT<T>& L, T h, T q) {
   Eig<T> e;
-  node_eig<T, LAW>(L, h, q, e);
+  node_eig<T, LAW, false>(L, h, q, e);
   return d_max(d_abs(e.l1), d_abs(e.l3));
 }
 

@@ -5,9 +5,15 @@ namespace adot {
 
 bool step_block_supported(int block) { return block == 128 || block == 256 || block == 512; }
 
-cudaError_t launch_step_f32(const StepParams& p, int law, int block, StateF32 in, StateF32 out,
+bool step_variant_supported(StepVariant v) {
+  for (int i = 0; i < kNumStepVariants; ++i)
+    if (kStepVariants[i].block == v.block && kStepVariants[i].reg_cap == v.reg_cap) return true;
+  return false;
+}
+
+cudaError_t launch_step_f32(const StepParams& p, int law, StepVariant v, StateF32 in, StateF32 out,
                             int slot, cudaStream_t s) {
-  return launch_step_impl<float>(p, law, block, in, out, slot, s);
+  return launch_step_impl<float>(p, law, v, in, out, slot, s);
 }
 
 cudaError_t launch_rho_f32(const StepParams& p, int law, StateF32 st, int slot, cudaStream_t s) {

@@ -3,9 +3,9 @@
 
 namespace adot {
 
-cudaError_t launch_step_f64(const StepParams& p, int law, int block, StateF64 in, StateF64 out,
+cudaError_t launch_step_f64(const StepParams& p, int law, StepVariant v, StateF64 in, StateF64 out,
                             int slot, cudaStream_t s) {
-  return launch_step_impl<double>(p, law, block, in, out, slot, s);
+  return launch_step_impl<double>(p, law, v, in, out, slot, s);
 }
 
 cudaError_t launch_rho_f64(const StepParams& p, int law, StateF64 st, int slot, cudaStream_t s) {

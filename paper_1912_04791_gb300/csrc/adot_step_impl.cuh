@@ -164,8 +164,15 @@ __device__ __forceinline__ void edge_fluct(const StepParams& p, const typename P
   }
 }
 
-template <typename R, int LAW, int B>
-__global__ void __launch_bounds__(B) k_step(const StepParams p, const typename Prec<R>::State in,
+// Resident blocks per SM requested from the register allocator: CAP registers
+// per thread out of the SM's 65536, or no request (CAP = 0).
+template <int B, int CAP>
+struct MinBlocks {
+  static constexpr int value = CAP ? 65536 / (B * CAP) : 1;
+};
+
+template <typename R, int LAW, int B, int CAP>
+__global__ void __launch_bounds__(B, MinBlocks<B, CAP>::value) k_step(const StepParams p, const typename Prec<R>::State in,
                                             const typename Prec<R>::State out, const int slot) {
   using S = typename Prec<R>::S;
   __shared__ R sDp[3][B];
@@ -293,27 +300,34 @@ __global__ void __launch_bounds__(256) k_rho(const StepParams p, const typename 
 }
 
 template <typename R, int LAW>
-cudaError_t launch_step_law(const StepParams& p, int block, typename Prec<R>::State in,
+cudaError_t launch_step_law(const StepParams& p, StepVariant v, typename Prec<R>::State in,
                             typename Prec<R>::State out, int slot, cudaStream_t s) {
   if (p.ctl == nullptr || p.n < 1) return cudaErrorInvalidValue;
   // edges 0..n, B-1 new edges per block: ceil((n+1)/(B-1)) blocks
-  const int64_t cells = block - 1;
+  const int64_t cells = v.block - 1;
   const int64_t g = (p.n + 1 + cells - 1) / cells;
   if (g > 0x7fffffffLL) return cudaErrorInvalidValue;
-  switch (block) {
-    case 128: k_step<R, LAW, 128><<<(unsigned)g, 128, 0, s>>>(p, in, out, slot); break;
-    case 256: k_step<R, LAW, 256><<<(unsigned)g, 256, 0, s>>>(p, in, out, slot); break;
-    case 512: k_step<R, LAW, 512><<<(unsigned)g, 512, 0, s>>>(p, in, out, slot); break;
-    default: return cudaErrorInvalidValue;
+  const unsigned G = (unsigned)g;
+#define ADOT_STEP_CASE(BB, CC)                                       \
+  if (v.block == BB && v.reg_cap == CC) {                            \
+    k_step<R, LAW, BB, CC><<<G, BB, 0, s>>>(p, in, out, slot);       \
+    return cudaGetLastError();                                       \
   }
-  return cudaGetLastError();
+  ADOT_STEP_CASE(128, 0)
+  ADOT_STEP_CASE(128, 64)
+  ADOT_STEP_CASE(256, 0)
+  ADOT_STEP_CASE(256, 64)
+  ADOT_STEP_CASE(512, 0)
+  ADOT_STEP_CASE(512, 64)
+#undef ADOT_STEP_CASE
+  return cudaErrorInvalidValue;
 }
 
 template <typename R>
-cudaError_t launch_step_impl(const StepParams& p, int law, int block, typename Prec<R>::State in,
+cudaError_t launch_step_impl(const StepParams& p, int law, StepVariant v, typename Prec<R>::State in,
                              typename Prec<R>::State out, int slot, cudaStream_t s) {
-  if (law == LAW_GRASS) return launch_step_law<R, LAW_GRASS>(p, block, in, out, slot, s);
-  if (law == LAW_MPM) return launch_step_law<R, LAW_MPM>(p, block, in, out, slot, s);
+  if (law == LAW_GRASS) return launch_step_law<R, LAW_GRASS>(p, v, in, out, slot, s);
+  if (law == LAW_MPM) return launch_step_law<R, LAW_MPM>(p, v, in, out, slot, s);
   return cudaErrorInvalidValue;
 }
 

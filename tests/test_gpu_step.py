@@ -39,13 +39,16 @@ def _run_gpu(gpu, P, prec, steps=None, t_end=None, **kw):
     return h, q, z, t, nsteps, dt
 
 
+VARIANTS = [(128, 64), (128, -1), (256, 64), (256, -1), (512, 64), (512, -1)]
+
+
 @pytest.mark.parametrize("n", [1, 2, 255, 256, 511, 1000, 2049])
-@pytest.mark.parametrize("block", [128, 256, 512])
-def test_fp64_smooth_periodic_matches_oracle(gpu, n, block):
+@pytest.mark.parametrize("block,cap", VARIANTS)
+def test_fp64_smooth_periodic_matches_oracle(gpu, n, block, cap):
     P = W.smooth_periodic(n)
     K = 60
     ho, qo, zo, to, _, _ = O.run(_ocfg(P), P.h, P.q, P.z, max_steps=K)
-    h, q, z, t, steps, _ = _run_gpu(gpu, P, gpu.FP64, steps=K, block_threads=block)
+    h, q, z, t, steps, _ = _run_gpu(gpu, P, gpu.FP64, steps=K, block_threads=block, reg_cap=cap)
     assert steps == K
     assert t == pytest.approx(to, rel=1e-13)
     for a, b in ((h, ho), (q, qo), (z, zo)):
@@ -105,6 +108,37 @@ def test_fp32_movable_bed_riemann_l1(gpu):
     assert t == P.t_end
     for a, b in ((h, ho), (q, qo), (z, zo)):
         assert np.abs(a - b).sum() <= 1e-5 * np.abs(b).sum()
+
+
+def test_fp32_variants_agree(gpu):
+    """Every compiled variant evaluates each edge and cell with the same code:
+    float32 increments agree to 1e-7 of their L1 norm."""
+    P = W.smooth_periodic(5003)
+    ref = None
+    for block, cap in VARIANTS:
+        h, q, z, *_ = _run_gpu(gpu, P, gpu.FP32, steps=50, block_threads=block, reg_cap=cap)
+        inc = np.concatenate([h - P.h, q - P.q, z - P.z])
+        if ref is None:
+            ref = inc
+        assert np.abs(inc - ref).sum() <= 1e-7 * np.abs(ref).sum()
+
+
+def test_autotune_keeps_state_and_picks_a_variant(gpu):
+    P = W.smooth_periodic(20000)
+    with gpu.Solver(gpu.config_for(P, gpu.FP32, block_threads=256, reg_cap=64)) as s:
+        s.set_state(P.h, P.q, P.z)
+        s.step(12)
+        ref = s.get_state()
+    with gpu.Solver(gpu.config_for(P, gpu.FP32)) as s:  # every field free: tuned in set_state
+        s.set_state(P.h, P.q, P.z)
+        b, r = gpu.adot_autotune(s.ctx, 4)
+        assert (b, r) in [(bb, cc) for bb, cc in VARIANTS]
+        t, steps, _ = s.query()
+        assert t == 0.0 and steps == 0
+        s.step(12)
+        got = s.get_state()
+    for a, b_ in zip(got, ref):
+        assert np.abs((a - b_)).sum() <= 1e-7 * max(np.abs(b_).sum(), 1.0)
 
 
 @pytest.mark.parametrize("prec", [0, 1])
