@@ -158,6 +158,33 @@ adot_status adot_autotune(adot_ctx* ctx, int64_t trial_steps, int32_t* block_out
  * bit-reproducible). Multiply by dx for the integrals. */
 adot_status adot_conserved_sums(adot_ctx* ctx, double sums_out[3]);
 
+/* Largest number of cells adot_step_noalloc accepts. */
+#define ADOT_NOALLOC_MAX_CELLS 65536
+
+/* Allocation-free time stepping. The paper has no counterpart: this entry point
+ * serves callers that cannot call cudaMalloc, such as a custom operation inside
+ * another framework whose device memory must come from that framework's
+ * allocator, or a real-time loop that reserves all memory before it starts.
+ * It advances a caller-owned float64 state by n_steps steps of Eq. scheme and
+ * allocates nothing, on the device or the host.
+ *  - cfg: as for adot_create; precision must be ADOT_FP64 (else
+ *    ADOT_E_UNSUPPORTED) and n_cells <= ADOT_NOALLOC_MAX_CELLS (else
+ *    ADOT_E_INVALID_ARG). block_threads, reg_cap and steps_per_graph are
+ *    ignored; cfg->device >= 0 is made current.
+ *  - h, q, z: device arrays of n_cells float64, read and overwritten in place.
+ *  - t_io: host pointer; the start time in, the time after the steps out.
+ *  - cuda_stream: a cudaStream_t, or NULL for the legacy default stream. The call
+ *    waits for the stream before it returns, and reports the first device-side
+ *    error as adot_step does.
+ * The second state buffer and the control block live in a file-scope device
+ * array of ADOT_NOALLOC_MAX_CELLS cells (about 1.5 MB) that every GPU which
+ * loads the library holds until the process exits. All calls share it: calls
+ * that overlap on the GPU race, and each call clears the control block before
+ * use. The first call on a device looks up the array's device address (once per
+ * device); make that first call before any stream capture. */
+adot_status adot_step_noalloc(const adot_config* cfg, double* h, double* q, double* z,
+                              int64_t n_steps, double* t_io, void* cuda_stream);
+
 /* Name of a status code (static string). */
 const char* adot_status_string(adot_status s);
 

@@ -73,6 +73,7 @@ def lib() -> ctypes.CDLL:
             "adot_fluctuations": ([_P, _P, _P, i64, _P, _P, _D, i32], i32),
             "adot_conserved_sums": ([_P, _D], i32),
             "adot_autotune": ([_P, i64, ctypes.POINTER(i32), ctypes.POINTER(i32)], i32),
+            "adot_step_noalloc": ([ctypes.POINTER(Config), _P, _P, _P, i64, _D, _P], i32),
             "adot_status_string": ([i32], ctypes.c_char_p),
             "adot_version": ([], ctypes.c_char_p),
         }
@@ -221,6 +222,21 @@ def adot_autotune(ctx: int, trial_steps: int = 8):
     b, r = ctypes.c_int32(), ctypes.c_int32()
     _check(lib().adot_autotune(ctx, trial_steps, ctypes.byref(b), ctypes.byref(r)), "adot_autotune")
     return b.value, r.value
+
+
+def adot_step_noalloc(cfg: Config, h, q, z, n_steps: int, t0: float = 0.0, stream=None) -> float:
+    """Allocation-free stepping of caller-owned float64 CUDA tensors h, q, z
+    (in place); returns the time after the steps."""
+    (ph, dh), (pq, dq), (pz, dz) = _ptr(h, cfg.n_cells), _ptr(q, cfg.n_cells), _ptr(z, cfg.n_cells)
+    if not (dh == dq == dz == 1):
+        raise ValueError("adot_step_noalloc takes device arrays")
+    s = stream
+    if s is not None and not isinstance(s, int):
+        s = s.cuda_stream
+    t = ctypes.c_double(t0)
+    _check(lib().adot_step_noalloc(ctypes.byref(cfg), ph, pq, pz, n_steps, ctypes.byref(t), s),
+           "adot_step_noalloc")
+    return t.value
 
 
 def adot_conserved_sums(ctx: int) -> np.ndarray:

@@ -71,7 +71,14 @@ adot_status status_from_bits(unsigned bits) {
 
 bool valid_bc(int k) { return k >= ADOT_BC_TRANSMISSIVE && k <= ADOT_BC_INFLOW_QZ; }
 
-adot_status validate(const adot_config* c) {
+}  // namespace
+
+namespace adot {
+adot_status validate_config(const adot_config* c);
+void make_step_params(const adot_config* cfg, StepParams* p);
+}  // namespace adot
+
+adot_status adot::validate_config(const adot_config* c) {
   if (!c) return ADOT_E_INVALID_ARG;
   if (c->n_cells < 1) return ADOT_E_INVALID_ARG;
   if (!(c->x_max > c->x_min) || !isfinite(c->x_min) || !isfinite(c->x_max)) return ADOT_E_INVALID_ARG;
@@ -93,6 +100,34 @@ adot_status validate(const adot_config* c) {
   if (c->steps_per_graph < 0 || c->device < -1) return ADOT_E_INVALID_ARG;
   return ADOT_OK;
 }
+
+// Launch parameters of a configuration (everything but the control block).
+void adot::make_step_params(const adot_config* cfg, StepParams* out) {
+  StepParams& p = *out;
+  p = StepParams{};
+  const int64_t n = cfg->n_cells;
+  p.n = n;
+  p.dx = (cfg->x_max - cfg->x_min) / (double)n;
+  p.cfl = cfg->cfl;
+  p.periodic = (cfg->bc_left == ADOT_BC_PERIODIC) ? 1 : 0;
+  p.bc_left = cfg->bc_left;
+  p.bc_right = cfg->bc_right;
+  for (int i = 0; i < 3; ++i) {
+    p.bcl[i] = cfg->bc_left_value[i];
+    p.bcr[i] = cfg->bc_right_value[i];
+  }
+  const adot_law& L = cfg->law;
+  double K3 = 3.0 * L.xi * L.Ag;
+  double mpm_c = 0.0, mpm_scale = 0.0;
+  if (L.kind == ADOT_LAW_MPM) {
+    mpm_c = L.manning_n * L.manning_n / ((L.s_rel - 1.0) * L.d50);
+    mpm_scale = L.xi * sqrt(L.g * (L.s_rel - 1.0) * L.d50 * L.d50 * L.d50);
+  }
+  p.ld = LawT<double>{L.g, K3, mpm_c, mpm_scale};
+  p.lf = LawT<float>{(float)L.g, (float)K3, (float)mpm_c, (float)mpm_scale};
+}
+
+namespace {
 
 StateF32 st32(adot_ctx* c, int which) {
   return StateF32{(float2*)c->buf[which][0], (float2*)c->buf[which][1], (float2*)c->buf[which][2]};
@@ -277,7 +312,7 @@ const char* adot_status_string(adot_status s) {
 adot_status adot_create(const adot_config* cfg, void* cuda_stream, adot_ctx** out) {
   if (!out) return ADOT_E_INVALID_ARG;
   *out = nullptr;
-  adot_status st = validate(cfg);
+  adot_status st = validate_config(cfg);
   if (st) return st;
   int dev = 0;
   if (cfg->device >= 0 && cudaSetDevice(cfg->device) != cudaSuccess) return ADOT_E_CUDA;
@@ -289,7 +324,7 @@ adot_status adot_create(const adot_config* cfg, void* cuda_stream, adot_ctx** ou
   c->prec = cfg->precision;
   c->law = cfg->law.kind;
   c->var = StepVariant{cfg->block_threads ? cfg->block_threads : 256,
-                       cfg->reg_cap == 64 ? 64 : 0};
+                       cfg->reg_cap == -1 ? 0 : 64};
   {
     int n_cand = 0;
     for (int i = 0; i < kNumStepVariants; ++i) n_cand += candidate(*cfg, kStepVariants[i]) ? 1 : 0;
@@ -300,26 +335,8 @@ adot_status adot_create(const adot_config* cfg, void* cuda_stream, adot_ctx** ou
   c->t_end_dev = INFINITY;
   const int64_t n = cfg->n_cells;
 
+  make_step_params(cfg, &c->p);
   StepParams& p = c->p;
-  p.n = n;
-  p.dx = (cfg->x_max - cfg->x_min) / (double)n;
-  p.cfl = cfg->cfl;
-  p.periodic = (cfg->bc_left == ADOT_BC_PERIODIC) ? 1 : 0;
-  p.bc_left = cfg->bc_left;
-  p.bc_right = cfg->bc_right;
-  for (int i = 0; i < 3; ++i) {
-    p.bcl[i] = cfg->bc_left_value[i];
-    p.bcr[i] = cfg->bc_right_value[i];
-  }
-  const adot_law& L = cfg->law;
-  double K3 = 3.0 * L.xi * L.Ag;
-  double mpm_c = 0.0, mpm_scale = 0.0;
-  if (L.kind == ADOT_LAW_MPM) {
-    mpm_c = L.manning_n * L.manning_n / ((L.s_rel - 1.0) * L.d50);
-    mpm_scale = L.xi * sqrt(L.g * (L.s_rel - 1.0) * L.d50 * L.d50 * L.d50);
-  }
-  p.ld = LawT<double>{L.g, K3, mpm_c, mpm_scale};
-  p.lf = LawT<float>{(float)L.g, (float)K3, (float)mpm_c, (float)mpm_scale};
 
   cudaError_t e = cudaSuccess;
   if (cuda_stream) {
