@@ -30,9 +30,12 @@ METRIC = "cell-updates/s at N=1e7 (A-DOT FP32 vs surrogate) at L1 err vs FP64 or
 UNIT = "cell-updates/s"
 # FP32 flops per cell-update of the fused step kernel (FMA = 2): three
 # Gauss-Legendre nodes of the edge fluctuation, the float-float update and the
-# CFL spectral radius of the new state. Derivation and the ncu cross-check of
-# this count are in the design notes.
-FLOPS_PER_CELL_UPDATE = 1240.0
+# CFL spectral radius of the new state, counted from ncu's executed FFMA/FADD/
+# FMUL thread instructions of one launch divided by the cells it updates.
+FLOPS_PER_CELL_UPDATE = 636.1
+# DRAM read + write bytes per cell-update of that launch (ncu, N = 4e6): the
+# 24 B read match the algorithmic read; part of the 24 B written is still in L2.
+DRAM_BYTES_PER_CELL_UPDATE = (96.09e6 + 59.29e6) / 4e6
 BYTES_PER_CELL_UPDATE = 48.0  # float-float state: 3 x 8 B read + 3 x 8 B written
 
 
@@ -58,6 +61,8 @@ def parse():
                     help="oracle steps on the full workload for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--ensemble-t-end", type=float, default=0.02,
+                    help="t_end of the 4096-channel ensemble measurement (0 = skip)")
     ap.add_argument("--accuracy-steps", type=int, default=96,
                     help="steps of the FP32-vs-FP64 increment check (0 = skip)")
     return ap.parse_args()
@@ -299,6 +304,30 @@ def main():
                                                          / np.abs(b - a0).sum())
             accuracy[f"l1_rel_state_{name}"] = float(np.abs(a - b).sum() / np.abs(b).sum())
 
+    # batched ensemble: 4096 movable-bed Riemann channels, N_c log-uniform in [1e3, 1e5]
+    ensemble = None
+    if args.ensemble_t_end > 0 and rank == 0:
+        E = W.riemann_ensemble(4096)
+        with adot.Ensemble.from_workload(E, adot.FP32, device=local, stream=stream) as ens:
+            ens.set_state(E.h, E.q, E.z)
+            blk, n_tiles, grid = ens.info()
+            torch.cuda.synchronize(dev)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            launches = ens.run_to(args.ensemble_t_end)
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+            t_c, steps_c, cu = ens.query()
+            ms_e = a.elapsed_time(b)
+        ensemble = {"workload": "4096 movable-bed Riemann channels, N_c log-uniform [1e3,1e5], FP32",
+                    "total_cells": int(E.n_cells.sum()), "t_end": args.ensemble_t_end,
+                    "cell_updates": int(cu), "seconds": ms_e * 1e-3,
+                    "cell_updates_per_s": cu / (ms_e * 1e-3), "launches": int(launches),
+                    "max_steps": int(steps_c.max()), "min_steps": int(steps_c.min()),
+                    "tile_threads": blk, "tiles": n_tiles, "grid": grid,
+                    "all_at_t_end": bool((t_c == args.ensemble_t_end).all())}
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         rate, sec, thr = oracle_throughput(n, args.cpu_steps)
@@ -320,13 +349,16 @@ def main():
                        "l2": "inputs larger than L2 (2 x 240 MB state buffers, no flush)",
                        "parallelism": "replicas" if ws > 1 else "single"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": f_peak, "unit": "TFLOP/s",
-                         "frac": achieved / f_peak, "traffic": None,
+                         "frac": achieved / f_peak,
+                         "traffic": DRAM_BYTES_PER_CELL_UPDATE * n,
+                         "traffic_note": "ncu dram read+write of one launch at N=4e6, scaled to N",
                          "kernel": f"k_step<float,GRASS,{block},{max(reg_cap, 0)}>",
                          "peak_source": "152 SM x 128 FP32 lanes x 2 x 2070 MHz (derived)",
                          "hbm_achieved_gbs": BYTES_PER_CELL_UPDATE * n / per_launch_s / 1e9,
                          "hbm_peak_gbs": measured_peaks().get("hbm_gbs", 6800.0)},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps, "clocks": clocks,
             "accuracy": accuracy, "sim_time_after_timed_steps": t_sim, "variants": variants,
+            "ensemble": ensemble,
         }
         print(json.dumps(line), flush=True)
     if dist:

@@ -158,6 +158,60 @@ adot_status adot_autotune(adot_ctx* ctx, int64_t trial_steps, int32_t* block_out
  * bit-reproducible). Multiply by dx for the integrals. */
 adot_status adot_conserved_sums(adot_ctx* ctx, double sums_out[3]);
 
+/* ---- Batched ensembles of independent channels ------------------------------
+ * Each channel is a separate dSVE problem advanced by Eq. scheme with the DOT
+ * fluctuations of Eq. DOTjumpN and its own time step dt_c = cfl dx_c / rho_c
+ * (reading of the unstated CFL rule as for a single channel), Grass law
+ * (Eq. Grass) with a per-channel A_g, transmissive ends. The channels' cells lie
+ * end to end in the state arrays: channel c owns cells off[c] .. off[c+1]-1 with
+ * off[c] = n_cells[0] + ... + n_cells[c-1]. One kernel launch advances every
+ * running channel by one of its own steps; channels stop at t_end individually. */
+typedef struct {
+  int32_t n_channels;       /* >= 1 */
+  const int64_t* n_cells;   /* host [n_channels], each >= 1 */
+  const double* length;     /* host [n_channels], channel length [m] (dx_c = length/n_cells) */
+  const double* Ag;         /* host [n_channels], Grass coefficient [s^2/m] */
+  double g, xi, cfl;        /* shared: gravity, 1/(1-p), CFL number in (0, 1] */
+  int32_t precision;        /* ADOT_FP64 or ADOT_FP32 (float-float state) */
+  int32_t block_threads;    /* tile = block_threads - 1 cells: 128, 256, 512; 0 = autotuned */
+  int32_t steps_per_graph;  /* launches captured per CUDA graph; 0 = default (48) */
+  int32_t device;           /* CUDA device ordinal; -1 = current */
+} adot_ensemble_config;
+
+typedef struct adot_ensemble adot_ensemble;
+
+/* Creates an ensemble: validates cfg (ADOT_E_INVALID_ARG), copies the host
+ * arrays, allocates the device state (two ping-pong copies of all cells), the
+ * per-channel control arrays and the tile list (channels longest first). */
+adot_status adot_ensemble_create(const adot_ensemble_config* cfg, void* cuda_stream,
+                                 adot_ensemble** out);
+void adot_ensemble_destroy(adot_ensemble* ens);
+
+/* Copies in the concatenated float64 state (sum n_cells values each, host or
+ * device per on_device), puts every channel at t = 0 with no steps taken and
+ * computes each channel's first CFL maximum. With block_threads = 0 the first
+ * call times the tile sizes (two trial launches each, state unchanged). */
+adot_status adot_ensemble_set_state(adot_ensemble* ens, const double* h, const double* q,
+                                    const double* z, int on_device);
+adot_status adot_ensemble_get_state(adot_ensemble* ens, double* h, double* q, double* z,
+                                    int on_device);
+
+/* Advances every channel until its own time reaches t_end (last step shortened
+ * to land on it). *launches_out (may be NULL): kernel launches issued. */
+adot_status adot_ensemble_run_to(adot_ensemble* ens, double t_end, int64_t* launches_out);
+
+/* Advances every channel by n_steps of its own steps (no end time). */
+adot_status adot_ensemble_step(adot_ensemble* ens, int64_t n_steps);
+
+/* Per-channel time and step count (host arrays [n_channels], may be NULL) and
+ * the total cell-updates sum_c steps_c n_cells_c; waits for the stream. */
+adot_status adot_ensemble_query(adot_ensemble* ens, double* t_out, int64_t* steps_out,
+                                int64_t* cell_updates_out);
+
+/* Tile size in use (block threads), number of tiles and the resident grid. */
+adot_status adot_ensemble_info(adot_ensemble* ens, int32_t* block_out, int64_t* tiles_out,
+                               int32_t* grid_out);
+
 /* Largest number of cells adot_step_noalloc accepts. */
 #define ADOT_NOALLOC_MAX_CELLS 65536
 

@@ -48,6 +48,14 @@ class Config(ctypes.Structure):
                 ("reg_cap", ctypes.c_int32)]
 
 
+class EnsembleConfig(ctypes.Structure):
+    _fields_ = [("n_channels", ctypes.c_int32), ("n_cells", ctypes.POINTER(ctypes.c_int64)),
+                ("length", ctypes.POINTER(ctypes.c_double)), ("Ag", ctypes.POINTER(ctypes.c_double)),
+                ("g", ctypes.c_double), ("xi", ctypes.c_double), ("cfl", ctypes.c_double),
+                ("precision", ctypes.c_int32), ("block_threads", ctypes.c_int32),
+                ("steps_per_graph", ctypes.c_int32), ("device", ctypes.c_int32)]
+
+
 _lib = None
 _P = ctypes.c_void_p
 _D = ctypes.POINTER(ctypes.c_double)
@@ -74,6 +82,15 @@ def lib() -> ctypes.CDLL:
             "adot_conserved_sums": ([_P, _D], i32),
             "adot_autotune": ([_P, i64, ctypes.POINTER(i32), ctypes.POINTER(i32)], i32),
             "adot_step_noalloc": ([ctypes.POINTER(Config), _P, _P, _P, i64, _D, _P], i32),
+            "adot_ensemble_create": ([ctypes.POINTER(EnsembleConfig), _P, ctypes.POINTER(_P)], i32),
+            "adot_ensemble_destroy": ([_P], None),
+            "adot_ensemble_set_state": ([_P, _P, _P, _P, i32], i32),
+            "adot_ensemble_get_state": ([_P, _P, _P, _P, i32], i32),
+            "adot_ensemble_run_to": ([_P, dbl, ctypes.POINTER(i64)], i32),
+            "adot_ensemble_step": ([_P, i64], i32),
+            "adot_ensemble_query": ([_P, _P, _P, ctypes.POINTER(i64)], i32),
+            "adot_ensemble_info": ([_P, ctypes.POINTER(i32), ctypes.POINTER(i64),
+                                    ctypes.POINTER(i32)], i32),
             "adot_status_string": ([i32], ctypes.c_char_p),
             "adot_version": ([], ctypes.c_char_p),
         }
@@ -237,6 +254,89 @@ def adot_step_noalloc(cfg: Config, h, q, z, n_steps: int, t0: float = 0.0, strea
     _check(lib().adot_step_noalloc(ctypes.byref(cfg), ph, pq, pz, n_steps, ctypes.byref(t), s),
            "adot_step_noalloc")
     return t.value
+
+
+class Ensemble:
+    """Owning wrapper around an adot_ensemble (batched independent channels)."""
+
+    def __init__(self, n_cells, length, Ag, xi, cfl=0.9, g=9.81, precision=FP32, block_threads=0,
+                 steps_per_graph=0, device=-1, stream=None):
+        self._n = np.ascontiguousarray(n_cells, dtype=np.int64)
+        self._len = np.ascontiguousarray(length, dtype=np.float64)
+        self._ag = np.ascontiguousarray(Ag, dtype=np.float64)
+        c = EnsembleConfig()
+        c.n_channels = len(self._n)
+        c.n_cells = self._n.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+        c.length = self._len.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        c.Ag = self._ag.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        c.g, c.xi, c.cfl = g, xi, cfl
+        c.precision, c.block_threads, c.steps_per_graph, c.device = precision, block_threads, \
+            steps_per_graph, device
+        s = stream
+        if s is not None and not isinstance(s, int):
+            s = s.cuda_stream
+        out = _P()
+        _check(lib().adot_ensemble_create(ctypes.byref(c), s, ctypes.byref(out)),
+               "adot_ensemble_create")
+        self.ptr = out.value
+        self.C = len(self._n)
+        self.total = int(self._n.sum())
+
+    @classmethod
+    def from_workload(cls, E, precision=FP32, **kw):
+        return cls(E.n_cells, E.length, E.Ag, E.xi, E.cfl, E.g, precision, **kw)
+
+    def set_state(self, h, q, z):
+        (ph, dh), (pq, dq), (pz, dz) = _ptr(h, self.total), _ptr(q, self.total), _ptr(z, self.total)
+        if not dh == dq == dz:
+            raise ValueError("h, q, z must all be on the host or all on the device")
+        _check(lib().adot_ensemble_set_state(self.ptr, ph, pq, pz, dh), "adot_ensemble_set_state")
+
+    def get_state(self):
+        h, q, z = np.empty(self.total), np.empty(self.total), np.empty(self.total)
+        _check(lib().adot_ensemble_get_state(self.ptr, h.ctypes.data, q.ctypes.data, z.ctypes.data, 0),
+               "adot_ensemble_get_state")
+        return h, q, z
+
+    def run_to(self, t_end: float) -> int:
+        n = ctypes.c_int64()
+        _check(lib().adot_ensemble_run_to(self.ptr, t_end, ctypes.byref(n)), "adot_ensemble_run_to")
+        return n.value
+
+    def step(self, n: int) -> None:
+        _check(lib().adot_ensemble_step(self.ptr, n), "adot_ensemble_step")
+
+    def query(self):
+        t = np.empty(self.C)
+        s = np.empty(self.C, dtype=np.int64)
+        cu = ctypes.c_int64()
+        _check(lib().adot_ensemble_query(self.ptr, t.ctypes.data, s.ctypes.data, ctypes.byref(cu)),
+               "adot_ensemble_query")
+        return t, s, cu.value
+
+    def info(self):
+        b, g = ctypes.c_int32(), ctypes.c_int32()
+        nt = ctypes.c_int64()
+        _check(lib().adot_ensemble_info(self.ptr, ctypes.byref(b), ctypes.byref(nt), ctypes.byref(g)),
+               "adot_ensemble_info")
+        return b.value, nt.value, g.value
+
+    def close(self):
+        if getattr(self, "ptr", 0):
+            lib().adot_ensemble_destroy(self.ptr)
+            self.ptr = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def adot_conserved_sums(ctx: int) -> np.ndarray:

@@ -1,0 +1,781 @@
+// Batched ensemble of independent channels (adot_ensemble_*).
+//
+// Every channel is its own first-order DOT problem (Eq. scheme, Grass law with
+// its own A_g, transmissive ends) with its own dt = cfl dx_c / rho_c. The
+// channels' cells lie end to end in one state array. One launch advances every
+// running channel by one of its own steps:
+//  - channels are cut into tiles of B-1 cells (B threads evaluate B edges and
+//    update the B-1 cells between them, as in the single-channel kernel); the
+//    tile list is ordered longest channel first;
+//  - a fixed grid (resident blocks x SMs) walks the tiles [0, A), where A is
+//    one past the last tile of any channel that was running at the start of
+//    the previous step (set by device atomics), so finished short channels
+//    drop out of the walk without a host round trip;
+//  - each channel has three rotating control slots (t, dt, steps, CFL max);
+//    the channel's first tile ("leader") writes the next slot, the other tiles
+//    only read the current one and fold their CFL maxima in with atomicMax;
+//  - a channel that has reached t_end copies its state across once (so both
+//    ping-pong buffers hold it; the global step of that copy is kept in fin[c])
+//    and is skipped from then on.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "../../include/adot.h"
+#include "adot_step_impl.cuh"
+
+namespace adot {
+
+struct EnsDev {
+  // per channel, [3][C] rotating slots
+  double* t;
+  double* dt;
+  long long* steps;
+  unsigned long long* rho;
+  // per channel, latest values written by the leader
+  double* t_cur;
+  double* dt_cur;
+  long long* steps_cur;
+  long long* fin;  // global step of the copy step after t_end (LLONG_MAX before)
+  // global
+  long long* gstep;  // [3]
+  int* active;       // [3] tile bound
+  double* t_end;     // scalar
+  unsigned* status;  // scalar
+};
+
+struct EnsParams {
+  int C;
+  int64_t n_tiles;
+  double cfl;
+  float g_f;
+  double g_d;
+  const int64_t* off;   // [C+1]
+  const double* dx;     // [C]
+  const float* K3f;     // [C] 3 xi A_g
+  const double* K3d;    // [C]
+  const int* tile_chan; // [T]
+  const int* tile_e0;   // [T] first edge of the tile within its channel
+  const int* chan_tile_end;  // [C] one past the channel's last tile
+  EnsDev d;
+};
+
+template <typename R, int B>
+__global__ void __launch_bounds__(B, 65536 / (B * 64))
+    k_ens_step(const EnsParams p, const typename Prec<R>::State in,
+               const typename Prec<R>::State out, const int slot) {
+  using S = typename Prec<R>::S;
+  __shared__ R sDp[3][B];
+  __shared__ R sRed[B / 32];
+  __shared__ R sNu;
+  __shared__ int sMode;  // 0 step, 1 copy (first step after t_end), 2 skip
+
+  const int tid = threadIdx.x;
+  const int C = p.C;
+  const int nx = (slot + 1) % 3, pv = (slot + 2) % 3;
+  const int A = p.d.active[slot];
+  const long long k = p.d.gstep[slot];
+  const double t_end = *p.d.t_end;
+  if (blockIdx.x == 0 && tid == 0) {
+    p.d.active[pv] = 0;
+    p.d.gstep[nx] = k + 1;
+  }
+  unsigned flags = 0;
+  for (int64_t tile = blockIdx.x; tile < A; tile += gridDim.x) {
+    const int c = p.tile_chan[tile];
+    const int64_t e0 = p.tile_e0[tile];
+    const int64_t base = p.off[c];
+    const int64_t nc = p.off[c + 1] - base;
+    const int64_t e = e0 + tid;
+    // states on both sides of edge e (cells e-1 and e of the channel; copies at the ends)
+    S wl[3], wr[3];
+    const bool valid = e <= nc;
+    if (valid) {
+      const int64_t il = (e > 0) ? e - 1 : 0;
+      const int64_t ir = (e < nc) ? e : nc - 1;
+      wl[0] = in.h[base + il];
+      wl[1] = in.q[base + il];
+      wl[2] = in.z[base + il];
+      wr[0] = in.h[base + ir];
+      wr[1] = in.q[base + ir];
+      wr[2] = in.z[base + ir];
+    }
+    if (tid == 0) {
+      int mode;
+      const long long fin = p.d.fin[c];
+      const double t = p.d.t[slot * C + c];
+      double dt = 0.0;
+      double tn = t;
+      if (k > fin) {
+        mode = 2;
+      } else if (!(t < t_end)) {
+        mode = 1;
+      } else {
+        mode = 0;
+        const double rho = Prec<R>::from_bits(p.d.rho[slot * C + c]);
+        dt = p.cfl * p.dx[c] / rho;
+        tn = t + dt;
+        if (tn >= t_end) {
+          dt = t_end - t;
+          tn = t_end;
+        }
+      }
+      sMode = mode;
+      sNu = (mode == 0) ? R(dt / p.dx[c]) : R(0);
+      if (e0 == 0 && mode != 2) {  // leader
+        const long long st = p.d.steps[slot * C + c] + (mode == 0 ? 1 : 0);
+        p.d.t[nx * C + c] = tn;
+        p.d.dt[nx * C + c] = (mode == 0) ? dt : p.d.dt[slot * C + c];
+        p.d.steps[nx * C + c] = st;
+        p.d.rho[pv * C + c] = 0ull;
+        p.d.t_cur[c] = tn;
+        p.d.steps_cur[c] = st;
+        if (mode == 0) {
+          p.d.dt_cur[c] = dt;
+          atomicMax(&p.d.active[nx], p.chan_tile_end[c]);
+        } else {
+          p.d.rho[nx * C + c] = p.d.rho[slot * C + c];
+          p.d.fin[c] = k;
+        }
+      }
+    }
+    __syncthreads();
+    const int mode = sMode;
+    const R nu = sNu;
+    if (mode == 2) {
+      __syncthreads();
+      continue;
+    }
+    const int64_t i = e - 1;  // cell updated by this thread
+    if (mode == 1) {
+      if (tid >= 1 && i < nc) {
+        out.h[base + i] = wl[0];
+        out.q[base + i] = wl[1];
+        out.z[base + i] = wl[2];
+      }
+      __syncthreads();
+      continue;
+    }
+    StepParams lp;
+    lp.lf = LawT<float>{p.g_f, p.K3f[c], 0.0f, 0.0f};
+    lp.ld = LawT<double>{p.g_d, p.K3d[c], 0.0, 0.0};
+    R dm[3] = {R(0), R(0), R(0)}, dp[3] = {R(0), R(0), R(0)};
+    if (valid && e > 0 && e < nc) edge_fluct<R, LAW_GRASS>(lp, wl, wr, dm, dp, flags);
+    sDp[0][tid] = dp[0];
+    sDp[1][tid] = dp[1];
+    sDp[2][tid] = dp[2];
+    __syncthreads();
+    R rho = R(0);
+    if (tid >= 1 && i < nc) {
+      const S nh = Prec<R>::add(wl[0], -nu * (dm[0] + sDp[0][tid - 1]));
+      const S nq = Prec<R>::add(wl[1], -nu * (dm[1] + sDp[1][tid - 1]));
+      const S nz = Prec<R>::add(wl[2], -nu * (dm[2] + sDp[2][tid - 1]));
+      out.h[base + i] = nh;
+      out.q[base + i] = nq;
+      out.z[base + i] = nz;
+      const R hh = Prec<R>::hi(nh);
+      if (!(hh > R(0))) flags |= ST_DEPTH;
+      if (!(Prec<R>::finite(nh) && Prec<R>::finite(nq) && Prec<R>::finite(nz))) {
+        flags |= ST_NONFINITE;
+      } else if (hh > R(0)) {
+        rho = Prec<R>::template rho<LAW_GRASS>(lp, hh, Prec<R>::hi(nq));
+        if (!(rho <= R(3.0e38))) {
+          flags |= ST_NONFINITE;
+          rho = R(0);
+        }
+      }
+    }
+    rho = warp_max(rho);
+    if ((tid & 31) == 0) sRed[tid >> 5] = rho;
+    __syncthreads();
+    if (tid < 32) {
+      rho = (tid < B / 32) ? sRed[tid] : R(0);
+      rho = warp_max(rho);
+      if (tid == 0 && rho > R(0)) atomicMax(&p.d.rho[nx * C + c], Prec<R>::bits(rho));
+    }
+  }
+  if (flags) atomicOr(p.d.status, flags);
+}
+
+// Initial CFL maxima of every channel into slot 0 (grid-stride over cells).
+template <typename R>
+__global__ void __launch_bounds__(256) k_ens_rho(const EnsParams p, const typename Prec<R>::State st,
+                                                  int64_t n_total) {
+  unsigned flags = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    // channel of cell i by binary search over the offsets
+    int lo = 0, hi = p.C - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (p.off[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    const int c = lo;
+    const auto h = st.h[i], q = st.q[i], z = st.z[i];
+    const R hh = Prec<R>::hi(h);
+    if (!(Prec<R>::finite(h) && Prec<R>::finite(q) && Prec<R>::finite(z))) {
+      flags |= ST_NONFINITE;
+      continue;
+    }
+    if (!(hh > R(0))) {
+      flags |= ST_DEPTH;
+      continue;
+    }
+    StepParams lp;
+    lp.lf = LawT<float>{p.g_f, p.K3f[c], 0.0f, 0.0f};
+    lp.ld = LawT<double>{p.g_d, p.K3d[c], 0.0, 0.0};
+    const R r = Prec<R>::template rho<LAW_GRASS>(lp, hh, Prec<R>::hi(q));
+    if (!(r <= R(3.0e38))) {
+      flags |= ST_NONFINITE;
+      continue;
+    }
+    atomicMax(&p.d.rho[c], Prec<R>::bits(r));
+  }
+  if (flags) atomicOr(p.d.status, flags);
+}
+
+}  // namespace adot
+
+using namespace adot;
+
+namespace {
+
+constexpr int kEnsBlocks[3] = {256, 128, 512};
+
+struct HostCtl {
+  long long gstep[3];
+  int active[3];
+  unsigned status;
+};
+
+}  // namespace
+
+struct adot_ensemble {
+  int C;
+  int prec;
+  int device;
+  int block;
+  bool tuned;
+  int steps_per_graph;
+  double cfl, g, xi;
+  int64_t n_total;
+  std::vector<int64_t> n_cells;
+  std::vector<int64_t> off;
+  std::vector<int> order;  // channels, longest first
+  cudaStream_t stream;
+  bool own_stream;
+  cudaStream_t cap_stream;
+  // device
+  void* buf[2][3];
+  int cur;
+  int phase;
+  int64_t* d_off;
+  double* d_dx;
+  float* d_K3f;
+  double* d_K3d;
+  int* d_tile_chan;
+  int* d_tile_e0;
+  int* d_chan_tile_end;
+  int64_t n_tiles;
+  int grid;
+  void* d_ctl_mem;  // all EnsDev arrays in one allocation
+  size_t ctl_bytes;
+  EnsDev dev;
+  double* d_io;
+  cudaGraphExec_t graph;
+  bool graph_ready;
+  bool state_set;
+  double t_end_dev;
+};
+
+namespace {
+
+#define CKE(expr)                               \
+  do {                                          \
+    cudaError_t _e = (expr);                    \
+    if (_e != cudaSuccess) return ADOT_E_CUDA;  \
+  } while (0)
+
+adot_status ens_status(unsigned bits) {
+  if (bits & ST_NONFINITE) return ADOT_E_NONFINITE;
+  if (bits & ST_DEPTH) return ADOT_E_NONPOSITIVE_DEPTH;
+  if (bits & ST_NONHYPERBOLIC) return ADOT_E_NONHYPERBOLIC;
+  if (bits & ST_TIMEOUT) return ADOT_E_TIMEOUT;
+  return ADOT_OK;
+}
+
+EnsParams ens_params(const adot_ensemble* e) {
+  EnsParams p;
+  p.C = e->C;
+  p.n_tiles = e->n_tiles;
+  p.cfl = e->cfl;
+  p.g_f = (float)e->g;
+  p.g_d = e->g;
+  p.off = e->d_off;
+  p.dx = e->d_dx;
+  p.K3f = e->d_K3f;
+  p.K3d = e->d_K3d;
+  p.tile_chan = e->d_tile_chan;
+  p.tile_e0 = e->d_tile_e0;
+  p.chan_tile_end = e->d_chan_tile_end;
+  p.d = e->dev;
+  return p;
+}
+
+template <typename R>
+typename Prec<R>::State ens_state(adot_ensemble* e, int which) {
+  using S = typename Prec<R>::S;
+  return typename Prec<R>::State{(S*)e->buf[which][0], (S*)e->buf[which][1], (S*)e->buf[which][2]};
+}
+
+template <typename R>
+cudaError_t ens_launch_t(adot_ensemble* e, int block, int grid, cudaStream_t s, int cur, int phase) {
+  const EnsParams p = ens_params(e);
+  const auto in = ens_state<R>(e, cur), out = ens_state<R>(e, 1 - cur);
+  const int slot = phase % 3;
+  switch (block) {
+    case 128: k_ens_step<R, 128><<<grid, 128, 0, s>>>(p, in, out, slot); break;
+    case 256: k_ens_step<R, 256><<<grid, 256, 0, s>>>(p, in, out, slot); break;
+    case 512: k_ens_step<R, 512><<<grid, 512, 0, s>>>(p, in, out, slot); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t ens_launch(adot_ensemble* e, cudaStream_t s, int cur, int phase) {
+  if (e->prec == ADOT_FP32) return ens_launch_t<float>(e, e->block, e->grid, s, cur, phase);
+  return ens_launch_t<double>(e, e->block, e->grid, s, cur, phase);
+}
+
+int resident_grid(adot_ensemble* e, int block) {
+  int per_sm = 1, sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, e->device);
+  cudaError_t err;
+  if (e->prec == ADOT_FP32) {
+    if (block == 128) err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ens_step<float, 128>, 128, 0);
+    else if (block == 256) err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ens_step<float, 256>, 256, 0);
+    else err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ens_step<float, 512>, 512, 0);
+  } else {
+    if (block == 128) err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ens_step<double, 128>, 128, 0);
+    else if (block == 256) err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ens_step<double, 256>, 256, 0);
+    else err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ens_step<double, 512>, 512, 0);
+  }
+  if (err != cudaSuccess || per_sm < 1) per_sm = 1;
+  int64_t g = (int64_t)sms * per_sm;
+  return (int)g;
+}
+
+// Tile list for block size B: channels longest first, tiles of B-1 cells.
+adot_status build_tiles(adot_ensemble* e, int block) {
+  std::vector<int> tc, te;
+  std::vector<int> tend(e->C);
+  const int64_t cells = block - 1;
+  for (int c : e->order) {
+    const int64_t nt = (e->n_cells[c] + cells - 1) / cells;
+    for (int64_t j = 0; j < nt; ++j) {
+      tc.push_back(c);
+      te.push_back((int)(j * cells));
+    }
+    tend[c] = (int)tc.size();
+  }
+  if (tc.size() > 0x7fffffff) return ADOT_E_INVALID_ARG;
+  if (e->d_tile_chan) cudaFree(e->d_tile_chan);
+  if (e->d_tile_e0) cudaFree(e->d_tile_e0);
+  e->d_tile_chan = nullptr;
+  e->d_tile_e0 = nullptr;
+  e->n_tiles = (int64_t)tc.size();
+  CKE(cudaMalloc((void**)&e->d_tile_chan, sizeof(int) * tc.size()));
+  CKE(cudaMalloc((void**)&e->d_tile_e0, sizeof(int) * te.size()));
+  CKE(cudaMemcpy(e->d_tile_chan, tc.data(), sizeof(int) * tc.size(), cudaMemcpyHostToDevice));
+  CKE(cudaMemcpy(e->d_tile_e0, te.data(), sizeof(int) * te.size(), cudaMemcpyHostToDevice));
+  CKE(cudaMemcpy(e->d_chan_tile_end, tend.data(), sizeof(int) * e->C, cudaMemcpyHostToDevice));
+  e->block = block;
+  int g = resident_grid(e, block);
+  e->grid = (int)std::min<int64_t>(g, std::max<int64_t>(1, e->n_tiles));
+  return ADOT_OK;
+}
+
+adot_status ens_build_graph(adot_ensemble* e) {
+  if (e->graph_ready) {
+    cudaGraphExecDestroy(e->graph);
+    e->graph_ready = false;
+  }
+  cudaGraph_t g = nullptr;
+  CKE(cudaStreamBeginCapture(e->cap_stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t err = cudaSuccess;
+  for (int k = 0; k < e->steps_per_graph && err == cudaSuccess; ++k)
+    err = ens_launch(e, e->cap_stream, k & 1, k % 6);
+  cudaError_t e2 = cudaStreamEndCapture(e->cap_stream, &g);
+  if (err != cudaSuccess || e2 != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return ADOT_E_CUDA;
+  }
+  err = cudaGraphInstantiate(&e->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (err != cudaSuccess) return ADOT_E_CUDA;
+  e->graph_ready = true;
+  return ADOT_OK;
+}
+
+adot_status ens_enqueue(adot_ensemble* e, int64_t n) {
+  while (n > 0) {
+    if (e->phase == 0 && n >= e->steps_per_graph) {
+      CKE(cudaGraphLaunch(e->graph, e->stream));
+      n -= e->steps_per_graph;
+    } else {
+      CKE(ens_launch(e, e->stream, e->cur, e->phase));
+      e->cur ^= 1;
+      e->phase = (e->phase + 1) % 6;
+      --n;
+    }
+  }
+  return ADOT_OK;
+}
+
+adot_status ens_read(adot_ensemble* e, HostCtl* h) {
+  CKE(cudaMemcpyAsync(h->gstep, e->dev.gstep, sizeof(h->gstep), cudaMemcpyDeviceToHost, e->stream));
+  CKE(cudaMemcpyAsync(h->active, e->dev.active, sizeof(h->active), cudaMemcpyDeviceToHost, e->stream));
+  CKE(cudaMemcpyAsync(&h->status, e->dev.status, sizeof(unsigned), cudaMemcpyDeviceToHost, e->stream));
+  CKE(cudaStreamSynchronize(e->stream));
+  return ADOT_OK;
+}
+
+adot_status ens_set_t_end(adot_ensemble* e, double t_end) {
+  if (e->t_end_dev == t_end) return ADOT_OK;
+  CKE(cudaStreamSynchronize(e->stream));
+  CKE(cudaMemcpy(e->dev.t_end, &t_end, sizeof(double), cudaMemcpyHostToDevice));
+  e->t_end_dev = t_end;
+  return ADOT_OK;
+}
+
+// Resets every control array: all channels at t0 = 0, nothing finished, the
+// whole tile list active, the previous-step slot at -inf.
+adot_status ens_reset_ctl(adot_ensemble* e) {
+  const int C = e->C;
+  CKE(cudaMemsetAsync(e->d_ctl_mem, 0, e->ctl_bytes, e->stream));
+  std::vector<long long> fin(C, 0x7fffffffffffffffLL);
+  CKE(cudaMemcpyAsync(e->dev.fin, fin.data(), sizeof(long long) * C, cudaMemcpyHostToDevice, e->stream));
+  int act[3] = {(int)e->n_tiles, 0, 0};
+  CKE(cudaMemcpyAsync(e->dev.active, act, sizeof(act), cudaMemcpyHostToDevice, e->stream));
+  double inf = INFINITY;
+  CKE(cudaMemcpyAsync(e->dev.t_end, &inf, sizeof(double), cudaMemcpyHostToDevice, e->stream));
+  CKE(cudaStreamSynchronize(e->stream));
+  e->t_end_dev = INFINITY;
+  e->cur = 0;
+  e->phase = 0;
+  return ADOT_OK;
+}
+
+// Trial steps of each block size on the current state (no state advance:
+// with t_end = inf no channel finishes; the written slot and the tile bound
+// are reset afterwards).
+adot_status ens_tune(adot_ensemble* e, int trial) {
+  cudaEvent_t a, b;
+  CKE(cudaEventCreate(&a));
+  if (cudaEventCreate(&b) != cudaSuccess) {
+    cudaEventDestroy(a);
+    return ADOT_E_CUDA;
+  }
+  float best = 0.0f;
+  int best_block = e->block;
+  bool have = false;
+  cudaError_t err = cudaSuccess;
+  for (int i = 0; i < 3 && err == cudaSuccess; ++i) {
+    const int blk = kEnsBlocks[i];
+    if (build_tiles(e, blk) != ADOT_OK) {
+      err = cudaErrorUnknown;
+      break;
+    }
+    int act[3] = {(int)e->n_tiles, 0, 0};
+    err = cudaMemcpy(e->dev.active, act, sizeof(act), cudaMemcpyHostToDevice);
+    for (int k = 0; k < 1 + trial && err == cudaSuccess; ++k) {
+      if (k == 1) err = cudaEventRecord(a, e->stream);
+      if (err == cudaSuccess) err = ens_launch(e, e->stream, e->cur, e->phase);
+    }
+    if (err == cudaSuccess) err = cudaEventRecord(b, e->stream);
+    if (err == cudaSuccess) err = cudaEventSynchronize(b);
+    float ms = 0.0f;
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, a, b);
+    if (err == cudaSuccess && (!have || ms < best)) {
+      best = ms;
+      best_block = blk;
+      have = true;
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (err != cudaSuccess) return ADOT_E_CUDA;
+  adot_status st = build_tiles(e, best_block);
+  if (st) return st;
+  // undo what the trials wrote: slot 1 (CFL maxima, times) and the tile bounds
+  const int C = e->C;
+  CKE(cudaMemsetAsync(e->dev.rho + C, 0, sizeof(unsigned long long) * C, e->stream));
+  int act[3] = {(int)e->n_tiles, 0, 0};
+  CKE(cudaMemcpyAsync(e->dev.active, act, sizeof(act), cudaMemcpyHostToDevice, e->stream));
+  long long g0[3] = {0, 0, 0};
+  CKE(cudaMemcpyAsync(e->dev.gstep, g0, sizeof(g0), cudaMemcpyHostToDevice, e->stream));
+  CKE(cudaStreamSynchronize(e->stream));
+  e->tuned = true;
+  return ens_build_graph(e);
+}
+
+void ens_free(adot_ensemble* e) {
+  if (!e) return;
+  if (e->graph_ready) cudaGraphExecDestroy(e->graph);
+  for (int b = 0; b < 2; ++b)
+    for (int k = 0; k < 3; ++k)
+      if (e->buf[b][k]) cudaFree(e->buf[b][k]);
+  if (e->d_off) cudaFree(e->d_off);
+  if (e->d_dx) cudaFree(e->d_dx);
+  if (e->d_K3f) cudaFree(e->d_K3f);
+  if (e->d_K3d) cudaFree(e->d_K3d);
+  if (e->d_tile_chan) cudaFree(e->d_tile_chan);
+  if (e->d_tile_e0) cudaFree(e->d_tile_e0);
+  if (e->d_chan_tile_end) cudaFree(e->d_chan_tile_end);
+  if (e->d_ctl_mem) cudaFree(e->d_ctl_mem);
+  if (e->d_io) cudaFree(e->d_io);
+  if (e->cap_stream) cudaStreamDestroy(e->cap_stream);
+  if (e->own_stream && e->stream) cudaStreamDestroy(e->stream);
+  delete e;
+}
+
+}  // namespace
+
+extern "C" {
+
+adot_status adot_ensemble_create(const adot_ensemble_config* cfg, void* cuda_stream,
+                                 adot_ensemble** out) {
+  if (!out) return ADOT_E_INVALID_ARG;
+  *out = nullptr;
+  if (!cfg || cfg->n_channels < 1 || !cfg->n_cells || !cfg->length || !cfg->Ag) return ADOT_E_INVALID_ARG;
+  if (!(cfg->g > 0.0) || !(cfg->xi > 0.0) || !(cfg->cfl > 0.0 && cfg->cfl <= 1.0)) return ADOT_E_INVALID_ARG;
+  if (cfg->precision != ADOT_FP64 && cfg->precision != ADOT_FP32) return ADOT_E_INVALID_ARG;
+  if (cfg->block_threads != 0 && cfg->block_threads != 128 && cfg->block_threads != 256 &&
+      cfg->block_threads != 512)
+    return ADOT_E_INVALID_ARG;
+  if (cfg->steps_per_graph < 0 || cfg->device < -1) return ADOT_E_INVALID_ARG;
+  const int C = cfg->n_channels;
+  int64_t total = 0;
+  for (int c = 0; c < C; ++c) {
+    if (cfg->n_cells[c] < 1 || cfg->n_cells[c] > 0x7fff0000LL) return ADOT_E_INVALID_ARG;
+    if (!(cfg->length[c] > 0.0) || !isfinite(cfg->Ag[c])) return ADOT_E_INVALID_ARG;
+    total += cfg->n_cells[c];
+  }
+  if (cfg->device >= 0 && cudaSetDevice(cfg->device) != cudaSuccess) return ADOT_E_CUDA;
+  adot_ensemble* e = new adot_ensemble();
+  memset(e->buf, 0, sizeof(e->buf));
+  e->C = C;
+  e->prec = cfg->precision;
+  cudaGetDevice(&e->device);
+  e->cfl = cfg->cfl;
+  e->g = cfg->g;
+  e->xi = cfg->xi;
+  e->n_total = total;
+  e->n_cells.assign(cfg->n_cells, cfg->n_cells + C);
+  e->off.resize(C + 1);
+  e->off[0] = 0;
+  for (int c = 0; c < C; ++c) e->off[c + 1] = e->off[c] + e->n_cells[c];
+  e->order.resize(C);
+  for (int c = 0; c < C; ++c) e->order[c] = c;
+  std::stable_sort(e->order.begin(), e->order.end(),
+                   [&](int a, int b) { return e->n_cells[a] > e->n_cells[b]; });
+  int spg = cfg->steps_per_graph ? cfg->steps_per_graph : 48;
+  e->steps_per_graph = ((spg + 5) / 6) * 6;
+  e->tuned = cfg->block_threads != 0;
+  e->t_end_dev = INFINITY;
+
+  std::vector<double> dx(C), K3d(C);
+  std::vector<float> K3f(C);
+  for (int c = 0; c < C; ++c) {
+    dx[c] = cfg->length[c] / (double)e->n_cells[c];
+    K3d[c] = 3.0 * cfg->xi * cfg->Ag[c];
+    K3f[c] = (float)K3d[c];
+  }
+  cudaError_t err = cudaSuccess;
+  if (cuda_stream) {
+    e->stream = (cudaStream_t)cuda_stream;
+  } else {
+    err = cudaStreamCreateWithFlags(&e->stream, cudaStreamNonBlocking);
+    e->own_stream = true;
+  }
+  if (err == cudaSuccess) err = cudaStreamCreateWithFlags(&e->cap_stream, cudaStreamNonBlocking);
+  const size_t elem = (e->prec == ADOT_FP32) ? sizeof(float2) : sizeof(double);
+  for (int b = 0; b < 2 && err == cudaSuccess; ++b)
+    for (int k = 0; k < 3 && err == cudaSuccess; ++k) err = cudaMalloc(&e->buf[b][k], elem * (size_t)total);
+  if (err == cudaSuccess) err = cudaMalloc((void**)&e->d_off, sizeof(int64_t) * (C + 1));
+  if (err == cudaSuccess) err = cudaMalloc((void**)&e->d_dx, sizeof(double) * C);
+  if (err == cudaSuccess) err = cudaMalloc((void**)&e->d_K3f, sizeof(float) * C);
+  if (err == cudaSuccess) err = cudaMalloc((void**)&e->d_K3d, sizeof(double) * C);
+  if (err == cudaSuccess) err = cudaMalloc((void**)&e->d_chan_tile_end, sizeof(int) * C);
+  if (err == cudaSuccess && e->prec == ADOT_FP32) err = cudaMalloc((void**)&e->d_io, sizeof(double) * (size_t)total);
+  // control arrays in one allocation
+  const size_t slots = 3 * (size_t)C;
+  e->ctl_bytes = slots * (sizeof(double) * 2 + sizeof(long long) + sizeof(unsigned long long)) +
+                 (size_t)C * (sizeof(double) * 2 + sizeof(long long) * 2) + sizeof(long long) * 3 +
+                 sizeof(int) * 4 + sizeof(double) + sizeof(unsigned) + 64;
+  if (err == cudaSuccess) err = cudaMalloc(&e->d_ctl_mem, e->ctl_bytes);
+  if (err == cudaSuccess) {
+    char* m = (char*)e->d_ctl_mem;
+    auto take = [&](size_t bytes) {
+      char* r = m;
+      m += (bytes + 7) & ~(size_t)7;
+      return r;
+    };
+    e->dev.t = (double*)take(sizeof(double) * slots);
+    e->dev.dt = (double*)take(sizeof(double) * slots);
+    e->dev.steps = (long long*)take(sizeof(long long) * slots);
+    e->dev.rho = (unsigned long long*)take(sizeof(unsigned long long) * slots);
+    e->dev.t_cur = (double*)take(sizeof(double) * C);
+    e->dev.dt_cur = (double*)take(sizeof(double) * C);
+    e->dev.steps_cur = (long long*)take(sizeof(long long) * C);
+    e->dev.fin = (long long*)take(sizeof(long long) * C);
+    e->dev.gstep = (long long*)take(sizeof(long long) * 3);
+    e->dev.active = (int*)take(sizeof(int) * 4);
+    e->dev.t_end = (double*)take(sizeof(double));
+    e->dev.status = (unsigned*)take(sizeof(unsigned));
+  }
+  if (err == cudaSuccess) err = cudaMemcpy(e->d_off, e->off.data(), sizeof(int64_t) * (C + 1), cudaMemcpyHostToDevice);
+  if (err == cudaSuccess) err = cudaMemcpy(e->d_dx, dx.data(), sizeof(double) * C, cudaMemcpyHostToDevice);
+  if (err == cudaSuccess) err = cudaMemcpy(e->d_K3f, K3f.data(), sizeof(float) * C, cudaMemcpyHostToDevice);
+  if (err == cudaSuccess) err = cudaMemcpy(e->d_K3d, K3d.data(), sizeof(double) * C, cudaMemcpyHostToDevice);
+  if (err != cudaSuccess || build_tiles(e, cfg->block_threads ? cfg->block_threads : 256) != ADOT_OK ||
+      ens_reset_ctl(e) != ADOT_OK || ens_build_graph(e) != ADOT_OK) {
+    ens_free(e);
+    return ADOT_E_CUDA;
+  }
+  *out = e;
+  return ADOT_OK;
+}
+
+void adot_ensemble_destroy(adot_ensemble* e) {
+  if (!e) return;
+  cudaStreamSynchronize(e->stream);
+  ens_free(e);
+}
+
+adot_status adot_ensemble_set_state(adot_ensemble* e, const double* h, const double* q,
+                                    const double* z, int on_device) {
+  if (!e || !h || !q || !z) return ADOT_E_INVALID_ARG;
+  const int64_t n = e->n_total;
+  const size_t bytes = sizeof(double) * (size_t)n;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const double* src[3] = {h, q, z};
+  CKE(cudaStreamSynchronize(e->stream));
+  adot_status st = ens_reset_ctl(e);
+  if (st) return st;
+  for (int k = 0; k < 3; ++k) {
+    if (e->prec == ADOT_FP32) {
+      CKE(cudaMemcpyAsync(e->d_io, src[k], bytes, kind, e->stream));
+      CKE(launch_to_ff(e->d_io, (float2*)e->buf[0][k], n, e->stream));
+    } else {
+      CKE(cudaMemcpyAsync(e->buf[0][k], src[k], bytes, kind, e->stream));
+    }
+  }
+  // previous-step slot (2) at -inf so that no channel reads as already finished
+  std::vector<double> neg(e->C, -INFINITY);
+  CKE(cudaMemcpyAsync(e->dev.t + 2 * (size_t)e->C, neg.data(), sizeof(double) * e->C,
+                      cudaMemcpyHostToDevice, e->stream));
+  const EnsParams p = ens_params(e);
+  int64_t g = (n + 255) / 256;
+  if (g > 152 * 16) g = 152 * 16;
+  if (e->prec == ADOT_FP32)
+    k_ens_rho<float><<<(unsigned)g, 256, 0, e->stream>>>(p, ens_state<float>(e, 0), n);
+  else
+    k_ens_rho<double><<<(unsigned)g, 256, 0, e->stream>>>(p, ens_state<double>(e, 0), n);
+  CKE(cudaGetLastError());
+  HostCtl hc;
+  st = ens_read(e, &hc);
+  if (st) return st;
+  st = ens_status(hc.status);
+  if (st) return st;
+  e->state_set = true;
+  if (!e->tuned) return ens_tune(e, 2);
+  return ADOT_OK;
+}
+
+adot_status adot_ensemble_get_state(adot_ensemble* e, double* h, double* q, double* z, int on_device) {
+  if (!e || !h || !q || !z) return ADOT_E_INVALID_ARG;
+  const int64_t n = e->n_total;
+  const size_t bytes = sizeof(double) * (size_t)n;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  double* dst[3] = {h, q, z};
+  for (int k = 0; k < 3; ++k) {
+    if (e->prec == ADOT_FP32) {
+      CKE(launch_from_ff((const float2*)e->buf[e->cur][k], e->d_io, n, e->stream));
+      CKE(cudaMemcpyAsync(dst[k], e->d_io, bytes, kind, e->stream));
+      CKE(cudaStreamSynchronize(e->stream));
+    } else {
+      CKE(cudaMemcpyAsync(dst[k], e->buf[e->cur][k], bytes, kind, e->stream));
+    }
+  }
+  CKE(cudaStreamSynchronize(e->stream));
+  return ADOT_OK;
+}
+
+adot_status adot_ensemble_run_to(adot_ensemble* e, double t_end, int64_t* launches_out) {
+  if (!e || !e->state_set || !isfinite(t_end)) return ADOT_E_INVALID_ARG;
+  adot_status st = ens_set_t_end(e, t_end);
+  if (st) return st;
+  int64_t launches = 0;
+  for (;;) {
+    const int64_t chunk = e->phase ? (6 - e->phase) : e->steps_per_graph;
+    st = ens_enqueue(e, chunk);
+    if (st) return st;
+    launches += chunk;
+    HostCtl hc;
+    st = ens_read(e, &hc);
+    if (st) return st;
+    st = ens_status(hc.status);
+    if (st) return st;
+    if (hc.active[e->phase % 3] == 0) break;  // every channel finished and copied across
+  }
+  if (launches_out) *launches_out = launches;
+  return ADOT_OK;
+}
+
+adot_status adot_ensemble_step(adot_ensemble* e, int64_t n_steps) {
+  if (!e || !e->state_set || n_steps < 0) return ADOT_E_INVALID_ARG;
+  adot_status st = ens_set_t_end(e, INFINITY);
+  if (st) return st;
+  st = ens_enqueue(e, n_steps);
+  if (st) return st;
+  HostCtl hc;
+  st = ens_read(e, &hc);
+  if (st) return st;
+  return ens_status(hc.status);
+}
+
+adot_status adot_ensemble_query(adot_ensemble* e, double* t_out, int64_t* steps_out,
+                                int64_t* cell_updates_out) {
+  if (!e) return ADOT_E_INVALID_ARG;
+  std::vector<long long> steps(e->C);
+  CKE(cudaMemcpyAsync(steps.data(), e->dev.steps_cur, sizeof(long long) * e->C,
+                      cudaMemcpyDeviceToHost, e->stream));
+  if (t_out)
+    CKE(cudaMemcpyAsync(t_out, e->dev.t_cur, sizeof(double) * e->C, cudaMemcpyDeviceToHost, e->stream));
+  HostCtl hc;
+  adot_status st = ens_read(e, &hc);
+  if (st) return st;
+  int64_t cu = 0;
+  for (int c = 0; c < e->C; ++c) {
+    if (steps_out) steps_out[c] = steps[c];
+    cu += steps[c] * e->n_cells[c];
+  }
+  if (cell_updates_out) *cell_updates_out = cu;
+  return ens_status(hc.status);
+}
+
+adot_status adot_ensemble_info(adot_ensemble* e, int32_t* block_out, int64_t* tiles_out,
+                               int32_t* grid_out) {
+  if (!e) return ADOT_E_INVALID_ARG;
+  if (block_out) *block_out = e->block;
+  if (tiles_out) *tiles_out = e->n_tiles;
+  if (grid_out) *grid_out = e->grid;
+  return ADOT_OK;
+}
+
+}  // extern "C"

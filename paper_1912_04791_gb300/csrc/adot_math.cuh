@@ -62,7 +62,9 @@ __device__ __forceinline__ float d_rsqrt(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double d_rsqrt(double x) { return rsqrt(x); }
 __device__ __forceinline__ float d_acos(float x) { return acosf(x); }
 __device__ __forceinline__ double d_acos(double x) { return acos(x); }
-__device__ __forceinline__ void d_sincos(float x, float* s, float* c) { sincosf(x, s, c); }
+// float32: the hardware sine/cosine; the argument is phi/3 in [0, pi/3], where
+// their absolute error is below 2^-21.4.
+__device__ __forceinline__ void d_sincos(float x, float* s, float* c) { __sincosf(x, s, c); }
 __device__ __forceinline__ void d_sincos(double x, double* s, double* c) { sincos(x, s, c); }
 __device__ __forceinline__ float d_rcbrt(float x) { return rcbrtf(x); }
 __device__ __forceinline__ double d_rcbrt(double x) { return rcbrt(x); }
@@ -317,13 +319,60 @@ __device__ __forceinline__ void node_f32(const LawT<float>& L, const LawT<double
   abs_A_times_eigvec(e, dh, dq, dz, x[0], x[1], x[2]);
 }
 
-// Spectral radius max(|l1|, |l3|) at a state (the extreme roots need no
-// small-root correction).
+// Spectral radius max(|l1|, |l3|) at a state (float64: from Eq. lambda; the
+// extreme roots need no small-root correction).
 template <typename T, int LAW>
 __device__ __forceinline__ T spectral_radius(const LawT<T>& L, T h, T q) {
   Eig<T> e;
   node_eig<T, LAW, false>(L, h, q, e);
   return d_max(d_abs(e.l1), d_abs(e.l3));
+}
+
+// float32 spectral radius from Eq. lambda, kept out of line: the fallback of
+// spectral_radius_f32.
+template <int LAW>
+__device__ __noinline__ float spectral_radius_f32_trig(const LawT<float>& L, float h, float q) {
+  return spectral_radius<float, LAW>(L, h, q);
+}
+
+// float32 spectral radius. The root of largest magnitude is l3 when u >= 0 and
+// l1 when u < 0 (the water waves u +- c carry the extreme speeds); by the
+// mirror symmetry x -> -x (u -> -u, a -> -a, l -> -l) both cases reduce to the
+// largest root of p(l) = l^3 - 2u l^2 - (c^2 - u^2 + c^2 b) l - c^2 a with
+// u >= 0. p'' = 6l - 4u > 0 on [u + c, inf), so when p(u + c) <= 0 and
+// p'(u + c) > 0 Newton's method from u + c (the root when a = b = 0) converges
+// monotonically after its first step to the only root in [u + c, inf), the
+// largest. Four steps are taken; if the start does not meet those conditions
+// (strong transport, b > ~2) or the last correction is not below 1e-5 of the
+// root, the roots of Eq. lambda are used instead.
+template <int LAW>
+__device__ __forceinline__ float spectral_radius_f32(const LawT<float>& L, float h, float q) {
+  const float inv_h = __fdividef(1.0f, h);
+  const float u = q * inv_h;
+  const float c2 = L.g * h;
+  const float c = c2 * rsqrtf(c2);
+  float a, b;
+  sediment_derivs<float, LAW>(L, h, q, inv_h, u, a, b);
+  const float sg = (u >= 0.0f) ? 1.0f : -1.0f;
+  const float us = sg * u;
+  const float K = c2 - u * u + c2 * b;
+  const float ca = c2 * (sg * a);
+  const float tu = 2.0f * us, fu = 4.0f * us;
+  float l = us + c;
+  float pv = ((l - tu) * l - K) * l - ca;
+  float dp = (3.0f * l - fu) * l - K;
+  bool ok = (pv <= 1e-5f * c2 * c) && (dp > 0.0f);
+  float d = 0.0f;
+#pragma unroll
+  for (int it = 0; it < 4; ++it) {
+    d = __fdividef(pv, dp);
+    l -= d;
+    pv = ((l - tu) * l - K) * l - ca;
+    dp = (3.0f * l - fu) * l - K;
+  }
+  ok = ok && (fabsf(d) <= 1e-5f * l);
+  if (!ok) return spectral_radius_f32_trig<LAW>(L, h, q);
+  return l;
 }
 
 // ---------------------------------------------------------------------------

@@ -49,6 +49,10 @@ struct Prec<float> {
     node_f32<LAW>(p.lf, p.ld, h, q, dh, dq, dz, y, x, flags);
   }
   __device__ static __forceinline__ const LawT<float>& law(const StepParams& p) { return p.lf; }
+  template <int LAW>
+  __device__ static __forceinline__ float rho(const StepParams& p, float h, float q) {
+    return spectral_radius_f32<LAW>(p.lf, h, q);
+  }
 };
 
 template <>
@@ -73,6 +77,10 @@ struct Prec<double> {
     node_f64<LAW>(p.ld, h, q, dh, dq, dz, y, x, flags);
   }
   __device__ static __forceinline__ const LawT<double>& law(const StepParams& p) { return p.ld; }
+  template <int LAW>
+  __device__ static __forceinline__ double rho(const StepParams& p, double h, double q) {
+    return spectral_radius<double, LAW>(p.ld, h, q);
+  }
 };
 
 // Ghost state beyond one end (adj = the adjacent cell).
@@ -241,7 +249,7 @@ __global__ void __launch_bounds__(B, MinBlocks<B, CAP>::value) k_step(const Step
       if (!(Prec<R>::finite(nh) && Prec<R>::finite(nq) && Prec<R>::finite(nz))) {
         flags |= ST_NONFINITE;
       } else if (hh > R(0)) {
-        rho = spectral_radius<R, LAW>(Prec<R>::law(p), hh, Prec<R>::hi(nq));
+        rho = Prec<R>::template rho<LAW>(p, hh, Prec<R>::hi(nq));
         if (!(rho <= R(3.0e38))) {
           flags |= ST_NONFINITE;
           rho = R(0);
@@ -281,7 +289,7 @@ __global__ void __launch_bounds__(256) k_rho(const StepParams p, const typename 
       flags |= ST_DEPTH;
       continue;
     }
-    R r = spectral_radius<R, LAW>(Prec<R>::law(p), hh, Prec<R>::hi(q));
+    R r = Prec<R>::template rho<LAW>(p, hh, Prec<R>::hi(q));
     if (!(r <= R(3.0e38))) {
       flags |= ST_NONFINITE;
       continue;

@@ -133,3 +133,50 @@ def random_states(n: int, seed: int, h_range=(0.05, 5.0), fr_range=(-3.0, 3.0),
     h = rng.uniform(*h_range, size=n)
     fr = rng.uniform(*fr_range, size=n)
     return h, fr * np.sqrt(g * h) * h
+
+
+@dataclass
+class Ensemble:
+    """Independent channels laid end to end: channel c owns cells
+    offsets[c] .. offsets[c+1]-1 of the concatenated h, q, z arrays."""
+    n_cells: np.ndarray  # int64 [C]
+    length: np.ndarray   # float64 [C], channel length [m]
+    Ag: np.ndarray       # float64 [C]
+    h: np.ndarray
+    q: np.ndarray
+    z: np.ndarray
+    xi: float = XI_P04
+    cfl: float = 0.9
+    t_end: float = 1.0
+    g: float = G
+
+    @property
+    def offsets(self) -> np.ndarray:
+        return np.concatenate([[0], np.cumsum(self.n_cells)]).astype(np.int64)
+
+    def channel(self, c: int):
+        o = self.offsets
+        return self.h[o[c]:o[c + 1]], self.q[o[c]:o[c + 1]], self.z[o[c]:o[c + 1]]
+
+
+def riemann_ensemble(n_channels: int = 4096, seed: int = 20191210, n_min: int = 1000,
+                     n_max: int = 100000, length: float = 10.0) -> Ensemble:
+    """Batch of movable-bed Riemann problems: N_c log-uniform in [n_min, n_max];
+    h_L, h_R ~ U(0.5, 3) m; u_L, u_R ~ U(-0.5, 1.0) m/s drawn per side;
+    z_L = 0, z_R ~ U(-0.3, 0.3) m; A_g ~ U(0.001, 0.02); discontinuity at the
+    channel centre; transmissive ends; CFL 0.9, t_end 1 s."""
+    rng = np.random.default_rng(seed)
+    n = np.exp(rng.uniform(np.log(n_min), np.log(n_max), n_channels)).astype(np.int64)
+    hL, hR = rng.uniform(0.5, 3.0, n_channels), rng.uniform(0.5, 3.0, n_channels)
+    uL, uR = rng.uniform(-0.5, 1.0, n_channels), rng.uniform(-0.5, 1.0, n_channels)
+    zR = rng.uniform(-0.3, 0.3, n_channels)
+    Ag = rng.uniform(0.001, 0.02, n_channels)
+    hs, qs, zs = [], [], []
+    for c in range(n_channels):
+        h, q, z = riemann(int(n[c]), 0.0, length, 0.5 * length, (hL[c], hL[c] * uL[c], 0.0),
+                          (hR[c], hR[c] * uR[c], zR[c]))
+        hs.append(h)
+        qs.append(q)
+        zs.append(z)
+    return Ensemble(n, np.full(n_channels, length), Ag, np.concatenate(hs), np.concatenate(qs),
+                    np.concatenate(zs))

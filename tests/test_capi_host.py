@@ -85,3 +85,24 @@ def test_null_arguments_rejected(L):
     assert L.adot_fluctuations(None, None, None, 0, None, None, None, 0) == adot.E_INVALID_ARG
     assert L.adot_autotune(None, 8, None, None) == adot.E_INVALID_ARG
     L.adot_destroy(None)
+
+
+def test_invalid_ensemble_config_rejected(L):
+    import numpy as np
+    n = np.array([10, 0], dtype=np.int64)
+    ln = np.array([1.0, 1.0])
+    ag = np.array([0.01, 0.01])
+    c = adot.EnsembleConfig()
+    c.n_channels = 2
+    c.n_cells = n.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    c.length = ln.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    c.Ag = ag.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    c.g, c.xi, c.cfl, c.precision, c.block_threads, c.device = 9.81, 1.0, 0.9, 1, 0, -1
+    out = ctypes.c_void_p()
+    assert L.adot_ensemble_create(ctypes.byref(c), None, ctypes.byref(out)) == adot.E_INVALID_ARG
+    n[1] = 5
+    c.cfl = 2.0
+    assert L.adot_ensemble_create(ctypes.byref(c), None, ctypes.byref(out)) == adot.E_INVALID_ARG
+    c.cfl = 0.9
+    c.block_threads = 100
+    assert L.adot_ensemble_create(ctypes.byref(c), None, ctypes.byref(out)) == adot.E_INVALID_ARG

@@ -1,0 +1,113 @@
+"""Parity of the batched ensemble (adot_ensemble_*, independent channels with
+their own dt, one launch per step) with per-channel oracle runs, on seeded
+movable-bed Riemann channels of ragged lengths (1 cell up to several tiles).
+
+Tolerances as for single channels: FP64 1e-12 of each variable's scale and the
+same step count; FP32 (float-float state) L1 relative error 1e-5 per channel."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1912_04791_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+G = 9.81
+
+
+def _small_ensemble(sizes, seed=3):
+    rng = np.random.default_rng(seed)
+    E = W.riemann_ensemble(len(sizes), seed=seed, n_min=2, n_max=3)
+    hs, qs, zs = [], [], []
+    for c, n in enumerate(sizes):
+        hL, hR = rng.uniform(0.5, 3.0, 2)
+        uL, uR = rng.uniform(-0.5, 1.0, 2)
+        zR = rng.uniform(-0.3, 0.3)
+        h, q, z = W.riemann(n, 0.0, 10.0, 5.0, (hL, hL * uL, 0.0), (hR, hR * uR, zR))
+        hs.append(h), qs.append(q), zs.append(z)
+    E.n_cells = np.array(sizes, dtype=np.int64)
+    E.length = np.full(len(sizes), 10.0)
+    E.Ag = rng.uniform(0.001, 0.02, len(sizes))
+    E.h, E.q, E.z = np.concatenate(hs), np.concatenate(qs), np.concatenate(zs)
+    return E
+
+
+SIZES = [1, 2, 7, 100, 254, 255, 256, 300, 511, 700, 1023, 40]
+
+
+def _oracle_channel(E, c, t_end):
+    h, q, z = E.channel(c)
+    cfg = O.make_cfg(int(E.n_cells[c]), 0.0, float(E.length[c]), E.cfl,
+                     O.grass(float(E.Ag[c]), xi=E.xi, g=G))
+    return O.run(cfg, h, q, z, t_end=t_end)
+
+
+@pytest.mark.parametrize("block", [0, 128, 256, 512])
+def test_fp64_ensemble_matches_oracle_per_channel(gpu, block):
+    E = _small_ensemble(SIZES)
+    with gpu.Ensemble.from_workload(E, gpu.FP64, block_threads=block) as ens:
+        ens.set_state(E.h, E.q, E.z)
+        t, steps, _ = ens.query()
+        assert (steps == 0).all()
+        ens.run_to(0.15)
+        t, steps, cu = ens.query()
+        h, q, z = ens.get_state()
+    o = E.offsets
+    assert cu == int((steps * E.n_cells).sum())
+    for c in range(len(SIZES)):
+        ho, qo, zo, to, so, _ = _oracle_channel(E, c, 0.15)
+        assert t[c] == 0.15 and steps[c] == so, (c, steps[c], so)
+        for a, b in ((h, ho), (q, qo), (z, zo)):
+            sc = max(np.abs(b).max(), 1e-300)
+            assert np.abs(a[o[c]:o[c + 1]] - b).max() <= 1e-12 * sc, c
+
+
+def test_fp32_ensemble_matches_oracle_per_channel(gpu):
+    E = _small_ensemble(SIZES, seed=4)
+    with gpu.Ensemble.from_workload(E, gpu.FP32) as ens:
+        ens.set_state(E.h, E.q, E.z)
+        ens.run_to(0.2)
+        t, steps, _ = ens.query()
+        h, q, z = ens.get_state()
+    o = E.offsets
+    for c in range(len(SIZES)):
+        ho, qo, zo, to, so, _ = _oracle_channel(E, c, 0.2)
+        assert t[c] == 0.2
+        for a, b in ((h, ho), (q, qo), (z, zo)):
+            assert np.abs(a[o[c]:o[c + 1]] - b).sum() <= 1e-5 * max(np.abs(b).sum(), 1e-12)
+
+
+def test_ensemble_steps_equal_single_channel_contexts(gpu):
+    """A fixed number of steps per channel gives, in FP64, the same state as one
+    context per channel (same kernels' arithmetic, different launch geometry)."""
+    E = _small_ensemble([300, 57, 1000], seed=5)
+    with gpu.Ensemble.from_workload(E, gpu.FP64, block_threads=256) as ens:
+        ens.set_state(E.h, E.q, E.z)
+        ens.step(37)
+        _, steps, _ = ens.query()
+        h, q, z = ens.get_state()
+    assert (steps == 37).all()
+    o = E.offsets
+    for c in range(3):
+        hc, qc, zc = E.channel(c)
+        cfg = gpu.make_config(int(E.n_cells[c]), 0.0, 10.0, E.cfl, float(E.Ag[c]), E.xi,
+                              precision=gpu.FP64, block_threads=256, reg_cap=64)
+        with gpu.Solver(cfg) as s:
+            s.set_state(hc, qc, zc)
+            s.step(37)
+            ref = s.get_state()
+        for a, b in zip((h, q, z), ref):
+            assert np.abs(a[o[c]:o[c + 1]] - b).max() <= 1e-12 * max(np.abs(b).max(), 1e-300)
+
+
+def test_large_ensemble_all_channels_land_on_t_end(gpu):
+    E = W.riemann_ensemble(256, seed=11, n_min=200, n_max=20000)
+    with gpu.Ensemble.from_workload(E, gpu.FP32) as ens:
+        ens.set_state(E.h, E.q, E.z)
+        launches = ens.run_to(0.02)
+        t, steps, cu = ens.query()
+        h, q, z = ens.get_state()
+    assert (t == 0.02).all()
+    assert launches >= steps.max()
+    assert np.isfinite(h).all() and (h > 0).all()
+    # longer channels need more steps (dt ~ dx)
+    assert steps[np.argmax(E.n_cells)] > steps[np.argmin(E.n_cells)]

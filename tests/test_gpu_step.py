@@ -250,3 +250,31 @@ def test_device_state_roundtrip(gpu):
         torch.cuda.synchronize()
         for a, b in ((oh, ho), (oq, qo), (oz, zo)):
             assert np.abs(a.cpu().numpy() - b).max() <= 1e-12 * _scale(b)
+
+
+@pytest.mark.parametrize("law", ["grass", "mpm"])
+def test_fp32_time_step_matches_oracle(gpu, law):
+    """The float32 CFL maximum (Newton on the flow-side extreme root) gives the
+    oracle's dt (trigonometric roots, R2) to float32 rounding, on states with
+    both signs of u, sub- and supercritical."""
+    n = 4001
+    rng = np.random.default_rng(77)
+    for trial in range(4):
+        h = rng.uniform(0.1, 3.0, n)
+        fr = rng.uniform(-2.5, 2.5, n)
+        q = fr * np.sqrt(G * h) * h
+        z = rng.uniform(0.0, 0.2, n)
+        if law == "grass":
+            Ag = rng.uniform(0.001, 0.05)
+            olaw = O.grass(Ag, xi=W.XI_P04, g=G)
+            cfg = gpu.make_config(n, 0.0, 10.0, 0.9, Ag, W.XI_P04, precision=gpu.FP32)
+        else:
+            olaw = O.mpm(2.65, 1e-3, 0.02, xi=W.XI_P04, g=G)
+            cfg = gpu.make_config(n, 0.0, 10.0, 0.9, 0.0, W.XI_P04, precision=gpu.FP32,
+                                  law=gpu.LAW_MPM, s_rel=2.65, d50=1e-3, manning_n=0.02)
+        ocfg = O.make_cfg(n, 0.0, 10.0, 0.9, olaw)
+        _, _, _, _, _, dt_ref = O.run(ocfg, h, q, z, max_steps=1)
+        with gpu.Solver(cfg) as s:
+            s.set_state(h, q, z)
+            _, dt = s.step(1)
+        assert dt == pytest.approx(dt_ref, rel=2e-6)
