@@ -518,6 +518,9 @@ adot_status ens_tune(adot_ensemble* e, int trial) {
   CKE(cudaMemcpyAsync(e->dev.active, act, sizeof(act), cudaMemcpyHostToDevice, e->stream));
   long long g0[3] = {0, 0, 0};
   CKE(cudaMemcpyAsync(e->dev.gstep, g0, sizeof(g0), cudaMemcpyHostToDevice, e->stream));
+  CKE(cudaMemsetAsync(e->dev.t_cur, 0, sizeof(double) * C, e->stream));
+  CKE(cudaMemsetAsync(e->dev.dt_cur, 0, sizeof(double) * C, e->stream));
+  CKE(cudaMemsetAsync(e->dev.steps_cur, 0, sizeof(long long) * C, e->stream));
   CKE(cudaStreamSynchronize(e->stream));
   e->tuned = true;
   return ens_build_graph(e);
