@@ -110,6 +110,7 @@ def lib() -> ctypes.CDLL:
         L.orc_spectral_radius.argtypes = [lp, ctypes.c_double, ctypes.c_double, dp]
         L.orc_run.argtypes = [ctypes.POINTER(Cfg), dp, dp, dp, ctypes.c_int64, ctypes.c_double,
                               dp, ctypes.POINTER(ctypes.c_int64), dp, dp]
+        L.orc_abs_psi_batch.argtypes = [lp, ctypes.c_int, ctypes.c_int64, dp, dp, dp]
         L.orc_num_threads.restype = ctypes.c_int
         L.orc_set_num_threads.argtypes = [ctypes.c_int]
         _lib = L
@@ -210,6 +211,16 @@ def fluct(law: Law, WL: np.ndarray, WR: np.ndarray, method: int = ABS_ANALYTIC):
     Dp = np.zeros((3, n))
     _check(lib().orc_fluct(ctypes.byref(law), method, n, _p(WL), _p(WR), _p(Dm), _p(Dp)), "fluct")
     return Dm, Dp
+
+
+def abs_psi(law: Law, WL: np.ndarray, WR: np.ndarray, method: int = ABS_ANALYTIC) -> np.ndarray:
+    """|A|_Psi = sum_k w_k |A(Psi(s_k))| of each edge (WL, WR: [3, n]); returns [n, 9]."""
+    WL = np.ascontiguousarray(WL, dtype=np.float64)
+    WR = np.ascontiguousarray(WR, dtype=np.float64)
+    n = WL.shape[1]
+    out = np.zeros((n, 9))
+    _check(lib().orc_abs_psi_batch(ctypes.byref(law), method, n, _p(WL), _p(WR), _p(out)), "abs_psi")
+    return out
 
 
 def make_cfg(n: int, x_min: float, x_max: float, cfl: float, law: Law,

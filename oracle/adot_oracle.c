@@ -724,3 +724,40 @@ void orc_set_num_threads(int n) {
   (void)n;
 #endif
 }
+
+/* Quadrature average of |A| along the segment path,
+ * |A|_Psi = sum_k w_k |A(Psi(s_k))| (the matrix that multiplies dW in the
+ * dissipative part of Eq. DOTjumpN), row-major; the label of the learned
+ * surrogate. */
+int orc_abs_psi(const orc_law* L, int method, const double WL[3], const double WR[3],
+                double out[9]) {
+  double s[3], w[3];
+  orc_gl3(s, w);
+  for (int i = 0; i < 9; ++i) out[i] = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    double ph = WL[0] + s[k] * (WR[0] - WL[0]);
+    double pq = WL[1] + s[k] * (WR[1] - WL[1]);
+    double X[9];
+    int st = orc_abs_matrix(L, method, ph, pq, X, 0);
+    if (st) return st;
+    for (int i = 0; i < 9; ++i) out[i] += w[k] * X[i];
+  }
+  return ORC_OK;
+}
+
+/* Batch of n edges: WL, WR [3][n]; out [n][9]. */
+int orc_abs_psi_batch(const orc_law* L, int method, int64_t n, const double* WL,
+                      const double* WR, double* out) {
+  int status = ORC_OK;
+#pragma omp parallel for schedule(static)
+  for (int64_t e = 0; e < n; ++e) {
+    double wl[3] = {WL[e], WL[n + e], WL[2 * n + e]};
+    double wr[3] = {WR[e], WR[n + e], WR[2 * n + e]};
+    int st = orc_abs_psi(L, method, wl, wr, out + 9 * e);
+    if (st) {
+#pragma omp critical
+      if (!status) status = st;
+    }
+  }
+  return status;
+}
