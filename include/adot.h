@@ -212,6 +212,61 @@ adot_status adot_ensemble_query(adot_ensemble* ens, double* t_out, int64_t* step
 adot_status adot_ensemble_info(adot_ensemble* ens, int32_t* block_out, int64_t* tiles_out,
                                int32_t* grid_out);
 
+/* ---- Learned surrogate of the quadrature-averaged |A| ----------------------
+ * |A|_Psi = sum_k w_k |A(Psi(s_k))|, the matrix that multiplies W+ - W- in the
+ * dissipative half of Eq. DOTjumpN, is approximated by a multilayer perceptron
+ * 7 -> 128 -> 128 -> 128 -> 128 -> 9 with GELU hidden activations (tanh form),
+ * bfloat16 weights and activations and float32 accumulation on tensor cores.
+ * Inputs: standardised (h_L, q_L, z_L, h_R, q_R, z_R, A_g); outputs: the
+ * standardised 9 entries of |A|_Psi (row-major). Training minimises the mean
+ * squared error with Adam (beta1 0.9, beta2 0.999, eps 1e-8, cosine-decayed
+ * step size to 5% of lr). Parameters are exchanged as one float32 vector, layer
+ * by layer, W_l ([out][in] row-major) then b_l: 51721 values. */
+typedef struct adot_mlp adot_mlp;
+#define ADOT_MLP_PARAMS 51721
+
+/* Allocates a network (parameters zero) for batches up to max_batch rows. */
+adot_status adot_mlp_create(int64_t max_batch, void* cuda_stream, adot_mlp** out);
+void adot_mlp_destroy(adot_mlp* mlp);
+/* Parameters in (host [ADOT_MLP_PARAMS]); resets the Adam moments and step. */
+adot_status adot_mlp_set_params(adot_mlp* mlp, const float* params);
+adot_status adot_mlp_get_params(adot_mlp* mlp, float* params);
+/* Training set: raw inputs X [n][7] and labels T [n][9] (float32, host or
+ * device). Sets the standardisation (per-column mean and standard deviation)
+ * and the training box (per-input min/max widened by 5% of the range). */
+adot_status adot_mlp_set_data(adot_mlp* mlp, const float* X, const float* T, int64_t n,
+                              int on_device);
+/* stats32 (may be NULL): x mean[7], x sd[7], y mean[9], y sd[9]; box14 (may be
+ * NULL): input lower bounds[7], upper bounds[7]. */
+adot_status adot_mlp_get_stats(adot_mlp* mlp, float* stats32, float* box14);
+/* Forward pass of n <= max_batch standardised inputs Xs [n][7] (host) to
+ * standardised outputs Y [n][9] (host); fused = 1 uses the single-kernel
+ * inference path of the surrogate step, 0 the per-layer training kernels. */
+adot_status adot_mlp_forward(adot_mlp* mlp, const float* Xs, int64_t n, float* Y, int fused);
+/* Loss and gradient (host [ADOT_MLP_PARAMS]) of the mean squared error on a
+ * batch of standardised inputs Xs [n][7] and targets Ts [n][9] (host). */
+adot_status adot_mlp_gradient(adot_mlp* mlp, const float* Xs, const float* Ts, int64_t n,
+                              float* loss_out, float* grad);
+/* `steps` Adam steps on batches of `batch` rows drawn from the training set with
+ * splitmix64(seed, step, row); loss_hist (host [steps], may be NULL) receives
+ * each step's batch loss. One step is a replayed CUDA graph. */
+adot_status adot_mlp_train(adot_mlp* mlp, int64_t steps, int64_t batch, double lr, uint64_t seed,
+                           float* loss_hist);
+
+/* Makes every later step of a float32 Grass context take |A|_Psi from the
+ * network (A dW stays analytic), except on edges whose local Froude number
+ * max(|Fr_L|, |Fr_R|, |Fr_mid|) lies in [fr_lo, fr_hi], whose two sides lie on
+ * opposite sides of Fr = 1, or whose inputs leave the training box: those use
+ * the analytic eigenstructure. mlp = NULL detaches. The network must outlive
+ * its use by the context. ADOT_E_UNSUPPORTED for other contexts. */
+adot_status adot_set_surrogate(adot_ctx* ctx, adot_mlp* mlp, double fr_lo, double fr_hi);
+/* Edges evaluated and edges that fell back since the surrogate was attached. */
+adot_status adot_surrogate_stats(adot_ctx* ctx, int64_t* edges_out, int64_t* fallback_out);
+/* n edge samples of the current state (edge indices drawn with splitmix64 from
+ * seed and the sample number): X [n][7] raw inputs and T [n][9] labels
+ * |A|_Psi computed in float64, stored as float32 (host or device). Grass law. */
+adot_status adot_harvest(adot_ctx* ctx, int64_t n, uint64_t seed, float* X, float* T, int on_device);
+
 /* Largest number of cells adot_step_noalloc accepts. */
 #define ADOT_NOALLOC_MAX_CELLS 65536
 

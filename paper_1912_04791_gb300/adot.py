@@ -82,6 +82,18 @@ def lib() -> ctypes.CDLL:
             "adot_conserved_sums": ([_P, _D], i32),
             "adot_autotune": ([_P, i64, ctypes.POINTER(i32), ctypes.POINTER(i32)], i32),
             "adot_step_noalloc": ([ctypes.POINTER(Config), _P, _P, _P, i64, _D, _P], i32),
+            "adot_mlp_create": ([i64, _P, ctypes.POINTER(_P)], i32),
+            "adot_mlp_destroy": ([_P], None),
+            "adot_mlp_set_params": ([_P, _P], i32),
+            "adot_mlp_get_params": ([_P, _P], i32),
+            "adot_mlp_set_data": ([_P, _P, _P, i64, i32], i32),
+            "adot_mlp_get_stats": ([_P, _P, _P], i32),
+            "adot_mlp_forward": ([_P, _P, i64, _P, i32], i32),
+            "adot_mlp_gradient": ([_P, _P, _P, i64, ctypes.POINTER(ctypes.c_float), _P], i32),
+            "adot_mlp_train": ([_P, i64, i64, dbl, ctypes.c_uint64, _P], i32),
+            "adot_set_surrogate": ([_P, _P, dbl, dbl], i32),
+            "adot_surrogate_stats": ([_P, ctypes.POINTER(i64), ctypes.POINTER(i64)], i32),
+            "adot_harvest": ([_P, i64, ctypes.c_uint64, _P, _P, i32], i32),
             "adot_ensemble_create": ([ctypes.POINTER(EnsembleConfig), _P, ctypes.POINTER(_P)], i32),
             "adot_ensemble_destroy": ([_P], None),
             "adot_ensemble_set_state": ([_P, _P, _P, _P, i32], i32),
@@ -337,6 +349,109 @@ class Ensemble:
             self.close()
         except Exception:
             pass
+
+
+MLP_PARAMS = 51721
+
+
+def _f32(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    if shape is not None and a.shape != shape:
+        raise ValueError(f"expected shape {shape}, got {a.shape}")
+    return a
+
+
+class Mlp:
+    """Owning wrapper around an adot_mlp (the |A|_Psi surrogate network)."""
+
+    def __init__(self, max_batch: int, stream=None):
+        s = stream
+        if s is not None and not isinstance(s, int):
+            s = s.cuda_stream
+        out = _P()
+        _check(lib().adot_mlp_create(max_batch, s, ctypes.byref(out)), "adot_mlp_create")
+        self.ptr = out.value
+        self.max_batch = max_batch
+
+    def set_params(self, theta):
+        t = _f32(theta, (MLP_PARAMS,))
+        _check(lib().adot_mlp_set_params(self.ptr, t.ctypes.data), "adot_mlp_set_params")
+
+    def get_params(self) -> np.ndarray:
+        t = np.empty(MLP_PARAMS, dtype=np.float32)
+        _check(lib().adot_mlp_get_params(self.ptr, t.ctypes.data), "adot_mlp_get_params")
+        return t
+
+    def set_data(self, X, T):
+        X = _f32(X)
+        T = _f32(T)
+        n = X.shape[0]
+        assert X.shape == (n, 7) and T.shape == (n, 9)
+        _check(lib().adot_mlp_set_data(self.ptr, X.ctypes.data, T.ctypes.data, n, 0), "adot_mlp_set_data")
+
+    def stats(self):
+        st = np.empty(32, dtype=np.float32)
+        box = np.empty(14, dtype=np.float32)
+        _check(lib().adot_mlp_get_stats(self.ptr, st.ctypes.data, box.ctypes.data), "adot_mlp_get_stats")
+        return st, box
+
+    def forward(self, Xs, fused=False) -> np.ndarray:
+        Xs = _f32(Xs)
+        n = Xs.shape[0]
+        Y = np.empty((n, 9), dtype=np.float32)
+        _check(lib().adot_mlp_forward(self.ptr, Xs.ctypes.data, n, Y.ctypes.data, int(fused)),
+               "adot_mlp_forward")
+        return Y
+
+    def gradient(self, Xs, Ts):
+        Xs, Ts = _f32(Xs), _f32(Ts)
+        n = Xs.shape[0]
+        g = np.empty(MLP_PARAMS, dtype=np.float32)
+        loss = ctypes.c_float()
+        _check(lib().adot_mlp_gradient(self.ptr, Xs.ctypes.data, Ts.ctypes.data, n, ctypes.byref(loss),
+                                       g.ctypes.data), "adot_mlp_gradient")
+        return loss.value, g
+
+    def train(self, steps: int, batch: int, lr: float = 1e-3, seed: int = 1) -> np.ndarray:
+        h = np.empty(max(steps, 1), dtype=np.float32)
+        _check(lib().adot_mlp_train(self.ptr, steps, batch, lr, seed, h.ctypes.data), "adot_mlp_train")
+        return h[:steps]
+
+    def close(self):
+        if getattr(self, "ptr", 0):
+            lib().adot_mlp_destroy(self.ptr)
+            self.ptr = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def adot_set_surrogate(ctx: int, mlp, fr_lo: float = 0.8, fr_hi: float = 1.2) -> None:
+    _check(lib().adot_set_surrogate(ctx, mlp.ptr if mlp is not None else None, fr_lo, fr_hi),
+           "adot_set_surrogate")
+
+
+def adot_surrogate_stats(ctx: int):
+    e, f = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().adot_surrogate_stats(ctx, ctypes.byref(e), ctypes.byref(f)), "adot_surrogate_stats")
+    return e.value, f.value
+
+
+def adot_harvest(ctx: int, n: int, seed: int = 1):
+    """n edge samples of the context's state: (X [n, 7] raw inputs, T [n, 9] labels)."""
+    X = np.empty((n, 7), dtype=np.float32)
+    T = np.empty((n, 9), dtype=np.float32)
+    _check(lib().adot_harvest(ctx, n, seed, X.ctypes.data, T.ctypes.data, 0), "adot_harvest")
+    return X, T
 
 
 def adot_conserved_sums(ctx: int) -> np.ndarray:

@@ -17,7 +17,7 @@ BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(HERE, "libadot.so")
 
 SOURCES = ["adot_step_f32.cu", "adot_step_f64.cu", "adot_aux.cu", "adot_capi.cu",
-           "adot_noalloc.cu", "adot_ensemble.cu"]
+           "adot_noalloc.cu", "adot_ensemble.cu", "adot_mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # -ftz / -prec-div / -prec-sqrt relax float32 only (denormals flushed, division and
 # square root to ~2 ulp); float64 arithmetic is unaffected.

@@ -1,8 +1,16 @@
 // Auxiliary kernels: stateless edge fluctuations, float64 <-> float-float
 // conversion and fixed-order conserved sums.
+#include <type_traits>
+
 #include "adot_step_impl.cuh"
 
 namespace adot {
+
+static unsigned grid_for(int64_t n) {
+  int64_t g = (n + 255) / 256;
+  if (g > 152 * 16) g = 152 * 16;
+  return (unsigned)(g < 1 ? 1 : g);
+}
 
 // D-/+ of n independent edges (Eq. DOTjumpN) from [3][n] float64 arrays. In
 // float32 the inputs are rounded to float-float, as the time-step state is.
@@ -78,6 +86,65 @@ cudaError_t launch_fluct(int precision, int law, const LawT<float>& lf, const La
   return cudaGetLastError();
 }
 
+// Edge samples with float64 labels (see launch_harvest_f32).
+template <typename R>
+__global__ void __launch_bounds__(256) k_harvest(const StepParams p, const typename Prec<R>::State st,
+                                                 int slot, int64_t n, uint64_t seed, float Ag,
+                                                 float* __restrict__ X, float* __restrict__ T,
+                                                 unsigned* status) {
+  using S = typename Prec<R>::S;
+  unsigned flags = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = (int64_t)(splitmix64(seed ^ (0xD1B54A32D192ED03ull * (uint64_t)(i + 1))) %
+                                (uint64_t)(p.n + 1));
+    S wl[3], wr[3];
+    load_edge<R>(p, st, e, slot, wl, wr);
+    double dl[3], dr[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      if constexpr (std::is_same<R, float>::value) {
+        dl[r] = ff_to_double(*reinterpret_cast<const float2*>(&wl[r]));
+        dr[r] = ff_to_double(*reinterpret_cast<const float2*>(&wr[r]));
+      } else {
+        dl[r] = *reinterpret_cast<const double*>(&wl[r]);
+        dr[r] = *reinterpret_cast<const double*>(&wr[r]);
+      }
+      X[i * 7 + r] = (float)dl[r];
+      X[i * 7 + 3 + r] = (float)dr[r];
+    }
+    X[i * 7 + 6] = Ag;
+    double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const double sk = (k == 0) ? GL3_S0 : ((k == 1) ? 0.5 : GL3_S2);
+      const double w = (k == 1) ? GL3_W1 : GL3_W0;
+      double M[9];
+      abs_A_matrix_f64<LAW_GRASS>(p.ld, dl[0] + sk * (dr[0] - dl[0]), dl[1] + sk * (dr[1] - dl[1]), M,
+                                  flags);
+#pragma unroll
+      for (int r = 0; r < 9; ++r) acc[r] += w * M[r];
+    }
+#pragma unroll
+    for (int r = 0; r < 9; ++r) T[i * 9 + r] = (float)acc[r];
+  }
+  if (flags && status) atomicOr(status, flags);
+}
+
+cudaError_t launch_harvest_f32(const StepParams& p, StateF32 st, int slot, int64_t n, uint64_t seed,
+                               float Ag, float* X, float* T, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_harvest<float><<<grid_for(n), 256, 0, s>>>(p, st, slot, n, seed, Ag, X, T, &p.ctl->status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_harvest_f64(const StepParams& p, StateF64 st, int slot, int64_t n, uint64_t seed,
+                               float Ag, float* X, float* T, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_harvest<double><<<grid_for(n), 256, 0, s>>>(p, st, slot, n, seed, Ag, X, T, &p.ctl->status);
+  return cudaGetLastError();
+}
+
 __global__ void __launch_bounds__(256) k_to_ff(const double* __restrict__ src, float2* __restrict__ dst,
                                                int64_t n) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -90,12 +157,6 @@ __global__ void __launch_bounds__(256) k_from_ff(const float2* __restrict__ src,
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
     dst[i] = ff_to_double(src[i]);
-}
-
-static unsigned grid_for(int64_t n) {
-  int64_t g = (n + 255) / 256;
-  if (g > 152 * 16) g = 152 * 16;
-  return (unsigned)(g < 1 ? 1 : g);
 }
 
 cudaError_t launch_to_ff(const double* src, float2* dst, int64_t n, cudaStream_t s) {

@@ -50,7 +50,21 @@ struct adot_ctx {
   bool graph_ready;
   bool state_set;
   double t_end_dev;  // t_end currently stored in the control block
+  // learned surrogate of |A|_Psi (float32 Grass contexts)
+  adot_mlp* mlp;
+  float fr_lo, fr_hi;
+  float* d_absA;                 // [9][n+1]
+  unsigned long long* d_fb;      // edges that fell back (cumulative)
+  long long sur_steps0;          // step counter when the surrogate was attached
+  unsigned long long fb0;        // fallback count when it was attached
 };
+
+namespace adot {
+cudaError_t launch_mlp_edges(const adot_mlp* m, const StepParams& sp, StateF32 st, int slot,
+                             float Ag, float fr_lo, float fr_hi, float* absA,
+                             unsigned long long* fb, cudaStream_t s);
+bool mlp_ready(const adot_mlp* m);
+}  // namespace adot
 
 namespace {
 
@@ -138,6 +152,14 @@ StateF64 st64(adot_ctx* c, int which) {
 
 cudaError_t launch_one_v(adot_ctx* c, StepVariant v, cudaStream_t s, int cur, int phase) {
   const int slot = phase % 3;
+  if (c->mlp) {  // surrogate |A|_Psi for every edge, then the update
+    cudaError_t e = launch_mlp_edges(c->mlp, c->p, st32(c, cur), slot, (float)c->cfg.law.Ag,
+                                     c->fr_lo, c->fr_hi, c->d_absA, c->d_fb, s);
+    if (e != cudaSuccess) return e;
+    StepParams p = c->p;
+    p.absA = c->d_absA;
+    return launch_step_sur_f32(p, st32(c, cur), st32(c, 1 - cur), slot, s);
+  }
   if (c->prec == ADOT_FP32)
     return launch_step_f32(c->p, c->law, v, st32(c, cur), st32(c, 1 - cur), slot, s);
   return launch_step_f64(c->p, c->law, v, st64(c, cur), st64(c, 1 - cur), slot, s);
@@ -284,6 +306,8 @@ void free_ctx(adot_ctx* c) {
   if (c->d_fl) cudaFree(c->d_fl);
   if (c->d_flrho) cudaFree(c->d_flrho);
   if (c->h_flrho) cudaFreeHost(c->h_flrho);
+  if (c->d_absA) cudaFree(c->d_absA);
+  if (c->d_fb) cudaFree(c->d_fb);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   free(c);
@@ -553,6 +577,77 @@ adot_status adot_autotune(adot_ctx* c, int64_t trial_steps, int32_t* block_out,
   if (block_out) *block_out = c->var.block;
   if (reg_cap_out) *reg_cap_out = c->var.reg_cap ? c->var.reg_cap : -1;
   return ADOT_OK;
+}
+
+adot_status adot_set_surrogate(adot_ctx* c, adot_mlp* m, double fr_lo, double fr_hi) {
+  if (!c) return ADOT_E_INVALID_ARG;
+  if (m == nullptr) {
+    c->mlp = nullptr;
+    return build_graph(c);
+  }
+  if (c->prec != ADOT_FP32 || c->law != ADOT_LAW_GRASS) return ADOT_E_UNSUPPORTED;
+  if (!mlp_ready(m) || !(fr_lo <= fr_hi)) return ADOT_E_INVALID_ARG;
+  CK(cudaStreamSynchronize(c->stream));
+  if (!c->d_absA) {
+    CK(cudaMalloc((void**)&c->d_absA, sizeof(float) * 9 * (size_t)(c->p.n + 1)));
+    CK(cudaMalloc((void**)&c->d_fb, sizeof(unsigned long long)));
+    CK(cudaMemset(c->d_fb, 0, sizeof(unsigned long long)));
+  }
+  c->mlp = m;
+  c->fr_lo = (float)fr_lo;
+  c->fr_hi = (float)fr_hi;
+  adot_status st = read_ctl(c);
+  if (st) return st;
+  c->sur_steps0 = c->h_ctl->s[c->phase % 3].steps;
+  CK(cudaMemcpy(&c->fb0, c->d_fb, sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+  return build_graph(c);
+}
+
+adot_status adot_surrogate_stats(adot_ctx* c, int64_t* edges_out, int64_t* fallback_out) {
+  if (!c) return ADOT_E_INVALID_ARG;
+  adot_status st = read_ctl(c);
+  if (st) return st;
+  unsigned long long fb = 0;
+  if (c->d_fb) CK(cudaMemcpy(&fb, c->d_fb, sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+  const long long steps = c->h_ctl->s[c->phase % 3].steps - c->sur_steps0;
+  if (edges_out) *edges_out = c->mlp ? steps * (c->p.n + 1) : 0;
+  if (fallback_out) *fallback_out = (int64_t)(fb - c->fb0);
+  return ADOT_OK;
+}
+
+adot_status adot_harvest(adot_ctx* c, int64_t n, uint64_t seed, float* X, float* T, int on_device) {
+  if (!c || !c->state_set || n < 0 || (n > 0 && (!X || !T))) return ADOT_E_INVALID_ARG;
+  if (c->law != ADOT_LAW_GRASS) return ADOT_E_UNSUPPORTED;
+  if (n == 0) return ADOT_OK;
+  float* dX = X;
+  float* dT = T;
+  if (!on_device) {
+    CK(cudaMalloc((void**)&dX, sizeof(float) * 7 * (size_t)n));
+    if (cudaMalloc((void**)&dT, sizeof(float) * 9 * (size_t)n) != cudaSuccess) {
+      cudaFree(dX);
+      return ADOT_E_CUDA;
+    }
+  }
+  const int slot = c->phase % 3;
+  cudaError_t e;
+  if (c->prec == ADOT_FP32)
+    e = launch_harvest_f32(c->p, st32(c, c->cur), slot, n, seed, (float)c->cfg.law.Ag, dX, dT, c->stream);
+  else
+    e = launch_harvest_f64(c->p, st64(c, c->cur), slot, n, seed, (float)c->cfg.law.Ag, dX, dT, c->stream);
+  if (e == cudaSuccess && !on_device) {
+    e = cudaMemcpyAsync(X, dX, sizeof(float) * 7 * (size_t)n, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(T, dT, sizeof(float) * 9 * (size_t)n, cudaMemcpyDeviceToHost, c->stream);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (!on_device) {
+    cudaFree(dX);
+    cudaFree(dT);
+  }
+  if (e != cudaSuccess) return ADOT_E_CUDA;
+  adot_status st = read_ctl(c);
+  if (st) return st;
+  return status_from_bits(c->h_ctl->status);
 }
 
 adot_status adot_conserved_sums(adot_ctx* c, double sums_out[3]) {

@@ -49,6 +49,7 @@ struct StepParams {
   LawT<float> lf;
   LawT<double> ld;
   Ctl* ctl;
+  const float* absA;  // surrogate |A|_Psi per edge, [9][n+1] (NaN in row 0: analytic edge)
 };
 
 enum : int { BC_TRANSMISSIVE = 0, BC_PERIODIC = 1, BC_INFLOW_Q = 2, BC_OUTFLOW_H = 3, BC_INFLOW_QZ = 4 };
@@ -74,6 +75,18 @@ cudaError_t launch_step_f32(const StepParams& p, int law, StepVariant v, StateF3
                             int slot, cudaStream_t s);
 cudaError_t launch_step_f64(const StepParams& p, int law, StepVariant v, StateF64 in, StateF64 out,
                             int slot, cudaStream_t s);
+
+// Time step whose edges take |A|_Psi from p.absA (float32, Grass law, 256 x 64).
+cudaError_t launch_step_sur_f32(const StepParams& p, StateF32 in, StateF32 out, int slot,
+                                cudaStream_t s);
+
+// n edge samples of a state (edge index drawn with splitmix64 from seed and the
+// sample number): raw inputs X [n][7] (h, q, z left and right, A_g) and float64
+// labels T [n][9] = sum_k w_k |A(Psi_k)|, stored as float32.
+cudaError_t launch_harvest_f32(const StepParams& p, StateF32 st, int slot, int64_t n, uint64_t seed,
+                               float Ag, float* X, float* T, cudaStream_t s);
+cudaError_t launch_harvest_f64(const StepParams& p, StateF64 st, int slot, int64_t n, uint64_t seed,
+                               float Ag, float* X, float* T, cudaStream_t s);
 
 // CFL maximum of a state into ctl->s[slot].rho_bits (which must be zero), and
 // admissibility (h > 0, finite) into ctl->status.

@@ -375,6 +375,37 @@ __device__ __forceinline__ float spectral_radius_f32(const LawT<float>& L, float
   return l;
 }
 
+// Full |A| (row-major 3x3) at a state in float64, column by column through the
+// same evaluation as |A| dW (eigenvectors, or the Newton form near coalescence).
+template <int LAW>
+__device__ __forceinline__ void abs_A_matrix_f64(const LawT<double>& L, double h, double q,
+                                                 double X[9], unsigned& flags) {
+  Eig<double> e;
+  node_eig<double, LAW>(L, h, q, e);
+  if (!(d_abs(e.arg) <= 1.0 + TAU_HYP)) flags |= ST_NONHYPERBOLIC;
+  const bool newton = d_min(e.l2 - e.l1, e.l3 - e.l2) < TAU_GAP * e.c;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const double v0 = (j == 0) ? 1.0 : 0.0, v1 = (j == 1) ? 1.0 : 0.0, v2 = (j == 2) ? 1.0 : 0.0;
+    double x0, x1, x2;
+    if (newton)
+      abs_A_times_newton(e, v0, v1, v2, x0, x1, x2);
+    else
+      abs_A_times_eigvec(e, v0, v1, v2, x0, x1, x2);
+    X[0 * 3 + j] = x0;
+    X[1 * 3 + j] = x1;
+    X[2 * 3 + j] = x2;
+  }
+}
+
+// splitmix64 (Steele, Lea & Flood 2014): counter-based 64-bit mixer.
+__host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
 // ---------------------------------------------------------------------------
 // float-float helpers (value = hi + lo, |lo| <= ulp(hi)/2)
 // ---------------------------------------------------------------------------

@@ -1,0 +1,1134 @@
+// Learned surrogate of the quadrature-averaged |A|: an MLP
+// 7 -> 128 -> 128 -> 128 -> 128 -> 9 (GELU on the hidden layers) with bfloat16
+// weights and activations and float32 accumulation on the tensor cores
+// (mma.sync m16n8k16), trained by Adam on standardised inputs and outputs.
+//
+// The surrogate replaces only |A|_Psi = sum_k w_k |A(Psi(s_k))| in
+// Eq. DOTjumpN; A dW keeps its analytic form, and edges with a local Froude
+// number in [0.8, 1.2] (or inputs outside the training box) use the analytic
+// eigenstructure (Sec. 3.3).
+//
+// Layout: every layer is stored padded to multiples of 16 (in 7 -> 16, out
+// 9 -> 16) with zero padding, W as [out][in] row-major (the K-contiguous
+// operand both mma operands want) plus its transpose for the backward pass.
+// Matrix products are C[M x N] = A[M x K] S[N x K]^T with A and S row-major.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <vector>
+
+#include "../../include/adot.h"
+#include "adot_step_impl.cuh"
+
+namespace adot {
+
+constexpr int kLayers = 5;
+constexpr int kIn = 7, kOut = 9, kHid = 128, kPad = 16;
+// padded input (K) and output (N) widths of layer l, and the unpadded ones
+__host__ __device__ constexpr int dim_in(int l) { return l == 0 ? kPad : kHid; }
+__host__ __device__ constexpr int dim_out(int l) { return l == kLayers - 1 ? kPad : kHid; }
+__host__ __device__ constexpr int real_in(int l) { return l == 0 ? kIn : kHid; }
+__host__ __device__ constexpr int real_out(int l) { return l == kLayers - 1 ? kOut : kHid; }
+constexpr int kTileRows = 64;  // batch rows per CTA in the layer kernels
+
+__host__ __device__ constexpr int w_offset(int l) {
+  int o = 0;
+  for (int i = 0; i < l; ++i) o += dim_in(i) * dim_out(i);
+  return o;
+}
+__host__ __device__ constexpr int b_offset(int l) {
+  int o = 0;
+  for (int i = 0; i < l; ++i) o += dim_out(i);
+  return o;
+}
+constexpr int kWTotal = w_offset(kLayers);
+constexpr int kBTotal = b_offset(kLayers);
+static_assert(kIn * kHid + kHid + 3 * (kHid * kHid + kHid) + kHid * kOut + kOut == ADOT_MLP_PARAMS,
+              "packed parameter count");
+
+// --------------------------------------------------------------------------
+// device helpers
+// --------------------------------------------------------------------------
+
+__host__ __device__ __forceinline__ int64_t imin64(int64_t a, int64_t b) { return a < b ? a : b; }
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&v);
+}
+
+__device__ __forceinline__ uint32_t pack_raw(__nv_bfloat16 lo, __nv_bfloat16 hi) {
+  const uint32_t l = *reinterpret_cast<const uint16_t*>(&lo);
+  const uint32_t h = *reinterpret_cast<const uint16_t*>(&hi);
+  return l | (h << 16);
+}
+
+__device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], const uint32_t b[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// GELU, tanh form (Hendrycks & Gimpel 2016), and its derivative.
+__device__ __forceinline__ float gelu_f(float x) {
+  const float c = 0.7978845608028654f;  // sqrt(2/pi)
+  return 0.5f * x * (1.0f + tanhf(c * (x + 0.044715f * x * x * x)));
+}
+__device__ __forceinline__ float gelu_prime_f(float x) {
+  const float c = 0.7978845608028654f;
+  const float t = tanhf(c * (x + 0.044715f * x * x * x));
+  return 0.5f * (1.0f + t) + 0.5f * x * (1.0f - t * t) * c * (1.0f + 3.0f * 0.044715f * x * x);
+}
+
+// Copies a rows x cols bf16 block (global row stride gs, cols a multiple of 8)
+// into shared memory with row stride ss.
+__device__ __forceinline__ void load_tile_bf16(__nv_bfloat16* s, int ss, const __nv_bfloat16* g,
+                                               int64_t gs, int rows, int cols, int rows_valid) {
+  const int vec_per_row = cols / 8;
+  for (int i = threadIdx.x; i < rows * vec_per_row; i += blockDim.x) {
+    const int r = i / vec_per_row, v = i % vec_per_row;
+    uint4 val = make_uint4(0, 0, 0, 0);
+    if (r < rows_valid) val = *reinterpret_cast<const uint4*>(g + (int64_t)r * gs + v * 8);
+    *reinterpret_cast<uint4*>(s + r * ss + v * 8) = val;
+  }
+}
+
+// Warp-level product of a 16-row slab of sA (rows r0.., stride lda) with NT
+// 8-column tiles of sS (rows n0 + 8j.., stride lds) over K; accumulates in acc.
+template <int K, int NT>
+__device__ __forceinline__ void warp_gemm(const __nv_bfloat16* sA, int lda, int r0,
+                                          const __nv_bfloat16* sS, int lds, int n0,
+                                          float acc[NT][4]) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+#pragma unroll
+  for (int k0 = 0; k0 < K; k0 += 16) {
+    uint32_t a[4];
+    a[0] = *reinterpret_cast<const uint32_t*>(sA + (r0 + g) * lda + k0 + 2 * t);
+    a[1] = *reinterpret_cast<const uint32_t*>(sA + (r0 + g + 8) * lda + k0 + 2 * t);
+    a[2] = *reinterpret_cast<const uint32_t*>(sA + (r0 + g) * lda + k0 + 8 + 2 * t);
+    a[3] = *reinterpret_cast<const uint32_t*>(sA + (r0 + g + 8) * lda + k0 + 8 + 2 * t);
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+      uint32_t b[2];
+      const __nv_bfloat16* sr = sS + (n0 + 8 * j + g) * lds + k0 + 2 * t;
+      b[0] = *reinterpret_cast<const uint32_t*>(sr);
+      b[1] = *reinterpret_cast<const uint32_t*>(sr + 8);
+      mma_bf16(acc[j], a, b);
+    }
+  }
+}
+
+// --------------------------------------------------------------------------
+// training kernels
+// --------------------------------------------------------------------------
+
+enum : int { EPI_GELU = 0, EPI_LINEAR = 1, EPI_BWD = 2 };
+
+// One layer over a 64-row tile: C = A S^T (+ bias).
+//  EPI_GELU:   z = C + b -> Z (bf16), H = gelu(z) (bf16)
+//  EPI_LINEAR: y = C + b -> Y (float32, N columns)
+//  EPI_BWD:    dZprev = C * gelu'(Zprev) (bf16)
+template <int K, int N>
+__host__ __device__ constexpr size_t layer_smem() {
+  return sizeof(__nv_bfloat16) * (size_t)(kTileRows + N) * (K + 8);
+}
+
+template <int K, int N, int EPI>
+__global__ void __launch_bounds__(256) k_layer(const __nv_bfloat16* __restrict__ A,
+                                               const __nv_bfloat16* __restrict__ S,
+                                               const float* __restrict__ bias,
+                                               const __nv_bfloat16* __restrict__ aux, void* out0,
+                                               __nv_bfloat16* __restrict__ out1, int64_t rows) {
+  constexpr int LDA = K + 8, LDS = K + 8;
+  constexpr int NT = N / 16;  // 8-column tiles per warp (two column halves)
+  extern __shared__ __align__(16) unsigned char lsm[];
+  __nv_bfloat16* sA = reinterpret_cast<__nv_bfloat16*>(lsm);
+  __nv_bfloat16* sS = sA + kTileRows * LDA;
+  const int64_t row0 = (int64_t)blockIdx.x * kTileRows;
+  const int valid = (int)imin64(kTileRows, rows - row0);
+  load_tile_bf16(sA, LDA, A + row0 * K, K, kTileRows, K, valid);
+  load_tile_bf16(sS, LDS, S, K, N, K, N);
+  __syncthreads();
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int r0 = (w & 3) * 16, n0 = (w >> 2) * (N / 2);
+  float acc[NT][4];
+#pragma unroll
+  for (int j = 0; j < NT; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.0f;
+  warp_gemm<K, NT>(sA, LDA, r0, sS, LDS, n0, acc);
+#pragma unroll
+  for (int j = 0; j < NT; ++j) {
+    const int col = n0 + 8 * j + 2 * t;
+#pragma unroll
+    for (int hh = 0; hh < 2; ++hh) {
+      const int lr = r0 + g + 8 * hh;
+      if (lr >= valid) continue;
+      const int64_t row = row0 + lr;
+      float v0 = acc[j][2 * hh], v1 = acc[j][2 * hh + 1];
+      if (EPI == EPI_GELU) {
+        v0 += bias[col];
+        v1 += bias[col + 1];
+        *reinterpret_cast<uint32_t*>((__nv_bfloat16*)out0 + row * N + col) = pack_bf16(v0, v1);
+        *reinterpret_cast<uint32_t*>(out1 + row * N + col) = pack_bf16(gelu_f(v0), gelu_f(v1));
+      } else if (EPI == EPI_LINEAR) {
+        v0 += bias[col];
+        v1 += bias[col + 1];
+        *reinterpret_cast<float2*>((float*)out0 + row * N + col) = make_float2(v0, v1);
+      } else {
+        const __nv_bfloat162 z = *reinterpret_cast<const __nv_bfloat162*>(aux + row * N + col);
+        v0 *= gelu_prime_f(__bfloat162float(z.x));
+        v1 *= gelu_prime_f(__bfloat162float(z.y));
+        *reinterpret_cast<uint32_t*>((__nv_bfloat16*)out0 + row * N + col) = pack_bf16(v0, v1);
+      }
+    }
+  }
+}
+
+// Weight gradient partial over `chunk` batch rows: dW[N x K] = dZ^T X and
+// db[N] = column sums of dZ, written to the block's partial slots.
+template <int K, int N>
+__global__ void __launch_bounds__(256) k_wgrad(const __nv_bfloat16* __restrict__ dZ,
+                                               const __nv_bfloat16* __restrict__ X,
+                                               float* __restrict__ pW, float* __restrict__ pB,
+                                               int64_t rows, int chunk) {
+  constexpr int LDD = N + 8, LDX = K + 8;
+  constexpr int RT = N / 16;            // 16-row tiles of dW
+  constexpr int WPR = 8 / RT;           // warps per row tile
+  constexpr int KT = K / 8 / WPR;       // 8-column tiles per warp
+  __shared__ __align__(16) __nv_bfloat16 sD[kTileRows * LDD];
+  __shared__ __align__(16) __nv_bfloat16 sX[kTileRows * LDX];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int rt = w / WPR, jw = w % WPR;
+  float acc[KT][4];
+#pragma unroll
+  for (int j = 0; j < KT; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.0f;
+  float bsum = 0.0f;
+  const int64_t c0 = (int64_t)blockIdx.x * chunk;
+  const int64_t c1 = imin64(c0 + chunk, rows);
+  for (int64_t r = c0; r < c1; r += kTileRows) {
+    const int valid = (int)imin64(kTileRows, c1 - r);
+    __syncthreads();
+    load_tile_bf16(sD, LDD, dZ + r * N, N, kTileRows, N, valid);
+    load_tile_bf16(sX, LDX, X + r * K, K, kTileRows, K, valid);
+    __syncthreads();
+    if (threadIdx.x < N)
+      for (int i = 0; i < valid; ++i) bsum += __bfloat162float(sD[i * LDD + threadIdx.x]);
+#pragma unroll
+    for (int k0 = 0; k0 < kTileRows; k0 += 16) {
+      // A[m][k] = dZ[k][16 rt + m]; B[k][n] = X[k][8 j + n]
+      uint32_t a[4];
+      const int m0 = rt * 16 + g;
+      a[0] = pack_raw(sD[(k0 + 2 * t) * LDD + m0], sD[(k0 + 2 * t + 1) * LDD + m0]);
+      a[1] = pack_raw(sD[(k0 + 2 * t) * LDD + m0 + 8], sD[(k0 + 2 * t + 1) * LDD + m0 + 8]);
+      a[2] = pack_raw(sD[(k0 + 2 * t + 8) * LDD + m0], sD[(k0 + 2 * t + 9) * LDD + m0]);
+      a[3] = pack_raw(sD[(k0 + 2 * t + 8) * LDD + m0 + 8], sD[(k0 + 2 * t + 9) * LDD + m0 + 8]);
+#pragma unroll
+      for (int j = 0; j < KT; ++j) {
+        const int n = 8 * (jw + j * WPR) + g;
+        uint32_t b[2];
+        b[0] = pack_raw(sX[(k0 + 2 * t) * LDX + n], sX[(k0 + 2 * t + 1) * LDX + n]);
+        b[1] = pack_raw(sX[(k0 + 2 * t + 8) * LDX + n], sX[(k0 + 2 * t + 9) * LDX + n]);
+        mma_bf16(acc[j], a, b);
+      }
+    }
+  }
+  float* dst = pW + (int64_t)blockIdx.x * N * K;
+#pragma unroll
+  for (int j = 0; j < KT; ++j) {
+    const int col = 8 * (jw + j * WPR) + 2 * t;
+    const int rA = rt * 16 + g;
+    dst[rA * K + col] = acc[j][0];
+    dst[rA * K + col + 1] = acc[j][1];
+    dst[(rA + 8) * K + col] = acc[j][2];
+    dst[(rA + 8) * K + col + 1] = acc[j][3];
+  }
+  if (threadIdx.x < N) pB[(int64_t)blockIdx.x * N + threadIdx.x] = bsum;
+}
+
+struct MlpDev {
+  float* master;   // [kWTotal + kBTotal] padded float32 parameters (weights then biases)
+  float* m;        // Adam first moments
+  float* v;        // Adam second moments
+  float* grad;     // reduced gradient (padded layout)
+  __nv_bfloat16* W;   // [kWTotal] bf16 W_l [N][K]
+  __nv_bfloat16* Wt;  // [kWTotal] bf16 W_l^T [K][N]
+  float* stats;    // x_mean[7], x_std[7], y_mean[9], y_std[9]
+  long long* step; // training step counter
+};
+
+// Sum of the block partials (fixed order) for every padded parameter, Adam
+// update of the float32 master copy (Kingma & Ba 2015) with a cosine-decayed
+// step size, and refresh of the bf16 copies W and W^T.
+struct AdamArgs {
+  const float* pW[kLayers];
+  const float* pB[kLayers];
+  int nchunk[kLayers];
+};
+
+__global__ void __launch_bounds__(256) k_adam(MlpDev d, const AdamArgs a, float lr0,
+                                              int64_t total_steps, float b1, float b2, float eps,
+                                              int apply) {
+  const float* const* pW = a.pW;
+  const float* const* pB = a.pB;
+  const int* nchunk = a.nchunk;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= kWTotal + kBTotal) return;
+  int l = 0, local = 0;
+  bool is_w = i < kWTotal;
+  if (is_w) {
+    while (l + 1 < kLayers && i >= w_offset(l + 1)) ++l;
+    local = i - w_offset(l);
+  } else {
+    const int j = i - kWTotal;
+    while (l + 1 < kLayers && j >= b_offset(l + 1)) ++l;
+    local = j - b_offset(l);
+  }
+  const int size = is_w ? dim_in(l) * dim_out(l) : dim_out(l);
+  const float* src = is_w ? pW[l] : pB[l];
+  float gsum = 0.0f;
+  for (int c = 0; c < nchunk[l]; ++c) gsum += src[(int64_t)c * size + local];
+  d.grad[i] = gsum;
+  if (!apply) return;
+  const long long t = *d.step + 1;
+  const double frac = total_steps > 0 ? fmin(1.0, (double)(t - 1) / (double)total_steps) : 0.0;
+  const float lr = lr0 * (float)(0.05 + 0.95 * 0.5 * (1.0 + cos(3.14159265358979 * frac)));
+  const float m = b1 * d.m[i] + (1.0f - b1) * gsum;
+  const float v = b2 * d.v[i] + (1.0f - b2) * gsum * gsum;
+  d.m[i] = m;
+  d.v[i] = v;
+  const float mh = m / (1.0f - powf(b1, (float)t));
+  const float vh = v / (1.0f - powf(b2, (float)t));
+  const float p = d.master[i] - lr * mh / (sqrtf(vh) + eps);
+  d.master[i] = p;
+  if (is_w) {
+    const int K = dim_in(l), N = dim_out(l);
+    const int n = local / K, k = local % K;
+    d.W[w_offset(l) + n * K + k] = __float2bfloat16_rn(p);
+    d.Wt[w_offset(l) + k * N + n] = __float2bfloat16_rn(p);
+  }
+}
+
+__global__ void k_step_incr(long long* step) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *step += 1;
+}
+
+// bf16 copies of the master parameters.
+__global__ void k_refresh_bf16(MlpDev d) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= kWTotal) return;
+  int l = 0;
+  while (l + 1 < kLayers && i >= w_offset(l + 1)) ++l;
+  const int local = i - w_offset(l);
+  const int K = dim_in(l), N = dim_out(l);
+  const int n = local / K, k = local % K;
+  d.W[i] = __float2bfloat16_rn(d.master[i]);
+  d.Wt[w_offset(l) + k * N + n] = __float2bfloat16_rn(d.master[i]);
+}
+
+// Batch of standardised samples: rows idx (explicit) or drawn with splitmix64
+// from (seed, step, row); X bf16 [B][16] zero-padded, T float32 [B][9].
+__global__ void k_gather(const float* __restrict__ Xraw, const float* __restrict__ Traw,
+                         int64_t n_data, const int64_t* __restrict__ idx, uint64_t seed,
+                         const long long* step, int64_t B, const float* __restrict__ stats,
+                         __nv_bfloat16* __restrict__ Xb, float* __restrict__ Tb) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  int64_t r;
+  if (idx) {
+    r = idx[b];
+  } else {
+    const uint64_t s = (uint64_t)(step ? *step : 0);
+    r = (int64_t)(splitmix64(seed ^ (s * 0x100000001B3ull + (uint64_t)b)) % (uint64_t)n_data);
+  }
+  __align__(16) __nv_bfloat16 xs[kPad];
+#pragma unroll
+  for (int k = 0; k < kPad; ++k) {
+    float v = 0.0f;
+    if (k < kIn) v = (Xraw[r * kIn + k] - stats[k]) / stats[kIn + k];
+    xs[k] = __float2bfloat16_rn(v);
+  }
+  *reinterpret_cast<uint4*>(Xb + b * kPad) = *reinterpret_cast<uint4*>(xs);
+  *reinterpret_cast<uint4*>(Xb + b * kPad + 8) = *reinterpret_cast<uint4*>(xs + 8);
+  if (Tb && Traw)
+    for (int k = 0; k < kOut; ++k)
+      Tb[b * kOut + k] = (Traw[r * kOut + k] - stats[2 * kIn + k]) / stats[2 * kIn + kOut + k];
+}
+
+// MSE loss on the 9 outputs and its gradient (bf16, zero in the padding).
+__global__ void __launch_bounds__(256) k_loss(const float* __restrict__ Y, const float* __restrict__ T,
+                                              int64_t B, __nv_bfloat16* __restrict__ dY,
+                                              float* __restrict__ loss_part) {
+  __shared__ float sred[8];
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  float acc = 0.0f;
+  if (b < B) {
+    __align__(16) __nv_bfloat16 g[kPad];
+    const float scale = 2.0f / ((float)B * (float)kOut);
+#pragma unroll
+    for (int k = 0; k < kPad; ++k) {
+      float d = 0.0f;
+      if (k < kOut) {
+        d = Y[b * kPad + k] - T[b * kOut + k];
+        acc += d * d;
+      }
+      g[k] = __float2bfloat16_rn(scale * d);
+    }
+    *reinterpret_cast<uint4*>(dY + b * kPad) = *reinterpret_cast<uint4*>(g);
+    *reinterpret_cast<uint4*>(dY + b * kPad + 8) = *reinterpret_cast<uint4*>(g + 8);
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) sred[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float s = 0.0f;
+    for (int i = 0; i < 8; ++i) s += sred[i];
+    loss_part[blockIdx.x] = s;
+  }
+}
+
+// Loss of the step = sum of block partials / (B * 9), in fixed order.
+__global__ void k_loss_sum(const float* part, int nparts, int64_t B, const long long* step,
+                           float* hist, int64_t hist_len) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double s = 0.0;
+  for (int i = 0; i < nparts; ++i) s += part[i];
+  const long long k = *step;
+  if (k >= 0 && k < hist_len) hist[k] = (float)(s / ((double)B * kOut));
+}
+
+// Dataset statistics: per-column mean and standard deviation of X (7) and T (9).
+__global__ void k_stats(const float* __restrict__ Xraw, const float* __restrict__ Traw, int64_t n,
+                        float* stats) {
+  const int col = blockIdx.x;  // 0..15
+  const bool isx = col < kIn;
+  const int c = isx ? col : col - kIn;
+  const int stride = isx ? kIn : kOut;
+  const float* src = isx ? Xraw : Traw;
+  __shared__ double s1[256], s2[256];
+  double a = 0.0, b = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += 256) {
+    const double v = src[i * stride + c];
+    a += v;
+    b += v * v;
+  }
+  s1[threadIdx.x] = a;
+  s2[threadIdx.x] = b;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      s1[threadIdx.x] += s1[threadIdx.x + w];
+      s2[threadIdx.x] += s2[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double mean = s1[0] / (double)n;
+    double var = s2[0] / (double)n - mean * mean;
+    double sd = var > 0.0 ? sqrt(var) : 0.0;
+    if (!(sd > 1e-12 * (fabs(mean) + 1e-30))) sd = 1.0;
+    const int base = isx ? 0 : 2 * kIn;
+    const int nn = isx ? kIn : kOut;
+    stats[base + c] = (float)mean;
+    stats[base + nn + c] = (float)sd;
+  }
+}
+
+// --------------------------------------------------------------------------
+// fused inference over edges
+// --------------------------------------------------------------------------
+
+constexpr int kInferRows = 128;
+constexpr int kInferThreads = 512;
+constexpr int kLdh = kHid + 8;
+
+struct InferParams {
+  const __nv_bfloat16* W;  // bf16 weights, padded layout
+  const float* bias;       // float32 biases, padded layout (master + kWTotal)
+  const float* stats;
+  float lo[kIn], hi[kIn];  // training box per raw input (with margin)
+  float fr_lo, fr_hi;      // Froude band that falls back
+  float Ag;
+};
+
+__host__ __device__ constexpr size_t infer_smem_bytes() {
+  return sizeof(__nv_bfloat16) * ((size_t)w_offset(kLayers) + kLayers * 8 * 128 +  // weights (+row pad)
+                                  2 * (size_t)kInferRows * kLdh) +                   // activations
+         sizeof(float) * kInferRows * kPad;                                           // outputs
+}
+
+// Runs the MLP on one 128-row tile held in sX ([128][16] bf16, stride kLdh):
+// ping-pong activations in sH0/sH1, output rows in sY ([128][16] float32).
+__device__ __forceinline__ void infer_tile(const __nv_bfloat16* sW, const int* wstride,
+                                           const float* bias, __nv_bfloat16* sH0,
+                                           __nv_bfloat16* sH1, float* sY) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int r0 = (w & 7) * 16;  // 16 warps: 8 row tiles x 2 column halves
+  const int half = w >> 3;
+  __nv_bfloat16* in = sH0;
+  __nv_bfloat16* out = sH1;
+  for (int l = 0; l < kLayers; ++l) {
+    const __nv_bfloat16* sS = sW + w_offset(l) + l * 8 * 128;  // see the smem layout below
+    const int lds = wstride[l];
+    if (l < kLayers - 1) {
+      float acc[8][4];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.0f;
+      if (l == 0)
+        warp_gemm<16, 8>(in, kLdh, r0, sS, lds, half * 64, acc);
+      else
+        warp_gemm<128, 8>(in, kLdh, r0, sS, lds, half * 64, acc);
+      const float* b = bias + b_offset(l);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int col = half * 64 + 8 * j + 2 * t;
+        out[(r0 + g) * kLdh + col] = __float2bfloat16_rn(gelu_f(acc[j][0] + b[col]));
+        out[(r0 + g) * kLdh + col + 1] = __float2bfloat16_rn(gelu_f(acc[j][1] + b[col + 1]));
+        out[(r0 + g + 8) * kLdh + col] = __float2bfloat16_rn(gelu_f(acc[j][2] + b[col]));
+        out[(r0 + g + 8) * kLdh + col + 1] = __float2bfloat16_rn(gelu_f(acc[j][3] + b[col + 1]));
+      }
+    } else if (half == 0) {
+      float acc[2][4];
+#pragma unroll
+      for (int j = 0; j < 2; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.0f;
+      warp_gemm<128, 2>(in, kLdh, r0, sS, lds, 0, acc);
+      const float* b = bias + b_offset(l);
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const int col = 8 * j + 2 * t;
+        sY[(r0 + g) * kPad + col] = acc[j][0] + b[col];
+        sY[(r0 + g) * kPad + col + 1] = acc[j][1] + b[col + 1];
+        sY[(r0 + g + 8) * kPad + col] = acc[j][2] + b[col];
+        sY[(r0 + g + 8) * kPad + col + 1] = acc[j][3] + b[col + 1];
+      }
+    }
+    __syncthreads();
+    __nv_bfloat16* tmp = in;
+    in = out;
+    out = tmp;
+  }
+}
+
+// Loads the bf16 weights into shared memory with a padded row stride
+// (K + 8) so that the fragment loads are free of bank conflicts.
+__device__ __forceinline__ void load_weights_smem(__nv_bfloat16* sW, const __nv_bfloat16* W,
+                                                  int* wstride) {
+  for (int l = 0; l < kLayers; ++l) {
+    const int K = dim_in(l), N = dim_out(l);
+    wstride[l] = K + 8;
+    __nv_bfloat16* dst = sW + w_offset(l) + l * 8 * 128;
+    for (int i = threadIdx.x; i < N * (K / 8); i += blockDim.x) {
+      const int n = i / (K / 8), v = i % (K / 8);
+      *reinterpret_cast<uint4*>(dst + n * (K + 8) + v * 8) =
+          *reinterpret_cast<const uint4*>(W + w_offset(l) + n * K + v * 8);
+    }
+  }
+}
+
+// Standardised MLP inputs of one edge; returns false when the edge must use
+// the analytic eigenstructure (input outside the training box, local Froude
+// in [fr_lo, fr_hi], or the two sides on opposite sides of Fr = 1).
+__device__ __forceinline__ bool edge_inputs(const InferParams& P, const float x[kIn],
+                                            float g_acc, float z[kIn]) {
+  bool ok = true;
+#pragma unroll
+  for (int k = 0; k < kIn; ++k) {
+    ok = ok && (x[k] >= P.lo[k]) && (x[k] <= P.hi[k]);
+    z[k] = (x[k] - P.stats[k]) / P.stats[kIn + k];
+  }
+  const float hL = x[0], qL = x[1], hR = x[3], qR = x[4];
+  const float frL = fabsf(qL / hL) * rsqrtf(g_acc * hL);
+  const float frR = fabsf(qR / hR) * rsqrtf(g_acc * hR);
+  const float hM = 0.5f * (hL + hR), qM = 0.5f * (qL + qR);
+  const float frM = fabsf(qM / hM) * rsqrtf(g_acc * hM);
+  const float fr = fmaxf(frM, fmaxf(frL, frR));
+  if (fr >= P.fr_lo && fr <= P.fr_hi) ok = false;
+  if ((frL - 1.0f) * (frR - 1.0f) < 0.0f) ok = false;
+  return ok && isfinite(fr);
+}
+
+// |A|_Psi of every edge 0..n of a float-float state through the MLP, into
+// absA [9][n+1] (float32, de-standardised); edges that fall back are marked
+// with absA[0][e] = NaN. Persistent over 128-edge tiles.
+__global__ void __launch_bounds__(kInferThreads, 1)
+    k_mlp_edges(const InferParams P, const StepParams sp, const StateF32 st, int slot,
+                float* __restrict__ absA, unsigned long long* fallback_count) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __nv_bfloat16* sW = reinterpret_cast<__nv_bfloat16*>(smem);
+  __nv_bfloat16* sH0 = sW + w_offset(kLayers) + kLayers * 8 * 128;
+  __nv_bfloat16* sH1 = sH0 + kInferRows * kLdh;
+  float* sY = reinterpret_cast<float*>(sH1 + kInferRows * kLdh);
+  __shared__ int wstride[kLayers];
+  __shared__ unsigned sFb;
+  if (threadIdx.x < kLayers) wstride[threadIdx.x] = dim_in(threadIdx.x) + 8;
+  load_weights_smem(sW, P.W, wstride);
+  const int64_t n_edges = sp.n + 1;
+  const int64_t n_tiles = (n_edges + kInferRows - 1) / kInferRows;
+  unsigned long long fb_total = 0;
+  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    if (threadIdx.x == 0) sFb = 0;
+    __syncthreads();
+    const int64_t e0 = tile * kInferRows;
+    // inputs: threads 0..127 build one row each
+    if (threadIdx.x < kInferRows) {
+      const int64_t e = e0 + threadIdx.x;
+      float z[kIn] = {0, 0, 0, 0, 0, 0, 0};
+      bool ok = false;
+      if (e < n_edges) {
+        float2 wl[3], wr[3];
+        load_edge<float>(sp, st, e, slot, wl, wr);
+        const float x[kIn] = {wl[0].x, wl[1].x, wl[2].x, wr[0].x, wr[1].x, wr[2].x, P.Ag};
+        ok = edge_inputs(P, x, sp.lf.g, z);
+        if (!ok) atomicAdd(&sFb, 1u);
+      }
+      __nv_bfloat16* row = sH0 + threadIdx.x * kLdh;
+#pragma unroll
+      for (int k = 0; k < kPad; ++k) row[k] = __float2bfloat16_rn(k < kIn ? z[k] : 0.0f);
+      sY[threadIdx.x * kPad + 15] = ok ? 1.0f : 0.0f;  // carried in an unused output column
+    }
+    __syncthreads();
+    // the flag lives in column 15, which the last layer overwrites: keep it aside
+    float okf = 0.0f;
+    if (threadIdx.x < kInferRows) okf = sY[threadIdx.x * kPad + 15];
+    __syncthreads();
+    infer_tile(sW, wstride, P.bias, sH0, sH1, sY);
+    if (threadIdx.x < kInferRows) {
+      const int64_t e = e0 + threadIdx.x;
+      if (e < n_edges) {
+#pragma unroll
+        for (int k = 0; k < kOut; ++k) {
+          float v = sY[threadIdx.x * kPad + k] * P.stats[2 * kIn + kOut + k] + P.stats[2 * kIn + k];
+          if (k == 0 && okf == 0.0f) v = __int_as_float(0x7fc00000);
+          absA[(int64_t)k * n_edges + e] = v;
+        }
+      }
+    }
+    if (threadIdx.x == 0) fb_total += sFb;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && fb_total) atomicAdd(fallback_count, fb_total);
+}
+
+// Plain forward of standardised inputs X [n][16] bf16 through the fused
+// tile routine: Y [n][16] float32 (for parity tests of the fused path).
+__global__ void __launch_bounds__(kInferThreads, 1)
+    k_mlp_forward_fused(const __nv_bfloat16* W, const float* bias, const __nv_bfloat16* X, int64_t n,
+                        float* Y) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __nv_bfloat16* sW = reinterpret_cast<__nv_bfloat16*>(smem);
+  __nv_bfloat16* sH0 = sW + w_offset(kLayers) + kLayers * 8 * 128;
+  __nv_bfloat16* sH1 = sH0 + kInferRows * kLdh;
+  float* sY = reinterpret_cast<float*>(sH1 + kInferRows * kLdh);
+  __shared__ int wstride[kLayers];
+  if (threadIdx.x < kLayers) wstride[threadIdx.x] = dim_in(threadIdx.x) + 8;
+  load_weights_smem(sW, W, wstride);
+  const int64_t n_tiles = (n + kInferRows - 1) / kInferRows;
+  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    __syncthreads();
+    const int64_t r0 = tile * kInferRows;
+    if (threadIdx.x < kInferRows) {
+      const int64_t r = r0 + threadIdx.x;
+      for (int k = 0; k < kPad; ++k)
+        sH0[threadIdx.x * kLdh + k] = (r < n) ? X[r * kPad + k] : __float2bfloat16_rn(0.0f);
+    }
+    __syncthreads();
+    infer_tile(sW, wstride, bias, sH0, sH1, sY);
+    if (threadIdx.x < kInferRows) {
+      const int64_t r = r0 + threadIdx.x;
+      if (r < n)
+        for (int k = 0; k < kPad; ++k) Y[r * kPad + k] = sY[threadIdx.x * kPad + k];
+    }
+  }
+}
+
+// Column minima and maxima of the raw inputs X [n][7].
+__global__ void k_minmax(const float* __restrict__ X, int64_t n, float* out /* [2][7] */) {
+  const int c = blockIdx.x;
+  __shared__ float smin[256], smax[256];
+  float lo = INFINITY, hi = -INFINITY;
+  for (int64_t i = threadIdx.x; i < n; i += 256) {
+    const float v = X[i * kIn + c];
+    lo = fminf(lo, v);
+    hi = fmaxf(hi, v);
+  }
+  smin[threadIdx.x] = lo;
+  smax[threadIdx.x] = hi;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      smin[threadIdx.x] = fminf(smin[threadIdx.x], smin[threadIdx.x + w]);
+      smax[threadIdx.x] = fmaxf(smax[threadIdx.x], smax[threadIdx.x + w]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[c] = smin[0];
+    out[kIn + c] = smax[0];
+  }
+}
+
+}  // namespace adot
+
+using namespace adot;
+
+struct adot_mlp {
+  int device;
+  cudaStream_t stream;
+  bool own_stream;
+  int64_t max_batch;
+  MlpDev d;
+  float* d_ident;  // identity statistics (mean 0, sd 1)
+  // dataset
+  float* X;
+  float* T;
+  int64_t n_data;
+  float box_lo[kIn], box_hi[kIn];
+  bool have_data;
+  // batch buffers
+  __nv_bfloat16* Xb;
+  float* Tb;
+  __nv_bfloat16* Z[4];
+  __nv_bfloat16* H[4];
+  float* Y;
+  __nv_bfloat16* dY;
+  __nv_bfloat16* dZ[4];
+  float* pW[kLayers];
+  float* pB[kLayers];
+  int chunk;
+  float* loss_part;
+  float* loss_hist;
+  int64_t hist_cap;
+  int64_t* idx;
+  float* tmpX;  // [max_batch][7] staging
+  float* tmpT;  // [max_batch][9]
+  cudaGraphExec_t graph;
+  bool graph_ready;
+  int64_t graph_batch;
+  uint64_t graph_seed;
+  double graph_lr;
+  int64_t graph_steps;
+};
+
+namespace {
+
+#define CKM(expr)                              \
+  do {                                         \
+    cudaError_t _e = (expr);                   \
+    if (_e != cudaSuccess) return ADOT_E_CUDA; \
+  } while (0)
+
+template <int K, int N, int EPI>
+cudaError_t layer_attr() {
+  return cudaFuncSetAttribute(k_layer<K, N, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)layer_smem<K, N>());
+}
+
+// Dynamic shared memory limits of every layer kernel (set before any capture).
+cudaError_t set_layer_attributes() {
+  cudaError_t e = layer_attr<16, 128, EPI_GELU>();
+  if (e == cudaSuccess) e = layer_attr<128, 128, EPI_GELU>();
+  if (e == cudaSuccess) e = layer_attr<128, 16, EPI_LINEAR>();
+  if (e == cudaSuccess) e = layer_attr<16, 128, EPI_BWD>();
+  if (e == cudaSuccess) e = layer_attr<128, 128, EPI_BWD>();
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_mlp_edges, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)infer_smem_bytes());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_mlp_forward_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)infer_smem_bytes());
+  return e;
+}
+
+template <int K, int N, int EPI>
+cudaError_t layer(const __nv_bfloat16* A, const __nv_bfloat16* S, const float* bias,
+                  const __nv_bfloat16* aux, void* out0, __nv_bfloat16* out1, int64_t rows,
+                  cudaStream_t s) {
+  constexpr size_t sm = layer_smem<K, N>();
+  const int64_t g = (rows + kTileRows - 1) / kTileRows;
+  k_layer<K, N, EPI><<<(unsigned)g, 256, sm, s>>>(A, S, bias, aux, out0, out1, rows);
+  return cudaGetLastError();
+}
+
+const __nv_bfloat16* Wl(const adot_mlp* m, int l) { return m->d.W + w_offset(l); }
+const __nv_bfloat16* Wtl(const adot_mlp* m, int l) { return m->d.Wt + w_offset(l); }
+const float* bl(const adot_mlp* m, int l) { return m->d.master + kWTotal + b_offset(l); }
+
+cudaError_t forward_batch(adot_mlp* m, int64_t B, cudaStream_t s) {
+  cudaError_t e;
+  if ((e = layer<16, 128, EPI_GELU>(m->Xb, Wl(m, 0), bl(m, 0), nullptr, m->Z[0], m->H[0], B, s))) return e;
+  for (int l = 1; l < 4; ++l)
+    if ((e = layer<128, 128, EPI_GELU>(m->H[l - 1], Wl(m, l), bl(m, l), nullptr, m->Z[l], m->H[l], B, s)))
+      return e;
+  return layer<128, 16, EPI_LINEAR>(m->H[3], Wl(m, 4), bl(m, 4), nullptr, m->Y, nullptr, B, s);
+}
+
+cudaError_t backward_batch(adot_mlp* m, int64_t B, cudaStream_t s) {
+  cudaError_t e;
+  const int lg = (int)((B + 255) / 256);
+  k_loss<<<lg, 256, 0, s>>>(m->Y, m->Tb, B, m->dY, m->loss_part);
+  if ((e = cudaGetLastError())) return e;
+  if ((e = layer<16, 128, EPI_BWD>(m->dY, Wtl(m, 4), nullptr, m->Z[3], m->dZ[3], nullptr, B, s))) return e;
+  for (int l = 3; l >= 1; --l)
+    if ((e = layer<128, 128, EPI_BWD>(m->dZ[l], Wtl(m, l), nullptr, m->Z[l - 1], m->dZ[l - 1], nullptr, B, s)))
+      return e;
+  const int nch = (int)((B + m->chunk - 1) / m->chunk);
+  k_wgrad<128, 16><<<nch, 256, 0, s>>>(m->dY, m->H[3], m->pW[4], m->pB[4], B, m->chunk);
+  for (int l = 3; l >= 1; --l)
+    k_wgrad<128, 128><<<nch, 256, 0, s>>>(m->dZ[l], m->H[l - 1], m->pW[l], m->pB[l], B, m->chunk);
+  k_wgrad<16, 128><<<nch, 256, 0, s>>>(m->dZ[0], m->Xb, m->pW[0], m->pB[0], B, m->chunk);
+  return cudaGetLastError();
+}
+
+AdamArgs adam_args(const adot_mlp* m, int64_t B) {
+  AdamArgs a;
+  const int nch = (int)((B + m->chunk - 1) / m->chunk);
+  for (int l = 0; l < kLayers; ++l) {
+    a.pW[l] = m->pW[l];
+    a.pB[l] = m->pB[l];
+    a.nchunk[l] = nch;
+  }
+  return a;
+}
+
+// packed (oracle) layout <-> padded layout
+void pack_to_padded(const float* packed, std::vector<float>& padded) {
+  padded.assign(kWTotal + kBTotal, 0.0f);
+  int k = 0;
+  for (int l = 0; l < kLayers; ++l) {
+    const int ro = real_out(l), ri = real_in(l), K = dim_in(l);
+    for (int n = 0; n < ro; ++n)
+      for (int i = 0; i < ri; ++i) padded[w_offset(l) + n * K + i] = packed[k++];
+    for (int n = 0; n < ro; ++n) padded[kWTotal + b_offset(l) + n] = packed[k++];
+  }
+}
+
+void padded_to_pack(const float* padded, float* packed) {
+  int k = 0;
+  for (int l = 0; l < kLayers; ++l) {
+    const int ro = real_out(l), ri = real_in(l), K = dim_in(l);
+    for (int n = 0; n < ro; ++n)
+      for (int i = 0; i < ri; ++i) packed[k++] = padded[w_offset(l) + n * K + i];
+    for (int n = 0; n < ro; ++n) packed[k++] = padded[kWTotal + b_offset(l) + n];
+  }
+}
+
+void mlp_free(adot_mlp* m) {
+  if (!m) return;
+  if (m->graph_ready) cudaGraphExecDestroy(m->graph);
+  void* ptrs[] = {m->d.master, m->d.m, m->d.v, m->d.grad, m->d.W, m->d.Wt, m->d.stats, m->d.step,
+                  m->d_ident, m->X, m->T, m->Xb, m->Tb, m->Y, m->dY, m->loss_part, m->loss_hist,
+                  m->idx, m->tmpX, m->tmpT};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  for (int i = 0; i < 4; ++i) {
+    if (m->Z[i]) cudaFree(m->Z[i]);
+    if (m->H[i]) cudaFree(m->H[i]);
+    if (m->dZ[i]) cudaFree(m->dZ[i]);
+  }
+  for (int l = 0; l < kLayers; ++l) {
+    if (m->pW[l]) cudaFree(m->pW[l]);
+    if (m->pB[l]) cudaFree(m->pB[l]);
+  }
+  if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
+  delete m;
+}
+
+adot_status upload_batch(adot_mlp* m, const float* Xs, const float* Ts, int64_t n) {
+  CKM(cudaMemcpyAsync(m->tmpX, Xs, sizeof(float) * kIn * n, cudaMemcpyHostToDevice, m->stream));
+  if (Ts) CKM(cudaMemcpyAsync(m->tmpT, Ts, sizeof(float) * kOut * n, cudaMemcpyHostToDevice, m->stream));
+  std::vector<int64_t> iota(n);
+  for (int64_t i = 0; i < n; ++i) iota[i] = i;
+  CKM(cudaMemcpyAsync(m->idx, iota.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, m->stream));
+  // identity statistics: the caller's inputs and targets are already standardised
+  k_gather<<<(unsigned)((n + 255) / 256), 256, 0, m->stream>>>(m->tmpX, Ts ? m->tmpT : nullptr, n, m->idx, 0,
+                                                               nullptr, n, m->d_ident, m->Xb,
+                                                               Ts ? m->Tb : nullptr);
+  CKM(cudaGetLastError());
+  CKM(cudaStreamSynchronize(m->stream));
+  return ADOT_OK;
+}
+
+}  // namespace
+
+namespace adot {
+// Internal: launches the surrogate over every edge of a float-float state.
+cudaError_t launch_mlp_edges(const adot_mlp* m, const StepParams& sp, StateF32 st, int slot,
+                             float Ag, float fr_lo, float fr_hi, float* absA,
+                             unsigned long long* fb, cudaStream_t s) {
+  InferParams P;
+  P.W = m->d.W;
+  P.bias = m->d.master + kWTotal;
+  P.stats = m->d.stats;
+  for (int k = 0; k < kIn; ++k) {
+    P.lo[k] = m->box_lo[k];
+    P.hi[k] = m->box_hi[k];
+  }
+  P.fr_lo = fr_lo;
+  P.fr_hi = fr_hi;
+  P.Ag = Ag;
+  constexpr size_t sm = infer_smem_bytes();
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device);
+  const int64_t tiles = (sp.n + 1 + kInferRows - 1) / kInferRows;
+  const int grid = (int)imin64(tiles, sms);
+  k_mlp_edges<<<grid, kInferThreads, sm, s>>>(P, sp, st, slot, absA, fb);
+  return cudaGetLastError();
+}
+bool mlp_ready(const adot_mlp* m) { return m && m->have_data; }
+}  // namespace adot
+
+extern "C" {
+
+adot_status adot_mlp_create(int64_t max_batch, void* cuda_stream, adot_mlp** out) {
+  if (!out || max_batch < 1 || max_batch > (1ll << 26)) return ADOT_E_INVALID_ARG;
+  *out = nullptr;
+  adot_mlp* m = new adot_mlp();
+  memset(m, 0, sizeof(adot_mlp));
+  cudaGetDevice(&m->device);
+  m->max_batch = ((max_batch + 63) / 64) * 64;
+  m->chunk = 512;
+  cudaError_t e = cudaSuccess;
+  if (cuda_stream) {
+    m->stream = (cudaStream_t)cuda_stream;
+  } else {
+    e = cudaStreamCreateWithFlags(&m->stream, cudaStreamNonBlocking);
+    m->own_stream = true;
+  }
+  const int64_t B = m->max_batch;
+  const int nch = (int)((B + m->chunk - 1) / m->chunk);
+  auto al = [&](void** p, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) e = cudaMemset(*p, 0, bytes);
+  };
+  const size_t P = kWTotal + kBTotal;
+  al((void**)&m->d.master, sizeof(float) * P);
+  al((void**)&m->d.m, sizeof(float) * P);
+  al((void**)&m->d.v, sizeof(float) * P);
+  al((void**)&m->d.grad, sizeof(float) * P);
+  al((void**)&m->d.W, sizeof(__nv_bfloat16) * kWTotal);
+  al((void**)&m->d.Wt, sizeof(__nv_bfloat16) * kWTotal);
+  al((void**)&m->d.stats, sizeof(float) * 32);
+  al((void**)&m->d.step, sizeof(long long));
+  al((void**)&m->d_ident, sizeof(float) * 32);
+  al((void**)&m->Xb, sizeof(__nv_bfloat16) * kPad * B);
+  al((void**)&m->Tb, sizeof(float) * kOut * B);
+  for (int i = 0; i < 4; ++i) {
+    al((void**)&m->Z[i], sizeof(__nv_bfloat16) * kHid * B);
+    al((void**)&m->H[i], sizeof(__nv_bfloat16) * kHid * B);
+    al((void**)&m->dZ[i], sizeof(__nv_bfloat16) * kHid * B);
+  }
+  al((void**)&m->Y, sizeof(float) * kPad * B);
+  al((void**)&m->dY, sizeof(__nv_bfloat16) * kPad * B);
+  for (int l = 0; l < kLayers; ++l) {
+    al((void**)&m->pW[l], sizeof(float) * (size_t)nch * dim_in(l) * dim_out(l));
+    al((void**)&m->pB[l], sizeof(float) * (size_t)nch * dim_out(l));
+  }
+  al((void**)&m->loss_part, sizeof(float) * ((B + 255) / 256));
+  al((void**)&m->idx, sizeof(int64_t) * B);
+  al((void**)&m->tmpX, sizeof(float) * kIn * B);
+  al((void**)&m->tmpT, sizeof(float) * kOut * B);
+  if (e == cudaSuccess) {
+    float ident[32];
+    for (int i = 0; i < 32; ++i) ident[i] = 0.0f;
+    for (int k = 0; k < kIn; ++k) ident[kIn + k] = 1.0f;
+    for (int k = 0; k < kOut; ++k) ident[2 * kIn + kOut + k] = 1.0f;
+    e = cudaMemcpy(m->d_ident, ident, sizeof(ident), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(m->d.stats, ident, sizeof(ident), cudaMemcpyHostToDevice);
+  }
+  if (e == cudaSuccess) e = set_layer_attributes();
+  if (e != cudaSuccess) {
+    mlp_free(m);
+    return ADOT_E_CUDA;
+  }
+  *out = m;
+  return ADOT_OK;
+}
+
+void adot_mlp_destroy(adot_mlp* m) {
+  if (!m) return;
+  cudaStreamSynchronize(m->stream);
+  mlp_free(m);
+}
+
+adot_status adot_mlp_set_params(adot_mlp* m, const float* packed) {
+  if (!m || !packed) return ADOT_E_INVALID_ARG;
+  std::vector<float> padded;
+  pack_to_padded(packed, padded);
+  const size_t P = kWTotal + kBTotal;
+  CKM(cudaStreamSynchronize(m->stream));
+  CKM(cudaMemcpy(m->d.master, padded.data(), sizeof(float) * P, cudaMemcpyHostToDevice));
+  CKM(cudaMemset(m->d.m, 0, sizeof(float) * P));
+  CKM(cudaMemset(m->d.v, 0, sizeof(float) * P));
+  CKM(cudaMemset(m->d.step, 0, sizeof(long long)));
+  k_refresh_bf16<<<(kWTotal + 255) / 256, 256, 0, m->stream>>>(m->d);
+  CKM(cudaGetLastError());
+  CKM(cudaStreamSynchronize(m->stream));
+  return ADOT_OK;
+}
+
+adot_status adot_mlp_get_params(adot_mlp* m, float* packed) {
+  if (!m || !packed) return ADOT_E_INVALID_ARG;
+  std::vector<float> padded(kWTotal + kBTotal);
+  CKM(cudaStreamSynchronize(m->stream));
+  CKM(cudaMemcpy(padded.data(), m->d.master, sizeof(float) * padded.size(), cudaMemcpyDeviceToHost));
+  padded_to_pack(padded.data(), packed);
+  return ADOT_OK;
+}
+
+adot_status adot_mlp_set_data(adot_mlp* m, const float* X, const float* T, int64_t n, int on_device) {
+  if (!m || !X || !T || n < 2) return ADOT_E_INVALID_ARG;
+  CKM(cudaStreamSynchronize(m->stream));
+  if (m->X) cudaFree(m->X);
+  if (m->T) cudaFree(m->T);
+  m->X = nullptr;
+  m->T = nullptr;
+  m->have_data = false;
+  CKM(cudaMalloc((void**)&m->X, sizeof(float) * kIn * n));
+  CKM(cudaMalloc((void**)&m->T, sizeof(float) * kOut * n));
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  CKM(cudaMemcpy(m->X, X, sizeof(float) * kIn * n, kind));
+  CKM(cudaMemcpy(m->T, T, sizeof(float) * kOut * n, kind));
+  m->n_data = n;
+  k_stats<<<kIn + kOut, 256, 0, m->stream>>>(m->X, m->T, n, m->d.stats);
+  float* mm = nullptr;
+  CKM(cudaMalloc((void**)&mm, sizeof(float) * 2 * kIn));
+  k_minmax<<<kIn, 256, 0, m->stream>>>(m->X, n, mm);
+  float h[2 * kIn];
+  cudaError_t e = cudaMemcpyAsync(h, mm, sizeof(h), cudaMemcpyDeviceToHost, m->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+  cudaFree(mm);
+  if (e != cudaSuccess) return ADOT_E_CUDA;
+  for (int k = 0; k < kIn; ++k) {
+    const float span = h[kIn + k] - h[k];
+    const float margin = 0.05f * (span > 0.0f ? span : fabsf(h[k]) + 1e-6f);
+    m->box_lo[k] = h[k] - margin;
+    m->box_hi[k] = h[kIn + k] + margin;
+  }
+  m->have_data = true;
+  return ADOT_OK;
+}
+
+adot_status adot_mlp_get_stats(adot_mlp* m, float* stats32, float* box14) {
+  if (!m) return ADOT_E_INVALID_ARG;
+  if (stats32) CKM(cudaMemcpy(stats32, m->d.stats, sizeof(float) * 32, cudaMemcpyDeviceToHost));
+  if (box14)
+    for (int k = 0; k < kIn; ++k) {
+      box14[k] = m->box_lo[k];
+      box14[kIn + k] = m->box_hi[k];
+    }
+  return ADOT_OK;
+}
+
+adot_status adot_mlp_forward(adot_mlp* m, const float* Xs, int64_t n, float* Y, int fused) {
+  if (!m || !Xs || !Y || n < 1 || n > m->max_batch) return ADOT_E_INVALID_ARG;
+  adot_status st = upload_batch(m, Xs, nullptr, n);
+  if (st) return st;
+  if (fused) {
+    constexpr size_t sm = infer_smem_bytes();
+    const int64_t tiles = (n + kInferRows - 1) / kInferRows;
+    k_mlp_forward_fused<<<(unsigned)imin64(tiles, 152), kInferThreads, sm, m->stream>>>(
+        m->d.W, m->d.master + kWTotal, m->Xb, n, m->Y);
+    CKM(cudaGetLastError());
+  } else {
+    CKM(forward_batch(m, n, m->stream));
+  }
+  std::vector<float> y((size_t)n * kPad);
+  CKM(cudaMemcpyAsync(y.data(), m->Y, sizeof(float) * kPad * n, cudaMemcpyDeviceToHost, m->stream));
+  CKM(cudaStreamSynchronize(m->stream));
+  for (int64_t i = 0; i < n; ++i)
+    for (int k = 0; k < kOut; ++k) Y[i * kOut + k] = y[i * kPad + k];
+  return ADOT_OK;
+}
+
+adot_status adot_mlp_gradient(adot_mlp* m, const float* Xs, const float* Ts, int64_t n, float* loss_out,
+                              float* grad_packed) {
+  if (!m || !Xs || !Ts || n < 1 || n > m->max_batch) return ADOT_E_INVALID_ARG;
+  adot_status st = upload_batch(m, Xs, Ts, n);
+  if (st) return st;
+  CKM(forward_batch(m, n, m->stream));
+  CKM(backward_batch(m, n, m->stream));
+  k_adam<<<(kWTotal + kBTotal + 255) / 256, 256, 0, m->stream>>>(m->d, adam_args(m, n), 0.0f, 0, 0.9f,
+                                                                 0.999f, 1e-8f, 0);
+  CKM(cudaGetLastError());
+  const int lg = (int)((n + 255) / 256);
+  std::vector<float> part(lg);
+  std::vector<float> padded(kWTotal + kBTotal);
+  CKM(cudaMemcpyAsync(part.data(), m->loss_part, sizeof(float) * lg, cudaMemcpyDeviceToHost, m->stream));
+  CKM(cudaMemcpyAsync(padded.data(), m->d.grad, sizeof(float) * padded.size(), cudaMemcpyDeviceToHost,
+                      m->stream));
+  CKM(cudaStreamSynchronize(m->stream));
+  double ls = 0.0;
+  for (float v : part) ls += v;
+  if (loss_out) *loss_out = (float)(ls / ((double)n * kOut));
+  if (grad_packed) padded_to_pack(padded.data(), grad_packed);
+  return ADOT_OK;
+}
+
+adot_status adot_mlp_train(adot_mlp* m, int64_t steps, int64_t batch, double lr, uint64_t seed,
+                           float* loss_hist) {
+  if (!m || !m->have_data || steps < 0 || batch < 64 || batch > m->max_batch || !(lr > 0.0))
+    return ADOT_E_INVALID_ARG;
+  batch = (batch / 64) * 64;
+  long long step0 = 0;
+  CKM(cudaStreamSynchronize(m->stream));
+  CKM(cudaMemcpy(&step0, m->d.step, sizeof(long long), cudaMemcpyDeviceToHost));
+  if (m->hist_cap < step0 + steps) {
+    if (m->graph_ready) cudaGraphExecDestroy(m->graph);
+    m->graph_ready = false;
+    if (m->loss_hist) cudaFree(m->loss_hist);
+    m->loss_hist = nullptr;
+    m->hist_cap = 0;
+    const int64_t cap = step0 + steps > 0 ? step0 + steps : 1;
+    CKM(cudaMalloc((void**)&m->loss_hist, sizeof(float) * cap));
+    m->hist_cap = cap;
+  }
+  const bool rebuild = !m->graph_ready || m->graph_batch != batch || m->graph_seed != seed ||
+                       m->graph_lr != lr || m->graph_steps != step0 + steps;
+  if (rebuild) {
+    if (m->graph_ready) cudaGraphExecDestroy(m->graph);
+    m->graph_ready = false;
+    cudaStream_t cs;
+    CKM(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      k_gather<<<(unsigned)((batch + 255) / 256), 256, 0, cs>>>(m->X, m->T, m->n_data, nullptr, seed,
+                                                                m->d.step, batch, m->d.stats, m->Xb, m->Tb);
+      e = cudaGetLastError();
+      if (e == cudaSuccess) e = forward_batch(m, batch, cs);
+      if (e == cudaSuccess) e = backward_batch(m, batch, cs);
+      if (e == cudaSuccess) {
+        k_adam<<<(kWTotal + kBTotal + 255) / 256, 256, 0, cs>>>(m->d, adam_args(m, batch), (float)lr,
+                                                                step0 + steps, 0.9f, 0.999f, 1e-8f, 1);
+        k_loss_sum<<<1, 32, 0, cs>>>(m->loss_part, (int)((batch + 255) / 256), batch, m->d.step,
+                                     m->loss_hist, m->hist_cap);
+        k_step_incr<<<1, 32, 0, cs>>>(m->d.step);
+        e = cudaGetLastError();
+      }
+      cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+      if (e == cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&m->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) return ADOT_E_CUDA;
+    m->graph_ready = true;
+    m->graph_batch = batch;
+    m->graph_seed = seed;
+    m->graph_lr = lr;
+    m->graph_steps = step0 + steps;
+  }
+  for (int64_t k = 0; k < steps; ++k) CKM(cudaGraphLaunch(m->graph, m->stream));
+  CKM(cudaStreamSynchronize(m->stream));
+  if (loss_hist && steps > 0) {
+    std::vector<float> h(m->hist_cap);
+    CKM(cudaMemcpy(h.data(), m->loss_hist, sizeof(float) * m->hist_cap, cudaMemcpyDeviceToHost));
+    for (int64_t k = 0; k < steps; ++k) loss_hist[k] = (step0 + k < m->hist_cap) ? h[step0 + k] : NAN;
+  }
+  return ADOT_OK;
+}
+
+}  // extern "C"

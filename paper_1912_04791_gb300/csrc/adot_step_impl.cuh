@@ -172,6 +172,37 @@ __device__ __forceinline__ void edge_fluct(const StepParams& p, const typename P
   }
 }
 
+// D-/+ of one float32 edge whose |A|_Psi (row-major 3x3) comes from the
+// surrogate: |A|_Psi dW replaces sum_k w_k |A_k| dW, and sum_k w_k A_k dW keeps
+// its analytic form (Eq. DOTjumpN, segment path).
+template <int LAW>
+__device__ __forceinline__ void edge_fluct_sur(const StepParams& p, const float2 wl[3],
+                                               const float2 wr[3], const float M[9], float dm[3],
+                                               float dp[3]) {
+  const float dh = ff_diff(wr[0], wl[0]), dq = ff_diff(wr[1], wl[1]), dz = ff_diff(wr[2], wl[2]);
+  const float h0 = wl[0].x, q0 = wl[1].x;
+  float ya[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float sk = (k == 0) ? (float)GL3_S0 : ((k == 1) ? 0.5f : (float)GL3_S2);
+    const float w = (k == 1) ? (float)GL3_W1 : (float)GL3_W0;
+    const float h = h0 + sk * dh, q = q0 + sk * dq;
+    const float inv_h = __fdividef(1.0f, h);
+    const float u = q * inv_h, c2 = p.lf.g * h;
+    float a, b;
+    sediment_derivs<float, LAW>(p.lf, h, q, inv_h, u, a, b);
+    ya[0] += w * dq;
+    ya[1] += w * ((c2 - u * u) * dh + 2.0f * u * dq + c2 * dz);
+    ya[2] += w * (a * dh + b * dq);
+  }
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const float x = M[3 * r] * dh + M[3 * r + 1] * dq + M[3 * r + 2] * dz;
+    dm[r] = 0.5f * (ya[r] - x);
+    dp[r] = 0.5f * (ya[r] + x);
+  }
+}
+
 // Resident blocks per SM requested from the register allocator: CAP registers
 // per thread out of the SM's 65536, or no request (CAP = 0).
 template <int B, int CAP>
@@ -179,7 +210,7 @@ struct MinBlocks {
   static constexpr int value = CAP ? 65536 / (B * CAP) : 1;
 };
 
-template <typename R, int LAW, int B, int CAP>
+template <typename R, int LAW, int B, int CAP, bool SUR = false>
 __global__ void __launch_bounds__(B, MinBlocks<B, CAP>::value) k_step(const StepParams p, const typename Prec<R>::State in,
                                             const typename Prec<R>::State out, const int slot) {
   using S = typename Prec<R>::S;
@@ -222,7 +253,17 @@ __global__ void __launch_bounds__(B, MinBlocks<B, CAP>::value) k_step(const Step
   if (e <= n) {
     S wr[3];
     load_edge<R>(p, in, e, slot, wl, wr);
-    edge_fluct<R, LAW>(p, wl, wr, dm, dp, flags);
+    if constexpr (SUR) {
+      float M[9];
+#pragma unroll
+      for (int r = 0; r < 9; ++r) M[r] = p.absA[(int64_t)r * (n + 1) + e];
+      if (isnan(M[0]))
+        edge_fluct<R, LAW>(p, wl, wr, dm, dp, flags);
+      else
+        edge_fluct_sur<LAW>(p, wl, wr, M, dm, dp);
+    } else {
+      edge_fluct<R, LAW>(p, wl, wr, dm, dp, flags);
+    }
   }
   sDp[0][tid] = dp[0];
   sDp[1][tid] = dp[1];

@@ -1,0 +1,167 @@
+"""The |A|_Psi surrogate on the GPU: tensor-core forward and backward kernels
+against the FP64 reference MLP (oracle/mlp.py), training, harvested labels
+against the oracle's |A|_Psi, and the surrogate time step.
+
+Tolerances: the GPU holds weights, activations and output gradients in
+bfloat16 and accumulates in float32. Against the reference that rounds the
+same operands to bfloat16 (everything else float64), outputs agree to 1e-2 of
+their scale at worst (a float32/float64 difference can flip one bfloat16
+rounding) and 1e-4 typically; gradients to a cosine above 0.999 and a relative
+norm error below 2e-2."""
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import mlp as M
+from paper_1912_04791_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _theta(seed, scale=1.0):
+    rng = np.random.default_rng(seed)
+    parts = []
+    for o, i in M.layer_shapes():
+        parts.append(rng.standard_normal(o * i) * scale * np.sqrt(2.0 / i))
+        parts.append(rng.standard_normal(o) * 0.1)
+    return np.concatenate(parts).astype(np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("n", [1, 63, 64, 1000, 4099])
+def test_forward_matches_reference(gpu, n):
+    theta = _theta(1)
+    rng = np.random.default_rng(n)
+    X = rng.standard_normal((n, 7)).astype(np.float32)
+    ref, _ = M.forward(theta, X.astype(np.float64), bf16=True)
+    with gpu.Mlp(8192) as net:
+        net.set_params(theta)
+        y = net.forward(X, fused=False)
+        yf = net.forward(X, fused=True)
+    sc = np.abs(ref).max()
+    err = np.abs(y - ref)
+    assert err.max() <= 1e-2 * sc and np.median(err) <= 1e-4 * sc, (err.max(), np.median(err))
+    assert np.abs(yf - y).max() <= 1e-5 * sc
+
+
+def test_gradient_matches_reference(gpu):
+    theta = _theta(2)
+    rng = np.random.default_rng(3)
+    n = 2048
+    X = rng.standard_normal((n, 7)).astype(np.float32)
+    T = rng.standard_normal((n, 9)).astype(np.float32)
+    Y, cache = M.forward(theta, X.astype(np.float64), bf16=True)
+    loss_ref, dY = M.mse(Y, T.astype(np.float64))
+    g_ref = M.backward(theta, cache, dY, bf16=True)
+    with gpu.Mlp(n) as net:
+        net.set_params(theta)
+        loss, g = net.gradient(X, T)
+    assert loss == pytest.approx(loss_ref, rel=1e-3)
+    cos = float(g @ g_ref / (np.linalg.norm(g) * np.linalg.norm(g_ref)))
+    rel = float(np.linalg.norm(g - g_ref) / np.linalg.norm(g_ref))
+    assert cos > 0.999 and rel < 2e-2, (cos, rel)
+    # and against the exact float64 gradient (no bfloat16 anywhere)
+    Y64, c64 = M.forward(theta, X.astype(np.float64))
+    g64 = M.backward(theta, c64, M.mse(Y64, T.astype(np.float64))[1])
+    assert float(g @ g64 / (np.linalg.norm(g) * np.linalg.norm(g64))) > 0.99
+
+
+def test_params_roundtrip_and_padding(gpu):
+    theta = _theta(4).astype(np.float32)
+    with gpu.Mlp(128) as net:
+        net.set_params(theta)
+        assert np.array_equal(net.get_params(), theta)
+
+
+def _edge_dataset(n, seed):
+    WL, WR = W.random_edges(n, seed, h_range=(0.5, 2.0), fr_range=(-0.6, 0.6), rel_jump=0.05,
+                            dz_scale=0.02)
+    rng = np.random.default_rng(seed + 1)
+    Ag = rng.uniform(0.001, 0.02, n)
+    T = np.stack([O.abs_psi(O.grass(a, xi=W.XI_P04), WL[:, k:k + 1], WR[:, k:k + 1])[0]
+                  for k, a in enumerate(Ag)])
+    X = np.concatenate([WL.T, WR.T, Ag[:, None]], axis=1)
+    return X.astype(np.float32), T.astype(np.float32)
+
+
+def test_training_reduces_loss(gpu):
+    X, T = _edge_dataset(3000, 5)
+    with gpu.Mlp(1024) as net:
+        net.set_params(_theta(6, 0.5))
+        net.set_data(X, T)
+        st, box = net.stats()
+        assert np.allclose(st[:7], X.mean(0), rtol=1e-4, atol=1e-5)
+        assert np.allclose(st[7:14], X.std(0), rtol=1e-3)
+        h = net.train(400, 1024, lr=2e-3, seed=7)
+    assert np.isfinite(h).all()
+    assert h[-20:].mean() < 0.1 * h[:5].mean(), (h[:5], h[-20:])
+
+
+def test_harvest_labels_match_oracle(gpu):
+    P = W.smooth_periodic(5000)
+    for prec in (0, 1):
+        with gpu.Solver(gpu.config_for(P, prec)) as s:
+            s.set_state(P.h, P.q, P.z)
+            s.step(20)
+            X, T = gpu.adot_harvest(s.ctx, 3000, seed=11)
+        WL = X[:, 0:3].T.astype(np.float64)
+        WR = X[:, 3:6].T.astype(np.float64)
+        assert (X[:, 6] == np.float32(P.Ag)).all()
+        ref = O.abs_psi(O.grass(P.Ag, xi=P.xi), WL, WR)
+        sc = np.abs(ref).max(axis=1, keepdims=True)
+        assert (np.abs(T - ref) <= 1e-5 * sc).all()
+
+
+def test_surrogate_all_fallback_equals_analytic_path(gpu):
+    """With the fallback band covering every Froude number each edge takes the
+    analytic eigenstructure: the surrogate step equals the plain float32 step."""
+    P = W.smooth_periodic(3000)
+    X, T = _edge_dataset(500, 8)
+    with gpu.Mlp(512) as net:
+        net.set_params(_theta(9))
+        net.set_data(X, T)
+        with gpu.Solver(gpu.config_for(P, gpu.FP32, block_threads=256, reg_cap=64)) as s:
+            s.set_state(P.h, P.q, P.z)
+            gpu.adot_set_surrogate(s.ctx, net, 0.0, 100.0)
+            s.step(30)
+            a = s.get_state()
+            edges, fb = gpu.adot_surrogate_stats(s.ctx)
+        assert edges == fb == 30 * 3001
+    with gpu.Solver(gpu.config_for(P, gpu.FP32, block_threads=256, reg_cap=64)) as s:
+        s.set_state(P.h, P.q, P.z)
+        s.step(30)
+        b = s.get_state()
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+
+
+def test_trained_surrogate_step(gpu):
+    """A network trained on edges harvested from the smooth periodic problem
+    drives the same problem: the state stays finite, few edges fall back, and
+    the increment over 50 steps stays within 5e-2 (L1, relative) of the
+    oracle's; the analytic path's error is reported next to it."""
+    P = W.smooth_periodic(4096)
+    with gpu.Solver(gpu.config_for(P, gpu.FP32)) as s:
+        s.set_state(P.h, P.q, P.z)
+        Xs, Ts = [], []
+        for k in range(6):
+            X, T = gpu.adot_harvest(s.ctx, 20000, seed=100 + k)
+            Xs.append(X), Ts.append(T)
+            s.step(40)
+    X, T = np.concatenate(Xs), np.concatenate(Ts)
+    cfg = O.make_cfg(P.n, P.x_min, P.x_max, P.cfl, O.grass(P.Ag, xi=P.xi), P.bc_left, P.bc_right)
+    ho, qo, zo, *_ = O.run(cfg, P.h, P.q, P.z, max_steps=50)
+    with gpu.Mlp(8192) as net:
+        net.set_params(_theta(10, 0.5))
+        net.set_data(X, T)
+        h = net.train(1500, 8192, lr=2e-3, seed=3)
+        assert h[-50:].mean() < 1e-2
+        with gpu.Solver(gpu.config_for(P, gpu.FP32)) as s:
+            s.set_state(P.h, P.q, P.z)
+            gpu.adot_set_surrogate(s.ctx, net, 0.8, 1.2)
+            s.step(50)
+            hs, qs, zs = s.get_state()
+            edges, fb = gpu.adot_surrogate_stats(s.ctx)
+    assert np.isfinite(hs).all() and edges == 50 * 4097
+    assert fb / edges < 0.05
+    for a, b, a0 in ((hs, ho, P.h), (qs, qo, P.q), (zs, zo, P.z)):
+        assert np.abs((a - a0) - (b - a0)).sum() <= 5e-2 * np.abs(b - a0).sum()
