@@ -63,6 +63,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ensemble-t-end", type=float, default=0.02,
                     help="t_end of the 4096-channel ensemble measurement (0 = skip)")
+    ap.add_argument("--sur-steps", type=int, default=20000,
+                    help="training steps of the |A|_Psi surrogate at batch 65536 (0 = skip the leg)")
+    ap.add_argument("--sur-samples", type=int, default=50_000_000,
+                    help="edge samples harvested from the smooth, bump and ensemble workloads")
     ap.add_argument("--accuracy-steps", type=int, default=96,
                     help="steps of the FP32-vs-FP64 increment check (0 = skip)")
     return ap.parse_args()
@@ -146,6 +150,86 @@ def oracle_throughput(n: int, steps: int, threads: int | None = None):
     O.run(cfg, P.h, P.q, P.z, max_steps=steps)
     dt = time.perf_counter() - t0
     return n * steps / dt, dt, O.num_threads()
+
+
+def surrogate_leg(args, adot, W, P, n, stream, dev, local, time_steps, ref64):
+    """Harvest edges (float64 labels) from the smooth periodic, Gaussian-bump and
+    ensemble workloads, train the MLP at batch 65536, then run the benchmark
+    workload with |A|_Psi from the network (analytic fallback near Fr = 1)."""
+    import torch
+    n_h = int(args.sur_samples)
+    X = torch.empty((n_h, 7), dtype=torch.float32, device=dev)
+    T = torch.empty((n_h, 9), dtype=torch.float32, device=dev)
+    k = 0
+    seed = 1000
+
+    def harvest(solver, m, steps_between, parts):
+        nonlocal k, seed
+        for _ in range(parts):
+            take = min(m // parts, n_h - k)
+            if take <= 0:
+                return
+            adot.adot_harvest(solver.ctx, take, seed, X[k:k + take], T[k:k + take])
+            k += take
+            seed += 1
+            solver.step(steps_between)
+
+    t0 = time.perf_counter()
+    P2 = W.smooth_periodic(1_000_000)
+    with adot.Solver(adot.config_for(P2, adot.FP32, device=local), stream=stream) as s2:
+        s2.set_state(P2.h, P2.q, P2.z)
+        harvest(s2, int(0.4 * n_h), 3000, 4)
+    P3 = W.gaussian_bump(100_000, Ag=0.001)
+    with adot.Solver(adot.config_for(P3, adot.FP32, device=local), stream=stream) as s3:
+        s3.set_state(P3.h, P3.q, P3.z)
+        harvest(s3, int(0.2 * n_h), 3000, 4)
+    E = W.riemann_ensemble(64, seed=77, n_min=1000, n_max=100000)
+    per_c = (n_h - k) // len(E.n_cells) + 1
+    for c in range(len(E.n_cells)):
+        h, q, z = E.channel(c)
+        cfg = adot.make_config(int(E.n_cells[c]), 0.0, float(E.length[c]), E.cfl, float(E.Ag[c]), E.xi,
+                               precision=adot.FP32, device=local)
+        with adot.Solver(cfg, stream=stream) as sc:
+            sc.set_state(h.copy(), q.copy(), z.copy())
+            sc.step(int(E.n_cells[c]) // 20)
+            harvest(sc, per_c, 0, 1)
+    harvest_s = time.perf_counter() - t0
+    with adot.Mlp(65536, stream=stream) as net:
+        net.set_params(W.mlp_init())
+        net.set_data(X[:k], T[:k])
+        torch.cuda.synchronize(dev)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        hist = net.train(args.sur_steps, 65536, lr=1e-3, seed=4242)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        train_ms = a.elapsed_time(b)
+        del X, T
+        out = {"samples": k, "harvest_s": harvest_s, "train_steps": args.sur_steps, "batch": 65536,
+               "train_ms_per_step": train_ms / max(args.sur_steps, 1),
+               "train_flops_per_step": 3 * 2 * 65536 * 51200,
+               "loss_first": float(hist[:10].mean()), "loss_last": float(hist[-10:].mean())}
+        out["train_tflops"] = out["train_flops_per_step"] / (out["train_ms_per_step"] * 1e-3) / 1e12
+        with adot.Solver(adot.config_for(P, adot.FP32, device=local), stream=stream) as ss:
+            ss.set_state(P.h, P.q, P.z)
+            adot.adot_set_surrogate(ss.ctx, net, 0.8, 1.2)
+            K = ref64[0] if ref64 else 96
+            ms_k = time_steps(ss, K)
+            got = ss.get_state()
+            edges, fb = adot.adot_surrogate_stats(ss.ctx)
+            ss.set_state(P.h, P.q, P.z)
+            adot.adot_step(ss.ctx, 6)
+            ms_t = time_steps(ss, 480)
+        out.update({"cell_updates_per_s": n * 480 / (ms_t * 1e-3),
+                    "infer_flops_per_edge": 2 * 51200,
+                    "fallback_fraction": fb / max(edges, 1)})
+        if ref64:
+            for name, a_, b_, a0 in zip("hqz", got, ref64[1], (P.h, P.q, P.z)):
+                out[f"l1_rel_increment_{name}"] = float(np.abs((a_ - a0) - (b_ - a0)).sum()
+                                                        / np.abs(b_ - a0).sum())
+                out[f"l1_rel_state_{name}"] = float(np.abs(a_ - b_).sum() / np.abs(b_).sum())
+        return out
 
 
 def run_reference(args, rank, ws):
@@ -288,12 +372,14 @@ def main():
 
     # accuracy: FP32 increment vs the GPU FP64 path over the same steps
     accuracy = None
+    ref64 = None
     if args.accuracy_steps > 0 and rank == 0:
         K = args.accuracy_steps
         with adot.Solver(adot.config_for(P, adot.FP64, device=local), stream=stream) as s64:
             s64.set_state(P.h, P.q, P.z)
             ms64 = time_steps(s64, K)
             ref = s64.get_state()
+            ref64 = (K, ref)
         solver.set_state(P.h, P.q, P.z)
         solver.step(K)
         got = solver.get_state()
@@ -328,6 +414,11 @@ def main():
                     "tile_threads": blk, "tiles": n_tiles, "grid": grid,
                     "all_at_t_end": bool((t_c == args.ensemble_t_end).all())}
 
+    # learned |A|_Psi surrogate: harvest, train, then drive the benchmark workload
+    surrogate = None
+    if args.sur_steps > 0 and rank == 0:
+        surrogate = surrogate_leg(args, adot, W, P, n, stream, dev, local, time_steps, ref64)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         rate, sec, thr = oracle_throughput(n, args.cpu_steps)
@@ -358,7 +449,7 @@ def main():
                          "hbm_peak_gbs": measured_peaks().get("hbm_gbs", 6800.0)},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps, "clocks": clocks,
             "accuracy": accuracy, "sim_time_after_timed_steps": t_sim, "variants": variants,
-            "ensemble": ensemble,
+            "ensemble": ensemble, "surrogate": surrogate,
         }
         print(json.dumps(line), flush=True)
     if dist:

@@ -383,6 +383,13 @@ class Mlp:
         return t
 
     def set_data(self, X, T):
+        """Training set from host arrays or float32 CUDA tensors X [n, 7], T [n, 9]."""
+        if not isinstance(X, np.ndarray):
+            n = X.shape[0]
+            assert X.shape == (n, 7) and T.shape == (n, 9) and X.is_cuda and T.is_cuda
+            _check(lib().adot_mlp_set_data(self.ptr, X.data_ptr(), T.data_ptr(), n, 1),
+                   "adot_mlp_set_data")
+            return
         X = _f32(X)
         T = _f32(T)
         n = X.shape[0]
@@ -446,11 +453,17 @@ def adot_surrogate_stats(ctx: int):
     return e.value, f.value
 
 
-def adot_harvest(ctx: int, n: int, seed: int = 1):
-    """n edge samples of the context's state: (X [n, 7] raw inputs, T [n, 9] labels)."""
-    X = np.empty((n, 7), dtype=np.float32)
-    T = np.empty((n, 9), dtype=np.float32)
-    _check(lib().adot_harvest(ctx, n, seed, X.ctypes.data, T.ctypes.data, 0), "adot_harvest")
+def adot_harvest(ctx: int, n: int, seed: int = 1, X=None, T=None):
+    """n edge samples of the context's state: (X [n, 7] raw inputs, T [n, 9]
+    labels), into new host arrays or the given float32 CUDA tensors."""
+    if X is None:
+        X = np.empty((n, 7), dtype=np.float32)
+        T = np.empty((n, 9), dtype=np.float32)
+        _check(lib().adot_harvest(ctx, n, seed, X.ctypes.data, T.ctypes.data, 0), "adot_harvest")
+        return X, T
+    if X.shape != (n, 7) or T.shape != (n, 9) or not (X.is_cuda and T.is_cuda):
+        raise ValueError("X, T must be CUDA tensors of shapes (n, 7) and (n, 9)")
+    _check(lib().adot_harvest(ctx, n, seed, X.data_ptr(), T.data_ptr(), 1), "adot_harvest")
     return X, T
 
 

@@ -180,3 +180,14 @@ def riemann_ensemble(n_channels: int = 4096, seed: int = 20191210, n_min: int = 
         zs.append(z)
     return Ensemble(n, np.full(n_channels, length), Ag, np.concatenate(hs), np.concatenate(qs),
                     np.concatenate(zs))
+
+
+def mlp_init(seed: int = 2019, sizes=(7, 128, 128, 128, 128, 9)) -> np.ndarray:
+    """Initial surrogate parameters, packed layer by layer (W_l [out][in]
+    row-major, then b_l): He-normal weights, zero biases."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for i, o in zip(sizes[:-1], sizes[1:]):
+        parts.append(rng.standard_normal(o * i) * np.sqrt(2.0 / i))
+        parts.append(np.zeros(o))
+    return np.concatenate(parts).astype(np.float32)
