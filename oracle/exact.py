@@ -5,6 +5,11 @@
   and z constant). Standard textbook construction: two nonlinear waves, each a
   shock (Rankine-Hugoniot) or a rarefaction (Riemann invariants); the star depth
   solves f_L(h*) + f_R(h*) + u_R - u_L = 0 (Newton), no dry bed.
+* ``MovableBedRiemann``: exact self-similar solution of the movable-bed Riemann
+  problem with the Grass law, built from the PDE (Eq. SV-Ex): rarefactions
+  along integral curves of the eigenvectors (LAPACK), shocks from the
+  generalised Rankine-Hugoniot conditions of the segment path (Eq. path) with
+  the Lax entropy condition. The paper cites this solution but does not give it.
 * ``berthon``: the smooth steady-flow-plus-linear-erosion solution of Test 2
   (Sec. 4.2, Eq. berthon and the initial/boundary data that follow it). The
   paper's form has z_t = -alpha, which solves Eq. SV-Ex3 with xi = 1; for
@@ -131,3 +136,191 @@ def berthon_boundary(q0, L=7.0, alpha=0.005, beta=0.005, Ag=0.005, C=1.0, g=9.81
     h0, _, z0 = berthon(np.array([0.0]), 0.0, q0, alpha, beta, Ag, C, g, xi)
     hL, _, _ = berthon(np.array([L]), 0.0, q0, alpha, beta, Ag, C, g, xi)
     return q0, float(z0[0]), xi * alpha, float(hL[0])
+
+
+# ---------------------------------------------------------------------------
+# Exact solution of the movable-bed Riemann problem (segment path).
+# ---------------------------------------------------------------------------
+# The solution of W_t + A(W) W_x = 0 (Eq. quasiLinNC with S = 0) for piecewise
+# constant data is self-similar: three waves, one per characteristic family,
+# separate constant states W_L, W1, W2, W_R. A wave of family i is either a
+# rarefaction, along the integral curve dW/dh = r_i(W) (the eigenvector with
+# unit h-entry, from LAPACK here) across which lambda_i increases left to right,
+# or a shock moving at sigma with the generalised Rankine-Hugoniot conditions
+# of the segment path (Eq. path), which hold exactly for this system:
+#     sigma dh = dq,
+#     sigma dq = d(q^2/h + g h^2/2) + g (h_l + h_r)/2 dz,
+#     sigma dz = xi d(q_s),
+# and the Lax condition lambda_i(W_r) < sigma < lambda_i(W_l). Which branch a
+# given change of h takes follows from the sign of d(lambda_i)/dh along r_i.
+
+def _flux_matrix(h, q, g, xi, Ag):
+    u = q / h
+    c2 = g * h
+    return np.array([[0.0, 1.0, 0.0],
+                     [c2 - u * u, 2.0 * u, c2],
+                     [-3.0 * xi * Ag * u ** 3 / h, 3.0 * xi * Ag * u * u / h, 0.0]])
+
+
+def _eig(h, q, g, xi, Ag):
+    w, V = np.linalg.eig(_flux_matrix(h, q, g, xi, Ag))
+    o = np.argsort(w.real)
+    w, V = w.real[o], V.real[:, o]
+    return w, V / V[0]  # unit h-entry
+
+
+def _lam(W, i, g, xi, Ag):
+    return _eig(W[0], W[1], g, xi, Ag)[0][i]
+
+
+def _grad_lam_dot_r(W, i, g, xi, Ag):
+    """d lambda_i / dh along the integral curve of r_i (central difference)."""
+    _, V = _eig(W[0], W[1], g, xi, Ag)
+    r = V[:, i]
+    e = 1e-6 * W[0]
+    return (_lam(W + e * r, i, g, xi, Ag) - _lam(W - e * r, i, g, xi, Ag)) / (2 * e)
+
+
+def _integral_curve(W0, i, h1, g, xi, Ag, rtol=1e-12):
+    from scipy.integrate import solve_ivp
+    if h1 == W0[0]:
+        return np.array(W0, dtype=float)
+
+    def rhs(h, y):
+        W = np.array([h, y[0], y[1]])
+        r = _eig(W[0], W[1], g, xi, Ag)[1][:, i]
+        # continue the eigenvector with a consistent sign (unit h-entry makes it unique)
+        return [r[1], r[2]]
+
+    sol = solve_ivp(rhs, (W0[0], h1), [W0[1], W0[2]], method="DOP853", rtol=rtol, atol=1e-14)
+    return np.array([h1, sol.y[0, -1], sol.y[1, -1]])
+
+
+def _rh_residual(Wl, Wr, sigma, g, xi, Ag):
+    hl, ql, zl = Wl
+    hr, qr, zr = Wr
+    F = lambda h, q: q * q / h + 0.5 * g * h * h  # noqa: E731
+    qs = lambda h, q: Ag * (q / h) ** 3  # noqa: E731
+    return np.array([sigma * (hr - hl) - (qr - ql),
+                     sigma * (qr - ql) - (F(hr, qr) - F(hl, ql)) - g * 0.5 * (hl + hr) * (zr - zl),
+                     sigma * (zr - zl) - xi * (qs(hr, qr) - qs(hl, ql))])
+
+
+def _shock(W0, i, h1, g, xi, Ag, left_known=True):
+    """State across a family-i shock with depth h1 on the other side, and its speed."""
+    from scipy.optimize import fsolve
+    lam, V = _eig(W0[0], W0[1], g, xi, Ag)
+    guess_W = W0 + (h1 - W0[0]) * V[:, i]
+    x0 = [guess_W[1], guess_W[2], lam[i]]
+
+    def F(x):
+        W1 = np.array([h1, x[0], x[1]])
+        Wl, Wr = (W0, W1) if left_known else (W1, W0)
+        return _rh_residual(Wl, Wr, x[2], g, xi, Ag)
+
+    x, info, ier, msg = fsolve(F, x0, xtol=1e-14, full_output=True)
+    return np.array([h1, x[0], x[1]]), x[2]
+
+
+class MovableBedRiemann:
+    """Exact solution for left/right states WL, WR = (h, q, z) of the dSVE system
+    with the Grass law q_s = A_g u^3 (Eq. SV-Ex, Eq. Grass), frictionless."""
+
+    def __init__(self, WL, WR, Ag, xi=1.0, g=9.81):
+        from scipy.optimize import fsolve
+        self.WL, self.WR = np.array(WL, float), np.array(WR, float)
+        self.Ag, self.xi, self.g = Ag, xi, g
+
+        def waves(p):
+            W = self.WL
+            out = []
+            for i, h1 in ((0, p[0]), (1, p[1])):
+                out.append(self._wave(W, i, h1))
+                W = out[-1][0]
+            out.append(self._wave(W, 2, self.WR[0]))
+            return out
+
+        def resid(p):
+            W3 = waves(p)[-1][0]
+            return [(W3[1] - self.WR[1]) / (abs(self.WR[1]) + 1.0),
+                    (W3[2] - self.WR[2]) / (abs(self.WR[2]) + 1.0)]
+
+        # initial guess: SWE star depth on the water surface jump
+        hs, _ = swe_star(self.WL[0], self.WL[1] / self.WL[0], self.WR[0] + self.WR[2] - self.WL[2],
+                         self.WR[1] / self.WR[0], g)
+        p0 = [hs, max(hs - (self.WR[2] - self.WL[2]), 0.05)]
+        p, info, ier, msg = fsolve(resid, p0, xtol=1e-13, full_output=True)
+        self.converged = ier == 1 and np.abs(resid(p)).max() < 1e-10
+        self.params = p
+        self.waves = waves(p)
+        self.states = [self.WL] + [w[0] for w in self.waves]
+
+    def _wave(self, W0, i, h1):
+        """(W1, kind, speeds) for family i from W0 (left) to depth h1 (right)."""
+        G = _grad_lam_dot_r(W0, i, self.g, self.xi, self.Ag)
+        rare = (h1 - W0[0]) * G > 0
+        if rare or abs(G) < 1e-12:
+            W1 = _integral_curve(W0, i, h1, self.g, self.xi, self.Ag)
+            return W1, "rarefaction", (_lam(W0, i, self.g, self.xi, self.Ag),
+                                       _lam(W1, i, self.g, self.xi, self.Ag))
+        W1, sigma = _shock(W0, i, h1, self.g, self.xi, self.Ag)
+        return W1, "shock", (sigma, sigma)
+
+    def rh_residuals(self):
+        """Rankine-Hugoniot residuals of the shocks (scaled), for checking."""
+        out = []
+        W = self.WL
+        for W1, kind, (s0, s1) in self.waves:
+            if kind == "shock":
+                out.append(np.abs(_rh_residual(W, W1, s0, self.g, self.xi, self.Ag)).max())
+            W = W1
+        return out
+
+    def lax_ok(self):
+        W = self.WL
+        for i, (W1, kind, (s0, s1)) in enumerate(self.waves):
+            if kind == "shock":
+                if not (_lam(W1, i, self.g, self.xi, self.Ag) < s0 < _lam(W, i, self.g, self.xi, self.Ag)):
+                    return False
+            W = W1
+        return True
+
+    def sample(self, x, t, x0=0.0):
+        """(h, q, z) at positions x and time t > 0."""
+        xs = (np.asarray(x, float) - x0) / t
+        out = np.empty((3,) + xs.shape)
+        for idx, S in np.ndenumerate(xs):
+            W = self.WL
+            val = None
+            for i, (W1, kind, (s0, s1)) in enumerate(self.waves):
+                if S < s0:
+                    val = W
+                    break
+                if kind == "rarefaction" and S < s1:
+                    val = self._fan_state(W, i, S)
+                    break
+                W = W1
+            if val is None:
+                val = self.WR
+            out[(slice(None),) + idx] = val
+        return out[0], out[1], out[2]
+
+    def _fan_state(self, W0, i, S):
+        """State inside the family-i rarefaction where lambda_i = S (one dense
+        integration of the integral curve per wave, then a root solve on it)."""
+        from scipy.integrate import solve_ivp
+        from scipy.optimize import brentq
+        if not hasattr(self, "_dense"):
+            self._dense = {}
+        h1 = self.waves[i][0][0]
+        if i not in self._dense:
+            def rhs(h, y):
+                r = _eig(h, y[0], self.g, self.xi, self.Ag)[1][:, i]
+                return [r[1], r[2]]
+            self._dense[i] = solve_ivp(rhs, (W0[0], h1), [W0[1], W0[2]], method="DOP853",
+                                       rtol=1e-12, atol=1e-14, dense_output=True).sol
+        sol = self._dense[i]
+        W = lambda h: np.array([h, *sol(h)])  # noqa: E731
+        h = brentq(lambda hh: _lam(W(hh), i, self.g, self.xi, self.Ag) - S,
+                   min(W0[0], h1), max(W0[0], h1), xtol=1e-14)
+        return W(h)
