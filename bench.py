@@ -67,6 +67,8 @@ def parse():
                     help="training steps of the |A|_Psi surrogate at batch 65536 (0 = skip the leg)")
     ap.add_argument("--sur-samples", type=int, default=50_000_000,
                     help="edge samples harvested from the smooth, bump and ensemble workloads")
+    ap.add_argument("--l1-sweep", action="store_true",
+                    help="also run the smooth problem to t_end = 0.5 s at N = 1e3 * 2^k (FP32, FP64, oracle)")
     ap.add_argument("--accuracy-steps", type=int, default=96,
                     help="steps of the FP32-vs-FP64 increment check (0 = skip)")
     return ap.parse_args()
@@ -230,6 +232,41 @@ def surrogate_leg(args, adot, W, P, n, stream, dev, local, time_steps, ref64):
                                                         / np.abs(b_ - a0).sum())
                 out[f"l1_rel_state_{name}"] = float(np.abs(a_ - b_).sum() / np.abs(b_).sum())
         return out
+
+
+def l1_sweep(adot, W, stream, local, k_max=8, n_oracle_max=32000):
+    """Full-t_end errors on the smooth periodic problem: FP32 vs the GPU FP64
+    path (itself parity-tested against the oracle) for N = 1e3 * 2^k, k <= k_max,
+    and GPU FP64 / FP32 vs the CPU oracle for N <= n_oracle_max."""
+    import oracle as O
+    rows = []
+    for k in range(k_max + 1):
+        n = 1000 * 2 ** k
+        P = W.smooth_periodic(n)
+        res = {"n": n}
+        states = {}
+        for name, prec in (("fp64", adot.FP64), ("fp32", adot.FP32)):
+            with adot.Solver(adot.config_for(P, prec, device=local), stream=stream) as s:
+                s.set_state(P.h, P.q, P.z)
+                t0 = time.perf_counter()
+                s.run_to(P.t_end)
+                res[f"{name}_seconds"] = time.perf_counter() - t0
+                _, steps, _ = s.query()
+                res[f"{name}_steps"] = steps
+                states[name] = s.get_state()
+        for v, a, b in zip("hqz", states["fp32"], states["fp64"]):
+            res[f"l1_fp32_vs_fp64_{v}"] = float(np.abs(a - b).sum() / np.abs(b).sum())
+        if n <= n_oracle_max:
+            cfg = O.make_cfg(n, P.x_min, P.x_max, P.cfl, O.grass(P.Ag, xi=P.xi), P.bc_left, P.bc_right)
+            t0 = time.perf_counter()
+            ho, qo, zo, _, so, _ = O.run(cfg, P.h, P.q, P.z, t_end=P.t_end)
+            res["oracle_seconds"] = time.perf_counter() - t0
+            res["oracle_steps"] = so
+            for name in ("fp64", "fp32"):
+                res[f"l1_{name}_vs_oracle"] = max(float(np.abs(a - b).sum() / np.abs(b).sum())
+                                                  for a, b in zip(states[name], (ho, qo, zo)))
+        rows.append(res)
+    return rows
 
 
 def run_reference(args, rank, ws):
@@ -419,6 +456,8 @@ def main():
     if args.sur_steps > 0 and rank == 0:
         surrogate = surrogate_leg(args, adot, W, P, n, stream, dev, local, time_steps, ref64)
 
+    sweep = l1_sweep(adot, W, stream, local) if (args.l1_sweep and rank == 0) else None
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         rate, sec, thr = oracle_throughput(n, args.cpu_steps)
@@ -449,7 +488,7 @@ def main():
                          "hbm_peak_gbs": measured_peaks().get("hbm_gbs", 6800.0)},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps, "clocks": clocks,
             "accuracy": accuracy, "sim_time_after_timed_steps": t_sim, "variants": variants,
-            "ensemble": ensemble, "surrogate": surrogate,
+            "ensemble": ensemble, "surrogate": surrogate, "l1_t_end_sweep": sweep,
         }
         print(json.dumps(line), flush=True)
     if dist:

@@ -1,0 +1,74 @@
+"""Flow over a Gaussian bump (inflow q = 0.6, outflow h = 0.33): a fixed-bed
+spin-up (A_g = 0) that crosses Fr = 1, where the fixed-bed eigenvalues
+coalesce (coalescence reading) and the float32 path redoes nodes in float64,
+then morphodynamic runs with the Grass (A_g = 0.001) and the Meyer-Peter &
+Mueller laws. GPU against the oracle: FP64 within 1e-11 of each variable's
+scale, FP32 within 1e-5 (L1, relative)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1912_04791_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+N = 2000
+MPM = dict(s_rel=2.65, d50=1e-3, manning_n=0.02)
+
+
+def _olaw(kind, P):
+    return O.grass(P.Ag, xi=P.xi) if kind == "grass" else O.mpm(xi=P.xi, **MPM)
+
+
+def _gcfg(gpu, P, kind, prec):
+    if kind == "grass":
+        return gpu.config_for(P, prec)
+    return gpu.config_for(P, prec, law=gpu.LAW_MPM, **MPM)
+
+
+@pytest.fixture(scope="module")
+def spun_up(gpu):
+    """(oracle state, GPU FP64 state, GPU FP32 state) after 6 s of fixed-bed flow."""
+    P = W.gaussian_bump(N, Ag=0.0)
+    cfg = O.make_cfg(N, 0, 10, 0.9, O.grass(0.0, xi=P.xi), P.bc_left, P.bc_right, P.bcl, P.bcr)
+    ho, qo, zo, to, so, _ = O.run(cfg, P.h, P.q, P.z, t_end=6.0)
+    out = [(ho, qo, zo, so)]
+    for prec in (gpu.FP64, gpu.FP32):
+        with gpu.Solver(gpu.config_for(P, prec)) as s:
+            s.set_state(P.h, P.q, P.z)
+            s.run_to(6.0)
+            t, steps, _ = s.query()
+            out.append(s.get_state() + (steps,))
+    return P, out
+
+
+def test_spin_up_crosses_critical_flow(spun_up):
+    P, (o, g64, g32) = spun_up
+    h, q = o[0], o[1]
+    fr = q / h / np.sqrt(9.81 * h)
+    assert fr.min() < 0.9 and fr.max() > 1.1  # transcritical
+    assert g64[3] == o[3]  # same number of steps
+    for a, b in zip(g64[:3], o[:3]):
+        assert np.abs(a - b).max() <= 1e-11 * np.abs(b).max()
+    for a, b in zip(g32[:3], o[:3]):
+        assert np.abs(a - b).sum() <= 1e-5 * np.abs(b).sum()
+
+
+@pytest.mark.parametrize("kind", ["grass", "mpm"])
+def test_morphodynamic_runs_match_oracle(gpu, spun_up, kind):
+    P0, (o, g64, g32) = spun_up
+    P = W.gaussian_bump(N, Ag=0.001)
+    ocfg = O.make_cfg(N, 0, 10, 0.9, _olaw(kind, P), P.bc_left, P.bc_right, P.bcl, P.bcr)
+    ho, qo, zo, *_ = O.run(ocfg, o[0], o[1], o[2], max_steps=300)
+    assert np.abs(zo - o[2]).max() > 1e-4  # the bed moved
+    with gpu.Solver(_gcfg(gpu, P, kind, gpu.FP64)) as s:
+        s.set_state(*g64[:3])
+        s.step(300)
+        h, q, z = s.get_state()
+    for a, b in ((h, ho), (q, qo), (z, zo)):
+        assert np.abs(a - b).max() <= 1e-10 * np.abs(b).max()
+    with gpu.Solver(_gcfg(gpu, P, kind, gpu.FP32)) as s:
+        s.set_state(*g32[:3])
+        s.step(300)
+        h, q, z = s.get_state()
+    for a, b in ((h, ho), (q, qo), (z, zo)):
+        assert np.abs(a - b).sum() <= 1e-5 * np.abs(b).sum()
