@@ -332,7 +332,7 @@ def main():
                           device=local)
     solver = adot.Solver(cfg, stream=stream)
     solver.set_state(P.h, P.q, P.z)
-    block, reg_cap = adot.adot_autotune(solver.ctx, 8)
+    block, reg_cap, kern = adot.adot_autotune(solver.ctx, 8)
 
     def time_steps(s, k):
         torch.cuda.synchronize(dev)
@@ -348,13 +348,15 @@ def main():
     variants = None
     if args.sweep and rank == 0:
         variants = {}
-        for vb, vc in [(128, 64), (128, -1), (256, 64), (256, -1), (512, 64), (512, -1)]:
+        for vb, vc, vk in [(128, 64, 1), (128, -1, 1), (256, 64, 1), (256, -1, 1), (512, 64, 1),
+                           (512, -1, 1), (256, 64, 2), (128, 64, 2), (128, 72, 2), (256, 80, 2)]:
             with adot.Solver(adot.config_for(P, adot.FP32, block_threads=vb, reg_cap=vc,
-                                             device=local), stream=stream) as sv:
+                                             step_kernel=vk, device=local), stream=stream) as sv:
                 sv.set_state(P.h, P.q, P.z)
                 adot.adot_step(sv.ctx, 48)
                 ms_v = time_steps(sv, 480)
-            variants[f"{vb}x{'cap64' if vc == 64 else 'nocap'}"] = n * 480 / (ms_v * 1e-3)
+            name = f"{'warp' if vk == 2 else 'block'}{vb}x{'cap%d' % vc if vc > 0 else 'nocap'}"
+            variants[name] = n * 480 / (ms_v * 1e-3)
 
     # warm-up
     adot.adot_step(solver.ctx, args.warmup)
@@ -475,6 +477,7 @@ def main():
             "config": {"workload": f"smooth_periodic N={n} (A-DOT FP32, float-float state)",
                        "n_cells": n, "domain": "[0,1] m periodic", "Ag": P.Ag, "xi": P.xi,
                        "cfl": P.cfl, "block_threads": block, "reg_cap": reg_cap,
+                       "step_kernel": "warp tiles" if kern == 2 else "block",
                        "steps_per_graph": 48,
                        "l2": "inputs larger than L2 (2 x 240 MB state buffers, no flush)",
                        "parallelism": "replicas" if ws > 1 else "single"},
@@ -482,7 +485,7 @@ def main():
                          "frac": achieved / f_peak,
                          "traffic": DRAM_BYTES_PER_CELL_UPDATE * n,
                          "traffic_note": "ncu dram read+write of one launch at N=4e6, scaled to N",
-                         "kernel": f"k_step<float,GRASS,{block},{max(reg_cap, 0)}>",
+                         "kernel": f"{'k_step_warp' if kern == 2 else 'k_step'}<float,GRASS,{block},{max(reg_cap, 0)}>",
                          "peak_source": "152 SM x 128 FP32 lanes x 2 x 2070 MHz (derived)",
                          "hbm_achieved_gbs": BYTES_PER_CELL_UPDATE * n / per_launch_s / 1e9,
                          "hbm_peak_gbs": measured_peaks().get("hbm_gbs", 6800.0)},

@@ -93,8 +93,12 @@ typedef struct {
   int32_t block_threads;    /* threads per block of the step kernel: 128, 256, 512; 0 = autotuned */
   int32_t steps_per_graph;  /* time steps captured per CUDA graph; 0 = default (48) */
   int32_t device;           /* CUDA device ordinal; -1 = the calling thread's current device */
-  int32_t reg_cap;          /* register cap per thread of the step kernel: 64, or -1 = none;
-                               0 = autotuned */
+  int32_t reg_cap;          /* register cap per thread of the step kernel: 64 (block kernel
+                               or warp tiles), 72 (warp tiles, 128 threads), 80 (warp tiles,
+                               256 threads), or -1 = none (block kernel); 0 = autotuned */
+  int32_t step_kernel;      /* 1 = block kernel (B-1 cells per block, shared-memory exchange),
+                               2 = persistent warp tiles (31 cells per warp tile, shuffle
+                               exchange); 0 = autotuned */
 } adot_config;
 
 typedef struct adot_ctx adot_ctx;
@@ -143,16 +147,16 @@ adot_status adot_fluctuations(adot_ctx* ctx, const double* WL, const double* WR,
                               double* Dminus, double* Dplus, double* rho_max_out,
                               int on_device);
 
-/* Times the compiled step-kernel variants allowed by the configuration (block
- * size and register cap; a field left at 0 is free) on the current state with
+/* Times the compiled step-kernel variants allowed by the configuration (kernel
+ * kind, block size and register cap; a field left at 0 is free) on the current state with
  * `trial_steps` steps each, keeps the fastest and re-captures the time-loop
  * graph. Trial steps write only the scratch buffer, so the state and time do
  * not advance. The choice is cached per (device, law, precision, log2 n) for
  * the process; adot_set_state runs this once per context with trial_steps = 8
- * when a field is free and nothing is cached. block_out / reg_cap_out (may be
- * NULL) receive the choice. ADOT_E_INVALID_ARG before adot_set_state. */
+ * when a field is free and nothing is cached. block_out, reg_cap_out and
+ * step_kernel_out (each may be NULL) receive the choice. ADOT_E_INVALID_ARG before adot_set_state. */
 adot_status adot_autotune(adot_ctx* ctx, int64_t trial_steps, int32_t* block_out,
-                          int32_t* reg_cap_out);
+                          int32_t* reg_cap_out, int32_t* step_kernel_out);
 
 /* Sums over the cells of h, q and z (float64, fixed-order tree: the result is
  * bit-reproducible). Multiply by dx for the integrals. */

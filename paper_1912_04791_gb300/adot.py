@@ -45,7 +45,7 @@ class Config(ctypes.Structure):
                 ("bc_right", ctypes.c_int32), ("bc_left_value", ctypes.c_double * 3),
                 ("bc_right_value", ctypes.c_double * 3), ("block_threads", ctypes.c_int32),
                 ("steps_per_graph", ctypes.c_int32), ("device", ctypes.c_int32),
-                ("reg_cap", ctypes.c_int32)]
+                ("reg_cap", ctypes.c_int32), ("step_kernel", ctypes.c_int32)]
 
 
 class EnsembleConfig(ctypes.Structure):
@@ -80,7 +80,8 @@ def lib() -> ctypes.CDLL:
             "adot_query": ([_P, _D, ctypes.POINTER(i64), _D], i32),
             "adot_fluctuations": ([_P, _P, _P, i64, _P, _P, _D, i32], i32),
             "adot_conserved_sums": ([_P, _D], i32),
-            "adot_autotune": ([_P, i64, ctypes.POINTER(i32), ctypes.POINTER(i32)], i32),
+            "adot_autotune": ([_P, i64, ctypes.POINTER(i32), ctypes.POINTER(i32),
+                               ctypes.POINTER(i32)], i32),
             "adot_step_noalloc": ([ctypes.POINTER(Config), _P, _P, _P, i64, _D, _P], i32),
             "adot_mlp_create": ([i64, _P, ctypes.POINTER(_P)], i32),
             "adot_mlp_destroy": ([_P], None),
@@ -156,7 +157,7 @@ def _ptr(a, n=None):
 def make_config(n_cells, x_min, x_max, cfl, Ag, xi, precision=FP32, bc_left=BC_TRANSMISSIVE,
                 bc_right=BC_TRANSMISSIVE, bcl=(0.0, 0.0, 0.0), bcr=(0.0, 0.0, 0.0), g=9.81,
                 law=LAW_GRASS, s_rel=0.0, d50=0.0, manning_n=0.0, block_threads=0,
-                steps_per_graph=0, device=-1, reg_cap=0) -> Config:
+                steps_per_graph=0, device=-1, reg_cap=0, step_kernel=0) -> Config:
     c = Config()
     c.n_cells = int(n_cells)
     c.x_min, c.x_max, c.cfl = float(x_min), float(x_max), float(cfl)
@@ -170,6 +171,7 @@ def make_config(n_cells, x_min, x_max, cfl, Ag, xi, precision=FP32, bc_left=BC_T
     c.steps_per_graph = steps_per_graph
     c.device = device
     c.reg_cap = reg_cap
+    c.step_kernel = step_kernel
     return c
 
 
@@ -247,10 +249,11 @@ def adot_fluctuations(ctx: int, WL, WR, Dm=None, Dp=None):
 
 
 def adot_autotune(ctx: int, trial_steps: int = 8):
-    """Times the allowed step-kernel variants; returns (block_threads, reg_cap)."""
-    b, r = ctypes.c_int32(), ctypes.c_int32()
-    _check(lib().adot_autotune(ctx, trial_steps, ctypes.byref(b), ctypes.byref(r)), "adot_autotune")
-    return b.value, r.value
+    """Times the allowed step-kernel variants; returns (block_threads, reg_cap, step_kernel)."""
+    b, r, k = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().adot_autotune(ctx, trial_steps, ctypes.byref(b), ctypes.byref(r), ctypes.byref(k)),
+           "adot_autotune")
+    return b.value, r.value, k.value
 
 
 def adot_step_noalloc(cfg: Config, h, q, z, n_steps: int, t0: float = 0.0, stream=None) -> float:

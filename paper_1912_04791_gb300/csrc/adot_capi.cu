@@ -110,7 +110,9 @@ adot_status adot::validate_config(const adot_config* c) {
   for (int i = 0; i < 3; ++i)
     if (!isfinite(c->bc_left_value[i]) || !isfinite(c->bc_right_value[i])) return ADOT_E_INVALID_ARG;
   if (c->block_threads != 0 && !step_block_supported(c->block_threads)) return ADOT_E_INVALID_ARG;
-  if (c->reg_cap != 0 && c->reg_cap != 64 && c->reg_cap != -1) return ADOT_E_INVALID_ARG;
+  if (c->reg_cap != 0 && c->reg_cap != 64 && c->reg_cap != 72 && c->reg_cap != 80 && c->reg_cap != -1)
+    return ADOT_E_INVALID_ARG;
+  if (c->step_kernel < 0 || c->step_kernel > 2) return ADOT_E_INVALID_ARG;
   if (c->steps_per_graph < 0 || c->device < -1) return ADOT_E_INVALID_ARG;
   return ADOT_OK;
 }
@@ -210,18 +212,21 @@ adot_status enqueue(adot_ctx* c, int64_t n) {
 
 // Process-wide cache of tuned variants: (device, law, precision, log2 n, filters).
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int, int, int, int>, StepVariant> g_tune_cache;
+std::map<std::tuple<int, int, int, int, int, int, int>, StepVariant> g_tune_cache;
 
-std::tuple<int, int, int, int, int, int> tune_key(const adot_ctx* c) {
+std::tuple<int, int, int, int, int, int, int> tune_key(const adot_ctx* c) {
   int lg = 0;
   for (int64_t n = c->p.n; n > 1; n >>= 1) ++lg;
-  return std::make_tuple(c->device, c->law, c->prec, lg, c->cfg.block_threads, c->cfg.reg_cap);
+  return std::make_tuple(c->device, c->law, c->prec, lg, c->cfg.block_threads, c->cfg.reg_cap,
+                         c->cfg.step_kernel);
 }
 
 bool candidate(const adot_config& cfg, StepVariant v) {
   if (cfg.block_threads && v.block != cfg.block_threads) return false;
-  if (cfg.reg_cap == 64 && v.reg_cap != 64) return false;
+  if (cfg.reg_cap > 0 && v.reg_cap != cfg.reg_cap) return false;
   if (cfg.reg_cap == -1 && v.reg_cap != 0) return false;
+  if (cfg.step_kernel == 1 && v.warp_tiles) return false;
+  if (cfg.step_kernel == 2 && !v.warp_tiles) return false;
   return true;
 }
 
@@ -348,7 +353,14 @@ adot_status adot_create(const adot_config* cfg, void* cuda_stream, adot_ctx** ou
   c->prec = cfg->precision;
   c->law = cfg->law.kind;
   c->var = StepVariant{cfg->block_threads ? cfg->block_threads : 256,
-                       cfg->reg_cap == -1 ? 0 : 64};
+                       cfg->reg_cap == -1 ? 0 : 64, cfg->step_kernel == 2 ? 1 : 0};
+  if (!step_variant_supported(c->var)) {  // e.g. warp tiles without a register cap
+    for (int i = 0; i < kNumStepVariants; ++i)
+      if (candidate(*cfg, kStepVariants[i])) {
+        c->var = kStepVariants[i];
+        break;
+      }
+  }
   {
     int n_cand = 0;
     for (int i = 0; i < kNumStepVariants; ++i) n_cand += candidate(*cfg, kStepVariants[i]) ? 1 : 0;
@@ -570,12 +582,13 @@ adot_status adot_fluctuations(adot_ctx* c, const double* WL, const double* WR, i
 }
 
 adot_status adot_autotune(adot_ctx* c, int64_t trial_steps, int32_t* block_out,
-                          int32_t* reg_cap_out) {
+                          int32_t* reg_cap_out, int32_t* step_kernel_out) {
   if (!c || !c->state_set || trial_steps < 1) return ADOT_E_INVALID_ARG;
   adot_status st = tune(c, trial_steps);
   if (st) return st;
   if (block_out) *block_out = c->var.block;
   if (reg_cap_out) *reg_cap_out = c->var.reg_cap ? c->var.reg_cap : -1;
+  if (step_kernel_out) *step_kernel_out = c->var.warp_tiles ? 2 : 1;
   return ADOT_OK;
 }
 

@@ -59,12 +59,14 @@ enum : int { BC_TRANSMISSIVE = 0, BC_PERIODIC = 1, BC_INFLOW_Q = 2, BC_OUTFLOW_H
 struct StepVariant {
   int block;
   int reg_cap;
+  int warp_tiles;  // 1: persistent warp-tile kernel (k_step_warp), 0: block kernel (k_step)
 };
 
 // The compiled variants, in the order the autotuner tries them.
-constexpr int kNumStepVariants = 6;
+constexpr int kNumStepVariants = 10;
 constexpr StepVariant kStepVariants[kNumStepVariants] = {
-    {256, 0}, {256, 64}, {128, 0}, {128, 64}, {512, 0}, {512, 64}};
+    {256, 0, 0},  {256, 64, 0}, {128, 0, 0}, {128, 64, 0}, {512, 0, 0}, {512, 64, 0},
+    {256, 64, 1}, {128, 64, 1}, {128, 72, 1}, {256, 80, 1}};
 
 bool step_block_supported(int block);
 bool step_variant_supported(StepVariant v);

@@ -7,7 +7,9 @@ bool step_block_supported(int block) { return block == 128 || block == 256 || bl
 
 bool step_variant_supported(StepVariant v) {
   for (int i = 0; i < kNumStepVariants; ++i)
-    if (kStepVariants[i].block == v.block && kStepVariants[i].reg_cap == v.reg_cap) return true;
+    if (kStepVariants[i].block == v.block && kStepVariants[i].reg_cap == v.reg_cap &&
+        kStepVariants[i].warp_tiles == v.warp_tiles)
+      return true;
   return false;
 }
 

@@ -311,6 +311,99 @@ __global__ void __launch_bounds__(B, MinBlocks<B, CAP>::value) k_step(const Step
   if (flags) atomicOr(&ctl->status, flags);
 }
 
+// Persistent warp-tile variant of the time step. Each warp owns tiles of 32
+// edges / 31 cells (tile t: edges 31t .. 31t+31, cells 31t .. 31t+30) and walks
+// them with a grid-wide stride; D+ of edge e-1 comes from the left lane by a
+// shuffle, so warps never wait for one another. Each warp keeps its CFL maximum
+// in a register and folds it into the control slot once at the end. One edge
+// in 32 is evaluated twice.
+template <typename R, int LAW, int B, int CAP>
+__global__ void __launch_bounds__(B, MinBlocks<B, CAP>::value)
+    k_step_warp(const StepParams p, const typename Prec<R>::State in,
+                const typename Prec<R>::State out, const int slot) {
+  using S = typename Prec<R>::S;
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * B + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * B) >> 5;
+  const int64_t n = p.n;
+  const int64_t n_tiles = (n + 30) / 31;
+  Ctl* ctl = p.ctl;
+
+  // step size (every warp forms the same value from the control slot)
+  R nu0 = R(0);
+  int done0 = 0;
+  if (lane == 0) {
+    const CtlSlot cs = ctl->s[slot];
+    const double t_end = ctl->t_end;
+    const bool d = !(cs.t < t_end);
+    const double rho = Prec<R>::from_bits(cs.rho_bits);
+    double dt = p.cfl * p.dx / rho;
+    double tn = cs.t + dt;
+    if (tn >= t_end) {
+      dt = t_end - cs.t;
+      tn = t_end;
+    }
+    nu0 = d ? R(0) : R(dt / p.dx);
+    done0 = d ? 1 : 0;
+    if (gw == 0) {
+      CtlSlot& nx = ctl->s[(slot + 1) % 3];
+      nx.t = d ? cs.t : tn;
+      nx.dt = d ? cs.dt : dt;
+      nx.steps = cs.steps + (d ? 0 : 1);
+      if (d) nx.rho_bits = cs.rho_bits;
+      ctl->s[(slot + 2) % 3].rho_bits = 0ull;
+    }
+  }
+  const R nu = __shfl_sync(0xffffffffu, nu0, 0);
+  const bool done = __shfl_sync(0xffffffffu, done0, 0) != 0;
+
+  unsigned flags = 0;
+  R rho_run = R(0);
+  for (int64_t t = gw; t < n_tiles; t += nwarps) {
+    const int64_t e = 31 * t + lane;
+    S wl[3];
+    R dm[3] = {R(0), R(0), R(0)}, dp[3] = {R(0), R(0), R(0)};
+    if (e <= n) {
+      S wr[3];
+      load_edge<R>(p, in, e, slot, wl, wr);
+      edge_fluct<R, LAW>(p, wl, wr, dm, dp, flags);
+    }
+    R dl[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) dl[r] = __shfl_up_sync(0xffffffffu, dp[r], 1);
+    const int64_t i = e - 1;
+    if (lane >= 1 && i < n) {
+      S nh = wl[0], nq = wl[1], nz = wl[2];
+      if (!done) {
+        nh = Prec<R>::add(wl[0], -nu * (dm[0] + dl[0]));
+        nq = Prec<R>::add(wl[1], -nu * (dm[1] + dl[1]));
+        nz = Prec<R>::add(wl[2], -nu * (dm[2] + dl[2]));
+      }
+      out.h[i] = nh;
+      out.q[i] = nq;
+      out.z[i] = nz;
+      if (!done) {
+        const R hh = Prec<R>::hi(nh);
+        if (!(hh > R(0))) flags |= ST_DEPTH;
+        if (!(Prec<R>::finite(nh) && Prec<R>::finite(nq) && Prec<R>::finite(nz))) {
+          flags |= ST_NONFINITE;
+        } else if (hh > R(0)) {
+          R r = Prec<R>::template rho<LAW>(p, hh, Prec<R>::hi(nq));
+          if (!(r <= R(3.0e38))) {
+            flags |= ST_NONFINITE;
+            r = R(0);
+          }
+          rho_run = d_max(rho_run, r);
+        }
+      }
+    }
+  }
+  rho_run = warp_max(rho_run);
+  if (lane == 0 && !done && rho_run > R(0))
+    atomicMax(&ctl->s[(slot + 1) % 3].rho_bits, Prec<R>::bits(rho_run));
+  if (flags) atomicOr(&ctl->status, flags);
+}
+
 // CFL maximum and admissibility of a state (grid-stride).
 template <typename R, int LAW>
 __global__ void __launch_bounds__(256) k_rho(const StepParams p, const typename Prec<R>::State st,
@@ -357,6 +450,34 @@ cudaError_t launch_step_law(const StepParams& p, StepVariant v, typename Prec<R>
   const int64_t g = (p.n + 1 + cells - 1) / cells;
   if (g > 0x7fffffffLL) return cudaErrorInvalidValue;
   const unsigned G = (unsigned)g;
+  if (v.warp_tiles) {
+    // resident grid: blocks per SM from the register cap, times the SM count
+    int sms = 152, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t per_sm = v.reg_cap ? 65536 / (v.block * v.reg_cap) : 1;  // = MinBlocks
+    const int64_t tiles = (p.n + 30) / 31;
+    const int64_t wpb = v.block / 32;
+    int64_t gg = (tiles + wpb - 1) / wpb;
+    if (gg > sms * per_sm) gg = sms * per_sm;
+    if (v.block == 256 && v.reg_cap == 64) {
+      k_step_warp<R, LAW, 256, 64><<<(unsigned)gg, 256, 0, s>>>(p, in, out, slot);
+      return cudaGetLastError();
+    }
+    if (v.block == 128 && v.reg_cap == 64) {
+      k_step_warp<R, LAW, 128, 64><<<(unsigned)gg, 128, 0, s>>>(p, in, out, slot);
+      return cudaGetLastError();
+    }
+    if (v.block == 128 && v.reg_cap == 72) {
+      k_step_warp<R, LAW, 128, 72><<<(unsigned)gg, 128, 0, s>>>(p, in, out, slot);
+      return cudaGetLastError();
+    }
+    if (v.block == 256 && v.reg_cap == 80) {
+      k_step_warp<R, LAW, 256, 80><<<(unsigned)gg, 256, 0, s>>>(p, in, out, slot);
+      return cudaGetLastError();
+    }
+    return cudaErrorInvalidValue;
+  }
 #define ADOT_STEP_CASE(BB, CC)                                       \
   if (v.block == BB && v.reg_cap == CC) {                            \
     k_step<R, LAW, BB, CC><<<G, BB, 0, s>>>(p, in, out, slot);       \

@@ -37,7 +37,7 @@ int main(void) {
          offsetof(adot_config, law), offsetof(adot_config, precision),
          offsetof(adot_config, bc_left_value), offsetof(adot_config, bc_right_value),
          offsetof(adot_config, block_threads), offsetof(adot_config, device),
-         offsetof(adot_config, reg_cap), offsetof(adot_law, manning_n));
+         offsetof(adot_config, step_kernel), offsetof(adot_law, manning_n));
   return 0;
 }
 ''')
@@ -48,7 +48,7 @@ int main(void) {
     C, W = adot.Config, adot.Law
     want = [ctypes.sizeof(C), ctypes.sizeof(W), C.law.offset, C.precision.offset,
             C.bc_left_value.offset, C.bc_right_value.offset, C.block_threads.offset,
-            C.device.offset, C.reg_cap.offset, W.manning_n.offset]
+            C.device.offset, C.step_kernel.offset, W.manning_n.offset]
     assert got == want
 
 
@@ -62,7 +62,7 @@ def test_status_strings_and_version(L):
 @pytest.mark.parametrize("field,value", [
     ("n_cells", 0), ("cfl", 0.0), ("cfl", 1.5), ("x_max", -1.0), ("precision", 7),
     ("bc_left", 9), ("block_threads", 100), ("steps_per_graph", -6), ("device", -3),
-    ("reg_cap", 32)])
+    ("reg_cap", 32), ("step_kernel", 3)])
 def test_invalid_config_rejected_without_cuda(L, field, value):
     cfg = adot.make_config(64, 0.0, 1.0, 0.8, 0.005, 5 / 3)
     setattr(cfg, field, value)
@@ -83,7 +83,7 @@ def test_null_arguments_rejected(L):
     assert L.adot_step(None, 1, None, None) == adot.E_INVALID_ARG
     assert L.adot_query(None, None, None, None) == adot.E_INVALID_ARG
     assert L.adot_fluctuations(None, None, None, 0, None, None, None, 0) == adot.E_INVALID_ARG
-    assert L.adot_autotune(None, 8, None, None) == adot.E_INVALID_ARG
+    assert L.adot_autotune(None, 8, None, None, None) == adot.E_INVALID_ARG
     L.adot_destroy(None)
 
 

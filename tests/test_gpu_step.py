@@ -39,16 +39,18 @@ def _run_gpu(gpu, P, prec, steps=None, t_end=None, **kw):
     return h, q, z, t, nsteps, dt
 
 
-VARIANTS = [(128, 64), (128, -1), (256, 64), (256, -1), (512, 64), (512, -1)]
+VARIANTS = [(128, 64, 1), (128, -1, 1), (256, 64, 1), (256, -1, 1), (512, 64, 1), (512, -1, 1),
+            (256, 64, 2), (128, 64, 2), (128, 72, 2), (256, 80, 2)]
 
 
-@pytest.mark.parametrize("n", [1, 2, 255, 256, 511, 1000, 2049])
-@pytest.mark.parametrize("block,cap", VARIANTS)
-def test_fp64_smooth_periodic_matches_oracle(gpu, n, block, cap):
+@pytest.mark.parametrize("n", [1, 2, 31, 32, 255, 256, 511, 1000, 2049])
+@pytest.mark.parametrize("block,cap,kern", VARIANTS)
+def test_fp64_smooth_periodic_matches_oracle(gpu, n, block, cap, kern):
     P = W.smooth_periodic(n)
     K = 60
     ho, qo, zo, to, _, _ = O.run(_ocfg(P), P.h, P.q, P.z, max_steps=K)
-    h, q, z, t, steps, _ = _run_gpu(gpu, P, gpu.FP64, steps=K, block_threads=block, reg_cap=cap)
+    h, q, z, t, steps, _ = _run_gpu(gpu, P, gpu.FP64, steps=K, block_threads=block, reg_cap=cap,
+                                    step_kernel=kern)
     assert steps == K
     assert t == pytest.approx(to, rel=1e-13)
     for a, b in ((h, ho), (q, qo), (z, zo)):
@@ -115,8 +117,9 @@ def test_fp32_variants_agree(gpu):
     float32 increments agree to 1e-7 of their L1 norm."""
     P = W.smooth_periodic(5003)
     ref = None
-    for block, cap in VARIANTS:
-        h, q, z, *_ = _run_gpu(gpu, P, gpu.FP32, steps=50, block_threads=block, reg_cap=cap)
+    for block, cap, kern in VARIANTS:
+        h, q, z, *_ = _run_gpu(gpu, P, gpu.FP32, steps=50, block_threads=block, reg_cap=cap,
+                               step_kernel=kern)
         inc = np.concatenate([h - P.h, q - P.q, z - P.z])
         if ref is None:
             ref = inc
@@ -131,8 +134,8 @@ def test_autotune_keeps_state_and_picks_a_variant(gpu):
         ref = s.get_state()
     with gpu.Solver(gpu.config_for(P, gpu.FP32)) as s:  # every field free: tuned in set_state
         s.set_state(P.h, P.q, P.z)
-        b, r = gpu.adot_autotune(s.ctx, 4)
-        assert (b, r) in [(bb, cc) for bb, cc in VARIANTS]
+        b, r, k = gpu.adot_autotune(s.ctx, 4)
+        assert (b, r, k) in VARIANTS
         t, steps, _ = s.query()
         assert t == 0.0 and steps == 0
         s.step(12)
