@@ -32,10 +32,13 @@ UNIT = "cell-updates/s"
 # Gauss-Legendre nodes of the edge fluctuation, the float-float update and the
 # CFL spectral radius of the new state, counted from ncu's executed FFMA/FADD/
 # FMUL thread instructions of one launch divided by the cells it updates.
-FLOPS_PER_CELL_UPDATE = 636.1
-# DRAM read + write bytes per cell-update of that launch (ncu, N = 4e6): the
-# 24 B read match the algorithmic read; part of the 24 B written is still in L2.
-DRAM_BYTES_PER_CELL_UPDATE = (96.09e6 + 59.29e6) / 4e6
+# Per kernel kind: the block kernel repeats 1 edge in 256, the warp-tile
+# kernel 1 in 32; that repeated work is removed from the executed counts
+# (636.1 x 255/256 and 648.3 x 31/32).
+FLOPS_PER_CELL_UPDATE = {"block": 633.6, "warp": 628.0}
+# DRAM read + write bytes per cell-update of one launch (ncu, N = 4e6): the
+# ~24 B read match the algorithmic read; part of the 24 B written is still in L2.
+DRAM_BYTES_PER_CELL_UPDATE = {"block": (96.09e6 + 59.29e6) / 4e6, "warp": (97.76e6 + 64.64e6) / 4e6}
 BYTES_PER_CELL_UPDATE = 48.0  # float-float state: 3 x 8 B read + 3 x 8 B written
 
 
@@ -56,6 +59,8 @@ def parse():
     ap.add_argument("--n", type=float, default=1e7)
     ap.add_argument("--block", type=int, default=0, help="threads per block (0 = autotuned)")
     ap.add_argument("--reg-cap", type=int, default=0, help="64, -1 = none, 0 = autotuned")
+    ap.add_argument("--step-kernel", type=int, default=0,
+                    help="1 = block kernel, 2 = persistent warp tiles, 0 = autotuned")
     ap.add_argument("--sweep", action="store_true", help="also time every kernel variant")
     ap.add_argument("--cpu-steps", type=int, default=3,
                     help="oracle steps on the full workload for cpu_baseline")
@@ -329,7 +334,7 @@ def main():
     P = W.smooth_periodic(n)
     stream = torch.cuda.Stream(device=dev)
     cfg = adot.config_for(P, adot.FP32, block_threads=args.block, reg_cap=args.reg_cap,
-                          device=local)
+                          step_kernel=args.step_kernel, device=local)
     solver = adot.Solver(cfg, stream=stream)
     solver.set_state(P.h, P.q, P.z)
     block, reg_cap, kern = adot.adot_autotune(solver.ctx, 8)
@@ -469,7 +474,8 @@ def main():
     solver.close()
     if rank == 0:
         f_peak = 152 * 128 * 2 * (2070e6) / 1e12  # FP32 FMA peak at the maximum SM clock, TFLOP/s
-        achieved = FLOPS_PER_CELL_UPDATE * n / per_launch_s / 1e12
+        kind = "warp" if kern == 2 else "block"
+        achieved = FLOPS_PER_CELL_UPDATE[kind] * n / per_launch_s / 1e12
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -483,7 +489,7 @@ def main():
                        "parallelism": "replicas" if ws > 1 else "single"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": f_peak, "unit": "TFLOP/s",
                          "frac": achieved / f_peak,
-                         "traffic": DRAM_BYTES_PER_CELL_UPDATE * n,
+                         "traffic": DRAM_BYTES_PER_CELL_UPDATE[kind] * n,
                          "traffic_note": "ncu dram read+write of one launch at N=4e6, scaled to N",
                          "kernel": f"{'k_step_warp' if kern == 2 else 'k_step'}<float,GRASS,{block},{max(reg_cap, 0)}>",
                          "peak_source": "152 SM x 128 FP32 lanes x 2 x 2070 MHz (derived)",
