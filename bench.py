@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=2400)
     ap.add_argument("--warmup", type=int, default=96)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=float, default=1e7)
+    ap.add_argument("--cells", type=float, default=1e7, help="cells of the benchmark workload")
     ap.add_argument("--block", type=int, default=0, help="threads per block (0 = autotuned)")
     ap.add_argument("--reg-cap", type=int, default=0, help="64, -1 = none, 0 = autotuned")
     ap.add_argument("--step-kernel", type=int, default=0,
@@ -140,6 +140,18 @@ def dist_init():
         torch.cuda.set_device(local)
     dist.init_process_group(backend)
     return dist, rank, ws, local
+
+
+def max_over_ranks(value: float, dist, device=None) -> float:
+    """Largest value over all ranks (the slowest rank's time); the value itself
+    when not distributed. Uses the process group's backend (NCCL on GPUs, gloo
+    on CPUs)."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def oracle_throughput(n: int, steps: int, threads: int | None = None):
@@ -282,7 +294,7 @@ def run_reference(args, rank, ws):
     import oracle as O
     from paper_1912_04791_gb300 import workloads as W
     O.build()
-    n_full = int(args.n)
+    n_full = int(args.cells)
     # calibrate the per-cell cost on a small grid
     rate, _, thr = oracle_throughput(100_000, 2)
     budget = 150.0  # seconds for warmup + timed steps
@@ -330,7 +342,7 @@ def main():
     B.build()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    n = int(args.n)
+    n = int(args.cells)
     P = W.smooth_periodic(n)
     stream = torch.cuda.Stream(device=dev)
     cfg = adot.config_for(P, adot.FP32, block_threads=args.block, reg_cap=args.reg_cap,
@@ -384,10 +396,7 @@ def main():
     clocks = sampler.stop()
     ms = ev0.elapsed_time(ev1)
     t_sim, steps_done, dt_last = adot.adot_query(solver.ctx)  # raises on a device error
-    if dist:
-        tt = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(ms, dist, dev)
     value = ws * n * args.steps / (ms * 1e-3)
     per_launch_s = ms * 1e-3 / args.steps
 
@@ -404,11 +413,7 @@ def main():
         adot.adot_set_state(solver.ctx, *hin)
         adot.adot_enqueue_steps(solver.ctx, args.steps)
         adot.adot_get_state(solver.ctx, *hout)
-        sec = time.perf_counter() - t0
-        if dist:
-            tt = torch.tensor([sec], dtype=torch.float64, device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            sec = float(tt.item())
+        sec = max_over_ranks(time.perf_counter() - t0, dist, dev)
         e2e = {"value": ws * n * args.steps / sec, "unit": UNIT,
                "h2d_bytes_per_step": 3 * 8 * n / args.steps,
                "d2h_bytes_per_step": 3 * 8 * n / args.steps,
