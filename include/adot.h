@@ -121,6 +121,30 @@ adot_status adot_set_state(adot_ctx* ctx, const double* h, const double* q, cons
 /* Copies the current state out (float-float states are summed to float64). */
 adot_status adot_get_state(adot_ctx* ctx, double* h, double* q, double* z, int on_device);
 
+/* Checkpoint and resume. A checkpoint is one byte blob: a 128-byte header
+ * (magic "ADOT", version 1, n_cells, precision, law, time, last dt, step
+ * count, the spectral-radius maximum the next step's dt is taken from, the
+ * sticky device status, and a 64-bit FNV-1a fingerprint of the config fields
+ * that enter the arithmetic: n_cells, domain, cfl, law, precision and both
+ * boundary conditions; not the launch shape), followed by the state's stored
+ * words as rows h, q, z of n 8-byte values each (float64 in ADOT_FP64, the
+ * (hi, lo) float32 pair of the float-float value in ADOT_FP32: nothing is
+ * rounded). Restoring it into a context of the same config makes every later
+ * step bit-identical to the steps the saved context would have taken.
+ *
+ * adot_checkpoint_size: *bytes_out = 128 + 24 n.
+ * adot_checkpoint_save: writes the blob to `buf` (host, or device when
+ *   on_device = 1) of `bytes` >= that size; ADOT_E_INVALID_ARG before a state
+ *   was set or when the buffer is short. Waits for the stream.
+ * adot_checkpoint_load: reads a blob; ADOT_E_INVALID_ARG when the magic, the
+ *   version, the sizes or the fingerprint do not match this context (the state
+ *   is then left as it was). Resets the step-phase bookkeeping as
+ *   adot_set_state does, but keeps the saved time and step count; returns the
+ *   saved sticky status, if any. */
+adot_status adot_checkpoint_size(adot_ctx* ctx, int64_t* bytes_out);
+adot_status adot_checkpoint_save(adot_ctx* ctx, void* buf, int64_t bytes, int on_device);
+adot_status adot_checkpoint_load(adot_ctx* ctx, const void* buf, int64_t bytes, int on_device);
+
 /* Advances n_steps >= 0 time steps (Eq. scheme) with no end time, then waits
  * for the stream and reports the time and the last step's dt (either pointer
  * may be NULL) and the first device-side error. */

@@ -74,6 +74,9 @@ def lib() -> ctypes.CDLL:
             "adot_destroy": ([_P], None),
             "adot_set_state": ([_P, _P, _P, _P, i32, dbl], i32),
             "adot_get_state": ([_P, _P, _P, _P, i32], i32),
+            "adot_checkpoint_size": ([_P, ctypes.POINTER(i64)], i32),
+            "adot_checkpoint_save": ([_P, _P, i64, i32], i32),
+            "adot_checkpoint_load": ([_P, _P, i64, i32], i32),
             "adot_step": ([_P, i64, _D, _D], i32),
             "adot_enqueue_steps": ([_P, i64], i32),
             "adot_run_to": ([_P, dbl, ctypes.POINTER(i64)], i32),
@@ -207,6 +210,39 @@ def adot_get_state(ctx: int, h, q, z) -> None:
     if not dh == dq == dz:
         raise ValueError("h, q, z must all be on the host or all on the device")
     _check(lib().adot_get_state(ctx, ph, pq, pz, dh), "adot_get_state")
+
+
+def adot_checkpoint_size(ctx: int) -> int:
+    out = ctypes.c_int64()
+    _check(lib().adot_checkpoint_size(ctx, ctypes.byref(out)), "adot_checkpoint_size")
+    return out.value
+
+
+def _blob_ptr(buf):
+    """(address, bytes, on_device) of a contiguous uint8 numpy array or torch tensor."""
+    if isinstance(buf, np.ndarray):
+        if buf.dtype != np.uint8 or not buf.flags["C_CONTIGUOUS"]:
+            raise ValueError("checkpoint arrays must be contiguous uint8")
+        return buf.ctypes.data, buf.size, 0
+    import torch  # only for device memory
+    if buf.dtype != torch.uint8 or not buf.is_contiguous():
+        raise ValueError("checkpoint tensors must be contiguous uint8")
+    return buf.data_ptr(), buf.numel(), (1 if buf.is_cuda else 0)
+
+
+def adot_checkpoint_save(ctx: int, buf=None):
+    """Writes the checkpoint blob into `buf` (uint8 numpy array or CUDA tensor),
+    or into a new host array, and returns it."""
+    if buf is None:
+        buf = np.empty(adot_checkpoint_size(ctx), dtype=np.uint8)
+    p, nb, dev = _blob_ptr(buf)
+    _check(lib().adot_checkpoint_save(ctx, p, nb, dev), "adot_checkpoint_save")
+    return buf
+
+
+def adot_checkpoint_load(ctx: int, buf) -> None:
+    p, nb, dev = _blob_ptr(buf)
+    _check(lib().adot_checkpoint_load(ctx, p, nb, dev), "adot_checkpoint_load")
 
 
 def adot_step(ctx: int, n_steps: int):
@@ -491,6 +527,12 @@ class Solver:
         h, q, z = np.empty(self.n), np.empty(self.n), np.empty(self.n)
         adot_get_state(self.ctx, h, q, z)
         return h, q, z
+
+    def checkpoint(self, buf=None):
+        return adot_checkpoint_save(self.ctx, buf)
+
+    def restore(self, buf):
+        adot_checkpoint_load(self.ctx, buf)
 
     def step(self, n):
         return adot_step(self.ctx, n)

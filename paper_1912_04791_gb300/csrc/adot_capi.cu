@@ -296,6 +296,82 @@ adot_status read_ctl(adot_ctx* c) {
   return ADOT_OK;
 }
 
+// Fixes the step variant once a state is present: from the config, the
+// process-wide cache, or by timing the candidates on this state.
+adot_status choose_variant(adot_ctx* c) {
+  if (!c->tuned) {
+    bool cached = false;
+    {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      auto it = g_tune_cache.find(tune_key(c));
+      if (it != g_tune_cache.end()) {
+        c->var = it->second;
+        cached = true;
+      }
+    }
+    if (cached) {
+      c->tuned = true;
+      return build_graph(c);
+    }
+    return tune(c, 8);
+  }
+  return ADOT_OK;
+}
+
+
+// Checkpoint header: fixed 128 bytes ahead of the raw state words.
+struct CkptHeader {
+  uint32_t magic;    // 'ADOT' little-endian
+  uint32_t version;  // 1
+  int64_t n_cells;
+  int32_t precision;
+  int32_t law;
+  double t, dt;
+  int64_t steps;
+  uint64_t rho_bits;
+  uint32_t status;
+  uint32_t state_words;  // bytes per stored value: 8 (float-float pair or float64)
+  uint64_t fingerprint;
+  uint8_t reserved[128 - 72];
+};
+static_assert(sizeof(CkptHeader) == 128, "checkpoint header is 128 bytes");
+constexpr uint32_t kCkptMagic = 0x544F4441u;
+
+// FNV-1a over the config fields that enter the arithmetic (not the launch shape).
+uint64_t fnv1a(uint64_t h, const void* p, size_t n) {
+  const unsigned char* b = static_cast<const unsigned char*>(p);
+  for (size_t i = 0; i < n; ++i) {
+    h ^= b[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+uint64_t config_fingerprint(const adot_config& c) {
+  uint64_t h = 1469598103934665603ull;
+  h = fnv1a(h, &c.n_cells, sizeof c.n_cells);
+  h = fnv1a(h, &c.x_min, sizeof c.x_min);
+  h = fnv1a(h, &c.x_max, sizeof c.x_max);
+  h = fnv1a(h, &c.cfl, sizeof c.cfl);
+  h = fnv1a(h, &c.law.kind, sizeof c.law.kind);
+  h = fnv1a(h, &c.law.g, sizeof c.law.g);
+  h = fnv1a(h, &c.law.xi, sizeof c.law.xi);
+  h = fnv1a(h, &c.law.Ag, sizeof c.law.Ag);
+  h = fnv1a(h, &c.law.s_rel, sizeof c.law.s_rel);
+  h = fnv1a(h, &c.law.d50, sizeof c.law.d50);
+  h = fnv1a(h, &c.law.manning_n, sizeof c.law.manning_n);
+  h = fnv1a(h, &c.precision, sizeof c.precision);
+  h = fnv1a(h, &c.bc_left, sizeof c.bc_left);
+  h = fnv1a(h, &c.bc_right, sizeof c.bc_right);
+  h = fnv1a(h, c.bc_left_value, sizeof c.bc_left_value);
+  h = fnv1a(h, c.bc_right_value, sizeof c.bc_right_value);
+  return h;
+}
+
+int64_t checkpoint_bytes(const adot_ctx* c) {
+  return (int64_t)sizeof(CkptHeader) + 3 * c->p.n * 8;
+}
+
 void free_ctx(adot_ctx* c) {
   if (!c) return;
   if (c->graph_ready) cudaGraphExecDestroy(c->graph);
@@ -449,23 +525,7 @@ adot_status adot_set_state(adot_ctx* c, const double* h, const double* q, const 
   c->state_set = true;
   st = status_from_bits(c->h_ctl->status);
   if (st) return st;
-  if (!c->tuned) {
-    bool cached = false;
-    {
-      std::lock_guard<std::mutex> lk(g_tune_mu);
-      auto it = g_tune_cache.find(tune_key(c));
-      if (it != g_tune_cache.end()) {
-        c->var = it->second;
-        cached = true;
-      }
-    }
-    if (cached) {
-      c->tuned = true;
-      return build_graph(c);
-    }
-    return tune(c, 8);
-  }
-  return ADOT_OK;
+  return choose_variant(c);
 }
 
 adot_status adot_get_state(adot_ctx* c, double* h, double* q, double* z, int on_device) {
@@ -484,6 +544,81 @@ adot_status adot_get_state(adot_ctx* c, double* h, double* q, double* z, int on_
   }
   CK(cudaStreamSynchronize(c->stream));
   return ADOT_OK;
+}
+
+adot_status adot_checkpoint_size(adot_ctx* c, int64_t* bytes_out) {
+  if (!c || !bytes_out) return ADOT_E_INVALID_ARG;
+  *bytes_out = checkpoint_bytes(c);
+  return ADOT_OK;
+}
+
+adot_status adot_checkpoint_save(adot_ctx* c, void* buf, int64_t bytes, int on_device) {
+  if (!c || !buf || !c->state_set || bytes < checkpoint_bytes(c)) return ADOT_E_INVALID_ARG;
+  adot_status st = read_ctl(c);
+  if (st) return st;
+  const CtlSlot& s = c->h_ctl->s[c->phase % 3];
+  CkptHeader hd;
+  memset(&hd, 0, sizeof hd);
+  hd.magic = kCkptMagic;
+  hd.version = 1;
+  hd.n_cells = c->p.n;
+  hd.precision = c->prec;
+  hd.law = c->law;
+  hd.t = s.t;
+  hd.dt = s.dt;
+  hd.steps = s.steps;
+  hd.rho_bits = s.rho_bits;
+  hd.status = c->h_ctl->status;
+  hd.state_words = 8;
+  hd.fingerprint = config_fingerprint(c->cfg);
+  const size_t row = (size_t)c->p.n * 8;
+  unsigned char* out = static_cast<unsigned char*>(buf);
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (on_device)
+    CK(cudaMemcpyAsync(out, &hd, sizeof hd, cudaMemcpyHostToDevice, c->stream));
+  else
+    memcpy(out, &hd, sizeof hd);
+  for (int k = 0; k < 3; ++k)
+    CK(cudaMemcpyAsync(out + sizeof hd + k * row, c->buf[c->cur][k], row, kind, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return ADOT_OK;
+}
+
+adot_status adot_checkpoint_load(adot_ctx* c, const void* buf, int64_t bytes, int on_device) {
+  if (!c || !buf || bytes < (int64_t)sizeof(CkptHeader)) return ADOT_E_INVALID_ARG;
+  CkptHeader hd;
+  const unsigned char* in = static_cast<const unsigned char*>(buf);
+  CK(cudaStreamSynchronize(c->stream));
+  if (on_device) {
+    CK(cudaMemcpyAsync(&hd, in, sizeof hd, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  } else {
+    memcpy(&hd, in, sizeof hd);
+  }
+  if (hd.magic != kCkptMagic || hd.version != 1 || hd.state_words != 8 || hd.n_cells != c->p.n ||
+      hd.precision != c->prec || hd.law != c->law || hd.fingerprint != config_fingerprint(c->cfg) ||
+      bytes < checkpoint_bytes(c) || !isfinite(hd.t))
+    return ADOT_E_INVALID_ARG;
+  const size_t row = (size_t)c->p.n * 8;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  for (int k = 0; k < 3; ++k)
+    CK(cudaMemcpyAsync(c->buf[0][k], in + sizeof hd + k * row, row, kind, c->stream));
+  memset(c->h_ctl, 0, sizeof(Ctl));
+  c->h_ctl->s[0].t = hd.t;
+  c->h_ctl->s[0].dt = hd.dt;
+  c->h_ctl->s[0].steps = hd.steps;
+  c->h_ctl->s[0].rho_bits = hd.rho_bits;
+  c->h_ctl->status = hd.status;
+  c->h_ctl->t_end = INFINITY;
+  c->t_end_dev = INFINITY;
+  CK(cudaMemcpyAsync(c->d_ctl, c->h_ctl, sizeof(Ctl), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->cur = 0;
+  c->phase = 0;
+  c->state_set = true;
+  adot_status st = status_from_bits(hd.status);
+  if (st) return st;
+  return choose_variant(c);
 }
 
 adot_status adot_enqueue_steps(adot_ctx* c, int64_t n_steps) {

@@ -84,6 +84,9 @@ def test_null_arguments_rejected(L):
     assert L.adot_query(None, None, None, None) == adot.E_INVALID_ARG
     assert L.adot_fluctuations(None, None, None, 0, None, None, None, 0) == adot.E_INVALID_ARG
     assert L.adot_autotune(None, 8, None, None, None) == adot.E_INVALID_ARG
+    assert L.adot_checkpoint_size(None, None) == adot.E_INVALID_ARG
+    assert L.adot_checkpoint_save(None, None, 0, 0) == adot.E_INVALID_ARG
+    assert L.adot_checkpoint_load(None, None, 0, 0) == adot.E_INVALID_ARG
     L.adot_destroy(None)
 
 
