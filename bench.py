@@ -240,7 +240,14 @@ def surrogate_leg(args, adot, W, P, n, stream, dev, local, time_steps, ref64):
             ss.set_state(P.h, P.q, P.z)
             adot.adot_step(ss.ctx, 6)
             ms_t = time_steps(ss, 480)
-        out.update({"cell_updates_per_s": n * 480 / (ms_t * 1e-3),
+            # the same steps with the mma.sync inference engine
+            net.set_engine(1)
+            ss.set_state(P.h, P.q, P.z)
+            adot.adot_step(ss.ctx, 6)
+            ms_m = time_steps(ss, 480)
+            net.set_engine(0)
+        out.update({"cell_updates_per_s": n * 480 / (ms_t * 1e-3), "engine": "tcgen05",
+                    "cell_updates_per_s_mma_sync": n * 480 / (ms_m * 1e-3),
                     "infer_flops_per_edge": 2 * 51200,
                     "fallback_fraction": fb / max(edges, 1)})
         if ref64:

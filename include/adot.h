@@ -259,6 +259,9 @@ void adot_mlp_destroy(adot_mlp* mlp);
 /* Parameters in (host [ADOT_MLP_PARAMS]); resets the Adam moments and step. */
 adot_status adot_mlp_set_params(adot_mlp* mlp, const float* params);
 adot_status adot_mlp_get_params(adot_mlp* mlp, float* params);
+/* Engine of the surrogate step's fused inference: 0 = tcgen05 (default),
+ * 1 = mma.sync. ADOT_E_INVALID_ARG for another value. */
+adot_status adot_mlp_set_engine(adot_mlp* mlp, int engine);
 /* Training set: raw inputs X [n][7] and labels T [n][9] (float32, host or
  * device). Sets the standardisation (per-column mean and standard deviation)
  * and the training box (per-input min/max widened by 5% of the range). */
@@ -268,8 +271,12 @@ adot_status adot_mlp_set_data(adot_mlp* mlp, const float* X, const float* T, int
  * NULL): input lower bounds[7], upper bounds[7]. */
 adot_status adot_mlp_get_stats(adot_mlp* mlp, float* stats32, float* box14);
 /* Forward pass of n <= max_batch standardised inputs Xs [n][7] (host) to
- * standardised outputs Y [n][9] (host); fused = 1 uses the single-kernel
- * inference path of the surrogate step, 0 the per-layer training kernels. */
+ * standardised outputs Y [n][9] (host). fused = 0: the per-layer training
+ * kernels (mma.sync); 1: the single-kernel inference on mma.sync with the
+ * tanhf GELU; 2: the single-kernel inference on the 5th-generation tensor
+ * cores (tcgen05.mma, accumulators in tensor memory) with the tanh.approx GELU,
+ * the default engine of the surrogate step. ADOT_E_TIMEOUT if a bounded
+ * device-side wait for the tensor cores ran out. */
 adot_status adot_mlp_forward(adot_mlp* mlp, const float* Xs, int64_t n, float* Y, int fused);
 /* Loss and gradient (host [ADOT_MLP_PARAMS]) of the mean squared error on a
  * batch of standardised inputs Xs [n][7] and targets Ts [n][9] (host). */

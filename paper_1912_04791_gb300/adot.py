@@ -90,6 +90,7 @@ def lib() -> ctypes.CDLL:
             "adot_mlp_destroy": ([_P], None),
             "adot_mlp_set_params": ([_P, _P], i32),
             "adot_mlp_get_params": ([_P, _P], i32),
+            "adot_mlp_set_engine": ([_P, i32], i32),
             "adot_mlp_set_data": ([_P, _P, _P, i64, i32], i32),
             "adot_mlp_get_stats": ([_P, _P, _P], i32),
             "adot_mlp_forward": ([_P, _P, i64, _P, i32], i32),
@@ -441,7 +442,12 @@ class Mlp:
         _check(lib().adot_mlp_get_stats(self.ptr, st.ctypes.data, box.ctypes.data), "adot_mlp_get_stats")
         return st, box
 
+    def set_engine(self, engine: int) -> None:
+        """Fused inference engine of the surrogate step: 0 = tcgen05, 1 = mma.sync."""
+        _check(lib().adot_mlp_set_engine(self.ptr, int(engine)), "adot_mlp_set_engine")
+
     def forward(self, Xs, fused=False) -> np.ndarray:
+        """fused: 0/False per-layer kernels, 1/True mma.sync fused, 2 tcgen05 fused."""
         Xs = _f32(Xs)
         n = Xs.shape[0]
         Y = np.empty((n, 9), dtype=np.float32)

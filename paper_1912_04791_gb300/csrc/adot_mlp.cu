@@ -644,6 +644,317 @@ __global__ void __launch_bounds__(kInferThreads, 1)
   }
 }
 
+// --------------------------------------------------------------------------
+// fused inference on the 5th-generation tensor cores (tcgen05.mma + TMEM)
+// --------------------------------------------------------------------------
+// Each layer is one product D[128 x N] = A[128 x K] B[N x K]^T over a tile of
+// 128 rows (edges), issued by one thread as K/16 tcgen05.mma of kind::f16
+// (bf16 operands, float32 accumulator in tensor memory). Both operands sit in
+// shared memory in the K-major layout without swizzle: 8-row x 16-byte core
+// matrices, element (r, k) at (r/8)*16K + (k/8)*128 + (r%8)*16 + (k%8)*2 bytes,
+// so the descriptors take LBO = 128 B (next core matrix along K) and
+// SBO = 16K B (next 8-row group).
+// A CTA runs two independent 128-thread groups, each with its own activation
+// tile, 128 TMEM columns and mbarrier: one group's epilogue (TMEM -> registers,
+// bias, GELU, bf16, shared memory) overlaps the other group's products.
+// Thread i of a group owns row i of its tile: it builds the row's inputs, and
+// its warp (lane quadrant i/32) reads row i of the accumulator.
+
+constexpr int kTcThreads = 256;
+constexpr int kTcRows = 128;
+__host__ __device__ constexpr uint32_t tc_w_off(int l) {
+  return l == 0 ? 0u : (l < kLayers - 1 ? 4096u + (uint32_t)(l - 1) * 32768u : 102400u);
+}
+constexpr uint32_t kTcBiasOff = 106496;  // after the weights (4 + 3 x 32 + 4 KB)
+constexpr uint32_t kTcActOff = 109568;   // 1024-aligned, after the biases
+constexpr uint32_t kTcActBytes = (uint32_t)kTcRows * kHid * 2;
+constexpr size_t kTcSmem = kTcActOff + 2 * kTcActBytes + 1024;  // + base alignment
+static_assert(tc_w_off(kLayers - 1) + 16 * kHid * 2 == kTcBiasOff, "weight block size");
+static_assert(kTcBiasOff + sizeof(float) * kBTotal <= kTcActOff, "bias block size");
+
+__device__ __forceinline__ uint32_t tc_canon(int r, int kc, int K) {
+  return (uint32_t)((r >> 3) * (K * 16) + kc * 128 + (r & 7) * 16);
+}
+
+// Shared-memory matrix descriptor: start address, LBO, SBO (all >> 4), the
+// descriptor version of this architecture family (bit 46), no swizzle.
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, int K) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(128u >> 4) << 16) |
+         ((uint64_t)(((uint32_t)K * 16u >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16: float32 D, bf16 A and B, both K-major,
+// N >> 3 at bit 17, M >> 4 at bit 24 (M = 128).
+__host__ __device__ constexpr uint32_t tc_idesc(int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(kTcRows >> 4) << 24);
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t da, uint64_t db, uint32_t idesc,
+                                       uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(da), "l"(db), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void group_bar(int id) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(kTcRows) : "memory");
+}
+
+// Waits for phase `parity` of an mbarrier for at most 2^31 clock cycles
+// (about a second); false when the wait ran out.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity) {
+  const long long t0 = clock64();
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > (1ll << 31)) return false;
+  }
+}
+
+__device__ __forceinline__ void tmem_ld_x32(uint32_t taddr, uint32_t r[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+        "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+        "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+        "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_ld_x16(uint32_t taddr, uint32_t r[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15},"
+      " [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+        "=r"(r[15])
+      : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// GELU in the tanh form with the single-instruction tanh approximation
+// (relative error about 2^-11, below the bfloat16 rounding that follows).
+__device__ __forceinline__ float gelu_tc(float x) {
+  float t;
+  const float u = x * fmaf(0.0356774081f, x * x, 0.7978845608f);  // sqrt(2/pi) (x + 0.044715 x^3)
+  asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(u));
+  const float hx = 0.5f * x;
+  return fmaf(hx, t, hx);
+}
+
+// EDGES: inputs from the edges of a float-float state, outputs |A|_Psi into
+// absA [9][n+1] (NaN in row 0 marks a fallback edge). Otherwise: inputs are
+// rows of X [n][16] bf16 (standardised), outputs Y [n][16] float32.
+template <bool EDGES>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_mlp_tc(const InferParams P, const StepParams sp, const StateF32 st, int slot,
+             float* __restrict__ absA, unsigned long long* fallback_count,
+             const __nv_bfloat16* __restrict__ Xrows, int64_t n_rows, float* __restrict__ Yrows,
+             unsigned* status) {
+  extern __shared__ unsigned char tc_raw[];
+  __shared__ __align__(8) uint64_t s_mbar[2];
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_timeout[2];
+  const uint32_t raw = smem_addr(tc_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  unsigned char* sm = tc_raw + (base - raw);
+  float* sBias = reinterpret_cast<float*>(sm + kTcBiasOff);
+
+  // weights into the core-matrix layout, biases as they are
+  for (int l = 0; l < kLayers; ++l) {
+    const int K = dim_in(l), N = dim_out(l), kcs = K / 8;
+    const __nv_bfloat16* W = P.W + w_offset(l);
+    for (int i = threadIdx.x; i < N * kcs; i += blockDim.x) {
+      const int n = i / kcs, kc = i % kcs;
+      *reinterpret_cast<uint4*>(sm + tc_w_off(l) + tc_canon(n, kc, K)) =
+          *reinterpret_cast<const uint4*>(W + n * K + kc * 8);
+    }
+  }
+  for (int i = threadIdx.x; i < kBTotal; i += blockDim.x) sBias[i] = P.bias[i];
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&s_mbar[0])) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&s_mbar[1])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_timeout[0] = s_timeout[1] = 0;
+  }
+  if (threadIdx.x < 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_addr(&s_tmem)),
+                 "r"(2 * kTcRows)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+
+  const int g = threadIdx.x >> 7, tg = threadIdx.x & (kTcRows - 1), quad = tg >> 5;
+  unsigned char* act = sm + kTcActOff + g * kTcActBytes;
+  const uint32_t act_s = base + kTcActOff + g * kTcActBytes;
+  const uint32_t mbar = smem_addr(&s_mbar[g]);
+  const uint32_t d_tmem = s_tmem + (uint32_t)(g * kTcRows);           // this group's 128 columns
+  const uint32_t t_row = d_tmem + ((uint32_t)(quad * 32) << 16);      // this warp's lane quadrant
+  const int64_t n_items = EDGES ? sp.n + 1 : n_rows;
+  const int64_t n_tiles = (n_items + kTcRows - 1) / kTcRows;
+  uint32_t parity = 0;
+  unsigned long long fb = 0;
+
+  for (int64_t tile = (int64_t)blockIdx.x * 2 + g; tile < n_tiles; tile += (int64_t)gridDim.x * 2) {
+    const int64_t item = tile * kTcRows + tg;
+    bool ok = false;
+    // layer-0 operand: 16 bf16 inputs of this row (K = 16 core-matrix layout)
+    {
+      uint32_t pk[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      if (EDGES) {
+        if (item < n_items) {
+          float2 wl[3], wr[3];
+          load_edge<float>(sp, st, item, slot, wl, wr);
+          const float x[kIn] = {wl[0].x, wl[1].x, wl[2].x, wr[0].x, wr[1].x, wr[2].x, P.Ag};
+          float z[kIn];
+          ok = edge_inputs(P, x, sp.lf.g, z);
+          if (!ok) ++fb;
+          pk[0] = pack_bf16(z[0], z[1]);
+          pk[1] = pack_bf16(z[2], z[3]);
+          pk[2] = pack_bf16(z[4], z[5]);
+          pk[3] = pack_bf16(z[6], 0.0f);
+        }
+      } else if (item < n_items) {
+        const uint4 a = *reinterpret_cast<const uint4*>(Xrows + item * kPad);
+        const uint4 b = *reinterpret_cast<const uint4*>(Xrows + item * kPad + 8);
+        pk[0] = a.x; pk[1] = a.y; pk[2] = a.z; pk[3] = a.w;
+        pk[4] = b.x; pk[5] = b.y; pk[6] = b.z; pk[7] = b.w;
+      }
+      *reinterpret_cast<uint4*>(act + tc_canon(tg, 0, kPad)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+      *reinterpret_cast<uint4*>(act + tc_canon(tg, 1, kPad)) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+    }
+    fence_async_smem();
+    tc_fence_before();
+    group_bar(1 + g);
+    if (s_timeout[g]) break;
+
+    for (int l = 0; l < kLayers; ++l) {
+      const int K = dim_in(l);
+      if (tg == 0) {
+        tc_fence_after();
+        const uint32_t w_s = base + tc_w_off(l);
+        const uint32_t idesc = tc_idesc(dim_out(l));
+        for (int ks = 0; ks < K / 16; ++ks)
+          tc_mma(d_tmem, tc_desc(act_s + ks * 256, K), tc_desc(w_s + ks * 256, K), idesc, ks > 0);
+        tc_commit(mbar);
+      }
+      // warp-uniform, since tcgen05.ld below is a .sync.aligned instruction
+      const bool done = __all_sync(0xffffffffu, mbar_wait_bounded(mbar, parity));
+      parity ^= 1u;
+      if (!done) s_timeout[g] = 1;
+      tc_fence_after();
+      if (done && l < kLayers - 1) {
+        // hidden layer: bias + GELU, bf16, back into the (now free) A operand
+        const float* b = sBias + b_offset(l);
+#pragma unroll 1
+        for (int c0 = 0; c0 < kHid; c0 += 32) {
+          uint32_t r[32];
+          tmem_ld_x32(t_row + (uint32_t)c0, r);
+          tmem_wait_ld();
+          uint32_t pk[16];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const float4 bb = *reinterpret_cast<const float4*>(b + c0 + 4 * j);
+            pk[2 * j] = pack_bf16(gelu_tc(__uint_as_float(r[4 * j]) + bb.x),
+                                  gelu_tc(__uint_as_float(r[4 * j + 1]) + bb.y));
+            pk[2 * j + 1] = pack_bf16(gelu_tc(__uint_as_float(r[4 * j + 2]) + bb.z),
+                                      gelu_tc(__uint_as_float(r[4 * j + 3]) + bb.w));
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            *reinterpret_cast<uint4*>(act + tc_canon(tg, c0 / 8 + u, kHid)) =
+                make_uint4(pk[4 * u], pk[4 * u + 1], pk[4 * u + 2], pk[4 * u + 3]);
+        }
+      } else if (done) {
+        // output layer: 16 columns (9 used)
+        uint32_t r[16];
+        tmem_ld_x16(t_row, r);
+        tmem_wait_ld();
+        const float* b = sBias + b_offset(l);
+        if (item < n_items) {
+          if (EDGES) {
+#pragma unroll
+            for (int k = 0; k < kOut; ++k) {
+              float v = (__uint_as_float(r[k]) + b[k]) * P.stats[2 * kIn + kOut + k] + P.stats[2 * kIn + k];
+              if (k == 0 && !ok) v = __int_as_float(0x7fc00000);
+              absA[(int64_t)k * n_items + item] = v;
+            }
+          } else {
+#pragma unroll
+            for (int k = 0; k < kPad; k += 4)
+              *reinterpret_cast<float4*>(Yrows + item * kPad + k) =
+                  make_float4(__uint_as_float(r[k]) + b[k], __uint_as_float(r[k + 1]) + b[k + 1],
+                              __uint_as_float(r[k + 2]) + b[k + 2], __uint_as_float(r[k + 3]) + b[k + 3]);
+          }
+        }
+      }
+      if (l < kLayers - 1) {
+        fence_async_smem();
+        tc_fence_before();
+        group_bar(1 + g);
+        if (s_timeout[g]) break;
+      } else {
+        tc_fence_before();
+      }
+    }
+    if (s_timeout[g]) break;
+  }
+  // a wait that ran out: give the products in flight one more bounded wait
+  if (s_timeout[g] && tg == 0) {
+    mbar_wait_bounded(mbar, parity ^ 1u);
+    if (status) atomicOr(status, ST_TIMEOUT);
+  }
+  if (EDGES) {
+    fb += __shfl_xor_sync(0xffffffffu, fb, 16);
+    fb += __shfl_xor_sync(0xffffffffu, fb, 8);
+    fb += __shfl_xor_sync(0xffffffffu, fb, 4);
+    fb += __shfl_xor_sync(0xffffffffu, fb, 2);
+    fb += __shfl_xor_sync(0xffffffffu, fb, 1);
+    if ((threadIdx.x & 31) == 0 && fb) atomicAdd(fallback_count, fb);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(s_tmem), "r"(2 * kTcRows)
+                 : "memory");
+  }
+}
+
 // Column minima and maxima of the raw inputs X [n][7].
 __global__ void k_minmax(const float* __restrict__ X, int64_t n, float* out /* [2][7] */) {
   const int c = blockIdx.x;
@@ -710,6 +1021,8 @@ struct adot_mlp {
   uint64_t graph_seed;
   double graph_lr;
   int64_t graph_steps;
+  int engine;          // fused inference: 0 = tcgen05 (default), 1 = mma.sync
+  unsigned* d_status;  // sticky ST_* bits of the fused inference kernels
 };
 
 namespace {
@@ -739,6 +1052,10 @@ cudaError_t set_layer_attributes() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_mlp_forward_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)infer_smem_bytes());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_mlp_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_mlp_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
   return e;
 }
 
@@ -820,7 +1137,7 @@ void mlp_free(adot_mlp* m) {
   if (m->graph_ready) cudaGraphExecDestroy(m->graph);
   void* ptrs[] = {m->d.master, m->d.m, m->d.v, m->d.grad, m->d.W, m->d.Wt, m->d.stats, m->d.step,
                   m->d_ident, m->X, m->T, m->Xb, m->Tb, m->Y, m->dY, m->loss_part, m->loss_hist,
-                  m->idx, m->tmpX, m->tmpT};
+                  m->idx, m->tmpX, m->tmpT, m->d_status};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (int i = 0; i < 4; ++i) {
@@ -869,9 +1186,17 @@ cudaError_t launch_mlp_edges(const adot_mlp* m, const StepParams& sp, StateF32 s
   P.fr_lo = fr_lo;
   P.fr_hi = fr_hi;
   P.Ag = Ag;
-  constexpr size_t sm = infer_smem_bytes();
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device);
+  if (m->engine == 0) {
+    // two 128-row tiles in flight per CTA, one CTA per SM
+    const int64_t tiles = (sp.n + 1 + kTcRows - 1) / kTcRows;
+    const int grid = (int)imin64((tiles + 1) / 2, sms);
+    k_mlp_tc<true><<<grid, kTcThreads, kTcSmem, s>>>(P, sp, st, slot, absA, fb, nullptr, 0, nullptr,
+                                                     &sp.ctl->status);
+    return cudaGetLastError();
+  }
+  constexpr size_t sm = infer_smem_bytes();
   const int64_t tiles = (sp.n + 1 + kInferRows - 1) / kInferRows;
   const int grid = (int)imin64(tiles, sms);
   k_mlp_edges<<<grid, kInferThreads, sm, s>>>(P, sp, st, slot, absA, fb);
@@ -930,6 +1255,7 @@ adot_status adot_mlp_create(int64_t max_batch, void* cuda_stream, adot_mlp** out
   al((void**)&m->idx, sizeof(int64_t) * B);
   al((void**)&m->tmpX, sizeof(float) * kIn * B);
   al((void**)&m->tmpT, sizeof(float) * kOut * B);
+  al((void**)&m->d_status, sizeof(unsigned));
   if (e == cudaSuccess) {
     float ident[32];
     for (int i = 0; i < 32; ++i) ident[i] = 0.0f;
@@ -951,6 +1277,12 @@ void adot_mlp_destroy(adot_mlp* m) {
   if (!m) return;
   cudaStreamSynchronize(m->stream);
   mlp_free(m);
+}
+
+adot_status adot_mlp_set_engine(adot_mlp* m, int engine) {
+  if (!m || engine < 0 || engine > 1) return ADOT_E_INVALID_ARG;
+  m->engine = engine;
+  return ADOT_OK;
 }
 
 adot_status adot_mlp_set_params(adot_mlp* m, const float* packed) {
@@ -1026,7 +1358,20 @@ adot_status adot_mlp_forward(adot_mlp* m, const float* Xs, int64_t n, float* Y, 
   if (!m || !Xs || !Y || n < 1 || n > m->max_batch) return ADOT_E_INVALID_ARG;
   adot_status st = upload_batch(m, Xs, nullptr, n);
   if (st) return st;
-  if (fused) {
+  if (fused == 2) {
+    InferParams P{};
+    P.W = m->d.W;
+    P.bias = m->d.master + kWTotal;
+    P.stats = m->d_ident;
+    StepParams sp{};
+    const int64_t tiles = (n + kTcRows - 1) / kTcRows;
+    int sms = 152;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device);
+    CKM(cudaMemsetAsync(m->d_status, 0, sizeof(unsigned), m->stream));
+    k_mlp_tc<false><<<(unsigned)imin64((tiles + 1) / 2, sms), kTcThreads, kTcSmem, m->stream>>>(
+        P, sp, StateF32{}, 0, nullptr, nullptr, m->Xb, n, m->Y, m->d_status);
+    CKM(cudaGetLastError());
+  } else if (fused) {
     constexpr size_t sm = infer_smem_bytes();
     const int64_t tiles = (n + kInferRows - 1) / kInferRows;
     k_mlp_forward_fused<<<(unsigned)imin64(tiles, 152), kInferThreads, sm, m->stream>>>(
@@ -1036,8 +1381,11 @@ adot_status adot_mlp_forward(adot_mlp* m, const float* Xs, int64_t n, float* Y, 
     CKM(forward_batch(m, n, m->stream));
   }
   std::vector<float> y((size_t)n * kPad);
+  unsigned dev_status = 0;
   CKM(cudaMemcpyAsync(y.data(), m->Y, sizeof(float) * kPad * n, cudaMemcpyDeviceToHost, m->stream));
+  CKM(cudaMemcpyAsync(&dev_status, m->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, m->stream));
   CKM(cudaStreamSynchronize(m->stream));
+  if (dev_status & ST_TIMEOUT) return ADOT_E_TIMEOUT;
   for (int64_t i = 0; i < n; ++i)
     for (int k = 0; k < kOut; ++k) Y[i * kOut + k] = y[i * kPad + k];
   return ADOT_OK;

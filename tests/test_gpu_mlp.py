@@ -43,6 +43,38 @@ def test_forward_matches_reference(gpu, n):
     assert np.abs(yf - y).max() <= 1e-5 * sc
 
 
+@pytest.mark.parametrize("n", [1, 127, 128, 129, 256, 257, 1000, 4099, 8192])
+def test_forward_tcgen05_matches_reference(gpu, n):
+    """The tcgen05/TMEM inference kernel (two 128-row tiles per CTA) against
+    the reference with bf16 operands. Its GELU takes tanh.approx (relative error
+    below 2^-10.9), which moves a pre-rounding activation by at most about
+    2.5e-4 |x|: a bfloat16 rounding flips in a few per cent of activations, the
+    same size of effect as the float32/float64 difference; the bound is the
+    per-layer-kernel one with the median doubled."""
+    theta = _theta(1)
+    rng = np.random.default_rng(100 + n)
+    X = rng.standard_normal((n, 7)).astype(np.float32)
+    ref, _ = M.forward(theta, X.astype(np.float64), bf16=True)
+    with gpu.Mlp(8192) as net:
+        net.set_params(theta)
+        y_tc = net.forward(X, fused=2)
+        y_mma = net.forward(X, fused=1)
+    sc = np.abs(ref).max()
+    err = np.abs(y_tc - ref)
+    print(f"n={n} tcgen05 vs reference: max {err.max() / sc:.2e}, median {np.median(err) / sc:.2e} of scale")
+    assert np.isfinite(y_tc).all()
+    assert err.max() <= 1e-2 * sc and np.median(err) <= 2e-4 * sc, (err.max() / sc, np.median(err) / sc)
+    assert np.abs(y_tc - y_mma).max() <= 1e-2 * sc
+
+
+def test_engine_value_checked(gpu):
+    with gpu.Mlp(64) as net:
+        net.set_engine(1)
+        net.set_engine(0)
+        with pytest.raises(gpu.AdotError):
+            net.set_engine(2)
+
+
 def test_gradient_matches_reference(gpu):
     theta = _theta(2)
     rng = np.random.default_rng(3)
@@ -111,12 +143,14 @@ def test_harvest_labels_match_oracle(gpu):
         assert (np.abs(T - ref) <= 1e-5 * sc).all()
 
 
-def test_surrogate_all_fallback_equals_analytic_path(gpu):
+@pytest.mark.parametrize("engine", [0, 1])
+def test_surrogate_all_fallback_equals_analytic_path(gpu, engine):
     """With the fallback band covering every Froude number each edge takes the
     analytic eigenstructure: the surrogate step equals the plain float32 step."""
     P = W.smooth_periodic(3000)
     X, T = _edge_dataset(500, 8)
     with gpu.Mlp(512) as net:
+        net.set_engine(engine)
         net.set_params(_theta(9))
         net.set_data(X, T)
         with gpu.Solver(gpu.config_for(P, gpu.FP32, block_threads=256, reg_cap=64)) as s:
@@ -132,6 +166,50 @@ def test_surrogate_all_fallback_equals_analytic_path(gpu):
         b = s.get_state()
     for x, y in zip(a, b):
         assert np.array_equal(x, y)
+
+
+@pytest.fixture(scope="module")
+def trained_smooth_net(gpu):
+    """Parameters, data and oracle run of a network trained on edges harvested
+    from the smooth periodic problem (N = 4096)."""
+    P = W.smooth_periodic(4096)
+    with gpu.Solver(gpu.config_for(P, gpu.FP32)) as s:
+        s.set_state(P.h, P.q, P.z)
+        Xs, Ts = [], []
+        for k in range(6):
+            X, T = gpu.adot_harvest(s.ctx, 20000, seed=100 + k)
+            Xs.append(X), Ts.append(T)
+            s.step(40)
+    X, T = np.concatenate(Xs), np.concatenate(Ts)
+    with gpu.Mlp(8192) as net:
+        net.set_params(_theta(10, 0.5))
+        net.set_data(X, T)
+        h = net.train(1500, 8192, lr=2e-3, seed=3)
+        theta = net.get_params()
+    return P, X, T, theta, h
+
+
+@pytest.mark.parametrize("engine", [0, 1])
+def test_trained_surrogate_engines_agree(gpu, trained_smooth_net, engine):
+    """The tcgen05 and mma.sync inference engines drive the same trained
+    network through 30 surrogate steps: same fallback count, increments within
+    1e-3 (L1, relative) of each other."""
+    P, X, T, theta, _ = trained_smooth_net
+    out = []
+    for eng in (engine, 1 - engine):
+        with gpu.Mlp(512) as net:
+            net.set_engine(eng)
+            net.set_params(theta)
+            net.set_data(X, T)
+            with gpu.Solver(gpu.config_for(P, gpu.FP32)) as s:
+                s.set_state(P.h, P.q, P.z)
+                gpu.adot_set_surrogate(s.ctx, net, 0.8, 1.2)
+                s.step(30)
+                out.append((s.get_state(), gpu.adot_surrogate_stats(s.ctx)))
+    (a, sa), (b, sb) = out
+    assert sa == sb
+    for x, y, x0 in zip(a, b, (P.h, P.q, P.z)):
+        assert np.abs((x - x0) - (y - x0)).sum() <= 1e-3 * np.abs(y - x0).sum()
 
 
 def test_trained_surrogate_step(gpu):
