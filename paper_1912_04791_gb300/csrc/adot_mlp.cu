@@ -654,13 +654,17 @@ __global__ void __launch_bounds__(kInferThreads, 1)
 // matrices, element (r, k) at (r/8)*16K + (k/8)*128 + (r%8)*16 + (k%8)*2 bytes,
 // so the descriptors take LBO = 128 B (next core matrix along K) and
 // SBO = 16K B (next 8-row group).
-// A CTA runs two independent 128-thread groups, each with its own activation
+// A CTA runs two independent groups of 8 warps, each with its own activation
 // tile, 128 TMEM columns and mbarrier: one group's epilogue (TMEM -> registers,
 // bias, GELU, bf16, shared memory) overlaps the other group's products.
-// Thread i of a group owns row i of its tile: it builds the row's inputs, and
-// its warp (lane quadrant i/32) reads row i of the accumulator.
+// Warp w of a group reads TMEM lane quadrant w % 4 (rows 32 (w % 4) + lane)
+// and columns 64 (w / 4) .. + 63; the first four warps also build the tile's
+// inputs (one row per thread) and write the output rows.
+// The hidden activations are stored as 2 GELU(v) = v (1 + tanh(u)) and the
+// weights of layers 1-4 as W / 2 (both exact scalings by powers of two, so the
+// bf16 roundings and products are those of GELU(v) and W).
 
-constexpr int kTcThreads = 256;
+constexpr int kTcThreads = 512;
 constexpr int kTcRows = 128;
 __host__ __device__ constexpr uint32_t tc_w_off(int l) {
   return l == 0 ? 0u : (l < kLayers - 1 ? 4096u + (uint32_t)(l - 1) * 32768u : 102400u);
@@ -716,8 +720,8 @@ __device__ __forceinline__ void tc_fence_after() {
 __device__ __forceinline__ void fence_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
-__device__ __forceinline__ void group_bar(int id) {
-  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(kTcRows) : "memory");
+__device__ __forceinline__ void group_bar(int id, int threads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
 }
 
 // Waits for phase `parity` of an mbarrier for at most 2^31 clock cycles
@@ -759,16 +763,56 @@ __device__ __forceinline__ void tmem_ld_x16(uint32_t taddr, uint32_t r[16]) {
       : "r"(taddr));
 }
 
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// tcgen05.wait::ld that also marks the loaded registers as written by it, so
+// that no use of them is scheduled before the wait.
+__device__ __forceinline__ void tmem_wait_ld(uint32_t r[32]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]),
+                 "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]),
+                 "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]),
+                 "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]),
+                 "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+               :
+               : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld16(uint32_t r[16]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]),
+                 "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]),
+                 "+r"(r[14]), "+r"(r[15])
+               :
+               : "memory");
+}
 
-// GELU in the tanh form with the single-instruction tanh approximation
-// (relative error about 2^-11, below the bfloat16 rounding that follows).
-__device__ __forceinline__ float gelu_tc(float x) {
-  float t;
-  const float u = x * fmaf(0.0356774081f, x * x, 0.7978845608f);  // sqrt(2/pi) (x + 0.044715 x^3)
-  asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(u));
-  const float hx = 0.5f * x;
-  return fmaf(hx, t, hx);
+// 2 GELU(v) = v (1 + tanh(u)), u = sqrt(2/pi) (v + 0.044715 v^3), v = a + b,
+// for two accumulators a and biases b at once with the packed float32x2
+// arithmetic, the tanh from the single-instruction approximation (relative
+// error about 2^-11, below the bf16 rounding that follows); returns the bf16
+// pair (first value in the low half). c1 and c0 hold 0.044715 sqrt(2/pi) and
+// sqrt(2/pi) in both halves.
+__device__ __forceinline__ uint32_t gelu2x_bf16(uint32_t a0, uint32_t a1, uint32_t b0, uint32_t b1,
+                                                uint64_t c1, uint64_t c0) {
+  uint32_t out;
+  asm("{\n"
+      " .reg .b64 x, b, v, v2, p, u, t, y;\n"
+      " .reg .b32 u0, u1, t0, t1, y0, y1;\n"
+      " mov.b64 x, {%1, %2};\n"
+      " mov.b64 b, {%3, %4};\n"
+      " add.rn.f32x2 v, x, b;\n"
+      " mul.rn.f32x2 v2, v, v;\n"
+      " fma.rn.f32x2 p, v2, %5, %6;\n"
+      " mul.rn.f32x2 u, p, v;\n"
+      " mov.b64 {u0, u1}, u;\n"
+      " tanh.approx.f32 t0, u0;\n"
+      " tanh.approx.f32 t1, u1;\n"
+      " mov.b64 t, {t0, t1};\n"
+      " fma.rn.f32x2 y, v, t, v;\n"
+      " mov.b64 {y0, y1}, y;\n"
+      " cvt.rn.bf16x2.f32 %0, y1, y0;\n"
+      "}\n"
+      : "=r"(out)
+      : "r"(a0), "r"(a1), "r"(b0), "r"(b1), "l"(c1), "l"(c0));
+  return out;
 }
 
 // EDGES: inputs from the edges of a float-float state, outputs |A|_Psi into
@@ -789,14 +833,20 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   unsigned char* sm = tc_raw + (base - raw);
   float* sBias = reinterpret_cast<float*>(sm + kTcBiasOff);
 
-  // weights into the core-matrix layout, biases as they are
+  // weights into the core-matrix layout (layers 1-4 halved), biases as they are
+  const __nv_bfloat162 half2 = __floats2bfloat162_rn(0.5f, 0.5f);
   for (int l = 0; l < kLayers; ++l) {
     const int K = dim_in(l), N = dim_out(l), kcs = K / 8;
     const __nv_bfloat16* W = P.W + w_offset(l);
     for (int i = threadIdx.x; i < N * kcs; i += blockDim.x) {
       const int n = i / kcs, kc = i % kcs;
-      *reinterpret_cast<uint4*>(sm + tc_w_off(l) + tc_canon(n, kc, K)) =
-          *reinterpret_cast<const uint4*>(W + n * K + kc * 8);
+      uint4 v = *reinterpret_cast<const uint4*>(W + n * K + kc * 8);
+      if (l > 0) {
+        __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&v);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) h[j] = __hmul2(h[j], half2);
+      }
+      *reinterpret_cast<uint4*>(sm + tc_w_off(l) + tc_canon(n, kc, K)) = v;
     }
   }
   for (int i = threadIdx.x; i < kBTotal; i += blockDim.x) sBias[i] = P.bias[i];
@@ -818,22 +868,30 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   __syncthreads();
   tc_fence_after();
 
-  const int g = threadIdx.x >> 7, tg = threadIdx.x & (kTcRows - 1), quad = tg >> 5;
+  constexpr int kGroup = kTcThreads / 2;
+  const int g = threadIdx.x / kGroup, tg = threadIdx.x % kGroup;
+  const int wg = tg >> 5, lane = tg & 31;
+  const int row = ((wg & 3) << 5) | lane;  // accumulator row (TMEM lane) of this thread
+  const int col0 = (wg >> 2) * 64;          // its 64 accumulator columns
+  const bool lead = wg < 4;                 // builds inputs, writes outputs
   unsigned char* act = sm + kTcActOff + g * kTcActBytes;
   const uint32_t act_s = base + kTcActOff + g * kTcActBytes;
   const uint32_t mbar = smem_addr(&s_mbar[g]);
   const uint32_t d_tmem = s_tmem + (uint32_t)(g * kTcRows);           // this group's 128 columns
-  const uint32_t t_row = d_tmem + ((uint32_t)(quad * 32) << 16);      // this warp's lane quadrant
+  const uint32_t t_row = d_tmem + ((uint32_t)((wg & 3) * 32) << 16);  // this warp's lane quadrant
   const int64_t n_items = EDGES ? sp.n + 1 : n_rows;
   const int64_t n_tiles = (n_items + kTcRows - 1) / kTcRows;
+  const float c1f = 0.0356774081f, c0f = 0.7978845608f;  // 0.044715 sqrt(2/pi), sqrt(2/pi)
+  const uint64_t c1 = ((uint64_t)__float_as_uint(c1f) << 32) | __float_as_uint(c1f);
+  const uint64_t c0 = ((uint64_t)__float_as_uint(c0f) << 32) | __float_as_uint(c0f);
   uint32_t parity = 0;
   unsigned long long fb = 0;
 
   for (int64_t tile = (int64_t)blockIdx.x * 2 + g; tile < n_tiles; tile += (int64_t)gridDim.x * 2) {
-    const int64_t item = tile * kTcRows + tg;
+    const int64_t item = tile * kTcRows + row;
     bool ok = false;
     // layer-0 operand: 16 bf16 inputs of this row (K = 16 core-matrix layout)
-    {
+    if (lead) {
       uint32_t pk[8] = {0, 0, 0, 0, 0, 0, 0, 0};
       if (EDGES) {
         if (item < n_items) {
@@ -854,12 +912,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         pk[0] = a.x; pk[1] = a.y; pk[2] = a.z; pk[3] = a.w;
         pk[4] = b.x; pk[5] = b.y; pk[6] = b.z; pk[7] = b.w;
       }
-      *reinterpret_cast<uint4*>(act + tc_canon(tg, 0, kPad)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-      *reinterpret_cast<uint4*>(act + tc_canon(tg, 1, kPad)) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+      *reinterpret_cast<uint4*>(act + tc_canon(row, 0, kPad)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+      *reinterpret_cast<uint4*>(act + tc_canon(row, 1, kPad)) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
     }
     fence_async_smem();
     tc_fence_before();
-    group_bar(1 + g);
+    group_bar(1 + g, kGroup);
     if (s_timeout[g]) break;
 
     for (int l = 0; l < kLayers; ++l) {
@@ -878,32 +936,36 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       if (!done) s_timeout[g] = 1;
       tc_fence_after();
       if (done && l < kLayers - 1) {
-        // hidden layer: bias + GELU, bf16, back into the (now free) A operand
-        const float* b = sBias + b_offset(l);
-#pragma unroll 1
-        for (int c0 = 0; c0 < kHid; c0 += 32) {
-          uint32_t r[32];
-          tmem_ld_x32(t_row + (uint32_t)c0, r);
-          tmem_wait_ld();
+        // hidden layer: 2 GELU(acc + bias) in bf16, back into the (now free) A operand;
+        // the next 32 columns load from TMEM while this chunk is processed
+        const float* b = sBias + b_offset(l) + col0;
+        uint32_t ra[32], rb[32];
+        tmem_ld_x32(t_row + (uint32_t)col0, ra);
+        tmem_wait_ld(ra);
+        tmem_ld_x32(t_row + (uint32_t)(col0 + 32), rb);
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+          uint32_t* r = half ? rb : ra;
+          if (half) tmem_wait_ld(rb);
+          const int c = col0 + 32 * half;
           uint32_t pk[16];
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
-            const float4 bb = *reinterpret_cast<const float4*>(b + c0 + 4 * j);
-            pk[2 * j] = pack_bf16(gelu_tc(__uint_as_float(r[4 * j]) + bb.x),
-                                  gelu_tc(__uint_as_float(r[4 * j + 1]) + bb.y));
-            pk[2 * j + 1] = pack_bf16(gelu_tc(__uint_as_float(r[4 * j + 2]) + bb.z),
-                                      gelu_tc(__uint_as_float(r[4 * j + 3]) + bb.w));
+            const float4 bb = *reinterpret_cast<const float4*>(b + 32 * half + 4 * j);
+            pk[2 * j] = gelu2x_bf16(r[4 * j], r[4 * j + 1], __float_as_uint(bb.x), __float_as_uint(bb.y), c1, c0);
+            pk[2 * j + 1] =
+                gelu2x_bf16(r[4 * j + 2], r[4 * j + 3], __float_as_uint(bb.z), __float_as_uint(bb.w), c1, c0);
           }
 #pragma unroll
           for (int u = 0; u < 4; ++u)
-            *reinterpret_cast<uint4*>(act + tc_canon(tg, c0 / 8 + u, kHid)) =
+            *reinterpret_cast<uint4*>(act + tc_canon(row, c / 8 + u, kHid)) =
                 make_uint4(pk[4 * u], pk[4 * u + 1], pk[4 * u + 2], pk[4 * u + 3]);
         }
-      } else if (done) {
+      } else if (done && lead) {
         // output layer: 16 columns (9 used)
         uint32_t r[16];
         tmem_ld_x16(t_row, r);
-        tmem_wait_ld();
+        tmem_wait_ld16(r);
         const float* b = sBias + b_offset(l);
         if (item < n_items) {
           if (EDGES) {
@@ -925,7 +987,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       if (l < kLayers - 1) {
         fence_async_smem();
         tc_fence_before();
-        group_bar(1 + g);
+        group_bar(1 + g, kGroup);
         if (s_timeout[g]) break;
       } else {
         tc_fence_before();
@@ -944,7 +1006,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     fb += __shfl_xor_sync(0xffffffffu, fb, 4);
     fb += __shfl_xor_sync(0xffffffffu, fb, 2);
     fb += __shfl_xor_sync(0xffffffffu, fb, 1);
-    if ((threadIdx.x & 31) == 0 && fb) atomicAdd(fallback_count, fb);
+    if (lane == 0 && fb) atomicAdd(fallback_count, fb);
   }
   tc_fence_before();
   __syncthreads();

@@ -20,7 +20,10 @@
 
 #include <float.h>
 
+#include <type_traits>
+
 #include "adot_internal.h"
+#include "adot_math_x2.cuh"
 
 namespace adot {
 
@@ -148,6 +151,10 @@ template <typename R, int LAW>
 __device__ __forceinline__ void edge_fluct(const StepParams& p, const typename Prec<R>::S wl[3],
                                            const typename Prec<R>::S wr[3], R dm[3], R dp[3],
                                            unsigned& flags) {
+  if constexpr (std::is_same<R, float>::value) {
+    edge_fluct_f32x2<LAW>(p.lf, p.ld, wl, wr, dm, dp, flags);
+    return;
+  }
   const R dh = Prec<R>::diff(wr[0], wl[0]);
   const R dq = Prec<R>::diff(wr[1], wl[1]);
   const R dz = Prec<R>::diff(wr[2], wl[2]);
