@@ -34,11 +34,15 @@ UNIT = "cell-updates/s"
 # FMUL thread instructions of one launch divided by the cells it updates.
 # Per kernel kind: the block kernel repeats 1 edge in 256, the warp-tile
 # kernel 1 in 32; that repeated work is removed from the executed counts
-# (636.1 x 255/256 and 648.3 x 31/32).
+# (636.1 x 255/256 and 648.3 x 31/32). The counts were taken on the all-scalar
+# build: evaluating two nodes per paired float32x2 instruction leaves the
+# arithmetic unchanged, and ncu's per-opcode thread counters omit the paired
+# instructions.
 FLOPS_PER_CELL_UPDATE = {"block": 633.6, "warp": 628.0}
 # DRAM read + write bytes per cell-update of one launch (ncu, N = 4e6): the
-# ~24 B read match the algorithmic read; part of the 24 B written is still in L2.
-DRAM_BYTES_PER_CELL_UPDATE = {"block": (96.09e6 + 59.29e6) / 4e6, "warp": (97.76e6 + 64.64e6) / 4e6}
+# ~24 B read match the algorithmic read; part of the 24 B written is still in
+# L2. None where the kernel changed after its capture.
+DRAM_BYTES_PER_CELL_UPDATE = {"block": None, "warp": (97.88e6 + 64.74e6) / 4e6}
 BYTES_PER_CELL_UPDATE = 48.0  # float-float state: 3 x 8 B read + 3 x 8 B written
 
 
@@ -240,15 +244,37 @@ def surrogate_leg(args, adot, W, P, n, stream, dev, local, time_steps, ref64):
             ss.set_state(P.h, P.q, P.z)
             adot.adot_step(ss.ctx, 6)
             ms_t = time_steps(ss, 480)
+            # the inference kernel alone (adot_surrogate_eval, no copy-out), per engine:
+            # CUDA events on the context's stream around each call, mean of 10 after 2
+            infer = {}
+            for eng, name in ((0, "tcgen05"), (1, "mma.sync")):
+                net.set_engine(eng)
+                ts = []
+                for i in range(12):
+                    a.record(stream)
+                    adot.adot_surrogate_eval(ss.ctx, n + 1, False)
+                    b.record(stream)
+                    torch.cuda.synchronize(dev)
+                    if i >= 2:
+                        ts.append(a.elapsed_time(b))
+                ms_i = float(np.mean(ts))
+                infer[name] = {"ms_per_launch": ms_i, "edges": n + 1,
+                               "tflops": (n + 1) * 2 * 51200 / (ms_i * 1e-3) / 1e12}
             # the same steps with the mma.sync inference engine
             net.set_engine(1)
             ss.set_state(P.h, P.q, P.z)
             adot.adot_step(ss.ctx, 6)
             ms_m = time_steps(ss, 480)
             net.set_engine(0)
+        peak = measured_peaks().get("bf16_tflops")
+        tc = infer["tcgen05"]["tflops"]
         out.update({"cell_updates_per_s": n * 480 / (ms_t * 1e-3), "engine": "tcgen05",
                     "cell_updates_per_s_mma_sync": n * 480 / (ms_m * 1e-3),
-                    "infer_flops_per_edge": 2 * 51200,
+                    "infer_flops_per_edge": 2 * 51200, "inference_kernel": infer,
+                    "roofline": {"bound": "tensor", "kernel": "k_mlp_tc<edges> (tcgen05, bf16, TMEM)",
+                                 "achieved": tc, "peak": peak, "unit": "TFLOP/s",
+                                 "frac": tc / peak if peak else None,
+                                 "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst; kernel timed alone)"},
                     "fallback_fraction": fb / max(edges, 1)})
         if ref64:
             for name, a_, b_, a0 in zip("hqz", got, ref64[1], (P.h, P.q, P.z)):
@@ -501,7 +527,8 @@ def main():
                        "parallelism": "replicas" if ws > 1 else "single"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": f_peak, "unit": "TFLOP/s",
                          "frac": achieved / f_peak,
-                         "traffic": DRAM_BYTES_PER_CELL_UPDATE[kind] * n,
+                         "traffic": (DRAM_BYTES_PER_CELL_UPDATE[kind] * n
+                                     if DRAM_BYTES_PER_CELL_UPDATE[kind] else None),
                          "traffic_note": "ncu dram read+write of one launch at N=4e6, scaled to N",
                          "kernel": f"{'k_step_warp' if kern == 2 else 'k_step'}<float,GRASS,{block},{max(reg_cap, 0)}>",
                          "peak_source": "152 SM x 128 FP32 lanes x 2 x 2070 MHz (derived)",

@@ -297,6 +297,14 @@ adot_status adot_mlp_train(adot_mlp* mlp, int64_t steps, int64_t batch, double l
 adot_status adot_set_surrogate(adot_ctx* ctx, adot_mlp* mlp, double fr_lo, double fr_hi);
 /* Edges evaluated and edges that fell back since the surrogate was attached. */
 adot_status adot_surrogate_stats(adot_ctx* ctx, int64_t* edges_out, int64_t* fallback_out);
+/* Evaluates the attached network on every edge 0..n of the current state
+ * without stepping (the first half of a surrogate step). absA (may be NULL:
+ * evaluate only) receives float32 [9][n+1]: row r holds entry r of the
+ * row-major |A|_Psi, de-standardised; row 0 is NaN on the edges that take the
+ * analytic eigenstructure instead, and *fallback_out (may be NULL) counts
+ * them. Host or device pointer per on_device. Waits for the stream. Does not
+ * change adot_surrogate_stats. ADOT_E_INVALID_ARG without a surrogate or a state. */
+adot_status adot_surrogate_eval(adot_ctx* ctx, float* absA, int on_device, int64_t* fallback_out);
 /* n edge samples of the current state (edge indices drawn with splitmix64 from
  * seed and the sample number): X [n][7] raw inputs and T [n][9] labels
  * |A|_Psi computed in float64, stored as float32 (host or device). Grass law. */

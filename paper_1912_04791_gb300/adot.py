@@ -98,6 +98,7 @@ def lib() -> ctypes.CDLL:
             "adot_mlp_train": ([_P, i64, i64, dbl, ctypes.c_uint64, _P], i32),
             "adot_set_surrogate": ([_P, _P, dbl, dbl], i32),
             "adot_surrogate_stats": ([_P, ctypes.POINTER(i64), ctypes.POINTER(i64)], i32),
+            "adot_surrogate_eval": ([_P, _P, i32, ctypes.POINTER(i64)], i32),
             "adot_harvest": ([_P, i64, ctypes.c_uint64, _P, _P, i32], i32),
             "adot_ensemble_create": ([ctypes.POINTER(EnsembleConfig), _P, ctypes.POINTER(_P)], i32),
             "adot_ensemble_destroy": ([_P], None),
@@ -496,6 +497,24 @@ def adot_surrogate_stats(ctx: int):
     e, f = ctypes.c_int64(), ctypes.c_int64()
     _check(lib().adot_surrogate_stats(ctx, ctypes.byref(e), ctypes.byref(f)), "adot_surrogate_stats")
     return e.value, f.value
+
+
+def adot_surrogate_eval(ctx: int, n_edges: int, out=None):
+    """The attached network's |A|_Psi on every edge of the current state:
+    (absA [9, n_edges] float32 or None, fallback count). `out`: None (new host
+    array), False (evaluate only) or a float32 CUDA tensor of shape (9, n_edges)."""
+    fb = ctypes.c_int64()
+    if out is None:
+        out = np.empty((9, n_edges), dtype=np.float32)
+        _check(lib().adot_surrogate_eval(ctx, out.ctypes.data, 0, ctypes.byref(fb)), "adot_surrogate_eval")
+        return out, fb.value
+    if out is False:
+        _check(lib().adot_surrogate_eval(ctx, None, 0, ctypes.byref(fb)), "adot_surrogate_eval")
+        return None, fb.value
+    if tuple(out.shape) != (9, n_edges) or not out.is_cuda:
+        raise ValueError("out must be a CUDA tensor of shape (9, n_edges)")
+    _check(lib().adot_surrogate_eval(ctx, out.data_ptr(), 1, ctypes.byref(fb)), "adot_surrogate_eval")
+    return out, fb.value
 
 
 def adot_harvest(ctx: int, n: int, seed: int = 1, X=None, T=None):

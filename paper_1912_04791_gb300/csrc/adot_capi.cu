@@ -738,8 +738,9 @@ adot_status adot_set_surrogate(adot_ctx* c, adot_mlp* m, double fr_lo, double fr
   CK(cudaStreamSynchronize(c->stream));
   if (!c->d_absA) {
     CK(cudaMalloc((void**)&c->d_absA, sizeof(float) * 9 * (size_t)(c->p.n + 1)));
-    CK(cudaMalloc((void**)&c->d_fb, sizeof(unsigned long long)));
-    CK(cudaMemset(c->d_fb, 0, sizeof(unsigned long long)));
+    // [0]: fallbacks of the steps, [1]: fallbacks of adot_surrogate_eval
+    CK(cudaMalloc((void**)&c->d_fb, 2 * sizeof(unsigned long long)));
+    CK(cudaMemset(c->d_fb, 0, 2 * sizeof(unsigned long long)));
   }
   c->mlp = m;
   c->fr_lo = (float)fr_lo;
@@ -761,6 +762,23 @@ adot_status adot_surrogate_stats(adot_ctx* c, int64_t* edges_out, int64_t* fallb
   if (edges_out) *edges_out = c->mlp ? steps * (c->p.n + 1) : 0;
   if (fallback_out) *fallback_out = (int64_t)(fb - c->fb0);
   return ADOT_OK;
+}
+
+adot_status adot_surrogate_eval(adot_ctx* c, float* absA, int on_device, int64_t* fallback_out) {
+  if (!c || !c->mlp || !c->state_set) return ADOT_E_INVALID_ARG;
+  CK(cudaMemsetAsync(c->d_fb + 1, 0, sizeof(unsigned long long), c->stream));
+  CK(launch_mlp_edges(c->mlp, c->p, st32(c, c->cur), c->phase % 3, (float)c->cfg.law.Ag, c->fr_lo,
+                      c->fr_hi, c->d_absA, c->d_fb + 1, c->stream));
+  if (absA)
+    CK(cudaMemcpyAsync(absA, c->d_absA, sizeof(float) * 9 * (size_t)(c->p.n + 1),
+                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+  unsigned long long fb = 0;
+  if (fallback_out)
+    CK(cudaMemcpyAsync(&fb, c->d_fb + 1, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
+  adot_status st = read_ctl(c);  // waits for the stream
+  if (st) return st;
+  if (fallback_out) *fallback_out = (int64_t)fb;
+  return status_from_bits(c->h_ctl->status);
 }
 
 adot_status adot_harvest(adot_ctx* c, int64_t n, uint64_t seed, float* X, float* T, int on_device) {

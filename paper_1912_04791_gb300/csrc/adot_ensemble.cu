@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(B, 65536 / (B * 64))
     lp.lf = LawT<float>{p.g_f, p.K3f[c], 0.0f, 0.0f};
     lp.ld = LawT<double>{p.g_d, p.K3d[c], 0.0, 0.0};
     R dm[3] = {R(0), R(0), R(0)}, dp[3] = {R(0), R(0), R(0)};
-    if (valid && e > 0 && e < nc) edge_fluct<R, LAW_GRASS>(lp, wl, wr, dm, dp, flags);
+    if (valid && e > 0 && e < nc) edge_fluct<R, LAW_GRASS, false>(lp, wl, wr, dm, dp, flags);
     sDp[0][tid] = dp[0];
     sDp[1][tid] = dp[1];
     sDp[2][tid] = dp[2];

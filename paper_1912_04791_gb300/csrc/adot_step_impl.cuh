@@ -146,12 +146,14 @@ __device__ __forceinline__ R warp_max(R v) {
   return v;
 }
 
-// D-/+ of one edge from its two states.
-template <typename R, int LAW>
+// D-/+ of one edge from its two states. PAIRED: float32 edges take the
+// paired-instruction form of the two outer nodes (fewer issue slots, more
+// registers); the ensemble kernel, held to 64 registers, keeps the scalar form.
+template <typename R, int LAW, bool PAIRED = true>
 __device__ __forceinline__ void edge_fluct(const StepParams& p, const typename Prec<R>::S wl[3],
                                            const typename Prec<R>::S wr[3], R dm[3], R dp[3],
                                            unsigned& flags) {
-  if constexpr (std::is_same<R, float>::value) {
+  if constexpr (PAIRED && std::is_same<R, float>::value) {
     edge_fluct_f32x2<LAW>(p.lf, p.ld, wl, wr, dm, dp, flags);
     return;
   }

@@ -212,6 +212,44 @@ def test_trained_surrogate_engines_agree(gpu, trained_smooth_net, engine):
         assert np.abs((x - x0) - (y - x0)).sum() <= 1e-3 * np.abs(y - x0).sum()
 
 
+def test_surrogate_eval_matches_network_on_state_edges(gpu, trained_smooth_net):
+    """adot_surrogate_eval (tcgen05 engine) on every edge of a periodic state
+    equals the per-layer forward kernels applied to the same edge inputs built
+    on the host (left cell (e-1) mod n, right cell e mod n, the hi words of the
+    float-float state, A_g, standardised with the network's statistics), to the
+    bf16 bound of the forward tests; NaN rows match the fallback count, and the
+    evaluation leaves the step statistics alone."""
+    P, X, T, theta, _ = trained_smooth_net
+    with gpu.Mlp(8192) as net:
+        net.set_params(theta)
+        net.set_data(X, T)
+        st, _ = net.stats()
+        with gpu.Solver(gpu.config_for(P, gpu.FP32)) as s:
+            s.set_state(P.h, P.q, P.z)
+            s.step(10)
+            gpu.adot_set_surrogate(s.ctx, net, 0.8, 1.2)
+            s.step(3)
+            before = gpu.adot_surrogate_stats(s.ctx)
+            absA, fb = gpu.adot_surrogate_eval(s.ctx, P.n + 1)
+            assert gpu.adot_surrogate_stats(s.ctx) == before
+            h, q, z = (a.astype(np.float32) for a in s.get_state())
+            gpu.adot_set_surrogate(s.ctx, net, 0.0, 100.0)
+            all_fb, fb_all = gpu.adot_surrogate_eval(s.ctx, P.n + 1)
+        n = P.n
+        e = np.arange(n + 1)
+        L, R = (e - 1) % n, e % n
+        Xe = np.stack([h[L], q[L], z[L], h[R], q[R], z[R], np.full(n + 1, P.Ag, np.float32)], axis=1)
+        Zs = (Xe - st[:7]) / st[7:14]
+        Y = np.concatenate([net.forward(Zs[i:i + 8192], fused=False) for i in range(0, n + 1, 8192)])
+    assert fb == int(np.isnan(absA[0]).sum())
+    assert fb_all == n + 1 and np.isnan(all_fb[0]).all()
+    ok = ~np.isnan(absA[0])
+    assert ok.sum() > 0.9 * (n + 1)
+    got = (absA.T[ok] - st[14:23]) / st[23:32]
+    ref = Y[ok]
+    assert np.abs(got - ref).max() <= 1e-2 * np.abs(ref).max(), np.abs(got - ref).max() / np.abs(ref).max()
+
+
 def test_trained_surrogate_step(gpu):
     """A network trained on edges harvested from the smooth periodic problem
     drives the same problem: the state stays finite, few edges fall back, and
