@@ -247,7 +247,7 @@ def surrogate_leg(args, adot, W, P, n, stream, dev, local, time_steps, ref64):
             # the inference kernel alone (adot_surrogate_eval, no copy-out), per engine:
             # CUDA events on the context's stream around each call, mean of 10 after 2
             infer = {}
-            for eng, name in ((0, "tcgen05"), (1, "mma.sync")):
+            for eng, name in ((0, "tcgen05"), (2, "tcgen05_two_groups"), (1, "mma.sync")):
                 net.set_engine(eng)
                 ts = []
                 for i in range(12):
@@ -271,7 +271,8 @@ def surrogate_leg(args, adot, W, P, n, stream, dev, local, time_steps, ref64):
         out.update({"cell_updates_per_s": n * 480 / (ms_t * 1e-3), "engine": "tcgen05",
                     "cell_updates_per_s_mma_sync": n * 480 / (ms_m * 1e-3),
                     "infer_flops_per_edge": 2 * 51200, "inference_kernel": infer,
-                    "roofline": {"bound": "tensor", "kernel": "k_mlp_tc<edges> (tcgen05, bf16, TMEM)",
+                    "roofline": {"bound": "tensor",
+                                 "kernel": "k_mlp_tcp<edges> (tcgen05, bf16, TMEM, warp-specialised)",
                                  "achieved": tc, "peak": peak, "unit": "TFLOP/s",
                                  "frac": tc / peak if peak else None,
                                  "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst; kernel timed alone)"},

@@ -259,8 +259,9 @@ void adot_mlp_destroy(adot_mlp* mlp);
 /* Parameters in (host [ADOT_MLP_PARAMS]); resets the Adam moments and step. */
 adot_status adot_mlp_set_params(adot_mlp* mlp, const float* params);
 adot_status adot_mlp_get_params(adot_mlp* mlp, float* params);
-/* Engine of the surrogate step's fused inference: 0 = tcgen05 (default),
- * 1 = mma.sync. ADOT_E_INVALID_ARG for another value. */
+/* Engine of the surrogate step's fused inference: 0 = tcgen05, warp-specialised
+ * three-tile pipeline (default); 1 = mma.sync; 2 = tcgen05, two independent
+ * tile groups per CTA. ADOT_E_INVALID_ARG for another value. */
 adot_status adot_mlp_set_engine(adot_mlp* mlp, int engine);
 /* Training set: raw inputs X [n][7] and labels T [n][9] (float32, host or
  * device). Sets the standardisation (per-column mean and standard deviation)
@@ -273,10 +274,12 @@ adot_status adot_mlp_get_stats(adot_mlp* mlp, float* stats32, float* box14);
 /* Forward pass of n <= max_batch standardised inputs Xs [n][7] (host) to
  * standardised outputs Y [n][9] (host). fused = 0: the per-layer training
  * kernels (mma.sync); 1: the single-kernel inference on mma.sync with the
- * tanhf GELU; 2: the single-kernel inference on the 5th-generation tensor
- * cores (tcgen05.mma, accumulators in tensor memory) with the tanh.approx GELU,
- * the default engine of the surrogate step. ADOT_E_TIMEOUT if a bounded
- * device-side wait for the tensor cores ran out. */
+ * tanhf GELU; 2 and 3: the single-kernel inference on the 5th-generation
+ * tensor cores (tcgen05.mma, accumulators in tensor memory) with the
+ * tanh.approx GELU, as two independent tile groups per CTA (2) or as the
+ * warp-specialised three-tile pipeline (3) that the surrogate step uses by
+ * default. ADOT_E_TIMEOUT if a bounded device-side wait for the tensor cores
+ * ran out. */
 adot_status adot_mlp_forward(adot_mlp* mlp, const float* Xs, int64_t n, float* Y, int fused);
 /* Loss and gradient (host [ADOT_MLP_PARAMS]) of the mean squared error on a
  * batch of standardised inputs Xs [n][7] and targets Ts [n][9] (host). */

@@ -444,11 +444,13 @@ class Mlp:
         return st, box
 
     def set_engine(self, engine: int) -> None:
-        """Fused inference engine of the surrogate step: 0 = tcgen05, 1 = mma.sync."""
+        """Fused inference engine of the surrogate step: 0 = tcgen05 pipeline,
+        1 = mma.sync, 2 = tcgen05 with two independent tile groups."""
         _check(lib().adot_mlp_set_engine(self.ptr, int(engine)), "adot_mlp_set_engine")
 
     def forward(self, Xs, fused=False) -> np.ndarray:
-        """fused: 0/False per-layer kernels, 1/True mma.sync fused, 2 tcgen05 fused."""
+        """fused: 0/False per-layer kernels, 1/True mma.sync fused, 2 tcgen05 two
+        groups, 3 tcgen05 pipeline."""
         Xs = _f32(Xs)
         n = Xs.shape[0]
         Y = np.empty((n, 9), dtype=np.float32)

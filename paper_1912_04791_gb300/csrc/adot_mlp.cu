@@ -1017,6 +1017,345 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   }
 }
 
+// --------------------------------------------------------------------------
+// warp-specialised tcgen05 inference: a pipeline of three 128-row tiles
+// --------------------------------------------------------------------------
+// Roles per CTA (one CTA per SM, 21 warps):
+//  warp 0, one thread: issues every layer's tcgen05.mma (as in k_mlp_tc);
+//  warps 1-4: producers; build the layer-0 operand of the CTA's tiles (32 rows
+//    per warp, one per lane) into a ring of kRing entries, up to kRing tiles ahead;
+//  warps 5-20: epilogue; warp w reads TMEM lane quadrant w % 4 and the 32
+//    accumulator columns 32 ((w - 5) / 4) .. + 31 of the tile in work.
+// Three tile slots, each with 128 TMEM columns and a 32 KB activation tile,
+// rotate through the jobs (slot, layer) in the fixed order
+//   for k = 0, 1, ...: for s = 0, 1, 2: layer k % 5 of the slot's tile 3 (k / 5) + s,
+// which every role follows, so no role waits on a job that comes later in it.
+// Hand-offs (mbarriers): ring full (producer -> MMA), ring empty (tcgen05.commit
+// after a tile's layer 0), accumulator full (tcgen05.commit -> epilogue),
+// activation ready (the 16 epilogue warps -> MMA: next operand written and the
+// accumulator read, so it may be overwritten). Every wait is bounded; one that
+// runs out raises a CTA-wide abort, sets ST_TIMEOUT, and every role leaves its
+// loop; the MMA thread then waits (bounded) for its products in flight before
+// the TMEM is freed.
+
+constexpr int kTpProducers = 4;  // producer warps, 32 tile rows each
+constexpr int kTpWarps = 1 + kTpProducers + 16;
+constexpr int kTpThreads = kTpWarps * 32;
+constexpr int kTpSlots = 3;
+constexpr int kRing = 4;
+constexpr int kFlagBufs = 8;
+constexpr uint32_t kTpFlagOff = kTcBiasOff + sizeof(float) * kBTotal;           // [8][128] bytes
+constexpr uint32_t kTpRingOff = (kTpFlagOff + kFlagBufs * kTcRows + 1023u) & ~1023u;
+constexpr uint32_t kTpRingBytes = (uint32_t)kTcRows * kPad * 2;                  // 4 KB
+constexpr uint32_t kTpActOff = kTpRingOff + kRing * kTpRingBytes;
+constexpr size_t kTpSmem = kTpActOff + kTpSlots * kTcActBytes + 1024;
+static_assert(kTpSmem <= 232448, "shared memory of the pipelined kernel");
+static_assert((kRing & (kRing - 1)) == 0 && (kFlagBufs & (kFlagBufs - 1)) == 0, "ring sizes are powers of two");
+// descriptor start addresses advance by 16 (256 B >> 4) per K step inside the
+// 14-bit field: the last operand's last step stays below 2^14 (the shared
+// window of one CTA)
+static_assert(((kTpSmem + 1024) >> 4) + 7 * 16 < (1u << 14), "descriptor address field");
+
+struct TpBars {
+  uint64_t ring_full[kRing], ring_empty[kRing];
+  uint64_t acc_full[kTpSlots], act_ready[kTpSlots];
+  uint64_t drain;
+  uint64_t wdesc[kLayers];  // weight descriptors (written and read by the issuing thread only)
+};
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_addr(b))
+               : "memory");
+}
+
+// Bounded wait that also gives up when another role raised the abort flag.
+// try_wait may suspend the thread until the phase completes, for at most the
+// hint (20 us), so a waiting warp takes few issue slots from working ones.
+__device__ __forceinline__ bool tp_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag) {
+  const uint32_t a = smem_addr(b);
+  const long long t0 = clock64();
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity), "r"(20000)
+        : "memory");
+    if (done) return true;
+    if (*abort_flag) return false;
+    if (clock64() - t0 > (1ll << 31)) {
+      *abort_flag = 1;
+      return false;
+    }
+  }
+}
+
+// One layer's K/16 products, fully unrolled: compile-time K steps (start
+// addresses 256 B = 16 units of the >> 4 address field apart) and accumulate
+// flags, so that the single issuing thread keeps the tensor pipe fed.
+template <int K, int N>
+__device__ __forceinline__ void tc_issue_layer(uint32_t d, uint64_t da, uint64_t db) {
+  constexpr uint32_t idesc = tc_idesc(N);
+#pragma unroll
+  for (int ks = 0; ks < K / 16; ++ks)
+    tc_mma(d, da + (uint64_t)(ks * 16), db + (uint64_t)(ks * 16), idesc, ks > 0 ? 1u : 0u);
+}
+
+template <bool EDGES>
+__global__ void __launch_bounds__(kTpThreads, 1)
+    k_mlp_tcp(const InferParams P, const StepParams sp, const StateF32 st, int slot,
+              float* __restrict__ absA, unsigned long long* fallback_count,
+              const __nv_bfloat16* __restrict__ Xrows, int64_t n_rows, float* __restrict__ Yrows,
+              unsigned* status) {
+  extern __shared__ unsigned char tc_raw[];
+  __shared__ __align__(8) TpBars bars;
+  __shared__ uint32_t s_tmem;
+  __shared__ volatile int s_abort;
+  const uint32_t raw = smem_addr(tc_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  unsigned char* sm = tc_raw + (base - raw);
+  float* sBias = reinterpret_cast<float*>(sm + kTcBiasOff);
+  unsigned char* sFlags = sm + kTpFlagOff;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  // weights (layers 1-4 halved, see k_mlp_tc) and biases
+  const __nv_bfloat162 half2 = __floats2bfloat162_rn(0.5f, 0.5f);
+  for (int l = 0; l < kLayers; ++l) {
+    const int K = dim_in(l), N = dim_out(l), kcs = K / 8;
+    const __nv_bfloat16* W = P.W + w_offset(l);
+    for (int i = threadIdx.x; i < N * kcs; i += blockDim.x) {
+      const int n = i / kcs, kc = i % kcs;
+      uint4 v = *reinterpret_cast<const uint4*>(W + n * K + kc * 8);
+      if (l > 0) {
+        __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&v);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) h[j] = __hmul2(h[j], half2);
+      }
+      *reinterpret_cast<uint4*>(sm + tc_w_off(l) + tc_canon(n, kc, K)) = v;
+    }
+  }
+  for (int i = threadIdx.x; i < kBTotal; i += blockDim.x) sBias[i] = P.bias[i];
+  if (threadIdx.x == 0) {
+    for (int r = 0; r < kRing; ++r) {
+      mbar_init(&bars.ring_full[r], kTpProducers);
+      mbar_init(&bars.ring_empty[r], 1);
+    }
+    for (int s2 = 0; s2 < kTpSlots; ++s2) {
+      mbar_init(&bars.acc_full[s2], 1);
+      mbar_init(&bars.act_ready[s2], 16);
+    }
+    mbar_init(&bars.drain, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_abort = 0;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_addr(&s_tmem)),
+                 "r"(512)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+
+  const int64_t n_items = EDGES ? sp.n + 1 : n_rows;
+  const int64_t n_tiles = (n_items + kTcRows - 1) / kTcRows;
+  // this CTA's tiles are blockIdx.x + m gridDim.x, m < my_tiles (32-bit
+  // counters: the job bookkeeping runs on single threads' critical paths)
+  const int my_tiles = (n_tiles > (int64_t)blockIdx.x) ? (int)((n_tiles - 1 - blockIdx.x) / gridDim.x + 1) : 0;
+  const int rounds = (my_tiles + kTpSlots - 1) / kTpSlots;
+  const uint32_t tmem = s_tmem;
+
+  if (warp == 0) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      // descriptors of ring entry 0, activation tile 0 and each layer's weights
+      const uint64_t ring_desc = tc_desc(base + kTpRingOff, kPad);
+      const uint64_t act_desc = tc_desc(base + kTpActOff, kHid);
+      uint64_t* s_wdesc = bars.wdesc;  // the layers' weight descriptors, one shared load per job
+#pragma unroll
+      for (int l = 0; l < kLayers; ++l) s_wdesc[l] = tc_desc(base + tc_w_off(l), dim_in(l));
+      bool ok = true;
+      for (int kk = 0; ok && kk < rounds * kLayers; ++kk) {
+        const int rd = kk / kLayers, l = kk - rd * kLayers;
+        for (int sl = 0; ok && sl < kTpSlots; ++sl) {
+          const int m = kTpSlots * rd + sl;
+          if (m >= my_tiles) break;
+          if (kk > 0) ok = tp_wait(&bars.act_ready[sl], (uint32_t)((kk - 1) & 1), &s_abort);
+          const int r = m & (kRing - 1);
+          if (ok && l == 0) ok = tp_wait(&bars.ring_full[r], (uint32_t)((m / kRing) & 1), &s_abort);
+          if (!ok) break;
+          tc_fence_after();
+          const uint32_t d = tmem + (uint32_t)(sl * kTcRows);
+          if (l == 0) {
+            tc_issue_layer<kPad, kHid>(d, ring_desc + (uint64_t)(r * (kTpRingBytes >> 4)), s_wdesc[0]);
+          } else {
+            const uint64_t da = act_desc + (uint64_t)(sl * (kTcActBytes >> 4));
+            if (l < kLayers - 1)
+              tc_issue_layer<kHid, kHid>(d, da, s_wdesc[l]);
+            else
+              tc_issue_layer<kHid, kPad>(d, da, s_wdesc[kLayers - 1]);
+          }
+          tc_commit(smem_addr(&bars.acc_full[sl]));
+          if (l == 0) tc_commit(smem_addr(&bars.ring_empty[r]));
+        }
+      }
+      // products in flight finish before the TMEM is freed
+      tc_commit(smem_addr(&bars.drain));
+      mbar_wait_bounded(smem_addr(&bars.drain), 0);
+    }
+  } else if (warp <= kTpProducers) {
+    // ---------------- producers ----------------
+    // warp p (1..kTpProducers) builds rows 32 (p - 1) + lane of every tile; the
+    // edge states of the next tile are loaded as soon as the current one is
+    // handed over, so their latency overlaps the wait for a free ring entry
+    const int row = (warp - 1) * 32 + lane;
+    unsigned long long fb = 0;
+    float xs[6] = {1.0f, 0.0f, 0.0f, 1.0f, 0.0f, 0.0f};
+    uint4 xa = make_uint4(0, 0, 0, 0), xb = make_uint4(0, 0, 0, 0);
+    auto fetch = [&](int mm) {
+      const int64_t item = ((int64_t)blockIdx.x + (int64_t)mm * gridDim.x) * kTcRows + row;
+      if (item >= n_items) return;
+      if (EDGES) {
+        float2 wl[3], wr[3];
+        load_edge<float>(sp, st, item, slot, wl, wr);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          xs[k] = wl[k].x;
+          xs[3 + k] = wr[k].x;
+        }
+      } else {
+        xa = *reinterpret_cast<const uint4*>(Xrows + item * kPad);
+        xb = *reinterpret_cast<const uint4*>(Xrows + item * kPad + 8);
+      }
+    };
+    if (my_tiles > 0) fetch(0);
+    for (int m = 0; m < my_tiles; ++m) {
+      const int r = m & (kRing - 1);
+      const int u = m / kRing;
+      if (u > 0) {
+        const bool ok = __all_sync(0xffffffffu, tp_wait(&bars.ring_empty[r], (uint32_t)((u - 1) & 1), &s_abort));
+        if (!ok) break;
+      }
+      unsigned char* ring = sm + kTpRingOff + r * kTpRingBytes;
+      const int64_t item = ((int64_t)blockIdx.x + (int64_t)m * gridDim.x) * kTcRows + row;
+      uint32_t pk[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      bool okr = false;
+      if (item < n_items) {
+        if (EDGES) {
+          const float x[kIn] = {xs[0], xs[1], xs[2], xs[3], xs[4], xs[5], P.Ag};
+          float z[kIn];
+          okr = edge_inputs(P, x, sp.lf.g, z);
+          if (!okr) ++fb;
+          pk[0] = pack_bf16(z[0], z[1]);
+          pk[1] = pack_bf16(z[2], z[3]);
+          pk[2] = pack_bf16(z[4], z[5]);
+          pk[3] = pack_bf16(z[6], 0.0f);
+        } else {
+          pk[0] = xa.x; pk[1] = xa.y; pk[2] = xa.z; pk[3] = xa.w;
+          pk[4] = xb.x; pk[5] = xb.y; pk[6] = xb.z; pk[7] = xb.w;
+        }
+      }
+      *reinterpret_cast<uint4*>(ring + tc_canon(row, 0, kPad)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+      *reinterpret_cast<uint4*>(ring + tc_canon(row, 1, kPad)) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+      sFlags[(m & (kFlagBufs - 1)) * kTcRows + row] = okr ? 1 : 0;
+      fence_async_smem();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&bars.ring_full[r]);
+      if (m + 1 < my_tiles) fetch(m + 1);
+    }
+    if (EDGES) {
+      fb += __shfl_xor_sync(0xffffffffu, fb, 16);
+      fb += __shfl_xor_sync(0xffffffffu, fb, 8);
+      fb += __shfl_xor_sync(0xffffffffu, fb, 4);
+      fb += __shfl_xor_sync(0xffffffffu, fb, 2);
+      fb += __shfl_xor_sync(0xffffffffu, fb, 1);
+      if (lane == 0 && fb) atomicAdd(fallback_count, fb);
+    }
+  } else {
+    // ---------------- epilogue ----------------
+    const int quad = warp & 3;
+    const int cb = (warp - 1 - kTpProducers) >> 2;  // 32-column block 0..3
+    const int row = quad * 32 + lane;        // TMEM lane = tile row
+    const float c1f = 0.0356774081f, c0f = 0.7978845608f;
+    const uint64_t c1 = ((uint64_t)__float_as_uint(c1f) << 32) | __float_as_uint(c1f);
+    const uint64_t c0 = ((uint64_t)__float_as_uint(c0f) << 32) | __float_as_uint(c0f);
+    bool ok = true;
+    for (int kk = 0; ok && kk < rounds * kLayers; ++kk) {
+      const int rd = kk / kLayers, l = kk - rd * kLayers;
+      for (int sl = 0; sl < kTpSlots; ++sl) {
+        const int m = kTpSlots * rd + sl;
+        if (m >= my_tiles) break;
+        ok = __all_sync(0xffffffffu, tp_wait(&bars.acc_full[sl], (uint32_t)(kk & 1), &s_abort));
+        if (!ok) break;
+        tc_fence_after();
+        const uint32_t t_row = tmem + (uint32_t)(sl * kTcRows) + ((uint32_t)(quad * 32) << 16);
+        if (l < kLayers - 1) {
+          unsigned char* act = sm + kTpActOff + sl * kTcActBytes;
+          const int c = cb * 32;
+          uint32_t r[32];
+          tmem_ld_x32(t_row + (uint32_t)c, r);
+          tmem_wait_ld(r);
+          const float* b = sBias + b_offset(l) + c;
+          uint32_t pk[16];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const float4 bb = *reinterpret_cast<const float4*>(b + 4 * j);
+            pk[2 * j] = gelu2x_bf16(r[4 * j], r[4 * j + 1], __float_as_uint(bb.x), __float_as_uint(bb.y), c1, c0);
+            pk[2 * j + 1] =
+                gelu2x_bf16(r[4 * j + 2], r[4 * j + 3], __float_as_uint(bb.z), __float_as_uint(bb.w), c1, c0);
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            *reinterpret_cast<uint4*>(act + tc_canon(row, c / 8 + u, kHid)) =
+                make_uint4(pk[4 * u], pk[4 * u + 1], pk[4 * u + 2], pk[4 * u + 3]);
+          fence_async_smem();
+        } else if (cb == 0) {
+          uint32_t r[16];
+          tmem_ld_x16(t_row, r);
+          tmem_wait_ld16(r);
+          const int64_t tile = (int64_t)blockIdx.x + (int64_t)m * gridDim.x;
+          const int64_t item = tile * kTcRows + row;
+          const float* b = sBias + b_offset(l);
+          if (item < n_items) {
+            if (EDGES) {
+              const bool okr = sFlags[(m & (kFlagBufs - 1)) * kTcRows + row] != 0;
+#pragma unroll
+              for (int k = 0; k < kOut; ++k) {
+                float v = (__uint_as_float(r[k]) + b[k]) * P.stats[2 * kIn + kOut + k] + P.stats[2 * kIn + k];
+                if (k == 0 && !okr) v = __int_as_float(0x7fc00000);
+                absA[(int64_t)k * n_items + item] = v;
+              }
+            } else {
+#pragma unroll
+              for (int k = 0; k < kPad; k += 4)
+                *reinterpret_cast<float4*>(Yrows + item * kPad + k) =
+                    make_float4(__uint_as_float(r[k]) + b[k], __uint_as_float(r[k + 1]) + b[k + 1],
+                                __uint_as_float(r[k + 2]) + b[k + 2], __uint_as_float(r[k + 3]) + b[k + 3]);
+            }
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&bars.act_ready[sl]);
+      }
+    }
+  }
+  if (threadIdx.x == 0 && s_abort && status) atomicOr(status, ST_TIMEOUT);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+  }
+}
+
 // Column minima and maxima of the raw inputs X [n][7].
 __global__ void k_minmax(const float* __restrict__ X, int64_t n, float* out /* [2][7] */) {
   const int c = blockIdx.x;
@@ -1083,7 +1422,7 @@ struct adot_mlp {
   uint64_t graph_seed;
   double graph_lr;
   int64_t graph_steps;
-  int engine;          // fused inference: 0 = tcgen05 (default), 1 = mma.sync
+  int engine;          // fused inference: 0 = tcgen05 pipeline (default), 1 = mma.sync, 2 = tcgen05 two groups
   unsigned* d_status;  // sticky ST_* bits of the fused inference kernels
 };
 
@@ -1118,6 +1457,10 @@ cudaError_t set_layer_attributes() {
     e = cudaFuncSetAttribute(k_mlp_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_mlp_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_mlp_tcp<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTpSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_mlp_tcp<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTpSmem);
   return e;
 }
 
@@ -1250,10 +1593,17 @@ cudaError_t launch_mlp_edges(const adot_mlp* m, const StepParams& sp, StateF32 s
   P.Ag = Ag;
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device);
+  const int64_t tc_tiles = (sp.n + 1 + kTcRows - 1) / kTcRows;
   if (m->engine == 0) {
+    // warp-specialised pipeline, one CTA per SM walking its tiles
+    const int grid = (int)imin64(tc_tiles, sms);
+    k_mlp_tcp<true><<<grid, kTpThreads, kTpSmem, s>>>(P, sp, st, slot, absA, fb, nullptr, 0, nullptr,
+                                                      &sp.ctl->status);
+    return cudaGetLastError();
+  }
+  if (m->engine == 2) {
     // two 128-row tiles in flight per CTA, one CTA per SM
-    const int64_t tiles = (sp.n + 1 + kTcRows - 1) / kTcRows;
-    const int grid = (int)imin64((tiles + 1) / 2, sms);
+    const int grid = (int)imin64((tc_tiles + 1) / 2, sms);
     k_mlp_tc<true><<<grid, kTcThreads, kTcSmem, s>>>(P, sp, st, slot, absA, fb, nullptr, 0, nullptr,
                                                      &sp.ctl->status);
     return cudaGetLastError();
@@ -1342,7 +1692,7 @@ void adot_mlp_destroy(adot_mlp* m) {
 }
 
 adot_status adot_mlp_set_engine(adot_mlp* m, int engine) {
-  if (!m || engine < 0 || engine > 1) return ADOT_E_INVALID_ARG;
+  if (!m || engine < 0 || engine > 2) return ADOT_E_INVALID_ARG;
   m->engine = engine;
   return ADOT_OK;
 }
@@ -1420,7 +1770,7 @@ adot_status adot_mlp_forward(adot_mlp* m, const float* Xs, int64_t n, float* Y, 
   if (!m || !Xs || !Y || n < 1 || n > m->max_batch) return ADOT_E_INVALID_ARG;
   adot_status st = upload_batch(m, Xs, nullptr, n);
   if (st) return st;
-  if (fused == 2) {
+  if (fused == 2 || fused == 3) {
     InferParams P{};
     P.W = m->d.W;
     P.bias = m->d.master + kWTotal;
@@ -1430,8 +1780,12 @@ adot_status adot_mlp_forward(adot_mlp* m, const float* Xs, int64_t n, float* Y, 
     int sms = 152;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device);
     CKM(cudaMemsetAsync(m->d_status, 0, sizeof(unsigned), m->stream));
-    k_mlp_tc<false><<<(unsigned)imin64((tiles + 1) / 2, sms), kTcThreads, kTcSmem, m->stream>>>(
-        P, sp, StateF32{}, 0, nullptr, nullptr, m->Xb, n, m->Y, m->d_status);
+    if (fused == 2)
+      k_mlp_tc<false><<<(unsigned)imin64((tiles + 1) / 2, sms), kTcThreads, kTcSmem, m->stream>>>(
+          P, sp, StateF32{}, 0, nullptr, nullptr, m->Xb, n, m->Y, m->d_status);
+    else
+      k_mlp_tcp<false><<<(unsigned)imin64(tiles, sms), kTpThreads, kTpSmem, m->stream>>>(
+          P, sp, StateF32{}, 0, nullptr, nullptr, m->Xb, n, m->Y, m->d_status);
     CKM(cudaGetLastError());
   } else if (fused) {
     constexpr size_t sm = infer_smem_bytes();
