@@ -44,6 +44,23 @@ FLOPS_PER_CELL_UPDATE = {"block": 633.6, "warp": 628.0}
 # L2. None where the kernel changed after its capture.
 DRAM_BYTES_PER_CELL_UPDATE = {"block": None, "warp": (97.88e6 + 64.74e6) / 4e6}
 BYTES_PER_CELL_UPDATE = 48.0  # float-float state: 3 x 8 B read + 3 x 8 B written
+# Executed thread instructions per cell-update of one launch (ncu smsp__inst_executed x 32 / cells,
+# N = 4e6, the 1-in-32 repeated edge included); None where the kernel changed after its capture.
+INSTR_PER_CELL_UPDATE = {"block": None, "warp": 92.63e6 * 32 / 4e6}
+
+
+def issue_roofline(kind: str, n: int, per_launch_s: float):
+    """The binding term of the FP32 step kernel: instruction issue. Achieved
+    thread instructions per second (ncu count per cell-update x cells / live
+    launch time) against 152 SMs x 4 schedulers x 32 lanes x 2070 MHz."""
+    ipc = INSTR_PER_CELL_UPDATE.get(kind)
+    if not ipc:
+        return None
+    peak = 152 * 4 * 32 * 2070e6 / 1e12
+    achieved = ipc * n / per_launch_s / 1e12
+    return {"instr_per_cell_update": ipc, "achieved": achieved, "peak": peak,
+            "unit": "T thread-instructions/s", "frac": achieved / peak,
+            "peak_source": "152 SM x 4 schedulers x 32 lanes x 2070 MHz (derived)"}
 
 
 def measured_peaks() -> dict:
@@ -534,7 +551,8 @@ def main():
                          "kernel": f"{'k_step_warp' if kern == 2 else 'k_step'}<float,GRASS,{block},{max(reg_cap, 0)}>",
                          "peak_source": "152 SM x 128 FP32 lanes x 2 x 2070 MHz (derived)",
                          "hbm_achieved_gbs": BYTES_PER_CELL_UPDATE * n / per_launch_s / 1e9,
-                         "hbm_peak_gbs": measured_peaks().get("hbm_gbs", 6800.0)},
+                         "hbm_peak_gbs": measured_peaks().get("hbm_gbs", 6800.0),
+                         "issue_slots": issue_roofline(kind, n, per_launch_s)},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps, "clocks": clocks,
             "accuracy": accuracy, "sim_time_after_timed_steps": t_sim, "variants": variants,
             "ensemble": ensemble, "surrogate": surrogate, "l1_t_end_sweep": sweep,
