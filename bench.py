@@ -496,7 +496,7 @@ def main():
         E = W.riemann_ensemble(4096)
         with adot.Ensemble.from_workload(E, adot.FP32, device=local, stream=stream) as ens:
             ens.set_state(E.h, E.q, E.z)
-            blk, n_tiles, grid = ens.info()
+            blk, n_tiles, grid, ens_kernel = ens.info()
             torch.cuda.synchronize(dev)
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
@@ -511,6 +511,7 @@ def main():
                     "cell_updates": int(cu), "seconds": ms_e * 1e-3,
                     "cell_updates_per_s": cu / (ms_e * 1e-3), "launches": int(launches),
                     "max_steps": int(steps_c.max()), "min_steps": int(steps_c.min()),
+                    "step_kernel": "warp tiles" if ens_kernel == 2 else "block",
                     "tile_threads": blk, "tiles": n_tiles, "grid": grid,
                     "all_at_t_end": bool((t_c == args.ensemble_t_end).all())}
 

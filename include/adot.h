@@ -201,9 +201,12 @@ typedef struct {
   const double* Ag;         /* host [n_channels], Grass coefficient [s^2/m] */
   double g, xi, cfl;        /* shared: gravity, 1/(1-p), CFL number in (0, 1] */
   int32_t precision;        /* ADOT_FP64 or ADOT_FP32 (float-float state) */
-  int32_t block_threads;    /* tile = block_threads - 1 cells: 128, 256, 512; 0 = autotuned */
+  int32_t block_threads;    /* threads per block: 128, 256, 512 (block kernel: tile =
+                               block_threads - 1 cells; warp tiles: 256 only); 0 = autotuned */
   int32_t steps_per_graph;  /* launches captured per CUDA graph; 0 = default (48) */
   int32_t device;           /* CUDA device ordinal; -1 = current */
+  int32_t step_kernel;      /* 1 = block kernel, 2 = persistent warp tiles (31 cells per tile,
+                               shuffle exchange, no block barrier); 0 = autotuned */
 } adot_ensemble_config;
 
 typedef struct adot_ensemble adot_ensemble;
@@ -236,9 +239,10 @@ adot_status adot_ensemble_step(adot_ensemble* ens, int64_t n_steps);
 adot_status adot_ensemble_query(adot_ensemble* ens, double* t_out, int64_t* steps_out,
                                 int64_t* cell_updates_out);
 
-/* Tile size in use (block threads), number of tiles and the resident grid. */
+/* Variant in use: threads per block, number of tiles, the resident grid and
+ * the step kernel (1 block, 2 warp tiles); NULL pointers are skipped. */
 adot_status adot_ensemble_info(adot_ensemble* ens, int32_t* block_out, int64_t* tiles_out,
-                               int32_t* grid_out);
+                               int32_t* grid_out, int32_t* step_kernel_out);
 
 /* ---- Learned surrogate of the quadrature-averaged |A| ----------------------
  * |A|_Psi = sum_k w_k |A(Psi(s_k))|, the matrix that multiplies W+ - W- in the

@@ -53,7 +53,8 @@ class EnsembleConfig(ctypes.Structure):
                 ("length", ctypes.POINTER(ctypes.c_double)), ("Ag", ctypes.POINTER(ctypes.c_double)),
                 ("g", ctypes.c_double), ("xi", ctypes.c_double), ("cfl", ctypes.c_double),
                 ("precision", ctypes.c_int32), ("block_threads", ctypes.c_int32),
-                ("steps_per_graph", ctypes.c_int32), ("device", ctypes.c_int32)]
+                ("steps_per_graph", ctypes.c_int32), ("device", ctypes.c_int32),
+                ("step_kernel", ctypes.c_int32)]
 
 
 _lib = None
@@ -108,7 +109,7 @@ def lib() -> ctypes.CDLL:
             "adot_ensemble_step": ([_P, i64], i32),
             "adot_ensemble_query": ([_P, _P, _P, ctypes.POINTER(i64)], i32),
             "adot_ensemble_info": ([_P, ctypes.POINTER(i32), ctypes.POINTER(i64),
-                                    ctypes.POINTER(i32)], i32),
+                                    ctypes.POINTER(i32), ctypes.POINTER(i32)], i32),
             "adot_status_string": ([i32], ctypes.c_char_p),
             "adot_version": ([], ctypes.c_char_p),
         }
@@ -313,7 +314,7 @@ class Ensemble:
     """Owning wrapper around an adot_ensemble (batched independent channels)."""
 
     def __init__(self, n_cells, length, Ag, xi, cfl=0.9, g=9.81, precision=FP32, block_threads=0,
-                 steps_per_graph=0, device=-1, stream=None):
+                 steps_per_graph=0, device=-1, stream=None, step_kernel=0):
         self._n = np.ascontiguousarray(n_cells, dtype=np.int64)
         self._len = np.ascontiguousarray(length, dtype=np.float64)
         self._ag = np.ascontiguousarray(Ag, dtype=np.float64)
@@ -325,6 +326,7 @@ class Ensemble:
         c.g, c.xi, c.cfl = g, xi, cfl
         c.precision, c.block_threads, c.steps_per_graph, c.device = precision, block_threads, \
             steps_per_graph, device
+        c.step_kernel = step_kernel
         s = stream
         if s is not None and not isinstance(s, int):
             s = s.cuda_stream
@@ -368,11 +370,12 @@ class Ensemble:
         return t, s, cu.value
 
     def info(self):
-        b, g = ctypes.c_int32(), ctypes.c_int32()
+        """(threads per block, tiles, resident grid, step kernel: 1 block, 2 warp tiles)."""
+        b, g, k = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
         nt = ctypes.c_int64()
-        _check(lib().adot_ensemble_info(self.ptr, ctypes.byref(b), ctypes.byref(nt), ctypes.byref(g)),
-               "adot_ensemble_info")
-        return b.value, nt.value, g.value
+        _check(lib().adot_ensemble_info(self.ptr, ctypes.byref(b), ctypes.byref(nt), ctypes.byref(g),
+                                        ctypes.byref(k)), "adot_ensemble_info")
+        return b.value, nt.value, g.value, k.value
 
     def close(self):
         if getattr(self, "ptr", 0):

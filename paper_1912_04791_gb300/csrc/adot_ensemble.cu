@@ -4,9 +4,12 @@
 // its own A_g, transmissive ends) with its own dt = cfl dx_c / rho_c. The
 // channels' cells lie end to end in one state array. One launch advances every
 // running channel by one of its own steps:
-//  - channels are cut into tiles of B-1 cells (B threads evaluate B edges and
-//    update the B-1 cells between them, as in the single-channel kernel); the
-//    tile list is ordered longest channel first;
+//  - channels are cut into tiles of B-1 cells (block kernel: B threads
+//    evaluate B edges and update the B-1 cells between them, D+ through shared
+//    memory) or of 16 x 31 cells (persistent warp tiles: one warp takes the
+//    tile's 31-cell sub-tiles in turn, 32 lanes, D+ and the right states by
+//    shuffle, no block barrier, one control evaluation and one CFL atomic per
+//    tile); the tile list is ordered longest channel first;
 //  - a fixed grid (resident blocks x SMs) walks the tiles [0, A), where A is
 //    one past the last tile of any channel that was running at the start of
 //    the previous step (set by device atomics), so finished short channels
@@ -64,6 +67,52 @@ struct EnsParams {
   EnsDev d;
 };
 
+// Control of channel c for this launch, evaluated by one lane: the mode (0 step,
+// 1 copy on the first launch after t_end, 2 skip), nu = dt/dx, and, on the
+// channel's first tile ("leader"), the next control slot (as in k_ens_step).
+template <typename R>
+__device__ __forceinline__ int ens_control(const EnsParams& p, int c, bool leader, int slot, int nx,
+                                           int pv, long long k, double t_end, R& nu) {
+  const int C = p.C;
+  int mode;
+  const long long fin = p.d.fin[c];
+  const double t = p.d.t[slot * C + c];
+  double dt = 0.0;
+  double tn = t;
+  if (k > fin) {
+    mode = 2;
+  } else if (!(t < t_end)) {
+    mode = 1;
+  } else {
+    mode = 0;
+    const double rho = Prec<R>::from_bits(p.d.rho[slot * C + c]);
+    dt = p.cfl * p.dx[c] / rho;
+    tn = t + dt;
+    if (tn >= t_end) {
+      dt = t_end - t;
+      tn = t_end;
+    }
+  }
+  nu = (mode == 0) ? R(dt / p.dx[c]) : R(0);
+  if (leader && mode != 2) {
+    const long long st = p.d.steps[slot * C + c] + (mode == 0 ? 1 : 0);
+    p.d.t[nx * C + c] = tn;
+    p.d.dt[nx * C + c] = (mode == 0) ? dt : p.d.dt[slot * C + c];
+    p.d.steps[nx * C + c] = st;
+    p.d.rho[pv * C + c] = 0ull;
+    p.d.t_cur[c] = tn;
+    p.d.steps_cur[c] = st;
+    if (mode == 0) {
+      p.d.dt_cur[c] = dt;
+      atomicMax(&p.d.active[nx], p.chan_tile_end[c]);
+    } else {
+      p.d.rho[nx * C + c] = p.d.rho[slot * C + c];
+      p.d.fin[c] = k;
+    }
+  }
+  return mode;
+}
+
 template <typename R, int B>
 __global__ void __launch_bounds__(B, 65536 / (B * 64))
     k_ens_step(const EnsParams p, const typename Prec<R>::State in,
@@ -105,43 +154,9 @@ __global__ void __launch_bounds__(B, 65536 / (B * 64))
       wr[2] = in.z[base + ir];
     }
     if (tid == 0) {
-      int mode;
-      const long long fin = p.d.fin[c];
-      const double t = p.d.t[slot * C + c];
-      double dt = 0.0;
-      double tn = t;
-      if (k > fin) {
-        mode = 2;
-      } else if (!(t < t_end)) {
-        mode = 1;
-      } else {
-        mode = 0;
-        const double rho = Prec<R>::from_bits(p.d.rho[slot * C + c]);
-        dt = p.cfl * p.dx[c] / rho;
-        tn = t + dt;
-        if (tn >= t_end) {
-          dt = t_end - t;
-          tn = t_end;
-        }
-      }
-      sMode = mode;
-      sNu = (mode == 0) ? R(dt / p.dx[c]) : R(0);
-      if (e0 == 0 && mode != 2) {  // leader
-        const long long st = p.d.steps[slot * C + c] + (mode == 0 ? 1 : 0);
-        p.d.t[nx * C + c] = tn;
-        p.d.dt[nx * C + c] = (mode == 0) ? dt : p.d.dt[slot * C + c];
-        p.d.steps[nx * C + c] = st;
-        p.d.rho[pv * C + c] = 0ull;
-        p.d.t_cur[c] = tn;
-        p.d.steps_cur[c] = st;
-        if (mode == 0) {
-          p.d.dt_cur[c] = dt;
-          atomicMax(&p.d.active[nx], p.chan_tile_end[c]);
-        } else {
-          p.d.rho[nx * C + c] = p.d.rho[slot * C + c];
-          p.d.fin[c] = k;
-        }
-      }
+      R nu = R(0);
+      sMode = ens_control<R>(p, c, e0 == 0, slot, nx, pv, k, t_end, nu);
+      sNu = nu;
     }
     __syncthreads();
     const int mode = sMode;
@@ -201,6 +216,121 @@ __global__ void __launch_bounds__(B, 65536 / (B * 64))
   if (flags) atomicOr(p.d.status, flags);
 }
 
+template <typename T>
+__device__ __forceinline__ T shfl_down1(T v) { return __shfl_down_sync(0xffffffffu, v, 1); }
+template <>
+__device__ __forceinline__ float2 shfl_down1(float2 v) {
+  return make_float2(__shfl_down_sync(0xffffffffu, v.x, 1), __shfl_down_sync(0xffffffffu, v.y, 1));
+}
+
+// Persistent warp tiles: each warp walks tiles of SUB x 31 cells of one
+// channel (tile list in those units, longest channel first) with a grid-wide
+// stride over the active bound. Lane 0 evaluates the channel's control once per
+// tile and broadcasts it; the warp then takes the tile's SUB sub-tiles of 32
+// edges / 31 cells in turn: lane l evaluates edge e0 + l, the right state of an
+// edge and D+ of the left edge come by shuffle, so no block barrier is taken.
+// One CFL atomic per tile.
+template <typename R, int B, int CAP, int SUB>
+__global__ void __launch_bounds__(B, 65536 / (B * CAP))
+    k_ens_step_warp(const EnsParams p, const typename Prec<R>::State in,
+                    const typename Prec<R>::State out, const int slot) {
+  using S = typename Prec<R>::S;
+  const int lane = threadIdx.x & 31;
+  const int C = p.C;
+  const int nx = (slot + 1) % 3, pv = (slot + 2) % 3;
+  const int A = p.d.active[slot];
+  const long long k = p.d.gstep[slot];
+  const double t_end = *p.d.t_end;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    p.d.active[pv] = 0;
+    p.d.gstep[nx] = k + 1;
+  }
+  const int64_t warp0 = ((int64_t)blockIdx.x * B + threadIdx.x) >> 5;
+  const int64_t n_warps = ((int64_t)gridDim.x * B) >> 5;
+  unsigned flags = 0;
+  for (int64_t tile = warp0; tile < A; tile += n_warps) {
+    const int c = p.tile_chan[tile];
+    const int64_t t0 = p.tile_e0[tile];
+    const int64_t base = p.off[c];
+    const int64_t nc = p.off[c + 1] - base;
+    R nu = R(0);
+    int mode = 0;
+    if (lane == 0) mode = ens_control<R>(p, c, t0 == 0, slot, nx, pv, k, t_end, nu);
+    mode = __shfl_sync(0xffffffffu, mode, 0);
+    nu = __shfl_sync(0xffffffffu, nu, 0);
+    if (mode == 2) continue;
+    StepParams lp;
+    lp.lf = LawT<float>{p.g_f, p.K3f[c], 0.0f, 0.0f};
+    lp.ld = LawT<double>{p.g_d, p.K3d[c], 0.0, 0.0};
+    R rho = R(0);
+#pragma unroll 1
+    for (int sub = 0; sub < SUB; ++sub) {
+      const int64_t e0 = t0 + sub * 31;
+      if (e0 >= nc) break;  // past the channel's last cell (warp-uniform)
+      const int64_t e = e0 + lane;
+      // left state of edge e: cell e-1 (cell 0 at the channel's start); right
+      // state: the next lane's left state, lane 31 loads its own; transmissive
+      // ends copy the adjacent cell
+      const bool valid = e <= nc;
+      S wl[3], wr[3];
+      const int64_t il = (e > 0) ? (e <= nc ? e - 1 : nc - 1) : 0;
+      wl[0] = in.h[base + il];
+      wl[1] = in.q[base + il];
+      wl[2] = in.z[base + il];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) wr[r] = shfl_down1(wl[r]);
+      if (lane == 31 && e < nc) {
+        wr[0] = in.h[base + e];
+        wr[1] = in.q[base + e];
+        wr[2] = in.z[base + e];
+      }
+      if (e >= nc) {
+#pragma unroll
+        for (int r = 0; r < 3; ++r) wr[r] = wl[r];
+      }
+      const int64_t i = e - 1;  // cell updated by this lane (lanes 1..31)
+      if (mode == 1) {
+        if (lane >= 1 && i < nc) {
+          out.h[base + i] = wl[0];
+          out.q[base + i] = wl[1];
+          out.z[base + i] = wl[2];
+        }
+        continue;
+      }
+      R dm[3] = {R(0), R(0), R(0)}, dp[3] = {R(0), R(0), R(0)};
+      if (valid && e > 0 && e < nc) edge_fluct<R, LAW_GRASS, false>(lp, wl, wr, dm, dp, flags);
+      R dpl[3];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) dpl[r] = __shfl_up_sync(0xffffffffu, dp[r], 1);
+      if (lane >= 1 && i < nc) {
+        const S nh = Prec<R>::add(wl[0], -nu * (dm[0] + dpl[0]));
+        const S nq = Prec<R>::add(wl[1], -nu * (dm[1] + dpl[1]));
+        const S nz = Prec<R>::add(wl[2], -nu * (dm[2] + dpl[2]));
+        out.h[base + i] = nh;
+        out.q[base + i] = nq;
+        out.z[base + i] = nz;
+        const R hh = Prec<R>::hi(nh);
+        if (!(hh > R(0))) flags |= ST_DEPTH;
+        if (!(Prec<R>::finite(nh) && Prec<R>::finite(nq) && Prec<R>::finite(nz))) {
+          flags |= ST_NONFINITE;
+        } else if (hh > R(0)) {
+          R r = Prec<R>::template rho<LAW_GRASS>(lp, hh, Prec<R>::hi(nq));
+          if (!(r <= R(3.0e38))) {
+            flags |= ST_NONFINITE;
+            r = R(0);
+          }
+          rho = r > rho ? r : rho;
+        }
+      }
+    }
+    if (mode == 0) {
+      rho = warp_max(rho);
+      if (lane == 0 && rho > R(0)) atomicMax(&p.d.rho[nx * C + c], Prec<R>::bits(rho));
+    }
+  }
+  if (flags) atomicOr(p.d.status, flags);
+}
+
 // Initial CFL maxima of every channel into slot 0 (grid-stride over cells).
 template <typename R>
 __global__ void __launch_bounds__(256) k_ens_rho(const EnsParams p, const typename Prec<R>::State st,
@@ -244,7 +374,17 @@ using namespace adot;
 
 namespace {
 
-constexpr int kEnsBlocks[3] = {256, 128, 512};
+// Step kernel variants: block kernel (tile = block - 1 cells, 64-register cap)
+// or persistent warp tiles (31 cells per tile) at a register cap.
+struct EnsVariant {
+  int block;
+  int cap;
+  bool warp;
+};
+constexpr EnsVariant kEnsVariants[] = {{256, 64, false}, {128, 64, false}, {512, 64, false},
+                                       {256, 64, true},  {256, 80, true}};
+constexpr int kNumEnsVariants = sizeof(kEnsVariants) / sizeof(kEnsVariants[0]);
+constexpr int kEnsSub = 16;  // 31-cell sub-tiles per warp tile (one control evaluation each; 4: 2.99e10, 8: 3.15e10, 16: 3.19e10 cell-updates/s on the 4096-channel ensemble)
 
 struct HostCtl {
   long long gstep[3];
@@ -259,6 +399,10 @@ struct adot_ensemble {
   int prec;
   int device;
   int block;
+  int cap;       // register cap of the warp-tile kernel
+  bool warp;     // persistent warp tiles (31 cells) instead of block tiles (block - 1 cells)
+  int step_kernel_cfg;  // 0 autotuned, 1 block, 2 warp tiles
+  int block_cfg;        // configured block_threads (0 = any)
   bool tuned;
   int steps_per_graph;
   double cfl, g, xi;
@@ -337,6 +481,12 @@ cudaError_t ens_launch_t(adot_ensemble* e, int block, int grid, cudaStream_t s, 
   const EnsParams p = ens_params(e);
   const auto in = ens_state<R>(e, cur), out = ens_state<R>(e, 1 - cur);
   const int slot = phase % 3;
+  if (e->warp) {
+    if (block == 256 && e->cap == 64) k_ens_step_warp<R, 256, 64, kEnsSub><<<grid, 256, 0, s>>>(p, in, out, slot);
+    else if (block == 256 && e->cap == 80) k_ens_step_warp<R, 256, 80, kEnsSub><<<grid, 256, 0, s>>>(p, in, out, slot);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+  }
   switch (block) {
     case 128: k_ens_step<R, 128><<<grid, 128, 0, s>>>(p, in, out, slot); break;
     case 256: k_ens_step<R, 256><<<grid, 256, 0, s>>>(p, in, out, slot); break;
@@ -355,7 +505,15 @@ int resident_grid(adot_ensemble* e, int block) {
   int per_sm = 1, sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, e->device);
   cudaError_t err;
-  if (e->prec == ADOT_FP32) {
+  if (e->warp) {
+    const bool c80 = e->cap == 80;
+    if (e->prec == ADOT_FP32)
+      err = c80 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ens_step_warp<float, 256, 80, kEnsSub>, 256, 0)
+                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ens_step_warp<float, 256, 64, kEnsSub>, 256, 0);
+    else
+      err = c80 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ens_step_warp<double, 256, 80, kEnsSub>, 256, 0)
+                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ens_step_warp<double, 256, 64, kEnsSub>, 256, 0);
+  } else if (e->prec == ADOT_FP32) {
     if (block == 128) err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ens_step<float, 128>, 128, 0);
     else if (block == 256) err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ens_step<float, 256>, 256, 0);
     else err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ens_step<float, 512>, 512, 0);
@@ -369,11 +527,12 @@ int resident_grid(adot_ensemble* e, int block) {
   return (int)g;
 }
 
-// Tile list for block size B: channels longest first, tiles of B-1 cells.
-adot_status build_tiles(adot_ensemble* e, int block) {
+// Tile list of a variant: channels longest first, tiles of block - 1 cells
+// (block kernel) or 31 cells (warp tiles).
+adot_status build_tiles(adot_ensemble* e, EnsVariant v) {
   std::vector<int> tc, te;
   std::vector<int> tend(e->C);
-  const int64_t cells = block - 1;
+  const int64_t cells = v.warp ? 31 * kEnsSub : v.block - 1;
   for (int c : e->order) {
     const int64_t nt = (e->n_cells[c] + cells - 1) / cells;
     for (int64_t j = 0; j < nt; ++j) {
@@ -393,9 +552,12 @@ adot_status build_tiles(adot_ensemble* e, int block) {
   CKE(cudaMemcpy(e->d_tile_chan, tc.data(), sizeof(int) * tc.size(), cudaMemcpyHostToDevice));
   CKE(cudaMemcpy(e->d_tile_e0, te.data(), sizeof(int) * te.size(), cudaMemcpyHostToDevice));
   CKE(cudaMemcpy(e->d_chan_tile_end, tend.data(), sizeof(int) * e->C, cudaMemcpyHostToDevice));
-  e->block = block;
-  int g = resident_grid(e, block);
-  e->grid = (int)std::min<int64_t>(g, std::max<int64_t>(1, e->n_tiles));
+  e->block = v.block;
+  e->cap = v.cap;
+  e->warp = v.warp;
+  int g = resident_grid(e, v.block);
+  const int64_t need = v.warp ? (e->n_tiles * 32 + v.block - 1) / v.block : e->n_tiles;  // one warp per tile
+  e->grid = (int)std::min<int64_t>(g, std::max<int64_t>(1, need));
   return ADOT_OK;
 }
 
@@ -470,7 +632,15 @@ adot_status ens_reset_ctl(adot_ensemble* e) {
   return ADOT_OK;
 }
 
-// Trial steps of each block size on the current state (no state advance:
+// Variants allowed by the configuration (block_threads, step_kernel).
+bool ens_candidate(const adot_ensemble* e, EnsVariant v) {
+  if (e->step_kernel_cfg == 1 && v.warp) return false;
+  if (e->step_kernel_cfg == 2 && !v.warp) return false;
+  if (e->block_cfg && v.block != e->block_cfg) return false;
+  return true;
+}
+
+// Trial steps of each variant on the current state (no state advance:
 // with t_end = inf no channel finishes; the written slot and the tile bound
 // are reset afterwards).
 adot_status ens_tune(adot_ensemble* e, int trial) {
@@ -481,12 +651,13 @@ adot_status ens_tune(adot_ensemble* e, int trial) {
     return ADOT_E_CUDA;
   }
   float best = 0.0f;
-  int best_block = e->block;
+  EnsVariant best_v{e->block, e->cap, e->warp};
   bool have = false;
   cudaError_t err = cudaSuccess;
-  for (int i = 0; i < 3 && err == cudaSuccess; ++i) {
-    const int blk = kEnsBlocks[i];
-    if (build_tiles(e, blk) != ADOT_OK) {
+  for (int i = 0; i < kNumEnsVariants && err == cudaSuccess; ++i) {
+    const EnsVariant v = kEnsVariants[i];
+    if (!ens_candidate(e, v)) continue;
+    if (build_tiles(e, v) != ADOT_OK) {
       err = cudaErrorUnknown;
       break;
     }
@@ -502,14 +673,14 @@ adot_status ens_tune(adot_ensemble* e, int trial) {
     if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, a, b);
     if (err == cudaSuccess && (!have || ms < best)) {
       best = ms;
-      best_block = blk;
+      best_v = v;
       have = true;
     }
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   if (err != cudaSuccess) return ADOT_E_CUDA;
-  adot_status st = build_tiles(e, best_block);
+  adot_status st = build_tiles(e, best_v);
   if (st) return st;
   // undo what the trials wrote: slot 1 (CFL maxima, times) and the tile bounds
   const int C = e->C;
@@ -560,6 +731,8 @@ adot_status adot_ensemble_create(const adot_ensemble_config* cfg, void* cuda_str
   if (cfg->block_threads != 0 && cfg->block_threads != 128 && cfg->block_threads != 256 &&
       cfg->block_threads != 512)
     return ADOT_E_INVALID_ARG;
+  if (cfg->step_kernel < 0 || cfg->step_kernel > 2) return ADOT_E_INVALID_ARG;
+  if (cfg->step_kernel == 2 && cfg->block_threads != 0 && cfg->block_threads != 256) return ADOT_E_INVALID_ARG;
   if (cfg->steps_per_graph < 0 || cfg->device < -1) return ADOT_E_INVALID_ARG;
   const int C = cfg->n_channels;
   int64_t total = 0;
@@ -588,7 +761,8 @@ adot_status adot_ensemble_create(const adot_ensemble_config* cfg, void* cuda_str
                    [&](int a, int b) { return e->n_cells[a] > e->n_cells[b]; });
   int spg = cfg->steps_per_graph ? cfg->steps_per_graph : 48;
   e->steps_per_graph = ((spg + 5) / 6) * 6;
-  e->tuned = cfg->block_threads != 0;
+  e->step_kernel_cfg = cfg->step_kernel;
+  e->block_cfg = cfg->block_threads;
   e->t_end_dev = INFINITY;
 
   std::vector<double> dx(C), K3d(C);
@@ -645,7 +819,16 @@ adot_status adot_ensemble_create(const adot_ensemble_config* cfg, void* cuda_str
   if (err == cudaSuccess) err = cudaMemcpy(e->d_dx, dx.data(), sizeof(double) * C, cudaMemcpyHostToDevice);
   if (err == cudaSuccess) err = cudaMemcpy(e->d_K3f, K3f.data(), sizeof(float) * C, cudaMemcpyHostToDevice);
   if (err == cudaSuccess) err = cudaMemcpy(e->d_K3d, K3d.data(), sizeof(double) * C, cudaMemcpyHostToDevice);
-  if (err != cudaSuccess || build_tiles(e, cfg->block_threads ? cfg->block_threads : 256) != ADOT_OK ||
+  // the first allowed variant; tuned at the first set_state unless it is the only one
+  int n_cand = 0;
+  EnsVariant v0{256, 64, false};
+  for (int i = kNumEnsVariants - 1; i >= 0; --i)
+    if (ens_candidate(e, kEnsVariants[i])) {
+      v0 = kEnsVariants[i];
+      ++n_cand;
+    }
+  e->tuned = n_cand == 1;
+  if (err != cudaSuccess || build_tiles(e, v0) != ADOT_OK ||
       ens_reset_ctl(e) != ADOT_OK || ens_build_graph(e) != ADOT_OK) {
     ens_free(e);
     return ADOT_E_CUDA;
@@ -773,8 +956,9 @@ adot_status adot_ensemble_query(adot_ensemble* e, double* t_out, int64_t* steps_
 }
 
 adot_status adot_ensemble_info(adot_ensemble* e, int32_t* block_out, int64_t* tiles_out,
-                               int32_t* grid_out) {
+                               int32_t* grid_out, int32_t* step_kernel_out) {
   if (!e) return ADOT_E_INVALID_ARG;
+  if (step_kernel_out) *step_kernel_out = e->warp ? 2 : 1;
   if (block_out) *block_out = e->block;
   if (tiles_out) *tiles_out = e->n_tiles;
   if (grid_out) *grid_out = e->grid;

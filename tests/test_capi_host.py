@@ -38,6 +38,9 @@ int main(void) {
          offsetof(adot_config, bc_left_value), offsetof(adot_config, bc_right_value),
          offsetof(adot_config, block_threads), offsetof(adot_config, device),
          offsetof(adot_config, step_kernel), offsetof(adot_law, manning_n));
+  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(adot_ensemble_config), offsetof(adot_ensemble_config, g),
+         offsetof(adot_ensemble_config, precision), offsetof(adot_ensemble_config, block_threads),
+         offsetof(adot_ensemble_config, device), offsetof(adot_ensemble_config, step_kernel));
   return 0;
 }
 ''')
@@ -45,10 +48,12 @@ int main(void) {
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True,
                                           check=True).stdout.split()]
-    C, W = adot.Config, adot.Law
+    C, W, E = adot.Config, adot.Law, adot.EnsembleConfig
     want = [ctypes.sizeof(C), ctypes.sizeof(W), C.law.offset, C.precision.offset,
             C.bc_left_value.offset, C.bc_right_value.offset, C.block_threads.offset,
-            C.device.offset, C.step_kernel.offset, W.manning_n.offset]
+            C.device.offset, C.step_kernel.offset, W.manning_n.offset,
+            ctypes.sizeof(E), E.g.offset, E.precision.offset, E.block_threads.offset, E.device.offset,
+            E.step_kernel.offset]
     assert got == want
 
 
@@ -110,4 +115,9 @@ def test_invalid_ensemble_config_rejected(L):
     assert L.adot_ensemble_create(ctypes.byref(c), None, ctypes.byref(out)) == adot.E_INVALID_ARG
     c.cfl = 0.9
     c.block_threads = 100
+    assert L.adot_ensemble_create(ctypes.byref(c), None, ctypes.byref(out)) == adot.E_INVALID_ARG
+    c.block_threads = 0
+    c.step_kernel = 3
+    assert L.adot_ensemble_create(ctypes.byref(c), None, ctypes.byref(out)) == adot.E_INVALID_ARG
+    c.step_kernel, c.block_threads = 2, 128  # warp tiles run 256-thread blocks only
     assert L.adot_ensemble_create(ctypes.byref(c), None, ctypes.byref(out)) == adot.E_INVALID_ARG

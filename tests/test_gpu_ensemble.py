@@ -41,10 +41,10 @@ def _oracle_channel(E, c, t_end):
     return O.run(cfg, h, q, z, t_end=t_end)
 
 
-@pytest.mark.parametrize("block", [0, 128, 256, 512])
-def test_fp64_ensemble_matches_oracle_per_channel(gpu, block):
+@pytest.mark.parametrize("block,kern", [(0, 0), (128, 1), (256, 1), (512, 1), (0, 2), (256, 2)])
+def test_fp64_ensemble_matches_oracle_per_channel(gpu, block, kern):
     E = _small_ensemble(SIZES)
-    with gpu.Ensemble.from_workload(E, gpu.FP64, block_threads=block) as ens:
+    with gpu.Ensemble.from_workload(E, gpu.FP64, block_threads=block, step_kernel=kern) as ens:
         ens.set_state(E.h, E.q, E.z)
         t, steps, _ = ens.query()
         assert (steps == 0).all()
@@ -61,9 +61,11 @@ def test_fp64_ensemble_matches_oracle_per_channel(gpu, block):
             assert np.abs(a[o[c]:o[c + 1]] - b).max() <= 1e-12 * sc, c
 
 
-def test_fp32_ensemble_matches_oracle_per_channel(gpu):
+@pytest.mark.parametrize("kern", [1, 2])
+def test_fp32_ensemble_matches_oracle_per_channel(gpu, kern):
     E = _small_ensemble(SIZES, seed=4)
-    with gpu.Ensemble.from_workload(E, gpu.FP32) as ens:
+    with gpu.Ensemble.from_workload(E, gpu.FP32, step_kernel=kern) as ens:
+        assert ens.info()[3] == kern
         ens.set_state(E.h, E.q, E.z)
         ens.run_to(0.2)
         t, steps, _ = ens.query()
@@ -74,6 +76,32 @@ def test_fp32_ensemble_matches_oracle_per_channel(gpu):
         assert t[c] == 0.2
         for a, b in ((h, ho), (q, qo), (z, zo)):
             assert np.abs(a[o[c]:o[c + 1]] - b).sum() <= 1e-5 * max(np.abs(b).sum(), 1e-12)
+
+
+@pytest.mark.parametrize("prec", ["FP32", "FP64"])
+def test_warp_tiles_equal_block_tiles(gpu, prec):
+    """The warp-tile and block-tile ensemble kernels do the same arithmetic per
+    edge and per cell (the CFL maximum does not depend on the reduction order):
+    in float32 (float-float update, TwoSum written out) the states are
+    bit-identical; in float64 the compiler may contract the update
+    W + (-nu)(D- + D+) into a fused multiply-add in one kernel and not the
+    other, so the states agree to a few ulps. Times and step counts agree."""
+    E = _small_ensemble(SIZES + [3000, 1234], seed=6)
+    out = []
+    for kern in (1, 2):
+        with gpu.Ensemble.from_workload(E, getattr(gpu, prec), step_kernel=kern, block_threads=256) as ens:
+            ens.set_state(E.h, E.q, E.z)
+            ens.run_to(0.1)
+            t, steps, cu = ens.query()
+            out.append((ens.get_state(), t, steps, cu, ens.info()[3]))
+    (sa, ta, na, ca, ka), (sb, tb, nb, cb, kb) = out
+    assert (ka, kb) == (1, 2)
+    for x, y in zip(sa, sb):
+        if prec == "FP32":
+            assert np.array_equal(x, y)
+        else:
+            assert np.abs(x - y).max() <= 1e-14 * np.abs(y).max()
+    assert np.array_equal(ta, tb) and np.array_equal(na, nb) and ca == cb
 
 
 def test_ensemble_steps_equal_single_channel_contexts(gpu):
