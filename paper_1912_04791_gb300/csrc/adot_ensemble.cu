@@ -298,7 +298,8 @@ __global__ void __launch_bounds__(B, 65536 / (B * CAP))
         continue;
       }
       R dm[3] = {R(0), R(0), R(0)}, dp[3] = {R(0), R(0), R(0)};
-      if (valid && e > 0 && e < nc) edge_fluct<R, LAW_GRASS, false>(lp, wl, wr, dm, dp, flags);
+      // the paired-node float32 form where the register cap leaves it room
+      if (valid && e > 0 && e < nc) edge_fluct<R, LAW_GRASS, (CAP >= 80)>(lp, wl, wr, dm, dp, flags);
       R dpl[3];
 #pragma unroll
       for (int r = 0; r < 3; ++r) dpl[r] = __shfl_up_sync(0xffffffffu, dp[r], 1);
@@ -384,7 +385,9 @@ struct EnsVariant {
 constexpr EnsVariant kEnsVariants[] = {{256, 64, false}, {128, 64, false}, {512, 64, false},
                                        {256, 64, true},  {256, 80, true}};
 constexpr int kNumEnsVariants = sizeof(kEnsVariants) / sizeof(kEnsVariants[0]);
-constexpr int kEnsSub = 16;  // 31-cell sub-tiles per warp tile (one control evaluation each; 4: 2.99e10, 8: 3.15e10, 16: 3.19e10 cell-updates/s on the 4096-channel ensemble)
+// 31-cell sub-tiles per warp tile (one control evaluation each; on the 4096-channel
+// ensemble with scalar nodes 4: 2.99e10, 8: 3.15e10, 16: 3.19e10 cell-updates/s)
+constexpr int kEnsSub = 16;
 
 struct HostCtl {
   long long gstep[3];
