@@ -7,9 +7,9 @@
 //  - channels are cut into tiles of B-1 cells (block kernel: B threads
 //    evaluate B edges and update the B-1 cells between them, D+ through shared
 //    memory) or of 16 x 31 cells (persistent warp tiles: one warp takes the
-//    tile's 31-cell sub-tiles in turn, 32 lanes, D+ and the right states by
-//    shuffle, no block barrier, one control evaluation and one CFL atomic per
-//    tile); the tile list is ordered longest channel first;
+//    tile's 31-cell sub-tiles in turn, 32 lanes, D+ by shuffle, no block
+//    barrier, one control evaluation and one CFL atomic per tile); the tile
+//    list is ordered longest channel first;
 //  - a fixed grid (resident blocks x SMs) walks the tiles [0, A), where A is
 //    one past the last tile of any channel that was running at the start of
 //    the previous step (set by device atomics), so finished short channels
@@ -216,20 +216,12 @@ __global__ void __launch_bounds__(B, 65536 / (B * 64))
   if (flags) atomicOr(p.d.status, flags);
 }
 
-template <typename T>
-__device__ __forceinline__ T shfl_down1(T v) { return __shfl_down_sync(0xffffffffu, v, 1); }
-template <>
-__device__ __forceinline__ float2 shfl_down1(float2 v) {
-  return make_float2(__shfl_down_sync(0xffffffffu, v.x, 1), __shfl_down_sync(0xffffffffu, v.y, 1));
-}
-
 // Persistent warp tiles: each warp walks tiles of SUB x 31 cells of one
 // channel (tile list in those units, longest channel first) with a grid-wide
 // stride over the active bound. Lane 0 evaluates the channel's control once per
 // tile and broadcasts it; the warp then takes the tile's SUB sub-tiles of 32
-// edges / 31 cells in turn: lane l evaluates edge e0 + l, the right state of an
-// edge and D+ of the left edge come by shuffle, so no block barrier is taken.
-// One CFL atomic per tile.
+// edges / 31 cells in turn: lane l evaluates edge e0 + l and D+ of the left
+// edge comes by shuffle, so no block barrier is taken. One CFL atomic per tile.
 template <typename R, int B, int CAP, int SUB>
 __global__ void __launch_bounds__(B, 65536 / (B * CAP))
     k_ens_step_warp(const EnsParams p, const typename Prec<R>::State in,
@@ -268,26 +260,20 @@ __global__ void __launch_bounds__(B, 65536 / (B * CAP))
       const int64_t e0 = t0 + sub * 31;
       if (e0 >= nc) break;  // past the channel's last cell (warp-uniform)
       const int64_t e = e0 + lane;
-      // left state of edge e: cell e-1 (cell 0 at the channel's start); right
-      // state: the next lane's left state, lane 31 loads its own; transmissive
-      // ends copy the adjacent cell
+      // states of edge e: cells e-1 and e, each lane loading both (a right
+      // state taken from the next lane by shuffle measured 4 % slower: every
+      // lane then waits for its neighbour's load); transmissive ends copy the
+      // adjacent cell, lanes past the channel's end read its last cell
       const bool valid = e <= nc;
       S wl[3], wr[3];
       const int64_t il = (e > 0) ? (e <= nc ? e - 1 : nc - 1) : 0;
+      const int64_t ir = (e < nc) ? e : nc - 1;
       wl[0] = in.h[base + il];
       wl[1] = in.q[base + il];
       wl[2] = in.z[base + il];
-#pragma unroll
-      for (int r = 0; r < 3; ++r) wr[r] = shfl_down1(wl[r]);
-      if (lane == 31 && e < nc) {
-        wr[0] = in.h[base + e];
-        wr[1] = in.q[base + e];
-        wr[2] = in.z[base + e];
-      }
-      if (e >= nc) {
-#pragma unroll
-        for (int r = 0; r < 3; ++r) wr[r] = wl[r];
-      }
+      wr[0] = in.h[base + ir];
+      wr[1] = in.q[base + ir];
+      wr[2] = in.z[base + ir];
       const int64_t i = e - 1;  // cell updated by this lane (lanes 1..31)
       if (mode == 1) {
         if (lane >= 1 && i < nc) {
