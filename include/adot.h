@@ -267,6 +267,15 @@ adot_status adot_mlp_get_params(adot_mlp* mlp, float* params);
  * three-tile pipeline (default); 1 = mma.sync; 2 = tcgen05, two independent
  * tile groups per CTA. ADOT_E_INVALID_ARG for another value. */
 adot_status adot_mlp_set_engine(adot_mlp* mlp, int engine);
+/* Test hook for the failure detection of the tensor-core pipeline (no
+ * counterpart in the paper): kind = 1 makes the next adot_mlp_forward with
+ * fused = 3 withhold one accumulator hand-off in its first CTA, so that the
+ * epilogue's bounded device-side wait (about 2^31 clock cycles, ~1 s) runs
+ * out; that call returns ADOT_E_TIMEOUT and the network stays usable. The hook
+ * clears itself after that one call; kind = 0 clears it. Nothing faults, traps
+ * or hangs: every wait of the kernel is bounded and the products in flight
+ * complete before its tensor memory is freed. */
+adot_status adot_mlp_inject_fault(adot_mlp* mlp, int kind);
 /* Training set: raw inputs X [n][7] and labels T [n][9] (float32, host or
  * device). Sets the standardisation (per-column mean and standard deviation)
  * and the training box (per-input min/max widened by 5% of the range). */

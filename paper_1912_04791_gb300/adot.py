@@ -92,6 +92,7 @@ def lib() -> ctypes.CDLL:
             "adot_mlp_set_params": ([_P, _P], i32),
             "adot_mlp_get_params": ([_P, _P], i32),
             "adot_mlp_set_engine": ([_P, i32], i32),
+            "adot_mlp_inject_fault": ([_P, i32], i32),
             "adot_mlp_set_data": ([_P, _P, _P, i64, i32], i32),
             "adot_mlp_get_stats": ([_P, _P, _P], i32),
             "adot_mlp_forward": ([_P, _P, i64, _P, i32], i32),
@@ -450,6 +451,11 @@ class Mlp:
         """Fused inference engine of the surrogate step: 0 = tcgen05 pipeline,
         1 = mma.sync, 2 = tcgen05 with two independent tile groups."""
         _check(lib().adot_mlp_set_engine(self.ptr, int(engine)), "adot_mlp_set_engine")
+
+    def inject_fault(self, kind: int = 1) -> None:
+        """Test hook: the next forward(fused=3) withholds one hand-off so that a
+        bounded device-side wait runs out (ADOT_E_TIMEOUT)."""
+        _check(lib().adot_mlp_inject_fault(self.ptr, int(kind)), "adot_mlp_inject_fault")
 
     def forward(self, Xs, fused=False) -> np.ndarray:
         """fused: 0/False per-layer kernels, 1/True mma.sync fused, 2 tcgen05 two

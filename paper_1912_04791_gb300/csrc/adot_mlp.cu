@@ -452,6 +452,7 @@ struct InferParams {
   float lo[kIn], hi[kIn];  // training box per raw input (with margin)
   float fr_lo, fr_hi;      // Froude band that falls back
   float Ag;
+  int withhold_commit;     // test hook: CTA 0 withholds its first accumulator commit
 };
 
 __host__ __device__ constexpr size_t infer_smem_bytes() {
@@ -1202,7 +1203,10 @@ __global__ void __launch_bounds__(kTpThreads, 1)
             else
               tc_issue_layer<kHid, kPad>(d, da, s_wdesc[kLayers - 1]);
           }
-          tc_commit(smem_addr(&bars.acc_full[sl]));
+          // (the test hook leaves CTA 0's first job uncommitted: its epilogue's
+          // bounded wait runs out and the kernel reports ST_TIMEOUT)
+          if (!(P.withhold_commit && blockIdx.x == 0 && kk == 0 && sl == 0))
+            tc_commit(smem_addr(&bars.acc_full[sl]));
           if (l == 0) tc_commit(smem_addr(&bars.ring_empty[r]));
         }
       }
@@ -1423,6 +1427,7 @@ struct adot_mlp {
   double graph_lr;
   int64_t graph_steps;
   int engine;          // fused inference: 0 = tcgen05 pipeline (default), 1 = mma.sync, 2 = tcgen05 two groups
+  int inject;          // adot_mlp_inject_fault: 1 = the next pipelined launch withholds a commit
   unsigned* d_status;  // sticky ST_* bits of the fused inference kernels
 };
 
@@ -1597,6 +1602,7 @@ cudaError_t launch_mlp_edges(const adot_mlp* m, const StepParams& sp, StateF32 s
   if (m->engine == 0) {
     // warp-specialised pipeline, one CTA per SM walking its tiles
     const int grid = (int)imin64(tc_tiles, sms);
+    P.withhold_commit = 0;
     k_mlp_tcp<true><<<grid, kTpThreads, kTpSmem, s>>>(P, sp, st, slot, absA, fb, nullptr, 0, nullptr,
                                                       &sp.ctl->status);
     return cudaGetLastError();
@@ -1691,6 +1697,12 @@ void adot_mlp_destroy(adot_mlp* m) {
   mlp_free(m);
 }
 
+adot_status adot_mlp_inject_fault(adot_mlp* m, int kind) {
+  if (!m || kind < 0 || kind > 1) return ADOT_E_INVALID_ARG;
+  m->inject = kind;
+  return ADOT_OK;
+}
+
 adot_status adot_mlp_set_engine(adot_mlp* m, int engine) {
   if (!m || engine < 0 || engine > 2) return ADOT_E_INVALID_ARG;
   m->engine = engine;
@@ -1780,12 +1792,15 @@ adot_status adot_mlp_forward(adot_mlp* m, const float* Xs, int64_t n, float* Y, 
     int sms = 152;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device);
     CKM(cudaMemsetAsync(m->d_status, 0, sizeof(unsigned), m->stream));
-    if (fused == 2)
+    if (fused == 2) {
       k_mlp_tc<false><<<(unsigned)imin64((tiles + 1) / 2, sms), kTcThreads, kTcSmem, m->stream>>>(
           P, sp, StateF32{}, 0, nullptr, nullptr, m->Xb, n, m->Y, m->d_status);
-    else
+    } else {
+      P.withhold_commit = m->inject == 1 ? 1 : 0;
+      m->inject = 0;
       k_mlp_tcp<false><<<(unsigned)imin64(tiles, sms), kTpThreads, kTpSmem, m->stream>>>(
           P, sp, StateF32{}, 0, nullptr, nullptr, m->Xb, n, m->Y, m->d_status);
+    }
     CKM(cudaGetLastError());
   } else if (fused) {
     constexpr size_t sm = infer_smem_bytes();

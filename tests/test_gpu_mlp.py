@@ -71,6 +71,29 @@ def test_forward_tcgen05_matches_reference(gpu, n, fused):
     assert np.array_equal(y_tc, y_other)
 
 
+def test_tcgen05_bounded_wait_reports_timeout(gpu):
+    """Failure detection of the tensor-core pipeline without a GPU fault: the
+    test hook withholds one accumulator hand-off in the first CTA, so that the
+    epilogue's bounded wait (about a second) runs out; the call reports
+    ADOT_E_TIMEOUT, and the same network then gives the same outputs as
+    before (the hook clears itself; clearing it explicitly also works)."""
+    theta = _theta(1)
+    X = np.random.default_rng(7).standard_normal((4099, 7)).astype(np.float32)
+    with gpu.Mlp(8192) as net:
+        net.set_params(theta)
+        ref = net.forward(X, fused=3)
+        net.inject_fault(1)
+        with pytest.raises(gpu.AdotError) as err:
+            net.forward(X, fused=3)
+        assert err.value.status == gpu.E_TIMEOUT
+        assert np.array_equal(net.forward(X, fused=3), ref)
+        net.inject_fault(1)
+        net.inject_fault(0)
+        assert np.array_equal(net.forward(X, fused=3), ref)
+        with pytest.raises(gpu.AdotError):
+            net.inject_fault(2)
+
+
 def test_engine_value_checked(gpu):
     with gpu.Mlp(64) as net:
         for e in (1, 2, 0):
