@@ -42,11 +42,11 @@ FLOPS_PER_CELL_UPDATE = {"block": 633.6, "warp": 628.0}
 # DRAM read + write bytes per cell-update of one launch (ncu, N = 4e6): the
 # ~24 B read match the algorithmic read; part of the 24 B written is still in
 # L2. None where the kernel changed after its capture.
-DRAM_BYTES_PER_CELL_UPDATE = {"block": None, "warp": (97.88e6 + 64.74e6) / 4e6}
+DRAM_BYTES_PER_CELL_UPDATE = {"block": None, "warp": (97.90e6 + 65.27e6) / 4e6}
 BYTES_PER_CELL_UPDATE = 48.0  # float-float state: 3 x 8 B read + 3 x 8 B written
 # Executed thread instructions per cell-update of one launch (ncu smsp__inst_executed x 32 / cells,
 # N = 4e6, the 1-in-32 repeated edge included); None where the kernel changed after its capture.
-INSTR_PER_CELL_UPDATE = {"block": None, "warp": 92.63e6 * 32 / 4e6}
+INSTR_PER_CELL_UPDATE = {"block": None, "warp": 93.37e6 * 32 / 4e6}
 
 
 def issue_roofline(kind: str, n: int, per_launch_s: float):
