@@ -28,7 +28,7 @@ _lib = None
 
 # status codes (mirror the C enum)
 OK, E_INVALID, E_DEPTH, E_NONFINITE, E_NONHYPERBOLIC, E_NOCONVERGE = range(6)
-LAW_GRASS, LAW_MPM = 0, 1
+LAW_GRASS, LAW_MPM, LAW_GRASS_THR = 0, 1, 2
 ABS_ANALYTIC, ABS_NUMERIC, ABS_SYLVESTER, ABS_NEWTON = 0, 1, 2, 3
 BC_TRANSMISSIVE, BC_PERIODIC, BC_INFLOW_Q, BC_OUTFLOW_H, BC_INFLOW_QZ = range(5)
 
@@ -48,6 +48,7 @@ class Law(ctypes.Structure):
         ("s_rel", ctypes.c_double),
         ("d50", ctypes.c_double),
         ("manning_n", ctypes.c_double),
+        ("u_cr", ctypes.c_double),
     ]
 
 
@@ -69,6 +70,12 @@ class Cfg(ctypes.Structure):
 def grass(Ag: float, xi: float = 1.0, g: float = 9.81) -> Law:
     """Grass law q_s = A_g u^3 (Eq. Grass)."""
     return Law(LAW_GRASS, g, xi, Ag, 0.0, 0.0, 0.0)
+
+
+def grass_thr(Ag: float, u_cr: float, xi: float = 1.0, g: float = 9.81) -> Law:
+    """Grass law with a threshold velocity (Eq. GrassThr), read as
+    q_s = A_g sign(u) max(|u| - u_cr, 0)^3."""
+    return Law(LAW_GRASS_THR, g, xi, Ag, 0.0, 0.0, 0.0, u_cr)
 
 
 def mpm(s_rel: float, d50: float, manning_n: float, xi: float = 1.0, g: float = 9.81) -> Law:

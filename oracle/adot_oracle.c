@@ -50,7 +50,7 @@ enum {
   ORC_E_NOCONVERGE = 5
 };
 
-enum { ORC_LAW_GRASS = 0, ORC_LAW_MPM = 1 };
+enum { ORC_LAW_GRASS = 0, ORC_LAW_MPM = 1, ORC_LAW_GRASS_THR = 2 };
 
 /* How |A| is evaluated at a quadrature node. */
 enum {
@@ -76,6 +76,7 @@ typedef struct {
   double s_rel;     /* MPM: relative grain density S_g */
   double d50;       /* MPM: median grain size [m] */
   double manning_n; /* MPM: Manning coefficient (= 1/K_s) */
+  double u_cr;      /* Grass with threshold: incipient transport velocity [m/s] */
 } orc_law;
 
 typedef struct {
@@ -115,6 +116,24 @@ int orc_sediment(const orc_law* L, double h, double q, double* qs, double* dqs_d
     *qs = L->Ag * u * u * u;
     *dqs_dh = -3.0 * L->Ag * u * u * u / h;
     *dqs_dq = 3.0 * L->Ag * u * u / h;
+    return ORC_OK;
+  }
+  if (L->kind == ORC_LAW_GRASS_THR) {
+    /* Eq. GrassThr, q_s = A_g (u - u_cr)^3, read as transport along u that
+     * starts at |u| = u_cr: q_s = A_g sign(u) v^3 with v = |u| - u_cr > 0, and
+     * q_s = 0 for |u| <= u_cr. With d|u|/dq = sign(u)/h and d|u|/dh =
+     * -sign(u) u/h: dq_s/dq = 3 A_g v^2/h, dq_s/dh = -3 A_g v^2 u/h. */
+    double v = fabs(u) - L->u_cr;
+    if (v <= 0.0) {
+      *qs = 0.0;
+      *dqs_dh = 0.0;
+      *dqs_dq = 0.0;
+      return ORC_OK;
+    }
+    double sgn = (u > 0.0) ? 1.0 : -1.0;
+    *qs = L->Ag * sgn * v * v * v;
+    *dqs_dq = 3.0 * L->Ag * v * v / h;
+    *dqs_dh = -3.0 * L->Ag * v * v * u / h;
     return ORC_OK;
   }
   if (L->kind == ORC_LAW_MPM) {
