@@ -51,8 +51,10 @@ typedef enum {
 /* Sediment transport closure (Sec. 2). */
 typedef enum {
   ADOT_LAW_GRASS = 0, /* q_s = A_g u^3 (Eq. Grass) */
-  ADOT_LAW_MPM = 1    /* q_s = sign(u) 8 (theta-0.047)_+^1.5 sqrt(g (s-1) d50^3), Eq. MPM,
+  ADOT_LAW_MPM = 1,   /* q_s = sign(u) 8 (theta-0.047)_+^1.5 sqrt(g (s-1) d50^3), Eq. MPM,
                          theta = n^2 u^2 / ((s-1) d50 h^(1/3)) (Eq. Shields, Manning s_f) */
+  ADOT_LAW_GRASS_THR = 2 /* q_s = A_g (u - u_cr)^3 (Eq. GrassThr), read as
+                            A_g sign(u) max(|u| - u_cr, 0)^3: no transport at or below u_cr */
 } adot_law_kind;
 
 /* Arithmetic of the state and the fluctuations. */
@@ -80,6 +82,7 @@ typedef struct {
   double s_rel;     /* MPM: relative grain density */
   double d50;       /* MPM: median grain size [m] */
   double manning_n; /* MPM: Manning coefficient [s/m^(1/3)] */
+  double u_cr;      /* Grass with threshold: incipient transport velocity [m/s], >= 0 */
 } adot_law;
 
 typedef struct {

@@ -101,6 +101,8 @@ adot_status adot::validate_config(const adot_config* c) {
   if (c->law.kind == ADOT_LAW_MPM) {
     if (!(c->law.s_rel > 1.0) || !(c->law.d50 > 0.0) || !(c->law.manning_n >= 0.0))
       return ADOT_E_INVALID_ARG;
+  } else if (c->law.kind == ADOT_LAW_GRASS_THR) {
+    if (!(c->law.u_cr >= 0.0) || !isfinite(c->law.u_cr)) return ADOT_E_INVALID_ARG;
   } else if (c->law.kind != ADOT_LAW_GRASS) {
     return ADOT_E_INVALID_ARG;
   }
@@ -139,8 +141,9 @@ void adot::make_step_params(const adot_config* cfg, StepParams* out) {
     mpm_c = L.manning_n * L.manning_n / ((L.s_rel - 1.0) * L.d50);
     mpm_scale = L.xi * sqrt(L.g * (L.s_rel - 1.0) * L.d50 * L.d50 * L.d50);
   }
-  p.ld = LawT<double>{L.g, K3, mpm_c, mpm_scale};
-  p.lf = LawT<float>{(float)L.g, (float)K3, (float)mpm_c, (float)mpm_scale};
+  const double ucr = (L.kind == ADOT_LAW_GRASS_THR) ? L.u_cr : 0.0;
+  p.ld = LawT<double>{L.g, K3, mpm_c, mpm_scale, ucr};
+  p.lf = LawT<float>{(float)L.g, (float)K3, (float)mpm_c, (float)mpm_scale, (float)ucr};
 }
 
 namespace {

@@ -20,7 +20,7 @@
 
 namespace adot {
 
-enum : int { LAW_GRASS = 0, LAW_MPM = 1 };
+enum : int { LAW_GRASS = 0, LAW_MPM = 1, LAW_GRASS_THR = 2 };
 
 // Status bits recorded in the device control block.
 enum : unsigned {
@@ -38,6 +38,7 @@ struct LawT {
   T K3;         // Grass: 3 xi A_g, so b = K3 u^2 / h and a = -b u
   T mpm_c;      // MPM: n^2 / ((s - 1) d50), theta = mpm_c u^2 h^(-1/3)
   T mpm_scale;  // MPM: xi sqrt(g (s - 1) d50^3)
+  T ucr;        // Grass with threshold: incipient transport velocity u_cr
 };
 
 // Gap below which |A| dW switches to the Newton divided-difference form
@@ -89,6 +90,19 @@ __device__ __forceinline__ void sediment_derivs(const LawT<T>& L, T h, T q, T in
     (void)q;
     b = L.K3 * u * u * inv_h;
     a = -b * u;
+  } else if constexpr (LAW == LAW_GRASS_THR) {
+    // Eq. GrassThr read as q_s = A_g sign(u) v^3, v = |u| - u_cr > 0, else 0:
+    // b = K3 v^2 / h, a = -b u (d|u|/dq = sign(u)/h, d|u|/dh = -sign(u) u/h)
+    (void)h;
+    (void)q;
+    const T v = d_abs(u) - L.ucr;
+    if (v > T(0)) {
+      b = L.K3 * v * v * inv_h;
+      a = -b * u;
+    } else {
+      a = T(0);
+      b = T(0);
+    }
   } else {
     T r3 = d_rcbrt(h);
     T theta = L.mpm_c * u * u * r3;

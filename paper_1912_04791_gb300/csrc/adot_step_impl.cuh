@@ -516,6 +516,7 @@ cudaError_t launch_step_impl(const StepParams& p, int law, StepVariant v, typena
                              typename Prec<R>::State out, int slot, cudaStream_t s) {
   if (law == LAW_GRASS) return launch_step_law<R, LAW_GRASS>(p, v, in, out, slot, s);
   if (law == LAW_MPM) return launch_step_law<R, LAW_MPM>(p, v, in, out, slot, s);
+  if (law == LAW_GRASS_THR) return launch_step_law<R, LAW_GRASS_THR>(p, v, in, out, slot, s);
   return cudaErrorInvalidValue;
 }
 
@@ -530,6 +531,8 @@ cudaError_t launch_rho_impl(const StepParams& p, int law, typename Prec<R>::Stat
     k_rho<R, LAW_GRASS><<<(unsigned)g, 256, 0, s>>>(p, st, slot);
   else if (law == LAW_MPM)
     k_rho<R, LAW_MPM><<<(unsigned)g, 256, 0, s>>>(p, st, slot);
+  else if (law == LAW_GRASS_THR)
+    k_rho<R, LAW_GRASS_THR><<<(unsigned)g, 256, 0, s>>>(p, st, slot);
   else
     return cudaErrorInvalidValue;
   return cudaGetLastError();
