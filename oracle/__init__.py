@@ -9,7 +9,8 @@ Every routine follows the paper (arXiv 1912.04791) as cited in the C source:
 Eq. W&A_definition (flux matrix), Eq. charPol / lambda / parameters /
 parameters_bis (analytic eigenvalues), Eq. RR / RR-1 / circPerm (eigenvectors),
 Eq. asbA / ExAbsA (|A|), Eq. path / DOTjumpN (fluctuations), Eq. scheme
-(update). ``exact.py`` holds closed-form and exact solutions used as pins.
+(update, with the Strickler friction source of Sec. 2 when K_s > 0), and the
+sediment feed through an end of the Soni case (Sec. 5.1). ``exact.py`` holds closed-form and exact solutions used as pins.
 """
 from __future__ import annotations
 
@@ -28,9 +29,10 @@ _lib = None
 
 # status codes (mirror the C enum)
 OK, E_INVALID, E_DEPTH, E_NONFINITE, E_NONHYPERBOLIC, E_NOCONVERGE = range(6)
-LAW_GRASS, LAW_MPM, LAW_GRASS_THR = 0, 1, 2
+LAW_GRASS, LAW_MPM, LAW_GRASS_THR, LAW_POWER = 0, 1, 2, 3
 ABS_ANALYTIC, ABS_NUMERIC, ABS_SYLVESTER, ABS_NEWTON = 0, 1, 2, 3
-BC_TRANSMISSIVE, BC_PERIODIC, BC_INFLOW_Q, BC_OUTFLOW_H, BC_INFLOW_QZ = range(5)
+BC_TRANSMISSIVE, BC_PERIODIC, BC_INFLOW_Q, BC_OUTFLOW_H, BC_INFLOW_QZ, BC_INFLOW_QS, \
+    BC_OUTFLOW_HS = range(7)
 
 
 class OracleError(RuntimeError):
@@ -49,6 +51,7 @@ class Law(ctypes.Structure):
         ("d50", ctypes.c_double),
         ("manning_n", ctypes.c_double),
         ("u_cr", ctypes.c_double),
+        ("beta", ctypes.c_double),
     ]
 
 
@@ -64,6 +67,7 @@ class Cfg(ctypes.Structure):
         ("bc_right", ctypes.c_int),
         ("bcl", ctypes.c_double * 3),
         ("bcr", ctypes.c_double * 3),
+        ("ks", ctypes.c_double),
     ]
 
 
@@ -76,6 +80,12 @@ def grass_thr(Ag: float, u_cr: float, xi: float = 1.0, g: float = 9.81) -> Law:
     """Grass law with a threshold velocity (Eq. GrassThr), read as
     q_s = A_g sign(u) max(|u| - u_cr, 0)^3."""
     return Law(LAW_GRASS_THR, g, xi, Ag, 0.0, 0.0, 0.0, u_cr)
+
+
+def power(alpha: float, beta: float, u_cr: float = 0.0, xi: float = 1.0, g: float = 9.81) -> Law:
+    """Power law of the velocity, q_s = alpha sign(u) max(|u| - u_cr, 0)^beta
+    (Eq. Soni_qs with u_cr = 0; Eq. GrassThr at beta = 3)."""
+    return Law(LAW_POWER, g, xi, alpha, 0.0, 0.0, 0.0, u_cr, beta)
 
 
 def mpm(s_rel: float, d50: float, manning_n: float, xi: float = 1.0, g: float = 9.81) -> Law:
@@ -232,7 +242,9 @@ def abs_psi(law: Law, WL: np.ndarray, WR: np.ndarray, method: int = ABS_ANALYTIC
 
 def make_cfg(n: int, x_min: float, x_max: float, cfl: float, law: Law,
              bc_left: int = BC_TRANSMISSIVE, bc_right: int = BC_TRANSMISSIVE,
-             bcl=(0.0, 0.0, 0.0), bcr=(0.0, 0.0, 0.0), method: int = ABS_ANALYTIC) -> Cfg:
+             bcl=(0.0, 0.0, 0.0), bcr=(0.0, 0.0, 0.0), method: int = ABS_ANALYTIC,
+             ks: float = 0.0) -> Cfg:
+    """Run configuration; ks > 0 adds the Strickler friction source (Sec. 2)."""
     c = Cfg()
     c.n = n
     c.x_min = x_min
@@ -245,6 +257,7 @@ def make_cfg(n: int, x_min: float, x_max: float, cfl: float, law: Law,
     for i in range(3):
         c.bcl[i] = bcl[i]
         c.bcr[i] = bcr[i]
+    c.ks = ks
     return c
 
 

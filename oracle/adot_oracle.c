@@ -13,7 +13,8 @@
  * so every product and sum rounds exactly as written).
  *
  * Contents (each function cites the passage it follows):
- *   sediment laws and their derivatives ............ Sec. 2, Eq. Grass, Eq. MPM/Shields
+ *   sediment laws and their derivatives ............ Sec. 2, Eq. Grass, Eq. GrassThr,
+ *                                                    Eq. MPM/Shields, Eq. Soni_qs
  *   flux matrix A(W) ............................... Sec. 2, Eq. W&A_definition
  *   analytical eigenstructure (A-DOT) .............. Sec. 3.3, Eq. charPol, lambda,
  *                                                    parameters, parameters_bis, RR, RR-1,
@@ -27,8 +28,10 @@
  *                                                    eigenvalues; Newton form is the
  *                                                    coalescence reading)
  *   DOT fluctuations with G=3 Gauss-Legendre ....... Eq. path, Eq. DOTjumpN
- *   first-order update and time loop ............... Eq. scheme (S = 0, frictionless,
- *                                                    Sec. 4 opening)
+ *   first-order update and time loop ............... Eq. scheme; S = 0 (frictionless,
+ *                                                    Sec. 4 opening) or the Strickler
+ *                                                    friction source of Sec. 2
+ *   sediment feed through an end (Soni case) ....... Sec. 5.1 boundary data
  *
  * Parity status: every function here is pinned by tests (library eigensolver,
  * closed forms, invariants, textbook special cases); none is "parity unpinned".
@@ -50,7 +53,7 @@ enum {
   ORC_E_NOCONVERGE = 5
 };
 
-enum { ORC_LAW_GRASS = 0, ORC_LAW_MPM = 1, ORC_LAW_GRASS_THR = 2 };
+enum { ORC_LAW_GRASS = 0, ORC_LAW_MPM = 1, ORC_LAW_GRASS_THR = 2, ORC_LAW_POWER = 3 };
 
 /* How |A| is evaluated at a quadrature node. */
 enum {
@@ -65,7 +68,11 @@ enum {
   ORC_BC_PERIODIC = 1,
   ORC_BC_INFLOW_Q = 2,  /* ghost q = v0, h and z copied from the adjacent cell */
   ORC_BC_OUTFLOW_H = 3, /* ghost h = v0, q and z copied */
-  ORC_BC_INFLOW_QZ = 4  /* ghost q = v0, z = v1 - v2 * t, h copied (Test 2 inflow) */
+  ORC_BC_INFLOW_QZ = 4, /* ghost q = v0, z = v1 - v2 * t, h copied (Test 2 inflow) */
+  ORC_BC_INFLOW_QS = 5, /* ghost q = v0, h copied, z extrapolated linearly from the two
+                           cells next to the end; the sediment discharge v1 (signed,
+                           along +x) is imposed through the end edge */
+  ORC_BC_OUTFLOW_HS = 6 /* ghost h = v0, q copied, z extrapolated linearly */
 };
 
 typedef struct {
@@ -76,7 +83,8 @@ typedef struct {
   double s_rel;     /* MPM: relative grain density S_g */
   double d50;       /* MPM: median grain size [m] */
   double manning_n; /* MPM: Manning coefficient (= 1/K_s) */
-  double u_cr;      /* Grass with threshold: incipient transport velocity [m/s] */
+  double u_cr;      /* Grass with threshold / power law: incipient velocity [m/s] */
+  double beta;      /* power law: exponent (>= 1) */
 } orc_law;
 
 typedef struct {
@@ -87,6 +95,7 @@ typedef struct {
   int abs_method;   /* ORC_ABS_* used for every node */
   int bc_left, bc_right;
   double bcl[3], bcr[3];
+  double ks;        /* Strickler coefficient of the friction source [m^(1/3)/s]; 0 = none */
 } orc_cfg;
 
 /* Threshold on the eigenvalue gap, relative to c, below which |A| is taken
@@ -118,11 +127,13 @@ int orc_sediment(const orc_law* L, double h, double q, double* qs, double* dqs_d
     *dqs_dq = 3.0 * L->Ag * u * u / h;
     return ORC_OK;
   }
-  if (L->kind == ORC_LAW_GRASS_THR) {
+  if (L->kind == ORC_LAW_GRASS_THR || L->kind == ORC_LAW_POWER) {
     /* Eq. GrassThr, q_s = A_g (u - u_cr)^3, read as transport along u that
      * starts at |u| = u_cr: q_s = A_g sign(u) v^3 with v = |u| - u_cr > 0, and
      * q_s = 0 for |u| <= u_cr. With d|u|/dq = sign(u)/h and d|u|/dh =
-     * -sign(u) u/h: dq_s/dq = 3 A_g v^2/h, dq_s/dh = -3 A_g v^2 u/h. */
+     * -sign(u) u/h: dq_s/dq = 3 A_g v^2/h, dq_s/dh = -3 A_g v^2 u/h.
+     * Power law (Eq. Soni_qs, q_s = alpha u^beta, alpha in Ag, u_cr = 0 there):
+     * the same with the exponent beta, dq_s/dq = beta A_g v^(beta-1)/h. */
     double v = fabs(u) - L->u_cr;
     if (v <= 0.0) {
       *qs = 0.0;
@@ -131,9 +142,17 @@ int orc_sediment(const orc_law* L, double h, double q, double* qs, double* dqs_d
       return ORC_OK;
     }
     double sgn = (u > 0.0) ? 1.0 : -1.0;
-    *qs = L->Ag * sgn * v * v * v;
-    *dqs_dq = 3.0 * L->Ag * v * v / h;
-    *dqs_dh = -3.0 * L->Ag * v * v * u / h;
+    if (L->kind == ORC_LAW_GRASS_THR) {
+      *qs = L->Ag * sgn * v * v * v;
+      *dqs_dq = 3.0 * L->Ag * v * v / h;
+      *dqs_dh = -3.0 * L->Ag * v * v * u / h;
+      return ORC_OK;
+    }
+    if (!(L->beta >= 1.0)) return ORC_E_INVALID;
+    double vb1 = pow(v, L->beta - 1.0);
+    *qs = L->Ag * sgn * vb1 * v;
+    *dqs_dq = L->beta * L->Ag * vb1 / h;
+    *dqs_dh = -L->beta * L->Ag * vb1 * u / h;
     return ORC_OK;
   }
   if (L->kind == ORC_LAW_MPM) {
@@ -612,7 +631,7 @@ int orc_fluct(const orc_law* L, int method, int64_t n, const double* WL, const d
 }
 
 /* ---------------------------------------------------------------------- */
-/* Time loop (Eq. scheme with S = 0).                                       */
+/* Time loop (Eq. scheme).                                                 */
 /* ---------------------------------------------------------------------- */
 
 /* Largest characteristic speed max(|l1|, |l3|) at a state: the extreme
@@ -626,8 +645,13 @@ int orc_spectral_radius(const orc_law* L, double h, double q, double* rho) {
   return ORC_OK;
 }
 
+/* Ghost state beyond one end: adj = the cell next to the end, nxt = the one
+ * after it (equal to adj when the domain has one cell). The extrapolating
+ * kinds continue the bed of a sloping flume, z_g = 2 z_adj - z_nxt, so that a
+ * uniform flow on a constant slope meets the same bed step at the end edge as
+ * at every inner edge. */
 static void orc_ghost(int kind, const double v[3], double t, const double adj[3],
-                      double out[3]) {
+                      const double nxt[3], double out[3]) {
   out[0] = adj[0];
   out[1] = adj[1];
   out[2] = adj[2];
@@ -638,8 +662,24 @@ static void orc_ghost(int kind, const double v[3], double t, const double adj[3]
       out[1] = v[0];
       out[2] = v[1] - v[2] * t;
       break;
+    case ORC_BC_INFLOW_QS:
+      out[1] = v[0];
+      out[2] = 2.0 * adj[2] - nxt[2];
+      break;
+    case ORC_BC_OUTFLOW_HS:
+      out[0] = v[0];
+      out[2] = 2.0 * adj[2] - nxt[2];
+      break;
     default: break; /* transmissive: copy */
   }
+}
+
+/* Momentum source of Eq. SV-Ex2 at a cell state, -g h s_f with the Strickler
+ * closure of Sec. 2, s_f = q|q| / (K_s^2 h^(10/3)) (the printed q^2 taken with
+ * the sign of q, so that friction opposes the flow in both directions). */
+static double orc_friction_source(double g, double ks, double h, double q) {
+  double sf = q * fabs(q) / (ks * ks * pow(h, 10.0 / 3.0));
+  return -g * h * sf;
 }
 
 /* Advances the state (h, q, z arrays of n cells, in place) by at most
@@ -656,6 +696,7 @@ int orc_run(const orc_cfg* cfg, double* h, double* q, double* z, int64_t max_ste
   if (n < 1 || !(cfg->cfl > 0.0) || !(cfg->x_max > cfg->x_min)) return ORC_E_INVALID;
   int periodic = (cfg->bc_left == ORC_BC_PERIODIC);
   if (periodic != (cfg->bc_right == ORC_BC_PERIODIC)) return ORC_E_INVALID;
+  if (!(cfg->ks >= 0.0)) return ORC_E_INVALID;
   double dx = (cfg->x_max - cfg->x_min) / (double)n;
   int64_t ne = n + 1;
   double* Dm = work;
@@ -686,13 +727,17 @@ int orc_run(const orc_cfg* cfg, double* h, double* q, double* z, int64_t max_ste
         wl[0] = h[il]; wl[1] = q[il]; wl[2] = z[il];
         wr[0] = h[ir]; wr[1] = q[ir]; wr[2] = z[ir];
       } else if (e == 0) {
+        int64_t j = (n > 1) ? 1 : 0;
         double adj[3] = {h[0], q[0], z[0]};
-        orc_ghost(cfg->bc_left, cfg->bcl, t, adj, wl);
+        double nxt[3] = {h[j], q[j], z[j]};
+        orc_ghost(cfg->bc_left, cfg->bcl, t, adj, nxt, wl);
         wr[0] = h[0]; wr[1] = q[0]; wr[2] = z[0];
       } else if (e == n) {
+        int64_t j = (n > 1) ? n - 2 : 0;
         double adj[3] = {h[n - 1], q[n - 1], z[n - 1]};
+        double nxt[3] = {h[j], q[j], z[j]};
         wl[0] = h[n - 1]; wl[1] = q[n - 1]; wl[2] = z[n - 1];
-        orc_ghost(cfg->bc_right, cfg->bcr, t, adj, wr);
+        orc_ghost(cfg->bc_right, cfg->bcr, t, adj, nxt, wr);
       } else {
         wl[0] = h[e - 1]; wl[1] = q[e - 1]; wl[2] = z[e - 1];
         wr[0] = h[e]; wr[1] = q[e]; wr[2] = z[e];
@@ -709,11 +754,42 @@ int orc_run(const orc_cfg* cfg, double* h, double* q, double* z, int64_t max_ste
       }
     }
     if (status) return status;
-    /* update (Eq. scheme): W_i -= dt/dx (D-_{i+1/2} + D+_{i-1/2}) */
+    /* Sediment feed (Sec. 5.1: the solid discharge is set at the upstream
+     * end). The bed row of Eq. scheme for cell i reads
+     * z_i -= dt/dx (F_{i+1/2} - F_{i-1/2}) with the edge discharge
+     * F_{i+1/2} = xi q_s(W_i) + D-_{i+1/2} = xi q_s(W_{i+1}) - D+_{i+1/2}. A
+     * feeding end's edge discharge is the imposed xi q_s,in, so the bed gains
+     * exactly what is fed: the bed row of D+ of edge 0 (cell 0's only left term)
+     * becomes xi (q_s(W_0) - q_s,in), that of D- of edge n
+     * xi (q_s,in - q_s(W_{n-1})). The h and q rows keep the DOT edge against the
+     * ghost. (On a bed slope s the inner edges also carry the dissipative bed
+     * flux of |A| dW, about |A|_zz s dx / 2, which the imposed discharge does
+     * not; a uniform flow fed its own q_s therefore adjusts over the first cell
+     * by that first-order amount.) */
+    if (!periodic && (cfg->bc_left == ORC_BC_INFLOW_QS || cfg->bc_right == ORC_BC_INFLOW_QS)) {
+      double xi = cfg->law.xi;
+      if (cfg->bc_left == ORC_BC_INFLOW_QS) {
+        double qs, a, b;
+        int st = orc_sediment(&cfg->law, h[0], q[0], &qs, &a, &b);
+        if (st) return st;
+        Dp[2 * ne + 0] = xi * qs - xi * cfg->bcl[1];
+      }
+      if (cfg->bc_right == ORC_BC_INFLOW_QS) {
+        double qs, a, b;
+        int st = orc_sediment(&cfg->law, h[n - 1], q[n - 1], &qs, &a, &b);
+        if (st) return st;
+        Dm[2 * ne + n] = xi * cfg->bcr[1] - xi * qs;
+      }
+    }
+    /* update (Eq. scheme): W_i -= dt/dx (D-_{i+1/2} + D+_{i-1/2}) - dt S(W_i),
+     * S = (0, -g h s_f, 0) taken at the step's starting state */
     double nu = dt / dx;
+    int friction = cfg->ks > 0.0;
     for (int64_t i = 0; i < n; ++i) {
-      h[i] = h[i] - nu * (Dm[0 * ne + i + 1] + Dp[0 * ne + i]);
-      q[i] = q[i] - nu * (Dm[1 * ne + i + 1] + Dp[1 * ne + i]);
+      double h0 = h[i], q0 = q[i];
+      h[i] = h0 - nu * (Dm[0 * ne + i + 1] + Dp[0 * ne + i]);
+      q[i] = q0 - nu * (Dm[1 * ne + i + 1] + Dp[1 * ne + i]);
+      if (friction) q[i] = q[i] + dt * orc_friction_source(cfg->law.g, cfg->ks, h0, q0);
       z[i] = z[i] - nu * (Dm[2 * ne + i + 1] + Dp[2 * ne + i]);
       if (!(h[i] > 0.0)) status = ORC_E_DEPTH;
       if (!isfinite(h[i]) || !isfinite(q[i]) || !isfinite(z[i])) status = ORC_E_NONFINITE;

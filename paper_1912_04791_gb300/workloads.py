@@ -18,7 +18,8 @@ G = 9.81
 XI_P04 = 1.0 / (1.0 - 0.4)  # porosity p = 0.4
 
 # boundary kinds (same meaning on both sides of the boundary; values below)
-BC_TRANSMISSIVE, BC_PERIODIC, BC_INFLOW_Q, BC_OUTFLOW_H, BC_INFLOW_QZ = range(5)
+BC_TRANSMISSIVE, BC_PERIODIC, BC_INFLOW_Q, BC_OUTFLOW_H, BC_INFLOW_QZ, BC_INFLOW_QS, \
+    BC_OUTFLOW_HS = range(7)
 
 
 @dataclass
@@ -90,6 +91,28 @@ def gaussian_bump(n: int, Ag: float = 0.001) -> Problem:
     q = np.full(n, 0.6)
     return Problem("gaussian_bump", n, 0.0, 10.0, 0.9, 10.0, Ag, XI_P04, h, q, z,
                    BC_INFLOW_Q, BC_OUTFLOW_H, (0.6, 0.0, 0.0), (0.33, 0.0, 0.0))
+
+
+def soni_aggradation(n: int = 100, overfeed: float = 4.0, s0: float = 3.56e-3,
+                     length: float = 30.0) -> Problem:
+    """Aggradation by sediment overfeeding in a sloping flume (Sec. 5.1, the
+    Soni case), per unit width: h = 0.05 m, q = 0.02 m^2/s, z = 1.2 - s0 x
+    with s0 = 3.56 per mille on [0, 30] m (Eq. Soni0); transport
+    q_s = alpha u^beta, alpha = 1.45e-3, beta = 5 (Eq. Soni_qs); porosity 0.4;
+    Strickler friction K_s = 49.4 m^(1/3)/s; t_end = 2400 s. Upstream: q = 0.02
+    and the solid discharge (1 + overfeed) alpha (q/h)^beta, i.e. the
+    equilibrium discharge of the initial uniform flow raised by
+    Delta Q_S = overfeed Q_S0 (4 in the paper); downstream: h = 0.05. Both
+    ghosts continue the bed slope. CFL 0.9 (not printed for this case)."""
+    h0, q0, alpha, beta = 0.05, 0.02, 1.45e-3, 5.0
+    x = cell_centres(n, 0.0, length)
+    z = 1.2 - s0 * x
+    feed = (1.0 + overfeed) * alpha * (q0 / h0) ** beta
+    return Problem("soni_aggradation", n, 0.0, length, 0.9, 2400.0, alpha, XI_P04,
+                   np.full(n, h0), np.full(n, q0), z, BC_INFLOW_QS, BC_OUTFLOW_HS,
+                   (q0, feed, 0.0), (h0, 0.0, 0.0),
+                   extra={"ks": 49.4, "beta": beta, "s0": s0, "h0": h0, "q0": q0,
+                          "qs0": alpha * (q0 / h0) ** beta})
 
 
 def lake_at_rest(n: int, seed: int = 7, level: float = 1.0) -> Problem:
