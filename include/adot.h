@@ -53,8 +53,11 @@ typedef enum {
   ADOT_LAW_GRASS = 0, /* q_s = A_g u^3 (Eq. Grass) */
   ADOT_LAW_MPM = 1,   /* q_s = sign(u) 8 (theta-0.047)_+^1.5 sqrt(g (s-1) d50^3), Eq. MPM,
                          theta = n^2 u^2 / ((s-1) d50 h^(1/3)) (Eq. Shields, Manning s_f) */
-  ADOT_LAW_GRASS_THR = 2 /* q_s = A_g (u - u_cr)^3 (Eq. GrassThr), read as
-                            A_g sign(u) max(|u| - u_cr, 0)^3: no transport at or below u_cr */
+  ADOT_LAW_GRASS_THR = 2, /* q_s = A_g (u - u_cr)^3 (Eq. GrassThr), read as
+                             A_g sign(u) max(|u| - u_cr, 0)^3: no transport at or below u_cr */
+  ADOT_LAW_POWER = 3      /* q_s = A_g sign(u) max(|u| - u_cr, 0)^beta, beta >= 1: the power
+                             law of Eq. Soni_qs (alpha = A_g, u_cr = 0); beta = 3 is
+                             ADOT_LAW_GRASS_THR */
 } adot_law_kind;
 
 /* Arithmetic of the state and the fluctuations. */
@@ -71,7 +74,15 @@ typedef enum {
   ADOT_BC_PERIODIC = 1,     /* both ends: the domain wraps */
   ADOT_BC_INFLOW_Q = 2,     /* ghost q = value[0]; h, z copied */
   ADOT_BC_OUTFLOW_H = 3,    /* ghost h = value[0]; q, z copied */
-  ADOT_BC_INFLOW_QZ = 4     /* ghost q = value[0], z = value[1] - value[2] * t; h copied */
+  ADOT_BC_INFLOW_QZ = 4,    /* ghost q = value[0], z = value[1] - value[2] * t; h copied */
+  ADOT_BC_INFLOW_QS = 5,    /* sediment feed (Sec. 5.1): ghost q = value[0], h copied, z
+                               continued linearly from the two cells next to the end
+                               (2 z_1 - z_2); the bed discharge through the end edge is
+                               xi * value[1] exactly (value[1] = q_s,in, signed along +x):
+                               the edge's bed fluctuation on the cell side becomes
+                               xi (q_s(W_cell) - q_s,in) at the left end and
+                               xi (q_s,in - q_s(W_cell)) at the right end */
+  ADOT_BC_OUTFLOW_HS = 6    /* ghost h = value[0], q copied, z continued linearly */
 } adot_bc;
 
 typedef struct {
@@ -82,7 +93,8 @@ typedef struct {
   double s_rel;     /* MPM: relative grain density */
   double d50;       /* MPM: median grain size [m] */
   double manning_n; /* MPM: Manning coefficient [s/m^(1/3)] */
-  double u_cr;      /* Grass with threshold: incipient transport velocity [m/s], >= 0 */
+  double u_cr;      /* Grass with threshold / power law: incipient velocity [m/s], >= 0 */
+  double beta;      /* power law: exponent, >= 1 (ignored by the other kinds) */
 } adot_law;
 
 typedef struct {
@@ -102,6 +114,9 @@ typedef struct {
   int32_t step_kernel;      /* 1 = block kernel (B-1 cells per block, shared-memory exchange),
                                2 = persistent warp tiles (31 cells per warp tile, shuffle
                                exchange); 0 = autotuned */
+  double ks;                /* Strickler coefficient K_s [m^(1/3)/s] of the friction source
+                               S = (0, -g h s_f, 0), s_f = q|q| / (K_s^2 h^(10/3)) (Sec. 2),
+                               added as dt S(W_i^n) in Eq. scheme; 0 = frictionless */
 } adot_config;
 
 typedef struct adot_ctx adot_ctx;

@@ -20,9 +20,10 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "adot.h")
 
 OK, E_INVALID_ARG, E_NONPOSITIVE_DEPTH, E_NONFINITE, E_NONHYPERBOLIC, E_CUDA, E_TIMEOUT, \
     E_UNSUPPORTED = range(8)
-LAW_GRASS, LAW_MPM, LAW_GRASS_THR = 0, 1, 2
+LAW_GRASS, LAW_MPM, LAW_GRASS_THR, LAW_POWER = 0, 1, 2, 3
 FP64, FP32 = 0, 1
-BC_TRANSMISSIVE, BC_PERIODIC, BC_INFLOW_Q, BC_OUTFLOW_H, BC_INFLOW_QZ = range(5)
+BC_TRANSMISSIVE, BC_PERIODIC, BC_INFLOW_Q, BC_OUTFLOW_H, BC_INFLOW_QZ, BC_INFLOW_QS, \
+    BC_OUTFLOW_HS = range(7)
 
 
 class AdotError(RuntimeError):
@@ -35,7 +36,8 @@ class AdotError(RuntimeError):
 class Law(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("g", ctypes.c_double), ("xi", ctypes.c_double),
                 ("Ag", ctypes.c_double), ("s_rel", ctypes.c_double), ("d50", ctypes.c_double),
-                ("manning_n", ctypes.c_double), ("u_cr", ctypes.c_double)]
+                ("manning_n", ctypes.c_double), ("u_cr", ctypes.c_double),
+                ("beta", ctypes.c_double)]
 
 
 class Config(ctypes.Structure):
@@ -45,7 +47,8 @@ class Config(ctypes.Structure):
                 ("bc_right", ctypes.c_int32), ("bc_left_value", ctypes.c_double * 3),
                 ("bc_right_value", ctypes.c_double * 3), ("block_threads", ctypes.c_int32),
                 ("steps_per_graph", ctypes.c_int32), ("device", ctypes.c_int32),
-                ("reg_cap", ctypes.c_int32), ("step_kernel", ctypes.c_int32)]
+                ("reg_cap", ctypes.c_int32), ("step_kernel", ctypes.c_int32),
+                ("ks", ctypes.c_double)]
 
 
 class EnsembleConfig(ctypes.Structure):
@@ -164,11 +167,12 @@ def _ptr(a, n=None):
 def make_config(n_cells, x_min, x_max, cfl, Ag, xi, precision=FP32, bc_left=BC_TRANSMISSIVE,
                 bc_right=BC_TRANSMISSIVE, bcl=(0.0, 0.0, 0.0), bcr=(0.0, 0.0, 0.0), g=9.81,
                 law=LAW_GRASS, s_rel=0.0, d50=0.0, manning_n=0.0, block_threads=0,
-                steps_per_graph=0, device=-1, reg_cap=0, step_kernel=0, u_cr=0.0) -> Config:
+                steps_per_graph=0, device=-1, reg_cap=0, step_kernel=0, u_cr=0.0, beta=0.0,
+                ks=0.0) -> Config:
     c = Config()
     c.n_cells = int(n_cells)
     c.x_min, c.x_max, c.cfl = float(x_min), float(x_max), float(cfl)
-    c.law = Law(law, g, xi, Ag, s_rel, d50, manning_n, u_cr)
+    c.law = Law(law, g, xi, Ag, s_rel, d50, manning_n, u_cr, beta)
     c.precision = precision
     c.bc_left, c.bc_right = bc_left, bc_right
     for i in range(3):
@@ -179,6 +183,7 @@ def make_config(n_cells, x_min, x_max, cfl, Ag, xi, precision=FP32, bc_left=BC_T
     c.device = device
     c.reg_cap = reg_cap
     c.step_kernel = step_kernel
+    c.ks = float(ks)
     return c
 
 

@@ -77,13 +77,13 @@ cudaError_t launch_fluct(int precision, int law, const LawT<float>& lf, const La
   if (precision == 0) {
     if (law == LAW_GRASS) k_fluct<double, LAW_GRASS><<<G, 256, 0, s>>>(p, WL, WR, n, Dm, Dp, rho_bits, status);
     else if (law == LAW_MPM) k_fluct<double, LAW_MPM><<<G, 256, 0, s>>>(p, WL, WR, n, Dm, Dp, rho_bits, status);
-    else if (law == LAW_GRASS_THR)
+    else if (law == LAW_GRASS_THR || law == LAW_POWER)
       k_fluct<double, LAW_GRASS_THR><<<G, 256, 0, s>>>(p, WL, WR, n, Dm, Dp, rho_bits, status);
     else return cudaErrorInvalidValue;
   } else {
     if (law == LAW_GRASS) k_fluct<float, LAW_GRASS><<<G, 256, 0, s>>>(p, WL, WR, n, Dm, Dp, rho_bits, status);
     else if (law == LAW_MPM) k_fluct<float, LAW_MPM><<<G, 256, 0, s>>>(p, WL, WR, n, Dm, Dp, rho_bits, status);
-    else if (law == LAW_GRASS_THR)
+    else if (law == LAW_GRASS_THR || law == LAW_POWER)
       k_fluct<float, LAW_GRASS_THR><<<G, 256, 0, s>>>(p, WL, WR, n, Dm, Dp, rho_bits, status);
     else return cudaErrorInvalidValue;
   }

@@ -83,7 +83,7 @@ adot_status status_from_bits(unsigned bits) {
   return ADOT_OK;
 }
 
-bool valid_bc(int k) { return k >= ADOT_BC_TRANSMISSIVE && k <= ADOT_BC_INFLOW_QZ; }
+bool valid_bc(int k) { return k >= ADOT_BC_TRANSMISSIVE && k <= ADOT_BC_OUTFLOW_HS; }
 
 }  // namespace
 
@@ -103,6 +103,9 @@ adot_status adot::validate_config(const adot_config* c) {
       return ADOT_E_INVALID_ARG;
   } else if (c->law.kind == ADOT_LAW_GRASS_THR) {
     if (!(c->law.u_cr >= 0.0) || !isfinite(c->law.u_cr)) return ADOT_E_INVALID_ARG;
+  } else if (c->law.kind == ADOT_LAW_POWER) {
+    if (!(c->law.u_cr >= 0.0) || !isfinite(c->law.u_cr)) return ADOT_E_INVALID_ARG;
+    if (!(c->law.beta >= 1.0) || !isfinite(c->law.beta)) return ADOT_E_INVALID_ARG;
   } else if (c->law.kind != ADOT_LAW_GRASS) {
     return ADOT_E_INVALID_ARG;
   }
@@ -111,6 +114,7 @@ adot_status adot::validate_config(const adot_config* c) {
   if ((c->bc_left == ADOT_BC_PERIODIC) != (c->bc_right == ADOT_BC_PERIODIC)) return ADOT_E_INVALID_ARG;
   for (int i = 0; i < 3; ++i)
     if (!isfinite(c->bc_left_value[i]) || !isfinite(c->bc_right_value[i])) return ADOT_E_INVALID_ARG;
+  if (!(c->ks >= 0.0) || !isfinite(c->ks)) return ADOT_E_INVALID_ARG;
   if (c->block_threads != 0 && !step_block_supported(c->block_threads)) return ADOT_E_INVALID_ARG;
   if (c->reg_cap != 0 && c->reg_cap != 64 && c->reg_cap != 72 && c->reg_cap != 80 && c->reg_cap != -1)
     return ADOT_E_INVALID_ARG;
@@ -141,9 +145,17 @@ void adot::make_step_params(const adot_config* cfg, StepParams* out) {
     mpm_c = L.manning_n * L.manning_n / ((L.s_rel - 1.0) * L.d50);
     mpm_scale = L.xi * sqrt(L.g * (L.s_rel - 1.0) * L.d50 * L.d50 * L.d50);
   }
-  const double ucr = (L.kind == ADOT_LAW_GRASS_THR) ? L.u_cr : 0.0;
-  p.ld = LawT<double>{L.g, K3, mpm_c, mpm_scale, ucr};
-  p.lf = LawT<float>{(float)L.g, (float)K3, (float)mpm_c, (float)mpm_scale, (float)ucr};
+  const bool thr = L.kind == ADOT_LAW_GRASS_THR || L.kind == ADOT_LAW_POWER;
+  const double ucr = thr ? L.u_cr : 0.0;
+  const double beta = (L.kind == ADOT_LAW_POWER) ? L.beta : 3.0;
+  if (L.kind == ADOT_LAW_POWER) K3 = beta * L.xi * L.Ag;
+  const double xa = L.xi * L.Ag;
+  p.ld = LawT<double>{L.g, K3, mpm_c, mpm_scale, ucr, beta, xa};
+  p.lf = LawT<float>{(float)L.g,   (float)K3,  (float)mpm_c, (float)mpm_scale,
+                     (float)ucr,   (float)beta, (float)xa};
+  p.fric = (cfg->ks > 0.0) ? L.g / (cfg->ks * cfg->ks) : 0.0;
+  p.feed_l = L.xi * cfg->bc_left_value[1];
+  p.feed_r = L.xi * cfg->bc_right_value[1];
 }
 
 namespace {
@@ -213,15 +225,17 @@ adot_status enqueue(adot_ctx* c, int64_t n) {
   return ADOT_OK;
 }
 
-// Process-wide cache of tuned variants: (device, law, precision, log2 n, filters).
+// Process-wide cache of tuned variants: (device, law, precision, log2 n, filters,
+// friction / feed kernels or not).
+using TuneKey = std::tuple<int, int, int, int, int, int, int, int>;
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int, int, int, int, int>, StepVariant> g_tune_cache;
+std::map<TuneKey, StepVariant> g_tune_cache;
 
-std::tuple<int, int, int, int, int, int, int> tune_key(const adot_ctx* c) {
+TuneKey tune_key(const adot_ctx* c) {
   int lg = 0;
   for (int64_t n = c->p.n; n > 1; n >>= 1) ++lg;
   return std::make_tuple(c->device, c->law, c->prec, lg, c->cfg.block_threads, c->cfg.reg_cap,
-                         c->cfg.step_kernel);
+                         c->cfg.step_kernel, step_needs_ext(c->p) ? 1 : 0);
 }
 
 bool candidate(const adot_config& cfg, StepVariant v) {
@@ -363,6 +377,9 @@ uint64_t config_fingerprint(const adot_config& c) {
   h = fnv1a(h, &c.law.s_rel, sizeof c.law.s_rel);
   h = fnv1a(h, &c.law.d50, sizeof c.law.d50);
   h = fnv1a(h, &c.law.manning_n, sizeof c.law.manning_n);
+  h = fnv1a(h, &c.law.u_cr, sizeof c.law.u_cr);
+  h = fnv1a(h, &c.law.beta, sizeof c.law.beta);
+  h = fnv1a(h, &c.ks, sizeof c.ks);
   h = fnv1a(h, &c.precision, sizeof c.precision);
   h = fnv1a(h, &c.bc_left, sizeof c.bc_left);
   h = fnv1a(h, &c.bc_right, sizeof c.bc_right);

@@ -48,11 +48,31 @@ struct StepParams {
   double bcl[3], bcr[3];
   LawT<float> lf;
   LawT<double> ld;
+  double fric;              // g / K_s^2 of the Strickler friction source; 0 = none
+  double feed_l, feed_r;    // xi q_s,in imposed through a BC_INFLOW_QS end
   Ctl* ctl;
   const float* absA;  // surrogate |A|_Psi per edge, [9][n+1] (NaN in row 0: analytic edge)
 };
 
-enum : int { BC_TRANSMISSIVE = 0, BC_PERIODIC = 1, BC_INFLOW_Q = 2, BC_OUTFLOW_H = 3, BC_INFLOW_QZ = 4 };
+enum : int {
+  BC_TRANSMISSIVE = 0,
+  BC_PERIODIC = 1,
+  BC_INFLOW_Q = 2,
+  BC_OUTFLOW_H = 3,
+  BC_INFLOW_QZ = 4,
+  BC_INFLOW_QS = 5,
+  BC_OUTFLOW_HS = 6
+};
+
+// Whether a configuration runs the step kernels with the friction source, the
+// sediment feed and the slope-continuing ghosts compiled in.
+inline bool step_needs_ext(const StepParams& p) {
+  if (p.fric != 0.0) return true;
+  if (p.periodic) return false;
+  for (int k : {p.bc_left, p.bc_right})
+    if (k == BC_INFLOW_QS || k == BC_OUTFLOW_HS) return true;
+  return false;
+}
 
 // A compiled variant of the step kernel: threads per block and the register
 // cap per thread (0 = none) given to the register allocator.
@@ -78,9 +98,18 @@ cudaError_t launch_step_f32(const StepParams& p, int law, StepVariant v, StateF3
 cudaError_t launch_step_f64(const StepParams& p, int law, StepVariant v, StateF64 in, StateF64 out,
                             int slot, cudaStream_t s);
 
+// The same with the friction source and the sediment feed compiled in; the
+// plain entry points forward to these when the configuration uses either.
+cudaError_t launch_step_f32_ext(const StepParams& p, int law, StepVariant v, StateF32 in,
+                                StateF32 out, int slot, cudaStream_t s);
+cudaError_t launch_step_f64_ext(const StepParams& p, int law, StepVariant v, StateF64 in,
+                                StateF64 out, int slot, cudaStream_t s);
+
 // Time step whose edges take |A|_Psi from p.absA (float32, Grass law, 256 x 64).
 cudaError_t launch_step_sur_f32(const StepParams& p, StateF32 in, StateF32 out, int slot,
                                 cudaStream_t s);
+cudaError_t launch_step_sur_f32_ext(const StepParams& p, StateF32 in, StateF32 out, int slot,
+                                    cudaStream_t s);
 
 // n edge samples of a state (edge index drawn with splitmix64 from seed and the
 // sample number): raw inputs X [n][7] (h, q, z left and right, A_g) and float64

@@ -20,7 +20,9 @@
 
 namespace adot {
 
-enum : int { LAW_GRASS = 0, LAW_MPM = 1, LAW_GRASS_THR = 2 };
+// Transport laws. LAW_POWER (q_s = A sign(u) max(|u| - u_cr, 0)^beta) runs the
+// LAW_GRASS_THR code with its own exponent (LawT::beta; 3 for Eq. GrassThr).
+enum : int { LAW_GRASS = 0, LAW_MPM = 1, LAW_GRASS_THR = 2, LAW_POWER = 3 };
 
 // Status bits recorded in the device control block.
 enum : unsigned {
@@ -35,10 +37,12 @@ enum : unsigned {
 template <typename T>
 struct LawT {
   T g;
-  T K3;         // Grass: 3 xi A_g, so b = K3 u^2 / h and a = -b u
+  T K3;         // Grass: 3 xi A_g, so b = K3 u^2 / h and a = -b u; power law: beta xi A
   T mpm_c;      // MPM: n^2 / ((s - 1) d50), theta = mpm_c u^2 h^(-1/3)
   T mpm_scale;  // MPM: xi sqrt(g (s - 1) d50^3)
-  T ucr;        // Grass with threshold: incipient transport velocity u_cr
+  T ucr;        // Grass with threshold / power law: incipient transport velocity u_cr
+  T beta;       // Grass with threshold / power law: exponent (3 for Eq. GrassThr)
+  T xa;         // xi A_g (Grass, threshold and power laws): xi q_s = xa sign(u) v^beta
 };
 
 // Gap below which |A| dW switches to the Newton divided-difference form
@@ -69,6 +73,8 @@ __device__ __forceinline__ void d_sincos(float x, float* s, float* c) { __sincos
 __device__ __forceinline__ void d_sincos(double x, double* s, double* c) { sincos(x, s, c); }
 __device__ __forceinline__ float d_rcbrt(float x) { return rcbrtf(x); }
 __device__ __forceinline__ double d_rcbrt(double x) { return rcbrt(x); }
+__device__ __forceinline__ float d_pow(float x, float y) { return powf(x, y); }
+__device__ __forceinline__ double d_pow(double x, double y) { return pow(x, y); }
 __device__ __forceinline__ float d_abs(float x) { return fabsf(x); }
 __device__ __forceinline__ double d_abs(double x) { return fabs(x); }
 __device__ __forceinline__ float d_min(float a, float b) { return fminf(a, b); }
@@ -95,9 +101,11 @@ __device__ __forceinline__ void sediment_derivs(const LawT<T>& L, T h, T q, T in
     // b = K3 v^2 / h, a = -b u (d|u|/dq = sign(u)/h, d|u|/dh = -sign(u) u/h)
     (void)h;
     (void)q;
+    // Power law (Eq. Soni_qs): the same with v^(beta-1) in place of v^2.
     const T v = d_abs(u) - L.ucr;
     if (v > T(0)) {
-      b = L.K3 * v * v * inv_h;
+      const T vb1 = (L.beta == T(3)) ? v * v : d_pow(v, L.beta - T(1));
+      b = L.K3 * vb1 * inv_h;
       a = -b * u;
     } else {
       a = T(0);
@@ -116,6 +124,27 @@ __device__ __forceinline__ void sediment_derivs(const LawT<T>& L, T h, T q, T in
       a = T(0);
       b = T(0);
     }
+  }
+}
+
+// xi q_s at (h, q): the bed discharge of a state, which a feeding end compares
+// with the imposed one (Sec. 5.1).
+template <typename T, int LAW>
+__device__ __forceinline__ T sediment_xqs(const LawT<T>& L, T h, T q) {
+  const T u = q / h;
+  if constexpr (LAW == LAW_GRASS) {
+    return L.xa * u * u * u;
+  } else if constexpr (LAW == LAW_GRASS_THR) {
+    const T v = d_abs(u) - L.ucr;
+    if (!(v > T(0))) return T(0);
+    const T vb = (L.beta == T(3)) ? v * v * v : d_pow(v, L.beta);
+    return (u > T(0)) ? L.xa * vb : -(L.xa * vb);
+  } else {
+    const T theta = L.mpm_c * u * u * d_rcbrt(h);
+    const T ex = theta - T(0.047);
+    if (!(ex > T(0))) return T(0);
+    const T qs = L.mpm_scale * T(8) * ex * d_sqrt(ex);
+    return (q > T(0)) ? qs : ((q < T(0)) ? -qs : T(0));
   }
 }
 

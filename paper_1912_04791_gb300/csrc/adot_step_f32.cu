@@ -15,12 +15,14 @@ bool step_variant_supported(StepVariant v) {
 
 cudaError_t launch_step_f32(const StepParams& p, int law, StepVariant v, StateF32 in, StateF32 out,
                             int slot, cudaStream_t s) {
-  return launch_step_impl<float>(p, law, v, in, out, slot, s);
+  if (step_needs_ext(p)) return launch_step_f32_ext(p, law, v, in, out, slot, s);
+  return launch_step_impl<float, false>(p, law, v, in, out, slot, s);
 }
 
 cudaError_t launch_step_sur_f32(const StepParams& p, StateF32 in, StateF32 out, int slot,
                                 cudaStream_t s) {
   if (p.ctl == nullptr || p.absA == nullptr || p.n < 1) return cudaErrorInvalidValue;
+  if (step_needs_ext(p)) return launch_step_sur_f32_ext(p, in, out, slot, s);
   const int64_t g = (p.n + 1 + 254) / 255;
   if (g > 0x7fffffffLL) return cudaErrorInvalidValue;
   k_step<float, LAW_GRASS, 256, 64, true><<<(unsigned)g, 256, 0, s>>>(p, in, out, slot);

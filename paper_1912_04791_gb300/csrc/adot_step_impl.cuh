@@ -86,10 +86,14 @@ struct Prec<double> {
   }
 };
 
-// Ghost state beyond one end (adj = the adjacent cell).
-template <typename R>
+// Ghost state beyond one end: adj = the cell next to the end, nxt = the one
+// after it (adj itself when the domain has one cell). BC_INFLOW_QS and
+// BC_OUTFLOW_HS continue the bed slope, z_g = 2 z_adj - z_nxt, so a uniform
+// flow on a constant slope meets the same bed step at the end edge as inside.
+template <typename R, bool EXT = true>
 __device__ __forceinline__ void ghost_state(int kind, const double v[3], double t,
                                             const typename Prec<R>::S adj[3],
+                                            const typename Prec<R>::S& z_nxt,
                                             typename Prec<R>::S out[3]) {
   out[0] = adj[0];
   out[1] = adj[1];
@@ -101,11 +105,19 @@ __device__ __forceinline__ void ghost_state(int kind, const double v[3], double 
   } else if (kind == BC_INFLOW_QZ) {
     out[1] = Prec<R>::from_double(v[0]);
     out[2] = Prec<R>::from_double(v[1] - v[2] * t);
+  } else if (EXT && (kind == BC_INFLOW_QS || kind == BC_OUTFLOW_HS)) {
+    if (kind == BC_INFLOW_QS)
+      out[1] = Prec<R>::from_double(v[0]);
+    else
+      out[0] = Prec<R>::from_double(v[0]);
+    out[2] = Prec<R>::add(adj[2], Prec<R>::diff(adj[2], z_nxt));
   }
 }
 
-// States on both sides of edge e (joins cells e-1 and e), 0 <= e <= n.
-template <typename R>
+// States on both sides of edge e (joins cells e-1 and e), 0 <= e <= n. EXT:
+// the slope-continuing ghosts are compiled in (the plain step kernels run only
+// configurations without them).
+template <typename R, bool EXT = true>
 __device__ __forceinline__ void load_edge(const StepParams& p, const typename Prec<R>::State& st,
                                           int64_t e, int slot, typename Prec<R>::S wl[3],
                                           typename Prec<R>::S wr[3]) {
@@ -130,13 +142,48 @@ __device__ __forceinline__ void load_edge(const StepParams& p, const typename Pr
     wr[0] = st.h[0];
     wr[1] = st.q[0];
     wr[2] = st.z[0];
-    ghost_state<R>(p.bc_left, p.bcl, p.ctl->s[slot].t, wr, wl);
+    if constexpr (EXT)
+      ghost_state<R>(p.bc_left, p.bcl, p.ctl->s[slot].t, wr, st.z[n > 1 ? 1 : 0], wl);
+    else
+      ghost_state<R, false>(p.bc_left, p.bcl, p.ctl->s[slot].t, wr, wr[2], wl);
   } else {
     wl[0] = st.h[n - 1];
     wl[1] = st.q[n - 1];
     wl[2] = st.z[n - 1];
-    ghost_state<R>(p.bc_right, p.bcr, p.ctl->s[slot].t, wl, wr);
+    if constexpr (EXT)
+      ghost_state<R>(p.bc_right, p.bcr, p.ctl->s[slot].t, wl, st.z[n > 1 ? n - 2 : 0], wr);
+    else
+      ghost_state<R, false>(p.bc_right, p.bcr, p.ctl->s[slot].t, wl, wl[2], wr);
   }
+}
+
+// Sediment feed through an end (Sec. 5.1): the bed row of Eq. scheme is
+// z_i -= dt/dx (F_{i+1/2} - F_{i-1/2}) with the edge discharge
+// F_{i+1/2} = xi q_s(W_i) + D-_{i+1/2} = xi q_s(W_{i+1}) - D+_{i+1/2}; a feeding
+// end's edge discharge is the imposed xi q_s,in, so the bed gains exactly what
+// is fed. Edge 0: bed row of D+ = xi q_s(W_0) - xi q_s,in; edge n: bed row of
+// D- = xi q_s,in - xi q_s(W_{n-1}). The h and q rows keep the edge against the
+// ghost.
+template <typename R, int LAW>
+__device__ __forceinline__ void feed_edge(const StepParams& p, int64_t e,
+                                          const typename Prec<R>::S wl[3],
+                                          const typename Prec<R>::S wr[3], R dm[3], R dp[3]) {
+  if (p.periodic) return;
+  if (e == 0 && p.bc_left == BC_INFLOW_QS)
+    dp[2] = sediment_xqs<R, LAW>(Prec<R>::law(p), Prec<R>::hi(wr[0]), Prec<R>::hi(wr[1])) -
+            R(p.feed_l);
+  if (e == p.n && p.bc_right == BC_INFLOW_QS)
+    dm[2] = R(p.feed_r) -
+            sediment_xqs<R, LAW>(Prec<R>::law(p), Prec<R>::hi(wl[0]), Prec<R>::hi(wl[1]));
+}
+
+// Momentum source of Eq. SV-Ex2 times dt at the step's starting state:
+// -dt g h s_f, Strickler s_f = q|q| / (K_s^2 h^(10/3)) (Sec. 2), i.e.
+// -dt (g / K_s^2) q|q| h^(-7/3).
+template <typename R>
+__device__ __forceinline__ R friction_dt(const StepParams& p, R dt, R h, R q) {
+  const R ih = R(1) / h;
+  return -dt * R(p.fric) * q * d_abs(q) * (ih * ih * d_rcbrt(h));
 }
 
 template <typename R>
@@ -219,7 +266,10 @@ struct MinBlocks {
   static constexpr int value = CAP ? 65536 / (B * CAP) : 1;
 };
 
-template <typename R, int LAW, int B, int CAP, bool SUR = false>
+// EXT: the friction source and the sediment feed are compiled in (configs that
+// use neither run the EXT = false kernels, whose register allocation they would
+// otherwise share).
+template <typename R, int LAW, int B, int CAP, bool SUR = false, bool EXT = false>
 __global__ void __launch_bounds__(B, MinBlocks<B, CAP>::value) k_step(const StepParams p, const typename Prec<R>::State in,
                                             const typename Prec<R>::State out, const int slot) {
   using S = typename Prec<R>::S;
@@ -261,7 +311,7 @@ __global__ void __launch_bounds__(B, MinBlocks<B, CAP>::value) k_step(const Step
   R dm[3] = {R(0), R(0), R(0)}, dp[3] = {R(0), R(0), R(0)};
   if (e <= n) {
     S wr[3];
-    load_edge<R>(p, in, e, slot, wl, wr);
+    load_edge<R, EXT>(p, in, e, slot, wl, wr);
     if constexpr (SUR) {
       float M[9];
 #pragma unroll
@@ -273,6 +323,7 @@ __global__ void __launch_bounds__(B, MinBlocks<B, CAP>::value) k_step(const Step
     } else {
       edge_fluct<R, LAW>(p, wl, wr, dm, dp, flags);
     }
+    if constexpr (EXT) feed_edge<R, LAW>(p, e, wl, wr, dm, dp);
   }
   sDp[0][tid] = dp[0];
   sDp[1][tid] = dp[1];
@@ -286,8 +337,12 @@ __global__ void __launch_bounds__(B, MinBlocks<B, CAP>::value) k_step(const Step
   if (tid >= 1 && i < n) {
     S nh = wl[0], nq = wl[1], nz = wl[2];
     if (!done) {
+      R iq = -nu * (dm[1] + sDp[1][tid - 1]);
+      if constexpr (EXT)
+        if (p.fric != 0.0)
+          iq += friction_dt<R>(p, nu * R(p.dx), Prec<R>::hi(wl[0]), Prec<R>::hi(wl[1]));
       nh = Prec<R>::add(wl[0], -nu * (dm[0] + sDp[0][tid - 1]));
-      nq = Prec<R>::add(wl[1], -nu * (dm[1] + sDp[1][tid - 1]));
+      nq = Prec<R>::add(wl[1], iq);
       nz = Prec<R>::add(wl[2], -nu * (dm[2] + sDp[2][tid - 1]));
     }
     out.h[i] = nh;
@@ -326,7 +381,7 @@ __global__ void __launch_bounds__(B, MinBlocks<B, CAP>::value) k_step(const Step
 // shuffle, so warps never wait for one another. Each warp keeps its CFL maximum
 // in a register and folds it into the control slot once at the end. One edge
 // in 32 is evaluated twice.
-template <typename R, int LAW, int B, int CAP>
+template <typename R, int LAW, int B, int CAP, bool EXT = false>
 __global__ void __launch_bounds__(B, MinBlocks<B, CAP>::value)
     k_step_warp(const StepParams p, const typename Prec<R>::State in,
                 const typename Prec<R>::State out, const int slot) {
@@ -383,8 +438,9 @@ __global__ void __launch_bounds__(B, MinBlocks<B, CAP>::value)
     R dm[3] = {R(0), R(0), R(0)}, dp[3] = {R(0), R(0), R(0)};
     if (e <= n) {
       S wr[3];
-      load_edge<R>(p, in, e, slot, wl, wr);
+      load_edge<R, EXT>(p, in, e, slot, wl, wr);
       edge_fluct<R, LAW>(p, wl, wr, dm, dp, flags);
+      if constexpr (EXT) feed_edge<R, LAW>(p, e, wl, wr, dm, dp);
     }
     R dl[3];
 #pragma unroll
@@ -393,8 +449,12 @@ __global__ void __launch_bounds__(B, MinBlocks<B, CAP>::value)
     if (lane >= 1 && i < n) {
       S nh = wl[0], nq = wl[1], nz = wl[2];
       if (!done) {
+        R iq = -nu * (dm[1] + dl[1]);
+        if constexpr (EXT)
+          if (p.fric != 0.0)
+            iq += friction_dt<R>(p, nu * R(p.dx), Prec<R>::hi(wl[0]), Prec<R>::hi(wl[1]));
         nh = Prec<R>::add(wl[0], -nu * (dm[0] + dl[0]));
-        nq = Prec<R>::add(wl[1], -nu * (dm[1] + dl[1]));
+        nq = Prec<R>::add(wl[1], iq);
         nz = Prec<R>::add(wl[2], -nu * (dm[2] + dl[2]));
       }
       out.h[i] = nh;
@@ -459,7 +519,7 @@ __global__ void __launch_bounds__(256) k_rho(const StepParams p, const typename 
   if (flags) atomicOr(&p.ctl->status, flags);
 }
 
-template <typename R, int LAW>
+template <typename R, int LAW, bool EXT>
 cudaError_t launch_step_law(const StepParams& p, StepVariant v, typename Prec<R>::State in,
                             typename Prec<R>::State out, int slot, cudaStream_t s) {
   if (p.ctl == nullptr || p.n < 1) return cudaErrorInvalidValue;
@@ -479,26 +539,26 @@ cudaError_t launch_step_law(const StepParams& p, StepVariant v, typename Prec<R>
     int64_t gg = (tiles + wpb - 1) / wpb;
     if (gg > sms * per_sm) gg = sms * per_sm;
     if (v.block == 256 && v.reg_cap == 64) {
-      k_step_warp<R, LAW, 256, 64><<<(unsigned)gg, 256, 0, s>>>(p, in, out, slot);
+      k_step_warp<R, LAW, 256, 64, EXT><<<(unsigned)gg, 256, 0, s>>>(p, in, out, slot);
       return cudaGetLastError();
     }
     if (v.block == 128 && v.reg_cap == 64) {
-      k_step_warp<R, LAW, 128, 64><<<(unsigned)gg, 128, 0, s>>>(p, in, out, slot);
+      k_step_warp<R, LAW, 128, 64, EXT><<<(unsigned)gg, 128, 0, s>>>(p, in, out, slot);
       return cudaGetLastError();
     }
     if (v.block == 128 && v.reg_cap == 72) {
-      k_step_warp<R, LAW, 128, 72><<<(unsigned)gg, 128, 0, s>>>(p, in, out, slot);
+      k_step_warp<R, LAW, 128, 72, EXT><<<(unsigned)gg, 128, 0, s>>>(p, in, out, slot);
       return cudaGetLastError();
     }
     if (v.block == 256 && v.reg_cap == 80) {
-      k_step_warp<R, LAW, 256, 80><<<(unsigned)gg, 256, 0, s>>>(p, in, out, slot);
+      k_step_warp<R, LAW, 256, 80, EXT><<<(unsigned)gg, 256, 0, s>>>(p, in, out, slot);
       return cudaGetLastError();
     }
     return cudaErrorInvalidValue;
   }
 #define ADOT_STEP_CASE(BB, CC)                                       \
   if (v.block == BB && v.reg_cap == CC) {                            \
-    k_step<R, LAW, BB, CC><<<G, BB, 0, s>>>(p, in, out, slot);       \
+    k_step<R, LAW, BB, CC, false, EXT><<<G, BB, 0, s>>>(p, in, out, slot); \
     return cudaGetLastError();                                       \
   }
   ADOT_STEP_CASE(128, 0)
@@ -511,12 +571,13 @@ cudaError_t launch_step_law(const StepParams& p, StepVariant v, typename Prec<R>
   return cudaErrorInvalidValue;
 }
 
-template <typename R>
+template <typename R, bool EXT>
 cudaError_t launch_step_impl(const StepParams& p, int law, StepVariant v, typename Prec<R>::State in,
                              typename Prec<R>::State out, int slot, cudaStream_t s) {
-  if (law == LAW_GRASS) return launch_step_law<R, LAW_GRASS>(p, v, in, out, slot, s);
-  if (law == LAW_MPM) return launch_step_law<R, LAW_MPM>(p, v, in, out, slot, s);
-  if (law == LAW_GRASS_THR) return launch_step_law<R, LAW_GRASS_THR>(p, v, in, out, slot, s);
+  if (law == LAW_GRASS) return launch_step_law<R, LAW_GRASS, EXT>(p, v, in, out, slot, s);
+  if (law == LAW_MPM) return launch_step_law<R, LAW_MPM, EXT>(p, v, in, out, slot, s);
+  if (law == LAW_GRASS_THR || law == LAW_POWER)
+    return launch_step_law<R, LAW_GRASS_THR, EXT>(p, v, in, out, slot, s);
   return cudaErrorInvalidValue;
 }
 
@@ -531,7 +592,7 @@ cudaError_t launch_rho_impl(const StepParams& p, int law, typename Prec<R>::Stat
     k_rho<R, LAW_GRASS><<<(unsigned)g, 256, 0, s>>>(p, st, slot);
   else if (law == LAW_MPM)
     k_rho<R, LAW_MPM><<<(unsigned)g, 256, 0, s>>>(p, st, slot);
-  else if (law == LAW_GRASS_THR)
+  else if (law == LAW_GRASS_THR || law == LAW_POWER)
     k_rho<R, LAW_GRASS_THR><<<(unsigned)g, 256, 0, s>>>(p, st, slot);
   else
     return cudaErrorInvalidValue;

@@ -38,6 +38,8 @@ int main(void) {
          offsetof(adot_config, bc_left_value), offsetof(adot_config, bc_right_value),
          offsetof(adot_config, block_threads), offsetof(adot_config, device),
          offsetof(adot_config, step_kernel), offsetof(adot_law, manning_n));
+  printf("%zu %zu %zu\n", offsetof(adot_config, ks), offsetof(adot_law, u_cr),
+         offsetof(adot_law, beta));
   printf("%zu %zu %zu %zu %zu %zu\n", sizeof(adot_ensemble_config), offsetof(adot_ensemble_config, g),
          offsetof(adot_ensemble_config, precision), offsetof(adot_ensemble_config, block_threads),
          offsetof(adot_ensemble_config, device), offsetof(adot_ensemble_config, step_kernel));
@@ -52,6 +54,7 @@ int main(void) {
     want = [ctypes.sizeof(C), ctypes.sizeof(W), C.law.offset, C.precision.offset,
             C.bc_left_value.offset, C.bc_right_value.offset, C.block_threads.offset,
             C.device.offset, C.step_kernel.offset, W.manning_n.offset,
+            C.ks.offset, W.u_cr.offset, W.beta.offset,
             ctypes.sizeof(E), E.g.offset, E.precision.offset, E.block_threads.offset, E.device.offset,
             E.step_kernel.offset]
     assert got == want
@@ -67,13 +70,22 @@ def test_status_strings_and_version(L):
 @pytest.mark.parametrize("field,value", [
     ("n_cells", 0), ("cfl", 0.0), ("cfl", 1.5), ("x_max", -1.0), ("precision", 7),
     ("bc_left", 9), ("block_threads", 100), ("steps_per_graph", -6), ("device", -3),
-    ("reg_cap", 32), ("step_kernel", 3)])
+    ("reg_cap", 32), ("step_kernel", 3), ("bc_left", 7), ("bc_right", -1), ("ks", -1.0),
+    ("ks", float("nan")), ("ks", float("inf"))])
 def test_invalid_config_rejected_without_cuda(L, field, value):
     cfg = adot.make_config(64, 0.0, 1.0, 0.8, 0.005, 5 / 3)
     setattr(cfg, field, value)
     out = ctypes.c_void_p()
     st = L.adot_create(ctypes.byref(cfg), None, ctypes.byref(out))
     assert st == adot.E_INVALID_ARG and not out.value
+
+
+@pytest.mark.parametrize("beta,ucr", [(0.5, 0.0), (float("nan"), 0.0), (3.0, -0.1), (float("inf"), 0.0)])
+def test_invalid_power_law_rejected(L, beta, ucr):
+    cfg = adot.make_config(64, 0.0, 1.0, 0.8, 0.005, 5 / 3, law=adot.LAW_POWER, beta=beta, u_cr=ucr)
+    out = ctypes.c_void_p()
+    assert L.adot_create(ctypes.byref(cfg), None, ctypes.byref(out)) == adot.E_INVALID_ARG
+    assert not out.value
 
 
 def test_periodic_must_be_on_both_ends(L):

@@ -121,6 +121,28 @@ def test_mismatched_or_damaged_blob_is_refused(gpu):
         assert np.array_equal(x, y)
 
 
+@pytest.mark.parametrize("field", ["ks", "u_cr"])
+def test_blob_of_another_friction_or_threshold_is_refused(gpu, field):
+    """The fingerprint covers the friction coefficient and the law's threshold
+    and exponent: configs that differ only there do not share checkpoints."""
+    P = W.movable_bed_riemann(400)
+    kw = {"law": gpu.LAW_POWER, "beta": 3.0, "u_cr": 0.1, "ks": 30.0}
+    with gpu.Solver(gpu.config_for(P, gpu.FP64, **kw)) as a:
+        a.set_state(P.h, P.q, P.z)
+        a.step(5)
+        blob = a.checkpoint()
+        kw2 = dict(kw)
+        kw2[field] = kw[field] * 1.5
+        with gpu.Solver(gpu.config_for(P, gpu.FP64, **kw2)) as b:
+            b.set_state(P.h, P.q, P.z)
+            with pytest.raises(gpu.AdotError):
+                b.restore(blob)
+        with gpu.Solver(gpu.config_for(P, gpu.FP64, **kw)) as c:
+            c.set_state(P.h, P.q, P.z)
+            c.restore(blob)
+            assert c.query()[1] == 5
+
+
 def test_save_before_state_is_refused(gpu):
     P = W.smooth_periodic(64)
     with gpu.Solver(gpu.config_for(P, gpu.FP32)) as a:
