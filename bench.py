@@ -95,6 +95,8 @@ def parse():
                     help="edge samples harvested from the smooth, bump and ensemble workloads")
     ap.add_argument("--l1-sweep", action="store_true",
                     help="also run the smooth problem to t_end = 0.5 s at N = 1e3 * 2^k (FP32, FP64, oracle)")
+    ap.add_argument("--friction-steps", type=int, default=960,
+                    help="timed steps of the workload with the Strickler friction source (0 = skip)")
     ap.add_argument("--accuracy-steps", type=int, default=96,
                     help="steps of the FP32-vs-FP64 increment check (0 = skip)")
     return ap.parse_args()
@@ -300,6 +302,80 @@ def surrogate_leg(args, adot, W, P, n, stream, dev, local, time_steps, ref64):
                                                         / np.abs(b_ - a0).sum())
                 out[f"l1_rel_state_{name}"] = float(np.abs(a_ - b_).sum() / np.abs(b_).sum())
         return out
+
+
+KS_BENCH = 30.0  # Strickler coefficient of the friction line (s_f ~ 1e-4 on this flow)
+FRICTION_FLOPS_PER_CELL = 10.0  # q|q|, 1/h, h^(-1/3), four products, dt scaling, one add
+
+
+def friction_leg(args, adot, W, P, n, stream, dev, local, time_steps, plain_value):
+    """The benchmark workload with the friction source compiled in (the EXT step
+    kernels), then the Soni case end to end through the public API."""
+    import torch
+
+    K = args.friction_steps
+    cfg = adot.config_for(P, adot.FP32, block_threads=args.block, reg_cap=args.reg_cap,
+                          step_kernel=args.step_kernel, device=local, ks=KS_BENCH)
+    with adot.Solver(cfg, stream=stream) as sf:
+        sf.set_state(P.h, P.q, P.z)
+        fb, fc, fk = adot.adot_autotune(sf.ctx, 8)
+        adot.adot_step(sf.ctx, 48)
+        ms = time_steps(sf, K)
+    per_launch_s = ms * 1e-3 / K
+    kind = "warp" if fk == 2 else "block"
+    f_peak = 152 * 128 * 2 * (2070e6) / 1e12
+    achieved = (FLOPS_PER_CELL_UPDATE[kind] + FRICTION_FLOPS_PER_CELL) * n / per_launch_s / 1e12
+    out = {"workload": f"smooth_periodic N={n} with Strickler friction K_s={KS_BENCH} (FP32)",
+           "steps": K, "ms_per_step": ms / K, "cell_updates_per_s": n * K / (ms * 1e-3),
+           "vs_frictionless": (n * K / (ms * 1e-3)) / plain_value,
+           "kernel": f"{'k_step_warp' if fk == 2 else 'k_step'}<float,GRASS,{fb},{max(fc, 0)},EXT>",
+           "roofline": {"bound": "alu", "achieved": achieved, "peak": f_peak, "unit": "TFLOP/s",
+                        "frac": achieved / f_peak,
+                        "flops_per_cell_update": FLOPS_PER_CELL_UPDATE[kind] + FRICTION_FLOPS_PER_CELL,
+                        "hbm_achieved_gbs": BYTES_PER_CELL_UPDATE * n / per_launch_s / 1e9}}
+    S = W.soni_aggradation()
+    soni = {"case": "Soni aggradation as printed: 100 cells, 2400 s, q_s = 1.45e-3 u^5, K_s = 49.4, "
+                    "feed 5 Q_S0 upstream, h0 downstream",
+            "paper_cpu_s": {"A-DOT": 1.50, "DOT": 14.97, "PRICE-C": 1.48,
+                            "note": "the paper's own CPU times, hardware unstated: context"}}
+    for prec_name, prec in (("fp32", adot.FP32), ("fp64", adot.FP64)):
+        cfg = adot.config_for(S, prec, law=adot.LAW_POWER, beta=S.extra["beta"], ks=S.extra["ks"],
+                              device=local)
+        with adot.Solver(cfg, stream=stream) as ss:
+            ss.set_state(S.h, S.q, S.z)
+            ss.run_to(10.0)  # graph capture and autotuning outside the timed call
+            ss.set_state(S.h, S.q, S.z)
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            ss.run_to(S.t_end)
+            h, q, z = ss.get_state()
+            wall = time.perf_counter() - t0
+            t, steps, _ = ss.query()
+        soni[prec_name] = {"wall_s": wall, "steps": int(steps), "t_end": t,
+                           "dz_at_feed_m": float(z[0] - S.z[0]), "_z": z,
+                           "note": "run_to(2400 s) plus get_state, host wall clock"}
+    zs = {k: soni[k].pop("_z") for k in ("fp32", "fp64")}
+    soni["fp32_vs_fp64_max_rel_dz"] = float(np.abs(zs["fp32"] - zs["fp64"]).max()
+                                            / np.abs(zs["fp64"] - S.z).max())
+    out["soni"] = soni
+    return out
+
+
+def soni_oracle_time(W):
+    """The Soni case (100 cells, 2400 s) run by the FP64 oracle on one host core."""
+    import oracle as O
+
+    S = W.soni_aggradation()
+    law = O.power(S.Ag, S.extra["beta"], xi=S.xi, g=S.g)
+    cfg = O.make_cfg(S.n, S.x_min, S.x_max, S.cfl, law, S.bc_left, S.bc_right, S.bcl, S.bcr,
+                     ks=S.extra["ks"])
+    thr = O.num_threads()
+    O.set_num_threads(1)
+    t0 = time.perf_counter()
+    _, _, z, _, steps, _ = O.run(cfg, S.h, S.q, S.z, t_end=S.t_end)
+    wall = time.perf_counter() - t0
+    O.set_num_threads(thr)
+    return {"wall_s": wall, "steps": int(steps), "cores": 1, "dz_at_feed_m": float(z[0] - S.z[0])}
 
 
 def l1_sweep(adot, W, stream, local, k_max=8, n_oracle_max=32000):
@@ -515,6 +591,12 @@ def main():
                     "tile_threads": blk, "tiles": n_tiles, "grid": grid,
                     "all_at_t_end": bool((t_c == args.ensemble_t_end).all())}
 
+    # Strickler friction source (Sec. 2) on the benchmark workload, and the Soni
+    # aggradation case (Sec. 5.1: friction, sediment feed, q_s = alpha u^5) as printed
+    friction = None
+    if args.friction_steps > 0 and rank == 0:
+        friction = friction_leg(args, adot, W, P, n, stream, dev, local, time_steps, value)
+
     # learned |A|_Psi surrogate: harvest, train, then drive the benchmark workload
     surrogate = None
     if args.sur_steps > 0 and rank == 0:
@@ -527,6 +609,8 @@ def main():
         rate, sec, thr = oracle_throughput(n, args.cpu_steps)
         cpu = {"value": rate, "unit": UNIT, "cores": thr, "kind": "oracle",
                "sample": f"{args.cpu_steps} oracle time steps of the full N={n} workload ({sec:.1f} s)"}
+        if friction is not None:
+            cpu["soni"] = soni_oracle_time(W)
 
     solver.close()
     if rank == 0:
@@ -556,7 +640,8 @@ def main():
                          "issue_slots": issue_roofline(kind, n, per_launch_s)},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps, "clocks": clocks,
             "accuracy": accuracy, "sim_time_after_timed_steps": t_sim, "variants": variants,
-            "ensemble": ensemble, "surrogate": surrogate, "l1_t_end_sweep": sweep,
+            "ensemble": ensemble, "surrogate": surrogate, "friction": friction,
+            "l1_t_end_sweep": sweep,
         }
         print(json.dumps(line), flush=True)
     if dist:
