@@ -9,8 +9,10 @@ Every routine follows the paper (arXiv 1912.04791) as cited in the C source:
 Eq. W&A_definition (flux matrix), Eq. charPol / lambda / parameters /
 parameters_bis (analytic eigenvalues), Eq. RR / RR-1 / circPerm (eigenvectors),
 Eq. asbA / ExAbsA (|A|), Eq. path / DOTjumpN (fluctuations), Eq. scheme
-(update, with the Strickler friction source of Sec. 2 when K_s > 0), and the
-sediment feed through an end of the Soni case (Sec. 5.1). ``exact.py`` holds closed-form and exact solutions used as pins.
+(update, with the Strickler friction source of Sec. 2 when K_s > 0), the
+sediment feed through an end of the Soni case (Sec. 5.1), and a second-order
+MUSCL-Hancock variant of the scheme (path-conservative reconstruction of
+states) built on the same DOT edge. ``exact.py`` holds closed-form and exact solutions used as pins.
 """
 from __future__ import annotations
 
@@ -68,6 +70,8 @@ class Cfg(ctypes.Structure):
         ("bcl", ctypes.c_double * 3),
         ("bcr", ctypes.c_double * 3),
         ("ks", ctypes.c_double),
+        ("order", ctypes.c_int),
+        ("limiter", ctypes.c_int),
     ]
 
 
@@ -243,8 +247,10 @@ def abs_psi(law: Law, WL: np.ndarray, WR: np.ndarray, method: int = ABS_ANALYTIC
 def make_cfg(n: int, x_min: float, x_max: float, cfl: float, law: Law,
              bc_left: int = BC_TRANSMISSIVE, bc_right: int = BC_TRANSMISSIVE,
              bcl=(0.0, 0.0, 0.0), bcr=(0.0, 0.0, 0.0), method: int = ABS_ANALYTIC,
-             ks: float = 0.0) -> Cfg:
-    """Run configuration; ks > 0 adds the Strickler friction source (Sec. 2)."""
+             ks: float = 0.0, order: int = 1, limiter: int = 0) -> Cfg:
+    """Run configuration; ks > 0 adds the Strickler friction source (Sec. 2);
+    order = 2 selects the second-order MUSCL-Hancock variant (limiter 0 = minmod,
+    1 = zero slopes)."""
     c = Cfg()
     c.n = n
     c.x_min = x_min
@@ -258,6 +264,8 @@ def make_cfg(n: int, x_min: float, x_max: float, cfl: float, law: Law,
         c.bcl[i] = bcl[i]
         c.bcr[i] = bcr[i]
     c.ks = ks
+    c.order = order
+    c.limiter = limiter
     return c
 
 

@@ -32,12 +32,16 @@
  *                                                    Sec. 4 opening) or the Strickler
  *                                                    friction source of Sec. 2
  *   sediment feed through an end (Soni case) ....... Sec. 5.1 boundary data
+ *   second-order MUSCL-Hancock variant ............. Sec. 6 (no restriction on the order);
+ *                                                    Castro, Gallardo & Pares (2006), path-
+ *                                                    conservative reconstruction of states
  *
  * Parity status: every function here is pinned by tests (library eigensolver,
  * closed forms, invariants, textbook special cases); none is "parity unpinned".
  */
 #include <math.h>
 #include <stdint.h>
+#include <stdlib.h>
 #include <string.h>
 
 #ifdef _OPENMP
@@ -96,6 +100,9 @@ typedef struct {
   int bc_left, bc_right;
   double bcl[3], bcr[3];
   double ks;        /* Strickler coefficient of the friction source [m^(1/3)/s]; 0 = none */
+  int order;        /* 0 or 1: first-order scheme (Eq. scheme); 2: MUSCL-Hancock */
+  int limiter;      /* order 2: 0 = minmod slopes, 1 = zero slopes (the first-order scheme
+                       reached through the second-order code) */
 } orc_cfg;
 
 /* Threshold on the eigenvalue gap, relative to c, below which |A| is taken
@@ -682,6 +689,147 @@ static double orc_friction_source(double g, double ks, double h, double q) {
   return -g * h * sf;
 }
 
+/* ---------------------------------------------------------------------- */
+/* Second-order variant: MUSCL-Hancock in path-conservative form.           */
+/* ---------------------------------------------------------------------- */
+
+/* The paper applies A-DOT to the first-order scheme and notes (Sec. 6) that
+ * nothing restricts the order. This variant is the standard path-conservative
+ * reconstruction of states (Castro, Gallardo & Pares, Math. Comp. 2006) with a
+ * Hancock half-step predictor, built on the same DOT edge (Eq. DOTjumpN):
+ *   1. per cell, slopes of (eta = h + z, q, z) limited by minmod against both
+ *      neighbours; boundary values W-_i, W+_i at the cell's left and right
+ *      ends (reconstructing eta keeps a lake at rest exactly at rest);
+ *   2. predictor: both values advance half a step by the quasi-linear form
+ *      with the cell's own matrix, W+-_i <- W+-_i - dt/(2 dx) A(W_i) (W+_i - W-_i);
+ *   3. update: W_i <- W_i - dt/dx (D-(W+_i, W-_{i+1}) + D+(W+_{i-1}, W-_i)
+ *      + sum_k w_k A(Psi_i(s_k)) (W+_i - W-_i)), the last term being the
+ *      path integral of A along the segment inside the cell, on the same
+ *      three Gauss-Legendre nodes.
+ * A cell whose reconstructed or predicted depth is not positive keeps zero
+ * slopes (then W-_i = W+_i = W_i and the cell term vanishes). Ghost cells are
+ * those of the first-order scheme, with zero slopes. */
+static double orc_minmod(double a, double b) {
+  if (a > 0.0 && b > 0.0) return a < b ? a : b;
+  if (a < 0.0 && b < 0.0) return a > b ? a : b;
+  return 0.0;
+}
+
+/* State of cell j, -1 <= j <= n, with the ghost rules or the periodic wrap. */
+static void orc_cell_or_ghost(const orc_cfg* cfg, int periodic, const double* h, const double* q,
+                              const double* z, int64_t j, double t, double out[3]) {
+  int64_t n = cfg->n;
+  if (j >= 0 && j < n) {
+    out[0] = h[j]; out[1] = q[j]; out[2] = z[j];
+  } else if (periodic) {
+    int64_t k = (j < 0) ? j + n : j - n;
+    out[0] = h[k]; out[1] = q[k]; out[2] = z[k];
+  } else if (j < 0) {
+    int64_t k = (n > 1) ? 1 : 0;
+    double adj[3] = {h[0], q[0], z[0]}, nxt[3] = {h[k], q[k], z[k]};
+    orc_ghost(cfg->bc_left, cfg->bcl, t, adj, nxt, out);
+  } else {
+    int64_t k = (n > 1) ? n - 2 : 0;
+    double adj[3] = {h[n - 1], q[n - 1], z[n - 1]}, nxt[3] = {h[k], q[k], z[k]};
+    orc_ghost(cfg->bc_right, cfg->bcr, t, adj, nxt, out);
+  }
+}
+
+/* Edge fluctuations Dm, Dp ([3][n+1]) and cell terms Ic ([3][n]) of one
+ * MUSCL-Hancock step; Wb ([6][n]) receives the predicted W-_i (rows 0-2) and
+ * W+_i (rows 3-5). */
+static int orc_mh_terms(const orc_cfg* cfg, int periodic, const double* h, const double* q,
+                        const double* z, double t, double dt, double dx, double* Dm, double* Dp,
+                        double* Ic, double* Wb) {
+  const orc_law* L = &cfg->law;
+  int64_t n = cfg->n, ne = n + 1;
+  double half = 0.5 * dt / dx;
+  for (int64_t i = 0; i < n; ++i) {
+    double Wm[3], W0[3], Wp[3];
+    orc_cell_or_ghost(cfg, periodic, h, q, z, i - 1, t, Wm);
+    orc_cell_or_ghost(cfg, periodic, h, q, z, i, t, W0);
+    orc_cell_or_ghost(cfg, periodic, h, q, z, i + 1, t, Wp);
+    double Vm[3] = {Wm[0] + Wm[2], Wm[1], Wm[2]};
+    double V0[3] = {W0[0] + W0[2], W0[1], W0[2]};
+    double Vp[3] = {Wp[0] + Wp[2], Wp[1], Wp[2]};
+    double sv[3], WL[3], WR[3];
+    for (int r = 0; r < 3; ++r)
+      sv[r] = (cfg->limiter == 1) ? 0.0 : orc_minmod(V0[r] - Vm[r], Vp[r] - V0[r]);
+    /* slopes of (h, q, z): the h slope is the eta slope minus the z slope */
+    double sw[3] = {sv[0] - sv[2], sv[1], sv[2]};
+    for (int r = 0; r < 3; ++r) {
+      WL[r] = W0[r] - 0.5 * sw[r];
+      WR[r] = W0[r] + 0.5 * sw[r];
+    }
+    int flat = !(WL[0] > 0.0) || !(WR[0] > 0.0);
+    if (!flat) {
+      double A[9];
+      int st = orc_flux_matrix(L, W0[0], W0[1], A);
+      if (st) return st;
+      double d[3] = {WR[0] - WL[0], WR[1] - WL[1], WR[2] - WL[2]};
+      for (int r = 0; r < 3; ++r) {
+        double Ad = A[3 * r] * d[0] + A[3 * r + 1] * d[1] + A[3 * r + 2] * d[2];
+        WL[r] -= half * Ad;
+        WR[r] -= half * Ad;
+      }
+      flat = !(WL[0] > 0.0) || !(WR[0] > 0.0);
+    }
+    if (flat) {
+      for (int r = 0; r < 3; ++r) WL[r] = WR[r] = W0[r];
+    }
+    for (int r = 0; r < 3; ++r) {
+      Wb[r * n + i] = WL[r];
+      Wb[(3 + r) * n + i] = WR[r];
+    }
+  }
+  int status = ORC_OK;
+#pragma omp parallel for schedule(static)
+  for (int64_t e = 0; e < ne; ++e) {
+    double wl[3], wr[3];
+    if (e == 0 && !periodic) {
+      orc_cell_or_ghost(cfg, periodic, h, q, z, -1, t, wl);
+    } else {
+      int64_t il = (e == 0) ? n - 1 : e - 1;
+      for (int r = 0; r < 3; ++r) wl[r] = Wb[(3 + r) * n + il];
+    }
+    if (e == n && !periodic) {
+      orc_cell_or_ghost(cfg, periodic, h, q, z, n, t, wr);
+    } else {
+      int64_t ir = (e == n) ? 0 : e;
+      for (int r = 0; r < 3; ++r) wr[r] = Wb[r * n + ir];
+    }
+    double dm[3], dp[3];
+    int st = orc_fluct_edge(L, cfg->abs_method, wl, wr, dm, dp);
+    if (st) {
+#pragma omp critical
+      if (!status) status = st;
+    }
+    for (int r = 0; r < 3; ++r) {
+      Dm[r * ne + e] = dm[r];
+      Dp[r * ne + e] = dp[r];
+    }
+  }
+  if (status) return status;
+  double s[3], w[3];
+  orc_gl3(s, w);
+  for (int64_t i = 0; i < n; ++i) {
+    double WL[3], d[3], acc[3] = {0.0, 0.0, 0.0};
+    for (int r = 0; r < 3; ++r) {
+      WL[r] = Wb[r * n + i];
+      d[r] = Wb[(3 + r) * n + i] - WL[r];
+    }
+    for (int k = 0; k < 3; ++k) {
+      double A[9];
+      int st = orc_flux_matrix(L, WL[0] + s[k] * d[0], WL[1] + s[k] * d[1], A);
+      if (st) return st;
+      for (int r = 0; r < 3; ++r)
+        acc[r] += w[k] * (A[3 * r] * d[0] + A[3 * r + 1] * d[1] + A[3 * r + 2] * d[2]);
+    }
+    for (int r = 0; r < 3; ++r) Ic[r * n + i] = acc[r];
+  }
+  return ORC_OK;
+}
+
 /* Advances the state (h, q, z arrays of n cells, in place) by at most
  * max_steps steps of Eq. scheme, stopping when the time reaches t_end.
  * Per step: dt = cfl * dx / max_i max(|l1|, |l3|)(W_i) over the cells; the last
@@ -697,6 +845,12 @@ int orc_run(const orc_cfg* cfg, double* h, double* q, double* z, int64_t max_ste
   int periodic = (cfg->bc_left == ORC_BC_PERIODIC);
   if (periodic != (cfg->bc_right == ORC_BC_PERIODIC)) return ORC_E_INVALID;
   if (!(cfg->ks >= 0.0)) return ORC_E_INVALID;
+  int order2 = (cfg->order == 2);
+  if (cfg->order < 0 || cfg->order > 2) return ORC_E_INVALID;
+  /* the second-order variant covers the frictionless scheme without a feed */
+  if (order2 && (cfg->ks > 0.0 || cfg->bc_left == ORC_BC_INFLOW_QS ||
+                 cfg->bc_right == ORC_BC_INFLOW_QS))
+    return ORC_E_INVALID;
   double dx = (cfg->x_max - cfg->x_min) / (double)n;
   int64_t ne = n + 1;
   double* Dm = work;
@@ -704,6 +858,16 @@ int orc_run(const orc_cfg* cfg, double* h, double* q, double* z, int64_t max_ste
   double t = *t_io;
   int64_t steps = 0;
   int status = ORC_OK;
+  double *Ic = NULL, *Wb = NULL;
+  if (order2) {
+    Ic = (double*)malloc(sizeof(double) * 3 * (size_t)n);
+    Wb = (double*)malloc(sizeof(double) * 6 * (size_t)n);
+    if (!Ic || !Wb) {
+      free(Ic);
+      free(Wb);
+      return ORC_E_INVALID;
+    }
+  }
   if (steps_out) *steps_out = 0;
   while (steps < max_steps && t < t_end) {
     /* CFL */
@@ -711,12 +875,38 @@ int orc_run(const orc_cfg* cfg, double* h, double* q, double* z, int64_t max_ste
     for (int64_t i = 0; i < n; ++i) {
       double r;
       int st = orc_spectral_radius(&cfg->law, h[i], q[i], &r);
-      if (st) return st;
+      if (st) {
+        status = st;
+        break;
+      }
       if (r > rho) rho = r;
     }
-    if (!(rho > 0.0) || !isfinite(rho)) return ORC_E_NONFINITE;
+    if (status) break;
+    if (!(rho > 0.0) || !isfinite(rho)) {
+      status = ORC_E_NONFINITE;
+      break;
+    }
     double dt = cfg->cfl * dx / rho;
     if (t + dt >= t_end) dt = t_end - t;
+    if (order2) {
+      /* second-order variant: MUSCL-Hancock terms, then the update */
+      status = orc_mh_terms(cfg, periodic, h, q, z, t, dt, dx, Dm, Dp, Ic, Wb);
+      if (status) break;
+      double nu2 = dt / dx;
+      for (int64_t i = 0; i < n; ++i) {
+        h[i] = h[i] - nu2 * (Dm[0 * ne + i + 1] + Dp[0 * ne + i] + Ic[0 * n + i]);
+        q[i] = q[i] - nu2 * (Dm[1 * ne + i + 1] + Dp[1 * ne + i] + Ic[1 * n + i]);
+        z[i] = z[i] - nu2 * (Dm[2 * ne + i + 1] + Dp[2 * ne + i] + Ic[2 * n + i]);
+        if (!(h[i] > 0.0)) status = ORC_E_DEPTH;
+        if (!isfinite(h[i]) || !isfinite(q[i]) || !isfinite(z[i])) status = ORC_E_NONFINITE;
+      }
+      t += dt;
+      ++steps;
+      if (dt_last) *dt_last = dt;
+      if (steps_out) *steps_out = steps;
+      if (status) break;
+      continue;
+    }
     /* fluctuations on every edge */
 #pragma omp parallel for schedule(static)
     for (int64_t e = 0; e < ne; ++e) {
@@ -800,6 +990,8 @@ int orc_run(const orc_cfg* cfg, double* h, double* q, double* z, int64_t max_ste
     if (steps_out) *steps_out = steps;
     if (status) break;
   }
+  free(Ic);
+  free(Wb);
   *t_io = t;
   return status;
 }
