@@ -97,6 +97,8 @@ def parse():
                     help="also run the smooth problem to t_end = 0.5 s at N = 1e3 * 2^k (FP32, FP64, oracle)")
     ap.add_argument("--friction-steps", type=int, default=960,
                     help="timed steps of the workload with the Strickler friction source (0 = skip)")
+    ap.add_argument("--order2-steps", type=int, default=480,
+                    help="timed steps of the second-order (MUSCL-Hancock) variant (0 = skip)")
     ap.add_argument("--accuracy-steps", type=int, default=96,
                     help="steps of the FP32-vs-FP64 increment check (0 = skip)")
     return ap.parse_args()
@@ -361,6 +363,40 @@ def friction_leg(args, adot, W, P, n, stream, dev, local, time_steps, plain_valu
     return out
 
 
+def order2_leg(args, adot, P, n, stream, local, time_steps, plain_value, acc_steps=96):
+    """The benchmark workload with the second-order variant (order = 2), FP32,
+    autotuned among its warp-tile variants; its FP32 increment over acc_steps
+    steps against the GPU FP64 second-order path."""
+    K = args.order2_steps
+    cfg = adot.config_for(P, adot.FP32, block_threads=args.block, reg_cap=args.reg_cap,
+                          step_kernel=args.step_kernel, device=local, order=2)
+    with adot.Solver(cfg, stream=stream) as s2:
+        s2.set_state(P.h, P.q, P.z)
+        b2, c2, k2 = adot.adot_autotune(s2.ctx, 8)
+        adot.adot_step(s2.ctx, 48)
+        ms = time_steps(s2, K)
+        s2.set_state(P.h, P.q, P.z)
+        s2.step(acc_steps)
+        got = s2.get_state()
+    with adot.Solver(adot.config_for(P, adot.FP64, device=local, order=2), stream=stream) as s64:
+        s64.set_state(P.h, P.q, P.z)
+        s64.step(acc_steps)
+        ref = s64.get_state()
+    per_launch_s = ms * 1e-3 / K
+    out = {"workload": f"smooth_periodic N={n}, second-order MUSCL-Hancock (FP32)",
+           "steps": K, "ms_per_step": ms / K, "cell_updates_per_s": n * K / (ms * 1e-3),
+           "vs_first_order": (n * K / (ms * 1e-3)) / plain_value,
+           "kernel": f"k_step2_warp<float,GRASS,{b2},{max(c2, 0)}>",
+           "hbm_achieved_gbs": BYTES_PER_CELL_UPDATE * n / per_launch_s / 1e9,
+           "accuracy": {"steps": acc_steps, "reference": "GPU FP64 second-order path"}}
+    if INSTR_PER_CELL_UPDATE.get("order2"):
+        out["issue_slots"] = issue_roofline("order2", n, per_launch_s)
+    for name, a, b, a0 in zip("hqz", got, ref, (P.h, P.q, P.z)):
+        out["accuracy"][f"l1_rel_increment_{name}"] = float(np.abs((a - a0) - (b - a0)).sum()
+                                                            / np.abs(b - a0).sum())
+    return out
+
+
 def soni_oracle_time(W):
     """The Soni case (100 cells, 2400 s) run by the FP64 oracle on one host core."""
     import oracle as O
@@ -597,6 +633,11 @@ def main():
     if args.friction_steps > 0 and rank == 0:
         friction = friction_leg(args, adot, W, P, n, stream, dev, local, time_steps, value)
 
+    # second-order MUSCL-Hancock variant on the benchmark workload
+    order2 = None
+    if args.order2_steps > 0 and rank == 0:
+        order2 = order2_leg(args, adot, P, n, stream, local, time_steps, value)
+
     # learned |A|_Psi surrogate: harvest, train, then drive the benchmark workload
     surrogate = None
     if args.sur_steps > 0 and rank == 0:
@@ -640,7 +681,7 @@ def main():
                          "issue_slots": issue_roofline(kind, n, per_launch_s)},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps, "clocks": clocks,
             "accuracy": accuracy, "sim_time_after_timed_steps": t_sim, "variants": variants,
-            "ensemble": ensemble, "surrogate": surrogate, "friction": friction,
+            "ensemble": ensemble, "surrogate": surrogate, "friction": friction, "order2": order2,
             "l1_t_end_sweep": sweep,
         }
         print(json.dumps(line), flush=True)

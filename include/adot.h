@@ -117,6 +117,13 @@ typedef struct {
   double ks;                /* Strickler coefficient K_s [m^(1/3)/s] of the friction source
                                S = (0, -g h s_f, 0), s_f = q|q| / (K_s^2 h^(10/3)) (Sec. 2),
                                added as dt S(W_i^n) in Eq. scheme; 0 = frictionless */
+  int32_t order;            /* 0 or 1: the first-order scheme (Eq. scheme); 2: second-order
+                               MUSCL-Hancock variant (minmod slopes of h + z, q, z, Hancock
+                               half-step predictor, DOT edges between the predicted states
+                               plus the path integral of A inside each cell; Sec. 6 leaves
+                               the order open). Order 2 runs the warp-tile kernel only
+                               (step_kernel 0 or 2) and is frictionless without a feed
+                               (ks = 0, no ADOT_BC_INFLOW_QS): ADOT_E_UNSUPPORTED otherwise */
 } adot_config;
 
 typedef struct adot_ctx adot_ctx;

@@ -48,7 +48,7 @@ class Config(ctypes.Structure):
                 ("bc_right_value", ctypes.c_double * 3), ("block_threads", ctypes.c_int32),
                 ("steps_per_graph", ctypes.c_int32), ("device", ctypes.c_int32),
                 ("reg_cap", ctypes.c_int32), ("step_kernel", ctypes.c_int32),
-                ("ks", ctypes.c_double)]
+                ("ks", ctypes.c_double), ("order", ctypes.c_int32)]
 
 
 class EnsembleConfig(ctypes.Structure):
@@ -168,7 +168,7 @@ def make_config(n_cells, x_min, x_max, cfl, Ag, xi, precision=FP32, bc_left=BC_T
                 bc_right=BC_TRANSMISSIVE, bcl=(0.0, 0.0, 0.0), bcr=(0.0, 0.0, 0.0), g=9.81,
                 law=LAW_GRASS, s_rel=0.0, d50=0.0, manning_n=0.0, block_threads=0,
                 steps_per_graph=0, device=-1, reg_cap=0, step_kernel=0, u_cr=0.0, beta=0.0,
-                ks=0.0) -> Config:
+                ks=0.0, order=0) -> Config:
     c = Config()
     c.n_cells = int(n_cells)
     c.x_min, c.x_max, c.cfl = float(x_min), float(x_max), float(cfl)
@@ -184,6 +184,7 @@ def make_config(n_cells, x_min, x_max, cfl, Ag, xi, precision=FP32, bc_left=BC_T
     c.reg_cap = reg_cap
     c.step_kernel = step_kernel
     c.ks = float(ks)
+    c.order = int(order)
     return c
 
 

@@ -115,11 +115,15 @@ adot_status adot::validate_config(const adot_config* c) {
   for (int i = 0; i < 3; ++i)
     if (!isfinite(c->bc_left_value[i]) || !isfinite(c->bc_right_value[i])) return ADOT_E_INVALID_ARG;
   if (!(c->ks >= 0.0) || !isfinite(c->ks)) return ADOT_E_INVALID_ARG;
+  if (c->order < 0 || c->order > 2) return ADOT_E_INVALID_ARG;
   if (c->block_threads != 0 && !step_block_supported(c->block_threads)) return ADOT_E_INVALID_ARG;
   if (c->reg_cap != 0 && c->reg_cap != 64 && c->reg_cap != 72 && c->reg_cap != 80 && c->reg_cap != -1)
     return ADOT_E_INVALID_ARG;
   if (c->step_kernel < 0 || c->step_kernel > 2) return ADOT_E_INVALID_ARG;
   if (c->steps_per_graph < 0 || c->device < -1) return ADOT_E_INVALID_ARG;
+  if (c->order == 2 && (c->step_kernel == 1 || c->reg_cap == -1 || c->ks != 0.0 ||
+                        c->bc_left == ADOT_BC_INFLOW_QS || c->bc_right == ADOT_BC_INFLOW_QS))
+    return ADOT_E_UNSUPPORTED;
   return ADOT_OK;
 }
 
@@ -156,6 +160,7 @@ void adot::make_step_params(const adot_config* cfg, StepParams* out) {
   p.fric = (cfg->ks > 0.0) ? L.g / (cfg->ks * cfg->ks) : 0.0;
   p.feed_l = L.xi * cfg->bc_left_value[1];
   p.feed_r = L.xi * cfg->bc_right_value[1];
+  p.order = (cfg->order == 2) ? 2 : 1;
 }
 
 namespace {
@@ -226,8 +231,8 @@ adot_status enqueue(adot_ctx* c, int64_t n) {
 }
 
 // Process-wide cache of tuned variants: (device, law, precision, log2 n, filters,
-// friction / feed kernels or not).
-using TuneKey = std::tuple<int, int, int, int, int, int, int, int>;
+// friction / feed kernels or not, order of the scheme).
+using TuneKey = std::tuple<int, int, int, int, int, int, int, int, int>;
 std::mutex g_tune_mu;
 std::map<TuneKey, StepVariant> g_tune_cache;
 
@@ -235,7 +240,7 @@ TuneKey tune_key(const adot_ctx* c) {
   int lg = 0;
   for (int64_t n = c->p.n; n > 1; n >>= 1) ++lg;
   return std::make_tuple(c->device, c->law, c->prec, lg, c->cfg.block_threads, c->cfg.reg_cap,
-                         c->cfg.step_kernel, step_needs_ext(c->p) ? 1 : 0);
+                         c->cfg.step_kernel, step_needs_ext(c->p) ? 1 : 0, c->p.order);
 }
 
 bool candidate(const adot_config& cfg, StepVariant v) {
@@ -244,6 +249,7 @@ bool candidate(const adot_config& cfg, StepVariant v) {
   if (cfg.reg_cap == -1 && v.reg_cap != 0) return false;
   if (cfg.step_kernel == 1 && v.warp_tiles) return false;
   if (cfg.step_kernel == 2 && !v.warp_tiles) return false;
+  if (cfg.order == 2 && !v.warp_tiles) return false;  // the second-order kernel is warp tiles
   return true;
 }
 
@@ -380,6 +386,8 @@ uint64_t config_fingerprint(const adot_config& c) {
   h = fnv1a(h, &c.law.u_cr, sizeof c.law.u_cr);
   h = fnv1a(h, &c.law.beta, sizeof c.law.beta);
   h = fnv1a(h, &c.ks, sizeof c.ks);
+  const int32_t order = (c.order == 2) ? 2 : 1;
+  h = fnv1a(h, &order, sizeof order);
   h = fnv1a(h, &c.precision, sizeof c.precision);
   h = fnv1a(h, &c.bc_left, sizeof c.bc_left);
   h = fnv1a(h, &c.bc_right, sizeof c.bc_right);
@@ -450,7 +458,7 @@ adot_status adot_create(const adot_config* cfg, void* cuda_stream, adot_ctx** ou
   c->law = cfg->law.kind;
   c->var = StepVariant{cfg->block_threads ? cfg->block_threads : 256,
                        cfg->reg_cap == -1 ? 0 : 64, cfg->step_kernel == 2 ? 1 : 0};
-  if (!step_variant_supported(c->var)) {  // e.g. warp tiles without a register cap
+  if (!step_variant_supported(c->var) || !candidate(*cfg, c->var)) {  // e.g. warp tiles without a cap
     for (int i = 0; i < kNumStepVariants; ++i)
       if (candidate(*cfg, kStepVariants[i])) {
         c->var = kStepVariants[i];
@@ -753,7 +761,8 @@ adot_status adot_set_surrogate(adot_ctx* c, adot_mlp* m, double fr_lo, double fr
     c->mlp = nullptr;
     return build_graph(c);
   }
-  if (c->prec != ADOT_FP32 || c->law != ADOT_LAW_GRASS) return ADOT_E_UNSUPPORTED;
+  if (c->prec != ADOT_FP32 || c->law != ADOT_LAW_GRASS || c->p.order == 2)
+    return ADOT_E_UNSUPPORTED;
   if (!mlp_ready(m) || !(fr_lo <= fr_hi)) return ADOT_E_INVALID_ARG;
   CK(cudaStreamSynchronize(c->stream));
   if (!c->d_absA) {

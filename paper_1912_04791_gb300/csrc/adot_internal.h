@@ -50,6 +50,7 @@ struct StepParams {
   LawT<double> ld;
   double fric;              // g / K_s^2 of the Strickler friction source; 0 = none
   double feed_l, feed_r;    // xi q_s,in imposed through a BC_INFLOW_QS end
+  int order;                // 1: Eq. scheme; 2: MUSCL-Hancock (k_step2_warp)
   Ctl* ctl;
   const float* absA;  // surrogate |A|_Psi per edge, [9][n+1] (NaN in row 0: analytic edge)
 };
@@ -104,6 +105,13 @@ cudaError_t launch_step_f32_ext(const StepParams& p, int law, StepVariant v, Sta
                                 StateF32 out, int slot, cudaStream_t s);
 cudaError_t launch_step_f64_ext(const StepParams& p, int law, StepVariant v, StateF64 in,
                                 StateF64 out, int slot, cudaStream_t s);
+
+// Second-order (MUSCL-Hancock) time step, warp-tile variants only; the plain
+// entry points forward to these when p.order == 2.
+cudaError_t launch_step2_f32(const StepParams& p, int law, StepVariant v, StateF32 in,
+                             StateF32 out, int slot, cudaStream_t s);
+cudaError_t launch_step2_f64(const StepParams& p, int law, StepVariant v, StateF64 in,
+                             StateF64 out, int slot, cudaStream_t s);
 
 // Time step whose edges take |A|_Psi from p.absA (float32, Grass law, 256 x 64).
 cudaError_t launch_step_sur_f32(const StepParams& p, StateF32 in, StateF32 out, int slot,

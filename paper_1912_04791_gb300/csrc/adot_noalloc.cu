@@ -101,7 +101,7 @@ extern "C" adot_status adot_step_noalloc(const adot_config* cfg, double* h, doub
   double* buf = scratch + kCtlWords;
   const StateF64 user{h, q, z};
   const StateF64 tmp{buf, buf + ADOT_NOALLOC_MAX_CELLS, buf + 2 * ADOT_NOALLOC_MAX_CELLS};
-  const StepVariant v{256, 64};
+  const StepVariant v{256, 64, p.order == 2 ? 1 : 0};  // order 2 runs warp tiles
   const int law = cfg->law.kind;
 
   k_noalloc_ctl_init<<<1, 32, 0, s>>>(p.ctl, *t_io);

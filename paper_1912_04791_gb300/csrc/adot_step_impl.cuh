@@ -375,6 +375,41 @@ __global__ void __launch_bounds__(B, MinBlocks<B, CAP>::value) k_step(const Step
   if (flags) atomicOr(&ctl->status, flags);
 }
 
+// Step size of a warp-tile kernel: lane 0 forms dt = cfl dx / rho from the
+// control slot (clipped to land on t_end) and the first warp of the grid writes
+// the next slot; every warp gets nu = dt/dx and whether the run is done.
+template <typename R>
+__device__ __forceinline__ void warp_step_size(const StepParams& p, int slot, int lane,
+                                               bool first_warp, R& nu, bool& done) {
+  Ctl* ctl = p.ctl;
+  R nu0 = R(0);
+  int done0 = 0;
+  if (lane == 0) {
+    const CtlSlot cs = ctl->s[slot];
+    const double t_end = ctl->t_end;
+    const bool d = !(cs.t < t_end);
+    const double rho = Prec<R>::from_bits(cs.rho_bits);
+    double dt = p.cfl * p.dx / rho;
+    double tn = cs.t + dt;
+    if (tn >= t_end) {
+      dt = t_end - cs.t;
+      tn = t_end;
+    }
+    nu0 = d ? R(0) : R(dt / p.dx);
+    done0 = d ? 1 : 0;
+    if (first_warp) {
+      CtlSlot& nx = ctl->s[(slot + 1) % 3];
+      nx.t = d ? cs.t : tn;
+      nx.dt = d ? cs.dt : dt;
+      nx.steps = cs.steps + (d ? 0 : 1);
+      if (d) nx.rho_bits = cs.rho_bits;
+      ctl->s[(slot + 2) % 3].rho_bits = 0ull;
+    }
+  }
+  nu = __shfl_sync(0xffffffffu, nu0, 0);
+  done = __shfl_sync(0xffffffffu, done0, 0) != 0;
+}
+
 // Persistent warp-tile variant of the time step. Each warp owns tiles of 32
 // edges / 31 cells (tile t: edges 31t .. 31t+31, cells 31t .. 31t+30) and walks
 // them with a grid-wide stride; D+ of edge e-1 comes from the left lane by a
@@ -393,33 +428,9 @@ __global__ void __launch_bounds__(B, MinBlocks<B, CAP>::value)
   const int64_t n_tiles = (n + 30) / 31;
   Ctl* ctl = p.ctl;
 
-  // step size (every warp forms the same value from the control slot)
-  R nu0 = R(0);
-  int done0 = 0;
-  if (lane == 0) {
-    const CtlSlot cs = ctl->s[slot];
-    const double t_end = ctl->t_end;
-    const bool d = !(cs.t < t_end);
-    const double rho = Prec<R>::from_bits(cs.rho_bits);
-    double dt = p.cfl * p.dx / rho;
-    double tn = cs.t + dt;
-    if (tn >= t_end) {
-      dt = t_end - cs.t;
-      tn = t_end;
-    }
-    nu0 = d ? R(0) : R(dt / p.dx);
-    done0 = d ? 1 : 0;
-    if (gw == 0) {
-      CtlSlot& nx = ctl->s[(slot + 1) % 3];
-      nx.t = d ? cs.t : tn;
-      nx.dt = d ? cs.dt : dt;
-      nx.steps = cs.steps + (d ? 0 : 1);
-      if (d) nx.rho_bits = cs.rho_bits;
-      ctl->s[(slot + 2) % 3].rho_bits = 0ull;
-    }
-  }
-  const R nu = __shfl_sync(0xffffffffu, nu0, 0);
-  const bool done = __shfl_sync(0xffffffffu, done0, 0) != 0;
+  R nu;
+  bool done;
+  warp_step_size<R>(p, slot, lane, gw == 0, nu, done);
 
   unsigned flags = 0;
   R rho_run = R(0);

@@ -38,8 +38,8 @@ int main(void) {
          offsetof(adot_config, bc_left_value), offsetof(adot_config, bc_right_value),
          offsetof(adot_config, block_threads), offsetof(adot_config, device),
          offsetof(adot_config, step_kernel), offsetof(adot_law, manning_n));
-  printf("%zu %zu %zu\n", offsetof(adot_config, ks), offsetof(adot_law, u_cr),
-         offsetof(adot_law, beta));
+  printf("%zu %zu %zu %zu\n", offsetof(adot_config, ks), offsetof(adot_law, u_cr),
+         offsetof(adot_law, beta), offsetof(adot_config, order));
   printf("%zu %zu %zu %zu %zu %zu\n", sizeof(adot_ensemble_config), offsetof(adot_ensemble_config, g),
          offsetof(adot_ensemble_config, precision), offsetof(adot_ensemble_config, block_threads),
          offsetof(adot_ensemble_config, device), offsetof(adot_ensemble_config, step_kernel));
@@ -54,7 +54,7 @@ int main(void) {
     want = [ctypes.sizeof(C), ctypes.sizeof(W), C.law.offset, C.precision.offset,
             C.bc_left_value.offset, C.bc_right_value.offset, C.block_threads.offset,
             C.device.offset, C.step_kernel.offset, W.manning_n.offset,
-            C.ks.offset, W.u_cr.offset, W.beta.offset,
+            C.ks.offset, W.u_cr.offset, W.beta.offset, C.order.offset,
             ctypes.sizeof(E), E.g.offset, E.precision.offset, E.block_threads.offset, E.device.offset,
             E.step_kernel.offset]
     assert got == want
@@ -71,7 +71,7 @@ def test_status_strings_and_version(L):
     ("n_cells", 0), ("cfl", 0.0), ("cfl", 1.5), ("x_max", -1.0), ("precision", 7),
     ("bc_left", 9), ("block_threads", 100), ("steps_per_graph", -6), ("device", -3),
     ("reg_cap", 32), ("step_kernel", 3), ("bc_left", 7), ("bc_right", -1), ("ks", -1.0),
-    ("ks", float("nan")), ("ks", float("inf"))])
+    ("ks", float("nan")), ("ks", float("inf")), ("order", 3), ("order", -1)])
 def test_invalid_config_rejected_without_cuda(L, field, value):
     cfg = adot.make_config(64, 0.0, 1.0, 0.8, 0.005, 5 / 3)
     setattr(cfg, field, value)
@@ -85,6 +85,16 @@ def test_invalid_power_law_rejected(L, beta, ucr):
     cfg = adot.make_config(64, 0.0, 1.0, 0.8, 0.005, 5 / 3, law=adot.LAW_POWER, beta=beta, u_cr=ucr)
     out = ctypes.c_void_p()
     assert L.adot_create(ctypes.byref(cfg), None, ctypes.byref(out)) == adot.E_INVALID_ARG
+    assert not out.value
+
+
+@pytest.mark.parametrize("kw", [{"step_kernel": 1}, {"reg_cap": -1}, {"ks": 30.0},
+                                {"bc_left": adot.BC_INFLOW_QS, "bcl": (0.2, 1e-4, 0.0)}])
+def test_second_order_combinations_unsupported(L, kw):
+    """Order 2 runs the warp-tile kernel only, without friction or a feed."""
+    cfg = adot.make_config(64, 0.0, 1.0, 0.8, 0.005, 5 / 3, order=2, **kw)
+    out = ctypes.c_void_p()
+    assert L.adot_create(ctypes.byref(cfg), None, ctypes.byref(out)) == adot.E_UNSUPPORTED
     assert not out.value
 
 

@@ -9,7 +9,8 @@ all 1e7 cells, every edge's fluctuations) compared cell by cell.
 Ensemble: the 4096-channel movable-bed Riemann ensemble (8.6e7 cells, one
 launch per step), with a set of sampled channels (longest, shortest, random)
 run by the oracle one by one to the same end time. The single-channel
-workload also runs with the Strickler friction source (K_s = 30).
+workload also runs with the Strickler friction source (K_s = 30) and with the
+second-order MUSCL-Hancock variant.
 
 Tolerances as for the small cases: FP64 every value within 1e-12 of the
 variable's scale and the same time; FP32 (float-float state, float32
@@ -99,6 +100,36 @@ def test_full_size_with_friction_matches_oracle(gpu, full_problem, full_oracle_f
     h, q, z, t = _gpu_run(gpu, P, getattr(gpu, prec), block_threads=256, reg_cap=64, step_kernel=2,
                           ks=KS_FULL)
     ho, qo, zo, to = full_oracle_friction
+    if prec == "FP64":
+        assert t == pytest.approx(to, rel=1e-13)
+        for a, b in ((h, ho), (q, qo), (z, zo)):
+            assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max()
+        return
+    assert t == pytest.approx(to, rel=1e-5)
+    for a, b, a0 in ((h, ho, P.h), (q, qo, P.q), (z, zo, P.z)):
+        inc, ref = a - a0, b - a0
+        err = np.abs(inc - ref)
+        assert err.sum() <= 1e-5 * np.abs(ref).sum(), err.sum() / np.abs(ref).sum()
+        assert err.max() <= 1e-4 * np.abs(ref).max(), err.max() / np.abs(ref).max()
+
+
+@pytest.fixture(scope="module")
+def full_oracle_order2(full_problem, oracle):
+    P = full_problem
+    cfg = O.make_cfg(P.n, P.x_min, P.x_max, P.cfl, O.grass(P.Ag, xi=P.xi, g=P.g), P.bc_left,
+                     P.bc_right, P.bcl, P.bcr, order=2)
+    h, q, z, t, steps, _ = O.run(cfg, P.h, P.q, P.z, max_steps=K)
+    assert steps == K
+    return h, q, z, t
+
+
+@pytest.mark.parametrize("prec", ["FP64", "FP32"])
+def test_full_size_second_order_matches_oracle(gpu, full_problem, full_oracle_order2, prec):
+    """The second-order variant (MUSCL-Hancock) on the same workload, autotuned
+    among its warp-tile variants as the benchmark's second-order line runs it."""
+    P = full_problem
+    h, q, z, t = _gpu_run(gpu, P, getattr(gpu, prec), order=2)
+    ho, qo, zo, to = full_oracle_order2
     if prec == "FP64":
         assert t == pytest.approx(to, rel=1e-13)
         for a, b in ((h, ho), (q, qo), (z, zo)):
