@@ -45,8 +45,10 @@ FLOPS_PER_CELL_UPDATE = {"block": 633.6, "warp": 628.0}
 DRAM_BYTES_PER_CELL_UPDATE = {"block": None, "warp": (97.90e6 + 65.27e6) / 4e6}
 BYTES_PER_CELL_UPDATE = 48.0  # float-float state: 3 x 8 B read + 3 x 8 B written
 # Executed thread instructions per cell-update of one launch (ncu smsp__inst_executed x 32 / cells,
-# N = 4e6, the 1-in-32 repeated edge included); None where the kernel changed after its capture.
-INSTR_PER_CELL_UPDATE = {"block": None, "warp": 93.37e6 * 32 / 4e6}
+# N = 4e6, repeated edges and boundary values included; "order2" is the second-order kernel);
+# None where the kernel changed after its capture.
+INSTR_PER_CELL_UPDATE = {"block": None, "warp": 93.37e6 * 32 / 4e6,
+                         "order2": 139.67e6 * 32 / 4e6}
 
 
 def issue_roofline(kind: str, n: int, per_launch_s: float):
