@@ -34,21 +34,21 @@ UNIT = "cell-updates/s"
 # FMUL thread instructions of one launch divided by the cells it updates.
 # Per kernel kind: the block kernel repeats 1 edge in 256, the warp-tile
 # kernel 1 in 32; that repeated work is removed from the executed counts
-# (636.1 x 255/256 and 648.3 x 31/32). The counts were taken on the all-scalar
+# (500.57 x 255/256 and 508.92 x 31/32). The counts were taken on the all-scalar
 # build: evaluating two nodes per paired float32x2 instruction leaves the
 # arithmetic unchanged, and ncu's per-opcode thread counters omit the paired
 # instructions.
-FLOPS_PER_CELL_UPDATE = {"block": 633.6, "warp": 628.0}
+FLOPS_PER_CELL_UPDATE = {"block": 498.6, "warp": 493.0}
 # DRAM read + write bytes per cell-update of one launch (ncu, N = 4e6): the
 # ~24 B read match the algorithmic read; part of the 24 B written is still in
 # L2. None where the kernel changed after its capture.
-DRAM_BYTES_PER_CELL_UPDATE = {"block": None, "warp": (97.90e6 + 65.27e6) / 4e6}
+DRAM_BYTES_PER_CELL_UPDATE = {"block": None, "warp": (97.77e6 + 61.40e6) / 4e6}
 BYTES_PER_CELL_UPDATE = 48.0  # float-float state: 3 x 8 B read + 3 x 8 B written
 # Executed thread instructions per cell-update of one launch (ncu smsp__inst_executed x 32 / cells,
 # N = 4e6, repeated edges and boundary values included; "order2" is the second-order kernel);
 # None where the kernel changed after its capture.
-INSTR_PER_CELL_UPDATE = {"block": None, "warp": 93.37e6 * 32 / 4e6,
-                         "order2": 139.67e6 * 32 / 4e6}
+INSTR_PER_CELL_UPDATE = {"block": None, "warp": 85.50e6 * 32 / 4e6,
+                         "order2": 131.54e6 * 32 / 4e6}
 
 
 def issue_roofline(kind: str, n: int, per_launch_s: float):

@@ -231,46 +231,45 @@ __device__ __forceinline__ void A_times(const Eig<T>& e, T v0, T v1, T v2, T& y0
   y2 = e.a * v0 + e.b * v1;
 }
 
-// Steps 4-5 applied to dW: |A| dW = sum_i |l_i| r_i (l_i . dW) with
-// r_i = [1, l_i, (u - l_i)^2/c^2 - 1] (Eq. RR) and
-// l_i = [c^2 - u^2 + l_j l_k, 2u - l_j - l_k, c^2] / ((l_i - l_j)(l_i - l_k)) (Eq. RR-1).
+// Steps 4-5 applied to dW through one spectral projector. With the projectors
+// P_i = r_i (l_i . ) / d_i of Eq. RR and RR-1 (r_i = [1, l_i, (u - l_i)^2/c^2 - 1],
+// l_i = [c^2 - u^2 + l_j l_k, 2u - l_j - l_k, c^2], d_i = (l_i - l_j)(l_i - l_k)),
+// A = sum_i l_i P_i and sum_i P_i = I, so Eq. asbA's |A| = sum_i |l_i| P_i equals
+// A - 2 sum_{l_i < 0} l_i P_i and -A + 2 sum_{l_i > 0} l_i P_i. Of three ordered roots
+// at most one lies on the minority side of zero: |A| dW = s (A dW - 2 m P_k dW)
+// with k = 1, s = 1, m = min(l1, 0) when l2 >= 0, else k = 3, s = -1, m = max(l3, 0).
 // The entries are evaluated through identities of the roots of Eq. charPol,
-// l^3 - 2u l^2 - (c^2 - u^2 + c^2 b) l - c^2 a = 0, which avoid cancelling
-// O(c) terms: 2u - l_j - l_k = l_i (sum of roots), c^2 - u^2 + l_j l_k =
-// l_i (l_i - 2u) - c^2 b (sum of pair products), and for the two roots of
-// larger magnitude (u - l_i)^2/c^2 - 1 = b + a / l_i.
+// l^3 - 2u l^2 - (c^2 - u^2 + c^2 b) l - c^2 a = 0, which avoid cancelling O(c)
+// terms: c^2 - u^2 + l_j l_k = l_k (l_k - 2u) - c^2 b (pair products), 2u - l_j - l_k =
+// l_k (sum of roots), and (u - l_k)^2/c^2 - 1 = b + a / l_k unless l_k is the root of
+// smallest magnitude. y = A dW.
 template <typename T>
-__device__ __forceinline__ void abs_A_times_eigvec(const Eig<T>& e, T dh, T dq, T dz, T& x0, T& x1,
-                                                   T& x2) {
-  const T l1 = e.l1, l2 = e.l2, l3 = e.l3;
-  const T e12 = l1 - l2, e13 = l1 - l3, e23 = l2 - l3;
-  const T invP = T(1) / (e12 * e13 * e23);
-  const T tu = T(2) * e.u;
-  const T cb = e.c2 * e.b;
-  const T cz = e.c2 * dz;
-  const T p1 = (l1 * (l1 - tu) - cb) * dh + l1 * dq + cz;
-  const T p2 = (l2 * (l2 - tu) - cb) * dh + l2 * dq + cz;
-  const T p3 = (l3 * (l3 - tu) - cb) * dh + l3 * dq + cz;
-  // 1/d1 = e23/P, 1/d2 = -e13/P, 1/d3 = e12/P
-  const T al1 = d_abs(l1) * p1 * (e23 * invP);
-  const T al2 = -d_abs(l2) * p2 * (e13 * invP);
-  const T al3 = d_abs(l3) * p3 * (e12 * invP);
-  // third entries of r_i; the root of smallest magnitude takes the direct form
-  const T v1 = e.u - l1, v2 = e.u - l2, v3 = e.u - l3;
-  T r1 = e.b + d_fdiv(e.a, l1);
-  T r2 = e.b + d_fdiv(e.a, l2);
-  T r3 = e.b + d_fdiv(e.a, l3);
-  if (e.ks == 1) r1 = v1 * v1 * e.inv_c2 - T(1);
-  if (e.ks == 2) r2 = v2 * v2 * e.inv_c2 - T(1);
-  if (e.ks == 3) r3 = v3 * v3 * e.inv_c2 - T(1);
-  if (e.ks == 0) {
-    r1 = v1 * v1 * e.inv_c2 - T(1);
-    r2 = v2 * v2 * e.inv_c2 - T(1);
-    r3 = v3 * v3 * e.inv_c2 - T(1);
+__device__ __forceinline__ void abs_A_times_proj(const Eig<T>& e, T dh, T dq, T dz, const T y[3],
+                                                 T x[3]) {
+  const bool lo = e.l2 >= T(0);
+  const T lk = lo ? e.l1 : e.l3;
+  const T lf = lo ? e.l3 : e.l1;  // the root on the far side
+  const T m2 = T(-2) * (lo ? d_min(e.l1, T(0)) : d_max(e.l3, T(0)));
+  const T dk = (lk - e.l2) * (lk - lf);
+  const T pk = (lk * (lk - T(2) * e.u) - e.c2 * e.b) * dh + lk * dq + e.c2 * dz;  // (l_k . dW) d_k
+  const int kk = lo ? 1 : 3;
+  T rk;
+  if (e.ks == kk || e.ks == 0) {
+    const T v = e.u - lk;
+    rk = v * v * e.inv_c2 - T(1);
+  } else {
+    rk = e.b + d_fdiv(e.a, lk);
   }
-  x0 = al1 + al2 + al3;
-  x1 = al1 * l1 + al2 * l2 + al3 * l3;
-  x2 = al1 * r1 + al2 * r2 + al3 * r3;
+  const T coef = m2 * d_fdiv(pk, dk);
+  if (lo) {
+    x[0] = y[0] + coef;
+    x[1] = y[1] + coef * lk;
+    x[2] = y[2] + coef * rk;
+  } else {
+    x[0] = -(y[0] + coef);
+    x[1] = -(y[1] + coef * lk);
+    x[2] = -(y[2] + coef * rk);
+  }
 }
 
 // First divided difference of |x| with the coalescence reading: a pair closer
@@ -326,7 +325,7 @@ __device__ __forceinline__ void node_f64(const LawT<double>& L, double h, double
   if (gap < TAU_GAP * e.c)
     abs_A_times_newton(e, dh, dq, dz, x[0], x[1], x[2]);
   else
-    abs_A_times_eigvec(e, dh, dq, dz, x[0], x[1], x[2]);
+    abs_A_times_proj(e, dh, dq, dz, y, x);
 }
 
 // Float64 redo of a float32 node (kept out of line so that its registers do
@@ -359,7 +358,7 @@ __device__ __forceinline__ void node_f32(const LawT<float>& L, const LawT<double
     return;
   }
   A_times(e, dh, dq, dz, y[0], y[1], y[2]);
-  abs_A_times_eigvec(e, dh, dq, dz, x[0], x[1], x[2]);
+  abs_A_times_proj(e, dh, dq, dz, y, x);
 }
 
 // Spectral radius max(|l1|, |l3|) at a state (float64: from Eq. lambda; the
@@ -430,14 +429,17 @@ __device__ __forceinline__ void abs_A_matrix_f64(const LawT<double>& L, double h
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
     const double v0 = (j == 0) ? 1.0 : 0.0, v1 = (j == 1) ? 1.0 : 0.0, v2 = (j == 2) ? 1.0 : 0.0;
-    double x0, x1, x2;
-    if (newton)
-      abs_A_times_newton(e, v0, v1, v2, x0, x1, x2);
-    else
-      abs_A_times_eigvec(e, v0, v1, v2, x0, x1, x2);
-    X[0 * 3 + j] = x0;
-    X[1 * 3 + j] = x1;
-    X[2 * 3 + j] = x2;
+    double x[3];
+    if (newton) {
+      abs_A_times_newton(e, v0, v1, v2, x[0], x[1], x[2]);
+    } else {
+      double y[3];
+      A_times(e, v0, v1, v2, y[0], y[1], y[2]);
+      abs_A_times_proj(e, v0, v1, v2, y, x);
+    }
+    X[0 * 3 + j] = x[0];
+    X[1 * 3 + j] = x[1];
+    X[2 * 3 + j] = x[2];
   }
 }
 

@@ -6,8 +6,8 @@
 // root, arccos and sincos steps and the choice of the root taken from the
 // product of the roots stay per lane. The midpoint node takes the scalar path.
 // The arithmetic is that of node_f32 (Eq. charPol/lambda, Eq. RR, RR-1,
-// Eq. asbA), with the same identities and the same float64 redo of a node
-// whose roots nearly coalesce.
+// Eq. asbA through one spectral projector), with the same identities and the
+// same float64 redo of a node whose roots nearly coalesce.
 #pragma once
 
 #include "adot_math.cuh"
@@ -115,47 +115,35 @@ __device__ __forceinline__ void A_times_x2(const Eig2& e, float dh, float dq, fl
   y[2] = fma2(e.na, p2(-dh), mul2(e.b, p2(dq)));
 }
 
-// (u - l)^2 / c^2 - 1 for the root of smallest magnitude of one lane.
-__device__ __forceinline__ void direct_r_lane(int ks, float u, float inv_c2, float l1, float l2, float l3,
-                                              float& r1, float& r2, float& r3) {
-  if (ks == 1) {
-    const float v = u - l1;
-    r1 = v * v * inv_c2 - 1.0f;
-  } else if (ks == 2) {
-    const float v = u - l2;
-    r2 = v * v * inv_c2 - 1.0f;
-  } else {
-    const float v = u - l3;
-    r3 = v * v * inv_c2 - 1.0f;
-  }
-}
-
-// |A| dW for two states, as abs_A_times_eigvec.
-__device__ __forceinline__ void abs_A_times_eigvec_x2(const Eig2& e, float dh, float dq, float dz,
-                                                      float2 x[3]) {
-  const float2 l1 = e.l1, l2 = e.l2, l3 = e.l3;
-  const float2 e12 = sub2(l1, l2), e31 = sub2(l3, l1), e23 = sub2(l2, l3);
-  const float2 invP = nrcp2(mul2(mul2(e12, e31), e23));  // 1 / ((l1-l2)(l1-l3)(l2-l3))
+// |A| dW for two states through one projector each, as abs_A_times_proj: the
+// projector's root (l1 or l3) and the sign are chosen per lane.
+__device__ __forceinline__ void abs_A_times_proj_x2(const Eig2& e, float dh, float dq, float dz,
+                                                    const float2 y[3], float2 x[3]) {
+  const bool lox = e.l2.x >= 0.0f, loy = e.l2.y >= 0.0f;
+  const float2 lk = make_float2(lox ? e.l1.x : e.l3.x, loy ? e.l1.y : e.l3.y);
+  const float2 lf = make_float2(lox ? e.l3.x : e.l1.x, loy ? e.l3.y : e.l1.y);
+  const float2 m2 = make_float2(lox ? -2.0f * fminf(e.l1.x, 0.0f) : -2.0f * fmaxf(e.l3.x, 0.0f),
+                                loy ? -2.0f * fminf(e.l1.y, 0.0f) : -2.0f * fmaxf(e.l3.y, 0.0f));
+  const float2 sg = make_float2(lox ? 1.0f : -1.0f, loy ? 1.0f : -1.0f);
+  const float2 dk = mul2(sub2(lk, e.l2), sub2(lk, lf));
+  // (l_k . dW) d_k = (l_k (l_k - 2u) - c^2 b) dh + l_k dq + c^2 dz
   const float2 ntu = mul2(e.u, p2(-2.0f));
-  // p_i = l_i . dW times (l_i - l_j)(l_i - l_k):
-  // (l_i (l_i - 2u) - c^2 b) dh + l_i dq + c^2 dz
   const float2 czb = mul2(e.c2, fma2(e.b, p2(-dh), p2(dz)));
-  const float2 p1 = fma2(mul2(l1, add2(l1, ntu)), p2(dh), fma2(l1, p2(dq), czb));
-  const float2 p2_ = fma2(mul2(l2, add2(l2, ntu)), p2(dh), fma2(l2, p2(dq), czb));
-  const float2 p3 = fma2(mul2(l3, add2(l3, ntu)), p2(dh), fma2(l3, p2(dq), czb));
-  // 1/d1 = e23/P, 1/d2 = -e13/P = e31/P, 1/d3 = e12/P
-  const float2 al1 = mul2(mul2(abs2(l1), p1), mul2(e23, invP));
-  const float2 al2 = mul2(mul2(abs2(l2), p2_), mul2(e31, invP));
-  const float2 al3 = mul2(mul2(abs2(l3), p3), mul2(e12, invP));
-  // third entries of r_i: b + a / l_i = b - na / l_i; the root of smallest magnitude directly
-  float2 r1 = fma2(e.na, nrcp2(l1), e.b);
-  float2 r2 = fma2(e.na, nrcp2(l2), e.b);
-  float2 r3 = fma2(e.na, nrcp2(l3), e.b);
-  direct_r_lane(e.ks0, e.u.x, e.inv_c2.x, l1.x, l2.x, l3.x, r1.x, r2.x, r3.x);
-  direct_r_lane(e.ks1, e.u.y, e.inv_c2.y, l1.y, l2.y, l3.y, r1.y, r2.y, r3.y);
-  x[0] = add2(add2(al1, al2), al3);
-  x[1] = fma2(al3, l3, fma2(al2, l2, mul2(al1, l1)));
-  x[2] = fma2(al3, r3, fma2(al2, r2, mul2(al1, r1)));
+  const float2 pk = fma2(mul2(lk, add2(lk, ntu)), p2(dh), fma2(lk, p2(dq), czb));
+  // third entry of r_k: b + a / l_k = b - na / l_k, or directly for the root of smallest magnitude
+  float2 rk = fma2(e.na, nrcp2(lk), e.b);
+  if (e.ks0 == (lox ? 1 : 3)) {
+    const float v = e.u.x - lk.x;
+    rk.x = v * v * e.inv_c2.x - 1.0f;
+  }
+  if (e.ks1 == (loy ? 1 : 3)) {
+    const float v = e.u.y - lk.y;
+    rk.y = v * v * e.inv_c2.y - 1.0f;
+  }
+  const float2 coef = mul2(m2, mul2(pk, rcp2(dk)));
+  x[0] = mul2(sg, add2(y[0], coef));
+  x[1] = mul2(sg, fma2(coef, lk, y[1]));
+  x[2] = mul2(sg, fma2(coef, rk, y[2]));
 }
 
 // D-/+ of one float32 edge (float-float states wl, wr): nodes s0 and s2 paired,
@@ -176,7 +164,7 @@ __device__ __forceinline__ void edge_fluct_f32x2(const LawT<float>& L, const Law
   node_eig_x2<LAW>(L, h, q, e);
   float2 y[3], x[3];
   A_times_x2(e, dh, dq, dz, y);
-  abs_A_times_eigvec_x2(e, dh, dq, dz, x);
+  abs_A_times_proj_x2(e, dh, dq, dz, y, x);
   const float2 delta = make_float2(fmaf(-e.arg.x, e.arg.x, 1.0f), fmaf(-e.arg.y, e.arg.y, 1.0f));
   if (!(delta.x >= TAU_FP64_FALLBACK)) {
     float yy[3], xx[3];
