@@ -292,6 +292,17 @@ adot_status adot_mlp_get_params(adot_mlp* mlp, float* params);
  * three-tile pipeline (default); 1 = mma.sync; 2 = tcgen05, two independent
  * tile groups per CTA. ADOT_E_INVALID_ARG for another value. */
 adot_status adot_mlp_set_engine(adot_mlp* mlp, int engine);
+/* Engine of the per-layer training kernels (forward and backward layer
+ * products, weight gradients; adot_mlp_train, adot_mlp_gradient and
+ * adot_mlp_forward with fused = 0): 0 = tcgen05.mma with tensor-memory
+ * accumulators (128-row x 64-column units for the layers, the batch rows as the
+ * reduction dimension for the weight gradients); 1 = mma.sync over 64-row tiles
+ * (default: at batch 65536 the per-layer step is bound by latency and memory
+ * traffic, not by the tensor pipes, and this engine measures faster). Both take
+ * bf16 operands and accumulate in float32. ADOT_E_INVALID_ARG for another
+ * value. A bounded device-side wait that runs out makes the call that launched
+ * it return ADOT_E_TIMEOUT. */
+adot_status adot_mlp_set_train_engine(adot_mlp* mlp, int engine);
 /* Test hook for the failure detection of the tensor-core pipeline (no
  * counterpart in the paper): kind = 1 makes the next adot_mlp_forward with
  * fused = 3 withhold one accumulator hand-off in its first CTA, so that the
@@ -311,7 +322,7 @@ adot_status adot_mlp_set_data(adot_mlp* mlp, const float* X, const float* T, int
 adot_status adot_mlp_get_stats(adot_mlp* mlp, float* stats32, float* box14);
 /* Forward pass of n <= max_batch standardised inputs Xs [n][7] (host) to
  * standardised outputs Y [n][9] (host). fused = 0: the per-layer training
- * kernels (mma.sync); 1: the single-kernel inference on mma.sync with the
+ * kernels (engine of adot_mlp_set_train_engine); 1: the single-kernel inference on mma.sync with the
  * tanhf GELU; 2 and 3: the single-kernel inference on the 5th-generation
  * tensor cores (tcgen05.mma, accumulators in tensor memory) with the
  * tanh.approx GELU, as two independent tile groups per CTA (2) or as the

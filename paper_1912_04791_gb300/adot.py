@@ -95,6 +95,7 @@ def lib() -> ctypes.CDLL:
             "adot_mlp_set_params": ([_P, _P], i32),
             "adot_mlp_get_params": ([_P, _P], i32),
             "adot_mlp_set_engine": ([_P, i32], i32),
+            "adot_mlp_set_train_engine": ([_P, i32], i32),
             "adot_mlp_inject_fault": ([_P, i32], i32),
             "adot_mlp_set_data": ([_P, _P, _P, i64, i32], i32),
             "adot_mlp_get_stats": ([_P, _P, _P], i32),
@@ -457,6 +458,10 @@ class Mlp:
         """Fused inference engine of the surrogate step: 0 = tcgen05 pipeline,
         1 = mma.sync, 2 = tcgen05 with two independent tile groups."""
         _check(lib().adot_mlp_set_engine(self.ptr, int(engine)), "adot_mlp_set_engine")
+
+    def set_train_engine(self, engine: int) -> None:
+        """Per-layer training kernels: 0 = tcgen05, 1 = mma.sync (default)."""
+        _check(lib().adot_mlp_set_train_engine(self.ptr, int(engine)), "adot_mlp_set_train_engine")
 
     def inject_fault(self, kind: int = 1) -> None:
         """Test hook: the next forward(fused=3) withholds one hand-off so that a

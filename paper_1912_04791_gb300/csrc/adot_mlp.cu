@@ -1,7 +1,8 @@
 // Learned surrogate of the quadrature-averaged |A|: an MLP
 // 7 -> 128 -> 128 -> 128 -> 128 -> 9 (GELU on the hidden layers) with bfloat16
 // weights and activations and float32 accumulation on the tensor cores
-// (mma.sync m16n8k16), trained by Adam on standardised inputs and outputs.
+// (tcgen05.mma with tensor-memory accumulators, or mma.sync m16n8k16 as the
+// selectable alternative), trained by Adam on standardised inputs and outputs.
 //
 // The surrogate replaces only |A|_Psi = sum_k w_k |A(Psi(s_k))| in
 // Eq. DOTjumpN; A dW keeps its analytic form, and edges with a local Froude
@@ -1019,6 +1020,353 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 }
 
 // --------------------------------------------------------------------------
+// training on the 5th-generation tensor cores
+// --------------------------------------------------------------------------
+// k_tc_layer: the products of k_layer, C = A S^T (+ bias) with the same
+// epilogues, on the 5th-generation tensor cores. A CTA of 8 warps computes one
+// unit of NS output columns of a 128-row tile (NS = 64 for the 128-wide layers,
+// so that four CTAs share an SM and the 1024 units of a 65536-row batch leave a
+// short tail): S rows n0 .. n0+NS-1 and the A tile [128][K] (row-major bf16) are
+// copied with cp.async into the K-major core-matrix layout of tc_canon (rows
+// past the end zero-filled); thread 0 issues K/16 tcgen05.mma of kind::f16 into
+// NS tensor-memory columns and commits to an mbarrier; warp w reads lane
+// quadrant w % 4 (tile rows 32 (w % 4) ..) and the column half w / 4, one row
+// per thread. A wait that runs out sets ST_TIMEOUT in *status, skips the
+// epilogue, and waits once more (bounded) for the products in flight before the
+// tensor memory is freed.
+constexpr int kTwThreads = 256;  // k_tc_wgrad
+constexpr int kTlThreads = 256;  // k_tc_layer
+
+// Output columns per k_tc_layer CTA, and its shared memory: the two operands
+// plus base alignment, at least 56 KB so that no more than four CTAs share an SM.
+__host__ __device__ constexpr int tc_layer_ns(int N) { return N > 64 ? 64 : N; }
+template <int K, int N>
+__host__ __device__ constexpr size_t tc_layer_smem() {
+  return ((size_t)(kTcRows + tc_layer_ns(N)) * K * 2 + 1024) > 57344
+             ? (size_t)(kTcRows + tc_layer_ns(N)) * K * 2 + 1024
+             : 57344;
+}
+
+__device__ __forceinline__ void tc_alloc(uint32_t* dst, uint32_t cols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(dst)),
+               "r"(cols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tc_dealloc(uint32_t taddr, uint32_t cols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(cols) : "memory");
+}
+
+// 16-byte asynchronous copy global -> shared; src_bytes = 0 writes zeros.
+__device__ __forceinline__ void cp_async16(uint32_t saddr, const void* g, uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(saddr), "l"(g), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n cp.async.wait_group 0;" ::: "memory");
+}
+
+// Epilogue of 16 accumulator columns c0 .. c0+15 of one row.
+template <int N, int EPI>
+__device__ __forceinline__ void tc_layer_epi16(const uint32_t* v, int c0, int64_t row,
+                                               const float* __restrict__ bias,
+                                               const __nv_bfloat16* __restrict__ aux, void* out0,
+                                               __nv_bfloat16* __restrict__ out1) {
+  if (EPI == EPI_GELU) {
+    uint32_t z[8], hh[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const float a0 = __uint_as_float(v[2 * j]) + bias[c0 + 2 * j];
+      const float a1 = __uint_as_float(v[2 * j + 1]) + bias[c0 + 2 * j + 1];
+      z[j] = pack_bf16(a0, a1);
+      hh[j] = pack_bf16(gelu_f(a0), gelu_f(a1));
+    }
+    uint4* zd = reinterpret_cast<uint4*>((__nv_bfloat16*)out0 + row * N + c0);
+    uint4* hd = reinterpret_cast<uint4*>(out1 + row * N + c0);
+    zd[0] = make_uint4(z[0], z[1], z[2], z[3]);
+    zd[1] = make_uint4(z[4], z[5], z[6], z[7]);
+    hd[0] = make_uint4(hh[0], hh[1], hh[2], hh[3]);
+    hd[1] = make_uint4(hh[4], hh[5], hh[6], hh[7]);
+  } else if (EPI == EPI_LINEAR) {
+    float4* yd = reinterpret_cast<float4*>((float*)out0 + row * N + c0);
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      yd[j] = make_float4(__uint_as_float(v[4 * j]) + bias[c0 + 4 * j],
+                          __uint_as_float(v[4 * j + 1]) + bias[c0 + 4 * j + 1],
+                          __uint_as_float(v[4 * j + 2]) + bias[c0 + 4 * j + 2],
+                          __uint_as_float(v[4 * j + 3]) + bias[c0 + 4 * j + 3]);
+  } else {
+    const uint4* zs = reinterpret_cast<const uint4*>(aux + row * N + c0);
+    const uint4 za = zs[0], zb = zs[1];
+    const uint32_t zw[8] = {za.x, za.y, za.z, za.w, zb.x, zb.y, zb.z, zb.w};
+    uint32_t o[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const __nv_bfloat162 zz = *reinterpret_cast<const __nv_bfloat162*>(&zw[j]);
+      o[j] = pack_bf16(__uint_as_float(v[2 * j]) * gelu_prime_f(__bfloat162float(zz.x)),
+                       __uint_as_float(v[2 * j + 1]) * gelu_prime_f(__bfloat162float(zz.y)));
+    }
+    uint4* od = reinterpret_cast<uint4*>((__nv_bfloat16*)out0 + row * N + c0);
+    od[0] = make_uint4(o[0], o[1], o[2], o[3]);
+    od[1] = make_uint4(o[4], o[5], o[6], o[7]);
+  }
+}
+
+template <int K, int N, int EPI>
+__global__ void __launch_bounds__(kTlThreads, 4) k_tc_layer(const __nv_bfloat16* __restrict__ A,
+                                                         const __nv_bfloat16* __restrict__ S,
+                                                         const float* __restrict__ bias,
+                                                         const __nv_bfloat16* __restrict__ aux,
+                                                         void* out0, __nv_bfloat16* __restrict__ out1,
+                                                         int64_t rows, unsigned* status) {
+  static_assert(K % 16 == 0 && (N == 16 || N == 128), "layer shape");
+  constexpr int NS = tc_layer_ns(N);
+  extern __shared__ unsigned char tl_raw[];
+  __shared__ __align__(8) uint64_t s_mbar;
+  __shared__ uint32_t s_tmem;
+  const uint32_t raw_s = smem_addr(tl_raw);
+  const uint32_t base = (raw_s + 1023u) & ~1023u;  // sA at base, sS after it
+  const uint32_t sS = base + kTcRows * K * 2;
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  const int q = w & 3, hc = w >> 2;
+  constexpr int KC = K / 8;
+  constexpr uint32_t kCols = (NS < 32) ? 32u : (uint32_t)NS;
+  const int64_t tile = (int64_t)blockIdx.x / (N / NS);
+  const int n0 = (int)(blockIdx.x % (N / NS)) * NS;
+  const int64_t row0 = tile * kTcRows;
+  for (int i = tid; i < NS * KC; i += kTlThreads) {
+    const int r = i / KC, kc = i % KC;
+    cp_async16(sS + tc_canon(r, kc, K), S + (int64_t)(n0 + r) * K + kc * 8, 16u);
+  }
+  for (int i = tid; i < kTcRows * KC; i += kTlThreads) {
+    const int r = i / KC, kc = i % KC;
+    const bool valid = row0 + r < rows;
+    cp_async16(base + tc_canon(r, kc, K), valid ? (const void*)(A + (row0 + r) * K + kc * 8) : (const void*)A,
+               valid ? 16u : 0u);
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&s_mbar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (w == 0) tc_alloc(&s_tmem, kCols);
+  cp_async_wait_all();
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+  const uint32_t mbar = smem_addr(&s_mbar);
+  if (tid == 0) {
+    const uint32_t idesc = tc_idesc(NS);
+#pragma unroll
+    for (int ks = 0; ks < K / 16; ++ks)
+      tc_mma(tmem, tc_desc(base + ks * 256, K), tc_desc(sS + ks * 256, K), idesc, ks > 0);
+    tc_commit(mbar);
+  }
+  // warp-uniform, since tcgen05.ld below is a .sync.aligned instruction
+  const bool done = __all_sync(0xffffffffu, mbar_wait_bounded(mbar, 0));
+  tc_fence_after();
+  if (done) {
+    const int64_t row = row0 + 32 * q + lane;
+    const uint32_t t_row = tmem + ((uint32_t)(32 * q) << 16);
+    if (NS == 64) {
+      // columns 32 hc .. 32 hc + 31 of the unit in two 16-column chunks, the
+      // second loading from tensor memory while the first is processed
+      const int cb = 32 * hc;
+      uint32_t va[16], vb[16];
+      tmem_ld_x16(t_row + (uint32_t)cb, va);
+      tmem_wait_ld16(va);
+      tmem_ld_x16(t_row + (uint32_t)(cb + 16), vb);
+      if (row < rows) tc_layer_epi16<N, EPI>(va, n0 + cb, row, bias, aux, out0, out1);
+      tmem_wait_ld16(vb);
+      if (row < rows) tc_layer_epi16<N, EPI>(vb, n0 + cb + 16, row, bias, aux, out0, out1);
+    } else if (hc == 0) {
+      uint32_t v[16];
+      tmem_ld_x16(t_row, v);
+      tmem_wait_ld16(v);
+      if (row < rows) tc_layer_epi16<N, EPI>(v, n0, row, bias, aux, out0, out1);
+    }
+  } else if (tid == 0) {
+    mbar_wait_bounded(mbar, 0);
+    if (status) atomicOr(status, ST_TIMEOUT);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (w == 0) {
+    tc_fence_after();
+    tc_dealloc(tmem, kCols);
+  }
+}
+
+// k_tc_wgrad: the weight-gradient partials of k_wgrad, dW[N][K] = sum over the
+// block's `chunk` batch rows of dZ[r][n] X[r][k] and db[n] = sum of dZ[r][n],
+// with the batch rows as the reduction dimension of tcgen05.mma: per 128-row
+// sub-chunk the loading threads transpose dZ and X into K-major operands
+// (element (m, r) of an operand at tc_canon(m, r / 8, 128) + (r % 8) * 2; each
+// thread packs two consecutive batch rows into one 32-bit word), thread 0
+// issues eight products (K = 16 each) that accumulate in tensor memory over the
+// whole chunk, and the first four warps write the block's float32 partial. With
+// N < 64 (the output layer) the product is dW^T = X^T dZ so that M = K = 128.
+// Eight warps: thread t loads batch rows 2 (t % 64) and 2 (t % 64) + 1 and a
+// quarter of the columns of each operand (a half of the 16-wide ones, which the
+// other half of the threads skip).
+template <int K, int N>
+__host__ __device__ constexpr size_t tc_wgrad_smem() {
+  return (size_t)(K + N) * kTcRows * 2 + 1024;
+}
+
+// Rows ra and rb (< c1, else zeros) of a [rows][C] bf16 matrix, columns of this
+// thread's part (C / NP columns), stored transposed into the K-major operand
+// dst[c][p, p + 1] (one 32-bit word per column: the two rows' values).
+template <int C, int NP>
+__device__ __forceinline__ void tc_scatter_rows(const __nv_bfloat16* __restrict__ src, int64_t ra,
+                                                int64_t rb, int64_t c1, int part, unsigned char* dst,
+                                                int p) {
+  constexpr int NJ = C / (8 * NP);  // 8-column groups in a part
+  static_assert(NJ >= 1 && NJ * 8 * NP == C, "columns per part");
+  uint4 va[NJ], vb[NJ];
+#pragma unroll
+  for (int j = 0; j < NJ; ++j) {
+    const int c0 = part * (C / NP) + 8 * j;
+    va[j] = (ra < c1) ? *reinterpret_cast<const uint4*>(src + ra * C + c0) : make_uint4(0, 0, 0, 0);
+    vb[j] = (rb < c1) ? *reinterpret_cast<const uint4*>(src + rb * C + c0) : make_uint4(0, 0, 0, 0);
+  }
+#pragma unroll
+  for (int j = 0; j < NJ; ++j) {
+    const int c0 = part * (C / NP) + 8 * j;
+    const __nv_bfloat16* av = reinterpret_cast<const __nv_bfloat16*>(&va[j]);
+    const __nv_bfloat16* bv = reinterpret_cast<const __nv_bfloat16*>(&vb[j]);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      __nv_bfloat162 pair;
+      pair.x = av[e];
+      pair.y = bv[e];
+      *reinterpret_cast<__nv_bfloat162*>(dst + tc_canon(c0 + e, p >> 3, kTcRows) + (p & 7) * 2) = pair;
+    }
+  }
+}
+
+template <int K, int N>
+__global__ void __launch_bounds__(kTwThreads) k_tc_wgrad(const __nv_bfloat16* __restrict__ dZ,
+                                                         const __nv_bfloat16* __restrict__ X,
+                                                         float* __restrict__ pW, float* __restrict__ pB,
+                                                         int64_t rows, int chunk, unsigned* status) {
+  constexpr bool TR = N < 64;
+  constexpr int M = TR ? K : N;    // rows of the accumulator
+  constexpr int NN = TR ? N : K;   // its columns
+  static_assert(M == 128 && NN % 16 == 0 && NN <= 128, "weight-gradient shape");
+  constexpr int RK = kTcRows;      // batch rows per sub-chunk (the products' K)
+  constexpr uint32_t kCols = (NN < 32) ? 32u : (uint32_t)NN;
+  extern __shared__ unsigned char tw_raw[];
+  __shared__ __align__(8) uint64_t s_mbar;
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_timeout;
+  const uint32_t raw_s = smem_addr(tw_raw);
+  const uint32_t base = (raw_s + 1023u) & ~1023u;
+  unsigned char* sA = tw_raw + (base - raw_s);  // [M][RK]
+  unsigned char* sB = sA + M * RK * 2;          // [NN][RK]
+  unsigned char* sDz = TR ? sB : sA;            // the dZ operand ([N][RK])
+  unsigned char* sX = TR ? sA : sB;             // the X operand ([K][RK])
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&s_mbar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_timeout = 0;
+  }
+  if (w == 0) tc_alloc(&s_tmem, kCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+  const uint32_t mbar = smem_addr(&s_mbar);
+  const uint32_t idesc = tc_idesc(NN);
+  const int64_t c0 = (int64_t)blockIdx.x * chunk;
+  const int64_t c1 = imin64(c0 + chunk, rows);
+  // this thread's pair of batch rows in a sub-chunk and its part of the operand rows
+  const int pr = 2 * (tid & 63), part = tid >> 6;
+  float bsum = 0.0f;
+  uint32_t parity = 0;
+  int sub = 0;
+  for (int64_t r0 = c0; r0 < c1; r0 += RK, ++sub) {
+    __syncthreads();  // the previous sub-chunk's bias reads are done
+    const int64_t ra = r0 + pr, rb = ra + 1;
+    // dZ rows ra, rb -> sDz[n][pr, pr + 1] for n in this thread's half of 0 .. N-1,
+    // then X rows ra, rb -> sX[k][pr, pr + 1]; each operand's loads are issued together
+    if constexpr (N >= 32)
+      tc_scatter_rows<N, 4>(dZ, ra, rb, c1, part, sDz, pr);
+    else if (part < 2)
+      tc_scatter_rows<N, 2>(dZ, ra, rb, c1, part, sDz, pr);
+    if constexpr (K >= 32)
+      tc_scatter_rows<K, 4>(X, ra, rb, c1, part, sX, pr);
+    else if (part < 2)
+      tc_scatter_rows<K, 2>(X, ra, rb, c1, part, sX, pr);
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (tid == 0) {
+#pragma unroll
+      for (int ks = 0; ks < RK / 16; ++ks)
+        tc_mma(tmem, tc_desc(base + ks * 256, RK), tc_desc(base + M * RK * 2 + ks * 256, RK), idesc,
+               (sub > 0 || ks > 0) ? 1u : 0u);
+      tc_commit(mbar);
+    }
+    // bias partial: thread n sums row n of the dZ operand while the products run
+    if (tid < N) {
+#pragma unroll
+      for (int kc = 0; kc < RK / 8; ++kc) {
+        const uint4 v = *reinterpret_cast<const uint4*>(sDz + tc_canon(tid, kc, RK));
+        const __nv_bfloat162* p2v = reinterpret_cast<const __nv_bfloat162*>(&v);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const float2 f = __bfloat1622float2(p2v[j]);
+          bsum += f.x + f.y;
+        }
+      }
+    }
+    const bool done = __all_sync(0xffffffffu, mbar_wait_bounded(mbar, parity));
+    parity ^= 1u;
+    tc_fence_after();
+    if (!done) s_timeout = 1;
+    __syncthreads();
+    if (s_timeout) break;
+  }
+  if (!s_timeout) {
+    if (sub > 0 && w < 4) {
+      // accumulator row m = 32 w + lane, columns 0 .. NN-1
+      const int m = 32 * w + lane;
+      const uint32_t t_row = tmem + ((uint32_t)(32 * w) << 16);
+      float* dst = pW + (int64_t)blockIdx.x * N * K;
+#pragma unroll
+      for (int cc = 0; cc < NN; cc += 16) {
+        uint32_t v[16];
+        tmem_ld_x16(t_row + (uint32_t)cc, v);
+        tmem_wait_ld16(v);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          if (TR)
+            dst[(cc + j) * K + m] = __uint_as_float(v[j]);  // dW[n][k] = D[k][n]
+          else
+            dst[m * K + cc + j] = __uint_as_float(v[j]);
+        }
+      }
+    } else if (sub == 0) {
+      for (int i = tid; i < N * K; i += kTwThreads) pW[(int64_t)blockIdx.x * N * K + i] = 0.0f;
+    }
+    if (tid < N) pB[(int64_t)blockIdx.x * N + tid] = bsum;
+  } else if (tid == 0) {
+    mbar_wait_bounded(mbar, parity ^ 1u);
+    if (status) atomicOr(status, ST_TIMEOUT);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (w == 0) {
+    tc_fence_after();
+    tc_dealloc(tmem, kCols);
+  }
+}
+
+// --------------------------------------------------------------------------
 // warp-specialised tcgen05 inference: a pipeline of three 128-row tiles
 // --------------------------------------------------------------------------
 // Roles per CTA (one CTA per SM, 21 warps):
@@ -1427,6 +1775,7 @@ struct adot_mlp {
   double graph_lr;
   int64_t graph_steps;
   int engine;          // fused inference: 0 = tcgen05 pipeline (default), 1 = mma.sync, 2 = tcgen05 two groups
+  int train_engine;    // per-layer training kernels: 0 = tcgen05, 1 = mma.sync (default)
   int inject;          // adot_mlp_inject_fault: 1 = the next pipelined launch withholds a commit
   unsigned* d_status;  // sticky ST_* bits of the fused inference kernels
 };
@@ -1445,6 +1794,17 @@ cudaError_t layer_attr() {
                               (int)layer_smem<K, N>());
 }
 
+template <int K, int N, int EPI>
+cudaError_t tc_layer_attr() {
+  return cudaFuncSetAttribute(k_tc_layer<K, N, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)tc_layer_smem<K, N>());
+}
+template <int K, int N>
+cudaError_t tc_wgrad_attr() {
+  return cudaFuncSetAttribute(k_tc_wgrad<K, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)tc_wgrad_smem<K, N>());
+}
+
 // Dynamic shared memory limits of every layer kernel (set before any capture).
 cudaError_t set_layer_attributes() {
   cudaError_t e = layer_attr<16, 128, EPI_GELU>();
@@ -1452,6 +1812,14 @@ cudaError_t set_layer_attributes() {
   if (e == cudaSuccess) e = layer_attr<128, 16, EPI_LINEAR>();
   if (e == cudaSuccess) e = layer_attr<16, 128, EPI_BWD>();
   if (e == cudaSuccess) e = layer_attr<128, 128, EPI_BWD>();
+  if (e == cudaSuccess) e = tc_layer_attr<16, 128, EPI_GELU>();
+  if (e == cudaSuccess) e = tc_layer_attr<128, 128, EPI_GELU>();
+  if (e == cudaSuccess) e = tc_layer_attr<128, 16, EPI_LINEAR>();
+  if (e == cudaSuccess) e = tc_layer_attr<16, 128, EPI_BWD>();
+  if (e == cudaSuccess) e = tc_layer_attr<128, 128, EPI_BWD>();
+  if (e == cudaSuccess) e = tc_wgrad_attr<128, 16>();
+  if (e == cudaSuccess) e = tc_wgrad_attr<128, 128>();
+  if (e == cudaSuccess) e = tc_wgrad_attr<16, 128>();
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_mlp_edges, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)infer_smem_bytes());
@@ -1469,14 +1837,33 @@ cudaError_t set_layer_attributes() {
   return e;
 }
 
+// One layer product with its epilogue: tcgen05 (k_tc_layer, 128-row tiles) or
+// mma.sync (k_layer, 64-row tiles) after the network's training engine.
 template <int K, int N, int EPI>
-cudaError_t layer(const __nv_bfloat16* A, const __nv_bfloat16* S, const float* bias,
+cudaError_t layer(const adot_mlp* m, const __nv_bfloat16* A, const __nv_bfloat16* S, const float* bias,
                   const __nv_bfloat16* aux, void* out0, __nv_bfloat16* out1, int64_t rows,
                   cudaStream_t s) {
+  if (m->train_engine == 0) {
+    const int64_t g = (rows + kTcRows - 1) / kTcRows * (N / tc_layer_ns(N));  // one unit per CTA
+    k_tc_layer<K, N, EPI><<<(unsigned)g, kTlThreads, tc_layer_smem<K, N>(), s>>>(A, S, bias, aux, out0,
+                                                                                out1, rows, m->d_status);
+    return cudaGetLastError();
+  }
   constexpr size_t sm = layer_smem<K, N>();
   const int64_t g = (rows + kTileRows - 1) / kTileRows;
   k_layer<K, N, EPI><<<(unsigned)g, 256, sm, s>>>(A, S, bias, aux, out0, out1, rows);
   return cudaGetLastError();
+}
+
+// Weight-gradient partials of one layer, one block per `chunk` batch rows.
+template <int K, int N>
+void wgrad(const adot_mlp* m, const __nv_bfloat16* dZ, const __nv_bfloat16* X, float* pW, float* pB,
+           int64_t rows, int nch, cudaStream_t s) {
+  if (m->train_engine == 0)
+    k_tc_wgrad<K, N><<<nch, kTwThreads, tc_wgrad_smem<K, N>(), s>>>(dZ, X, pW, pB, rows, m->chunk,
+                                                                     m->d_status);
+  else
+    k_wgrad<K, N><<<nch, 256, 0, s>>>(dZ, X, pW, pB, rows, m->chunk);
 }
 
 const __nv_bfloat16* Wl(const adot_mlp* m, int l) { return m->d.W + w_offset(l); }
@@ -1485,11 +1872,13 @@ const float* bl(const adot_mlp* m, int l) { return m->d.master + kWTotal + b_off
 
 cudaError_t forward_batch(adot_mlp* m, int64_t B, cudaStream_t s) {
   cudaError_t e;
-  if ((e = layer<16, 128, EPI_GELU>(m->Xb, Wl(m, 0), bl(m, 0), nullptr, m->Z[0], m->H[0], B, s))) return e;
+  if ((e = layer<16, 128, EPI_GELU>(m, m->Xb, Wl(m, 0), bl(m, 0), nullptr, m->Z[0], m->H[0], B, s)))
+    return e;
   for (int l = 1; l < 4; ++l)
-    if ((e = layer<128, 128, EPI_GELU>(m->H[l - 1], Wl(m, l), bl(m, l), nullptr, m->Z[l], m->H[l], B, s)))
+    if ((e = layer<128, 128, EPI_GELU>(m, m->H[l - 1], Wl(m, l), bl(m, l), nullptr, m->Z[l], m->H[l], B,
+                                       s)))
       return e;
-  return layer<128, 16, EPI_LINEAR>(m->H[3], Wl(m, 4), bl(m, 4), nullptr, m->Y, nullptr, B, s);
+  return layer<128, 16, EPI_LINEAR>(m, m->H[3], Wl(m, 4), bl(m, 4), nullptr, m->Y, nullptr, B, s);
 }
 
 cudaError_t backward_batch(adot_mlp* m, int64_t B, cudaStream_t s) {
@@ -1497,15 +1886,16 @@ cudaError_t backward_batch(adot_mlp* m, int64_t B, cudaStream_t s) {
   const int lg = (int)((B + 255) / 256);
   k_loss<<<lg, 256, 0, s>>>(m->Y, m->Tb, B, m->dY, m->loss_part);
   if ((e = cudaGetLastError())) return e;
-  if ((e = layer<16, 128, EPI_BWD>(m->dY, Wtl(m, 4), nullptr, m->Z[3], m->dZ[3], nullptr, B, s))) return e;
+  if ((e = layer<16, 128, EPI_BWD>(m, m->dY, Wtl(m, 4), nullptr, m->Z[3], m->dZ[3], nullptr, B, s)))
+    return e;
   for (int l = 3; l >= 1; --l)
-    if ((e = layer<128, 128, EPI_BWD>(m->dZ[l], Wtl(m, l), nullptr, m->Z[l - 1], m->dZ[l - 1], nullptr, B, s)))
+    if ((e = layer<128, 128, EPI_BWD>(m, m->dZ[l], Wtl(m, l), nullptr, m->Z[l - 1], m->dZ[l - 1], nullptr,
+                                      B, s)))
       return e;
   const int nch = (int)((B + m->chunk - 1) / m->chunk);
-  k_wgrad<128, 16><<<nch, 256, 0, s>>>(m->dY, m->H[3], m->pW[4], m->pB[4], B, m->chunk);
-  for (int l = 3; l >= 1; --l)
-    k_wgrad<128, 128><<<nch, 256, 0, s>>>(m->dZ[l], m->H[l - 1], m->pW[l], m->pB[l], B, m->chunk);
-  k_wgrad<16, 128><<<nch, 256, 0, s>>>(m->dZ[0], m->Xb, m->pW[0], m->pB[0], B, m->chunk);
+  wgrad<128, 16>(m, m->dY, m->H[3], m->pW[4], m->pB[4], B, nch, s);
+  for (int l = 3; l >= 1; --l) wgrad<128, 128>(m, m->dZ[l], m->H[l - 1], m->pW[l], m->pB[l], B, nch, s);
+  wgrad<16, 128>(m, m->dZ[0], m->Xb, m->pW[0], m->pB[0], B, nch, s);
   return cudaGetLastError();
 }
 
@@ -1629,6 +2019,7 @@ adot_status adot_mlp_create(int64_t max_batch, void* cuda_stream, adot_mlp** out
   if (!out || max_batch < 1 || max_batch > (1ll << 26)) return ADOT_E_INVALID_ARG;
   *out = nullptr;
   adot_mlp* m = new adot_mlp();
+  m->train_engine = 1;
   memset(m, 0, sizeof(adot_mlp));
   cudaGetDevice(&m->device);
   m->max_batch = ((max_batch + 63) / 64) * 64;
@@ -1709,6 +2100,17 @@ adot_status adot_mlp_set_engine(adot_mlp* m, int engine) {
   return ADOT_OK;
 }
 
+adot_status adot_mlp_set_train_engine(adot_mlp* m, int engine) {
+  if (!m || engine < 0 || engine > 1) return ADOT_E_INVALID_ARG;
+  if (engine != m->train_engine) {
+    CKM(cudaStreamSynchronize(m->stream));
+    if (m->graph_ready) cudaGraphExecDestroy(m->graph);  // the training graph holds the old kernels
+    m->graph_ready = false;
+    m->train_engine = engine;
+  }
+  return ADOT_OK;
+}
+
 adot_status adot_mlp_set_params(adot_mlp* m, const float* packed) {
   if (!m || !packed) return ADOT_E_INVALID_ARG;
   std::vector<float> padded;
@@ -1782,6 +2184,7 @@ adot_status adot_mlp_forward(adot_mlp* m, const float* Xs, int64_t n, float* Y, 
   if (!m || !Xs || !Y || n < 1 || n > m->max_batch) return ADOT_E_INVALID_ARG;
   adot_status st = upload_batch(m, Xs, nullptr, n);
   if (st) return st;
+  CKM(cudaMemsetAsync(m->d_status, 0, sizeof(unsigned), m->stream));
   if (fused == 2 || fused == 3) {
     InferParams P{};
     P.W = m->d.W;
@@ -1791,7 +2194,6 @@ adot_status adot_mlp_forward(adot_mlp* m, const float* Xs, int64_t n, float* Y, 
     const int64_t tiles = (n + kTcRows - 1) / kTcRows;
     int sms = 152;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device);
-    CKM(cudaMemsetAsync(m->d_status, 0, sizeof(unsigned), m->stream));
     if (fused == 2) {
       k_mlp_tc<false><<<(unsigned)imin64((tiles + 1) / 2, sms), kTcThreads, kTcSmem, m->stream>>>(
           P, sp, StateF32{}, 0, nullptr, nullptr, m->Xb, n, m->Y, m->d_status);
@@ -1827,6 +2229,7 @@ adot_status adot_mlp_gradient(adot_mlp* m, const float* Xs, const float* Ts, int
   if (!m || !Xs || !Ts || n < 1 || n > m->max_batch) return ADOT_E_INVALID_ARG;
   adot_status st = upload_batch(m, Xs, Ts, n);
   if (st) return st;
+  CKM(cudaMemsetAsync(m->d_status, 0, sizeof(unsigned), m->stream));
   CKM(forward_batch(m, n, m->stream));
   CKM(backward_batch(m, n, m->stream));
   k_adam<<<(kWTotal + kBTotal + 255) / 256, 256, 0, m->stream>>>(m->d, adam_args(m, n), 0.0f, 0, 0.9f,
@@ -1838,7 +2241,10 @@ adot_status adot_mlp_gradient(adot_mlp* m, const float* Xs, const float* Ts, int
   CKM(cudaMemcpyAsync(part.data(), m->loss_part, sizeof(float) * lg, cudaMemcpyDeviceToHost, m->stream));
   CKM(cudaMemcpyAsync(padded.data(), m->d.grad, sizeof(float) * padded.size(), cudaMemcpyDeviceToHost,
                       m->stream));
+  unsigned dev_status = 0;
+  CKM(cudaMemcpyAsync(&dev_status, m->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, m->stream));
   CKM(cudaStreamSynchronize(m->stream));
+  if (dev_status & ST_TIMEOUT) return ADOT_E_TIMEOUT;
   double ls = 0.0;
   for (float v : part) ls += v;
   if (loss_out) *loss_out = (float)(ls / ((double)n * kOut));
@@ -1900,8 +2306,12 @@ adot_status adot_mlp_train(adot_mlp* m, int64_t steps, int64_t batch, double lr,
     m->graph_lr = lr;
     m->graph_steps = step0 + steps;
   }
+  CKM(cudaMemsetAsync(m->d_status, 0, sizeof(unsigned), m->stream));
   for (int64_t k = 0; k < steps; ++k) CKM(cudaGraphLaunch(m->graph, m->stream));
+  unsigned dev_status = 0;
+  CKM(cudaMemcpyAsync(&dev_status, m->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, m->stream));
   CKM(cudaStreamSynchronize(m->stream));
+  if (dev_status & ST_TIMEOUT) return ADOT_E_TIMEOUT;
   if (loss_hist && steps > 0) {
     std::vector<float> h(m->hist_cap);
     CKM(cudaMemcpy(h.data(), m->loss_hist, sizeof(float) * m->hist_cap, cudaMemcpyDeviceToHost));

@@ -115,6 +115,7 @@ def test_null_arguments_rejected(L):
     assert L.adot_checkpoint_save(None, None, 0, 0) == adot.E_INVALID_ARG
     assert L.adot_checkpoint_load(None, None, 0, 0) == adot.E_INVALID_ARG
     assert L.adot_mlp_set_engine(None, 0) == adot.E_INVALID_ARG
+    assert L.adot_mlp_set_train_engine(None, 0) == adot.E_INVALID_ARG
     assert L.adot_mlp_inject_fault(None, 1) == adot.E_INVALID_ARG
     assert L.adot_surrogate_eval(None, None, 0, None) == adot.E_INVALID_ARG
     L.adot_destroy(None)

@@ -27,20 +27,26 @@ def _theta(seed, scale=1.0):
     return np.concatenate(parts).astype(np.float32).astype(np.float64)
 
 
-@pytest.mark.parametrize("n", [1, 63, 64, 1000, 4099])
-def test_forward_matches_reference(gpu, n):
+@pytest.mark.parametrize("train_engine", [0, 1], ids=["tcgen05", "mma_sync"])
+@pytest.mark.parametrize("n", [1, 63, 64, 127, 129, 1000, 4099])
+def test_forward_matches_reference(gpu, n, train_engine):
+    """The per-layer training kernels' forward pass (tcgen05 over 128-row tiles
+    or mma.sync over 64-row tiles); the mma.sync layers and the single-kernel
+    mma.sync inference accumulate alike and agree to 1e-5."""
     theta = _theta(1)
     rng = np.random.default_rng(n)
     X = rng.standard_normal((n, 7)).astype(np.float32)
     ref, _ = M.forward(theta, X.astype(np.float64), bf16=True)
     with gpu.Mlp(8192) as net:
         net.set_params(theta)
+        net.set_train_engine(train_engine)
         y = net.forward(X, fused=False)
         yf = net.forward(X, fused=True)
     sc = np.abs(ref).max()
     err = np.abs(y - ref)
     assert err.max() <= 1e-2 * sc and np.median(err) <= 1e-4 * sc, (err.max(), np.median(err))
-    assert np.abs(yf - y).max() <= 1e-5 * sc
+    if train_engine == 1:
+        assert np.abs(yf - y).max() <= 1e-5 * sc
 
 
 @pytest.mark.parametrize("fused", [2, 3], ids=["two_groups", "pipeline"])
@@ -102,10 +108,13 @@ def test_engine_value_checked(gpu):
             net.set_engine(3)
 
 
-def test_gradient_matches_reference(gpu):
+@pytest.mark.parametrize("train_engine", [0, 1], ids=["tcgen05", "mma_sync"])
+@pytest.mark.parametrize("n", [2048, 1000])
+def test_gradient_matches_reference(gpu, n, train_engine):
+    """Forward, backward and the weight gradients (the batch rows as the
+    reduction dimension; 1000 rows leave ragged 128-row and 512-row chunks)."""
     theta = _theta(2)
     rng = np.random.default_rng(3)
-    n = 2048
     X = rng.standard_normal((n, 7)).astype(np.float32)
     T = rng.standard_normal((n, 9)).astype(np.float32)
     Y, cache = M.forward(theta, X.astype(np.float64), bf16=True)
@@ -113,6 +122,7 @@ def test_gradient_matches_reference(gpu):
     g_ref = M.backward(theta, cache, dY, bf16=True)
     with gpu.Mlp(n) as net:
         net.set_params(theta)
+        net.set_train_engine(train_engine)
         loss, g = net.gradient(X, T)
     assert loss == pytest.approx(loss_ref, rel=1e-3)
     cos = float(g @ g_ref / (np.linalg.norm(g) * np.linalg.norm(g_ref)))
@@ -122,6 +132,28 @@ def test_gradient_matches_reference(gpu):
     Y64, c64 = M.forward(theta, X.astype(np.float64))
     g64 = M.backward(theta, c64, M.mse(Y64, T.astype(np.float64))[1])
     assert float(g @ g64 / (np.linalg.norm(g) * np.linalg.norm(g64))) > 0.99
+
+
+def test_train_engines_agree(gpu):
+    """tcgen05 and mma.sync training kernels on the same batch: the same bf16
+    operands, float32 accumulation in another order."""
+    theta = _theta(5)
+    rng = np.random.default_rng(9)
+    n = 4096
+    X = rng.standard_normal((n, 7)).astype(np.float32)
+    T = rng.standard_normal((n, 9)).astype(np.float32)
+    out = []
+    with gpu.Mlp(n) as net:
+        for e in (0, 1):
+            net.set_params(theta)
+            net.set_train_engine(e)
+            out.append(net.gradient(X, T))
+        with pytest.raises(gpu.AdotError):
+            net.set_train_engine(2)
+    (l0, g0), (l1, g1) = out
+    assert l0 == pytest.approx(l1, rel=1e-3)
+    assert float(g0 @ g1 / (np.linalg.norm(g0) * np.linalg.norm(g1))) > 0.9999
+    assert float(np.linalg.norm(g0 - g1) / np.linalg.norm(g1)) < 1e-2
 
 
 def test_params_roundtrip_and_padding(gpu):
@@ -142,9 +174,11 @@ def _edge_dataset(n, seed):
     return X.astype(np.float32), T.astype(np.float32)
 
 
-def test_training_reduces_loss(gpu):
+@pytest.mark.parametrize("train_engine", [0, 1], ids=["tcgen05", "mma_sync"])
+def test_training_reduces_loss(gpu, train_engine):
     X, T = _edge_dataset(3000, 5)
     with gpu.Mlp(1024) as net:
+        net.set_train_engine(train_engine)
         net.set_params(_theta(6, 0.5))
         net.set_data(X, T)
         st, box = net.stats()
