@@ -54,6 +54,27 @@ def test_resume_is_bit_exact(gpu, P, prec, k1, k2):
 
 
 @pytest.mark.parametrize("prec", ["FP32", "FP64"])
+def test_resume_is_bit_exact_with_friction_and_feed(gpu, prec):
+    """The Soni case (the step kernels with the friction source, the sediment
+    feed and the slope-continuing ghosts compiled in)."""
+    P = W.soni_aggradation()
+    cfg = gpu.config_for(P, getattr(gpu, prec), law=gpu.LAW_POWER, beta=5.0, ks=49.4)
+    with gpu.Solver(cfg) as a:
+        a.set_state(P.h, P.q, P.z)
+        a.step(53)
+        blob = a.checkpoint()
+        a.step(101)
+        ref = a.get_state(), a.query()
+    with gpu.Solver(cfg) as b:
+        b.restore(blob)
+        b.step(101)
+        got = b.get_state(), b.query()
+    assert got[1] == ref[1]
+    for x, y in zip(got[0], ref[0]):
+        assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("prec", ["FP32", "FP64"])
 def test_device_blob_and_rewind_in_place(gpu, prec):
     torch = pytest.importorskip("torch")
     P = W.smooth_periodic(2049)

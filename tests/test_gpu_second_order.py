@@ -8,6 +8,8 @@ variable's scale and the same step count; FP32 (float-float state, float32
 arithmetic) the increment W^K - W^0 within 1e-5 in L1 relative (smooth flow)
 or 1e-4 (flows with jumps, where minmod switches on rounding-level
 differences of the slopes)."""
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -87,6 +89,20 @@ def test_small_and_ragged_grids_with_ghosts(gpu, n):
     ref = _oracle(P, max_steps=25)
     got = _gpu(gpu, P, 0, steps=25)
     _check(0, got, ref, P)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_sloping_flume_with_continued_bed(gpu, prec):
+    """The slope-continuing outflow ghost (OUTFLOW_HS) and the power law of
+    Eq. Soni_qs with the second-order variant: the Soni flume without friction,
+    inflow q at the left end."""
+    S = W.soni_aggradation(n=200)
+    P = dataclasses.replace(S, bc_left=W.BC_INFLOW_Q)
+    law = O.power(P.Ag, 5.0, xi=P.xi, g=P.g)
+    cfg = O.make_cfg(P.n, P.x_min, P.x_max, P.cfl, law, P.bc_left, P.bc_right, P.bcl, P.bcr, order=2)
+    ref = O.run(cfg, P.h, P.q, P.z, max_steps=150)
+    got = _gpu(gpu, P, prec, steps=150, law=gpu.LAW_POWER, beta=5.0)
+    _check(prec, got, ref, P, 1e-4)
 
 
 @pytest.mark.parametrize("block,cap", WARP_VARIANTS)

@@ -43,6 +43,29 @@ def test_noalloc_matches_context_path_on_two_calls(gpu, make):
             assert np.abs(a - b).max() <= 1e-12 * max(np.abs(b).max(), 1e-300)
 
 
+@pytest.mark.parametrize("kind", ["second_order", "soni"])
+def test_noalloc_second_order_and_friction(gpu, kind):
+    """The second-order variant (warp tiles) and the Soni case (friction,
+    sediment feed, power law: the extended step kernels) through the same
+    entry point."""
+    torch = pytest.importorskip("torch")
+    if kind == "second_order":
+        P, kw = W.movable_bed_riemann(300), {"order": 2}
+    else:
+        P, kw = W.soni_aggradation(), {"law": gpu.LAW_POWER, "beta": 5.0, "ks": 49.4}
+    h, q, z = (torch.tensor(a, device="cuda") for a in (P.h, P.q, P.z))
+    t = gpu.adot_step_noalloc(gpu.config_for(P, gpu.FP64, **kw), h, q, z, 20, 0.0,
+                              torch.cuda.current_stream())
+    with gpu.Solver(gpu.config_for(P, gpu.FP64, block_threads=256, reg_cap=64, **kw)) as s:
+        s.set_state(P.h, P.q, P.z)
+        s.step(20)
+        t_ref, _, _ = s.query()
+        ref = s.get_state()
+    assert t == pytest.approx(t_ref, rel=1e-13)
+    for a, b in zip((h, q, z), ref):
+        assert np.abs(a.cpu().numpy() - b).max() <= 1e-12 * np.abs(b).max()
+
+
 def test_noalloc_rejects_what_it_cannot_do(gpu):
     torch = pytest.importorskip("torch")
     P = W.smooth_periodic(64)
