@@ -292,14 +292,14 @@ adot_status adot_mlp_get_params(adot_mlp* mlp, float* params);
  * three-tile pipeline (default); 1 = mma.sync; 2 = tcgen05, two independent
  * tile groups per CTA. ADOT_E_INVALID_ARG for another value. */
 adot_status adot_mlp_set_engine(adot_mlp* mlp, int engine);
-/* Engine of the per-layer training kernels (forward and backward layer
- * products, weight gradients; adot_mlp_train, adot_mlp_gradient and
+/* Engine of the training kernels (adot_mlp_train, adot_mlp_gradient and
  * adot_mlp_forward with fused = 0): 0 = tcgen05.mma with tensor-memory
- * accumulators (128-row x 64-column units for the layers, the batch rows as the
- * reduction dimension for the weight gradients); 1 = mma.sync over 64-row tiles
- * (default: at batch 65536 the per-layer step is bound by latency and memory
- * traffic, not by the tensor pipes, and this engine measures faster). Both take
- * bf16 operands and accumulate in float32. ADOT_E_INVALID_ARG for another
+ * accumulators (default): the forward pass in the fused two-group kernel
+ * (fused = 2), which also stores every hidden layer's pre-activation and
+ * activation, the backward layer products in 128-row x 64-column units, the
+ * weight gradients with the batch rows as the reduction dimension; 1 =
+ * mma.sync, one kernel per layer over 64-row tiles, GELU through tanhf. Both
+ * take bf16 operands and accumulate in float32. ADOT_E_INVALID_ARG for another
  * value. A bounded device-side wait that runs out makes the call that launched
  * it return ADOT_E_TIMEOUT. */
 adot_status adot_mlp_set_train_engine(adot_mlp* mlp, int engine);

@@ -460,7 +460,7 @@ class Mlp:
         _check(lib().adot_mlp_set_engine(self.ptr, int(engine)), "adot_mlp_set_engine")
 
     def set_train_engine(self, engine: int) -> None:
-        """Per-layer training kernels: 0 = tcgen05, 1 = mma.sync (default)."""
+        """Training kernels: 0 = tcgen05 (default), 1 = mma.sync."""
         _check(lib().adot_mlp_set_train_engine(self.ptr, int(engine)), "adot_mlp_set_train_engine")
 
     def inject_fault(self, kind: int = 1) -> None:

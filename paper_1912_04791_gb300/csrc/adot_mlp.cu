@@ -291,6 +291,7 @@ __global__ void __launch_bounds__(256) k_adam(MlpDev d, const AdamArgs a, float 
   const int size = is_w ? dim_in(l) * dim_out(l) : dim_out(l);
   const float* src = is_w ? pW[l] : pB[l];
   float gsum = 0.0f;
+#pragma unroll 8
   for (int c = 0; c < nchunk[l]; ++c) gsum += src[(int64_t)c * size + local];
   d.grad[i] = gsum;
   if (!apply) return;
@@ -391,14 +392,17 @@ __global__ void __launch_bounds__(256) k_loss(const float* __restrict__ Y, const
   }
 }
 
-// Loss of the step = sum of block partials / (B * 9), in fixed order.
+// Loss of the step = sum of block partials / (B * 9), in a fixed order: one
+// warp, lane l summing partials l, l + 32, ..., then a fixed shuffle tree.
 __global__ void k_loss_sum(const float* part, int nparts, int64_t B, const long long* step,
                            float* hist, int64_t hist_len) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (threadIdx.x >= 32 || blockIdx.x != 0) return;
   double s = 0.0;
-  for (int i = 0; i < nparts; ++i) s += part[i];
+  for (int i = threadIdx.x; i < nparts; i += 32) s += part[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   const long long k = *step;
-  if (k >= 0 && k < hist_len) hist[k] = (float)(s / ((double)B * kOut));
+  if (threadIdx.x == 0 && k >= 0 && k < hist_len) hist[k] = (float)(s / ((double)B * kOut));
 }
 
 // Dataset statistics: per-column mean and standard deviation of X (7) and T (9).
@@ -454,6 +458,8 @@ struct InferParams {
   float fr_lo, fr_hi;      // Froude band that falls back
   float Ag;
   int withhold_commit;     // test hook: CTA 0 withholds its first accumulator commit
+  __nv_bfloat16* trZ[kLayers - 1];  // training forward: pre-activations of the hidden layers
+  __nv_bfloat16* trH[kLayers - 1];  // and their GELU, [rows][128] bf16
 };
 
 __host__ __device__ constexpr size_t infer_smem_bytes() {
@@ -819,8 +825,11 @@ __device__ __forceinline__ uint32_t gelu2x_bf16(uint32_t a0, uint32_t a1, uint32
 
 // EDGES: inputs from the edges of a float-float state, outputs |A|_Psi into
 // absA [9][n+1] (NaN in row 0 marks a fallback edge). Otherwise: inputs are
-// rows of X [n][16] bf16 (standardised), outputs Y [n][16] float32.
-template <bool EDGES>
+// rows of X [n][16] bf16 (standardised), outputs Y [n][16] float32; with TRAIN
+// the hidden layers' pre-activations z = acc + b and activations GELU(z) also
+// go to P.trZ / P.trH (bf16, [n][128]) for the backward pass of training (the
+// stored activation 2 GELU(z) halved, an exact scaling).
+template <bool EDGES, bool TRAIN = false>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_mlp_tc(const InferParams P, const StepParams sp, const StateF32 st, int slot,
              float* __restrict__ absA, unsigned long long* fallback_count,
@@ -962,6 +971,30 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           for (int u = 0; u < 4; ++u)
             *reinterpret_cast<uint4*>(act + tc_canon(row, c / 8 + u, kHid)) =
                 make_uint4(pk[4 * u], pk[4 * u + 1], pk[4 * u + 2], pk[4 * u + 3]);
+          if (TRAIN && item < n_items) {
+            const __nv_bfloat162 halfv = __floats2bfloat162_rn(0.5f, 0.5f);
+            uint32_t zk[16], hk[16];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              const float4 bb = *reinterpret_cast<const float4*>(b + 32 * half + 4 * j);
+              zk[2 * j] = pack_bf16(__uint_as_float(r[4 * j]) + bb.x, __uint_as_float(r[4 * j + 1]) + bb.y);
+              zk[2 * j + 1] =
+                  pack_bf16(__uint_as_float(r[4 * j + 2]) + bb.z, __uint_as_float(r[4 * j + 3]) + bb.w);
+#pragma unroll
+              for (int e = 0; e < 2; ++e) {
+                __nv_bfloat162 g = *reinterpret_cast<const __nv_bfloat162*>(&pk[2 * j + e]);
+                g = __hmul2(g, halfv);
+                hk[2 * j + e] = *reinterpret_cast<const uint32_t*>(&g);
+              }
+            }
+            uint4* zd = reinterpret_cast<uint4*>(P.trZ[l] + item * kHid + c);
+            uint4* hd = reinterpret_cast<uint4*>(P.trH[l] + item * kHid + c);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              zd[u] = make_uint4(zk[4 * u], zk[4 * u + 1], zk[4 * u + 2], zk[4 * u + 3]);
+              hd[u] = make_uint4(hk[4 * u], hk[4 * u + 1], hk[4 * u + 2], hk[4 * u + 3]);
+            }
+          }
         }
       } else if (done && lead) {
         // output layer: 16 columns (9 used)
@@ -1775,7 +1808,7 @@ struct adot_mlp {
   double graph_lr;
   int64_t graph_steps;
   int engine;          // fused inference: 0 = tcgen05 pipeline (default), 1 = mma.sync, 2 = tcgen05 two groups
-  int train_engine;    // per-layer training kernels: 0 = tcgen05, 1 = mma.sync (default)
+  int train_engine;    // training kernels: 0 = tcgen05 (default), 1 = mma.sync
   int inject;          // adot_mlp_inject_fault: 1 = the next pipelined launch withholds a commit
   unsigned* d_status;  // sticky ST_* bits of the fused inference kernels
 };
@@ -1831,6 +1864,9 @@ cudaError_t set_layer_attributes() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_mlp_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
   if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_mlp_tc<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kTcSmem);
+  if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_mlp_tcp<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTpSmem);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_mlp_tcp<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTpSmem);
@@ -1871,6 +1907,25 @@ const __nv_bfloat16* Wtl(const adot_mlp* m, int l) { return m->d.Wt + w_offset(l
 const float* bl(const adot_mlp* m, int l) { return m->d.master + kWTotal + b_offset(l); }
 
 cudaError_t forward_batch(adot_mlp* m, int64_t B, cudaStream_t s) {
+  if (m->train_engine == 0) {
+    // tcgen05: the whole forward pass in the fused two-group kernel, which also
+    // writes the hidden layers' Z and H for the backward pass
+    InferParams P{};
+    P.W = m->d.W;
+    P.bias = m->d.master + kWTotal;
+    P.stats = m->d_ident;
+    for (int l = 0; l < kLayers - 1; ++l) {
+      P.trZ[l] = m->Z[l];
+      P.trH[l] = m->H[l];
+    }
+    StepParams sp{};
+    int sms = 152;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device);
+    const int64_t tiles = (B + kTcRows - 1) / kTcRows;
+    k_mlp_tc<false, true><<<(unsigned)imin64((tiles + 1) / 2, sms), kTcThreads, kTcSmem, s>>>(
+        P, sp, StateF32{}, 0, nullptr, nullptr, m->Xb, B, m->Y, m->d_status);
+    return cudaGetLastError();
+  }
   cudaError_t e;
   if ((e = layer<16, 128, EPI_GELU>(m, m->Xb, Wl(m, 0), bl(m, 0), nullptr, m->Z[0], m->H[0], B, s)))
     return e;
@@ -2019,7 +2074,6 @@ adot_status adot_mlp_create(int64_t max_batch, void* cuda_stream, adot_mlp** out
   if (!out || max_batch < 1 || max_batch > (1ll << 26)) return ADOT_E_INVALID_ARG;
   *out = nullptr;
   adot_mlp* m = new adot_mlp();
-  m->train_engine = 1;
   memset(m, 0, sizeof(adot_mlp));
   cudaGetDevice(&m->device);
   m->max_batch = ((max_batch + 63) / 64) * 64;

@@ -30,9 +30,11 @@ def _theta(seed, scale=1.0):
 @pytest.mark.parametrize("train_engine", [0, 1], ids=["tcgen05", "mma_sync"])
 @pytest.mark.parametrize("n", [1, 63, 64, 127, 129, 1000, 4099])
 def test_forward_matches_reference(gpu, n, train_engine):
-    """The per-layer training kernels' forward pass (tcgen05 over 128-row tiles
-    or mma.sync over 64-row tiles); the mma.sync layers and the single-kernel
-    mma.sync inference accumulate alike and agree to 1e-5."""
+    """The training forward pass: on tcgen05 the fused two-group kernel, which
+    also stores every hidden layer's Z and H, bit-identical to its inference
+    use (fused = 2; tanh.approx GELU, so the median bound of the tcgen05
+    inference test); on mma.sync the per-layer kernels, which accumulate like
+    the single-kernel mma.sync inference and agree with it to 1e-5."""
     theta = _theta(1)
     rng = np.random.default_rng(n)
     X = rng.standard_normal((n, 7)).astype(np.float32)
@@ -42,11 +44,17 @@ def test_forward_matches_reference(gpu, n, train_engine):
         net.set_train_engine(train_engine)
         y = net.forward(X, fused=False)
         yf = net.forward(X, fused=True)
+        y2 = net.forward(X, fused=2)
     sc = np.abs(ref).max()
     err = np.abs(y - ref)
-    assert err.max() <= 1e-2 * sc and np.median(err) <= 1e-4 * sc, (err.max(), np.median(err))
+    med = 1e-4 if train_engine == 1 else 2e-4
+    assert err.max() <= 1e-2 * sc, err.max()
+    if n >= 64:  # a median over fewer than 576 outputs says little
+        assert np.median(err) <= med * sc, np.median(err)
     if train_engine == 1:
         assert np.abs(yf - y).max() <= 1e-5 * sc
+    else:
+        assert np.array_equal(y, y2)
 
 
 @pytest.mark.parametrize("fused", [2, 3], ids=["two_groups", "pipeline"])
@@ -135,8 +143,10 @@ def test_gradient_matches_reference(gpu, n, train_engine):
 
 
 def test_train_engines_agree(gpu):
-    """tcgen05 and mma.sync training kernels on the same batch: the same bf16
-    operands, float32 accumulation in another order."""
+    """tcgen05 and mma.sync training on the same batch: bf16 operands, float32
+    accumulation in another order, and the tcgen05 forward's GELU through
+    tanh.approx (a bf16 rounding flips in a few per cent of activations), so
+    the bounds against the reference apply between the engines too."""
     theta = _theta(5)
     rng = np.random.default_rng(9)
     n = 4096
@@ -152,8 +162,8 @@ def test_train_engines_agree(gpu):
             net.set_train_engine(2)
     (l0, g0), (l1, g1) = out
     assert l0 == pytest.approx(l1, rel=1e-3)
-    assert float(g0 @ g1 / (np.linalg.norm(g0) * np.linalg.norm(g1))) > 0.9999
-    assert float(np.linalg.norm(g0 - g1) / np.linalg.norm(g1)) < 1e-2
+    assert float(g0 @ g1 / (np.linalg.norm(g0) * np.linalg.norm(g1))) > 0.999
+    assert float(np.linalg.norm(g0 - g1) / np.linalg.norm(g1)) < 2e-2
 
 
 def test_params_roundtrip_and_padding(gpu):
