@@ -1055,11 +1055,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 // --------------------------------------------------------------------------
 // training on the 5th-generation tensor cores
 // --------------------------------------------------------------------------
-// k_tc_layer: the products of k_layer, C = A S^T (+ bias) with the same
-// epilogues, on the 5th-generation tensor cores. A CTA of 8 warps computes one
-// unit of NS output columns of a 128-row tile (NS = 64 for the 128-wide layers,
-// so that four CTAs share an SM and the 1024 units of a 65536-row batch leave a
-// short tail): S rows n0 .. n0+NS-1 and the A tile [128][K] (row-major bf16) are
+// k_tc_layer: the backward layer products of k_layer (EPI_BWD), dZprev =
+// (A S^T) * gelu'(Zprev) with A = dZ and S = W^T, on the 5th-generation tensor
+// cores (the tcgen05 engine's forward pass is the fused k_mlp_tc). A CTA of 8
+// warps computes one unit of NS = 64 output columns of a 128-row tile (so that
+// four CTAs share an SM and the 1024 units of a 65536-row batch leave a short
+// tail): S rows n0 .. n0+NS-1 and the A tile [128][K] (row-major bf16) are
 // copied with cp.async into the K-major core-matrix layout of tc_canon (rows
 // past the end zero-filled); thread 0 issues K/16 tcgen05.mma of kind::f16 into
 // NS tensor-memory columns and commits to an mbarrier; warp w reads lane
@@ -1099,60 +1100,34 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\n cp.async.wait_group 0;" ::: "memory");
 }
 
-// Epilogue of 16 accumulator columns c0 .. c0+15 of one row.
-template <int N, int EPI>
-__device__ __forceinline__ void tc_layer_epi16(const uint32_t* v, int c0, int64_t row,
-                                               const float* __restrict__ bias,
-                                               const __nv_bfloat16* __restrict__ aux, void* out0,
-                                               __nv_bfloat16* __restrict__ out1) {
-  if (EPI == EPI_GELU) {
-    uint32_t z[8], hh[8];
+// Backward epilogue of 16 accumulator columns c0 .. c0+15 of one row:
+// dZprev = C * gelu'(Zprev) (bf16), as k_layer's EPI_BWD.
+template <int N>
+__device__ __forceinline__ void tc_layer_bwd16(const uint32_t* v, int c0, int64_t row,
+                                               const __nv_bfloat16* __restrict__ aux,
+                                               __nv_bfloat16* __restrict__ out) {
+  const uint4* zs = reinterpret_cast<const uint4*>(aux + row * N + c0);
+  const uint4 za = zs[0], zb = zs[1];
+  const uint32_t zw[8] = {za.x, za.y, za.z, za.w, zb.x, zb.y, zb.z, zb.w};
+  uint32_t o[8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const float a0 = __uint_as_float(v[2 * j]) + bias[c0 + 2 * j];
-      const float a1 = __uint_as_float(v[2 * j + 1]) + bias[c0 + 2 * j + 1];
-      z[j] = pack_bf16(a0, a1);
-      hh[j] = pack_bf16(gelu_f(a0), gelu_f(a1));
-    }
-    uint4* zd = reinterpret_cast<uint4*>((__nv_bfloat16*)out0 + row * N + c0);
-    uint4* hd = reinterpret_cast<uint4*>(out1 + row * N + c0);
-    zd[0] = make_uint4(z[0], z[1], z[2], z[3]);
-    zd[1] = make_uint4(z[4], z[5], z[6], z[7]);
-    hd[0] = make_uint4(hh[0], hh[1], hh[2], hh[3]);
-    hd[1] = make_uint4(hh[4], hh[5], hh[6], hh[7]);
-  } else if (EPI == EPI_LINEAR) {
-    float4* yd = reinterpret_cast<float4*>((float*)out0 + row * N + c0);
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-      yd[j] = make_float4(__uint_as_float(v[4 * j]) + bias[c0 + 4 * j],
-                          __uint_as_float(v[4 * j + 1]) + bias[c0 + 4 * j + 1],
-                          __uint_as_float(v[4 * j + 2]) + bias[c0 + 4 * j + 2],
-                          __uint_as_float(v[4 * j + 3]) + bias[c0 + 4 * j + 3]);
-  } else {
-    const uint4* zs = reinterpret_cast<const uint4*>(aux + row * N + c0);
-    const uint4 za = zs[0], zb = zs[1];
-    const uint32_t zw[8] = {za.x, za.y, za.z, za.w, zb.x, zb.y, zb.z, zb.w};
-    uint32_t o[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const __nv_bfloat162 zz = *reinterpret_cast<const __nv_bfloat162*>(&zw[j]);
-      o[j] = pack_bf16(__uint_as_float(v[2 * j]) * gelu_prime_f(__bfloat162float(zz.x)),
-                       __uint_as_float(v[2 * j + 1]) * gelu_prime_f(__bfloat162float(zz.y)));
-    }
-    uint4* od = reinterpret_cast<uint4*>((__nv_bfloat16*)out0 + row * N + c0);
-    od[0] = make_uint4(o[0], o[1], o[2], o[3]);
-    od[1] = make_uint4(o[4], o[5], o[6], o[7]);
+  for (int j = 0; j < 8; ++j) {
+    const __nv_bfloat162 zz = *reinterpret_cast<const __nv_bfloat162*>(&zw[j]);
+    o[j] = pack_bf16(__uint_as_float(v[2 * j]) * gelu_prime_f(__bfloat162float(zz.x)),
+                     __uint_as_float(v[2 * j + 1]) * gelu_prime_f(__bfloat162float(zz.y)));
   }
+  uint4* od = reinterpret_cast<uint4*>(out + row * N + c0);
+  od[0] = make_uint4(o[0], o[1], o[2], o[3]);
+  od[1] = make_uint4(o[4], o[5], o[6], o[7]);
 }
 
-template <int K, int N, int EPI>
+template <int K, int N>
 __global__ void __launch_bounds__(kTlThreads, 4) k_tc_layer(const __nv_bfloat16* __restrict__ A,
                                                          const __nv_bfloat16* __restrict__ S,
-                                                         const float* __restrict__ bias,
                                                          const __nv_bfloat16* __restrict__ aux,
-                                                         void* out0, __nv_bfloat16* __restrict__ out1,
-                                                         int64_t rows, unsigned* status) {
-  static_assert(K % 16 == 0 && (N == 16 || N == 128), "layer shape");
+                                                         __nv_bfloat16* __restrict__ out, int64_t rows,
+                                                         unsigned* status) {
+  static_assert(K % 16 == 0 && N == 128, "layer shape");
   constexpr int NS = tc_layer_ns(N);
   extern __shared__ unsigned char tl_raw[];
   __shared__ __align__(8) uint64_t s_mbar;
@@ -1202,7 +1177,7 @@ __global__ void __launch_bounds__(kTlThreads, 4) k_tc_layer(const __nv_bfloat16*
   if (done) {
     const int64_t row = row0 + 32 * q + lane;
     const uint32_t t_row = tmem + ((uint32_t)(32 * q) << 16);
-    if (NS == 64) {
+    {
       // columns 32 hc .. 32 hc + 31 of the unit in two 16-column chunks, the
       // second loading from tensor memory while the first is processed
       const int cb = 32 * hc;
@@ -1210,14 +1185,9 @@ __global__ void __launch_bounds__(kTlThreads, 4) k_tc_layer(const __nv_bfloat16*
       tmem_ld_x16(t_row + (uint32_t)cb, va);
       tmem_wait_ld16(va);
       tmem_ld_x16(t_row + (uint32_t)(cb + 16), vb);
-      if (row < rows) tc_layer_epi16<N, EPI>(va, n0 + cb, row, bias, aux, out0, out1);
+      if (row < rows) tc_layer_bwd16<N>(va, n0 + cb, row, aux, out);
       tmem_wait_ld16(vb);
-      if (row < rows) tc_layer_epi16<N, EPI>(vb, n0 + cb + 16, row, bias, aux, out0, out1);
-    } else if (hc == 0) {
-      uint32_t v[16];
-      tmem_ld_x16(t_row, v);
-      tmem_wait_ld16(v);
-      if (row < rows) tc_layer_epi16<N, EPI>(v, n0, row, bias, aux, out0, out1);
+      if (row < rows) tc_layer_bwd16<N>(vb, n0 + cb + 16, row, aux, out);
     }
   } else if (tid == 0) {
     mbar_wait_bounded(mbar, 0);
@@ -1827,9 +1797,9 @@ cudaError_t layer_attr() {
                               (int)layer_smem<K, N>());
 }
 
-template <int K, int N, int EPI>
+template <int K, int N>
 cudaError_t tc_layer_attr() {
-  return cudaFuncSetAttribute(k_tc_layer<K, N, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  return cudaFuncSetAttribute(k_tc_layer<K, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)tc_layer_smem<K, N>());
 }
 template <int K, int N>
@@ -1845,11 +1815,8 @@ cudaError_t set_layer_attributes() {
   if (e == cudaSuccess) e = layer_attr<128, 16, EPI_LINEAR>();
   if (e == cudaSuccess) e = layer_attr<16, 128, EPI_BWD>();
   if (e == cudaSuccess) e = layer_attr<128, 128, EPI_BWD>();
-  if (e == cudaSuccess) e = tc_layer_attr<16, 128, EPI_GELU>();
-  if (e == cudaSuccess) e = tc_layer_attr<128, 128, EPI_GELU>();
-  if (e == cudaSuccess) e = tc_layer_attr<128, 16, EPI_LINEAR>();
-  if (e == cudaSuccess) e = tc_layer_attr<16, 128, EPI_BWD>();
-  if (e == cudaSuccess) e = tc_layer_attr<128, 128, EPI_BWD>();
+  if (e == cudaSuccess) e = tc_layer_attr<16, 128>();
+  if (e == cudaSuccess) e = tc_layer_attr<128, 128>();
   if (e == cudaSuccess) e = tc_wgrad_attr<128, 16>();
   if (e == cudaSuccess) e = tc_wgrad_attr<128, 128>();
   if (e == cudaSuccess) e = tc_wgrad_attr<16, 128>();
@@ -1873,17 +1840,20 @@ cudaError_t set_layer_attributes() {
   return e;
 }
 
-// One layer product with its epilogue: tcgen05 (k_tc_layer, 128-row tiles) or
-// mma.sync (k_layer, 64-row tiles) after the network's training engine.
+// One layer product with its epilogue: mma.sync (k_layer, 64-row tiles), or for
+// the backward products of the tcgen05 engine k_tc_layer (128-row x 64-column
+// units).
 template <int K, int N, int EPI>
 cudaError_t layer(const adot_mlp* m, const __nv_bfloat16* A, const __nv_bfloat16* S, const float* bias,
                   const __nv_bfloat16* aux, void* out0, __nv_bfloat16* out1, int64_t rows,
                   cudaStream_t s) {
-  if (m->train_engine == 0) {
-    const int64_t g = (rows + kTcRows - 1) / kTcRows * (N / tc_layer_ns(N));  // one unit per CTA
-    k_tc_layer<K, N, EPI><<<(unsigned)g, kTlThreads, tc_layer_smem<K, N>(), s>>>(A, S, bias, aux, out0,
-                                                                                out1, rows, m->d_status);
-    return cudaGetLastError();
+  if constexpr (EPI == EPI_BWD) {
+    if (m->train_engine == 0) {
+      const int64_t g = (rows + kTcRows - 1) / kTcRows * (N / tc_layer_ns(N));  // one unit per CTA
+      k_tc_layer<K, N><<<(unsigned)g, kTlThreads, tc_layer_smem<K, N>(), s>>>(
+          A, S, aux, (__nv_bfloat16*)out0, rows, m->d_status);
+      return cudaGetLastError();
+    }
   }
   constexpr size_t sm = layer_smem<K, N>();
   const int64_t g = (rows + kTileRows - 1) / kTileRows;
