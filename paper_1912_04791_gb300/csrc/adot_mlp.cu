@@ -688,6 +688,22 @@ __device__ __forceinline__ uint32_t tc_canon(int r, int kc, int K) {
   return (uint32_t)((r >> 3) * (K * 16) + kc * 128 + (r & 7) * 16);
 }
 
+// K-major layout of the weight-gradient operands (K = 128 batch rows) with the
+// core matrices along K 144 B apart instead of 128: the transposing stores of a
+// warp (consecutive row pairs, so consecutive core matrices along K) then fall
+// on all 32 banks instead of the same four.
+constexpr uint32_t kWgLbo = 144;
+constexpr uint32_t kWgSbo = 16 * kWgLbo;  // 16 core matrices along K per 8-row group
+__device__ __forceinline__ uint32_t wg_canon(int r, int kc) {
+  return (uint32_t)(r >> 3) * kWgSbo + (uint32_t)kc * kWgLbo + (uint32_t)(r & 7) * 16u;
+}
+
+// Shared-memory matrix descriptor with explicit LBO and SBO (bytes).
+__device__ __forceinline__ uint64_t tc_desc_ls(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
 // Shared-memory matrix descriptor: start address, LBO, SBO (all >> 4), the
 // descriptor version of this architecture family (bit 46), no swizzle.
 __device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, int K) {
@@ -1205,8 +1221,9 @@ __global__ void __launch_bounds__(kTlThreads, 4) k_tc_layer(const __nv_bfloat16*
 // block's `chunk` batch rows of dZ[r][n] X[r][k] and db[n] = sum of dZ[r][n],
 // with the batch rows as the reduction dimension of tcgen05.mma: per 128-row
 // sub-chunk the loading threads transpose dZ and X into K-major operands
-// (element (m, r) of an operand at tc_canon(m, r / 8, 128) + (r % 8) * 2; each
-// thread packs two consecutive batch rows into one 32-bit word), thread 0
+// (element (m, r) of an operand at wg_canon(m, r / 8) + (r % 8) * 2; each
+// thread packs two consecutive batch rows into one 32-bit word; the layout of
+// wg_canon, core matrices 144 B apart along K), thread 0
 // issues eight products (K = 16 each) that accumulate in tensor memory over the
 // whole chunk, and the first four warps write the block's float32 partial. With
 // N < 64 (the output layer) the product is dW^T = X^T dZ so that M = K = 128.
@@ -1215,7 +1232,7 @@ __global__ void __launch_bounds__(kTlThreads, 4) k_tc_layer(const __nv_bfloat16*
 // other half of the threads skip).
 template <int K, int N>
 __host__ __device__ constexpr size_t tc_wgrad_smem() {
-  return (size_t)(K + N) * kTcRows * 2 + 1024;
+  return (size_t)(K + N) / 8 * kWgSbo + 1024;  // two operands of (rows / 8) row groups
 }
 
 // Rows ra and rb (< c1, else zeros) of a [rows][C] bf16 matrix, columns of this
@@ -1244,7 +1261,7 @@ __device__ __forceinline__ void tc_scatter_rows(const __nv_bfloat16* __restrict_
       __nv_bfloat162 pair;
       pair.x = av[e];
       pair.y = bv[e];
-      *reinterpret_cast<__nv_bfloat162*>(dst + tc_canon(c0 + e, p >> 3, kTcRows) + (p & 7) * 2) = pair;
+      *reinterpret_cast<__nv_bfloat162*>(dst + wg_canon(c0 + e, p >> 3) + (p & 7) * 2) = pair;
     }
   }
 }
@@ -1267,7 +1284,7 @@ __global__ void __launch_bounds__(kTwThreads) k_tc_wgrad(const __nv_bfloat16* __
   const uint32_t raw_s = smem_addr(tw_raw);
   const uint32_t base = (raw_s + 1023u) & ~1023u;
   unsigned char* sA = tw_raw + (base - raw_s);  // [M][RK]
-  unsigned char* sB = sA + M * RK * 2;          // [NN][RK]
+  unsigned char* sB = sA + (M / 8) * kWgSbo;    // [NN][RK]
   unsigned char* sDz = TR ? sB : sA;            // the dZ operand ([N][RK])
   unsigned char* sX = TR ? sA : sB;             // the X operand ([K][RK])
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
@@ -1310,7 +1327,8 @@ __global__ void __launch_bounds__(kTwThreads) k_tc_wgrad(const __nv_bfloat16* __
     if (tid == 0) {
 #pragma unroll
       for (int ks = 0; ks < RK / 16; ++ks)
-        tc_mma(tmem, tc_desc(base + ks * 256, RK), tc_desc(base + M * RK * 2 + ks * 256, RK), idesc,
+        tc_mma(tmem, tc_desc_ls(base + ks * 2 * kWgLbo, kWgLbo, kWgSbo),
+               tc_desc_ls(base + (M / 8) * kWgSbo + ks * 2 * kWgLbo, kWgLbo, kWgSbo), idesc,
                (sub > 0 || ks > 0) ? 1u : 0u);
       tc_commit(mbar);
     }
@@ -1318,7 +1336,7 @@ __global__ void __launch_bounds__(kTwThreads) k_tc_wgrad(const __nv_bfloat16* __
     if (tid < N) {
 #pragma unroll
       for (int kc = 0; kc < RK / 8; ++kc) {
-        const uint4 v = *reinterpret_cast<const uint4*>(sDz + tc_canon(tid, kc, RK));
+        const uint4 v = *reinterpret_cast<const uint4*>(sDz + wg_canon(tid, kc));
         const __nv_bfloat162* p2v = reinterpret_cast<const __nv_bfloat162*>(&v);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
@@ -1764,7 +1782,7 @@ struct adot_mlp {
   __nv_bfloat16* dZ[4];
   float* pW[kLayers];
   float* pB[kLayers];
-  int chunk;
+  int chunk;  // rows per weight-gradient block of the mma.sync engine (sizes the partials)
   float* loss_part;
   float* loss_hist;
   int64_t hist_cap;
@@ -1840,6 +1858,11 @@ cudaError_t set_layer_attributes() {
   return e;
 }
 
+// Batch rows per weight-gradient block: 512 on tcgen05 (whose blocks carry a
+// fixed tensor-memory and partial-write cost), 256 on mma.sync (measured
+// faster); both are multiples of m->chunk, which sizes the partial buffers.
+int train_chunk(const adot_mlp* m) { return m->train_engine == 0 ? 512 : 256; }
+
 // One layer product with its epilogue: mma.sync (k_layer, 64-row tiles), or for
 // the backward products of the tcgen05 engine k_tc_layer (128-row x 64-column
 // units).
@@ -1866,10 +1889,10 @@ template <int K, int N>
 void wgrad(const adot_mlp* m, const __nv_bfloat16* dZ, const __nv_bfloat16* X, float* pW, float* pB,
            int64_t rows, int nch, cudaStream_t s) {
   if (m->train_engine == 0)
-    k_tc_wgrad<K, N><<<nch, kTwThreads, tc_wgrad_smem<K, N>(), s>>>(dZ, X, pW, pB, rows, m->chunk,
+    k_tc_wgrad<K, N><<<nch, kTwThreads, tc_wgrad_smem<K, N>(), s>>>(dZ, X, pW, pB, rows, train_chunk(m),
                                                                      m->d_status);
   else
-    k_wgrad<K, N><<<nch, 256, 0, s>>>(dZ, X, pW, pB, rows, m->chunk);
+    k_wgrad<K, N><<<nch, 256, 0, s>>>(dZ, X, pW, pB, rows, train_chunk(m));
 }
 
 const __nv_bfloat16* Wl(const adot_mlp* m, int l) { return m->d.W + w_offset(l); }
@@ -1917,7 +1940,7 @@ cudaError_t backward_batch(adot_mlp* m, int64_t B, cudaStream_t s) {
     if ((e = layer<128, 128, EPI_BWD>(m, m->dZ[l], Wtl(m, l), nullptr, m->Z[l - 1], m->dZ[l - 1], nullptr,
                                       B, s)))
       return e;
-  const int nch = (int)((B + m->chunk - 1) / m->chunk);
+  const int nch = (int)((B + train_chunk(m) - 1) / train_chunk(m));
   wgrad<128, 16>(m, m->dY, m->H[3], m->pW[4], m->pB[4], B, nch, s);
   for (int l = 3; l >= 1; --l) wgrad<128, 128>(m, m->dZ[l], m->H[l - 1], m->pW[l], m->pB[l], B, nch, s);
   wgrad<16, 128>(m, m->dZ[0], m->Xb, m->pW[0], m->pB[0], B, nch, s);
@@ -1926,7 +1949,7 @@ cudaError_t backward_batch(adot_mlp* m, int64_t B, cudaStream_t s) {
 
 AdamArgs adam_args(const adot_mlp* m, int64_t B) {
   AdamArgs a;
-  const int nch = (int)((B + m->chunk - 1) / m->chunk);
+  const int nch = (int)((B + train_chunk(m) - 1) / train_chunk(m));
   for (int l = 0; l < kLayers; ++l) {
     a.pW[l] = m->pW[l];
     a.pB[l] = m->pB[l];
@@ -2047,7 +2070,7 @@ adot_status adot_mlp_create(int64_t max_batch, void* cuda_stream, adot_mlp** out
   memset(m, 0, sizeof(adot_mlp));
   cudaGetDevice(&m->device);
   m->max_batch = ((max_batch + 63) / 64) * 64;
-  m->chunk = 512;
+  m->chunk = 256;  // the smaller of the engines' chunks sizes the partial buffers
   cudaError_t e = cudaSuccess;
   if (cuda_stream) {
     m->stream = (cudaStream_t)cuda_stream;
