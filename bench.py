@@ -32,9 +32,11 @@ UNIT = "cell-updates/s"
 # Gauss-Legendre nodes of the edge fluctuation, the float-float update and the
 # CFL spectral radius of the new state, counted from ncu's executed FFMA/FADD/
 # FMUL thread instructions of one launch divided by the cells it updates.
-# Per kernel kind: the block kernel repeats 1 edge in 256, the warp-tile
-# kernel 1 in 32; that repeated work is removed from the executed counts
-# (500.57 x 255/256 and 508.92 x 31/32). The counts were taken on the all-scalar
+# Per kernel kind: the block kernel repeats 1 edge in 256, and the warp-tile
+# kernel, in the tile form the count was taken on, repeated 1 in 32; that
+# repeated work is removed from the executed counts (500.57 x 255/256 and
+# 508.92 x 31/32), so the figures are per updated cell of the algorithm (the
+# warp kernel's contiguous ranges now repeat 1 edge in ~2000). The counts were taken on the all-scalar
 # build: evaluating two nodes per paired float32x2 instruction leaves the
 # arithmetic unchanged, and ncu's per-opcode thread counters omit the paired
 # instructions.
@@ -42,12 +44,12 @@ FLOPS_PER_CELL_UPDATE = {"block": 498.6, "warp": 493.0}
 # DRAM read + write bytes per cell-update of one launch (ncu, N = 4e6): the
 # ~24 B read match the algorithmic read; part of the 24 B written is still in
 # L2. None where the kernel changed after its capture.
-DRAM_BYTES_PER_CELL_UPDATE = {"block": None, "warp": (97.77e6 + 61.40e6) / 4e6}
+DRAM_BYTES_PER_CELL_UPDATE = {"block": None, "warp": (99.54e6 + 62.40e6) / 4e6}
 BYTES_PER_CELL_UPDATE = 48.0  # float-float state: 3 x 8 B read + 3 x 8 B written
 # Executed thread instructions per cell-update of one launch (ncu smsp__inst_executed x 32 / cells,
 # N = 4e6, repeated edges and boundary values included; "order2" is the second-order kernel);
 # None where the kernel changed after its capture.
-INSTR_PER_CELL_UPDATE = {"block": None, "warp": 85.50e6 * 32 / 4e6,
+INSTR_PER_CELL_UPDATE = {"block": None, "warp": 84.74e6 * 32 / 4e6,
                          "order2": 131.54e6 * 32 / 4e6}
 
 

@@ -112,8 +112,8 @@ typedef struct {
                                or warp tiles), 72 (warp tiles, 128 threads), 80 (warp tiles,
                                256 threads), or -1 = none (block kernel); 0 = autotuned */
   int32_t step_kernel;      /* 1 = block kernel (B-1 cells per block, shared-memory exchange),
-                               2 = persistent warp tiles (31 cells per warp tile, shuffle
-                               exchange); 0 = autotuned */
+                               2 = persistent warps, each over a contiguous range of cells
+                               in chunks of 32 edges (shuffle exchange); 0 = autotuned */
   double ks;                /* Strickler coefficient K_s [m^(1/3)/s] of the friction source
                                S = (0, -g h s_f, 0), s_f = q|q| / (K_s^2 h^(10/3)) (Sec. 2),
                                added as dt S(W_i^n) in Eq. scheme; 0 = frictionless */

@@ -186,6 +186,8 @@ __device__ __forceinline__ R friction_dt(const StepParams& p, R dt, R h, R q) {
   return -dt * R(p.fric) * q * d_abs(q) * (ih * ih * d_rcbrt(h));
 }
 
+__device__ __forceinline__ int64_t d_min_i64(int64_t a, int64_t b) { return a < b ? a : b; }
+
 template <typename R>
 __device__ __forceinline__ R warp_max(R v) {
 #pragma unroll
@@ -410,12 +412,16 @@ __device__ __forceinline__ void warp_step_size(const StepParams& p, int slot, in
   done = __shfl_sync(0xffffffffu, done0, 0) != 0;
 }
 
-// Persistent warp-tile variant of the time step. Each warp owns tiles of 32
-// edges / 31 cells (tile t: edges 31t .. 31t+31, cells 31t .. 31t+30) and walks
-// them with a grid-wide stride; D+ of edge e-1 comes from the left lane by a
-// shuffle, so warps never wait for one another. Each warp keeps its CFL maximum
-// in a register and folds it into the control slot once at the end. One edge
-// in 32 is evaluated twice.
+// Persistent warp-tile variant of the time step. Warp w owns a contiguous
+// range of cells, processed in chunks of 32 edges (one per lane): the edge of
+// lane l in chunk j is E_w + 32 j + l, and the lane updates cell e - 1 with D-
+// of its own edge and D+ of edge e - 1, taken from lane l - 1 by a shuffle or,
+// in lane 0, carried over from lane 31 of the previous chunk. So a warp of k
+// chunks updates 32 k - 1 cells and consecutive warps share one edge (the only
+// edge evaluated twice). With A active warps and K chunks in all, the ranges
+// cover 32 K - A >= n cells; each warp takes K / A or K / A + 1 chunks. Warps
+// never wait for one another; each keeps its CFL maximum in a register and
+// folds it into the control slot once at the end.
 template <typename R, int LAW, int B, int CAP, bool EXT = false>
 __global__ void __launch_bounds__(B, MinBlocks<B, CAP>::value)
     k_step_warp(const StepParams p, const typename Prec<R>::State in,
@@ -425,21 +431,39 @@ __global__ void __launch_bounds__(B, MinBlocks<B, CAP>::value)
   const int64_t gw = ((int64_t)blockIdx.x * B + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * B) >> 5;
   const int64_t n = p.n;
-  const int64_t n_tiles = (n + 30) / 31;
   Ctl* ctl = p.ctl;
 
   R nu;
   bool done;
   warp_step_size<R>(p, slot, lane, gw == 0, nu, done);
 
+  // active warps (at least 31 cells each) and chunks in all
+  const int64_t nact = d_min_i64(nwarps, (n + 30) / 31);
+  const int64_t K = (n + nact + 31) / 32;
+  const int64_t kb = K / nact, kr = K % nact;
+  const int64_t kw = (gw < nact) ? kb + (gw < kr ? 1 : 0) : 0;
+  const int64_t e0 = 32 * (gw * kb + d_min_i64(gw, kr)) - gw;  // first edge = first cell
+  // edges left in the range after the chunk's first (< 2^31 per warp)
+  int rem = (int)(d_min_i64(e0 + 32 * kw - 1, n) - e0);
+
+  // Lane 0 carries D+ of the previous chunk's last edge: in registers, or with
+  // the friction/feed/ghost extension compiled in, in shared memory (lane 0 is
+  // the only reader), which frees three registers at the 64 cap and costs the
+  // plain kernel a shared-memory round trip per chunk.
+  constexpr bool kSharedCarry = EXT;
+  __shared__ R s_carry[kSharedCarry ? B / 32 : 1][3];
+  R carry[3] = {R(0), R(0), R(0)};
+
   unsigned flags = 0;
   R rho_run = R(0);
-  for (int64_t t = gw; t < n_tiles; t += nwarps) {
-    const int64_t e = 31 * t + lane;
+  bool lead = lane >= 1;  // the lane's cell is in the range (all lanes after the first chunk)
+  for (int64_t eb = e0; rem >= 0; eb += 32, rem -= 32) {
+    const int64_t e = eb + lane;
+    const bool in_range = lane <= rem;
     {
-      // the warp's next tile into L2 while this one is computed (+2 % at N = 1e7)
-      const int64_t cn = 31 * (t + nwarps) + lane - 1;
-      if (t + nwarps < n_tiles && cn >= 0 && cn < n) {
+      // the warp's next chunk into L2 while this one is computed
+      const int64_t cn = e + 31;
+      if (rem >= 32 && cn < n) {
         asm volatile("prefetch.global.L2 [%0];" ::"l"(in.h + cn));
         asm volatile("prefetch.global.L2 [%0];" ::"l"(in.q + cn));
         asm volatile("prefetch.global.L2 [%0];" ::"l"(in.z + cn));
@@ -447,7 +471,7 @@ __global__ void __launch_bounds__(B, MinBlocks<B, CAP>::value)
     }
     S wl[3];
     R dm[3] = {R(0), R(0), R(0)}, dp[3] = {R(0), R(0), R(0)};
-    if (e <= n) {
+    if (in_range) {
       S wr[3];
       load_edge<R, EXT>(p, in, e, slot, wl, wr);
       edge_fluct<R, LAW>(p, wl, wr, dm, dp, flags);
@@ -455,9 +479,22 @@ __global__ void __launch_bounds__(B, MinBlocks<B, CAP>::value)
     }
     R dl[3];
 #pragma unroll
-    for (int r = 0; r < 3; ++r) dl[r] = __shfl_up_sync(0xffffffffu, dp[r], 1);
+    for (int r = 0; r < 3; ++r) {
+      const R up = __shfl_sync(0xffffffffu, dp[r], (lane + 31) & 31);
+      if constexpr (kSharedCarry) {
+        dl[r] = up;
+        if (lane == 0) {
+          R* sc = s_carry[threadIdx.x >> 5];
+          if (lead) dl[r] = sc[r];
+          sc[r] = up;  // D+ of this chunk's last edge
+        }
+      } else {
+        dl[r] = lane ? up : carry[r];
+        carry[r] = up;  // lane 0: D+ of this chunk's last edge
+      }
+    }
     const int64_t i = e - 1;
-    if (lane >= 1 && i < n) {
+    if (lead && in_range) {
       S nh = wl[0], nq = wl[1], nz = wl[2];
       if (!done) {
         R iq = -nu * (dm[1] + dl[1]);
@@ -486,6 +523,7 @@ __global__ void __launch_bounds__(B, MinBlocks<B, CAP>::value)
         }
       }
     }
+    lead = true;
   }
   rho_run = warp_max(rho_run);
   if (lane == 0 && !done && rho_run > R(0))
