@@ -281,3 +281,29 @@ def test_fp32_time_step_matches_oracle(gpu, law):
             s.set_state(h, q, z)
             _, dt = s.step(1)
         assert dt == pytest.approx(dt_ref, rel=2e-6)
+
+
+@pytest.mark.parametrize("block,cap", [(256, 64), (256, 80)])
+@pytest.mark.parametrize("shape", ["one_chunk_each", "one_more", "one_less", "many_chunks"])
+def test_fp64_warp_ranges_at_partition_edges(gpu, block, cap, shape):
+    """The warp kernel splits the cells into contiguous per-warp ranges of
+    32 k - 1 cells (chunks of 32 edges, D+ carried from lane 31 into the next
+    chunk's lane 0). With W resident warps: 31 W cells give every warp exactly
+    one chunk; one cell more gives one warp a second chunk; one cell less
+    truncates the last range; 4 x 31 W + 17 gives several chunks per warp and a
+    ragged last one. FP64 against the oracle, every value within 1e-12."""
+    import torch
+
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    w = sms * (65536 // (block * cap)) * block // 32
+    n = {"one_chunk_each": 31 * w, "one_more": 31 * w + 1, "one_less": 31 * w - 1,
+         "many_chunks": 4 * 31 * w + 17}[shape]
+    P = W.smooth_periodic(n)
+    K = 12
+    ho, qo, zo, to, _, _ = O.run(_ocfg(P), P.h, P.q, P.z, max_steps=K)
+    h, q, z, t, steps, _ = _run_gpu(gpu, P, gpu.FP64, steps=K, block_threads=block, reg_cap=cap,
+                                    step_kernel=2)
+    assert steps == K
+    assert t == pytest.approx(to, rel=1e-13)
+    for a, b in ((h, ho), (q, qo), (z, zo)):
+        assert np.abs(a - b).max() <= 1e-12 * _scale(b)
