@@ -1225,14 +1225,22 @@ __global__ void __launch_bounds__(kTlThreads, 4) k_tc_layer(const __nv_bfloat16*
 // thread packs two consecutive batch rows into one 32-bit word; the layout of
 // wg_canon, core matrices 144 B apart along K), thread 0
 // issues eight products (K = 16 each) that accumulate in tensor memory over the
-// whole chunk, and the first four warps write the block's float32 partial. With
+// whole chunk, and the first four warps write the block's float32 partial. The
+// operands are double-buffered: sub-chunk s is loaded into buffer s % 2 while
+// the products of s - 1 run, and a buffer is refilled only after the products
+// of s - 2 that read it have completed (one mbarrier per buffer). With
 // N < 64 (the output layer) the product is dW^T = X^T dZ so that M = K = 128.
 // Eight warps: thread t loads batch rows 2 (t % 64) and 2 (t % 64) + 1 and a
 // quarter of the columns of each operand (a half of the 16-wide ones, which the
 // other half of the threads skip).
+// Bytes of one operand buffer: both operands' (rows / 8) row groups, rounded to 1 KB.
+template <int K, int N>
+__host__ __device__ constexpr uint32_t tc_wgrad_buf() {
+  return ((uint32_t)(K + N) / 8 * kWgSbo + 1023u) & ~1023u;
+}
 template <int K, int N>
 __host__ __device__ constexpr size_t tc_wgrad_smem() {
-  return (size_t)(K + N) / 8 * kWgSbo + 1024;  // two operands of (rows / 8) row groups
+  return 2 * (size_t)tc_wgrad_buf<K, N>() + 1024;  // two buffers, 1 KB alignment slack
 }
 
 // Rows ra and rb (< c1, else zeros) of a [rows][C] bf16 matrix, columns of this
@@ -1277,19 +1285,18 @@ __global__ void __launch_bounds__(kTwThreads) k_tc_wgrad(const __nv_bfloat16* __
   static_assert(M == 128 && NN % 16 == 0 && NN <= 128, "weight-gradient shape");
   constexpr int RK = kTcRows;      // batch rows per sub-chunk (the products' K)
   constexpr uint32_t kCols = (NN < 32) ? 32u : (uint32_t)NN;
+  constexpr uint32_t kBuf = tc_wgrad_buf<K, N>();
   extern __shared__ unsigned char tw_raw[];
-  __shared__ __align__(8) uint64_t s_mbar;
+  __shared__ __align__(8) uint64_t s_mbar[2];
   __shared__ uint32_t s_tmem;
   __shared__ int s_timeout;
   const uint32_t raw_s = smem_addr(tw_raw);
-  const uint32_t base = (raw_s + 1023u) & ~1023u;
-  unsigned char* sA = tw_raw + (base - raw_s);  // [M][RK]
-  unsigned char* sB = sA + (M / 8) * kWgSbo;    // [NN][RK]
-  unsigned char* sDz = TR ? sB : sA;            // the dZ operand ([N][RK])
-  unsigned char* sX = TR ? sA : sB;             // the X operand ([K][RK])
+  const uint32_t base0 = (raw_s + 1023u) & ~1023u;
+  unsigned char* sA0 = tw_raw + (base0 - raw_s);  // buffer 0: [M][RK] then [NN][RK]
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&s_mbar)) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&s_mbar[0])) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&s_mbar[1])) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_timeout = 0;
   }
@@ -1298,17 +1305,34 @@ __global__ void __launch_bounds__(kTwThreads) k_tc_wgrad(const __nv_bfloat16* __
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = s_tmem;
-  const uint32_t mbar = smem_addr(&s_mbar);
+  const uint32_t mbar0 = smem_addr(&s_mbar[0]), mbar1 = smem_addr(&s_mbar[1]);
   const uint32_t idesc = tc_idesc(NN);
   const int64_t c0 = (int64_t)blockIdx.x * chunk;
   const int64_t c1 = imin64(c0 + chunk, rows);
   // this thread's pair of batch rows in a sub-chunk and its part of the operand rows
   const int pr = 2 * (tid & 63), part = tid >> 6;
   float bsum = 0.0f;
-  uint32_t parity = 0;
+  uint32_t par0 = 0, par1 = 0;  // phase of each buffer's mbarrier
+  uint32_t last_mbar = mbar0, last_par = 0;  // the latest commit: its mbarrier and phase
   int sub = 0;
   for (int64_t r0 = c0; r0 < c1; r0 += RK, ++sub) {
-    __syncthreads();  // the previous sub-chunk's bias reads are done
+    const int bi = sub & 1;
+    const uint32_t mbar = bi ? mbar1 : mbar0;
+    if (sub >= 2) {
+      // the products of sub - 2 read this buffer (its bias reads ended before
+      // the barrier of sub - 1)
+      const bool done = __all_sync(0xffffffffu, mbar_wait_bounded(mbar, bi ? par1 : par0));
+      if (bi) par1 ^= 1u; else par0 ^= 1u;
+      tc_fence_after();
+      if (!done) s_timeout = 1;
+      __syncthreads();
+      if (s_timeout) break;
+    }
+    const uint32_t base = base0 + (uint32_t)bi * kBuf;
+    unsigned char* sA = sA0 + (size_t)bi * kBuf;  // [M][RK]
+    unsigned char* sB = sA + (M / 8) * kWgSbo;    // [NN][RK]
+    unsigned char* sDz = TR ? sB : sA;            // the dZ operand ([N][RK])
+    unsigned char* sX = TR ? sA : sB;             // the X operand ([K][RK])
     const int64_t ra = r0 + pr, rb = ra + 1;
     // dZ rows ra, rb -> sDz[n][pr, pr + 1] for n in this thread's half of 0 .. N-1,
     // then X rows ra, rb -> sX[k][pr, pr + 1]; each operand's loads are issued together
@@ -1332,6 +1356,9 @@ __global__ void __launch_bounds__(kTwThreads) k_tc_wgrad(const __nv_bfloat16* __
                (sub > 0 || ks > 0) ? 1u : 0u);
       tc_commit(mbar);
     }
+    // every earlier commit to this mbarrier was waited for, so its phase is this one's
+    last_mbar = mbar;
+    last_par = bi ? par1 : par0;
     // bias partial: thread n sums row n of the dZ operand while the products run
     if (tid < N) {
 #pragma unroll
@@ -1345,12 +1372,13 @@ __global__ void __launch_bounds__(kTwThreads) k_tc_wgrad(const __nv_bfloat16* __
         }
       }
     }
-    const bool done = __all_sync(0xffffffffu, mbar_wait_bounded(mbar, parity));
-    parity ^= 1u;
+  }
+  // the last commit tracks every product issued before it
+  if (sub > 0 && !s_timeout) {
+    const bool done = __all_sync(0xffffffffu, mbar_wait_bounded(last_mbar, last_par));
     tc_fence_after();
     if (!done) s_timeout = 1;
     __syncthreads();
-    if (s_timeout) break;
   }
   if (!s_timeout) {
     if (sub > 0 && w < 4) {
@@ -1376,7 +1404,8 @@ __global__ void __launch_bounds__(kTwThreads) k_tc_wgrad(const __nv_bfloat16* __
     }
     if (tid < N) pB[(int64_t)blockIdx.x * N + tid] = bsum;
   } else if (tid == 0) {
-    mbar_wait_bounded(mbar, parity ^ 1u);
+    // give the products in flight one more bounded wait before the columns are freed
+    mbar_wait_bounded(last_mbar, last_par);
     if (status) atomicOr(status, ST_TIMEOUT);
   }
   tc_fence_before();
