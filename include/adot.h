@@ -339,7 +339,6 @@ adot_status adot_mlp_gradient(adot_mlp* mlp, const float* Xs, const float* Ts, i
  * each step's batch loss. One step is a replayed CUDA graph. */
 adot_status adot_mlp_train(adot_mlp* mlp, int64_t steps, int64_t batch, double lr, uint64_t seed,
                            float* loss_hist);
-
 /* Makes every later step of a float32 Grass context take |A|_Psi from the
  * network (A dW stays analytic), except on edges whose local Froude number
  * max(|Fr_L|, |Fr_R|, |Fr_mid|) lies in [fr_lo, fr_hi], whose two sides lie on
@@ -378,14 +377,25 @@ adot_status adot_harvest(adot_ctx* ctx, int64_t n, uint64_t seed, float* X, floa
  *  - h, q, z: device arrays of n_cells float64, read and overwritten in place.
  *  - t_io: host pointer; the start time in, the time after the steps out.
  *  - cuda_stream: a cudaStream_t, or NULL for the legacy default stream. The call
- *    waits for the stream before it returns, and reports the first device-side
+ *    ends with a device-to-host read of the control block into host memory and
+ *    cudaStreamSynchronize on that stream, and reports the first device-side
  *    error as adot_step does.
  * The second state buffer and the control block live in a file-scope device
  * array of ADOT_NOALLOC_MAX_CELLS cells (about 1.5 MB) that every GPU which
  * loads the library holds until the process exits. All calls share it: calls
- * that overlap on the GPU race, and each call clears the control block before
- * use. The first call on a device looks up the array's device address (once per
- * device); make that first call before any stream capture. */
+ * that overlap on the GPU (on any stream or host thread) race, so callers must
+ * serialise them; each call clears the control block before use.
+ * Set-up: the first call on a device looks up the array's device address (once
+ * per device, with that device current) and keeps it for the process. Under
+ * CUDA's lazy module loading (the default) the driver places the array, and
+ * each kernel this entry point runs, in the device's memory when they are first
+ * used, not when the library is loaded. So the first call on a device is the
+ * one that may allocate: make one call with the configuration you will use
+ * (n_steps = 1 runs every kernel a longer call runs) before reserving the
+ * device's memory, and before any stream capture. After that, calls with the
+ * same configuration allocate nothing. A device reset (cudaDeviceReset) while
+ * the library is loaded is not supported here: the address found at set-up
+ * would no longer be valid. */
 adot_status adot_step_noalloc(const adot_config* cfg, double* h, double* q, double* z,
                               int64_t n_steps, double* t_io, void* cuda_stream);
 

@@ -13,6 +13,12 @@
 // until the process exits. Every call shares it, so calls that overlap on the
 // GPU race; it keeps the last call's contents, and the control block, which
 // must start from zero, is cleared at the start of every call.
+//
+// Under CUDA's lazy module loading the driver places this translation unit's
+// module (and so the array) on a device when something in it is first used,
+// which here is the set-up's cudaGetSymbolAddress; each step kernel is loaded
+// at its first launch. The first call on a device with a given configuration
+// is therefore the one that may allocate, and later calls allocate nothing.
 #include <cuda_runtime.h>
 #include <math.h>
 

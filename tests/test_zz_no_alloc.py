@@ -78,3 +78,25 @@ def test_noalloc_rejects_what_it_cannot_do(gpu):
     with pytest.raises(gpu.AdotError) as e:
         gpu.adot_step_noalloc(gpu.config_for(big, gpu.FP64), hb, qb, zb, 1)
     assert e.value.status == gpu.E_INVALID_ARG
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_noalloc_call_after_setup_allocates_nothing(gpu, order):
+    """The property the entry point exists for. The first call on a device with
+    a configuration may allocate (the driver loads the scratch array and the
+    kernels it runs on first use); every later call with that configuration
+    must leave the device's free memory exactly where it was."""
+    torch = pytest.importorskip("torch")
+    P = W.movable_bed_riemann(257)
+    cfg = gpu.config_for(P, gpu.FP64, order=order)
+    h, q, z = (torch.tensor(a, device="cuda") for a in (P.h, P.q, P.z))
+    stream = torch.cuda.current_stream()
+    t = gpu.adot_step_noalloc(cfg, h, q, z, 1, 0.0, stream)  # set-up call
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for k in (5, 6):
+        t = gpu.adot_step_noalloc(cfg, h, q, z, k, t, stream)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert np.isfinite(h.cpu().numpy()).all() and t > 0.0
