@@ -207,6 +207,16 @@ adot_status adot_fluctuations(adot_ctx* ctx, const double* WL, const double* WR,
 adot_status adot_autotune(adot_ctx* ctx, int64_t trial_steps, int32_t* block_out,
                           int32_t* reg_cap_out, int32_t* step_kernel_out);
 
+/* Precision diagnostic of the current state (not a step): *nodes_out (may be
+ * NULL) receives the quadrature nodes of one step, 3 per edge (edges 0..n, or
+ * 0..n-1 when periodic); *fp64_nodes_out (may be NULL) how many of them the
+ * float32 step kernels redo in float64 because the roots of Eq. lambda nearly
+ * coalesce (1 - arg^2 < 1e-4 with arg = k2 / sqrt(4 k1^3), Eq. parameters, or
+ * arg not finite), by the same float32 test on the same node values, run in a
+ * separate kernel. ADOT_FP64 contexts report 0. Waits for the stream.
+ * ADOT_E_INVALID_ARG before a state was set. */
+adot_status adot_precision_stats(adot_ctx* ctx, int64_t* nodes_out, int64_t* fp64_nodes_out);
+
 /* Sums over the cells of h, q and z (float64, fixed-order tree: the result is
  * bit-reproducible). Multiply by dx for the integrals. */
 adot_status adot_conserved_sums(adot_ctx* ctx, double sums_out[3]);
@@ -339,6 +349,17 @@ adot_status adot_mlp_gradient(adot_mlp* mlp, const float* Xs, const float* Ts, i
  * each step's batch loss. One step is a replayed CUDA graph. */
 adot_status adot_mlp_train(adot_mlp* mlp, int64_t steps, int64_t batch, double lr, uint64_t seed,
                            float* loss_hist);
+/* One Adam step on a caller-given gradient (host [ADOT_MLP_PARAMS], packed as
+ * adot_mlp_set_params), through the update kernel adot_mlp_train runs after
+ * its backward pass: moments m, v updated with beta1 0.9, beta2 0.999, the
+ * bias corrections of step t = (steps taken so far) + 1, eps 1e-8, step size
+ * lr (0.05 + 0.95 (1 + cos(pi min(1, (t - 1) / total_steps))) / 2) (constant lr
+ * when total_steps = 0), then the float32 master parameters and their bf16
+ * copies; the step counter advances by one. Waits for the stream.
+ * ADOT_E_INVALID_ARG for a NULL gradient, lr <= 0 or total_steps < 0. */
+adot_status adot_mlp_apply_gradient(adot_mlp* mlp, const float* grad, double lr,
+                                    int64_t total_steps);
+
 /* Makes every later step of a float32 Grass context take |A|_Psi from the
  * network (A dW stays analytic), except on edges whose local Froude number
  * max(|Fr_L|, |Fr_R|, |Fr_mid|) lies in [fr_lo, fr_hi], whose two sides lie on

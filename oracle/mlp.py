@@ -104,6 +104,15 @@ def adam(theta, grad, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):
     return theta - lr * mh / (np.sqrt(vh) + eps), m, v
 
 
+def cosine_lr(t, total, lr0, floor=0.05):
+    """Step size of Adam step t (counting from 1) under the training schedule
+    (a reading: the paper's surrogate is not in the paper): cosine decay from
+    lr0 at t = 1 to floor * lr0 at t = total + 1, constant after that,
+    lr_t = lr0 (floor + (1 - floor) (1 + cos(pi f)) / 2), f = min(1, (t - 1) / total)."""
+    f = min(1.0, (t - 1) / total) if total > 0 else 0.0
+    return lr0 * (floor + (1.0 - floor) * 0.5 * (1.0 + np.cos(np.pi * f)))
+
+
 def features(WL, WR, Ag):
     """Raw surrogate inputs [n, 7]: h_L, q_L, z_L, h_R, q_R, z_R, A_g."""
     WL, WR = np.asarray(WL), np.asarray(WR)

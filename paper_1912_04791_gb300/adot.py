@@ -87,6 +87,7 @@ def lib() -> ctypes.CDLL:
             "adot_query": ([_P, _D, ctypes.POINTER(i64), _D], i32),
             "adot_fluctuations": ([_P, _P, _P, i64, _P, _P, _D, i32], i32),
             "adot_conserved_sums": ([_P, _D], i32),
+            "adot_precision_stats": ([_P, ctypes.POINTER(i64), ctypes.POINTER(i64)], i32),
             "adot_autotune": ([_P, i64, ctypes.POINTER(i32), ctypes.POINTER(i32),
                                ctypes.POINTER(i32)], i32),
             "adot_step_noalloc": ([ctypes.POINTER(Config), _P, _P, _P, i64, _D, _P], i32),
@@ -102,6 +103,7 @@ def lib() -> ctypes.CDLL:
             "adot_mlp_forward": ([_P, _P, i64, _P, i32], i32),
             "adot_mlp_gradient": ([_P, _P, _P, i64, ctypes.POINTER(ctypes.c_float), _P], i32),
             "adot_mlp_train": ([_P, i64, i64, dbl, ctypes.c_uint64, _P], i32),
+            "adot_mlp_apply_gradient": ([_P, _P, dbl, i64], i32),
             "adot_set_surrogate": ([_P, _P, dbl, dbl], i32),
             "adot_surrogate_stats": ([_P, ctypes.POINTER(i64), ctypes.POINTER(i64)], i32),
             "adot_surrogate_eval": ([_P, _P, i32, ctypes.POINTER(i64)], i32),
@@ -487,6 +489,12 @@ class Mlp:
                                        g.ctypes.data), "adot_mlp_gradient")
         return loss.value, g
 
+    def apply_gradient(self, grad, lr: float, total_steps: int = 0) -> None:
+        """One Adam step on a given packed gradient (the training update kernel)."""
+        g = _f32(grad, (MLP_PARAMS,))
+        _check(lib().adot_mlp_apply_gradient(self.ptr, g.ctypes.data, float(lr), int(total_steps)),
+               "adot_mlp_apply_gradient")
+
     def train(self, steps: int, batch: int, lr: float = 1e-3, seed: int = 1) -> np.ndarray:
         h = np.empty(max(steps, 1), dtype=np.float32)
         _check(lib().adot_mlp_train(self.ptr, steps, batch, lr, seed, h.ctypes.data), "adot_mlp_train")
@@ -551,6 +559,14 @@ def adot_harvest(ctx: int, n: int, seed: int = 1, X=None, T=None):
         raise ValueError("X, T must be CUDA tensors of shapes (n, 7) and (n, 9)")
     _check(lib().adot_harvest(ctx, n, seed, X.data_ptr(), T.data_ptr(), 1), "adot_harvest")
     return X, T
+
+
+def adot_precision_stats(ctx: int):
+    """(quadrature nodes of one step, nodes the float32 kernels redo in float64)
+    at the current state."""
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().adot_precision_stats(ctx, ctypes.byref(a), ctypes.byref(b)), "adot_precision_stats")
+    return a.value, b.value
 
 
 def adot_conserved_sums(ctx: int) -> np.ndarray:

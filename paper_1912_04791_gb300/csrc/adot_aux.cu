@@ -149,6 +149,51 @@ cudaError_t launch_harvest_f64(const StepParams& p, StateF64 st, int slot, int64
   return cudaGetLastError();
 }
 
+// Quadrature nodes of a float-float state whose float32 cubic-root solve the
+// step kernels redo in float64: the same test (1 - arg^2 below
+// TAU_FP64_FALLBACK, or not finite) on the same node values, the two outer
+// Gauss-Legendre nodes in the paired form and the midpoint in the scalar form,
+// as edge_fluct_f32x2 evaluates them. A diagnostic over the current state; it
+// is not part of a time step.
+template <int LAW>
+__global__ void __launch_bounds__(256) k_redo_count(const StepParams p, const StateF32 st, int slot,
+                                                    int64_t n_edges,
+                                                    unsigned long long* __restrict__ count) {
+  unsigned long long mine = 0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n_edges;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    float2 wl[3], wr[3];
+    load_edge<float, true>(p, st, e, slot, wl, wr);
+    const float dh = ff_diff(wr[0], wl[0]), dq = ff_diff(wr[1], wl[1]);
+    const float h0 = wl[0].x, q0 = wl[1].x;
+    const float2 s2 = make_float2((float)GL3_S0, (float)GL3_S2);
+    Eig2 e2;
+    node_eig_x2<LAW>(p.lf, fma2(s2, p2(dh), p2(h0)), fma2(s2, p2(dq), p2(q0)), e2);
+    const float dx0 = fmaf(-e2.arg.x, e2.arg.x, 1.0f), dx1 = fmaf(-e2.arg.y, e2.arg.y, 1.0f);
+    Eig<float> em;
+    node_eig<float, LAW>(p.lf, h0 + 0.5f * dh, q0 + 0.5f * dq, em);
+    const float dm = 1.0f - em.arg * em.arg;
+    mine += (!(dx0 >= TAU_FP64_FALLBACK) ? 1 : 0) + (!(dx1 >= TAU_FP64_FALLBACK) ? 1 : 0) +
+            (!(dm >= TAU_FP64_FALLBACK) ? 1 : 0);
+  }
+  for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+  if ((threadIdx.x & 31) == 0 && mine) atomicAdd(count, mine);
+}
+
+cudaError_t launch_redo_count_f32(const StepParams& p, int law, StateF32 st, int slot,
+                                  unsigned long long* count, cudaStream_t s) {
+  const int64_t ne = p.periodic ? p.n : p.n + 1;
+  if (law == LAW_GRASS)
+    k_redo_count<LAW_GRASS><<<grid_for(ne), 256, 0, s>>>(p, st, slot, ne, count);
+  else if (law == LAW_MPM)
+    k_redo_count<LAW_MPM><<<grid_for(ne), 256, 0, s>>>(p, st, slot, ne, count);
+  else if (law == LAW_GRASS_THR || law == LAW_POWER)
+    k_redo_count<LAW_GRASS_THR><<<grid_for(ne), 256, 0, s>>>(p, st, slot, ne, count);
+  else
+    return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
 __global__ void __launch_bounds__(256) k_to_ff(const double* __restrict__ src, float2* __restrict__ dst,
                                                int64_t n) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;

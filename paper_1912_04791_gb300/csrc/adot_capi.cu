@@ -845,6 +845,23 @@ adot_status adot_harvest(adot_ctx* c, int64_t n, uint64_t seed, float* X, float*
   return status_from_bits(c->h_ctl->status);
 }
 
+adot_status adot_precision_stats(adot_ctx* c, int64_t* nodes_out, int64_t* fp64_nodes_out) {
+  if (!c || !c->state_set) return ADOT_E_INVALID_ARG;
+  const int64_t ne = c->p.periodic ? c->p.n : c->p.n + 1;
+  unsigned long long redo = 0;
+  if (c->prec == ADOT_FP32) {
+    CK(cudaMemsetAsync(c->d_flrho, 0, sizeof(unsigned long long), c->stream));
+    CK(launch_redo_count_f32(c->p, c->law, st32(c, c->cur), c->phase % 3, c->d_flrho, c->stream));
+    CK(cudaMemcpyAsync(c->h_flrho, c->d_flrho, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                       c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    redo = c->h_flrho[0];
+  }
+  if (nodes_out) *nodes_out = 3 * ne;
+  if (fp64_nodes_out) *fp64_nodes_out = (int64_t)redo;
+  return ADOT_OK;
+}
+
 adot_status adot_conserved_sums(adot_ctx* c, double sums_out[3]) {
   if (!c || !sums_out) return ADOT_E_INVALID_ARG;
   if (c->prec == ADOT_FP32)

@@ -132,6 +132,12 @@ cudaError_t launch_harvest_f64(const StepParams& p, StateF64 st, int slot, int64
 cudaError_t launch_rho_f32(const StepParams& p, int law, StateF32 st, int slot, cudaStream_t s);
 cudaError_t launch_rho_f64(const StepParams& p, int law, StateF64 st, int slot, cudaStream_t s);
 
+// Adds to *count the quadrature nodes of a float-float state whose float32
+// cubic-root solve the step kernels redo in float64 (3 per edge; edges 0..n,
+// or 0..n-1 when periodic).
+cudaError_t launch_redo_count_f32(const StepParams& p, int law, StateF32 st, int slot,
+                                  unsigned long long* count, cudaStream_t s);
+
 // float64 <-> float-float conversion of n values.
 cudaError_t launch_to_ff(const double* src, float2* dst, int64_t n, cudaStream_t s);
 cudaError_t launch_from_ff(const float2* src, double* dst, int64_t n, cudaStream_t s);

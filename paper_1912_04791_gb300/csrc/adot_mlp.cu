@@ -2328,6 +2328,28 @@ adot_status adot_mlp_gradient(adot_mlp* m, const float* Xs, const float* Ts, int
   return ADOT_OK;
 }
 
+adot_status adot_mlp_apply_gradient(adot_mlp* m, const float* grad_packed, double lr,
+                                    int64_t total_steps) {
+  if (!m || !grad_packed || !(lr > 0.0) || total_steps < 0) return ADOT_E_INVALID_ARG;
+  std::vector<float> padded;
+  pack_to_padded(grad_packed, padded);
+  // the gradient goes in as the single batch chunk that k_adam sums
+  for (int l = 0; l < kLayers; ++l) {
+    CKM(cudaMemcpyAsync(m->pW[l], padded.data() + w_offset(l),
+                        sizeof(float) * (size_t)dim_in(l) * dim_out(l), cudaMemcpyHostToDevice,
+                        m->stream));
+    CKM(cudaMemcpyAsync(m->pB[l], padded.data() + kWTotal + b_offset(l),
+                        sizeof(float) * (size_t)dim_out(l), cudaMemcpyHostToDevice, m->stream));
+  }
+  AdamArgs a = adam_args(m, 1);
+  k_adam<<<(kWTotal + kBTotal + 255) / 256, 256, 0, m->stream>>>(m->d, a, (float)lr, total_steps,
+                                                                 0.9f, 0.999f, 1e-8f, 1);
+  k_step_incr<<<1, 32, 0, m->stream>>>(m->d.step);
+  CKM(cudaGetLastError());
+  CKM(cudaStreamSynchronize(m->stream));
+  return ADOT_OK;
+}
+
 adot_status adot_mlp_train(adot_mlp* m, int64_t steps, int64_t batch, double lr, uint64_t seed,
                            float* loss_hist) {
   if (!m || !m->have_data || steps < 0 || batch < 64 || batch > m->max_batch || !(lr > 0.0))

@@ -93,6 +93,23 @@ def gaussian_bump(n: int, Ag: float = 0.001) -> Problem:
                    BC_INFLOW_Q, BC_OUTFLOW_H, (0.6, 0.0, 0.0), (0.33, 0.0, 0.0))
 
 
+def gaussian_bump_prolonged(h_coarse, q_coarse, n: int, Ag: float = 0.001) -> Problem:
+    """The bump flow at n cells from a coarser state of the same problem (e.g. a
+    fixed-bed spin-up on a coarse grid): the free surface h + z and q linearly
+    interpolated to the fine cell centres (held constant beyond the outer
+    centres), the bed z = 0.2 exp(-(x-5)^2) taken at the fine centres, h = (h +
+    z) - z. Same boundary data as gaussian_bump."""
+    m = len(h_coarse)
+    xc = cell_centres(m, 0.0, 10.0)
+    zc = 0.2 * np.exp(-(xc - 5.0) ** 2)
+    x = cell_centres(n, 0.0, 10.0)
+    z = 0.2 * np.exp(-(x - 5.0) ** 2)
+    eta = np.interp(x, xc, np.asarray(h_coarse) + zc)
+    q = np.interp(x, xc, np.asarray(q_coarse))
+    return Problem("gaussian_bump", n, 0.0, 10.0, 0.9, 10.0, Ag, XI_P04, eta - z, q, z,
+                   BC_INFLOW_Q, BC_OUTFLOW_H, (0.6, 0.0, 0.0), (0.33, 0.0, 0.0))
+
+
 def soni_aggradation(n: int = 100, overfeed: float = 4.0, s0: float = 3.56e-3,
                      length: float = 30.0) -> Problem:
     """Aggradation by sediment overfeeding in a sloping flume (Sec. 5.1, the

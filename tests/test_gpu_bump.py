@@ -2,8 +2,16 @@
 spin-up (A_g = 0) that crosses Fr = 1, where the fixed-bed eigenvalues
 coalesce (coalescence reading) and the float32 path redoes nodes in float64,
 then morphodynamic runs with the Grass (A_g = 0.001) and the Meyer-Peter &
-Mueller laws. GPU against the oracle: FP64 within 1e-11 of each variable's
-scale, FP32 within 1e-5 (L1, relative)."""
+Mueller laws.
+
+GPU against the oracle. The morphodynamic runs start from the oracle's
+spun-up state on both sides: FP64 within 1e-12 of each variable's scale, the
+FP32 increment within 1e-5 (L1, relative). The spin-up itself is
+ill-conditioned: its transients over the crest amplify rounding about a
+million-fold, so that the oracle run from a depth one ulp larger moves by
+~2e-10 of the scale at t = 0.5 s and ~3e-11 at t = 6 s. Its FP64 bar is
+therefore the larger of 1e-12 and twice that one-ulp spread of the oracle,
+measured in the test."""
 import numpy as np
 import pytest
 
@@ -27,10 +35,12 @@ def _gcfg(gpu, P, kind, prec):
 
 @pytest.fixture(scope="module")
 def spun_up(gpu):
-    """(oracle state, GPU FP64 state, GPU FP32 state) after 6 s of fixed-bed flow."""
+    """(oracle state, GPU FP64 state, GPU FP32 state, oracle state from a depth
+    one ulp larger) after 6 s of fixed-bed flow."""
     P = W.gaussian_bump(N, Ag=0.0)
     cfg = O.make_cfg(N, 0, 10, 0.9, O.grass(0.0, xi=P.xi), P.bc_left, P.bc_right, P.bcl, P.bcr)
     ho, qo, zo, to, so, _ = O.run(cfg, P.h, P.q, P.z, t_end=6.0)
+    hu, qu, zu, *_ = O.run(cfg, P.h * (1.0 + 2.0 ** -52), P.q, P.z, t_end=6.0)
     out = [(ho, qo, zo, so)]
     for prec in (gpu.FP64, gpu.FP32):
         with gpu.Solver(gpu.config_for(P, prec)) as s:
@@ -38,37 +48,43 @@ def spun_up(gpu):
             s.run_to(6.0)
             t, steps, _ = s.query()
             out.append(s.get_state() + (steps,))
+    out.append((hu, qu, zu))
     return P, out
 
 
 def test_spin_up_crosses_critical_flow(spun_up):
-    P, (o, g64, g32) = spun_up
+    P, (o, g64, g32, ou) = spun_up
     h, q = o[0], o[1]
     fr = q / h / np.sqrt(9.81 * h)
     assert fr.min() < 0.9 and fr.max() > 1.1  # transcritical
     assert g64[3] == o[3]  # same number of steps
-    for a, b in zip(g64[:3], o[:3]):
-        assert np.abs(a - b).max() <= 1e-11 * np.abs(b).max()
+    for a, b, c in zip(g64[:3], o[:3], ou):
+        sc = np.abs(b).max()
+        spread = np.abs(c - b).max() / sc  # the oracle's own response to one ulp
+        err = np.abs(a - b).max() / sc
+        assert err <= max(1e-12, 2.0 * spread), (err, spread)
     for a, b in zip(g32[:3], o[:3]):
         assert np.abs(a - b).sum() <= 1e-5 * np.abs(b).sum()
 
 
 @pytest.mark.parametrize("kind", ["grass", "mpm"])
 def test_morphodynamic_runs_match_oracle(gpu, spun_up, kind):
-    P0, (o, g64, g32) = spun_up
+    P0, (o, g64, g32, _) = spun_up
     P = W.gaussian_bump(N, Ag=0.001)
     ocfg = O.make_cfg(N, 0, 10, 0.9, _olaw(kind, P), P.bc_left, P.bc_right, P.bcl, P.bcr)
     ho, qo, zo, *_ = O.run(ocfg, o[0], o[1], o[2], max_steps=300)
     assert np.abs(zo - o[2]).max() > 1e-4  # the bed moved
     with gpu.Solver(_gcfg(gpu, P, kind, gpu.FP64)) as s:
-        s.set_state(*g64[:3])
+        s.set_state(*o[:3])
         s.step(300)
         h, q, z = s.get_state()
     for a, b in ((h, ho), (q, qo), (z, zo)):
-        assert np.abs(a - b).max() <= 1e-10 * np.abs(b).max()
+        assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max(), np.abs(a - b).max() / np.abs(b).max()
     with gpu.Solver(_gcfg(gpu, P, kind, gpu.FP32)) as s:
-        s.set_state(*g32[:3])
+        s.set_state(*o[:3])
         s.step(300)
         h, q, z = s.get_state()
-    for a, b in ((h, ho), (q, qo), (z, zo)):
-        assert np.abs(a - b).sum() <= 1e-5 * np.abs(b).sum()
+    for a, b, a0 in ((h, ho, o[0]), (q, qo, o[1]), (z, zo, o[2])):
+        inc, ref = a - a0, b - a0
+        assert np.abs(inc - ref).sum() <= 1e-5 * np.abs(ref).sum(), \
+            np.abs(inc - ref).sum() / np.abs(ref).sum()

@@ -167,9 +167,78 @@ def test_full_ensemble_sampled_channels_match_oracle(gpu, oracle, prec, t_end):
                          O.grass(float(E.Ag[c]), xi=E.xi, g=9.81))
         ho, qo, zo, to, so, _ = O.run(cfg, hc, qc, zc, t_end=t_end)
         sl = slice(o[c], o[c + 1])
-        for a, b in ((h[sl], ho), (q[sl], qo), (z[sl], zo)):
+        for a, b, a0 in ((h[sl], ho, hc), (q[sl], qo, qc), (z[sl], zo, zc)):
             if prec == "FP64":
                 assert steps[c] == so, (c, steps[c], so)
                 assert np.abs(a - b).max() <= 1e-12 * max(np.abs(b).max(), 1e-300), c
             else:
-                assert np.abs(a - b).sum() <= 1e-5 * max(np.abs(b).sum(), 1e-12), c
+                # increments W(t_end) - W(0), not whole states
+                inc, ref = a - a0, b - a0
+                assert np.abs(ref).sum() > 0.0, c
+                assert np.abs(inc - ref).sum() <= 1e-5 * np.abs(ref).sum(), \
+                    (c, np.abs(inc - ref).sum() / np.abs(ref).sum())
+
+
+# Trans-critical flow over the Gaussian bump at N = 1e6 (inflow q = 0.6, outflow
+# h = 0.33): the fixed-bed flow spun up by the oracle on 2000 cells to t = 6 s
+# (it crosses Fr = 1 over the crest), prolonged to 1e6 cells, then K_BUMP steps
+# with the fixed bed (A_g = 0: the roots u - c, 0, u + c coalesce at Fr = 1, where
+# the float32 kernels redo nodes in float64), with Grass (A_g = 0.001) and with
+# Meyer-Peter & Mueller (s = 2.65, d50 = 1 mm, n = 0.02).
+N_BUMP = 1_000_000
+K_BUMP = 100
+MPM = dict(s_rel=2.65, d50=1e-3, manning_n=0.02)
+
+
+@pytest.fixture(scope="module")
+def bump_spin_up(oracle):
+    P0 = W.gaussian_bump(2000, Ag=0.0)
+    cfg = O.make_cfg(P0.n, P0.x_min, P0.x_max, P0.cfl, O.grass(0.0, xi=P0.xi), P0.bc_left,
+                     P0.bc_right, P0.bcl, P0.bcr)
+    h, q, z, t, *_ = O.run(cfg, P0.h, P0.q, P0.z, t_end=6.0)
+    return h, q
+
+
+@pytest.mark.parametrize("kind", ["fixed", "grass", "mpm"])
+def test_bump_full_size_matches_oracle(gpu, bump_spin_up, kind):
+    P = W.gaussian_bump_prolonged(*bump_spin_up, N_BUMP, Ag=0.0 if kind == "fixed" else 0.001)
+    fr = P.q / P.h / np.sqrt(P.g * P.h)
+    assert fr.min() < 0.9 and fr.max() > 1.1  # trans-critical
+    if kind == "mpm":
+        olaw, kw = O.mpm(xi=P.xi, **MPM), dict(law=gpu.LAW_MPM, **MPM)
+    else:
+        olaw, kw = O.grass(P.Ag, xi=P.xi), {}
+    ocfg = O.make_cfg(P.n, P.x_min, P.x_max, P.cfl, olaw, P.bc_left, P.bc_right, P.bcl, P.bcr)
+    ho, qo, zo, to, so, _ = O.run(ocfg, P.h, P.q, P.z, max_steps=K_BUMP)
+    assert so == K_BUMP
+    h, q, z, t = _gpu_run_k(gpu, P, gpu.FP64, K_BUMP, **kw)
+    assert t == pytest.approx(to, rel=1e-13)
+    for a, b in ((h, ho), (q, qo), (z, zo)):
+        err = np.abs(a - b).max() / np.abs(b).max()
+        assert err <= 1e-12, err
+    with gpu.Solver(gpu.config_for(P, gpu.FP32, **kw)) as s:
+        s.set_state(P.h, P.q, P.z)
+        nodes, redo = gpu.adot_precision_stats(s.ctx)
+        s.step(K_BUMP)
+        h, q, z = s.get_state()
+    assert nodes == 3 * (N_BUMP + 1)
+    if kind == "fixed":
+        assert redo > 0  # coalescence at the crest: the float64 redo fires
+    for a, b, a0 in ((h, ho, P.h), (q, qo, P.q), (z, zo, P.z)):
+        inc, ref = a - a0, b - a0
+        if kind == "fixed" and a0 is P.z:
+            # a fixed bed stays in place up to the rounding of its zero row of |A| dW
+            assert np.abs(inc).max() <= 1e-8 * np.abs(a0).max()
+            continue
+        assert np.abs(inc - ref).sum() <= 1e-5 * np.abs(ref).sum(), \
+            np.abs(inc - ref).sum() / np.abs(ref).sum()
+
+
+def _gpu_run_k(gpu, P, prec, k, **kw):
+    with gpu.Solver(gpu.config_for(P, prec, **kw)) as s:
+        s.set_state(P.h, P.q, P.z)
+        s.step(k)
+        t, steps, _ = s.query()
+        h, q, z = s.get_state()
+    assert steps == k
+    return h, q, z, t

@@ -352,3 +352,37 @@ def test_trained_surrogate_step(gpu):
     assert fb / edges < 0.05
     for a, b, a0 in ((hs, ho, P.h), (qs, qo, P.q), (zs, zo, P.z)):
         assert np.abs((a - a0) - (b - a0)).sum() <= 5e-2 * np.abs(b - a0).sum()
+
+
+def test_adam_update_matches_reference(gpu):
+    """The update kernel of the training graph (Adam with the cosine-decayed
+    step size) against oracle/mlp.py's adam and cosine_lr, element by element,
+    on the same gradients, at t = 1, 2, mid-schedule and after the schedule's
+    end. The kernel holds beta1, beta2, eps and lr0 as float32 constants, so
+    the reference takes those float32 values; what remains is float32 rounding:
+    a few ulp of each step's update plus half an ulp of each stored parameter."""
+    f32 = lambda x: float(np.float32(x))  # noqa: E731
+    b1, b2, eps, lr0, T = f32(0.9), f32(0.999), f32(1e-8), f32(1e-3), 200
+    rng = np.random.default_rng(21)
+    theta0 = _theta(3)
+    P = theta0.size
+    th, m, v = theta0.copy(), np.zeros(P), np.zeros(P)
+    S = np.zeros(P)  # sum of the reference's step magnitudes
+    checked = []
+    with gpu.Mlp(256) as net:
+        net.set_params(theta0)
+        for t in range(1, 261):
+            g = (rng.standard_normal(P) * 10.0 ** rng.uniform(-3, 1, P)).astype(np.float32)
+            net.apply_gradient(g, lr0, T)
+            prev = th
+            th, m, v = M.adam(th, g.astype(np.float64), m, v, t, lr=M.cosine_lr(t, T, lr0),
+                              b1=b1, b2=b2, eps=eps)
+            S += np.abs(th - prev)
+            if t in (1, 2, 101, 260):
+                got = net.get_params().astype(np.float64)
+                bound = 2e-6 * S + t * 2.0 ** -24 * (np.abs(th) + S)
+                err = np.abs(got - th)
+                assert (err <= bound).all(), (t, (err / bound).max())
+                assert np.abs(got - theta0).max() > 0.5 * t * lr0 * 0.05  # the parameters moved
+                checked.append(t)
+    assert checked == [1, 2, 101, 260]

@@ -58,6 +58,37 @@ def test_adam_first_step_closed_form():
     assert np.allclose(m1, 0.1 * g) and np.allclose(v1, 0.001 * g * g)
 
 
+def test_adam_constant_gradient_closed_form():
+    """With a constant gradient g the bias-corrected moments are exactly g and
+    g^2 at every step (m_t = (1 - b1^t) g, v_t = (1 - b2^t) g^2), so each step
+    moves theta by lr_t g / (|g| + eps): after T steps the sum of the step sizes."""
+    rng = np.random.default_rng(5)
+    th0 = rng.standard_normal(40)
+    g = rng.standard_normal(40)
+    th, m, v = th0.copy(), np.zeros(40), np.zeros(40)
+    lrs = [mlp.cosine_lr(t, 30, 2e-3) for t in range(1, 41)]
+    for t, lr in enumerate(lrs, start=1):
+        th, m, v = mlp.adam(th, g, m, v, t, lr=lr)
+        assert np.allclose(m, (1 - 0.9 ** t) * g, rtol=1e-13, atol=0)
+        assert np.allclose(v, (1 - 0.999 ** t) * g * g, rtol=1e-12, atol=0)
+    ref = th0 - sum(lrs) * g / (np.abs(g) + 1e-8)
+    assert np.abs(th - ref).max() <= 1e-13
+
+
+def test_cosine_schedule_closed_forms():
+    lr0, T = 1e-3, 200
+    assert mlp.cosine_lr(1, T, lr0) == lr0
+    assert abs(mlp.cosine_lr(T // 2 + 1, T, lr0) - 0.525 * lr0) <= 1e-18  # cos(pi/2) = 0
+    assert abs(mlp.cosine_lr(T + 1, T, lr0) - 0.05 * lr0) <= 1e-18
+    assert mlp.cosine_lr(T + 50, T, lr0) == mlp.cosine_lr(T + 1, T, lr0)
+    # cos(pi f) + cos(pi (1 - f)) = 0: steps symmetric about the middle sum to 1.05 lr0
+    for t in (2, 17, 64, 150):
+        assert abs(mlp.cosine_lr(t, T, lr0) + mlp.cosine_lr(T + 2 - t, T, lr0) - 1.05 * lr0) <= 1e-18
+    lr = [mlp.cosine_lr(t, T, lr0) for t in range(1, T + 2)]
+    assert all(a > b for a, b in zip(lr, lr[1:]))
+    assert mlp.cosine_lr(7, 0, lr0) == lr0  # no schedule length: constant
+
+
 def test_label_is_gl3_average_of_lapack_abs():
     law = O.grass(0.01, xi=W.XI_P04)
     WL, WR = W.random_edges(200, 3)
