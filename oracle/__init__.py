@@ -8,7 +8,8 @@ it. ``build()`` compiles ``adot_oracle.c`` with gcc (``-O2
 Every routine follows the paper (arXiv 1912.04791) as cited in the C source:
 Eq. W&A_definition (flux matrix), Eq. charPol / lambda / parameters /
 parameters_bis (analytic eigenvalues), Eq. RR / RR-1 / circPerm (eigenvectors),
-Eq. asbA / ExAbsA (|A|), Eq. path / DOTjumpN (fluctuations), Eq. scheme
+Eq. asbA / ExAbsA (|A|), Eq. path / DOTjumpN (fluctuations), Eq. PRICEjump /
+AiPRICE / Apsi / Im (the PRICE-C comparison scheme), Eq. scheme
 (update, with the Strickler friction source of Sec. 2 when K_s > 0), the
 sediment feed through an end of the Soni case (Sec. 5.1), and a second-order
 MUSCL-Hancock variant of the scheme (path-conservative reconstruction of
@@ -33,6 +34,7 @@ _lib = None
 OK, E_INVALID, E_DEPTH, E_NONFINITE, E_NONHYPERBOLIC, E_NOCONVERGE = range(6)
 LAW_GRASS, LAW_MPM, LAW_GRASS_THR, LAW_POWER = 0, 1, 2, 3
 ABS_ANALYTIC, ABS_NUMERIC, ABS_SYLVESTER, ABS_NEWTON = 0, 1, 2, 3
+SCHEME_DOT, SCHEME_PRICE_C = 0, 1
 BC_TRANSMISSIVE, BC_PERIODIC, BC_INFLOW_Q, BC_OUTFLOW_H, BC_INFLOW_QZ, BC_INFLOW_QS, \
     BC_OUTFLOW_HS = range(7)
 
@@ -72,6 +74,8 @@ class Cfg(ctypes.Structure):
         ("ks", ctypes.c_double),
         ("order", ctypes.c_int),
         ("limiter", ctypes.c_int),
+        ("scheme", ctypes.c_int),
+        ("price_eps", ctypes.c_double),
     ]
 
 
@@ -132,6 +136,9 @@ def lib() -> ctypes.CDLL:
         L.orc_run.argtypes = [ctypes.POINTER(Cfg), dp, dp, dp, ctypes.c_int64, ctypes.c_double,
                               dp, ctypes.POINTER(ctypes.c_int64), dp, dp]
         L.orc_abs_psi_batch.argtypes = [lp, ctypes.c_int, ctypes.c_int64, dp, dp, dp]
+        L.orc_a_psi.argtypes = [lp, dp, dp, dp]
+        L.orc_price_fluct.argtypes = [lp, ctypes.c_int64, dp, dp, ctypes.c_double, ctypes.c_double,
+                                      dp, dp]
         L.orc_num_threads.restype = ctypes.c_int
         L.orc_set_num_threads.argtypes = [ctypes.c_int]
         _lib = L
@@ -244,13 +251,37 @@ def abs_psi(law: Law, WL: np.ndarray, WR: np.ndarray, method: int = ABS_ANALYTIC
     return out
 
 
+def a_psi(law: Law, WL, WR) -> np.ndarray:
+    """A^Psi of one edge (Eq. Apsi, 3-point Gauss-Legendre rule), 3 x 3."""
+    wl = np.ascontiguousarray(WL, dtype=np.float64)
+    wr = np.ascontiguousarray(WR, dtype=np.float64)
+    out = np.zeros(9)
+    _check(lib().orc_a_psi(ctypes.byref(law), _p(wl), _p(wr), _p(out)), "a_psi")
+    return out.reshape(3, 3)
+
+
+def price_fluct(law: Law, WL: np.ndarray, WR: np.ndarray, nu: float, eps: float):
+    """PRICE-C fluctuations (Eq. PRICEjump, Eq. AiPRICE) of a batch of edges,
+    WL, WR [3, n], with nu = dt/dx and the small parameter eps; (Dm, Dp) [3, n]."""
+    WL = np.ascontiguousarray(WL, dtype=np.float64)
+    WR = np.ascontiguousarray(WR, dtype=np.float64)
+    n = WL.shape[1]
+    Dm = np.zeros((3, n))
+    Dp = np.zeros((3, n))
+    _check(lib().orc_price_fluct(ctypes.byref(law), n, _p(WL), _p(WR), nu, eps, _p(Dm), _p(Dp)),
+           "price_fluct")
+    return Dm, Dp
+
+
 def make_cfg(n: int, x_min: float, x_max: float, cfl: float, law: Law,
              bc_left: int = BC_TRANSMISSIVE, bc_right: int = BC_TRANSMISSIVE,
              bcl=(0.0, 0.0, 0.0), bcr=(0.0, 0.0, 0.0), method: int = ABS_ANALYTIC,
-             ks: float = 0.0, order: int = 1, limiter: int = 0) -> Cfg:
+             ks: float = 0.0, order: int = 1, limiter: int = 0, scheme: int = SCHEME_DOT,
+             price_eps: float = 1.0) -> Cfg:
     """Run configuration; ks > 0 adds the Strickler friction source (Sec. 2);
     order = 2 selects the second-order MUSCL-Hancock variant (limiter 0 = minmod,
-    1 = zero slopes)."""
+    1 = zero slopes); scheme = SCHEME_PRICE_C replaces the DOT jump function by
+    PRICE-C's (Sec. 3.2) with the small parameter price_eps of Eq. Im."""
     c = Cfg()
     c.n = n
     c.x_min = x_min
@@ -266,6 +297,8 @@ def make_cfg(n: int, x_min: float, x_max: float, cfl: float, law: Law,
     c.ks = ks
     c.order = order
     c.limiter = limiter
+    c.scheme = scheme
+    c.price_eps = price_eps
     return c
 
 

@@ -35,6 +35,8 @@
  *   second-order MUSCL-Hancock variant ............. Sec. 6 (no restriction on the order);
  *                                                    Castro, Gallardo & Pares (2006), path-
  *                                                    conservative reconstruction of states
+ *   PRICE-C jump function (comparison scheme) ...... Sec. 3.2, Eq. PRICEjump, AiPRICE, Apsi,
+ *                                                    Im; A^Psi with the same 3-point rule
  *
  * Parity status: every function here is pinned by tests (library eigensolver,
  * closed forms, invariants, textbook special cases); none is "parity unpinned".
@@ -103,7 +105,12 @@ typedef struct {
   int order;        /* 0 or 1: first-order scheme (Eq. scheme); 2: MUSCL-Hancock */
   int limiter;      /* order 2: 0 = minmod slopes, 1 = zero slopes (the first-order scheme
                        reached through the second-order code) */
+  int scheme;       /* ORC_SCHEME_DOT (jump function of Eq. DOTjumpN) or ORC_SCHEME_PRICE_C
+                       (Eq. PRICEjump) */
+  double price_eps; /* PRICE-C: the small parameter epsilon of I_eps (Eq. Im) */
 } orc_cfg;
+
+enum { ORC_SCHEME_DOT = 0, ORC_SCHEME_PRICE_C = 1 };
 
 /* Threshold on the eigenvalue gap, relative to c, below which |A| is taken
  * from the Newton divided-difference form instead of R|L|R^-1, whose R^-1
@@ -638,6 +645,76 @@ int orc_fluct(const orc_law* L, int method, int64_t n, const double* WL, const d
 }
 
 /* ---------------------------------------------------------------------- */
+/* PRICE-C jump function (Sec. 3.2), the paper's centred comparison scheme. */
+/* ---------------------------------------------------------------------- */
+
+/* A^Psi = integral over [0, 1] of A(Psi(W-, W+, s)) ds along the segment path
+ * (Eq. Apsi, Eq. path), row-major, with the 3-point Gauss-Legendre rule that
+ * Eq. DOTjumpN uses for the DOT integral. */
+int orc_a_psi(const orc_law* L, const double WL[3], const double WR[3], double out[9]) {
+  double s[3], w[3];
+  orc_gl3(s, w);
+  for (int i = 0; i < 9; ++i) out[i] = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    double ph = WL[0] + s[k] * (WR[0] - WL[0]);
+    double pq = WL[1] + s[k] * (WR[1] - WL[1]);
+    double A[9];
+    int st = orc_flux_matrix(L, ph, pq, A);
+    if (st) return st;
+    for (int i = 0; i < 9; ++i) out[i] += w[k] * A[i];
+  }
+  return ORC_OK;
+}
+
+/* PRICE-C fluctuations of one edge (Eq. PRICEjump, Eq. AiPRICE, Eq. Im):
+ *   A-/+ = 1/4 [ 2 A^Psi -/+ (dx/dt) I_eps -/+ (dt/dx) (A^Psi)^2 ],
+ *   D-/+ = A-/+ (W+ - W-),   I_eps = diag(1, 1, eps),
+ * given nu = dt/dx > 0. Each matrix is formed in full, as printed. */
+int orc_price_fluct_edge(const orc_law* L, const double WL[3], const double WR[3], double nu,
+                         double eps, double Dm[3], double Dp[3]) {
+  if (!(nu > 0.0)) return ORC_E_INVALID;
+  double Ap[9], Ap2[9];
+  int st = orc_a_psi(L, WL, WR, Ap);
+  if (st) return st;
+  orc_matmul3(Ap, Ap, Ap2);
+  double Ie[9] = {1.0, 0.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0, eps};
+  double Mm[9], Mp[9];
+  for (int i = 0; i < 9; ++i) {
+    Mm[i] = 0.25 * (2.0 * Ap[i] - (1.0 / nu) * Ie[i] - nu * Ap2[i]);
+    Mp[i] = 0.25 * (2.0 * Ap[i] + (1.0 / nu) * Ie[i] + nu * Ap2[i]);
+  }
+  double dW[3] = {WR[0] - WL[0], WR[1] - WL[1], WR[2] - WL[2]};
+  for (int r = 0; r < 3; ++r) {
+    Dm[r] = Mm[r * 3 + 0] * dW[0] + Mm[r * 3 + 1] * dW[1] + Mm[r * 3 + 2] * dW[2];
+    Dp[r] = Mp[r * 3 + 0] * dW[0] + Mp[r * 3 + 1] * dW[1] + Mp[r * 3 + 2] * dW[2];
+  }
+  return ORC_OK;
+}
+
+/* Batch of n PRICE-C edges; arrays are [3][n]. */
+int orc_price_fluct(const orc_law* L, int64_t n, const double* WL, const double* WR, double nu,
+                    double eps, double* Dm, double* Dp) {
+  int status = ORC_OK;
+#pragma omp parallel for schedule(static)
+  for (int64_t e = 0; e < n; ++e) {
+    double wl[3] = {WL[e], WL[n + e], WL[2 * n + e]};
+    double wr[3] = {WR[e], WR[n + e], WR[2 * n + e]};
+    double dm[3], dp[3];
+    int st = orc_price_fluct_edge(L, wl, wr, nu, eps, dm, dp);
+    if (st) {
+#pragma omp critical
+      if (!status) status = st;
+      dm[0] = dm[1] = dm[2] = dp[0] = dp[1] = dp[2] = NAN;
+    }
+    for (int r = 0; r < 3; ++r) {
+      Dm[r * n + e] = dm[r];
+      Dp[r * n + e] = dp[r];
+    }
+  }
+  return status;
+}
+
+/* ---------------------------------------------------------------------- */
 /* Time loop (Eq. scheme).                                                 */
 /* ---------------------------------------------------------------------- */
 
@@ -847,6 +924,11 @@ int orc_run(const orc_cfg* cfg, double* h, double* q, double* z, int64_t max_ste
   if (!(cfg->ks >= 0.0)) return ORC_E_INVALID;
   int order2 = (cfg->order == 2);
   if (cfg->order < 0 || cfg->order > 2) return ORC_E_INVALID;
+  int price = (cfg->scheme == ORC_SCHEME_PRICE_C);
+  if (cfg->scheme != ORC_SCHEME_DOT && !price) return ORC_E_INVALID;
+  /* PRICE-C enters the first-order scheme only */
+  if (price && (order2 || !(cfg->price_eps >= 0.0) || !isfinite(cfg->price_eps)))
+    return ORC_E_INVALID;
   /* the second-order variant covers the frictionless scheme without a feed */
   if (order2 && (cfg->ks > 0.0 || cfg->bc_left == ORC_BC_INFLOW_QS ||
                  cfg->bc_right == ORC_BC_INFLOW_QS))
@@ -933,7 +1015,8 @@ int orc_run(const orc_cfg* cfg, double* h, double* q, double* z, int64_t max_ste
         wr[0] = h[e]; wr[1] = q[e]; wr[2] = z[e];
       }
       double dm[3], dp[3];
-      int st = orc_fluct_edge(&cfg->law, cfg->abs_method, wl, wr, dm, dp);
+      int st = price ? orc_price_fluct_edge(&cfg->law, wl, wr, dt / dx, cfg->price_eps, dm, dp)
+                     : orc_fluct_edge(&cfg->law, cfg->abs_method, wl, wr, dm, dp);
       if (st) {
 #pragma omp critical
         if (!status) status = st;
