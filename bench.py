@@ -103,6 +103,8 @@ def parse():
                     help="timed steps of the workload with the Strickler friction source (0 = skip)")
     ap.add_argument("--order2-steps", type=int, default=480,
                     help="timed steps of the second-order (MUSCL-Hancock) variant (0 = skip)")
+    ap.add_argument("--price-steps", type=int, default=960,
+                    help="timed steps of the PRICE-C jump function on the workload (0 = skip)")
     ap.add_argument("--accuracy-steps", type=int, default=96,
                     help="steps of the FP32-vs-FP64 increment check (0 = skip)")
     return ap.parse_args()
@@ -416,6 +418,43 @@ def order2_leg(args, adot, P, n, stream, local, time_steps, plain_value, acc_ste
     return out
 
 
+def price_leg(args, adot, P, n, stream, local, time_steps, plain_value, acc_steps=96):
+    """The benchmark workload advanced with the PRICE-C jump function (Sec. 3.2,
+    epsilon = 1e-4 as in the paper's Tests 1-2), FP32 float-float state,
+    autotuned among its launch shapes; HBM roofline of the step kernel and the
+    FP32 increment over acc_steps steps against the GPU FP64 PRICE-C path."""
+    K = args.price_steps
+    kw = dict(scheme=adot.SCHEME_PRICE_C, price_eps=1e-4, device=local)
+    with adot.Solver(adot.config_for(P, adot.FP32, **kw), stream=stream) as sp:
+        sp.set_state(P.h, P.q, P.z)
+        bp, cp, kp = adot.adot_autotune(sp.ctx, 8)
+        adot.adot_step(sp.ctx, 48)
+        ms = time_steps(sp, K)
+        sp.set_state(P.h, P.q, P.z)
+        sp.step(acc_steps)
+        got = sp.get_state()
+    with adot.Solver(adot.config_for(P, adot.FP64, **kw), stream=stream) as s64:
+        s64.set_state(P.h, P.q, P.z)
+        s64.step(acc_steps)
+        ref = s64.get_state()
+    per_launch_s = ms * 1e-3 / K
+    hbm = BYTES_PER_CELL_UPDATE * n / per_launch_s / 1e9
+    peak = measured_peaks().get("hbm_gbs")
+    out = {"workload": f"smooth_periodic N={n}, PRICE-C jump function, eps = 1e-4 (FP32)",
+           "steps": K, "ms_per_step": ms / K, "cell_updates_per_s": n * K / (ms * 1e-3),
+           "vs_adot": (n * K / (ms * 1e-3)) / plain_value,
+           "kernel": f"k_step_warp<float,GRASS,{bp},{max(cp, 0)},0,1> (PRICE-C edge)",
+           "roofline": {"bound": "hbm", "achieved": hbm, "peak": peak, "unit": "GB/s",
+                        "frac": hbm / peak if peak else None,
+                        "bytes_per_cell_update": BYTES_PER_CELL_UPDATE,
+                        "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy)"},
+           "accuracy": {"steps": acc_steps, "reference": "GPU FP64 PRICE-C path"}}
+    for name, a, b, a0 in zip("hqz", got, ref, (P.h, P.q, P.z)):
+        out["accuracy"][f"l1_rel_increment_{name}"] = float(np.abs((a - a0) - (b - a0)).sum()
+                                                            / np.abs(b - a0).sum())
+    return out
+
+
 def soni_oracle_time(W):
     """The Soni case (100 cells, 2400 s) run by the FP64 oracle on one host core."""
     import oracle as O
@@ -657,6 +696,11 @@ def main():
     if args.order2_steps > 0 and rank == 0:
         order2 = order2_leg(args, adot, P, n, stream, local, time_steps, value)
 
+    # PRICE-C jump function (the paper's centred comparison scheme) on the same workload
+    price = None
+    if args.price_steps > 0 and rank == 0:
+        price = price_leg(args, adot, P, n, stream, local, time_steps, value)
+
     # learned |A|_Psi surrogate: harvest, train, then drive the benchmark workload
     surrogate = None
     if args.sur_steps > 0 and rank == 0:
@@ -701,6 +745,7 @@ def main():
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps, "clocks": clocks,
             "accuracy": accuracy, "sim_time_after_timed_steps": t_sim, "variants": variants,
             "ensemble": ensemble, "surrogate": surrogate, "friction": friction, "order2": order2,
+            "price_c": price,
             "l1_t_end_sweep": sweep,
         }
         print(json.dumps(line), flush=True)

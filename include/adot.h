@@ -68,6 +68,17 @@ typedef enum {
                     redone in float64 when 1 - arg^2 < 1e-4 (near-coalescent roots) */
 } adot_precision;
 
+/* Jump function of Eq. scheme. */
+typedef enum {
+  ADOT_SCHEME_DOT = 0,    /* DOT fluctuations (Eq. DOTjumpN) with the analytic eigenstructure
+                             (A-DOT, Sec. 3.3) */
+  ADOT_SCHEME_PRICE_C = 1 /* PRICE-C, the paper's centred comparison scheme (Sec. 3.2):
+                             D-/+ = 1/4 [2 A^Psi -/+ (dx/dt) I_eps -/+ (dt/dx) (A^Psi)^2] dW
+                             (Eq. PRICEjump, AiPRICE), A^Psi the 3-point Gauss-Legendre mean
+                             of A along the segment path (Eq. Apsi), I_eps = diag(1, 1, eps)
+                             acting on (h, q, z) (Eq. Im); dt from the same CFL rule */
+} adot_scheme;
+
 /* Boundary kinds. A ghost cell outside each end supplies the edge state. */
 typedef enum {
   ADOT_BC_TRANSMISSIVE = 0, /* ghost = adjacent cell (zero jump, zero fluctuation) */
@@ -110,7 +121,8 @@ typedef struct {
   int32_t device;           /* CUDA device ordinal; -1 = the calling thread's current device */
   int32_t reg_cap;          /* register cap per thread of the step kernel: 64 (block kernel
                                or warp tiles), 72 (warp tiles, 128 threads), 80 (warp tiles,
-                               256 threads), or -1 = none (block kernel); 0 = autotuned */
+                               256 threads), 40 or 32 (warp tiles, 256 threads, PRICE-C only),
+                               or -1 = none (block kernel); 0 = autotuned */
   int32_t step_kernel;      /* 1 = block kernel (B-1 cells per block, shared-memory exchange),
                                2 = persistent warps, each over a contiguous range of cells
                                in chunks of 32 edges (shuffle exchange); 0 = autotuned */
@@ -124,6 +136,12 @@ typedef struct {
                                the order open). Order 2 runs the warp-tile kernel only
                                (step_kernel 0 or 2) and is frictionless without a feed
                                (ks = 0, no ADOT_BC_INFLOW_QS): ADOT_E_UNSUPPORTED otherwise */
+  int32_t scheme;           /* adot_scheme; 0 = DOT. PRICE-C runs the first-order warp-tile
+                               kernel of 256 threads (register cap 64, 40 or 32; 0 = autotuned):
+                               order 2, step_kernel 1 and other shapes give ADOT_E_UNSUPPORTED;
+                               it takes the friction source and the boundary kinds as DOT does */
+  double price_eps;         /* PRICE-C: epsilon of I_eps (Eq. Im), >= 0 (the paper's Tests 1
+                               and 2 use 1e-4); ignored by DOT */
 } adot_config;
 
 typedef struct adot_ctx adot_ctx;
@@ -188,13 +206,23 @@ adot_status adot_run_to(adot_ctx* ctx, double t_end, int64_t* steps_out);
 adot_status adot_query(adot_ctx* ctx, double* t_out, int64_t* steps_out, double* dt_last_out);
 
 /* DOT fluctuations of n independent edges (Eq. DOTjumpN, G = 3, segment path),
- * in the context's law and precision. WL, WR: [3][n] left and right states;
+ * in the context's law and precision (also in a PRICE-C context). WL, WR: [3][n] left and right states;
  * Dminus, Dplus: [3][n] outputs. rho_max_out (may be NULL): the largest
  * max(|l1|, |l3|) met at any quadrature node. n = 0 is valid and writes nothing.
  * In ADOT_FP32 the inputs are first rounded to float-float, as the state is. */
 adot_status adot_fluctuations(adot_ctx* ctx, const double* WL, const double* WR, int64_t n,
                               double* Dminus, double* Dplus, double* rho_max_out,
                               int on_device);
+
+/* PRICE-C fluctuations of n independent edges (Eq. PRICEjump, Eq. AiPRICE, G = 3
+ * Gauss-Legendre nodes for A^Psi) with dt/dx = dt_over_dx > 0 and the context's
+ * law, precision and price_eps (whatever the context's scheme). WL, WR, Dminus,
+ * Dplus as for adot_fluctuations ([3][n] float64; in ADOT_FP32 the inputs are
+ * first rounded to float-float). n = 0 is valid and writes nothing.
+ * ADOT_E_INVALID_ARG for a non-positive or non-finite dt_over_dx. */
+adot_status adot_price_fluctuations(adot_ctx* ctx, const double* WL, const double* WR, int64_t n,
+                                    double dt_over_dx, double* Dminus, double* Dplus,
+                                    int on_device);
 
 /* Times the compiled step-kernel variants allowed by the configuration (kernel
  * kind, block size and register cap; a field left at 0 is free) on the current state with

@@ -22,6 +22,7 @@ OK, E_INVALID_ARG, E_NONPOSITIVE_DEPTH, E_NONFINITE, E_NONHYPERBOLIC, E_CUDA, E_
     E_UNSUPPORTED = range(8)
 LAW_GRASS, LAW_MPM, LAW_GRASS_THR, LAW_POWER = 0, 1, 2, 3
 FP64, FP32 = 0, 1
+SCHEME_DOT, SCHEME_PRICE_C = 0, 1
 BC_TRANSMISSIVE, BC_PERIODIC, BC_INFLOW_Q, BC_OUTFLOW_H, BC_INFLOW_QZ, BC_INFLOW_QS, \
     BC_OUTFLOW_HS = range(7)
 
@@ -48,7 +49,8 @@ class Config(ctypes.Structure):
                 ("bc_right_value", ctypes.c_double * 3), ("block_threads", ctypes.c_int32),
                 ("steps_per_graph", ctypes.c_int32), ("device", ctypes.c_int32),
                 ("reg_cap", ctypes.c_int32), ("step_kernel", ctypes.c_int32),
-                ("ks", ctypes.c_double), ("order", ctypes.c_int32)]
+                ("ks", ctypes.c_double), ("order", ctypes.c_int32),
+                ("scheme", ctypes.c_int32), ("price_eps", ctypes.c_double)]
 
 
 class EnsembleConfig(ctypes.Structure):
@@ -86,6 +88,7 @@ def lib() -> ctypes.CDLL:
             "adot_run_to": ([_P, dbl, ctypes.POINTER(i64)], i32),
             "adot_query": ([_P, _D, ctypes.POINTER(i64), _D], i32),
             "adot_fluctuations": ([_P, _P, _P, i64, _P, _P, _D, i32], i32),
+            "adot_price_fluctuations": ([_P, _P, _P, i64, dbl, _P, _P, i32], i32),
             "adot_conserved_sums": ([_P, _D], i32),
             "adot_precision_stats": ([_P, ctypes.POINTER(i64), ctypes.POINTER(i64)], i32),
             "adot_autotune": ([_P, i64, ctypes.POINTER(i32), ctypes.POINTER(i32),
@@ -171,7 +174,7 @@ def make_config(n_cells, x_min, x_max, cfl, Ag, xi, precision=FP32, bc_left=BC_T
                 bc_right=BC_TRANSMISSIVE, bcl=(0.0, 0.0, 0.0), bcr=(0.0, 0.0, 0.0), g=9.81,
                 law=LAW_GRASS, s_rel=0.0, d50=0.0, manning_n=0.0, block_threads=0,
                 steps_per_graph=0, device=-1, reg_cap=0, step_kernel=0, u_cr=0.0, beta=0.0,
-                ks=0.0, order=0) -> Config:
+                ks=0.0, order=0, scheme=SCHEME_DOT, price_eps=1e-4) -> Config:
     c = Config()
     c.n_cells = int(n_cells)
     c.x_min, c.x_max, c.cfl = float(x_min), float(x_max), float(cfl)
@@ -188,6 +191,8 @@ def make_config(n_cells, x_min, x_max, cfl, Ag, xi, precision=FP32, bc_left=BC_T
     c.step_kernel = step_kernel
     c.ks = float(ks)
     c.order = int(order)
+    c.scheme = int(scheme)
+    c.price_eps = float(price_eps)
     return c
 
 
@@ -295,6 +300,22 @@ def adot_fluctuations(ctx: int, WL, WR, Dm=None, Dp=None):
     _check(lib().adot_fluctuations(ctx, pl, pr, n, pm, pp, ctypes.byref(rho), d1),
            "adot_fluctuations")
     return Dm, Dp, rho.value
+
+
+def adot_price_fluctuations(ctx: int, WL, WR, dt_over_dx: float, Dm=None, Dp=None):
+    """PRICE-C D-/+ of the edges WL -> WR ([3, n] float64, numpy or CUDA tensors)
+    with nu = dt/dx. Returns (Dm, Dp)."""
+    n = WL.shape[1]
+    if Dm is None:
+        Dm = np.empty((3, n)) if isinstance(WL, np.ndarray) else WL.new_empty((3, n))
+    if Dp is None:
+        Dp = np.empty((3, n)) if isinstance(WL, np.ndarray) else WL.new_empty((3, n))
+    (pl, d1), (pr, d2), (pm, d3), (pp, d4) = _ptr(WL), _ptr(WR), _ptr(Dm), _ptr(Dp)
+    if not d1 == d2 == d3 == d4:
+        raise ValueError("all arrays must be on the host or all on the device")
+    _check(lib().adot_price_fluctuations(ctx, pl, pr, n, float(dt_over_dx), pm, pp, d1),
+           "adot_price_fluctuations")
+    return Dm, Dp
 
 
 def adot_autotune(ctx: int, trial_steps: int = 8):

@@ -17,7 +17,7 @@ BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(HERE, "libadot.so")
 
 SOURCES = ["adot_step_f32.cu", "adot_step_f64.cu", "adot_step_f32_ext.cu", "adot_step_f64_ext.cu",
-           "adot_step2_f32.cu", "adot_step2_f64.cu",
+           "adot_step2_f32.cu", "adot_step2_f64.cu", "adot_step_price.cu",
            "adot_aux.cu", "adot_capi.cu",
            "adot_noalloc.cu", "adot_ensemble.cu", "adot_mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -117,8 +117,18 @@ adot_status adot::validate_config(const adot_config* c) {
   if (!(c->ks >= 0.0) || !isfinite(c->ks)) return ADOT_E_INVALID_ARG;
   if (c->order < 0 || c->order > 2) return ADOT_E_INVALID_ARG;
   if (c->block_threads != 0 && !step_block_supported(c->block_threads)) return ADOT_E_INVALID_ARG;
-  if (c->reg_cap != 0 && c->reg_cap != 64 && c->reg_cap != 72 && c->reg_cap != 80 && c->reg_cap != -1)
+  if (c->scheme != ADOT_SCHEME_DOT && c->scheme != ADOT_SCHEME_PRICE_C) return ADOT_E_INVALID_ARG;
+  const bool price = c->scheme == ADOT_SCHEME_PRICE_C;
+  if (price && (!(c->price_eps >= 0.0) || !isfinite(c->price_eps))) return ADOT_E_INVALID_ARG;
+  const bool price_cap = c->reg_cap == 32 || c->reg_cap == 40;
+  if (c->reg_cap != 0 && c->reg_cap != 64 && c->reg_cap != 72 && c->reg_cap != 80 &&
+      c->reg_cap != -1 && !price_cap)
     return ADOT_E_INVALID_ARG;
+  if (price_cap && !price) return ADOT_E_UNSUPPORTED;  // caps 32 and 40 serve PRICE-C only
+  // PRICE-C runs the first-order warp-tile kernel of 256 threads
+  if (price && (c->order == 2 || c->step_kernel == 1 || c->reg_cap == -1 || c->reg_cap == 72 ||
+                c->reg_cap == 80 || (c->block_threads != 0 && c->block_threads != 256)))
+    return ADOT_E_UNSUPPORTED;
   if (c->step_kernel < 0 || c->step_kernel > 2) return ADOT_E_INVALID_ARG;
   if (c->steps_per_graph < 0 || c->device < -1) return ADOT_E_INVALID_ARG;
   if (c->order == 2 && (c->step_kernel == 1 || c->reg_cap == -1 || c->ks != 0.0 ||
@@ -161,6 +171,8 @@ void adot::make_step_params(const adot_config* cfg, StepParams* out) {
   p.feed_l = L.xi * cfg->bc_left_value[1];
   p.feed_r = L.xi * cfg->bc_right_value[1];
   p.order = (cfg->order == 2) ? 2 : 1;
+  p.scheme = (cfg->scheme == ADOT_SCHEME_PRICE_C) ? 1 : 0;
+  p.price_eps = p.scheme ? cfg->price_eps : 0.0;
 }
 
 namespace {
@@ -231,8 +243,8 @@ adot_status enqueue(adot_ctx* c, int64_t n) {
 }
 
 // Process-wide cache of tuned variants: (device, law, precision, log2 n, filters,
-// friction / feed kernels or not, order of the scheme).
-using TuneKey = std::tuple<int, int, int, int, int, int, int, int, int>;
+// friction / feed kernels or not, order of the scheme, jump function).
+using TuneKey = std::tuple<int, int, int, int, int, int, int, int, int, int>;
 std::mutex g_tune_mu;
 std::map<TuneKey, StepVariant> g_tune_cache;
 
@@ -240,7 +252,8 @@ TuneKey tune_key(const adot_ctx* c) {
   int lg = 0;
   for (int64_t n = c->p.n; n > 1; n >>= 1) ++lg;
   return std::make_tuple(c->device, c->law, c->prec, lg, c->cfg.block_threads, c->cfg.reg_cap,
-                         c->cfg.step_kernel, step_needs_ext(c->p) ? 1 : 0, c->p.order);
+                         c->cfg.step_kernel, step_needs_ext(c->p) ? 1 : 0, c->p.order,
+                         c->p.scheme);
 }
 
 bool candidate(const adot_config& cfg, StepVariant v) {
@@ -250,6 +263,10 @@ bool candidate(const adot_config& cfg, StepVariant v) {
   if (cfg.step_kernel == 1 && v.warp_tiles) return false;
   if (cfg.step_kernel == 2 && !v.warp_tiles) return false;
   if (cfg.order == 2 && !v.warp_tiles) return false;  // the second-order kernel is warp tiles
+  const bool price_shape = v.warp_tiles && v.block == 256 &&
+                           (v.reg_cap == 64 || v.reg_cap == 40 || v.reg_cap == 32);
+  if (cfg.scheme == ADOT_SCHEME_PRICE_C) return price_shape;
+  if (v.reg_cap == 40 || v.reg_cap == 32) return false;  // PRICE-C shapes
   return true;
 }
 
@@ -388,6 +405,10 @@ uint64_t config_fingerprint(const adot_config& c) {
   h = fnv1a(h, &c.ks, sizeof c.ks);
   const int32_t order = (c.order == 2) ? 2 : 1;
   h = fnv1a(h, &order, sizeof order);
+  if (c.scheme == ADOT_SCHEME_PRICE_C) {  // DOT configurations keep their earlier fingerprint
+    h = fnv1a(h, &c.scheme, sizeof c.scheme);
+    h = fnv1a(h, &c.price_eps, sizeof c.price_eps);
+  }
   h = fnv1a(h, &c.precision, sizeof c.precision);
   h = fnv1a(h, &c.bc_left, sizeof c.bc_left);
   h = fnv1a(h, &c.bc_right, sizeof c.bc_right);
@@ -744,6 +765,42 @@ adot_status adot_fluctuations(adot_ctx* c, const double* WL, const double* WR, i
   return status_from_bits((unsigned)(c->h_flrho[1] & 0xffffffffu));
 }
 
+adot_status adot_price_fluctuations(adot_ctx* c, const double* WL, const double* WR, int64_t n,
+                                    double dt_over_dx, double* Dminus, double* Dplus,
+                                    int on_device) {
+  if (!c || n < 0 || !(dt_over_dx > 0.0) || !isfinite(dt_over_dx)) return ADOT_E_INVALID_ARG;
+  if (n > 0 && (!WL || !WR || !Dminus || !Dplus)) return ADOT_E_INVALID_ARG;
+  if (n == 0) return ADOT_OK;
+  const double *wl = WL, *wr = WR;
+  double *dm = Dminus, *dp = Dplus;
+  const size_t bytes = sizeof(double) * 3 * (size_t)n;
+  if (!on_device) {
+    if (c->fl_cap < n) {
+      if (c->d_fl) cudaFree(c->d_fl);
+      c->d_fl = nullptr;
+      c->fl_cap = 0;
+      CK(cudaMalloc((void**)&c->d_fl, 4 * bytes));
+      c->fl_cap = n;
+    }
+    double* base = c->d_fl;
+    CK(cudaMemcpyAsync(base, WL, bytes, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(base + 3 * n, WR, bytes, cudaMemcpyHostToDevice, c->stream));
+    wl = base;
+    wr = base + 3 * n;
+    dm = base + 6 * n;
+    dp = base + 9 * n;
+  }
+  StepParams p = c->p;
+  p.price_eps = c->cfg.price_eps;
+  CK(launch_price_fluct(c->prec, c->law, p, dt_over_dx, wl, wr, n, dm, dp, c->stream));
+  if (!on_device) {
+    CK(cudaMemcpyAsync(Dminus, dm, bytes, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(Dplus, dp, bytes, cudaMemcpyDeviceToHost, c->stream));
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  return ADOT_OK;
+}
+
 adot_status adot_autotune(adot_ctx* c, int64_t trial_steps, int32_t* block_out,
                           int32_t* reg_cap_out, int32_t* step_kernel_out) {
   if (!c || !c->state_set || trial_steps < 1) return ADOT_E_INVALID_ARG;
@@ -761,7 +818,7 @@ adot_status adot_set_surrogate(adot_ctx* c, adot_mlp* m, double fr_lo, double fr
     c->mlp = nullptr;
     return build_graph(c);
   }
-  if (c->prec != ADOT_FP32 || c->law != ADOT_LAW_GRASS || c->p.order == 2)
+  if (c->prec != ADOT_FP32 || c->law != ADOT_LAW_GRASS || c->p.order == 2 || c->p.scheme != 0)
     return ADOT_E_UNSUPPORTED;
   if (!mlp_ready(m) || !(fr_lo <= fr_hi)) return ADOT_E_INVALID_ARG;
   CK(cudaStreamSynchronize(c->stream));

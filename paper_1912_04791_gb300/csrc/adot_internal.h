@@ -51,6 +51,8 @@ struct StepParams {
   double fric;              // g / K_s^2 of the Strickler friction source; 0 = none
   double feed_l, feed_r;    // xi q_s,in imposed through a BC_INFLOW_QS end
   int order;                // 1: Eq. scheme; 2: MUSCL-Hancock (k_step2_warp)
+  int scheme;               // 0: DOT jump function (Eq. DOTjumpN); 1: PRICE-C (Eq. PRICEjump)
+  double price_eps;         // PRICE-C: epsilon of I_eps (Eq. Im)
   Ctl* ctl;
   const float* absA;  // surrogate |A|_Psi per edge, [9][n+1] (NaN in row 0: analytic edge)
 };
@@ -83,11 +85,14 @@ struct StepVariant {
   int warp_tiles;  // 1: persistent warp-tile kernel (k_step_warp), 0: block kernel (k_step)
 };
 
-// The compiled variants, in the order the autotuner tries them.
-constexpr int kNumStepVariants = 10;
+// The compiled variants, in the order the autotuner tries them. The warp-tile
+// shapes with register caps 32 and 40 exist for PRICE-C only (its edge needs no
+// eigen-solve); PRICE-C runs the warp-tile shapes of 256 threads with caps 64,
+// 40 and 32.
+constexpr int kNumStepVariants = 12;
 constexpr StepVariant kStepVariants[kNumStepVariants] = {
-    {256, 0, 0},  {256, 64, 0}, {128, 0, 0}, {128, 64, 0}, {512, 0, 0}, {512, 64, 0},
-    {256, 64, 1}, {128, 64, 1}, {128, 72, 1}, {256, 80, 1}};
+    {256, 0, 0},  {256, 64, 0}, {128, 0, 0}, {128, 64, 0}, {512, 0, 0},  {512, 64, 0},
+    {256, 64, 1}, {128, 64, 1}, {128, 72, 1}, {256, 80, 1}, {256, 40, 1}, {256, 32, 1}};
 
 bool step_block_supported(int block);
 bool step_variant_supported(StepVariant v);
@@ -112,6 +117,20 @@ cudaError_t launch_step2_f32(const StepParams& p, int law, StepVariant v, StateF
                              StateF32 out, int slot, cudaStream_t s);
 cudaError_t launch_step2_f64(const StepParams& p, int law, StepVariant v, StateF64 in,
                              StateF64 out, int slot, cudaStream_t s);
+
+// PRICE-C time step (p.scheme == 1), warp tiles only: the plain entry points
+// forward to these. A variant that is not one of PRICE-C's runs as 256 x 64.
+cudaError_t launch_step_price_f32(const StepParams& p, int law, StepVariant v, StateF32 in,
+                                  StateF32 out, int slot, cudaStream_t s);
+cudaError_t launch_step_price_f64(const StepParams& p, int law, StepVariant v, StateF64 in,
+                                  StateF64 out, int slot, cudaStream_t s);
+
+// Stateless PRICE-C fluctuations of n edges ([3][n] float64 device arrays) with
+// nu = dt/dx and p.price_eps, in float64 (precision 0) or float32 from
+// float-float inputs (precision 1).
+cudaError_t launch_price_fluct(int precision, int law, const StepParams& p, double nu,
+                               const double* WL, const double* WR, int64_t n, double* Dm,
+                               double* Dp, cudaStream_t s);
 
 // Time step whose edges take |A|_Psi from p.absA (float32, Grass law, 256 x 64).
 cudaError_t launch_step_sur_f32(const StepParams& p, StateF32 in, StateF32 out, int slot,

@@ -15,6 +15,7 @@ bool step_variant_supported(StepVariant v) {
 
 cudaError_t launch_step_f32(const StepParams& p, int law, StepVariant v, StateF32 in, StateF32 out,
                             int slot, cudaStream_t s) {
+  if (p.scheme == 1) return launch_step_price_f32(p, law, v, in, out, slot, s);
   if (p.order == 2) return launch_step2_f32(p, law, v, in, out, slot, s);
   if (step_needs_ext(p)) return launch_step_f32_ext(p, law, v, in, out, slot, s);
   return launch_step_impl<float, false>(p, law, v, in, out, slot, s);

@@ -5,6 +5,7 @@ namespace adot {
 
 cudaError_t launch_step_f64(const StepParams& p, int law, StepVariant v, StateF64 in, StateF64 out,
                             int slot, cudaStream_t s) {
+  if (p.scheme == 1) return launch_step_price_f64(p, law, v, in, out, slot, s);
   if (p.order == 2) return launch_step2_f64(p, law, v, in, out, slot, s);
   if (step_needs_ext(p)) return launch_step_f64_ext(p, law, v, in, out, slot, s);
   return launch_step_impl<double, false>(p, law, v, in, out, slot, s);

@@ -261,6 +261,56 @@ __device__ __forceinline__ void edge_fluct_sur(const StepParams& p, const float2
   }
 }
 
+// PRICE-C fluctuations of one edge (Sec. 3.2, Eq. PRICEjump, AiPRICE, Apsi,
+// Im): D-/+ = 1/4 [2 A^Psi -/+ (dx/dt) I_eps -/+ (dt/dx) (A^Psi)^2] dW. A^Psi is
+// the 3-point Gauss-Legendre mean of A(Psi(s)) along the segment path, whose
+// first row is (0, 1, 0) and whose other rows hold five entries:
+//   row 1: (mean of c^2 - u^2, mean of 2u, mean of c^2),  row 2: (mean of a, mean of b, 0).
+// The products are taken matrix-free: y = A^Psi dW, zz = A^Psi y = (A^Psi)^2 dW.
+// nu = dt/dx and inv_nu = dx/dt come from the step; eps is p.price_eps. No
+// eigen-solve: the per-node work is u, c^2 and the transport derivatives.
+template <typename R, int LAW>
+__device__ __forceinline__ void edge_fluct_price(const StepParams& p, R nu, R inv_nu,
+                                                 const typename Prec<R>::S wl[3],
+                                                 const typename Prec<R>::S wr[3], R dm[3], R dp[3]) {
+  const R dh = Prec<R>::diff(wr[0], wl[0]);
+  const R dq = Prec<R>::diff(wr[1], wl[1]);
+  const R dz = Prec<R>::diff(wr[2], wl[2]);
+  const R h0 = Prec<R>::hi(wl[0]), q0 = Prec<R>::hi(wl[1]);
+  const auto& L = Prec<R>::law(p);
+  R m10 = R(0), m11 = R(0), m12 = R(0), m20 = R(0), m21 = R(0);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const R sk = (k == 0) ? R(GL3_S0) : ((k == 1) ? R(0.5) : R(GL3_S2));
+    const R w = (k == 1) ? R(GL3_W1) : R(GL3_W0);
+    const R h = h0 + sk * dh, q = q0 + sk * dq;
+    const R inv_h = R(1) / h;
+    const R u = q * inv_h, c2 = L.g * h;
+    R a, b;
+    sediment_derivs<R, LAW>(L, h, q, inv_h, u, a, b);
+    m10 += w * (c2 - u * u);
+    m11 += w * (R(2) * u);
+    m12 += w * c2;
+    m20 += w * a;
+    m21 += w * b;
+  }
+  const R y0 = dq;
+  const R y1 = m10 * dh + m11 * dq + m12 * dz;
+  const R y2 = m20 * dh + m21 * dq;
+  const R z0 = y1;
+  const R z1 = m10 * y0 + m11 * y1 + m12 * y2;
+  const R z2 = m20 * y0 + m21 * y1;
+  const R y[3] = {y0, y1, y2};
+  const R zz[3] = {z0, z1, z2};
+  const R v[3] = {dh, dq, R(p.price_eps) * dz};
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const R dis = R(0.25) * (inv_nu * v[r] + nu * zz[r]);
+    dm[r] = R(0.5) * y[r] - dis;
+    dp[r] = R(0.5) * y[r] + dis;
+  }
+}
+
 // Resident blocks per SM requested from the register allocator: CAP registers
 // per thread out of the SM's 65536, or no request (CAP = 0).
 template <int B, int CAP>
@@ -422,7 +472,10 @@ __device__ __forceinline__ void warp_step_size(const StepParams& p, int slot, in
 // cover 32 K - A >= n cells; each warp takes K / A or K / A + 1 chunks. Warps
 // never wait for one another; each keeps its CFL maximum in a register and
 // folds it into the control slot once at the end.
-template <typename R, int LAW, int B, int CAP, bool EXT = false>
+//
+// SCHEME 0 evaluates the DOT edge of Eq. DOTjumpN; SCHEME 1 the PRICE-C edge
+// (edge_fluct_price), everything else unchanged.
+template <typename R, int LAW, int B, int CAP, bool EXT = false, int SCHEME = 0>
 __global__ void __launch_bounds__(B, MinBlocks<B, CAP>::value)
     k_step_warp(const StepParams p, const typename Prec<R>::State in,
                 const typename Prec<R>::State out, const int slot) {
@@ -436,6 +489,7 @@ __global__ void __launch_bounds__(B, MinBlocks<B, CAP>::value)
   R nu;
   bool done;
   warp_step_size<R>(p, slot, lane, gw == 0, nu, done);
+  const R inv_nu = (SCHEME == 1 && !done) ? R(1) / nu : R(0);  // dx/dt of Eq. AiPRICE
 
   // active warps (at least 31 cells each) and chunks in all
   const int64_t nact = d_min_i64(nwarps, (n + 30) / 31);
@@ -474,7 +528,10 @@ __global__ void __launch_bounds__(B, MinBlocks<B, CAP>::value)
     if (in_range) {
       S wr[3];
       load_edge<R, EXT>(p, in, e, slot, wl, wr);
-      edge_fluct<R, LAW>(p, wl, wr, dm, dp, flags);
+      if constexpr (SCHEME == 1)
+        edge_fluct_price<R, LAW>(p, nu, inv_nu, wl, wr, dm, dp);
+      else
+        edge_fluct<R, LAW>(p, wl, wr, dm, dp, flags);
       if constexpr (EXT) feed_edge<R, LAW>(p, e, wl, wr, dm, dp);
     }
     R dl[3];

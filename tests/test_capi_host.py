@@ -38,8 +38,9 @@ int main(void) {
          offsetof(adot_config, bc_left_value), offsetof(adot_config, bc_right_value),
          offsetof(adot_config, block_threads), offsetof(adot_config, device),
          offsetof(adot_config, step_kernel), offsetof(adot_law, manning_n));
-  printf("%zu %zu %zu %zu\n", offsetof(adot_config, ks), offsetof(adot_law, u_cr),
-         offsetof(adot_law, beta), offsetof(adot_config, order));
+  printf("%zu %zu %zu %zu %zu %zu\n", offsetof(adot_config, ks), offsetof(adot_law, u_cr),
+         offsetof(adot_law, beta), offsetof(adot_config, order), offsetof(adot_config, scheme),
+         offsetof(adot_config, price_eps));
   printf("%zu %zu %zu %zu %zu %zu\n", sizeof(adot_ensemble_config), offsetof(adot_ensemble_config, g),
          offsetof(adot_ensemble_config, precision), offsetof(adot_ensemble_config, block_threads),
          offsetof(adot_ensemble_config, device), offsetof(adot_ensemble_config, step_kernel));
@@ -54,7 +55,8 @@ int main(void) {
     want = [ctypes.sizeof(C), ctypes.sizeof(W), C.law.offset, C.precision.offset,
             C.bc_left_value.offset, C.bc_right_value.offset, C.block_threads.offset,
             C.device.offset, C.step_kernel.offset, W.manning_n.offset,
-            C.ks.offset, W.u_cr.offset, W.beta.offset, C.order.offset,
+            C.ks.offset, W.u_cr.offset, W.beta.offset, C.order.offset, C.scheme.offset,
+            C.price_eps.offset,
             ctypes.sizeof(E), E.g.offset, E.precision.offset, E.block_threads.offset, E.device.offset,
             E.step_kernel.offset]
     assert got == want
@@ -70,7 +72,7 @@ def test_status_strings_and_version(L):
 @pytest.mark.parametrize("field,value", [
     ("n_cells", 0), ("cfl", 0.0), ("cfl", 1.5), ("x_max", -1.0), ("precision", 7),
     ("bc_left", 9), ("block_threads", 100), ("steps_per_graph", -6), ("device", -3),
-    ("reg_cap", 32), ("step_kernel", 3), ("bc_left", 7), ("bc_right", -1), ("ks", -1.0),
+    ("reg_cap", 48), ("step_kernel", 3), ("scheme", 2), ("scheme", -1), ("bc_left", 7), ("bc_right", -1), ("ks", -1.0),
     ("ks", float("nan")), ("ks", float("inf")), ("order", 3), ("order", -1)])
 def test_invalid_config_rejected_without_cuda(L, field, value):
     cfg = adot.make_config(64, 0.0, 1.0, 0.8, 0.005, 5 / 3)
@@ -98,6 +100,26 @@ def test_second_order_combinations_unsupported(L, kw):
     assert not out.value
 
 
+@pytest.mark.parametrize("kw,status", [
+    ({"price_eps": -1e-4}, adot.E_INVALID_ARG), ({"price_eps": float("nan")}, adot.E_INVALID_ARG),
+    ({"order": 2}, adot.E_UNSUPPORTED), ({"step_kernel": 1}, adot.E_UNSUPPORTED),
+    ({"block_threads": 128}, adot.E_UNSUPPORTED), ({"reg_cap": 80}, adot.E_UNSUPPORTED),
+    ({"reg_cap": -1}, adot.E_UNSUPPORTED)])
+def test_price_c_combinations_rejected(L, kw, status):
+    """PRICE-C runs the first-order warp-tile kernel of 256 threads (caps 64, 40, 32)."""
+    cfg = adot.make_config(64, 0.0, 1.0, 0.8, 0.005, 5 / 3, scheme=adot.SCHEME_PRICE_C, **kw)
+    out = ctypes.c_void_p()
+    assert L.adot_create(ctypes.byref(cfg), None, ctypes.byref(out)) == status
+    assert not out.value
+
+
+@pytest.mark.parametrize("cap", [32, 40])
+def test_price_c_caps_unsupported_for_dot(L, cap):
+    cfg = adot.make_config(64, 0.0, 1.0, 0.8, 0.005, 5 / 3, reg_cap=cap)
+    out = ctypes.c_void_p()
+    assert L.adot_create(ctypes.byref(cfg), None, ctypes.byref(out)) == adot.E_UNSUPPORTED
+
+
 def test_periodic_must_be_on_both_ends(L):
     cfg = adot.make_config(64, 0.0, 1.0, 0.8, 0.005, 5 / 3, bc_left=adot.BC_PERIODIC)
     out = ctypes.c_void_p()
@@ -110,6 +132,9 @@ def test_null_arguments_rejected(L):
     assert L.adot_step(None, 1, None, None) == adot.E_INVALID_ARG
     assert L.adot_query(None, None, None, None) == adot.E_INVALID_ARG
     assert L.adot_fluctuations(None, None, None, 0, None, None, None, 0) == adot.E_INVALID_ARG
+    assert L.adot_price_fluctuations(None, None, None, 0, 0.5, None, None, 0) == adot.E_INVALID_ARG
+    assert L.adot_precision_stats(None, None, None) == adot.E_INVALID_ARG
+    assert L.adot_mlp_apply_gradient(None, None, 1e-3, 0) == adot.E_INVALID_ARG
     assert L.adot_autotune(None, 8, None, None, None) == adot.E_INVALID_ARG
     assert L.adot_checkpoint_size(None, None) == adot.E_INVALID_ARG
     assert L.adot_checkpoint_save(None, None, 0, 0) == adot.E_INVALID_ARG
