@@ -28,36 +28,47 @@ sys.path.insert(0, ROOT)
 
 METRIC = "cell-updates/s at N=1e7 (A-DOT FP32 vs surrogate) at L1 err vs FP64 oracle"
 UNIT = "cell-updates/s"
-# FP32 flops per cell-update of the fused step kernel (FMA = 2): three
-# Gauss-Legendre nodes of the edge fluctuation, the float-float update and the
-# CFL spectral radius of the new state, counted from ncu's executed FFMA/FADD/
-# FMUL thread instructions of one launch divided by the cells it updates.
-# Per kernel kind: the block kernel repeats 1 edge in 256, and the warp-tile
-# kernel, in the tile form the count was taken on, repeated 1 in 32; that
-# repeated work is removed from the executed counts (500.57 x 255/256 and
-# 508.92 x 31/32), so the figures are per updated cell of the algorithm (the
-# warp kernel's contiguous ranges now repeat 1 edge in ~2000). The counts were taken on the all-scalar
-# build: evaluating two nodes per paired float32x2 instruction leaves the
-# arithmetic unchanged, and ncu's per-opcode thread counters omit the paired
-# instructions.
-FLOPS_PER_CELL_UPDATE = {"block": 498.6, "warp": 493.0}
-# DRAM read + write bytes per cell-update of one launch (ncu, N = 4e6): the
-# ~24 B read match the algorithmic read; part of the 24 B written is still in
-# L2. None where the kernel changed after its capture.
-DRAM_BYTES_PER_CELL_UPDATE = {"block": None, "warp": (99.54e6 + 62.40e6) / 4e6}
+# Per-launch counts of the fused step kernel from ncu captures at N = 4e6 (one
+# launch = one time step), per kernel shape (kind, threads, register cap); None
+# where the kernel changed after its capture or no capture exists.
+#  flops: executed FP32 flops per updated cell (2 FFMA + FADD + FMUL thread
+#         instructions) of the -DADOT_SCALAR_NODES build (ncu's per-opcode
+#         counters skip the paired float32x2 instructions of the default build,
+#         which does the same arithmetic); the edges evaluated twice (1 per warp
+#         range, 0.09 %) removed;
+#  instr: executed thread instructions per cell-update (smsp__inst_executed x 32 / cells);
+#  xu:    XU-pipe thread instructions per cell-update (sm__inst_executed_pipe_xu x 32 / cells);
+#  dram:  dram__bytes_read.sum + dram__bytes_write.sum per cell-update.
+KERNEL_COUNTS = {
+    ("warp", 256, 80): {"flops": (2 * 564.42e6 + 304.15e6 + 565.16e6) / 4e6 * (1 - 3648 / 4e6),
+                        "instr": 81.809e6 * 32 / 4e6, "xu": 4.147e6 * 32 / 4e6,
+                        "dram": (98.44e6 + 57.48e6) / 4e6},
+    ("warp", 256, 64): {"flops": 493.0, "instr": 84.74e6 * 32 / 4e6, "xu": None,
+                        "dram": (99.54e6 + 62.40e6) / 4e6},
+    ("order2", 256, 64): {"flops": None, "instr": 131.54e6 * 32 / 4e6, "xu": None, "dram": None},
+}
+# The block kernel's all-scalar count (1 edge in 256 evaluated twice, removed).
+FLOPS_BLOCK = 498.6
+# The algorithmic flop count per cell-update of the planning estimate: three
+# Gauss-Legendre nodes of ~130 FP32-pipe instructions each plus ~20 for the
+# update and CFL epilogue, ~410 instructions, about 700-800 flops counting an
+# FMA as 2; the midpoint is the roofline's primary basis, the executed count
+# the second.
+FLOPS_PER_CELL_UPDATE_PLAN = 750.0
 BYTES_PER_CELL_UPDATE = 48.0  # float-float state: 3 x 8 B read + 3 x 8 B written
-# Executed thread instructions per cell-update of one launch (ncu smsp__inst_executed x 32 / cells,
-# N = 4e6, repeated edges and boundary values included; "order2" is the second-order kernel);
-# None where the kernel changed after its capture.
-INSTR_PER_CELL_UPDATE = {"block": None, "warp": 84.74e6 * 32 / 4e6,
-                         "order2": 131.54e6 * 32 / 4e6}
 
 
-def issue_roofline(kind: str, n: int, per_launch_s: float):
+def counts(kind: str, block: int, cap: int) -> dict:
+    c = KERNEL_COUNTS.get((kind, block, cap), {})
+    if kind == "block":
+        c = {"flops": FLOPS_BLOCK}
+    return c
+
+
+def issue_roofline(ipc, n: int, per_launch_s: float):
     """The binding term of the FP32 step kernel: instruction issue. Achieved
     thread instructions per second (ncu count per cell-update x cells / live
     launch time) against 152 SMs x 4 schedulers x 32 lanes x 2070 MHz."""
-    ipc = INSTR_PER_CELL_UPDATE.get(kind)
     if not ipc:
         return None
     peak = 152 * 4 * 32 * 2070e6 / 1e12
@@ -97,8 +108,13 @@ def parse():
                     help="training steps of the |A|_Psi surrogate at batch 65536 (0 = skip the leg)")
     ap.add_argument("--sur-samples", type=int, default=50_000_000,
                     help="edge samples harvested from the smooth, bump and ensemble workloads")
-    ap.add_argument("--l1-sweep", action="store_true",
-                    help="also run the smooth problem to t_end = 0.5 s at N = 1e3 * 2^k (FP32, FP64, oracle)")
+    ap.add_argument("--l1-sweep-kmax", type=int, default=6,
+                    help="t_end sweep of the smooth problem at N = 1e3 * 2^k, k <= this (-1 = skip)")
+    ap.add_argument("--l1-sweep-oracle-max", type=int, default=4000,
+                    help="largest N of the t_end sweep that the CPU oracle also runs")
+    ap.add_argument("--config3-steps", type=int, default=480,
+                    help="FP32 steps of the 1e6-cell bump workload per transport law (0 = skip)")
+    ap.add_argument("--no-peaks", action="store_true", help="skip the pipe-throughput probes")
     ap.add_argument("--friction-steps", type=int, default=960,
                     help="timed steps of the workload with the Strickler friction source (0 = skip)")
     ap.add_argument("--order2-steps", type=int, default=480,
@@ -202,10 +218,13 @@ def oracle_throughput(n: int, steps: int, threads: int | None = None):
     return n * steps / dt, dt, O.num_threads()
 
 
-def surrogate_leg(args, adot, W, P, n, stream, dev, local, time_steps, ref64):
-    """Harvest edges (float64 labels) from the smooth periodic, Gaussian-bump and
-    ensemble workloads, train the MLP at batch 65536, then run the benchmark
-    workload with |A|_Psi from the network (analytic fallback near Fr = 1)."""
+def surrogate_leg(args, adot, W, P, n, stream, dev, local, time_steps, ref64, sweep=None):
+    """Harvest edges (float64 labels) from the smooth periodic workload (over its
+    convergence sweep's sizes and times to t_end, and at N = 1e6), the
+    Gaussian bump and the ensemble, train the MLP at batch 65536, then run the benchmark
+    workload with |A|_Psi from the network (analytic fallback near Fr = 1).
+    sweep(net), when given, runs while the trained network is alive; its result
+    is returned under "_sweep"."""
     import torch
     n_h = int(args.sur_samples)
     X = torch.empty((n_h, 7), dtype=torch.float32, device=dev)
@@ -225,10 +244,25 @@ def surrogate_leg(args, adot, W, P, n, stream, dev, local, time_steps, ref64):
             solver.step(steps_between)
 
     t0 = time.perf_counter()
+    # the smooth problem over its convergence sweep (N = 1e3 ... 6.4e4), 16 snapshots
+    # each spread over [0, t_end): states of every size and time the sweep visits
+    sizes = [1000 * 2 ** j for j in range(7)]
+    for m in sizes:
+        Pm = W.smooth_periodic(m)
+        with adot.Solver(adot.config_for(Pm, adot.FP32, device=local), stream=stream) as sm:
+            sm.set_state(Pm.h, Pm.q, Pm.z)
+            per_snap = int(0.25 * n_h) // (len(sizes) * 16)
+            for j in range(16):
+                take = min(per_snap, n_h - k)
+                adot.adot_harvest(sm.ctx, take, seed, X[k:k + take], T[k:k + take])
+                k += take
+                seed += 1
+                sm.run_to(Pm.t_end * (j + 1) / 16)
+    # and at N = 1e6 (early times)
     P2 = W.smooth_periodic(1_000_000)
     with adot.Solver(adot.config_for(P2, adot.FP32, device=local), stream=stream) as s2:
         s2.set_state(P2.h, P2.q, P2.z)
-        harvest(s2, int(0.4 * n_h), 3000, 4)
+        harvest(s2, int(0.2 * n_h), 3000, 4)
     P3 = W.gaussian_bump(100_000, Ag=0.001)
     with adot.Solver(adot.config_for(P3, adot.FP32, device=local), stream=stream) as s3:
         s3.set_state(P3.h, P3.q, P3.z)
@@ -324,6 +358,8 @@ def surrogate_leg(args, adot, W, P, n, stream, dev, local, time_steps, ref64):
                 out[f"l1_rel_increment_{name}"] = float(np.abs((a_ - a0) - (b_ - a0)).sum()
                                                         / np.abs(b_ - a0).sum())
                 out[f"l1_rel_state_{name}"] = float(np.abs(a_ - b_).sum() / np.abs(b_).sum())
+        if sweep is not None:
+            out["_sweep"] = sweep(net)
         return out
 
 
@@ -331,7 +367,7 @@ KS_BENCH = 30.0  # Strickler coefficient of the friction line (s_f ~ 1e-4 on thi
 FRICTION_FLOPS_PER_CELL = 10.0  # q|q|, 1/h, h^(-1/3), four products, dt scaling, one add
 
 
-def friction_leg(args, adot, W, P, n, stream, dev, local, time_steps, plain_value):
+def friction_leg(args, adot, W, P, n, stream, dev, local, time_steps, plain_value, peaks=None):
     """The benchmark workload with the friction source compiled in (the EXT step
     kernels), then the Soni case end to end through the public API."""
     import torch
@@ -346,15 +382,18 @@ def friction_leg(args, adot, W, P, n, stream, dev, local, time_steps, plain_valu
         ms = time_steps(sf, K)
     per_launch_s = ms * 1e-3 / K
     kind = "warp" if fk == 2 else "block"
-    f_peak = 152 * 128 * 2 * (2070e6) / 1e12
-    achieved = (FLOPS_PER_CELL_UPDATE[kind] + FRICTION_FLOPS_PER_CELL) * n / per_launch_s / 1e12
+    f_peak = peaks["ffma_tflops"] if peaks else 152 * 128 * 2 * (2070e6) / 1e12
+    base = counts(kind, fb, max(fc, 0)).get("flops") or FLOPS_PER_CELL_UPDATE_PLAN
+    achieved = (base + FRICTION_FLOPS_PER_CELL) * n / per_launch_s / 1e12
     out = {"workload": f"smooth_periodic N={n} with Strickler friction K_s={KS_BENCH} (FP32)",
            "steps": K, "ms_per_step": ms / K, "cell_updates_per_s": n * K / (ms * 1e-3),
            "vs_frictionless": (n * K / (ms * 1e-3)) / plain_value,
            "kernel": f"{'k_step_warp' if fk == 2 else 'k_step'}<float,GRASS,{fb},{max(fc, 0)},EXT>",
            "roofline": {"bound": "alu", "achieved": achieved, "peak": f_peak, "unit": "TFLOP/s",
                         "frac": achieved / f_peak,
-                        "flops_per_cell_update": FLOPS_PER_CELL_UPDATE[kind] + FRICTION_FLOPS_PER_CELL,
+                        "flops_per_cell_update": base + FRICTION_FLOPS_PER_CELL,
+                        "flops_basis": "executed count of the frictionless kernel of the same shape "
+                                       "(the plan estimate where none) + the source's 10",
                         "hbm_achieved_gbs": BYTES_PER_CELL_UPDATE * n / per_launch_s / 1e9}}
     S = W.soni_aggradation()
     soni = {"case": "Soni aggradation as printed: 100 cells, 2400 s, q_s = 1.45e-3 u^5, K_s = 49.4, "
@@ -410,8 +449,9 @@ def order2_leg(args, adot, P, n, stream, local, time_steps, plain_value, acc_ste
            "kernel": f"k_step2_warp<float,GRASS,{b2},{max(c2, 0)}>",
            "hbm_achieved_gbs": BYTES_PER_CELL_UPDATE * n / per_launch_s / 1e9,
            "accuracy": {"steps": acc_steps, "reference": "GPU FP64 second-order path"}}
-    if INSTR_PER_CELL_UPDATE.get("order2"):
-        out["issue_slots"] = issue_roofline("order2", n, per_launch_s)
+    ipc = counts("order2", b2, max(c2, 0)).get("instr")
+    if ipc:
+        out["issue_slots"] = issue_roofline(ipc, n, per_launch_s)
     for name, a, b, a0 in zip("hqz", got, ref, (P.h, P.q, P.z)):
         out["accuracy"][f"l1_rel_increment_{name}"] = float(np.abs((a - a0) - (b - a0)).sum()
                                                             / np.abs(b - a0).sum())
@@ -455,6 +495,66 @@ def price_leg(args, adot, P, n, stream, local, time_steps, plain_value, acc_step
     return out
 
 
+def measure_pipes(adot, local):
+    """Measured throughput of the pipes the step kernels use (library probes,
+    CUDA events): FP32 FFMA and paired FFMA2 (TFLOP/s), MUFU rsqrt and sine
+    (T ops/s), FP64 DFMA (TFLOP/s)."""
+    out = {}
+    for kind, name in ((adot.PIPE_FFMA, "ffma_tflops"), (adot.PIPE_FFMA2, "ffma2_tflops"),
+                       (adot.PIPE_RSQ, "mufu_rsq_tops"), (adot.PIPE_SIN, "mufu_sin_tops"),
+                       (adot.PIPE_DFMA, "dfma_tflops")):
+        rate, sec = adot.adot_measure_pipe(kind, local)
+        out[name] = rate / 1e12
+    out["how"] = ("adot_measure_pipe: 8 blocks x 256 threads per SM, 8 independent chains per "
+                  "thread, one timed launch after a warm-up, CUDA events")
+    return out
+
+
+def config3_leg(args, adot, W, stream, local, time_steps):
+    """Trans-critical flow over the Gaussian bump at N = 1e6 (inflow q = 0.6,
+    outflow h = 0.33): a fixed-bed spin-up on the GPU (FP64, 1e4 cells, to
+    t = 6 s) prolonged to 1e6 cells, then K steps in FP32 with the fixed bed
+    (coalescing roots at Fr = 1, float64 redo), Grass A_g = 0.001 and MPM:
+    cell-updates/s, the share of quadrature nodes redone in float64, and the
+    FP32 increment against the GPU FP64 path over the same steps."""
+    K = args.config3_steps
+    P0 = W.gaussian_bump(10_000, Ag=0.0)
+    with adot.Solver(adot.config_for(P0, adot.FP64, device=local), stream=stream) as s0:
+        s0.set_state(P0.h, P0.q, P0.z)
+        s0.run_to(6.0)
+        h0, q0, _ = s0.get_state()
+    mpm = dict(law=adot.LAW_MPM, s_rel=2.65, d50=1e-3, manning_n=0.02)
+    out = {"workload": "Gaussian bump N=1e6, fixed-bed spin-up (1e4 cells, FP64, 6 s) prolonged, "
+                       "then FP32 steps", "steps": K}
+    for name, Ag, kw in (("fixed_bed", 0.0, {}), ("grass", 0.001, {}), ("mpm", 0.001, mpm)):
+        P = W.gaussian_bump_prolonged(h0, q0, 1_000_000, Ag=Ag)
+        with adot.Solver(adot.config_for(P, adot.FP32, device=local, **kw), stream=stream) as sf:
+            sf.set_state(P.h, P.q, P.z)
+            nodes, redo = adot.adot_precision_stats(sf.ctx)
+            b, c, k = adot.adot_autotune(sf.ctx, 8)
+            sf.set_state(P.h, P.q, P.z)
+            sf.step(K)
+            got = sf.get_state()
+            sf.set_state(P.h, P.q, P.z)
+            ms = time_steps(sf, K)
+        with adot.Solver(adot.config_for(P, adot.FP64, device=local, **kw), stream=stream) as s64:
+            s64.set_state(P.h, P.q, P.z)
+            s64.step(K)
+            ref = s64.get_state()
+        r = {"cell_updates_per_s": P.n * K / (ms * 1e-3), "ms_per_step": ms / K,
+             "kernel": f"{'k_step_warp' if k == 2 else 'k_step'}<float,{'MPM' if kw else 'GRASS'},{b},{max(c, 0)}>",
+             "fp64_redo_nodes": redo, "nodes": nodes, "fp64_redo_fraction": redo / nodes}
+        for v, a, bb, a0 in zip("hqz", got, ref, (P.h, P.q, P.z)):
+            if name == "fixed_bed" and v == "z":  # the bed stays: its motion is rounding only
+                r["max_abs_bed_motion_fp32"] = float(np.abs(a - a0).max())
+                r["max_abs_bed_motion_fp64"] = float(np.abs(bb - a0).max())
+                continue
+            r[f"l1_rel_increment_{v}"] = float(np.abs((a - a0) - (bb - a0)).sum()
+                                               / np.abs(bb - a0).sum())
+        out[name] = r
+    return out
+
+
 def soni_oracle_time(W):
     """The Soni case (100 cells, 2400 s) run by the FP64 oracle on one host core."""
     import oracle as O
@@ -472,10 +572,11 @@ def soni_oracle_time(W):
     return {"wall_s": wall, "steps": int(steps), "cores": 1, "dz_at_feed_m": float(z[0] - S.z[0])}
 
 
-def l1_sweep(adot, W, stream, local, k_max=8, n_oracle_max=32000):
-    """Full-t_end errors on the smooth periodic problem: FP32 vs the GPU FP64
-    path (itself parity-tested against the oracle) for N = 1e3 * 2^k, k <= k_max,
-    and GPU FP64 / FP32 vs the CPU oracle for N <= n_oracle_max."""
+def l1_sweep(adot, W, stream, local, k_max=8, n_oracle_max=32000, net=None):
+    """Full-t_end errors on the smooth periodic problem: FP32 (and, with a
+    trained network, the surrogate form) vs the GPU FP64 path (itself
+    parity-tested against the oracle) for N = 1e3 * 2^k, k <= k_max, and GPU
+    FP64 / FP32 vs the CPU oracle for N <= n_oracle_max."""
     import oracle as O
     rows = []
     for k in range(k_max + 1):
@@ -483,17 +584,26 @@ def l1_sweep(adot, W, stream, local, k_max=8, n_oracle_max=32000):
         P = W.smooth_periodic(n)
         res = {"n": n}
         states = {}
-        for name, prec in (("fp64", adot.FP64), ("fp32", adot.FP32)):
+        forms = [("fp64", adot.FP64), ("fp32", adot.FP32)] + ([("surrogate", adot.FP32)] if net else [])
+        for name, prec in forms:
             with adot.Solver(adot.config_for(P, prec, device=local), stream=stream) as s:
                 s.set_state(P.h, P.q, P.z)
+                if name == "surrogate":
+                    adot.adot_set_surrogate(s.ctx, net, 0.8, 1.2)
                 t0 = time.perf_counter()
                 s.run_to(P.t_end)
                 res[f"{name}_seconds"] = time.perf_counter() - t0
                 _, steps, _ = s.query()
                 res[f"{name}_steps"] = steps
                 states[name] = s.get_state()
+                if name == "surrogate":
+                    edges, fb = adot.adot_surrogate_stats(s.ctx)
+                    res["surrogate_fallback_fraction"] = fb / max(edges, 1)
         for v, a, b in zip("hqz", states["fp32"], states["fp64"]):
             res[f"l1_fp32_vs_fp64_{v}"] = float(np.abs(a - b).sum() / np.abs(b).sum())
+        if net:
+            for v, a, b in zip("hqz", states["surrogate"], states["fp64"]):
+                res[f"l1_surrogate_vs_fp64_{v}"] = float(np.abs(a - b).sum() / np.abs(b).sum())
         if n <= n_oracle_max:
             cfg = O.make_cfg(n, P.x_min, P.x_max, P.cfl, O.grass(P.Ag, xi=P.xi), P.bc_left, P.bc_right)
             t0 = time.perf_counter()
@@ -660,6 +770,11 @@ def main():
                                                          / np.abs(b - a0).sum())
             accuracy[f"l1_rel_state_{name}"] = float(np.abs(a - b).sum() / np.abs(b).sum())
 
+    # measured peaks of the FP32, MUFU and FP64 pipes (the ALU rooflines' denominators)
+    peaks = None
+    if rank == 0 and not args.no_peaks:
+        peaks = measure_pipes(adot, local)
+
     # batched ensemble: 4096 movable-bed Riemann channels, N_c log-uniform in [1e3, 1e5]
     ensemble = None
     if args.ensemble_t_end > 0 and rank == 0:
@@ -689,7 +804,7 @@ def main():
     # aggradation case (Sec. 5.1: friction, sediment feed, q_s = alpha u^5) as printed
     friction = None
     if args.friction_steps > 0 and rank == 0:
-        friction = friction_leg(args, adot, W, P, n, stream, dev, local, time_steps, value)
+        friction = friction_leg(args, adot, W, P, n, stream, dev, local, time_steps, value, peaks)
 
     # second-order MUSCL-Hancock variant on the benchmark workload
     order2 = None
@@ -701,12 +816,26 @@ def main():
     if args.price_steps > 0 and rank == 0:
         price = price_leg(args, adot, P, n, stream, local, time_steps, value)
 
+    # trans-critical bump at N = 1e6: fixed bed, Grass and MPM
+    config3 = None
+    if args.config3_steps > 0 and rank == 0:
+        config3 = config3_leg(args, adot, W, stream, local, time_steps)
+
+    # t_end errors of the smooth problem over a bounded size sweep (with the
+    # trained surrogate when its leg runs)
+    sweep_fn = None
+    if args.l1_sweep_kmax >= 0 and rank == 0:
+        def sweep_fn(net):
+            return l1_sweep(adot, W, stream, local, args.l1_sweep_kmax, args.l1_sweep_oracle_max, net)
+
     # learned |A|_Psi surrogate: harvest, train, then drive the benchmark workload
     surrogate = None
     if args.sur_steps > 0 and rank == 0:
-        surrogate = surrogate_leg(args, adot, W, P, n, stream, dev, local, time_steps, ref64)
+        surrogate = surrogate_leg(args, adot, W, P, n, stream, dev, local, time_steps, ref64, sweep_fn)
+    sweep = surrogate.pop("_sweep", None) if surrogate else None
+    if sweep is None and sweep_fn is not None:
+        sweep = sweep_fn(None)
 
-    sweep = l1_sweep(adot, W, stream, local) if (args.l1_sweep and rank == 0) else None
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -718,9 +847,19 @@ def main():
 
     solver.close()
     if rank == 0:
-        f_peak = 152 * 128 * 2 * (2070e6) / 1e12  # FP32 FMA peak at the maximum SM clock, TFLOP/s
+        f_derived = 152 * 128 * 2 * (2070e6) / 1e12  # FP32 FMA peak at the maximum SM clock, TFLOP/s
+        f_peak = peaks["ffma_tflops"] if peaks else f_derived
         kind = "warp" if kern == 2 else "block"
-        achieved = FLOPS_PER_CELL_UPDATE[kind] * n / per_launch_s / 1e12
+        kc = counts(kind, block, max(reg_cap, 0))
+        achieved = FLOPS_PER_CELL_UPDATE_PLAN * n / per_launch_s / 1e12
+        achieved_exec = kc["flops"] * n / per_launch_s / 1e12 if kc.get("flops") else None
+        xu = None
+        if peaks and kc.get("xu"):
+            xr = kc["xu"] * n / per_launch_s / 1e12
+            xu = {"ops_per_cell_update": kc["xu"], "achieved": xr,
+                  "peak": peaks["mufu_rsq_tops"], "unit": "T ops/s", "frac": xr / peaks["mufu_rsq_tops"],
+                  "note": "XU-pipe thread instructions (ncu sm__inst_executed_pipe_xu x 32 / cells) "
+                          "over the measured MUFU rsqrt rate"}
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -734,18 +873,27 @@ def main():
                        "parallelism": "replicas" if ws > 1 else "single"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": f_peak, "unit": "TFLOP/s",
                          "frac": achieved / f_peak,
-                         "traffic": (DRAM_BYTES_PER_CELL_UPDATE[kind] * n
-                                     if DRAM_BYTES_PER_CELL_UPDATE[kind] else None),
+                         "flops_per_cell_update": FLOPS_PER_CELL_UPDATE_PLAN,
+                         "flops_basis": "planning estimate: 3 nodes x ~130 FP32-pipe instructions + "
+                                        "~20, 700-800 flops with FMA = 2 (midpoint)",
+                         "achieved_executed": achieved_exec,
+                         "frac_executed": achieved_exec / f_peak if achieved_exec else None,
+                         "flops_per_cell_update_executed": kc.get("flops"),
+                         "executed_basis": "ncu FFMA x 2 + FADD + FMUL thread instructions of the "
+                                           "-DADOT_SCALAR_NODES build per updated cell",
+                         "traffic": kc["dram"] * n if kc.get("dram") else None,
                          "traffic_note": "ncu dram read+write of one launch at N=4e6, scaled to N",
                          "kernel": f"{'k_step_warp' if kern == 2 else 'k_step'}<float,GRASS,{block},{max(reg_cap, 0)}>",
-                         "peak_source": "152 SM x 128 FP32 lanes x 2 x 2070 MHz (derived)",
+                         "peak_source": ("measured: adot_measure_pipe FFMA (peaks.ffma_tflops)" if peaks
+                                         else "152 SM x 128 FP32 lanes x 2 x 2070 MHz (derived)"),
+                         "peak_derived": f_derived, "xu": xu,
                          "hbm_achieved_gbs": BYTES_PER_CELL_UPDATE * n / per_launch_s / 1e9,
                          "hbm_peak_gbs": measured_peaks().get("hbm_gbs", 6800.0),
-                         "issue_slots": issue_roofline(kind, n, per_launch_s)},
+                         "issue_slots": issue_roofline(kc.get("instr"), n, per_launch_s)},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps, "clocks": clocks,
             "accuracy": accuracy, "sim_time_after_timed_steps": t_sim, "variants": variants,
             "ensemble": ensemble, "surrogate": surrogate, "friction": friction, "order2": order2,
-            "price_c": price,
+            "price_c": price, "config3": config3, "peaks": peaks,
             "l1_t_end_sweep": sweep,
         }
         print(json.dumps(line), flush=True)

@@ -448,6 +448,18 @@ adot_status adot_harvest(adot_ctx* ctx, int64_t n, uint64_t seed, float* X, floa
 adot_status adot_step_noalloc(const adot_config* cfg, double* h, double* q, double* z,
                               int64_t n_steps, double* t_io, void* cuda_stream);
 
+/* Throughput probe of one arithmetic pipe on a device (no counterpart in the
+ * paper): the measured peaks that the step kernels' rooflines divide by. A
+ * resident grid (8 blocks of 256 threads per SM) runs 8 independent chains
+ * per thread; one warm-up launch, then one timed launch (CUDA events, tens of
+ * milliseconds). kind: 0 = float32 FFMA (2 flops each), 1 = paired float32
+ * FFMA2 (4 flops), 2 = MUFU reciprocal square root, 3 = MUFU sine (1 op each),
+ * 4 = float64 DFMA (2 flops). *rate_out: flops (or ops) per second;
+ * *seconds_out (may be NULL): the timed launch. device >= 0 is made current.
+ * Allocates and frees a small result buffer and a stream.
+ * ADOT_E_INVALID_ARG for another kind or a NULL rate_out. */
+adot_status adot_measure_pipe(int kind, int device, double* rate_out, double* seconds_out);
+
 /* Name of a status code (static string). */
 const char* adot_status_string(adot_status s);
 

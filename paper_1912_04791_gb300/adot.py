@@ -120,6 +120,7 @@ def lib() -> ctypes.CDLL:
             "adot_ensemble_query": ([_P, _P, _P, ctypes.POINTER(i64)], i32),
             "adot_ensemble_info": ([_P, ctypes.POINTER(i32), ctypes.POINTER(i64),
                                     ctypes.POINTER(i32), ctypes.POINTER(i32)], i32),
+            "adot_measure_pipe": ([i32, i32, _D, _D], i32),
             "adot_status_string": ([i32], ctypes.c_char_p),
             "adot_version": ([], ctypes.c_char_p),
         }
@@ -588,6 +589,18 @@ def adot_precision_stats(ctx: int):
     a, b = ctypes.c_int64(), ctypes.c_int64()
     _check(lib().adot_precision_stats(ctx, ctypes.byref(a), ctypes.byref(b)), "adot_precision_stats")
     return a.value, b.value
+
+
+PIPE_FFMA, PIPE_FFMA2, PIPE_RSQ, PIPE_SIN, PIPE_DFMA = range(5)
+
+
+def adot_measure_pipe(kind: int, device: int = -1):
+    """(rate, seconds) of one pipe-throughput probe: flops/s for FFMA, FFMA2
+    and DFMA, ops/s for the multi-function-unit kinds."""
+    r, sec = ctypes.c_double(), ctypes.c_double()
+    _check(lib().adot_measure_pipe(int(kind), int(device), ctypes.byref(r), ctypes.byref(sec)),
+           "adot_measure_pipe")
+    return r.value, sec.value
 
 
 def adot_conserved_sums(ctx: int) -> np.ndarray:

@@ -19,12 +19,15 @@ LIB_PATH = os.path.join(HERE, "libadot.so")
 SOURCES = ["adot_step_f32.cu", "adot_step_f64.cu", "adot_step_f32_ext.cu", "adot_step_f64_ext.cu",
            "adot_step2_f32.cu", "adot_step2_f64.cu", "adot_step_price.cu",
            "adot_aux.cu", "adot_capi.cu",
-           "adot_noalloc.cu", "adot_ensemble.cu", "adot_mlp.cu"]
+           "adot_noalloc.cu", "adot_ensemble.cu", "adot_mlp.cu", "adot_peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # -ftz / -prec-div / -prec-sqrt relax float32 only (denormals flushed, division and
 # square root to ~2 ulp); float64 arithmetic is unaffected.
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-v",
               "--expt-relaxed-constexpr", "-ftz=true", "-prec-div=false", "-prec-sqrt=false"]
+# Extra nvcc arguments for measurement builds, e.g. ADOT_NVCC_EXTRA=-DADOT_SCALAR_NODES for the
+# all-scalar float32 node path whose per-opcode ncu counters give the executed flop count.
+NVCC_FLAGS += os.environ.get("ADOT_NVCC_EXTRA", "").split()
 
 
 def nvcc() -> str:

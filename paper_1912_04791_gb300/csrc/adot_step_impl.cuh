@@ -195,10 +195,21 @@ __device__ __forceinline__ R warp_max(R v) {
   return v;
 }
 
+// Whether float32 edges evaluate the two outer Gauss-Legendre nodes in paired
+// float32x2 instructions. Building with -DADOT_SCALAR_NODES gives the all-scalar
+// form, whose per-opcode instruction counters (which do not count paired
+// instructions) give the kernels' executed float32 flops; the arithmetic is the
+// same, only the rounding order of the outer nodes differs.
+#ifdef ADOT_SCALAR_NODES
+constexpr bool kPairedNodes = false;
+#else
+constexpr bool kPairedNodes = true;
+#endif
+
 // D-/+ of one edge from its two states. PAIRED: float32 edges take the
 // paired-instruction form of the two outer nodes (fewer issue slots, more
 // registers); the ensemble kernel, held to 64 registers, keeps the scalar form.
-template <typename R, int LAW, bool PAIRED = true>
+template <typename R, int LAW, bool PAIRED = kPairedNodes>
 __device__ __forceinline__ void edge_fluct(const StepParams& p, const typename Prec<R>::S wl[3],
                                            const typename Prec<R>::S wr[3], R dm[3], R dp[3],
                                            unsigned& flags) {

@@ -322,10 +322,12 @@ def test_surrogate_eval_matches_network_on_state_edges(gpu, trained_smooth_net):
 
 
 def test_trained_surrogate_step(gpu):
-    """A network trained on edges harvested from the smooth periodic problem
-    drives the same problem: the state stays finite, few edges fall back, and
-    the increment over 50 steps stays within 5e-2 (L1, relative) of the
-    oracle's; the analytic path's error is reported next to it."""
+    """A network trained briefly (1500 steps) on edges harvested from the smooth
+    periodic problem drives the same problem: the state stays finite, few edges
+    fall back, and the increment over 50 steps stays within 5e-2 (L1, relative)
+    of the oracle's, while the analytic FP32 path's increment, computed on the
+    same state, stays within 1e-5. The trained-to-convergence network is held
+    to 1e-3 at t_end in tests/test_gpu_surrogate_gain.py."""
     P = W.smooth_periodic(4096)
     with gpu.Solver(gpu.config_for(P, gpu.FP32)) as s:
         s.set_state(P.h, P.q, P.z)
@@ -350,8 +352,13 @@ def test_trained_surrogate_step(gpu):
             edges, fb = gpu.adot_surrogate_stats(s.ctx)
     assert np.isfinite(hs).all() and edges == 50 * 4097
     assert fb / edges < 0.05
-    for a, b, a0 in ((hs, ho, P.h), (qs, qo, P.q), (zs, zo, P.z)):
+    with gpu.Solver(gpu.config_for(P, gpu.FP32)) as s:
+        s.set_state(P.h, P.q, P.z)
+        s.step(50)
+        ha, qa, za = s.get_state()
+    for a, c, b, a0 in ((hs, ha, ho, P.h), (qs, qa, qo, P.q), (zs, za, zo, P.z)):
         assert np.abs((a - a0) - (b - a0)).sum() <= 5e-2 * np.abs(b - a0).sum()
+        assert np.abs((c - a0) - (b - a0)).sum() <= 1e-5 * np.abs(b - a0).sum()
 
 
 def test_adam_update_matches_reference(gpu):
