@@ -40,12 +40,12 @@ UNIT = "cell-updates/s"
 #  xu:    XU-pipe thread instructions per cell-update (sm__inst_executed_pipe_xu x 32 / cells);
 #  dram:  dram__bytes_read.sum + dram__bytes_write.sum per cell-update.
 KERNEL_COUNTS = {
-    ("warp", 256, 80): {"flops": (2 * 564.42e6 + 304.15e6 + 565.16e6) / 4e6 * (1 - 3648 / 4e6),
-                        "instr": 81.809e6 * 32 / 4e6, "xu": 4.147e6 * 32 / 4e6,
-                        "dram": (98.44e6 + 57.48e6) / 4e6},
-    ("warp", 256, 64): {"flops": 493.0, "instr": 84.74e6 * 32 / 4e6, "xu": None,
-                        "dram": (99.54e6 + 62.40e6) / 4e6},
-    ("order2", 256, 64): {"flops": None, "instr": 131.54e6 * 32 / 4e6, "xu": None, "dram": None},
+    ("warp", 256, 80): {"flops": (2 * 500.39e6 + 344.19e6 + 609.19e6) / 4e6 * (1 - 3648 / 4e6),
+                        "instr": 73.305e6 * 32 / 4e6, "xu": 3.5214e6 * 32 / 4e6,
+                        "dram": (97.95e6 + 56.53e6) / 4e6},
+    ("warp", 256, 64): {"flops": None, "instr": 75.432e6 * 32 / 4e6, "xu": 3.5286e6 * 32 / 4e6,
+                        "dram": (98.55e6 + 59.74e6) / 4e6},
+    ("order2", 256, 64): {"flops": None, "instr": None, "xu": None, "dram": None},
 }
 # The block kernel's all-scalar count (1 edge in 256 evaluated twice, removed).
 FLOPS_BLOCK = 498.6

@@ -64,8 +64,8 @@ typedef enum {
 typedef enum {
   ADOT_FP64 = 0, /* everything in float64 */
   ADOT_FP32 = 1  /* state as float-float (two float32 per value, updated with TwoSum);
-                    fluctuations in float32; the cubic-root solve and |A| dW of a node
-                    redone in float64 when 1 - arg^2 < 1e-4 (near-coalescent roots) */
+                    fluctuations in float32; an edge with a quadrature node where
+                    1 - arg^2 < 1e-4 (near-coalescent roots) redone in float64 */
 } adot_precision;
 
 /* Jump function of Eq. scheme. */
@@ -237,11 +237,12 @@ adot_status adot_autotune(adot_ctx* ctx, int64_t trial_steps, int32_t* block_out
 
 /* Precision diagnostic of the current state (not a step): *nodes_out (may be
  * NULL) receives the quadrature nodes of one step, 3 per edge (edges 0..n, or
- * 0..n-1 when periodic); *fp64_nodes_out (may be NULL) how many of them the
- * float32 step kernels redo in float64 because the roots of Eq. lambda nearly
- * coalesce (1 - arg^2 < 1e-4 with arg = k2 / sqrt(4 k1^3), Eq. parameters, or
- * arg not finite), by the same float32 test on the same node values, run in a
- * separate kernel. ADOT_FP64 contexts report 0. Waits for the stream.
+ * 0..n-1 when periodic); *fp64_nodes_out (may be NULL) how many of them fail
+ * the float32 step kernels' test for nearly coalescing roots of Eq. lambda
+ * (1 - arg^2 < 1e-4 with arg = k2 / sqrt(4 k1^3), Eq. parameters, or arg not
+ * finite), by the same float32 test on the same node values, run in a
+ * separate kernel; an edge with such a node is redone in float64 by the step.
+ * ADOT_FP64 contexts report 0. Waits for the stream.
  * ADOT_E_INVALID_ARG before a state was set. */
 adot_status adot_precision_stats(adot_ctx* ctx, int64_t* nodes_out, int64_t* fp64_nodes_out);
 

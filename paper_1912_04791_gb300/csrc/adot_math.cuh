@@ -8,15 +8,16 @@
 //   step 3  the trigonometric roots of the characteristic polynomial
 //           (Eq. charPol, Eq. lambda);
 //   steps 4-5  |A| dW = R |Lambda| R^-1 dW (Eq. asbA, Eq. RR, Eq. RR-1).
-// Steps 4-5 are evaluated matrix-free, |A| dW = sum_i |l_i| r_i (l_i . dW),
-// which is the same product as the paper's three-matrix form applied to dW.
-// The three denominators d_i = (l_i - l_j)(l_i - l_k) share one reciprocal of
-// (l1-l2)(l1-l3)(l2-l3). The three cosines cos(phi/3 -+ pi/3), cos(phi/3) of
+// Steps 4-5 are evaluated matrix-free through one spectral projector (see
+// abs_A_times_proj), which is the same product as the paper's three-matrix
+// form applied to dW. The three cosines cos(phi/3 -+ pi/3), cos(phi/3) of
 // Eq. lambda come from one sincos through cos(x -+ pi/3) = C/2 +- (sqrt3/2) S.
 #pragma once
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <type_traits>
 
 namespace adot {
 
@@ -154,18 +155,21 @@ struct Eig {
   T u, c, c2, inv_c2, a, b;
   T l1, l2, l3;  // l1 <= l2 <= l3
   T arg;         // k2 / sqrt(4 k1^3) before clamping
-  int ks;        // index (1..3) of the root of smallest magnitude
 };
 
 __device__ __forceinline__ float d_fdiv(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ double d_fdiv(double a, double b) { return a / b; }
 
-// Steps 1-3: derivatives, k1, k2, phi, and the three roots of Eq. lambda.
-// The root of smallest magnitude comes out of Eq. lambda as a difference of
-// two O(c) terms; with ACCURATE it is recomputed from the product of the
-// roots, l1 l2 l3 = c^2 a (the constant term of Eq. charPol times c^3), so
-// that it keeps full relative precision.
-template <typename T, int LAW, bool ACCURATE = true>
+// Steps 1-3: derivatives, k1, k2, phi, and the three roots of Eq. lambda. A
+// root of small magnitude comes out of Eq. lambda as a difference of two O(c)
+// terms. In float64 the root of smallest magnitude is recomputed from the
+// product of the roots, l1 l2 l3 = c^2 a (the constant term of Eq. charPol
+// times c^3), unless the other two roots' product is zero (a double root at
+// 0): a fixed bed (a = 0) then has its zero root exactly, so the projector's
+// choice in abs_A_times_proj does not follow the sign of rounding noise. In
+// float32 only the projector's own root is recomputed, where |A| dW needs it
+// (abs_A_times_proj), which saves a division and a selection per node.
+template <typename T, int LAW>
 __device__ __forceinline__ void node_eig(const LawT<T>& L, T h, T q, Eig<T>& e) {
   const T inv_h = T(1) / h;
   const T u = q * inv_h;
@@ -187,36 +191,29 @@ __device__ __forceinline__ void node_eig(const LawT<T>& L, T h, T q, Eig<T>& e) 
   const T F = T(2.0 / 3.0) * Fr;
   const T hc = T(0.5) * C;
   const T hs = T(0.86602540378443864676) * S;  // (sqrt 3 / 2) S
-  T l1 = c * (F - m * (hc + hs));  // cos(phi/3 - pi/3) = C/2 + (sqrt3/2) S
-  T l2 = c * (F - m * (hc - hs));  // cos(phi/3 + pi/3) = C/2 - (sqrt3/2) S
-  T l3 = c * (F + m * C);
-  e.ks = 0;
-  if (ACCURATE) {
-    // The quotient is never less accurate than the trigonometric value; it is
-    // skipped only when the other two roots' product is zero (a double root
-    // at 0, e.g. a fixed bed exactly at |Fr| = 1).
-    const T m1 = d_abs(l1), m2 = d_abs(l2), m3 = d_abs(l3);
-    const T ca = c2 * a;
-    if (m1 <= m2 && m1 <= m3) {
-      const T pr = l2 * l3;
-      if (pr != T(0)) l1 = ca / pr;
-      e.ks = 1;
-    } else if (m2 <= m3) {
-      const T pr = l1 * l3;
-      if (pr != T(0)) l2 = ca / pr;
-      e.ks = 2;
-    } else {
-      const T pr = l1 * l2;
-      if (pr != T(0)) l3 = ca / pr;
-      e.ks = 3;
-    }
-  }
   e.u = u;
   e.c = c;
   e.c2 = c2;
   e.inv_c2 = rc * rc;
   e.a = a;
   e.b = b;
+  T l1 = c * (F - m * (hc + hs));  // cos(phi/3 - pi/3) = C/2 + (sqrt3/2) S
+  T l2 = c * (F - m * (hc - hs));  // cos(phi/3 + pi/3) = C/2 - (sqrt3/2) S
+  T l3 = c * (F + m * C);
+  if constexpr (std::is_same<T, double>::value) {
+    const T m1 = d_abs(l1), m2 = d_abs(l2), m3 = d_abs(l3);
+    const T ca = c2 * a;
+    if (m1 <= m2 && m1 <= m3) {
+      const T pr = l2 * l3;
+      if (pr != T(0)) l1 = ca / pr;
+    } else if (m2 <= m3) {
+      const T pr = l1 * l3;
+      if (pr != T(0)) l2 = ca / pr;
+    } else {
+      const T pr = l1 * l2;
+      if (pr != T(0)) l3 = ca / pr;
+    }
+  }
   e.l1 = l1;
   e.l2 = l2;
   e.l3 = l3;
@@ -241,34 +238,50 @@ __device__ __forceinline__ void A_times(const Eig<T>& e, T v0, T v1, T v2, T& y0
 // The entries are evaluated through identities of the roots of Eq. charPol,
 // l^3 - 2u l^2 - (c^2 - u^2 + c^2 b) l - c^2 a = 0, which avoid cancelling O(c)
 // terms: c^2 - u^2 + l_j l_k = l_k (l_k - 2u) - c^2 b (pair products), 2u - l_j - l_k =
-// l_k (sum of roots), and (u - l_k)^2/c^2 - 1 = b + a / l_k unless l_k is the root of
-// smallest magnitude. y = A dW.
+// l_k (sum of roots), and (u - l_k)^2/c^2 - 1 = b + a / l_k.
+// The root of smallest magnitude is l_k or l2 (|l_f| >= |l2| for the far root
+// l_f). When it is l_k (near critical flow), l_k is taken from the product of
+// the roots, l1 l2 l3 = c^2 a, so that it keeps its relative precision (in
+// float64 node_eig has done so already), and the third entry of r_k from its
+// definition (b + a / l_k would divide by it); the product is skipped when
+// l2 l_f = 0 (a double root at 0). When it is l2, its absolute error of a few
+// ulp of c (float32) enters only d_k through l_k - l2 and the choice of k, and
+// either choice gives the same |A| up to |l2| |P2 dW|.
+// The other case takes one reciprocal for both quotients: m p_k / d_k and
+// m p_k (b l_k + a) / (d_k l_k). y = A dW.
 template <typename T>
 __device__ __forceinline__ void abs_A_times_proj(const Eig<T>& e, T dh, T dq, T dz, const T y[3],
                                                  T x[3]) {
   const bool lo = e.l2 >= T(0);
-  const T lk = lo ? e.l1 : e.l3;
+  T lk = lo ? e.l1 : e.l3;
   const T lf = lo ? e.l3 : e.l1;  // the root on the far side
-  const T m2 = T(-2) * (lo ? d_min(e.l1, T(0)) : d_max(e.l3, T(0)));
+  const bool small = d_abs(lk) <= d_abs(e.l2);
+  if (small) {
+    const T pr = e.l2 * lf;
+    if (pr != T(0)) lk = e.c2 * e.a / pr;
+  }
+  const T m2 = T(-2) * (lo ? d_min(lk, T(0)) : d_max(lk, T(0)));
   const T dk = (lk - e.l2) * (lk - lf);
   const T pk = (lk * (lk - T(2) * e.u) - e.c2 * e.b) * dh + lk * dq + e.c2 * dz;  // (l_k . dW) d_k
-  const int kk = lo ? 1 : 3;
-  T rk;
-  if (e.ks == kk || e.ks == 0) {
+  const T mp = m2 * pk;
+  T coef, c2nd;
+  if (small) {
+    coef = d_fdiv(mp, dk);
     const T v = e.u - lk;
-    rk = v * v * e.inv_c2 - T(1);
+    c2nd = coef * (v * v * e.inv_c2 - T(1));
   } else {
-    rk = e.b + d_fdiv(e.a, lk);
+    const T inv = d_fdiv(T(1), dk * lk);
+    coef = mp * lk * inv;
+    c2nd = mp * (e.b * lk + e.a) * inv;
   }
-  const T coef = m2 * d_fdiv(pk, dk);
   if (lo) {
     x[0] = y[0] + coef;
     x[1] = y[1] + coef * lk;
-    x[2] = y[2] + coef * rk;
+    x[2] = y[2] + c2nd;
   } else {
     x[0] = -(y[0] + coef);
     x[1] = -(y[1] + coef * lk);
-    x[2] = -(y[2] + coef * rk);
+    x[2] = -(y[2] + c2nd);
   }
 }
 
@@ -366,7 +379,7 @@ __device__ __forceinline__ void node_f32(const LawT<float>& L, const LawT<double
 template <typename T, int LAW>
 __device__ __forceinline__ T spectral_radius(const LawT<T>& L, T h, T q) {
   Eig<T> e;
-  node_eig<T, LAW, false>(L, h, q, e);
+  node_eig<T, LAW>(L, h, q, e);
   return d_max(d_abs(e.l1), d_abs(e.l3));
 }
 
@@ -384,7 +397,8 @@ __device__ __noinline__ float spectral_radius_f32_trig(const LawT<float>& L, flo
 // u >= 0. p'' = 6l - 4u > 0 on [u + c, inf), so when p(u + c) <= 0 and
 // p'(u + c) > 0 Newton's method from u + c (the root when a = b = 0) converges
 // monotonically after its first step to the only root in [u + c, inf), the
-// largest. Four steps are taken; if the start does not meet those conditions
+// largest. At most four steps are taken (fewer once a correction falls below
+// 1e-7 of the root); if the start does not meet those conditions
 // (strong transport, b > ~2) or the last correction is not below 1e-5 of the
 // root, the roots of Eq. lambda are used instead.
 template <int LAW>
@@ -409,6 +423,9 @@ __device__ __forceinline__ float spectral_radius_f32(const LawT<float>& L, float
   for (int it = 0; it < 4; ++it) {
     d = __fdividef(pv, dp);
     l -= d;
+    // quadratic convergence: once a correction is below 1e-7 of the root the
+    // next one is below float rounding, so the iteration stops
+    if (fabsf(d) <= 1e-7f * l) break;
     pv = ((l - tu) * l - K) * l - ca;
     dp = (3.0f * l - fu) * l - K;
   }

@@ -6,8 +6,8 @@
 // root, arccos and sincos steps and the choice of the root taken from the
 // product of the roots stay per lane. The midpoint node takes the scalar path.
 // The arithmetic is that of node_f32 (Eq. charPol/lambda, Eq. RR, RR-1,
-// Eq. asbA through one spectral projector), with the same identities and the
-// same float64 redo of a node whose roots nearly coalesce.
+// Eq. asbA through one spectral projector), with the same identities; an edge
+// with a node whose roots nearly coalesce is redone in float64 as a whole.
 #pragma once
 
 #include "adot_math.cuh"
@@ -33,26 +33,7 @@ struct Eig2 {
   float2 u, c2, inv_c2, na, b;  // na = -a
   float2 l1, l2, l3;
   float2 arg;
-  int ks0, ks1;
 };
-
-// The root of smallest magnitude of one lane from l1 l2 l3 = c^2 a (as in node_eig).
-__device__ __forceinline__ int vieta_lane(float& l1, float& l2, float& l3, float ca) {
-  const float m1 = fabsf(l1), m2 = fabsf(l2), m3 = fabsf(l3);
-  if (m1 <= m2 && m1 <= m3) {
-    const float pr = l2 * l3;
-    if (pr != 0.0f) l1 = ca / pr;
-    return 1;
-  }
-  if (m2 <= m3) {
-    const float pr = l1 * l3;
-    if (pr != 0.0f) l2 = ca / pr;
-    return 2;
-  }
-  const float pr = l1 * l2;
-  if (pr != 0.0f) l3 = ca / pr;
-  return 3;
-}
 
 // Steps 1-3 of node_eig for two states.
 template <int LAW>
@@ -90,12 +71,9 @@ __device__ __forceinline__ void node_eig_x2(const LawT<float>& L, float2 h, floa
   const float2 F = mul2(p2((float)(2.0 / 3.0)), Fr);
   const float2 hc = mul2(p2(0.5f), C);
   const float2 hs = mul2(p2(0.86602540378443864676f), S);  // (sqrt 3 / 2) S
-  float2 l1 = mul2(c, fma2(nm, add2(hc, hs), F));  // cos(phi/3 - pi/3) = C/2 + (sqrt3/2) S
-  float2 l2 = mul2(c, fma2(nm, sub2(hc, hs), F));  // cos(phi/3 + pi/3) = C/2 - (sqrt3/2) S
-  float2 l3 = mul2(c, fma2(m, C, F));
-  const float2 nca = mul2(c2, na);  // -c^2 a
-  e.ks0 = vieta_lane(l1.x, l2.x, l3.x, -nca.x);
-  e.ks1 = vieta_lane(l1.y, l2.y, l3.y, -nca.y);
+  const float2 l1 = mul2(c, fma2(nm, add2(hc, hs), F));  // cos(phi/3 - pi/3) = C/2 + (sqrt3/2) S
+  const float2 l2 = mul2(c, fma2(nm, sub2(hc, hs), F));  // cos(phi/3 + pi/3) = C/2 - (sqrt3/2) S
+  const float2 l3 = mul2(c, fma2(m, C, F));
   e.u = u;
   e.c2 = c2;
   e.inv_c2 = mul2(rc, rc);
@@ -115,40 +93,93 @@ __device__ __forceinline__ void A_times_x2(const Eig2& e, float dh, float dq, fl
   y[2] = fma2(e.na, p2(-dh), mul2(e.b, p2(dq)));
 }
 
+// The projector's root of one lane when it is the root of smallest magnitude
+// (see abs_A_times_proj): from the product of the roots, l1 l2 l3 = c^2 a,
+// unless l2 l_f = 0.
+__device__ __forceinline__ float small_root(float lk, float l2, float lf, float c2, float na) {
+  const float pr = l2 * lf;
+  return (pr != 0.0f) ? -(c2 * na) / pr : lk;
+}
+
 // |A| dW for two states through one projector each, as abs_A_times_proj: the
-// projector's root (l1 or l3) and the sign are chosen per lane.
+// projector's root (l1 or l3), the sign and the small-root case are chosen per
+// lane; one reciprocal per lane serves both quotients.
 __device__ __forceinline__ void abs_A_times_proj_x2(const Eig2& e, float dh, float dq, float dz,
                                                     const float2 y[3], float2 x[3]) {
   const bool lox = e.l2.x >= 0.0f, loy = e.l2.y >= 0.0f;
-  const float2 lk = make_float2(lox ? e.l1.x : e.l3.x, loy ? e.l1.y : e.l3.y);
+  float2 lk = make_float2(lox ? e.l1.x : e.l3.x, loy ? e.l1.y : e.l3.y);
   const float2 lf = make_float2(lox ? e.l3.x : e.l1.x, loy ? e.l3.y : e.l1.y);
-  const float2 m2 = make_float2(lox ? -2.0f * fminf(e.l1.x, 0.0f) : -2.0f * fmaxf(e.l3.x, 0.0f),
-                                loy ? -2.0f * fminf(e.l1.y, 0.0f) : -2.0f * fmaxf(e.l3.y, 0.0f));
+  const bool smx = fabsf(lk.x) <= fabsf(e.l2.x), smy = fabsf(lk.y) <= fabsf(e.l2.y);
+  if (smx) lk.x = small_root(lk.x, e.l2.x, lf.x, e.c2.x, e.na.x);
+  if (smy) lk.y = small_root(lk.y, e.l2.y, lf.y, e.c2.y, e.na.y);
+  const float2 m2 = make_float2(lox ? -2.0f * fminf(lk.x, 0.0f) : -2.0f * fmaxf(lk.x, 0.0f),
+                                loy ? -2.0f * fminf(lk.y, 0.0f) : -2.0f * fmaxf(lk.y, 0.0f));
   const float2 sg = make_float2(lox ? 1.0f : -1.0f, loy ? 1.0f : -1.0f);
   const float2 dk = mul2(sub2(lk, e.l2), sub2(lk, lf));
   // (l_k . dW) d_k = (l_k (l_k - 2u) - c^2 b) dh + l_k dq + c^2 dz
   const float2 ntu = mul2(e.u, p2(-2.0f));
   const float2 czb = mul2(e.c2, fma2(e.b, p2(-dh), p2(dz)));
   const float2 pk = fma2(mul2(lk, add2(lk, ntu)), p2(dh), fma2(lk, p2(dq), czb));
-  // third entry of r_k: b + a / l_k = b - na / l_k, or directly for the root of smallest magnitude
-  float2 rk = fma2(e.na, nrcp2(lk), e.b);
-  if (e.ks0 == (lox ? 1 : 3)) {
-    const float v = e.u.x - lk.x;
-    rk.x = v * v * e.inv_c2.x - 1.0f;
-  }
-  if (e.ks1 == (loy ? 1 : 3)) {
-    const float v = e.u.y - lk.y;
-    rk.y = v * v * e.inv_c2.y - 1.0f;
-  }
-  const float2 coef = mul2(m2, mul2(pk, rcp2(dk)));
+  const float2 mp = mul2(m2, pk);
+  // small root: coef = m p_k / d_k, third entry of r_k = (u - l_k)^2 / c^2 - 1;
+  // otherwise coef = m p_k l_k / (d_k l_k), coef r_k = m p_k (b l_k + a) / (d_k l_k)
+  const float2 den = make_float2(smx ? dk.x : dk.x * lk.x, smy ? dk.y : dk.y * lk.y);
+  const float2 inv = rcp2(den);
+  const float2 coef = mul2(mp, make_float2(smx ? inv.x : lk.x * inv.x, smy ? inv.y : lk.y * inv.y));
+  const float2 vk = sub2(e.u, lk);
+  const float2 rdirect = fma2(mul2(vk, vk), e.inv_c2, p2(-1.0f));
+  const float2 rquot = mul2(mul2(mp, fma2(e.b, lk, mul2(e.na, p2(-1.0f)))), inv);
+  const float2 c2nd = make_float2(smx ? coef.x * rdirect.x : rquot.x,
+                                  smy ? coef.y * rdirect.y : rquot.y);
   x[0] = mul2(sg, add2(y[0], coef));
   x[1] = mul2(sg, fma2(coef, lk, y[1]));
-  x[2] = mul2(sg, fma2(coef, rk, y[2]));
+  x[2] = mul2(sg, add2(y[2], c2nd));
+}
+
+// Fluctuations of one edge, all in float64 (see edge_fluct_f32x2).
+struct EdgeD {
+  float dm[3], dp[3];
+  unsigned flags;
+};
+
+// The float64 redo of a float32 edge: the float-float states summed to
+// float64, the three nodes of Eq. DOTjumpN by node_f64 (the Newton form near
+// coalescence, the non-hyperbolic flag), D-/+ rounded to float32. Kept out of
+// line and called from one place, after the float32 nodes, with the states
+// passed by value and the result returned by value, so that the float32 path
+// around it keeps its values in registers.
+template <int LAW>
+__device__ __noinline__ EdgeD edge_fluct_f64_redo(const LawT<double>& Ld, float2 l0, float2 l1,
+                                                  float2 l2, float2 r0, float2 r1, float2 r2) {
+  const double hl = ff_to_double(l0), ql = ff_to_double(l1), zl = ff_to_double(l2);
+  const double dh = ff_to_double(r0) - hl, dq = ff_to_double(r1) - ql, dz = ff_to_double(r2) - zl;
+  double ya[3] = {0.0, 0.0, 0.0}, xa[3] = {0.0, 0.0, 0.0};
+  EdgeD out;
+  out.flags = 0u;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const double sk = (k == 0) ? GL3_S0 : ((k == 1) ? 0.5 : GL3_S2);
+    const double w = (k == 1) ? GL3_W1 : GL3_W0;
+    double y[3], x[3];
+    node_f64<LAW>(Ld, hl + sk * dh, ql + sk * dq, dh, dq, dz, y, x, out.flags);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      ya[r] += w * y[r];
+      xa[r] += w * x[r];
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    out.dm[r] = (float)(0.5 * (ya[r] - xa[r]));
+    out.dp[r] = (float)(0.5 * (ya[r] + xa[r]));
+  }
+  return out;
 }
 
 // D-/+ of one float32 edge (float-float states wl, wr): nodes s0 and s2 paired,
-// the midpoint node scalar, each node redone in float64 when 1 - arg^2 <
-// TAU_FP64_FALLBACK (or arg is not finite).
+// the midpoint node scalar. When any node has 1 - arg^2 < TAU_FP64_FALLBACK
+// (or arg not finite), i.e. two roots nearly coalesce, the whole edge is
+// redone in float64 (edge_fluct_f64_redo).
 template <int LAW>
 __device__ __forceinline__ void edge_fluct_f32x2(const LawT<float>& L, const LawT<double>& Ld,
                                                  const float2 wl[3], const float2 wr[3], float dm[3],
@@ -165,27 +196,24 @@ __device__ __forceinline__ void edge_fluct_f32x2(const LawT<float>& L, const Law
   float2 y[3], x[3];
   A_times_x2(e, dh, dq, dz, y);
   abs_A_times_proj_x2(e, dh, dq, dz, y, x);
-  const float2 delta = make_float2(fmaf(-e.arg.x, e.arg.x, 1.0f), fmaf(-e.arg.y, e.arg.y, 1.0f));
-  if (!(delta.x >= TAU_FP64_FALLBACK)) {
-    float yy[3], xx[3];
-    node_f64_fallback<LAW>(Ld, h.x, q.x, dh, dq, dz, yy, xx, &flags);
-#pragma unroll
-    for (int r = 0; r < 3; ++r) {
-      y[r].x = yy[r];
-      x[r].x = xx[r];
-    }
-  }
-  if (!(delta.y >= TAU_FP64_FALLBACK)) {
-    float yy[3], xx[3];
-    node_f64_fallback<LAW>(Ld, h.y, q.y, dh, dq, dz, yy, xx, &flags);
-#pragma unroll
-    for (int r = 0; r < 3; ++r) {
-      y[r].y = yy[r];
-      x[r].y = xx[r];
-    }
-  }
+  Eig<float> em;
+  node_eig<float, LAW>(L, h0 + 0.5f * dh, q0 + 0.5f * dq, em);
   float ym[3], xm[3];
-  node_f32<LAW>(L, Ld, h0 + 0.5f * dh, q0 + 0.5f * dq, dh, dq, dz, ym, xm, flags);
+  A_times(em, dh, dq, dz, ym[0], ym[1], ym[2]);
+  abs_A_times_proj(em, dh, dq, dz, ym, xm);
+  const bool redo = !(fmaf(-e.arg.x, e.arg.x, 1.0f) >= TAU_FP64_FALLBACK) ||
+                    !(fmaf(-e.arg.y, e.arg.y, 1.0f) >= TAU_FP64_FALLBACK) ||
+                    !(fmaf(-em.arg, em.arg, 1.0f) >= TAU_FP64_FALLBACK);
+  if (redo) {
+    const EdgeD d = edge_fluct_f64_redo<LAW>(Ld, wl[0], wl[1], wl[2], wr[0], wr[1], wr[2]);
+    flags |= d.flags;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      dm[r] = d.dm[r];
+      dp[r] = d.dp[r];
+    }
+    return;
+  }
   const float w0 = (float)GL3_W0, w1 = (float)GL3_W1;
 #pragma unroll
   for (int r = 0; r < 3; ++r) {

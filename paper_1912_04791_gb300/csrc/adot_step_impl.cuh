@@ -44,7 +44,9 @@ struct Prec<float> {
   __device__ static __forceinline__ double from_bits(unsigned long long b) {
     return (double)__uint_as_float((unsigned)b);
   }
-  __device__ static __forceinline__ bool finite(S a) { return isfinite(a.x) && isfinite(a.y); }
+  // A NaN or infinity in the low word reaches the high word: set_state stores
+  // lo = (float)(d - hi) of a finite d, and ff_add forms hi = s + lo.
+  __device__ static __forceinline__ bool finite(S a) { return isfinite(a.x); }
   template <int LAW>
   __device__ static __forceinline__ void node(const StepParams& p, float h, float q, float dh,
                                               float dq, float dz, float y[3], float x[3],
