@@ -341,39 +341,6 @@ __device__ __forceinline__ void node_f64(const LawT<double>& L, double h, double
     abs_A_times_proj(e, dh, dq, dz, y, x);
 }
 
-// Float64 redo of a float32 node (kept out of line so that its registers do
-// not weigh on the float32 fast path).
-template <int LAW>
-__device__ __noinline__ void node_f64_fallback(const LawT<double>& L, float h, float q, float dh,
-                                               float dq, float dz, float* y, float* x,
-                                               unsigned* flags) {
-  double yd[3], xd[3];
-  unsigned f = 0;
-  node_f64<LAW>(L, (double)h, (double)q, (double)dh, (double)dq, (double)dz, yd, xd, f);
-  *flags |= f;
-  for (int r = 0; r < 3; ++r) {
-    y[r] = (float)yd[r];
-    x[r] = (float)xd[r];
-  }
-}
-
-// Float32 node with the float64 redo when 1 - arg^2 < TAU_FP64_FALLBACK (or
-// arg is not finite).
-template <int LAW>
-__device__ __forceinline__ void node_f32(const LawT<float>& L, const LawT<double>& Ld, float h,
-                                         float q, float dh, float dq, float dz, float y[3],
-                                         float x[3], unsigned& flags) {
-  Eig<float> e;
-  node_eig<float, LAW>(L, h, q, e);
-  const float delta = 1.0f - e.arg * e.arg;
-  if (!(delta >= TAU_FP64_FALLBACK)) {
-    node_f64_fallback<LAW>(Ld, h, q, dh, dq, dz, y, x, &flags);
-    return;
-  }
-  A_times(e, dh, dq, dz, y[0], y[1], y[2]);
-  abs_A_times_proj(e, dh, dq, dz, y, x);
-}
-
 // Spectral radius max(|l1|, |l3|) at a state (float64: from Eq. lambda; the
 // extreme roots need no small-root correction).
 template <typename T, int LAW>

@@ -5,7 +5,7 @@
 // __ffma2_rn: one issue slot for two lanes of work). The reciprocal, square
 // root, arccos and sincos steps and the choice of the root taken from the
 // product of the roots stay per lane. The midpoint node takes the scalar path.
-// The arithmetic is that of node_f32 (Eq. charPol/lambda, Eq. RR, RR-1,
+// The arithmetic is that of the scalar nodes (Eq. charPol/lambda, Eq. RR, RR-1,
 // Eq. asbA through one spectral projector), with the same identities; an edge
 // with a node whose roots nearly coalesce is redone in float64 as a whole.
 #pragma once

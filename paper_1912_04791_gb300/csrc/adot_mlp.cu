@@ -1828,6 +1828,11 @@ struct adot_mlp {
   int train_engine;    // training kernels: 0 = tcgen05 (default), 1 = mma.sync
   int inject;          // adot_mlp_inject_fault: 1 = the next pipelined launch withholds a commit
   unsigned* d_status;  // sticky ST_* bits of the fused inference kernels
+  // the backward pass forks each weight gradient onto a side stream as soon as
+  // its output gradient exists, and joins it before returning
+  cudaStream_t side;
+  cudaEvent_t ev_fork[kLayers];
+  cudaEvent_t ev_join;
 };
 
 namespace {
@@ -1958,22 +1963,39 @@ cudaError_t forward_batch(adot_mlp* m, int64_t B, cudaStream_t s) {
   return layer<128, 16, EPI_LINEAR>(m, m->H[3], Wl(m, 4), bl(m, 4), nullptr, m->Y, nullptr, B, s);
 }
 
+// The backward pass. The output gradients run as a chain on s (output layer,
+// then hidden layers 3, 2, 1, each needing the previous one); the weight
+// gradient of a layer needs only that layer's output gradient and its stored
+// input activation, so each is forked onto the side stream as soon as its
+// output gradient is written, and runs beside the rest of the chain; the side
+// stream is joined into s before returning. Under stream capture this forms
+// parallel branches of the training graph.
 cudaError_t backward_batch(adot_mlp* m, int64_t B, cudaStream_t s) {
   cudaError_t e;
   const int lg = (int)((B + 255) / 256);
+  const int nch = (int)((B + train_chunk(m) - 1) / train_chunk(m));
+  auto fork = [&](int k) -> cudaError_t {
+    cudaError_t r = cudaEventRecord(m->ev_fork[k], s);
+    return r == cudaSuccess ? cudaStreamWaitEvent(m->side, m->ev_fork[k], 0) : r;
+  };
   k_loss<<<lg, 256, 0, s>>>(m->Y, m->Tb, B, m->dY, m->loss_part);
   if ((e = cudaGetLastError())) return e;
+  if ((e = fork(4))) return e;
+  wgrad<128, 16>(m, m->dY, m->H[3], m->pW[4], m->pB[4], B, nch, m->side);
   if ((e = layer<16, 128, EPI_BWD>(m, m->dY, Wtl(m, 4), nullptr, m->Z[3], m->dZ[3], nullptr, B, s)))
     return e;
-  for (int l = 3; l >= 1; --l)
+  for (int l = 3; l >= 1; --l) {
+    if ((e = fork(l))) return e;
+    wgrad<128, 128>(m, m->dZ[l], m->H[l - 1], m->pW[l], m->pB[l], B, nch, m->side);
     if ((e = layer<128, 128, EPI_BWD>(m, m->dZ[l], Wtl(m, l), nullptr, m->Z[l - 1], m->dZ[l - 1], nullptr,
                                       B, s)))
       return e;
-  const int nch = (int)((B + train_chunk(m) - 1) / train_chunk(m));
-  wgrad<128, 16>(m, m->dY, m->H[3], m->pW[4], m->pB[4], B, nch, s);
-  for (int l = 3; l >= 1; --l) wgrad<128, 128>(m, m->dZ[l], m->H[l - 1], m->pW[l], m->pB[l], B, nch, s);
-  wgrad<16, 128>(m, m->dZ[0], m->Xb, m->pW[0], m->pB[0], B, nch, s);
-  return cudaGetLastError();
+  }
+  if ((e = fork(0))) return e;
+  wgrad<16, 128>(m, m->dZ[0], m->Xb, m->pW[0], m->pB[0], B, nch, m->side);
+  if ((e = cudaGetLastError())) return e;
+  if ((e = cudaEventRecord(m->ev_join, m->side))) return e;
+  return cudaStreamWaitEvent(s, m->ev_join, 0);
 }
 
 AdamArgs adam_args(const adot_mlp* m, int64_t B) {
@@ -2026,6 +2048,10 @@ void mlp_free(adot_mlp* m) {
     if (m->pW[l]) cudaFree(m->pW[l]);
     if (m->pB[l]) cudaFree(m->pB[l]);
   }
+  for (int l = 0; l < kLayers; ++l)
+    if (m->ev_fork[l]) cudaEventDestroy(m->ev_fork[l]);
+  if (m->ev_join) cudaEventDestroy(m->ev_join);
+  if (m->side) cudaStreamDestroy(m->side);
   if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
   delete m;
 }
@@ -2107,6 +2133,10 @@ adot_status adot_mlp_create(int64_t max_batch, void* cuda_stream, adot_mlp** out
     e = cudaStreamCreateWithFlags(&m->stream, cudaStreamNonBlocking);
     m->own_stream = true;
   }
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&m->side, cudaStreamNonBlocking);
+  for (int l = 0; l < kLayers && e == cudaSuccess; ++l)
+    e = cudaEventCreateWithFlags(&m->ev_fork[l], cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->ev_join, cudaEventDisableTiming);
   const int64_t B = m->max_batch;
   const int nch = (int)((B + m->chunk - 1) / m->chunk);
   auto al = [&](void** p, size_t bytes) {

@@ -47,12 +47,6 @@ struct Prec<float> {
   // A NaN or infinity in the low word reaches the high word: set_state stores
   // lo = (float)(d - hi) of a finite d, and ff_add forms hi = s + lo.
   __device__ static __forceinline__ bool finite(S a) { return isfinite(a.x); }
-  template <int LAW>
-  __device__ static __forceinline__ void node(const StepParams& p, float h, float q, float dh,
-                                              float dq, float dz, float y[3], float x[3],
-                                              unsigned& flags) {
-    node_f32<LAW>(p.lf, p.ld, h, q, dh, dq, dz, y, x, flags);
-  }
   __device__ static __forceinline__ const LawT<float>& law(const StepParams& p) { return p.lf; }
   template <int LAW>
   __device__ static __forceinline__ float rho(const StepParams& p, float h, float q) {
@@ -75,12 +69,6 @@ struct Prec<double> {
     return __longlong_as_double((long long)b);
   }
   __device__ static __forceinline__ bool finite(S a) { return isfinite(a); }
-  template <int LAW>
-  __device__ static __forceinline__ void node(const StepParams& p, double h, double q, double dh,
-                                              double dq, double dz, double y[3], double x[3],
-                                              unsigned& flags) {
-    node_f64<LAW>(p.ld, h, q, dh, dq, dz, y, x, flags);
-  }
   __device__ static __forceinline__ const LawT<double>& law(const StepParams& p) { return p.ld; }
   template <int LAW>
   __device__ static __forceinline__ double rho(const StepParams& p, double h, double q) {
@@ -218,28 +206,67 @@ __device__ __forceinline__ void edge_fluct(const StepParams& p, const typename P
   if constexpr (PAIRED && std::is_same<R, float>::value) {
     edge_fluct_f32x2<LAW>(p.lf, p.ld, wl, wr, dm, dp, flags);
     return;
-  }
-  const R dh = Prec<R>::diff(wr[0], wl[0]);
-  const R dq = Prec<R>::diff(wr[1], wl[1]);
-  const R dz = Prec<R>::diff(wr[2], wl[2]);
-  const R h0 = Prec<R>::hi(wl[0]), q0 = Prec<R>::hi(wl[1]);
-  R ya[3] = {R(0), R(0), R(0)}, xa[3] = {R(0), R(0), R(0)};
+  } else if constexpr (std::is_same<R, float>::value) {
+    // all-scalar float32 nodes; as in edge_fluct_f32x2, an edge with a node
+    // whose roots nearly coalesce is redone in float64 as a whole
+    const float dh = ff_diff(wr[0], wl[0]), dq = ff_diff(wr[1], wl[1]), dz = ff_diff(wr[2], wl[2]);
+    const float h0 = wl[0].x, q0 = wl[1].x;
+    float ya[3] = {0.0f, 0.0f, 0.0f}, xa[3] = {0.0f, 0.0f, 0.0f};
+    bool redo = false;
 #pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    const R s = (k == 0) ? R(GL3_S0) : ((k == 1) ? R(0.5) : R(GL3_S2));
-    const R w = (k == 1) ? R(GL3_W1) : R(GL3_W0);
-    R y[3], x[3];
-    Prec<R>::template node<LAW>(p, h0 + s * dh, q0 + s * dq, dh, dq, dz, y, x, flags);
+    for (int k = 0; k < 3; ++k) {
+      const float sk = (k == 0) ? (float)GL3_S0 : ((k == 1) ? 0.5f : (float)GL3_S2);
+      const float w = (k == 1) ? (float)GL3_W1 : (float)GL3_W0;
+      Eig<float> e;
+      node_eig<float, LAW>(p.lf, h0 + sk * dh, q0 + sk * dq, e);
+      redo = redo || !(fmaf(-e.arg, e.arg, 1.0f) >= TAU_FP64_FALLBACK);
+      float y[3], x[3];
+      A_times(e, dh, dq, dz, y[0], y[1], y[2]);
+      abs_A_times_proj(e, dh, dq, dz, y, x);
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        ya[r] += w * y[r];
+        xa[r] += w * x[r];
+      }
+    }
+    if (redo) {
+      const EdgeD d = edge_fluct_f64_redo<LAW>(p.ld, wl[0], wl[1], wl[2], wr[0], wr[1], wr[2]);
+      flags |= d.flags;
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        dm[r] = d.dm[r];
+        dp[r] = d.dp[r];
+      }
+      return;
+    }
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
-      ya[r] += w * y[r];
-      xa[r] += w * x[r];
+      dm[r] = 0.5f * (ya[r] - xa[r]);
+      dp[r] = 0.5f * (ya[r] + xa[r]);
     }
-  }
+  } else {
+    const R dh = Prec<R>::diff(wr[0], wl[0]);
+    const R dq = Prec<R>::diff(wr[1], wl[1]);
+    const R dz = Prec<R>::diff(wr[2], wl[2]);
+    const R h0 = Prec<R>::hi(wl[0]), q0 = Prec<R>::hi(wl[1]);
+    R ya[3] = {R(0), R(0), R(0)}, xa[3] = {R(0), R(0), R(0)};
 #pragma unroll
-  for (int r = 0; r < 3; ++r) {
-    dm[r] = R(0.5) * (ya[r] - xa[r]);
-    dp[r] = R(0.5) * (ya[r] + xa[r]);
+    for (int k = 0; k < 3; ++k) {
+      const R s = (k == 0) ? R(GL3_S0) : ((k == 1) ? R(0.5) : R(GL3_S2));
+      const R w = (k == 1) ? R(GL3_W1) : R(GL3_W0);
+      R y[3], x[3];
+      node_f64<LAW>(p.ld, h0 + s * dh, q0 + s * dq, dh, dq, dz, y, x, flags);
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        ya[r] += w * y[r];
+        xa[r] += w * x[r];
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      dm[r] = R(0.5) * (ya[r] - xa[r]);
+      dp[r] = R(0.5) * (ya[r] + xa[r]);
+    }
   }
 }
 
