@@ -843,8 +843,9 @@ __device__ __forceinline__ uint32_t gelu2x_bf16(uint32_t a0, uint32_t a1, uint32
 // absA [9][n+1] (NaN in row 0 marks a fallback edge). Otherwise: inputs are
 // rows of X [n][16] bf16 (standardised), outputs Y [n][16] float32; with TRAIN
 // the hidden layers' pre-activations z = acc + b and activations GELU(z) also
-// go to P.trZ / P.trH (bf16, [n][128]) for the backward pass of training (the
-// stored activation 2 GELU(z) halved, an exact scaling).
+// go to P.trZ / P.trH (bf16, [n][128] chunk-major as described in the training
+// section) for the backward pass of training (the stored activation 2 GELU(z)
+// halved, an exact scaling).
 template <bool EDGES, bool TRAIN = false>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_mlp_tc(const InferParams P, const StepParams sp, const StateF32 st, int slot,
@@ -1003,12 +1004,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 hk[2 * j + e] = *reinterpret_cast<const uint32_t*>(&g);
               }
             }
-            uint4* zd = reinterpret_cast<uint4*>(P.trZ[l] + item * kHid + c);
-            uint4* hd = reinterpret_cast<uint4*>(P.trH[l] + item * kHid + c);
+            // chunk-major [n][128] (see the training section): a warp's rows are contiguous
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-              zd[u] = make_uint4(zk[4 * u], zk[4 * u + 1], zk[4 * u + 2], zk[4 * u + 3]);
-              hd[u] = make_uint4(hk[4 * u], hk[4 * u + 1], hk[4 * u + 2], hk[4 * u + 3]);
+              const int64_t o = ((int64_t)(c / 8 + u) * n_items + item) * 8;
+              *reinterpret_cast<uint4*>(P.trZ[l] + o) = make_uint4(zk[4 * u], zk[4 * u + 1], zk[4 * u + 2], zk[4 * u + 3]);
+              *reinterpret_cast<uint4*>(P.trH[l] + o) = make_uint4(hk[4 * u], hk[4 * u + 1], hk[4 * u + 2], hk[4 * u + 3]);
             }
           }
         }
@@ -1070,6 +1071,19 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
 // --------------------------------------------------------------------------
 // training on the 5th-generation tensor cores
+//
+// The 128-column intermediates of this engine's training step (the hidden
+// layers' pre-activations Z, activations H and output gradients dZ) are stored
+// chunk-major: 8-column chunks, and within a chunk the rows one after another,
+// element (r, c) of an n-row matrix at ((c / 8) n + r) 8 + c % 8. Their kernels
+// keep one row per thread (one accumulator lane of tensor memory per row), so
+// a warp's 16-byte accesses to one chunk cover 512 contiguous bytes; in a
+// row-major layout each such access touched 32 rows 256 B apart. The
+// 16-column matrices shared with the mma.sync engine (the input batch and the
+// output-layer gradient) stay row-major.
+__device__ __forceinline__ int64_t cm_off(int64_t r, int c, int64_t n) {
+  return ((int64_t)(c >> 3) * n + r) * 8 + (c & 7);
+}
 // --------------------------------------------------------------------------
 // k_tc_layer: the backward layer products of k_layer (EPI_BWD), dZprev =
 // (A S^T) * gelu'(Zprev) with A = dZ and S = W^T, on the 5th-generation tensor
@@ -1119,11 +1133,11 @@ __device__ __forceinline__ void cp_async_wait_all() {
 // Backward epilogue of 16 accumulator columns c0 .. c0+15 of one row:
 // dZprev = C * gelu'(Zprev) (bf16), as k_layer's EPI_BWD.
 template <int N>
-__device__ __forceinline__ void tc_layer_bwd16(const uint32_t* v, int c0, int64_t row,
+__device__ __forceinline__ void tc_layer_bwd16(const uint32_t* v, int c0, int64_t row, int64_t rows,
                                                const __nv_bfloat16* __restrict__ aux,
                                                __nv_bfloat16* __restrict__ out) {
-  const uint4* zs = reinterpret_cast<const uint4*>(aux + row * N + c0);
-  const uint4 za = zs[0], zb = zs[1];
+  const uint4 za = *reinterpret_cast<const uint4*>(aux + cm_off(row, c0, rows));
+  const uint4 zb = *reinterpret_cast<const uint4*>(aux + cm_off(row, c0 + 8, rows));
   const uint32_t zw[8] = {za.x, za.y, za.z, za.w, zb.x, zb.y, zb.z, zb.w};
   uint32_t o[8];
 #pragma unroll
@@ -1132,9 +1146,8 @@ __device__ __forceinline__ void tc_layer_bwd16(const uint32_t* v, int c0, int64_
     o[j] = pack_bf16(__uint_as_float(v[2 * j]) * gelu_prime_f(__bfloat162float(zz.x)),
                      __uint_as_float(v[2 * j + 1]) * gelu_prime_f(__bfloat162float(zz.y)));
   }
-  uint4* od = reinterpret_cast<uint4*>(out + row * N + c0);
-  od[0] = make_uint4(o[0], o[1], o[2], o[3]);
-  od[1] = make_uint4(o[4], o[5], o[6], o[7]);
+  *reinterpret_cast<uint4*>(out + cm_off(row, c0, rows)) = make_uint4(o[0], o[1], o[2], o[3]);
+  *reinterpret_cast<uint4*>(out + cm_off(row, c0 + 8, rows)) = make_uint4(o[4], o[5], o[6], o[7]);
 }
 
 template <int K, int N>
@@ -1162,11 +1175,14 @@ __global__ void __launch_bounds__(kTlThreads, 4) k_tc_layer(const __nv_bfloat16*
     const int r = i / KC, kc = i % KC;
     cp_async16(sS + tc_canon(r, kc, K), S + (int64_t)(n0 + r) * K + kc * 8, 16u);
   }
+  // A: the output-layer gradient row-major [rows][16] (K = 16), a hidden layer's
+  // chunk-major [rows][128] (K = 128), read with consecutive threads on
+  // consecutive rows of one chunk
   for (int i = tid; i < kTcRows * KC; i += kTlThreads) {
-    const int r = i / KC, kc = i % KC;
+    const int r = (K == kHid) ? i % kTcRows : i / KC, kc = (K == kHid) ? i / kTcRows : i % KC;
     const bool valid = row0 + r < rows;
-    cp_async16(base + tc_canon(r, kc, K), valid ? (const void*)(A + (row0 + r) * K + kc * 8) : (const void*)A,
-               valid ? 16u : 0u);
+    const __nv_bfloat16* src = (K == kHid) ? A + cm_off(row0 + r, kc * 8, rows) : A + (row0 + r) * K + kc * 8;
+    cp_async16(base + tc_canon(r, kc, K), valid ? (const void*)src : (const void*)A, valid ? 16u : 0u);
   }
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&s_mbar)) : "memory");
@@ -1201,9 +1217,9 @@ __global__ void __launch_bounds__(kTlThreads, 4) k_tc_layer(const __nv_bfloat16*
       tmem_ld_x16(t_row + (uint32_t)cb, va);
       tmem_wait_ld16(va);
       tmem_ld_x16(t_row + (uint32_t)(cb + 16), vb);
-      if (row < rows) tc_layer_bwd16<N>(va, n0 + cb, row, aux, out);
+      if (row < rows) tc_layer_bwd16<N>(va, n0 + cb, row, rows, aux, out);
       tmem_wait_ld16(vb);
-      if (row < rows) tc_layer_bwd16<N>(vb, n0 + cb + 16, row, aux, out);
+      if (row < rows) tc_layer_bwd16<N>(vb, n0 + cb + 16, row, rows, aux, out);
     }
   } else if (tid == 0) {
     mbar_wait_bounded(mbar, 0);
@@ -1248,16 +1264,19 @@ __host__ __device__ constexpr size_t tc_wgrad_smem() {
 // dst[c][p, p + 1] (one 32-bit word per column: the two rows' values).
 template <int C, int NP>
 __device__ __forceinline__ void tc_scatter_rows(const __nv_bfloat16* __restrict__ src, int64_t ra,
-                                                int64_t rb, int64_t c1, int part, unsigned char* dst,
-                                                int p) {
+                                                int64_t rb, int64_t c1, int64_t rows, int part,
+                                                unsigned char* dst, int p) {
   constexpr int NJ = C / (8 * NP);  // 8-column groups in a part
   static_assert(NJ >= 1 && NJ * 8 * NP == C, "columns per part");
   uint4 va[NJ], vb[NJ];
 #pragma unroll
   for (int j = 0; j < NJ; ++j) {
     const int c0 = part * (C / NP) + 8 * j;
-    va[j] = (ra < c1) ? *reinterpret_cast<const uint4*>(src + ra * C + c0) : make_uint4(0, 0, 0, 0);
-    vb[j] = (rb < c1) ? *reinterpret_cast<const uint4*>(src + rb * C + c0) : make_uint4(0, 0, 0, 0);
+    // 128-column operands are chunk-major, 16-column ones row-major
+    const int64_t oa = (C == kHid) ? cm_off(ra, c0, rows) : ra * C + c0;
+    const int64_t ob = (C == kHid) ? cm_off(rb, c0, rows) : rb * C + c0;
+    va[j] = (ra < c1) ? *reinterpret_cast<const uint4*>(src + oa) : make_uint4(0, 0, 0, 0);
+    vb[j] = (rb < c1) ? *reinterpret_cast<const uint4*>(src + ob) : make_uint4(0, 0, 0, 0);
   }
 #pragma unroll
   for (int j = 0; j < NJ; ++j) {
@@ -1337,13 +1356,13 @@ __global__ void __launch_bounds__(kTwThreads) k_tc_wgrad(const __nv_bfloat16* __
     // dZ rows ra, rb -> sDz[n][pr, pr + 1] for n in this thread's half of 0 .. N-1,
     // then X rows ra, rb -> sX[k][pr, pr + 1]; each operand's loads are issued together
     if constexpr (N >= 32)
-      tc_scatter_rows<N, 4>(dZ, ra, rb, c1, part, sDz, pr);
+      tc_scatter_rows<N, 4>(dZ, ra, rb, c1, rows, part, sDz, pr);
     else if (part < 2)
-      tc_scatter_rows<N, 2>(dZ, ra, rb, c1, part, sDz, pr);
+      tc_scatter_rows<N, 2>(dZ, ra, rb, c1, rows, part, sDz, pr);
     if constexpr (K >= 32)
-      tc_scatter_rows<K, 4>(X, ra, rb, c1, part, sX, pr);
+      tc_scatter_rows<K, 4>(X, ra, rb, c1, rows, part, sX, pr);
     else if (part < 2)
-      tc_scatter_rows<K, 2>(X, ra, rb, c1, part, sX, pr);
+      tc_scatter_rows<K, 2>(X, ra, rb, c1, rows, part, sX, pr);
     fence_async_smem();
     tc_fence_before();
     __syncthreads();
