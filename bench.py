@@ -102,8 +102,11 @@ def parse():
                     help="oracle steps on the full workload for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--ensemble-t-end", type=float, default=0.02,
-                    help="t_end of the 4096-channel ensemble measurement (0 = skip)")
+    ap.add_argument("--ensemble-t-end", type=float, default=0.1,
+                    help="t_end of the 4096-channel ensemble measurement, a tenth of the "
+                         "workload's 1 s (0 = skip)")
+    ap.add_argument("--ensemble-per-step", type=int, default=1,
+                    help="also time the per-step form of the ensemble (0 = skip)")
     ap.add_argument("--sur-steps", type=int, default=20000,
                     help="training steps of the |A|_Psi surrogate at batch 65536 (0 = skip the leg)")
     ap.add_argument("--sur-samples", type=int, default=50_000_000,
@@ -779,26 +782,34 @@ def main():
     ensemble = None
     if args.ensemble_t_end > 0 and rank == 0:
         E = W.riemann_ensemble(4096)
-        with adot.Ensemble.from_workload(E, adot.FP32, device=local, stream=stream) as ens:
-            ens.set_state(E.h, E.q, E.z)
-            blk, n_tiles, grid, ens_kernel = ens.info()
-            torch.cuda.synchronize(dev)
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            launches = ens.run_to(args.ensemble_t_end)
-            b.record(stream)
-            torch.cuda.synchronize(dev)
-            t_c, steps_c, cu = ens.query()
-            ms_e = a.elapsed_time(b)
+        forms = [0] + ([4] if args.ensemble_per_step else [])
+        runs = {}
+        for kern in forms:
+            with adot.Ensemble.from_workload(E, adot.FP32, device=local, stream=stream,
+                                             step_kernel=kern) as ens:
+                ens.set_state(E.h, E.q, E.z)
+                blk, n_tiles, grid, ens_kernel = ens.info()
+                torch.cuda.synchronize(dev)
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                launches = ens.run_to(args.ensemble_t_end)
+                b.record(stream)
+                torch.cuda.synchronize(dev)
+                t_c, steps_c, cu = ens.query()
+                ms_e = a.elapsed_time(b)
+            name = {1: "per-step block tiles", 2: "per-step warp tiles",
+                    3: "persistent channel loops"}[ens_kernel]
+            runs[kern] = {"form": name, "cell_updates": int(cu), "seconds": ms_e * 1e-3,
+                          "cell_updates_per_s": cu / (ms_e * 1e-3), "launches": int(launches),
+                          "max_steps": int(steps_c.max()), "min_steps": int(steps_c.min()),
+                          "threads_per_block": blk,
+                          ("channels" if ens_kernel == 3 else "tiles"): n_tiles, "grid": grid,
+                          "all_at_t_end": bool((t_c == args.ensemble_t_end).all())}
         ensemble = {"workload": "4096 movable-bed Riemann channels, N_c log-uniform [1e3,1e5], FP32",
-                    "total_cells": int(E.n_cells.sum()), "t_end": args.ensemble_t_end,
-                    "cell_updates": int(cu), "seconds": ms_e * 1e-3,
-                    "cell_updates_per_s": cu / (ms_e * 1e-3), "launches": int(launches),
-                    "max_steps": int(steps_c.max()), "min_steps": int(steps_c.min()),
-                    "step_kernel": "warp tiles" if ens_kernel == 2 else "block",
-                    "tile_threads": blk, "tiles": n_tiles, "grid": grid,
-                    "all_at_t_end": bool((t_c == args.ensemble_t_end).all())}
+                    "total_cells": int(E.n_cells.sum()), "t_end": args.ensemble_t_end, **runs[0]}
+        if 4 in runs:
+            ensemble["other_form"] = runs[4]
 
     # Strickler friction source (Sec. 2) on the benchmark workload, and the Soni
     # aggradation case (Sec. 5.1: friction, sediment feed, q_s = alpha u^5) as printed

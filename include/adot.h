@@ -256,8 +256,15 @@ adot_status adot_conserved_sums(adot_ctx* ctx, double sums_out[3]);
  * (reading of the unstated CFL rule as for a single channel), Grass law
  * (Eq. Grass) with a per-channel A_g, transmissive ends. The channels' cells lie
  * end to end in the state arrays: channel c owns cells off[c] .. off[c+1]-1 with
- * off[c] = n_cells[0] + ... + n_cells[c-1]. One kernel launch advances every
- * running channel by one of its own steps; channels stop at t_end individually. */
+ * off[c] = n_cells[0] + ... + n_cells[c-1]. Channels stop at t_end individually.
+ *
+ * Two forms run the channels. Persistent channel loops (the default): one launch
+ * per run_to (per 16384 steps of the longest-running channel); each CTA takes
+ * whole channels from a device queue, largest estimated work (N_c rho_c / dx_c)
+ * first, and steps each to t_end in a device-side loop with one block barrier
+ * per step; no CTA waits on another. Per-step launches: one launch (captured in
+ * CUDA graphs) advances every running channel by one of its own steps, over a
+ * tile list of all channels. Both evaluate the same edges and cells. */
 typedef struct {
   int32_t n_channels;       /* >= 1 */
   const int64_t* n_cells;   /* host [n_channels], each >= 1 */
@@ -265,12 +272,16 @@ typedef struct {
   const double* Ag;         /* host [n_channels], Grass coefficient [s^2/m] */
   double g, xi, cfl;        /* shared: gravity, 1/(1-p), CFL number in (0, 1] */
   int32_t precision;        /* ADOT_FP64 or ADOT_FP32 (float-float state) */
-  int32_t block_threads;    /* threads per block: 128, 256, 512 (block kernel: tile =
-                               block_threads - 1 cells; warp tiles: 256 only); 0 = autotuned */
-  int32_t steps_per_graph;  /* launches captured per CUDA graph; 0 = default (48) */
+  int32_t block_threads;    /* threads per block. Persistent channel loops: 256, 384, 512
+                               or 768 (0 = 384). Per-step: 128, 256, 512 (block kernel:
+                               tile = block_threads - 1 cells; warp tiles: 256 only);
+                               0 = autotuned */
+  int32_t steps_per_graph;  /* per-step launches captured per CUDA graph; 0 = default (48) */
   int32_t device;           /* CUDA device ordinal; -1 = current */
-  int32_t step_kernel;      /* 1 = block kernel, 2 = persistent warp tiles (31 cells per tile,
-                               shuffle exchange, no block barrier); 0 = autotuned */
+  int32_t step_kernel;      /* 0 or 3 = persistent channel loops (default); per-step launches:
+                               1 = block kernel, 2 = persistent warp tiles (31 cells per tile,
+                               shuffle exchange, no block barrier), 4 = the faster of 1 and 2
+                               by trial launches */
 } adot_ensemble_config;
 
 typedef struct adot_ensemble adot_ensemble;
@@ -284,15 +295,20 @@ void adot_ensemble_destroy(adot_ensemble* ens);
 
 /* Copies in the concatenated float64 state (sum n_cells values each, host or
  * device per on_device), puts every channel at t = 0 with no steps taken and
- * computes each channel's first CFL maximum. With block_threads = 0 the first
- * call times the tile sizes (two trial launches each, state unchanged). */
+ * computes each channel's first CFL maximum (persistent form: and orders the
+ * channel queue by estimated work). Per-step form with block_threads = 0: the
+ * first call times the tile sizes (two trial launches each, state unchanged). */
 adot_status adot_ensemble_set_state(adot_ensemble* ens, const double* h, const double* q,
                                     const double* z, int on_device);
 adot_status adot_ensemble_get_state(adot_ensemble* ens, double* h, double* q, double* z,
                                     int on_device);
 
 /* Advances every channel until its own time reaches t_end (last step shortened
- * to land on it). *launches_out (may be NULL): kernel launches issued. */
+ * to land on it). *launches_out (may be NULL): step-kernel launches issued. The
+ * persistent form continues channels that reached an earlier t_end; the
+ * per-step form leaves a channel frozen once it has reached one (until the next
+ * set_state). A non-finite value or non-positive depth ends the call with its
+ * status (persistent form: every CTA stops after its current step). */
 adot_status adot_ensemble_run_to(adot_ensemble* ens, double t_end, int64_t* launches_out);
 
 /* Advances every channel by n_steps of its own steps (no end time). */
@@ -303,8 +319,9 @@ adot_status adot_ensemble_step(adot_ensemble* ens, int64_t n_steps);
 adot_status adot_ensemble_query(adot_ensemble* ens, double* t_out, int64_t* steps_out,
                                 int64_t* cell_updates_out);
 
-/* Variant in use: threads per block, number of tiles, the resident grid and
- * the step kernel (1 block, 2 warp tiles); NULL pointers are skipped. */
+/* Variant in use: threads per block, number of tiles (persistent form: of
+ * channels), the resident grid and the step kernel (1 block, 2 warp tiles,
+ * 3 persistent channel loops); NULL pointers are skipped. */
 adot_status adot_ensemble_info(adot_ensemble* ens, int32_t* block_out, int64_t* tiles_out,
                                int32_t* grid_out, int32_t* step_kernel_out);
 

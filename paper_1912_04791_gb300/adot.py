@@ -343,7 +343,10 @@ def adot_step_noalloc(cfg: Config, h, q, z, n_steps: int, t0: float = 0.0, strea
 
 
 class Ensemble:
-    """Owning wrapper around an adot_ensemble (batched independent channels)."""
+    """Owning wrapper around an adot_ensemble (batched independent channels).
+
+    step_kernel: 0 or 3 persistent channel loops (default), 1 per-step block
+    kernel, 2 per-step warp tiles, 4 per-step, the faster of 1 and 2."""
 
     def __init__(self, n_cells, length, Ag, xi, cfl=0.9, g=9.81, precision=FP32, block_threads=0,
                  steps_per_graph=0, device=-1, stream=None, step_kernel=0):

@@ -49,6 +49,7 @@ struct EnsDev {
   int* active;       // [3] tile bound
   double* t_end;     // scalar
   unsigned* status;  // scalar
+  int* next;         // channel queue head of the persistent form
 };
 
 struct EnsParams {
@@ -216,6 +217,68 @@ __global__ void __launch_bounds__(B, 65536 / (B * 64))
   if (flags) atomicOr(p.d.status, flags);
 }
 
+// One sub-tile of a channel: lane l evaluates edge e0 + l (cells e0 + l - 1
+// and e0 + l, copies at the ends) and lanes 1..31 update cells e0 .. e0 + 30
+// with D+ of the left edge by shuffle. mode 0 steps with nu = dt/dx and folds
+// the new cells' CFL maxima into rho; mode 1 copies the cells across.
+template <typename R, int CAP>
+__device__ __forceinline__ void ens_subtile(const StepParams& lp, const typename Prec<R>::State& in,
+                                            const typename Prec<R>::State& out, const int64_t base,
+                                            const int64_t nc, const int64_t e0, const int lane,
+                                            const R nu, const int mode, R& rho, unsigned& flags) {
+  using S = typename Prec<R>::S;
+  const int64_t e = e0 + lane;
+    // states of edge e: cells e-1 and e, each lane loading both (a right
+    // state taken from the next lane by shuffle measured 4 % slower: every
+    // lane then waits for its neighbour's load); transmissive ends copy the
+    // adjacent cell, lanes past the channel's end read its last cell
+    const bool valid = e <= nc;
+    S wl[3], wr[3];
+    const int64_t il = (e > 0) ? (e <= nc ? e - 1 : nc - 1) : 0;
+    const int64_t ir = (e < nc) ? e : nc - 1;
+    wl[0] = in.h[base + il];
+    wl[1] = in.q[base + il];
+    wl[2] = in.z[base + il];
+    wr[0] = in.h[base + ir];
+    wr[1] = in.q[base + ir];
+    wr[2] = in.z[base + ir];
+    const int64_t i = e - 1;  // cell updated by this lane (lanes 1..31)
+    if (mode == 1) {
+      if (lane >= 1 && i < nc) {
+        out.h[base + i] = wl[0];
+        out.q[base + i] = wl[1];
+        out.z[base + i] = wl[2];
+      }
+      return;
+    }
+    R dm[3] = {R(0), R(0), R(0)}, dp[3] = {R(0), R(0), R(0)};
+    // the paired-node float32 form where the register cap leaves it room
+    if (valid && e > 0 && e < nc) edge_fluct<R, LAW_GRASS, (CAP >= 80)>(lp, wl, wr, dm, dp, flags);
+    R dpl[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) dpl[r] = __shfl_up_sync(0xffffffffu, dp[r], 1);
+    if (lane >= 1 && i < nc) {
+      const S nh = Prec<R>::add(wl[0], -nu * (dm[0] + dpl[0]));
+      const S nq = Prec<R>::add(wl[1], -nu * (dm[1] + dpl[1]));
+      const S nz = Prec<R>::add(wl[2], -nu * (dm[2] + dpl[2]));
+      out.h[base + i] = nh;
+      out.q[base + i] = nq;
+      out.z[base + i] = nz;
+      const R hh = Prec<R>::hi(nh);
+      if (!(hh > R(0))) flags |= ST_DEPTH;
+      if (!(Prec<R>::finite(nh) && Prec<R>::finite(nq) && Prec<R>::finite(nz))) {
+        flags |= ST_NONFINITE;
+      } else if (hh > R(0)) {
+        R r = Prec<R>::template rho<LAW_GRASS>(lp, hh, Prec<R>::hi(nq));
+        if (!(r <= R(3.0e38))) {
+          flags |= ST_NONFINITE;
+          r = R(0);
+        }
+        rho = r > rho ? r : rho;
+      }
+    }
+}
+
 // Persistent warp tiles: each warp walks tiles of SUB x 31 cells of one
 // channel (tile list in those units, longest channel first) with a grid-wide
 // stride over the active bound. Lane 0 evaluates the channel's control once per
@@ -226,7 +289,6 @@ template <typename R, int B, int CAP, int SUB>
 __global__ void __launch_bounds__(B, 65536 / (B * CAP))
     k_ens_step_warp(const EnsParams p, const typename Prec<R>::State in,
                     const typename Prec<R>::State out, const int slot) {
-  using S = typename Prec<R>::S;
   const int lane = threadIdx.x & 31;
   const int C = p.C;
   const int nx = (slot + 1) % 3, pv = (slot + 2) % 3;
@@ -259,7 +321,6 @@ __global__ void __launch_bounds__(B, 65536 / (B * CAP))
     for (int sub = 0; sub < SUB; ++sub) {
       const int64_t e0 = t0 + sub * 31;
       if (e0 >= nc) break;  // past the channel's last cell (warp-uniform)
-      const int64_t e = e0 + lane;
       {
         const int64_t cn = e0 + 31 + lane;  // the next sub-tile's cells into L2 (+1.5 %)
         if (sub + 1 < SUB && cn < nc) {
@@ -268,55 +329,7 @@ __global__ void __launch_bounds__(B, 65536 / (B * CAP))
           asm volatile("prefetch.global.L2 [%0];" ::"l"(in.z + base + cn));
         }
       }
-      // states of edge e: cells e-1 and e, each lane loading both (a right
-      // state taken from the next lane by shuffle measured 4 % slower: every
-      // lane then waits for its neighbour's load); transmissive ends copy the
-      // adjacent cell, lanes past the channel's end read its last cell
-      const bool valid = e <= nc;
-      S wl[3], wr[3];
-      const int64_t il = (e > 0) ? (e <= nc ? e - 1 : nc - 1) : 0;
-      const int64_t ir = (e < nc) ? e : nc - 1;
-      wl[0] = in.h[base + il];
-      wl[1] = in.q[base + il];
-      wl[2] = in.z[base + il];
-      wr[0] = in.h[base + ir];
-      wr[1] = in.q[base + ir];
-      wr[2] = in.z[base + ir];
-      const int64_t i = e - 1;  // cell updated by this lane (lanes 1..31)
-      if (mode == 1) {
-        if (lane >= 1 && i < nc) {
-          out.h[base + i] = wl[0];
-          out.q[base + i] = wl[1];
-          out.z[base + i] = wl[2];
-        }
-        continue;
-      }
-      R dm[3] = {R(0), R(0), R(0)}, dp[3] = {R(0), R(0), R(0)};
-      // the paired-node float32 form where the register cap leaves it room
-      if (valid && e > 0 && e < nc) edge_fluct<R, LAW_GRASS, (CAP >= 80)>(lp, wl, wr, dm, dp, flags);
-      R dpl[3];
-#pragma unroll
-      for (int r = 0; r < 3; ++r) dpl[r] = __shfl_up_sync(0xffffffffu, dp[r], 1);
-      if (lane >= 1 && i < nc) {
-        const S nh = Prec<R>::add(wl[0], -nu * (dm[0] + dpl[0]));
-        const S nq = Prec<R>::add(wl[1], -nu * (dm[1] + dpl[1]));
-        const S nz = Prec<R>::add(wl[2], -nu * (dm[2] + dpl[2]));
-        out.h[base + i] = nh;
-        out.q[base + i] = nq;
-        out.z[base + i] = nz;
-        const R hh = Prec<R>::hi(nh);
-        if (!(hh > R(0))) flags |= ST_DEPTH;
-        if (!(Prec<R>::finite(nh) && Prec<R>::finite(nq) && Prec<R>::finite(nz))) {
-          flags |= ST_NONFINITE;
-        } else if (hh > R(0)) {
-          R r = Prec<R>::template rho<LAW_GRASS>(lp, hh, Prec<R>::hi(nq));
-          if (!(r <= R(3.0e38))) {
-            flags |= ST_NONFINITE;
-            r = R(0);
-          }
-          rho = r > rho ? r : rho;
-        }
-      }
+      ens_subtile<R, CAP>(lp, in, out, base, nc, e0, lane, nu, mode, rho, flags);
     }
     if (mode == 0) {
       rho = warp_max(rho);
@@ -325,6 +338,141 @@ __global__ void __launch_bounds__(B, 65536 / (B * CAP))
   }
   if (flags) atomicOr(p.d.status, flags);
 }
+
+// Persistent form (one launch per run_to chunk). Each CTA takes whole channels
+// from a device queue, largest estimated work first (order[]; the head *next is
+// zeroed by the host before the launch), and advances each one alone: the CFL
+// maximum of its state, then up to max_steps of its own steps (dt and the
+// landing on t_end exactly as ens_control), the CTA's warps taking the
+// channel's 31-cell sub-tiles in turn and one block barrier (the CFL maximum of
+// the new state) between steps. No CTA waits on another. When the channel
+// stops, its state is copied into the other ping-pong buffer (so that both
+// hold it) and its control is left as the per-step launches read it at slot
+// `slot`: finished channels (t >= t_end) marked as copied before step
+// gstep[slot], running ones added to the tile bound active[slot]. A non-finite
+// value or non-positive depth (this CTA's or any other's, read from the status
+// word) stops the channel after its step and the CTA takes no further channel.
+struct EnsRun {
+  const int* order;  // [C] channels, largest estimated work first
+  int* next;         // queue head
+  double t_end;
+  long long max_steps;
+  int slot;
+};
+
+template <typename R, int NW>
+__device__ __forceinline__ R block_max(R v, R* red) {
+  v = warp_max(v);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  R m = red[0];
+#pragma unroll
+  for (int w = 1; w < NW; ++w) m = d_max(m, red[w]);
+  return m;
+}
+
+template <typename R, int B, int CAP>
+__global__ void __launch_bounds__(B, 65536 / (B * CAP))
+    k_ens_run(const EnsParams p, const typename Prec<R>::State b0, const typename Prec<R>::State b1,
+              const EnsRun r) {
+  constexpr int NW = B / 32;
+  __shared__ R sRed[NW];
+  __shared__ int sJ;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int C = p.C;
+  unsigned flags = 0;
+  bool stop = false;
+  while (!stop) {
+    __syncthreads();
+    if (threadIdx.x == 0) sJ = atomicAdd(r.next, 1);
+    __syncthreads();
+    const int j = sJ;
+    if (j >= C) break;
+    const int c = r.order[j];
+    const int64_t base = p.off[c];
+    const int64_t nc = p.off[c + 1] - base;
+    StepParams lp;
+    lp.lf = LawT<float>{p.g_f, p.K3f[c], 0.0f, 0.0f};
+    lp.ld = LawT<double>{p.g_d, p.K3d[c], 0.0, 0.0};
+    // CFL maximum of the channel's current state (as k_ens_rho)
+    R rho = R(0);
+    for (int64_t i = threadIdx.x; i < nc; i += B) {
+      const auto h = b0.h[base + i], q = b0.q[base + i], z = b0.z[base + i];
+      const R hh = Prec<R>::hi(h);
+      if (!(Prec<R>::finite(h) && Prec<R>::finite(q) && Prec<R>::finite(z))) {
+        flags |= ST_NONFINITE;
+        continue;
+      }
+      if (!(hh > R(0))) {
+        flags |= ST_DEPTH;
+        continue;
+      }
+      const R v = Prec<R>::template rho<LAW_GRASS>(lp, hh, Prec<R>::hi(q));
+      if (!(v <= R(3.0e38))) {
+        flags |= ST_NONFINITE;
+        continue;
+      }
+      rho = d_max(rho, v);
+    }
+    rho = block_max<R, NW>(rho, sRed);
+    double t = p.d.t_cur[c];
+    long long st = p.d.steps_cur[c];
+    double dt_last = p.d.dt_cur[c];
+    const double dx = p.dx[c];
+    int cur = 0;
+    stop = __syncthreads_or(flags != 0);
+    for (long long ns = 0; !stop && t < r.t_end && ns < r.max_steps; ++ns) {
+      double dt = p.cfl * dx / (double)rho;
+      double tn = t + dt;
+      if (tn >= r.t_end) {
+        dt = r.t_end - t;
+        tn = r.t_end;
+      }
+      const R nu = R(dt / dx);
+      const typename Prec<R>::State& in = cur ? b1 : b0;
+      const typename Prec<R>::State& out = cur ? b0 : b1;
+      R rr = R(0);
+      for (int64_t e0 = (int64_t)warp * 31; e0 < nc; e0 += NW * 31)
+        ens_subtile<R, CAP>(lp, in, out, base, nc, e0, lane, nu, 0, rr, flags);
+      rho = block_max<R, NW>(rr, sRed);
+      t = tn;
+      ++st;
+      dt_last = dt;
+      cur ^= 1;
+      stop = __syncthreads_or(flags != 0 || (threadIdx.x == 0 && *(volatile unsigned*)p.d.status != 0));
+    }
+    // both buffers hold the channel's state
+    {
+      const typename Prec<R>::State& src = cur ? b1 : b0;
+      const typename Prec<R>::State& dst = cur ? b0 : b1;
+      for (int64_t i = threadIdx.x; i < nc; i += B) {
+        dst.h[base + i] = src.h[base + i];
+        dst.q[base + i] = src.q[base + i];
+        dst.z[base + i] = src.z[base + i];
+      }
+    }
+    if (threadIdx.x == 0) {
+      const int s0 = r.slot, s1 = (r.slot + 1) % 3;
+      p.d.t[s0 * C + c] = t;
+      p.d.dt[s0 * C + c] = dt_last;
+      p.d.steps[s0 * C + c] = st;
+      p.d.rho[s0 * C + c] = rho > R(0) ? Prec<R>::bits(rho) : 0ull;
+      p.d.rho[s1 * C + c] = 0ull;
+      p.d.t_cur[c] = t;
+      p.d.steps_cur[c] = st;
+      p.d.dt_cur[c] = dt_last;
+      const bool done = !(t < r.t_end);
+      p.d.fin[c] = done ? p.d.gstep[s0] - 1 : 0x7fffffffffffffffLL;
+      if (!done) atomicMax(&p.d.active[s0], p.chan_tile_end[c]);
+    }
+    if (flags) {
+      atomicOr(p.d.status, flags);
+      flags = 0;
+    }
+  }
+}
+
 
 // Initial CFL maxima of every channel into slot 0 (grid-stride over cells).
 template <typename R>
@@ -379,6 +527,12 @@ struct EnsVariant {
 constexpr EnsVariant kEnsVariants[] = {{256, 64, false}, {128, 64, false}, {512, 64, false},
                                        {256, 64, true},  {256, 80, true}};
 constexpr int kNumEnsVariants = sizeof(kEnsVariants) / sizeof(kEnsVariants[0]);
+// Threads per CTA of the persistent form when block_threads = 0: on the 4096-channel
+// ensemble (float32, N_c log-uniform in [1e3, 1e5], t_end 0.02 and 0.1 s) 256 x 80:
+// 3.99e10, 384 x 80: 5.12e10, 512 x 64: 4.6-4.7e10 cell-updates/s (per-step warp
+// tiles: 4.36e10). With 256 threads the 456 CTAs hold less work each than the
+// largest channel alone.
+constexpr int kRunBlockDefault = 384;
 // 31-cell sub-tiles per warp tile (one control evaluation each; on the 4096-channel
 // ensemble with scalar nodes 4: 2.99e10, 8: 3.15e10, 16: 3.19e10 cell-updates/s)
 constexpr int kEnsSub = 16;
@@ -398,7 +552,12 @@ struct adot_ensemble {
   int block;
   int cap;       // register cap of the warp-tile kernel
   bool warp;     // persistent warp tiles (31 cells) instead of block tiles (block - 1 cells)
-  int step_kernel_cfg;  // 0 autotuned, 1 block, 2 warp tiles
+  int step_kernel_cfg;  // 0/3 persistent channel loops, 1 block, 2 warp tiles, 4 per-step autotuned
+  bool persistent;      // run_to and step by the persistent form (k_ens_run)
+  int run_block;        // its threads per block
+  int run_cap;          // and register cap
+  int run_grid;         // resident CTAs (at most one per channel)
+  int* d_order;         // [C] channels, largest estimated work first
   int block_cfg;        // configured block_threads (0 = any)
   bool tuned;
   int steps_per_graph;
@@ -407,6 +566,7 @@ struct adot_ensemble {
   std::vector<int64_t> n_cells;
   std::vector<int64_t> off;
   std::vector<int> order;  // channels, longest first
+  std::vector<double> length;
   cudaStream_t stream;
   bool own_stream;
   cudaStream_t cap_stream;
@@ -522,6 +682,28 @@ int resident_grid(adot_ensemble* e, int block) {
   if (err != cudaSuccess || per_sm < 1) per_sm = 1;
   int64_t g = (int64_t)sms * per_sm;
   return (int)g;
+}
+
+template <typename R, int B, int CAP>
+cudaError_t ens_run_launch_t(adot_ensemble* e, const EnsRun& r, bool occupancy_only, int* per_sm) {
+  if (occupancy_only) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_ens_run<R, B, CAP>, B, 0);
+  k_ens_run<R, B, CAP><<<e->run_grid, B, 0, e->stream>>>(ens_params(e), ens_state<R>(e, e->cur),
+                                                         ens_state<R>(e, 1 - e->cur), r);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t ens_run_dispatch(adot_ensemble* e, const EnsRun& r, bool occupancy_only, int* per_sm) {
+  if (e->run_block == 256) return ens_run_launch_t<R, 256, 80>(e, r, occupancy_only, per_sm);
+  if (e->run_block == 384) return ens_run_launch_t<R, 384, 80>(e, r, occupancy_only, per_sm);
+  if (e->run_block == 512) return ens_run_launch_t<R, 512, 64>(e, r, occupancy_only, per_sm);
+  if (e->run_block == 768) return ens_run_launch_t<R, 768, 80>(e, r, occupancy_only, per_sm);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t ens_run_call(adot_ensemble* e, const EnsRun& r, bool occupancy_only = false, int* per_sm = nullptr) {
+  if (e->prec == ADOT_FP32) return ens_run_dispatch<float>(e, r, occupancy_only, per_sm);
+  return ens_run_dispatch<double>(e, r, occupancy_only, per_sm);
 }
 
 // Tile list of a variant: channels longest first, tiles of block - 1 cells
@@ -694,6 +876,70 @@ adot_status ens_tune(adot_ensemble* e, int trial) {
   return ens_build_graph(e);
 }
 
+// Queue order of the persistent form: channels by estimated work, largest
+// first. Work of channel c = N_c x (steps per unit time) = N_c rho_c / (cfl dx_c)
+// from the first CFL maxima (slot 0), so that the list scheduling of channels
+// onto CTAs ends with the short channels.
+adot_status ens_order_by_work(adot_ensemble* e) {
+  const int C = e->C;
+  std::vector<unsigned long long> bits(C);
+  CKE(cudaMemcpyAsync(bits.data(), e->dev.rho, sizeof(unsigned long long) * C, cudaMemcpyDeviceToHost,
+                      e->stream));
+  CKE(cudaStreamSynchronize(e->stream));
+  std::vector<double> w(C);
+  for (int c = 0; c < C; ++c) {
+    double rho;
+    if (e->prec == ADOT_FP32) {
+      const unsigned u = (unsigned)bits[c];
+      float f;
+      memcpy(&f, &u, sizeof(f));
+      rho = f;
+    } else {
+      memcpy(&rho, &bits[c], sizeof(rho));
+    }
+    w[c] = (double)e->n_cells[c] * (double)e->n_cells[c] * rho / e->length[c];
+  }
+  std::vector<int> ord(C);
+  for (int c = 0; c < C; ++c) ord[c] = c;
+  std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return w[a] > w[b]; });
+  CKE(cudaMemcpyAsync(e->d_order, ord.data(), sizeof(int) * C, cudaMemcpyHostToDevice, e->stream));
+  CKE(cudaStreamSynchronize(e->stream));
+  return ADOT_OK;
+}
+
+// Persistent form: launches of at most kRunChunk steps per channel (the host
+// reads the status word between launches) until every channel has reached
+// t_end, or every channel has taken n_steps steps (n_steps >= 0, t_end = inf).
+constexpr long long kRunChunk = 1 << 14;
+
+adot_status ens_run(adot_ensemble* e, double t_end, long long n_steps, int64_t* launches_out) {
+  int64_t launches = 0;
+  long long left = n_steps;
+  for (;;) {
+    if (n_steps >= 0 && left <= 0) break;
+    const long long m = (n_steps >= 0) ? std::min(left, kRunChunk) : kRunChunk;
+    CKE(cudaMemsetAsync(e->dev.next, 0, sizeof(int), e->stream));
+    CKE(cudaMemsetAsync(e->dev.active, 0, sizeof(int) * 3, e->stream));
+    EnsRun r;
+    r.order = e->d_order;
+    r.next = e->dev.next;
+    r.t_end = t_end;
+    r.max_steps = m;
+    r.slot = e->phase % 3;
+    CKE(ens_run_call(e, r));
+    ++launches;
+    left -= m;
+    HostCtl hc;
+    adot_status st = ens_read(e, &hc);
+    if (st) return st;
+    st = ens_status(hc.status);
+    if (st) return st;
+    if (hc.active[r.slot] == 0) break;  // every channel at t_end
+  }
+  if (launches_out) *launches_out = launches;
+  return ADOT_OK;
+}
+
 void ens_free(adot_ensemble* e) {
   if (!e) return;
   if (e->graph_ready) cudaGraphExecDestroy(e->graph);
@@ -707,6 +953,7 @@ void ens_free(adot_ensemble* e) {
   if (e->d_tile_chan) cudaFree(e->d_tile_chan);
   if (e->d_tile_e0) cudaFree(e->d_tile_e0);
   if (e->d_chan_tile_end) cudaFree(e->d_chan_tile_end);
+  if (e->d_order) cudaFree(e->d_order);
   if (e->d_ctl_mem) cudaFree(e->d_ctl_mem);
   if (e->d_io) cudaFree(e->d_io);
   if (e->cap_stream) cudaStreamDestroy(e->cap_stream);
@@ -725,10 +972,15 @@ adot_status adot_ensemble_create(const adot_ensemble_config* cfg, void* cuda_str
   if (!cfg || cfg->n_channels < 1 || !cfg->n_cells || !cfg->length || !cfg->Ag) return ADOT_E_INVALID_ARG;
   if (!(cfg->g > 0.0) || !(cfg->xi > 0.0) || !(cfg->cfl > 0.0 && cfg->cfl <= 1.0)) return ADOT_E_INVALID_ARG;
   if (cfg->precision != ADOT_FP64 && cfg->precision != ADOT_FP32) return ADOT_E_INVALID_ARG;
-  if (cfg->block_threads != 0 && cfg->block_threads != 128 && cfg->block_threads != 256 &&
-      cfg->block_threads != 512)
+  if (cfg->step_kernel < 0 || cfg->step_kernel > 4) return ADOT_E_INVALID_ARG;
+  if (cfg->step_kernel == 0 || cfg->step_kernel == 3) {
+    if (cfg->block_threads != 0 && cfg->block_threads != 256 && cfg->block_threads != 384 &&
+        cfg->block_threads != 512 && cfg->block_threads != 768)
+      return ADOT_E_INVALID_ARG;
+  } else if (cfg->block_threads != 0 && cfg->block_threads != 128 && cfg->block_threads != 256 &&
+             cfg->block_threads != 512) {
     return ADOT_E_INVALID_ARG;
-  if (cfg->step_kernel < 0 || cfg->step_kernel > 2) return ADOT_E_INVALID_ARG;
+  }
   if (cfg->step_kernel == 2 && cfg->block_threads != 0 && cfg->block_threads != 256) return ADOT_E_INVALID_ARG;
   if (cfg->steps_per_graph < 0 || cfg->device < -1) return ADOT_E_INVALID_ARG;
   const int C = cfg->n_channels;
@@ -749,6 +1001,7 @@ adot_status adot_ensemble_create(const adot_ensemble_config* cfg, void* cuda_str
   e->xi = cfg->xi;
   e->n_total = total;
   e->n_cells.assign(cfg->n_cells, cfg->n_cells + C);
+  e->length.assign(cfg->length, cfg->length + C);
   e->off.resize(C + 1);
   e->off[0] = 0;
   for (int c = 0; c < C; ++c) e->off[c + 1] = e->off[c] + e->n_cells[c];
@@ -759,7 +1012,10 @@ adot_status adot_ensemble_create(const adot_ensemble_config* cfg, void* cuda_str
   int spg = cfg->steps_per_graph ? cfg->steps_per_graph : 48;
   e->steps_per_graph = ((spg + 5) / 6) * 6;
   e->step_kernel_cfg = cfg->step_kernel;
-  e->block_cfg = cfg->block_threads;
+  e->persistent = cfg->step_kernel == 0 || cfg->step_kernel == 3;
+  e->block_cfg = e->persistent ? 0 : cfg->block_threads;
+  e->run_block = (e->persistent && cfg->block_threads) ? cfg->block_threads : kRunBlockDefault;
+  e->run_cap = e->run_block == 512 ? 64 : 80;
   e->t_end_dev = INFINITY;
 
   std::vector<double> dx(C), K3d(C);
@@ -790,7 +1046,7 @@ adot_status adot_ensemble_create(const adot_ensemble_config* cfg, void* cuda_str
   const size_t slots = 3 * (size_t)C;
   e->ctl_bytes = slots * (sizeof(double) * 2 + sizeof(long long) + sizeof(unsigned long long)) +
                  (size_t)C * (sizeof(double) * 2 + sizeof(long long) * 2) + sizeof(long long) * 3 +
-                 sizeof(int) * 4 + sizeof(double) + sizeof(unsigned) + 64;
+                 sizeof(int) * 4 + sizeof(double) + sizeof(unsigned) + sizeof(int) + 64;
   if (err == cudaSuccess) err = cudaMalloc(&e->d_ctl_mem, e->ctl_bytes);
   if (err == cudaSuccess) {
     char* m = (char*)e->d_ctl_mem;
@@ -811,6 +1067,17 @@ adot_status adot_ensemble_create(const adot_ensemble_config* cfg, void* cuda_str
     e->dev.active = (int*)take(sizeof(int) * 4);
     e->dev.t_end = (double*)take(sizeof(double));
     e->dev.status = (unsigned*)take(sizeof(unsigned));
+    e->dev.next = (int*)take(sizeof(int));
+  }
+  if (err == cudaSuccess) err = cudaMalloc((void**)&e->d_order, sizeof(int) * C);
+  if (err == cudaSuccess)
+    err = cudaMemcpy(e->d_order, e->order.data(), sizeof(int) * C, cudaMemcpyHostToDevice);
+  if (err == cudaSuccess) {
+    int per_sm = 0, sms = 152;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, e->device);
+    err = ens_run_call(e, EnsRun{}, true, &per_sm);
+    if (per_sm < 1) per_sm = 1;
+    e->run_grid = (int)std::min<int64_t>((int64_t)sms * per_sm, C);
   }
   if (err == cudaSuccess) err = cudaMemcpy(e->d_off, e->off.data(), sizeof(int64_t) * (C + 1), cudaMemcpyHostToDevice);
   if (err == cudaSuccess) err = cudaMemcpy(e->d_dx, dx.data(), sizeof(double) * C, cudaMemcpyHostToDevice);
@@ -824,7 +1091,7 @@ adot_status adot_ensemble_create(const adot_ensemble_config* cfg, void* cuda_str
       v0 = kEnsVariants[i];
       ++n_cand;
     }
-  e->tuned = n_cand == 1;
+  e->tuned = n_cand == 1 || e->persistent;
   if (err != cudaSuccess || build_tiles(e, v0) != ADOT_OK ||
       ens_reset_ctl(e) != ADOT_OK || ens_build_graph(e) != ADOT_OK) {
     ens_free(e);
@@ -876,6 +1143,7 @@ adot_status adot_ensemble_set_state(adot_ensemble* e, const double* h, const dou
   st = ens_status(hc.status);
   if (st) return st;
   e->state_set = true;
+  if (e->persistent) return ens_order_by_work(e);
   if (!e->tuned) return ens_tune(e, 2);
   return ADOT_OK;
 }
@@ -903,6 +1171,7 @@ adot_status adot_ensemble_run_to(adot_ensemble* e, double t_end, int64_t* launch
   if (!e || !e->state_set || !isfinite(t_end)) return ADOT_E_INVALID_ARG;
   adot_status st = ens_set_t_end(e, t_end);
   if (st) return st;
+  if (e->persistent) return ens_run(e, t_end, -1, launches_out);
   int64_t launches = 0;
   for (;;) {
     const int64_t chunk = e->phase ? (6 - e->phase) : e->steps_per_graph;
@@ -924,6 +1193,7 @@ adot_status adot_ensemble_step(adot_ensemble* e, int64_t n_steps) {
   if (!e || !e->state_set || n_steps < 0) return ADOT_E_INVALID_ARG;
   adot_status st = ens_set_t_end(e, INFINITY);
   if (st) return st;
+  if (e->persistent) return ens_run(e, INFINITY, n_steps, nullptr);
   st = ens_enqueue(e, n_steps);
   if (st) return st;
   HostCtl hc;
@@ -955,6 +1225,13 @@ adot_status adot_ensemble_query(adot_ensemble* e, double* t_out, int64_t* steps_
 adot_status adot_ensemble_info(adot_ensemble* e, int32_t* block_out, int64_t* tiles_out,
                                int32_t* grid_out, int32_t* step_kernel_out) {
   if (!e) return ADOT_E_INVALID_ARG;
+  if (e->persistent) {
+    if (step_kernel_out) *step_kernel_out = 3;
+    if (block_out) *block_out = e->run_block;
+    if (tiles_out) *tiles_out = e->C;
+    if (grid_out) *grid_out = e->run_grid;
+    return ADOT_OK;
+  }
   if (step_kernel_out) *step_kernel_out = e->warp ? 2 : 1;
   if (block_out) *block_out = e->block;
   if (tiles_out) *tiles_out = e->n_tiles;

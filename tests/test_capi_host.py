@@ -166,7 +166,11 @@ def test_invalid_ensemble_config_rejected(L):
     c.block_threads = 100
     assert L.adot_ensemble_create(ctypes.byref(c), None, ctypes.byref(out)) == adot.E_INVALID_ARG
     c.block_threads = 0
-    c.step_kernel = 3
+    c.step_kernel = 5
+    assert L.adot_ensemble_create(ctypes.byref(c), None, ctypes.byref(out)) == adot.E_INVALID_ARG
+    c.step_kernel, c.block_threads = 4, 384  # 384-thread blocks: persistent channel loops only
+    assert L.adot_ensemble_create(ctypes.byref(c), None, ctypes.byref(out)) == adot.E_INVALID_ARG
+    c.step_kernel, c.block_threads = 3, 128
     assert L.adot_ensemble_create(ctypes.byref(c), None, ctypes.byref(out)) == adot.E_INVALID_ARG
     c.step_kernel, c.block_threads = 2, 128  # warp tiles run 256-thread blocks only
     assert L.adot_ensemble_create(ctypes.byref(c), None, ctypes.byref(out)) == adot.E_INVALID_ARG

@@ -1,6 +1,7 @@
 """Parity of the batched ensemble (adot_ensemble_*, independent channels with
-their own dt, one launch per step) with per-channel oracle runs, on seeded
-movable-bed Riemann channels of ragged lengths (1 cell up to several tiles).
+their own dt; persistent channel loops and per-step launches) with per-channel
+oracle runs, on seeded movable-bed Riemann channels of ragged lengths (1 cell up
+to several tiles).
 
 Tolerances as for single channels: FP64 1e-12 of each variable's scale and the
 same step count; FP32 (float-float state) L1 relative error 1e-5 per channel."""
@@ -41,7 +42,8 @@ def _oracle_channel(E, c, t_end):
     return O.run(cfg, h, q, z, t_end=t_end)
 
 
-@pytest.mark.parametrize("block,kern", [(0, 0), (128, 1), (256, 1), (512, 1), (0, 2), (256, 2)])
+@pytest.mark.parametrize("block,kern", [(0, 0), (128, 1), (256, 1), (512, 1), (0, 2), (256, 2),
+                                        (0, 4)])
 def test_fp64_ensemble_matches_oracle_per_channel(gpu, block, kern):
     E = _small_ensemble(SIZES)
     with gpu.Ensemble.from_workload(E, gpu.FP64, block_threads=block, step_kernel=kern) as ens:
@@ -134,15 +136,136 @@ def test_ensemble_steps_equal_single_channel_contexts(gpu):
             assert np.abs(a[o[c]:o[c + 1]] - b).max() <= 1e-12 * max(np.abs(b).max(), 1e-300)
 
 
-def test_large_ensemble_all_channels_land_on_t_end(gpu):
+@pytest.mark.parametrize("kern", [0, 4])
+def test_large_ensemble_all_channels_land_on_t_end(gpu, kern):
     E = W.riemann_ensemble(256, seed=11, n_min=200, n_max=20000)
-    with gpu.Ensemble.from_workload(E, gpu.FP32) as ens:
+    with gpu.Ensemble.from_workload(E, gpu.FP32, step_kernel=kern) as ens:
         ens.set_state(E.h, E.q, E.z)
         launches = ens.run_to(0.02)
         t, steps, cu = ens.query()
         h, q, z = ens.get_state()
+        form = ens.info()[3]
     assert (t == 0.02).all()
-    assert launches >= steps.max()
+    if kern == 0:  # persistent channel loops: one launch per 16384 steps
+        assert form == 3 and launches == 1
+    else:  # one launch per step of the longest-running channel
+        assert form in (1, 2) and launches >= steps.max()
     assert np.isfinite(h).all() and (h > 0).all()
     # longer channels need more steps (dt ~ dx)
     assert steps[np.argmax(E.n_cells)] > steps[np.argmin(E.n_cells)]
+
+
+RUN_BLOCKS = [0, 256, 384, 512, 768]
+
+
+@pytest.mark.parametrize("block", RUN_BLOCKS)
+def test_persistent_fp64_matches_oracle_per_channel(gpu, block):
+    """The persistent form (one launch per run_to, each CTA stepping whole
+    channels to t_end in a device-side loop) against the oracle per channel."""
+    E = _small_ensemble(SIZES + [3000, 1234], seed=8)
+    with gpu.Ensemble.from_workload(E, gpu.FP64, block_threads=block, step_kernel=3) as ens:
+        assert ens.info()[3] == 3
+        ens.set_state(E.h, E.q, E.z)
+        launches = ens.run_to(0.15)
+        t, steps, cu = ens.query()
+        h, q, z = ens.get_state()
+    assert launches == 1
+    o = E.offsets
+    assert cu == int((steps * E.n_cells).sum())
+    for c in range(len(E.n_cells)):
+        ho, qo, zo, to, so, _ = _oracle_channel(E, c, 0.15)
+        assert t[c] == 0.15 and steps[c] == so, (c, steps[c], so)
+        for a, b in ((h, ho), (q, qo), (z, zo)):
+            sc = max(np.abs(b).max(), 1e-300)
+            assert np.abs(a[o[c]:o[c + 1]] - b).max() <= 1e-12 * sc, c
+
+
+def test_persistent_fp32_matches_oracle_per_channel(gpu):
+    E = _small_ensemble(SIZES, seed=4)
+    with gpu.Ensemble.from_workload(E, gpu.FP32, step_kernel=3) as ens:
+        ens.set_state(E.h, E.q, E.z)
+        g0 = ens.get_state()
+        ens.run_to(0.2)
+        t, steps, _ = ens.query()
+        h, q, z = ens.get_state()
+    o = E.offsets
+    for c in range(len(SIZES)):
+        ho, qo, zo, to, so, _ = _oracle_channel(E, c, 0.2)
+        assert t[c] == 0.2
+        sl = slice(o[c], o[c + 1])
+        for a, b, a0, ag in ((h, ho, E.h, g0[0]), (q, qo, E.q, g0[1]), (z, zo, E.z, g0[2])):
+            inc, ref = a[sl] - ag[sl], b - a0[sl]
+            assert np.abs(inc - ref).sum() <= 1e-5 * np.abs(ref).sum(), \
+                (c, np.abs(inc - ref).sum() / np.abs(ref).sum())
+
+
+@pytest.mark.parametrize("prec", ["FP32", "FP64"])
+def test_persistent_agrees_with_per_step_warp_tiles(gpu, prec):
+    """Same sub-tile arithmetic (256 threads, 80-register cap) in both forms:
+    equal times and step counts, states within 1e-14 (float64, max; the
+    compiler may contract the update differently in the two kernels) and 1e-6
+    (float32, L1 relative), both after run_to and after a fixed step count."""
+    E = _small_ensemble(SIZES + [3000, 1234, 9000], seed=6)
+    out = []
+    for kern, blk in ((2, 256), (3, 256)):
+        with gpu.Ensemble.from_workload(E, getattr(gpu, prec), step_kernel=kern, block_threads=blk) as ens:
+            if kern == 2:
+                assert ens.info()[:1] == (256,)
+            ens.set_state(E.h, E.q, E.z)
+            ens.step(23)
+            s23 = ens.get_state()
+            _, n23, _ = ens.query()
+            ens.set_state(E.h, E.q, E.z)
+            ens.run_to(0.1)
+            t, steps, cu = ens.query()
+            out.append((s23, n23, ens.get_state(), t, steps, cu))
+    (a23, an, sa, ta, na, ca), (b23, bn, sb, tb, nb, cb) = out
+    assert (an == 23).all() and (bn == 23).all()
+    for x, y in list(zip(sa, sb)) + list(zip(a23, b23)):
+        if prec == "FP32":
+            assert np.abs(x - y).sum() <= 1e-6 * np.abs(y).sum()
+        else:
+            assert np.abs(x - y).max() <= 1e-14 * np.abs(y).max()
+    assert np.array_equal(ta, tb) and np.array_equal(na, nb) and ca == cb
+
+
+def test_persistent_run_to_resumes(gpu):
+    """run_to(0.05) then run_to(0.1): every channel continues from its state at
+    0.05 (the oracle restarted there) and lands on 0.1."""
+    E = _small_ensemble([700, 31, 2500, 1], seed=9)
+    with gpu.Ensemble.from_workload(E, gpu.FP64, step_kernel=3) as ens:
+        ens.set_state(E.h, E.q, E.z)
+        ens.run_to(0.05)
+        mid = ens.get_state()
+        _, s1, _ = ens.query()
+        ens.run_to(0.1)
+        t, s2, _ = ens.query()
+        h, q, z = ens.get_state()
+    assert (t == 0.1).all()
+    o = E.offsets
+    for c in range(len(E.n_cells)):
+        sl = slice(o[c], o[c + 1])
+        cfg = O.make_cfg(int(E.n_cells[c]), 0.0, float(E.length[c]), E.cfl,
+                         O.grass(float(E.Ag[c]), xi=E.xi, g=G))
+        h1, q1, z1, t1, n1, _ = O.run(cfg, *(m[sl] for m in mid), t_end=0.05)
+        assert s2[c] - s1[c] == n1
+        for a, b in ((h, h1), (q, q1), (z, z1)):
+            assert np.abs(a[sl] - b).max() <= 1e-12 * max(np.abs(b).max(), 1e-300)
+
+
+def test_persistent_dry_out_is_reported(gpu):
+    """A channel whose two streams leave each other (beyond the dry-bed limit)
+    drives h through zero: the persistent run stops and reports it, and the
+    state stays readable."""
+    E = _small_ensemble([400, 512, 900], seed=10)
+    P = W.dam_break(512, hL=0.1, hR=0.1, uL=-3.0, uR=3.0)
+    o = E.offsets
+    E.h[o[1]:o[2]], E.q[o[1]:o[2]], E.z[o[1]:o[2]] = P.h, P.q, P.z
+    E.length[1] = P.x_max - P.x_min
+    with gpu.Ensemble.from_workload(E, gpu.FP32, step_kernel=3) as ens:
+        ens.set_state(E.h, E.q, E.z)
+        with pytest.raises(gpu.AdotError) as e:
+            ens.run_to(1.0)
+        assert e.value.status in (gpu.E_NONPOSITIVE_DEPTH, gpu.E_NONFINITE)
+        h, q, z = ens.get_state()
+        assert h.shape == (int(E.n_cells.sum()),)
