@@ -105,6 +105,8 @@ def parse():
     ap.add_argument("--ensemble-t-end", type=float, default=0.1,
                     help="t_end of the 4096-channel ensemble measurement, a tenth of the "
                          "workload's 1 s (0 = skip)")
+    ap.add_argument("--ensemble-channels", type=int, default=4096,
+                    help="channels of the ensemble measurement (the first of the seeded 4096)")
     ap.add_argument("--ensemble-per-step", type=int, default=1,
                     help="also time the per-step form of the ensemble (0 = skip)")
     ap.add_argument("--sur-steps", type=int, default=20000,
@@ -500,11 +502,13 @@ def price_leg(args, adot, P, n, stream, local, time_steps, plain_value, acc_step
 
 def measure_pipes(adot, local):
     """Measured throughput of the pipes the step kernels use (library probes,
-    CUDA events): FP32 FFMA and paired FFMA2 (TFLOP/s), MUFU rsqrt and sine
-    (T ops/s), FP64 DFMA (TFLOP/s)."""
+    CUDA events): FP32 FFMA and paired FFMA2 (TFLOP/s), MUFU rsqrt, sine, float32
+    tanh and paired bf16 tanh (T ops/s), FP64 DFMA (TFLOP/s)."""
     out = {}
     for kind, name in ((adot.PIPE_FFMA, "ffma_tflops"), (adot.PIPE_FFMA2, "ffma2_tflops"),
                        (adot.PIPE_RSQ, "mufu_rsq_tops"), (adot.PIPE_SIN, "mufu_sin_tops"),
+                       (adot.PIPE_TANH, "mufu_tanh_tops"),
+                       (adot.PIPE_TANH_BF16X2, "mufu_tanh_bf16x2_tops"),
                        (adot.PIPE_DFMA, "dfma_tflops")):
         rate, sec = adot.adot_measure_pipe(kind, local)
         out[name] = rate / 1e12
@@ -782,6 +786,10 @@ def main():
     ensemble = None
     if args.ensemble_t_end > 0 and rank == 0:
         E = W.riemann_ensemble(4096)
+        if args.ensemble_channels < 4096:
+            E = W.Ensemble(E.n_cells[:args.ensemble_channels].copy(), E.length[:args.ensemble_channels].copy(),
+                           E.Ag[:args.ensemble_channels].copy(), *(v[:E.offsets[args.ensemble_channels]].copy()
+                                                                   for v in (E.h, E.q, E.z)))
         forms = [0] + ([4] if args.ensemble_per_step else [])
         runs = {}
         for kern in forms:
@@ -806,7 +814,7 @@ def main():
                           "threads_per_block": blk,
                           ("channels" if ens_kernel == 3 else "tiles"): n_tiles, "grid": grid,
                           "all_at_t_end": bool((t_c == args.ensemble_t_end).all())}
-        ensemble = {"workload": "4096 movable-bed Riemann channels, N_c log-uniform [1e3,1e5], FP32",
+        ensemble = {"workload": f"{len(E.n_cells)} movable-bed Riemann channels, N_c log-uniform [1e3,1e5], FP32",
                     "total_cells": int(E.n_cells.sum()), "t_end": args.ensemble_t_end, **runs[0]}
         if 4 in runs:
             ensemble["other_form"] = runs[4]

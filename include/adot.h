@@ -258,13 +258,15 @@ adot_status adot_conserved_sums(adot_ctx* ctx, double sums_out[3]);
  * end to end in the state arrays: channel c owns cells off[c] .. off[c+1]-1 with
  * off[c] = n_cells[0] + ... + n_cells[c-1]. Channels stop at t_end individually.
  *
- * Two forms run the channels. Persistent channel loops (the default): one launch
- * per run_to (per 16384 steps of the longest-running channel); each CTA takes
- * whole channels from a device queue, largest estimated work (N_c rho_c / dx_c)
- * first, and steps each to t_end in a device-side loop with one block barrier
- * per step; no CTA waits on another. Per-step launches: one launch (captured in
- * CUDA graphs) advances every running channel by one of its own steps, over a
- * tile list of all channels. Both evaluate the same edges and cells. */
+ * Two forms run the channels. Persistent channel loops: one launch per run_to
+ * (per 16384 steps of the longest-running channel); each CTA takes whole
+ * channels from a device queue, largest estimated work first (N_c^2 rho_c /
+ * length_c for run_to, N_c for step), and steps each to t_end in a
+ * device-side loop with one block barrier per step; no CTA waits on another,
+ * so a channel longer than a CTA's share of the work sets the run time.
+ * Per-step launches: one launch (captured in CUDA graphs) advances every
+ * running channel by one of its own steps, over a tile list of all channels.
+ * Both evaluate the same edges and cells. */
 typedef struct {
   int32_t n_channels;       /* >= 1 */
   const int64_t* n_cells;   /* host [n_channels], each >= 1 */
@@ -273,15 +275,19 @@ typedef struct {
   double g, xi, cfl;        /* shared: gravity, 1/(1-p), CFL number in (0, 1] */
   int32_t precision;        /* ADOT_FP64 or ADOT_FP32 (float-float state) */
   int32_t block_threads;    /* threads per block. Persistent channel loops: 256, 384, 512
-                               or 768 (0 = 384). Per-step: 128, 256, 512 (block kernel:
+                               or 768 (0 = 384 or 768, the better balanced). Per-step: 128,
+                               256, 512 (block kernel:
                                tile = block_threads - 1 cells; warp tiles: 256 only);
                                0 = autotuned */
   int32_t steps_per_graph;  /* per-step launches captured per CUDA graph; 0 = default (48) */
   int32_t device;           /* CUDA device ordinal; -1 = current */
-  int32_t step_kernel;      /* 0 or 3 = persistent channel loops (default); per-step launches:
-                               1 = block kernel, 2 = persistent warp tiles (31 cells per tile,
-                               shuffle exchange, no block barrier), 4 = the faster of 1 and 2
-                               by trial launches */
+  int32_t step_kernel;      /* 0 = chosen at each set_state (default): persistent channel loops
+                               when the estimated list schedule of the channels onto its CTAs
+                               is within 1/0.85 of balanced, else per-step launches (4);
+                               3 = persistent channel loops; per-step launches: 1 = block
+                               kernel, 2 = persistent warp tiles (31 cells per tile, shuffle
+                               exchange, no block barrier), 4 = the faster of 1 and 2 by
+                               trial launches */
 } adot_ensemble_config;
 
 typedef struct adot_ensemble adot_ensemble;
@@ -471,8 +477,9 @@ adot_status adot_step_noalloc(const adot_config* cfg, double* h, double* q, doub
  * resident grid (8 blocks of 256 threads per SM) runs 8 independent chains
  * per thread; one warm-up launch, then one timed launch (CUDA events, tens of
  * milliseconds). kind: 0 = float32 FFMA (2 flops each), 1 = paired float32
- * FFMA2 (4 flops), 2 = MUFU reciprocal square root, 3 = MUFU sine (1 op each),
- * 4 = float64 DFMA (2 flops). *rate_out: flops (or ops) per second;
+ * FFMA2 (4 flops), 2 = MUFU reciprocal square root, 3 = MUFU sine, 5 = MUFU
+ * float32 tanh (1 op each), 4 = float64 DFMA (2 flops), 6 = MUFU paired bfloat16
+ * tanh (2 ops). *rate_out: flops (or ops) per second;
  * *seconds_out (may be NULL): the timed launch. device >= 0 is made current.
  * Allocates and frees a small result buffer and a stream.
  * ADOT_E_INVALID_ARG for another kind or a NULL rate_out. */

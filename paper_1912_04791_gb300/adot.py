@@ -594,7 +594,7 @@ def adot_precision_stats(ctx: int):
     return a.value, b.value
 
 
-PIPE_FFMA, PIPE_FFMA2, PIPE_RSQ, PIPE_SIN, PIPE_DFMA = range(5)
+PIPE_FFMA, PIPE_FFMA2, PIPE_RSQ, PIPE_SIN, PIPE_DFMA, PIPE_TANH, PIPE_TANH_BF16X2 = range(7)
 
 
 def adot_measure_pipe(kind: int, device: int = -1):

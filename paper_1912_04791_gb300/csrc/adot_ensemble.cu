@@ -533,6 +533,13 @@ constexpr int kNumEnsVariants = sizeof(kEnsVariants) / sizeof(kEnsVariants[0]);
 // tiles: 4.36e10). With 256 threads the 456 CTAs hold less work each than the
 // largest channel alone.
 constexpr int kRunBlockDefault = 384;
+// Persistent shapes tried when block_threads = 0 (threads, register cap), and the
+// per-step form's measured speed relative to a balanced persistent run (4.36e10
+// against 5.13e10 cell-updates/s): the per-step form is used when the persistent
+// form's estimated imbalance exceeds 1 / kPerStepRel.
+constexpr int kRunBlocks[] = {384, 768};
+constexpr int kNumRunBlocks = 2;
+constexpr double kPerStepRel = 0.85;
 // 31-cell sub-tiles per warp tile (one control evaluation each; on the 4096-channel
 // ensemble with scalar nodes 4: 2.99e10, 8: 3.15e10, 16: 3.19e10 cell-updates/s)
 constexpr int kEnsSub = 16;
@@ -552,12 +559,18 @@ struct adot_ensemble {
   int block;
   int cap;       // register cap of the warp-tile kernel
   bool warp;     // persistent warp tiles (31 cells) instead of block tiles (block - 1 cells)
-  int step_kernel_cfg;  // 0/3 persistent channel loops, 1 block, 2 warp tiles, 4 per-step autotuned
-  bool persistent;      // run_to and step by the persistent form (k_ens_run)
-  int run_block;        // its threads per block
-  int run_cap;          // and register cap
-  int run_grid;         // resident CTAs (at most one per channel)
-  int* d_order;         // [C] channels, largest estimated work first
+  int step_kernel_cfg;  // 0 chosen per state, 1 block, 2 warp tiles, 3 persistent, 4 per-step autotuned
+  int run_block_cfg;    // configured threads per CTA of the persistent form (0 = chosen)
+  int n_sms;
+  int run_occ[kNumRunBlocks];  // resident CTAs per SM of each persistent shape
+  // how run_to (plan[0]) and step (plan[1]) advance the channels
+  struct Plan {
+    bool persistent;
+    int block;       // threads per CTA of k_ens_run
+    int grid;        // resident CTAs (at most one per channel)
+    double imbalance;  // estimated list-scheduling makespan / mean CTA load
+    int* d_order;    // [C] channel queue, largest estimated work first
+  } plan[2];
   int block_cfg;        // configured block_threads (0 = any)
   bool tuned;
   int steps_per_graph;
@@ -684,26 +697,36 @@ int resident_grid(adot_ensemble* e, int block) {
   return (int)g;
 }
 
+// Launch of the persistent form with `block` threads per CTA on `grid` CTAs, or
+// (grid = 0) the resident CTAs per SM of that shape into *per_sm.
 template <typename R, int B, int CAP>
-cudaError_t ens_run_launch_t(adot_ensemble* e, const EnsRun& r, bool occupancy_only, int* per_sm) {
-  if (occupancy_only) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_ens_run<R, B, CAP>, B, 0);
-  k_ens_run<R, B, CAP><<<e->run_grid, B, 0, e->stream>>>(ens_params(e), ens_state<R>(e, e->cur),
-                                                         ens_state<R>(e, 1 - e->cur), r);
+cudaError_t ens_run_launch_t(adot_ensemble* e, const EnsRun& r, int grid, int* per_sm) {
+  if (grid == 0) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_ens_run<R, B, CAP>, B, 0);
+  k_ens_run<R, B, CAP><<<grid, B, 0, e->stream>>>(ens_params(e), ens_state<R>(e, e->cur),
+                                                  ens_state<R>(e, 1 - e->cur), r);
   return cudaGetLastError();
 }
 
 template <typename R>
-cudaError_t ens_run_dispatch(adot_ensemble* e, const EnsRun& r, bool occupancy_only, int* per_sm) {
-  if (e->run_block == 256) return ens_run_launch_t<R, 256, 80>(e, r, occupancy_only, per_sm);
-  if (e->run_block == 384) return ens_run_launch_t<R, 384, 80>(e, r, occupancy_only, per_sm);
-  if (e->run_block == 512) return ens_run_launch_t<R, 512, 64>(e, r, occupancy_only, per_sm);
-  if (e->run_block == 768) return ens_run_launch_t<R, 768, 80>(e, r, occupancy_only, per_sm);
+cudaError_t ens_run_dispatch(adot_ensemble* e, const EnsRun& r, int block, int grid, int* per_sm) {
+  if (block == 256) return ens_run_launch_t<R, 256, 80>(e, r, grid, per_sm);
+  if (block == 384) return ens_run_launch_t<R, 384, 80>(e, r, grid, per_sm);
+  if (block == 512) return ens_run_launch_t<R, 512, 64>(e, r, grid, per_sm);
+  if (block == 768) return ens_run_launch_t<R, 768, 80>(e, r, grid, per_sm);
   return cudaErrorInvalidValue;
 }
 
-cudaError_t ens_run_call(adot_ensemble* e, const EnsRun& r, bool occupancy_only = false, int* per_sm = nullptr) {
-  if (e->prec == ADOT_FP32) return ens_run_dispatch<float>(e, r, occupancy_only, per_sm);
-  return ens_run_dispatch<double>(e, r, occupancy_only, per_sm);
+cudaError_t ens_run_call(adot_ensemble* e, const EnsRun& r, int block, int grid, int* per_sm = nullptr) {
+  if (e->prec == ADOT_FP32) return ens_run_dispatch<float>(e, r, block, grid, per_sm);
+  return ens_run_dispatch<double>(e, r, block, grid, per_sm);
+}
+
+// Resident grid of a persistent shape (at most one CTA per channel).
+int ens_run_grid(adot_ensemble* e, int block) {
+  int per_sm = 0, sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, e->device);
+  if (ens_run_call(e, EnsRun{}, block, 0, &per_sm) != cudaSuccess || per_sm < 1) per_sm = 1;
+  return (int)std::min<int64_t>((int64_t)sms * per_sm, e->C);
 }
 
 // Tile list of a variant: channels longest first, tiles of block - 1 cells
@@ -876,33 +899,81 @@ adot_status ens_tune(adot_ensemble* e, int trial) {
   return ens_build_graph(e);
 }
 
-// Queue order of the persistent form: channels by estimated work, largest
-// first. Work of channel c = N_c x (steps per unit time) = N_c rho_c / (cfl dx_c)
-// from the first CFL maxima (slot 0), so that the list scheduling of channels
-// onto CTAs ends with the short channels.
-adot_status ens_order_by_work(adot_ensemble* e) {
+// Longest-processing-time list scheduling of the work items w (sorted in
+// decreasing order) onto g equal workers: makespan / (sum w / g).
+double lpt_imbalance(const std::vector<double>& w_sorted, int g) {
+  if (g < 1 || w_sorted.empty()) return 1.0;
+  std::vector<double> load((size_t)g, 0.0);  // min-heap of worker loads
+  auto cmp = [](double a, double b) { return a > b; };
+  double total = 0.0;
+  for (double x : w_sorted) {
+    std::pop_heap(load.begin(), load.end(), cmp);
+    load.back() += x;
+    std::push_heap(load.begin(), load.end(), cmp);
+    total += x;
+  }
+  const double mk = *std::max_element(load.begin(), load.end());
+  return total > 0.0 ? mk / (total / g) : 1.0;
+}
+
+// Plans of run_to (k = 0) and step (k = 1). A channel's work is N_c times its
+// steps: for run_to N_c rho_c / dx_c (steps per unit time, from the first CFL
+// maxima in slot 0), for step N_c. Each CTA of the persistent form steps one
+// channel at a time, so its time is that of the list schedule of the channels,
+// largest first, onto the resident CTAs; the shape with the smaller estimated
+// imbalance is taken (or the configured one), and with step_kernel = 0 the
+// per-step form instead when that imbalance exceeds 1 / kPerStepRel.
+adot_status ens_plan(adot_ensemble* e) {
   const int C = e->C;
   std::vector<unsigned long long> bits(C);
   CKE(cudaMemcpyAsync(bits.data(), e->dev.rho, sizeof(unsigned long long) * C, cudaMemcpyDeviceToHost,
                       e->stream));
   CKE(cudaStreamSynchronize(e->stream));
-  std::vector<double> w(C);
-  for (int c = 0; c < C; ++c) {
-    double rho;
-    if (e->prec == ADOT_FP32) {
-      const unsigned u = (unsigned)bits[c];
-      float f;
-      memcpy(&f, &u, sizeof(f));
-      rho = f;
-    } else {
-      memcpy(&rho, &bits[c], sizeof(rho));
+  for (int k = 0; k < 2; ++k) {
+    std::vector<double> w(C);
+    for (int c = 0; c < C; ++c) {
+      const double n = (double)e->n_cells[c];
+      if (k == 1) {
+        w[c] = n;
+        continue;
+      }
+      double rho;
+      if (e->prec == ADOT_FP32) {
+        const unsigned u = (unsigned)bits[c];
+        float f;
+        memcpy(&f, &u, sizeof(f));
+        rho = f;
+      } else {
+        memcpy(&rho, &bits[c], sizeof(rho));
+      }
+      w[c] = n * n * rho / e->length[c];
     }
-    w[c] = (double)e->n_cells[c] * (double)e->n_cells[c] * rho / e->length[c];
+    std::vector<int> ord(C);
+    for (int c = 0; c < C; ++c) ord[c] = c;
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return w[a] > w[b]; });
+    std::vector<double> ws(C);
+    for (int i = 0; i < C; ++i) ws[i] = w[ord[i]];
+    adot_ensemble::Plan& pl = e->plan[k];
+    pl.imbalance = INFINITY;
+    for (int i = 0; i < kNumRunBlocks; ++i) {
+      const int blk = kRunBlocks[i];
+      if (e->run_block_cfg && blk != e->run_block_cfg) continue;
+      const int g = (int)std::min<int64_t>((int64_t)e->n_sms * e->run_occ[i], C);
+      const double imb = lpt_imbalance(ws, g);
+      if (imb < pl.imbalance) {
+        pl.imbalance = imb;
+        pl.block = blk;
+        pl.grid = g;
+      }
+    }
+    if (e->run_block_cfg && !(pl.imbalance < INFINITY)) {  // a configured shape outside kRunBlocks
+      pl.block = e->run_block_cfg;
+      pl.grid = ens_run_grid(e, pl.block);
+      pl.imbalance = lpt_imbalance(ws, pl.grid);
+    }
+    pl.persistent = e->step_kernel_cfg == 3 || pl.imbalance * kPerStepRel <= 1.0;
+    CKE(cudaMemcpyAsync(pl.d_order, ord.data(), sizeof(int) * C, cudaMemcpyHostToDevice, e->stream));
   }
-  std::vector<int> ord(C);
-  for (int c = 0; c < C; ++c) ord[c] = c;
-  std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return w[a] > w[b]; });
-  CKE(cudaMemcpyAsync(e->d_order, ord.data(), sizeof(int) * C, cudaMemcpyHostToDevice, e->stream));
   CKE(cudaStreamSynchronize(e->stream));
   return ADOT_OK;
 }
@@ -912,7 +983,8 @@ adot_status ens_order_by_work(adot_ensemble* e) {
 // t_end, or every channel has taken n_steps steps (n_steps >= 0, t_end = inf).
 constexpr long long kRunChunk = 1 << 14;
 
-adot_status ens_run(adot_ensemble* e, double t_end, long long n_steps, int64_t* launches_out) {
+adot_status ens_run(adot_ensemble* e, const adot_ensemble::Plan& pl, double t_end, long long n_steps,
+                    int64_t* launches_out) {
   int64_t launches = 0;
   long long left = n_steps;
   for (;;) {
@@ -921,12 +993,12 @@ adot_status ens_run(adot_ensemble* e, double t_end, long long n_steps, int64_t* 
     CKE(cudaMemsetAsync(e->dev.next, 0, sizeof(int), e->stream));
     CKE(cudaMemsetAsync(e->dev.active, 0, sizeof(int) * 3, e->stream));
     EnsRun r;
-    r.order = e->d_order;
+    r.order = pl.d_order;
     r.next = e->dev.next;
     r.t_end = t_end;
     r.max_steps = m;
     r.slot = e->phase % 3;
-    CKE(ens_run_call(e, r));
+    CKE(ens_run_call(e, r, pl.block, pl.grid));
     ++launches;
     left -= m;
     HostCtl hc;
@@ -953,7 +1025,8 @@ void ens_free(adot_ensemble* e) {
   if (e->d_tile_chan) cudaFree(e->d_tile_chan);
   if (e->d_tile_e0) cudaFree(e->d_tile_e0);
   if (e->d_chan_tile_end) cudaFree(e->d_chan_tile_end);
-  if (e->d_order) cudaFree(e->d_order);
+  for (int k = 0; k < 2; ++k)
+    if (e->plan[k].d_order) cudaFree(e->plan[k].d_order);
   if (e->d_ctl_mem) cudaFree(e->d_ctl_mem);
   if (e->d_io) cudaFree(e->d_io);
   if (e->cap_stream) cudaStreamDestroy(e->cap_stream);
@@ -1012,10 +1085,9 @@ adot_status adot_ensemble_create(const adot_ensemble_config* cfg, void* cuda_str
   int spg = cfg->steps_per_graph ? cfg->steps_per_graph : 48;
   e->steps_per_graph = ((spg + 5) / 6) * 6;
   e->step_kernel_cfg = cfg->step_kernel;
-  e->persistent = cfg->step_kernel == 0 || cfg->step_kernel == 3;
-  e->block_cfg = e->persistent ? 0 : cfg->block_threads;
-  e->run_block = (e->persistent && cfg->block_threads) ? cfg->block_threads : kRunBlockDefault;
-  e->run_cap = e->run_block == 512 ? 64 : 80;
+  const bool may_persist = cfg->step_kernel == 0 || cfg->step_kernel == 3;
+  e->block_cfg = may_persist ? 0 : cfg->block_threads;
+  e->run_block_cfg = may_persist ? cfg->block_threads : 0;
   e->t_end_dev = INFINITY;
 
   std::vector<double> dx(C), K3d(C);
@@ -1069,15 +1141,22 @@ adot_status adot_ensemble_create(const adot_ensemble_config* cfg, void* cuda_str
     e->dev.status = (unsigned*)take(sizeof(unsigned));
     e->dev.next = (int*)take(sizeof(int));
   }
-  if (err == cudaSuccess) err = cudaMalloc((void**)&e->d_order, sizeof(int) * C);
-  if (err == cudaSuccess)
-    err = cudaMemcpy(e->d_order, e->order.data(), sizeof(int) * C, cudaMemcpyHostToDevice);
-  if (err == cudaSuccess) {
-    int per_sm = 0, sms = 152;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, e->device);
-    err = ens_run_call(e, EnsRun{}, true, &per_sm);
-    if (per_sm < 1) per_sm = 1;
-    e->run_grid = (int)std::min<int64_t>((int64_t)sms * per_sm, C);
+  for (int k = 0; k < 2 && err == cudaSuccess; ++k) {
+    err = cudaMalloc((void**)&e->plan[k].d_order, sizeof(int) * C);
+    if (err == cudaSuccess)
+      err = cudaMemcpy(e->plan[k].d_order, e->order.data(), sizeof(int) * C, cudaMemcpyHostToDevice);
+    // until the first set_state: the configured form, persistent at the default shape
+    e->plan[k].persistent = may_persist;
+    e->plan[k].block = e->run_block_cfg ? e->run_block_cfg : kRunBlockDefault;
+    e->plan[k].grid = ens_run_grid(e, e->plan[k].block);
+    e->plan[k].imbalance = 1.0;
+  }
+  e->n_sms = 152;
+  cudaDeviceGetAttribute(&e->n_sms, cudaDevAttrMultiProcessorCount, e->device);
+  for (int i = 0; i < kNumRunBlocks; ++i) {
+    int per_sm = 0;
+    if (ens_run_call(e, EnsRun{}, kRunBlocks[i], 0, &per_sm) != cudaSuccess || per_sm < 1) per_sm = 1;
+    e->run_occ[i] = per_sm;
   }
   if (err == cudaSuccess) err = cudaMemcpy(e->d_off, e->off.data(), sizeof(int64_t) * (C + 1), cudaMemcpyHostToDevice);
   if (err == cudaSuccess) err = cudaMemcpy(e->d_dx, dx.data(), sizeof(double) * C, cudaMemcpyHostToDevice);
@@ -1091,7 +1170,7 @@ adot_status adot_ensemble_create(const adot_ensemble_config* cfg, void* cuda_str
       v0 = kEnsVariants[i];
       ++n_cand;
     }
-  e->tuned = n_cand == 1 || e->persistent;
+  e->tuned = n_cand == 1 || cfg->step_kernel == 3;
   if (err != cudaSuccess || build_tiles(e, v0) != ADOT_OK ||
       ens_reset_ctl(e) != ADOT_OK || ens_build_graph(e) != ADOT_OK) {
     ens_free(e);
@@ -1143,8 +1222,11 @@ adot_status adot_ensemble_set_state(adot_ensemble* e, const double* h, const dou
   st = ens_status(hc.status);
   if (st) return st;
   e->state_set = true;
-  if (e->persistent) return ens_order_by_work(e);
-  if (!e->tuned) return ens_tune(e, 2);
+  if (e->step_kernel_cfg == 0 || e->step_kernel_cfg == 3) {
+    st = ens_plan(e);
+    if (st) return st;
+  }
+  if (!e->tuned && !(e->plan[0].persistent && e->plan[1].persistent)) return ens_tune(e, 2);
   return ADOT_OK;
 }
 
@@ -1171,7 +1253,7 @@ adot_status adot_ensemble_run_to(adot_ensemble* e, double t_end, int64_t* launch
   if (!e || !e->state_set || !isfinite(t_end)) return ADOT_E_INVALID_ARG;
   adot_status st = ens_set_t_end(e, t_end);
   if (st) return st;
-  if (e->persistent) return ens_run(e, t_end, -1, launches_out);
+  if (e->plan[0].persistent) return ens_run(e, e->plan[0], t_end, -1, launches_out);
   int64_t launches = 0;
   for (;;) {
     const int64_t chunk = e->phase ? (6 - e->phase) : e->steps_per_graph;
@@ -1193,7 +1275,7 @@ adot_status adot_ensemble_step(adot_ensemble* e, int64_t n_steps) {
   if (!e || !e->state_set || n_steps < 0) return ADOT_E_INVALID_ARG;
   adot_status st = ens_set_t_end(e, INFINITY);
   if (st) return st;
-  if (e->persistent) return ens_run(e, INFINITY, n_steps, nullptr);
+  if (e->plan[1].persistent) return ens_run(e, e->plan[1], INFINITY, n_steps, nullptr);
   st = ens_enqueue(e, n_steps);
   if (st) return st;
   HostCtl hc;
@@ -1225,11 +1307,11 @@ adot_status adot_ensemble_query(adot_ensemble* e, double* t_out, int64_t* steps_
 adot_status adot_ensemble_info(adot_ensemble* e, int32_t* block_out, int64_t* tiles_out,
                                int32_t* grid_out, int32_t* step_kernel_out) {
   if (!e) return ADOT_E_INVALID_ARG;
-  if (e->persistent) {
+  if (e->plan[0].persistent) {
     if (step_kernel_out) *step_kernel_out = 3;
-    if (block_out) *block_out = e->run_block;
+    if (block_out) *block_out = e->plan[0].block;
     if (tiles_out) *tiles_out = e->C;
-    if (grid_out) *grid_out = e->run_grid;
+    if (grid_out) *grid_out = e->plan[0].grid;
     return ADOT_OK;
   }
   if (step_kernel_out) *step_kernel_out = e->warp ? 2 : 1;

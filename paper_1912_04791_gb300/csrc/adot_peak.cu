@@ -12,6 +12,8 @@
 //   2 RSQ     float32 reciprocal square root on the multi-function unit
 //   3 SIN     float32 sine approximation on the multi-function unit
 //   4 DFMA    float64 fused multiply-add, 2 flops
+//   5 TANH    float32 hyperbolic tangent approximation on the multi-function unit
+//   6 TANH2   paired bfloat16 hyperbolic tangent approximation (2 ops)
 #include <cuda_runtime.h>
 
 #include "../../include/adot.h"
@@ -25,6 +27,18 @@ constexpr int kBlocksPerSm = 8;
 __device__ __forceinline__ float mufu_rsq(float x) {
   float y;
   asm volatile("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ float mufu_tanh(float x) {
+  float y;
+  asm volatile("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ unsigned mufu_tanh_bf16x2(unsigned x) {
+  unsigned y;
+  asm volatile("tanh.approx.bf16x2 %0, %1;" : "=r"(y) : "r"(x));
   return y;
 }
 
@@ -51,6 +65,19 @@ __global__ void __launch_bounds__(kThreads) k_pipe_probe(float* out, double* out
 #pragma unroll
     for (int c = 0; c < kChains; ++c) s += x[c];
     if (s == -1.0) out64[t] = s;
+  } else if constexpr (KIND == 6) {
+    // bf16 pairs near 0.5 (0x3f00): tanh maps them into (0.46, 0.47), a fixed point region
+    unsigned x[kChains];
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) x[c] = 0x3f003f00u + (unsigned)((t + c) & 7) * 0x00010001u;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+      for (int c = 0; c < kChains; ++c) x[c] = mufu_tanh_bf16x2(x[c] + 0x00010001u);
+    }
+    unsigned s = 0;
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) s ^= x[c];
+    if (s == 0xffffffffu) out[t] = (float)s;
   } else if constexpr (KIND == 1) {
     float2 x[kChains];
 #pragma unroll
@@ -74,6 +101,7 @@ __global__ void __launch_bounds__(kThreads) k_pipe_probe(float* out, double* out
         if constexpr (KIND == 0) x[c] = fmaf(x[c], a, b);
         if constexpr (KIND == 2) x[c] = mufu_rsq(x[c] + b);
         if constexpr (KIND == 3) x[c] = mufu_sin(x[c] + b);
+        if constexpr (KIND == 5) x[c] = mufu_tanh(x[c] + b);
       }
     }
     float s = 0.0f;
@@ -96,6 +124,8 @@ cudaError_t launch_kind(int kind, unsigned grid, float* out, double* out64, int 
     case 1: return launch_probe<1>(grid, out, out64, iters, s);
     case 2: return launch_probe<2>(grid, out, out64, iters, s);
     case 3: return launch_probe<3>(grid, out, out64, iters, s);
+    case 5: return launch_probe<5>(grid, out, out64, iters, s);
+    case 6: return launch_probe<6>(grid, out, out64, iters, s);
     default: return launch_probe<4>(grid, out, out64, iters, s);
   }
 }
@@ -104,7 +134,7 @@ cudaError_t launch_kind(int kind, unsigned grid, float* out, double* out64, int 
 
 extern "C" adot_status adot_measure_pipe(int kind, int device, double* rate_out,
                                          double* seconds_out) {
-  if (kind < 0 || kind > 4 || !rate_out) return ADOT_E_INVALID_ARG;
+  if (kind < 0 || kind > 6 || !rate_out) return ADOT_E_INVALID_ARG;
   if (device >= 0 && cudaSetDevice(device) != cudaSuccess) return ADOT_E_CUDA;
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -130,7 +160,7 @@ extern "C" adot_status adot_measure_pipe(int kind, int device, double* rate_out,
   if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) goto done;
   if (cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess || !(ms > 0.0f)) goto done;
   {
-    const double per_op = (kind == 0 || kind == 4) ? 2.0 : (kind == 1 ? 4.0 : 1.0);
+    const double per_op = (kind == 0 || kind == 4 || kind == 6) ? 2.0 : (kind == 1 ? 4.0 : 1.0);
     const double ops = per_op * (double)kChains * (double)iters * (double)threads;
     *rate_out = ops / (ms * 1e-3);
     if (seconds_out) *seconds_out = ms * 1e-3;

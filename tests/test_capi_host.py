@@ -146,6 +146,13 @@ def test_null_arguments_rejected(L):
     L.adot_destroy(None)
 
 
+def test_measure_pipe_rejects_bad_kind(L):
+    r = ctypes.c_double()
+    assert L.adot_measure_pipe(7, -1, ctypes.byref(r), None) == adot.E_INVALID_ARG
+    assert L.adot_measure_pipe(-1, -1, ctypes.byref(r), None) == adot.E_INVALID_ARG
+    assert L.adot_measure_pipe(0, -1, None, None) == adot.E_INVALID_ARG
+
+
 def test_invalid_ensemble_config_rejected(L):
     import numpy as np
     n = np.array([10, 0], dtype=np.int64)

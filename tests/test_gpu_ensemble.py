@@ -136,7 +136,7 @@ def test_ensemble_steps_equal_single_channel_contexts(gpu):
             assert np.abs(a[o[c]:o[c + 1]] - b).max() <= 1e-12 * max(np.abs(b).max(), 1e-300)
 
 
-@pytest.mark.parametrize("kern", [0, 4])
+@pytest.mark.parametrize("kern", [0, 3, 4])
 def test_large_ensemble_all_channels_land_on_t_end(gpu, kern):
     E = W.riemann_ensemble(256, seed=11, n_min=200, n_max=20000)
     with gpu.Ensemble.from_workload(E, gpu.FP32, step_kernel=kern) as ens:
@@ -146,10 +146,14 @@ def test_large_ensemble_all_channels_land_on_t_end(gpu, kern):
         h, q, z = ens.get_state()
         form = ens.info()[3]
     assert (t == 0.02).all()
-    if kern == 0:  # persistent channel loops: one launch per 16384 steps
-        assert form == 3 and launches == 1
+    if kern == 3:
+        assert form == 3
+    if kern == 4:
+        assert form in (1, 2)
+    if form == 3:  # persistent channel loops: one launch per 16384 steps
+        assert launches == 1
     else:  # one launch per step of the longest-running channel
-        assert form in (1, 2) and launches >= steps.max()
+        assert launches >= steps.max()
     assert np.isfinite(h).all() and (h > 0).all()
     # longer channels need more steps (dt ~ dx)
     assert steps[np.argmax(E.n_cells)] > steps[np.argmin(E.n_cells)]
@@ -269,3 +273,28 @@ def test_persistent_dry_out_is_reported(gpu):
         assert e.value.status in (gpu.E_NONPOSITIVE_DEPTH, gpu.E_NONFINITE)
         h, q, z = ens.get_state()
         assert h.shape == (int(E.n_cells.sum()),)
+
+
+def test_form_chosen_by_estimated_balance(gpu):
+    """step_kernel = 0 runs the persistent form when the list schedule of the
+    channels (largest work first) onto its CTAs is balanced (many channels of
+    equal length) and per-step launches when one CTA would hold a channel much
+    longer than its share (a few long channels among short ones); both give the
+    forced persistent form's float64 state."""
+    cases = {"balanced": [300] * 2048, "skewed": [40000, 30000] + [200] * 40}
+    for name, sizes in cases.items():
+        E = _small_ensemble(sizes, seed=13)
+        out = []
+        for kern in (0, 3):
+            with gpu.Ensemble.from_workload(E, gpu.FP64, step_kernel=kern) as ens:
+                ens.set_state(E.h, E.q, E.z)
+                form = ens.info()[3]
+                ens.run_to(0.01)
+                t, steps, _ = ens.query()
+                out.append((form, ens.get_state(), steps))
+        (fa, sa, na), (fb, sb, nb) = out
+        assert fb == 3
+        assert (fa == 3) == (name == "balanced"), (name, fa)
+        assert np.array_equal(na, nb)
+        for x, y in zip(sa, sb):
+            assert np.abs(x - y).max() <= 1e-14 * np.abs(y).max()
