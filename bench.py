@@ -107,6 +107,9 @@ def parse():
                          "workload's 1 s (0 = skip)")
     ap.add_argument("--ensemble-channels", type=int, default=4096,
                     help="channels of the ensemble measurement (the first of the seeded 4096)")
+    ap.add_argument("--ensemble-form", type=int, default=0,
+                    help="step_kernel of the ensemble's main measurement: 0 = chosen per state, "
+                         "3 = persistent channel loops, 1/2/4 = per-step launches")
     ap.add_argument("--ensemble-per-step", type=int, default=1,
                     help="also time the per-step form of the ensemble (0 = skip)")
     ap.add_argument("--sur-steps", type=int, default=20000,
@@ -790,7 +793,7 @@ def main():
             E = W.Ensemble(E.n_cells[:args.ensemble_channels].copy(), E.length[:args.ensemble_channels].copy(),
                            E.Ag[:args.ensemble_channels].copy(), *(v[:E.offsets[args.ensemble_channels]].copy()
                                                                    for v in (E.h, E.q, E.z)))
-        forms = [0] + ([4] if args.ensemble_per_step else [])
+        forms = [args.ensemble_form] + ([4] if args.ensemble_per_step and args.ensemble_form != 4 else [])
         runs = {}
         for kern in forms:
             with adot.Ensemble.from_workload(E, adot.FP32, device=local, stream=stream,
@@ -815,8 +818,9 @@ def main():
                           ("channels" if ens_kernel == 3 else "tiles"): n_tiles, "grid": grid,
                           "all_at_t_end": bool((t_c == args.ensemble_t_end).all())}
         ensemble = {"workload": f"{len(E.n_cells)} movable-bed Riemann channels, N_c log-uniform [1e3,1e5], FP32",
-                    "total_cells": int(E.n_cells.sum()), "t_end": args.ensemble_t_end, **runs[0]}
-        if 4 in runs:
+                    "total_cells": int(E.n_cells.sum()), "t_end": args.ensemble_t_end,
+                    **runs[args.ensemble_form]}
+        if 4 in runs and args.ensemble_form != 4:
             ensemble["other_form"] = runs[4]
 
     # Strickler friction source (Sec. 2) on the benchmark workload, and the Soni
