@@ -40,11 +40,14 @@ UNIT = "cell-updates/s"
 #  xu:    XU-pipe thread instructions per cell-update (sm__inst_executed_pipe_xu x 32 / cells);
 #  dram:  dram__bytes_read.sum + dram__bytes_write.sum per cell-update.
 KERNEL_COUNTS = {
-    ("warp", 256, 80): {"flops": (2 * 500.39e6 + 344.19e6 + 609.19e6) / 4e6 * (1 - 3648 / 4e6),
-                        "instr": 73.305e6 * 32 / 4e6, "xu": 3.5214e6 * 32 / 4e6,
-                        "dram": (97.95e6 + 56.53e6) / 4e6},
-    ("warp", 256, 64): {"flops": None, "instr": 75.432e6 * 32 / 4e6, "xu": 3.5286e6 * 32 / 4e6,
-                        "dram": (98.55e6 + 59.74e6) / 4e6},
+    # static ranges over 6/8 of the chunks plus the 63-cell work pool: at 4e6 cells and
+    # 3648 warps, 4,020,875 edges evaluated for 4,000,001 (20,874 evaluated twice, removed)
+    ("warp", 256, 80): {"flops": (2 * 502.199171e6 + 345.064625e6 + 607.438689e6) / 4e6
+                        * (1 - 20874 / 4e6),
+                        "instr": 75.28878e6 * 32 / 4e6, "xu": 3.672718e6 * 32 / 4e6,
+                        "dram": (99.697152e6 + 58.275584e6) / 4e6},
+    ("warp", 256, 64): {"flops": None, "instr": 82.016855e6 * 32 / 4e6, "xu": 4.063696e6 * 32 / 4e6,
+                        "dram": (101.936128e6 + 60.351232e6) / 4e6},
     ("order2", 256, 64): {"flops": None, "instr": None, "xu": None, "dram": None},
 }
 # The block kernel's all-scalar count (1 edge in 256 evaluated twice, removed).

@@ -24,6 +24,10 @@ struct Ctl {
   double t_end;     // steps are clipped to land on t_end; no work once t >= t_end
   unsigned status;  // sticky ST_* bits
   unsigned pad;
+  // work-pool head of the warp-tile step kernel: 0 between launches (the warp
+  // that takes the launch's last ticket puts it back)
+  unsigned grab;
+  unsigned pad2;
 };
 
 struct StateF32 {

@@ -75,6 +75,8 @@ __global__ void k_noalloc_ctl_init(Ctl* ctl, double t0) {
   ctl->t_end = INFINITY;
   ctl->status = 0u;
   ctl->pad = 0u;
+  ctl->grab = 0u;
+  ctl->pad2 = 0u;
 }
 
 adot_status from_bits(unsigned bits) {

@@ -502,16 +502,43 @@ __device__ __forceinline__ void warp_step_size(const StepParams& p, int slot, in
   done = __shfl_sync(0xffffffffu, done0, 0) != 0;
 }
 
-// Persistent warp-tile variant of the time step. Warp w owns a contiguous
-// range of cells, processed in chunks of 32 edges (one per lane): the edge of
-// lane l in chunk j is E_w + 32 j + l, and the lane updates cell e - 1 with D-
-// of its own edge and D+ of edge e - 1, taken from lane l - 1 by a shuffle or,
-// in lane 0, carried over from lane 31 of the previous chunk. So a warp of k
-// chunks updates 32 k - 1 cells and consecutive warps share one edge (the only
-// edge evaluated twice). With A active warps and K chunks in all, the ranges
-// cover 32 K - A >= n cells; each warp takes K / A or K / A + 1 chunks. Warps
-// never wait for one another; each keeps its CFL maximum in a register and
-// folds it into the control slot once at the end.
+// Share of a warp's chunks taken as one static contiguous range (in eighths)
+// and the chunks per pool group. On the 1e7-cell smooth workload (cell-updates/s,
+// A-DOT / PRICE-C): 8/8 4.71e10 / 7.9e10, 7/8 4.81e10 / 8.2e10, 6/8 5.04-5.07e10 /
+// 8.5-8.6e10, 5/8 5.02e10 / 8.4e10, 4/8 4.92e10 / 8.1e10, all pool 5.04e10 /
+// 6.3e10 (contention on the counter at PRICE-C's rate); groups of 1 or 4 chunks
+// at 6/8: 4.92e10 and 5.02e10; static groups interleaved over the warps instead
+// of contiguous ranges: at most 4.97e10. Measurement builds may set other values
+// (-DADOT_STATIC_EIGHTHS=k, -DADOT_POOL_CHUNKS=c).
+#ifndef ADOT_STATIC_EIGHTHS
+#define ADOT_STATIC_EIGHTHS 6
+#endif
+#ifndef ADOT_POOL_CHUNKS
+#define ADOT_POOL_CHUNKS 2
+#endif
+
+// Persistent warp-tile variant of the time step. A warp processes ranges of
+// consecutive edges in chunks of 32 (one per lane): the edge of lane l in
+// chunk j of a range starting at edge E is E + 32 j + l, and the lane updates
+// cell e - 1 with D- of its own edge and D+ of edge e - 1, taken from lane
+// l - 1 by a shuffle or, in lane 0, carried over from lane 31 of the previous
+// chunk. A range of k chunks updates 32 k - 1 cells, and consecutive ranges
+// share one edge (the only edge evaluated twice).
+//  - static part: with W warps and K = n / 32 chunks, each warp first takes a
+//    contiguous range of k_s = floor((6/8) K / W) chunks (none when k_s < 2),
+//    so cells [0, N_s) with N_s = W' (32 k_s - 1), W' <= W;
+//  - work pool: cells [N_s, n) in groups of 63 cells (2 chunks), handed out by
+//    an atomic counter in the control block; a warp asks for its next group
+//    before it computes the current one, so the atomic's latency is hidden.
+// The pool evens out the warps' finishing times: with static ranges alone the
+// schedulers were active 92.6 % of a step at N = 1e7 (SM active cycles from
+// 391k to 426k of 430k), waiting for the slowest ranges. Every warp's
+// requests end with exactly one that finds the pool empty, so a launch takes
+// n_groups + W tickets; the warp holding the last one puts the counter back to
+// 0 for the next launch. Warps never wait for
+// one another; each keeps its CFL maximum in a register and folds it into the
+// control slot once at the end. Which warp evaluates an edge does not change
+// its value, so the results do not depend on the split.
 //
 // SCHEME 0 evaluates the DOT edge of Eq. DOTjumpN; SCHEME 1 the PRICE-C edge
 // (edge_fluct_price), everything else unchanged.
@@ -526,19 +553,14 @@ __global__ void __launch_bounds__(B, MinBlocks<B, CAP>::value)
   const int64_t n = p.n;
   Ctl* ctl = p.ctl;
 
+  // first pool ticket, asked for before anything else (used after the static range)
+  unsigned ticket = 0u;
+  if (lane == 0) ticket = atomicAdd(&ctl->grab, 1u);
+
   R nu;
   bool done;
   warp_step_size<R>(p, slot, lane, gw == 0, nu, done);
   const R inv_nu = (SCHEME == 1 && !done) ? R(1) / nu : R(0);  // dx/dt of Eq. AiPRICE
-
-  // active warps (at least 31 cells each) and chunks in all
-  const int64_t nact = d_min_i64(nwarps, (n + 30) / 31);
-  const int64_t K = (n + nact + 31) / 32;
-  const int64_t kb = K / nact, kr = K % nact;
-  const int64_t kw = (gw < nact) ? kb + (gw < kr ? 1 : 0) : 0;
-  const int64_t e0 = 32 * (gw * kb + d_min_i64(gw, kr)) - gw;  // first edge = first cell
-  // edges left in the range after the chunk's first (< 2^31 per warp)
-  int rem = (int)(d_min_i64(e0 + 32 * kw - 1, n) - e0);
 
   // Lane 0 carries D+ of the previous chunk's last edge: in registers, or with
   // the friction/feed/ghost extension compiled in, in shared memory (lane 0 is
@@ -550,12 +572,48 @@ __global__ void __launch_bounds__(B, MinBlocks<B, CAP>::value)
 
   unsigned flags = 0;
   R rho_run = R(0);
+  // the split: static ranges of cs cells over cells [0, n_s), then pool groups
+  auto static_split = [&](int64_t& cs, int64_t& n_s) {
+    int64_t ks = (((n + 31) / 32) * ADOT_STATIC_EIGHTHS / 8) / nwarps;
+    if (ks < 2) ks = 0;
+    cs = 32 * ks - 1;                                // cells per static range
+    n_s = ks ? d_min_i64(nwarps, n / cs) * cs : 0;    // cells [0, n_s)
+  };
+  constexpr int64_t kGroup = 32 * ADOT_POOL_CHUNKS - 1;  // cells per pool group
+  // current range: next chunk's first edge eb, rem = edges after it (< 2^31;
+  // negative when the range is finished)
+  int64_t eb = 0;
+  int rem = -1;
+  {
+    int64_t cs, n_s;
+    static_split(cs, n_s);
+    if ((gw + 1) * cs <= n_s) {
+      eb = gw * cs;
+      rem = (int)cs;
+    }
+  }
   bool lead = lane >= 1;  // the lane's cell is in the range (all lanes after the first chunk)
-  for (int64_t eb = e0; rem >= 0; eb += 32, rem -= 32) {
+  for (;;) {
+    if (rem < 0) {
+      // next range from the pool
+      int64_t cs, n_s;
+      static_split(cs, n_s);
+      const int64_t n_groups = (n - n_s + kGroup - 1) / kGroup;
+      const int64_t g = (int64_t)__shfl_sync(0xffffffffu, ticket, 0);
+      if (g >= n_groups) {
+        // the launch's last ticket: every other request has been served
+        if (lane == 0 && g == n_groups + nwarps - 1) atomicExch(&ctl->grab, 0u);
+        break;
+      }
+      if (lane == 0) ticket = atomicAdd(&ctl->grab, 1u);
+      eb = n_s + g * kGroup;
+      rem = (int)d_min_i64(kGroup, n - eb);
+      lead = lane >= 1;
+    }
     const int64_t e = eb + lane;
     const bool in_range = lane <= rem;
     {
-      // the warp's next chunk into L2 while this one is computed
+      // the range's next chunk into L2 while this one is computed
       const int64_t cn = e + 31;
       if (rem >= 32 && cn < n) {
         asm volatile("prefetch.global.L2 [%0];" ::"l"(in.h + cn));
@@ -621,6 +679,8 @@ __global__ void __launch_bounds__(B, MinBlocks<B, CAP>::value)
       }
     }
     lead = true;
+    eb += 32;
+    rem -= 32;
   }
   rho_run = warp_max(rho_run);
   if (lane == 0 && !done && rho_run > R(0))
