@@ -212,6 +212,27 @@ def max_over_ranks(value: float, dist, device=None) -> float:
     return float(t.item())
 
 
+def sum_over_ranks(value: float, dist, device=None) -> float:
+    """Sum of a per-rank value (work done by every rank); the value itself when
+    not distributed."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def min_over_ranks(value: float, dist, device=None) -> float:
+    """Smallest per-rank value (e.g. whether every rank's check held)."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MIN)
+    return float(t.item())
+
+
 def oracle_throughput(n: int, steps: int, threads: int | None = None):
     """The FP64 oracle (as it stands) on the smooth periodic workload with n
     cells for `steps` time steps on the host cores. Returns (cell-updates/s,
@@ -788,14 +809,20 @@ def main():
     if rank == 0 and not args.no_peaks:
         peaks = measure_pipes(adot, local)
 
-    # batched ensemble: 4096 movable-bed Riemann channels, N_c log-uniform in [1e3, 1e5]
+    # batched ensemble: 4096 movable-bed Riemann channels, N_c log-uniform in [1e3, 1e5];
+    # with N ranks each runs its shard of the channels (no data moves between ranks):
+    # the time is the slowest rank's, the cell-updates the sum over ranks
     ensemble = None
-    if args.ensemble_t_end > 0 and rank == 0:
+    if args.ensemble_t_end > 0:
         E = W.riemann_ensemble(4096)
         if args.ensemble_channels < 4096:
             E = W.Ensemble(E.n_cells[:args.ensemble_channels].copy(), E.length[:args.ensemble_channels].copy(),
                            E.Ag[:args.ensemble_channels].copy(), *(v[:E.offsets[args.ensemble_channels]].copy()
                                                                    for v in (E.h, E.q, E.z)))
+        total_cells = int(E.n_cells.sum())
+        n_channels = len(E.n_cells)
+        if ws > 1:
+            E = W.shard_ensemble(E, rank, ws)
         forms = [args.ensemble_form] + ([4] if args.ensemble_per_step and args.ensemble_form != 4 else [])
         runs = {}
         for kern in forms:
@@ -804,6 +831,8 @@ def main():
                 ens.set_state(E.h, E.q, E.z)
                 blk, n_tiles, grid, ens_kernel = ens.info()
                 torch.cuda.synchronize(dev)
+                if dist is not None:
+                    dist.barrier()
                 a = torch.cuda.Event(enable_timing=True)
                 b = torch.cuda.Event(enable_timing=True)
                 a.record(stream)
@@ -812,16 +841,23 @@ def main():
                 torch.cuda.synchronize(dev)
                 t_c, steps_c, cu = ens.query()
                 ms_e = a.elapsed_time(b)
+            all_at = bool((t_c == args.ensemble_t_end).all())
+            sec = max_over_ranks(ms_e * 1e-3, dist, device=dev)
+            cu_all = sum_over_ranks(float(cu), dist, device=dev)
+            all_at = min_over_ranks(1.0 if all_at else 0.0, dist, device=dev) == 1.0
             name = {1: "per-step block tiles", 2: "per-step warp tiles",
                     3: "persistent channel loops"}[ens_kernel]
-            runs[kern] = {"form": name, "cell_updates": int(cu), "seconds": ms_e * 1e-3,
-                          "cell_updates_per_s": cu / (ms_e * 1e-3), "launches": int(launches),
-                          "max_steps": int(steps_c.max()), "min_steps": int(steps_c.min()),
+            runs[kern] = {"form": name, "cell_updates": int(cu_all), "seconds": sec,
+                          "cell_updates_per_s": cu_all / sec, "launches": int(launches),
+                          "max_steps": int(max_over_ranks(float(steps_c.max()), dist, device=dev)),
+                          "min_steps": int(min_over_ranks(float(steps_c.min()), dist, device=dev)),
                           "threads_per_block": blk,
                           ("channels" if ens_kernel == 3 else "tiles"): n_tiles, "grid": grid,
-                          "all_at_t_end": bool((t_c == args.ensemble_t_end).all())}
-        ensemble = {"workload": f"{len(E.n_cells)} movable-bed Riemann channels, N_c log-uniform [1e3,1e5], FP32",
-                    "total_cells": int(E.n_cells.sum()), "t_end": args.ensemble_t_end,
+                          "all_at_t_end": all_at}
+        ensemble = {"workload": f"{n_channels} movable-bed Riemann channels, N_c log-uniform [1e3,1e5], FP32",
+                    "total_cells": total_cells, "t_end": args.ensemble_t_end,
+                    "ranks": ws, "sharding": "channels split over the ranks by list scheduling of "
+                                             "N_c^2/length_c, no collective" if ws > 1 else None,
                     **runs[args.ensemble_form]}
         if 4 in runs and args.ensemble_form != 4:
             ensemble["other_form"] = runs[4]

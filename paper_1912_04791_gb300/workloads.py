@@ -222,6 +222,30 @@ def riemann_ensemble(n_channels: int = 4096, seed: int = 20191210, n_min: int = 
                     np.concatenate(zs))
 
 
+def shard_ensemble(E: "Ensemble", rank: int, world: int) -> "Ensemble":
+    """The channels of rank `rank` when the ensemble is split over `world`
+    processes (one per GPU; the channels are independent, so no data moves
+    between them): longest-processing-time list scheduling of the channels,
+    work N_c^2 / length_c (cells times steps, dt ~ dx), largest first onto the
+    least-loaded rank (ties to the lower rank), the rank's channels kept in
+    their original order."""
+    if world < 1 or not 0 <= rank < world:
+        raise ValueError("rank outside [0, world)")
+    n = E.n_cells.astype(np.float64)
+    work = n * n / E.length
+    load = np.zeros(world)
+    owner = np.empty(len(n), dtype=np.int64)
+    for c in sorted(range(len(n)), key=lambda c: (-work[c], c)):
+        r = int(np.argmin(load))
+        owner[c] = r
+        load[r] += work[c]
+    mine = np.flatnonzero(owner == rank)
+    o = E.offsets
+    cells = np.concatenate([np.arange(o[c], o[c + 1]) for c in mine]) if len(mine) else np.zeros(0, np.int64)
+    return Ensemble(E.n_cells[mine].copy(), E.length[mine].copy(), E.Ag[mine].copy(), E.h[cells].copy(),
+                    E.q[cells].copy(), E.z[cells].copy(), E.xi, E.cfl, E.t_end, E.g)
+
+
 def mlp_init(seed: int = 2019, sizes=(7, 128, 128, 128, 128, 9)) -> np.ndarray:
     """Initial surrogate parameters, packed layer by layer (W_l [out][in]
     row-major, then b_l): He-normal weights, zero biases."""
