@@ -825,9 +825,9 @@ def main():
             E = W.shard_ensemble(E, rank, ws)
         forms = [args.ensemble_form] + ([4] if args.ensemble_per_step and args.ensemble_form != 4 else [])
         runs = {}
-        for kern in forms:
+        for form_k in forms:
             with adot.Ensemble.from_workload(E, adot.FP32, device=local, stream=stream,
-                                             step_kernel=kern) as ens:
+                                             step_kernel=form_k) as ens:
                 ens.set_state(E.h, E.q, E.z)
                 blk, n_tiles, grid, ens_kernel = ens.info()
                 torch.cuda.synchronize(dev)
@@ -847,7 +847,7 @@ def main():
             all_at = min_over_ranks(1.0 if all_at else 0.0, dist, device=dev) == 1.0
             name = {1: "per-step block tiles", 2: "per-step warp tiles",
                     3: "persistent channel loops"}[ens_kernel]
-            runs[kern] = {"form": name, "cell_updates": int(cu_all), "seconds": sec,
+            runs[form_k] = {"form": name, "cell_updates": int(cu_all), "seconds": sec,
                           "cell_updates_per_s": cu_all / sec, "launches": int(launches),
                           "max_steps": int(max_over_ranks(float(steps_c.max()), dist, device=dev)),
                           "min_steps": int(min_over_ranks(float(steps_c.min()), dist, device=dev)),
