@@ -1442,8 +1442,9 @@ __global__ void __launch_bounds__(kTwThreads) k_tc_wgrad(const __nv_bfloat16* __
 //  warp 0, one thread: issues every layer's tcgen05.mma (as in k_mlp_tc);
 //  warps 1-4: producers; build the layer-0 operand of the CTA's tiles (32 rows
 //    per warp, one per lane) into a ring of kRing entries, up to kRing tiles ahead;
-//  warps 5-20: epilogue; warp w reads TMEM lane quadrant w % 4 and the 32
-//    accumulator columns 32 ((w - 5) / 4) .. + 31 of the tile in work.
+//  warps 5-20: epilogue, two groups of 8 (warps 5-12 and 13-20) taking the
+//    jobs alternately (group = job number mod 2); warp w reads TMEM lane
+//    quadrant w % 4 and the 64 accumulator columns 64 (((w - 5) / 4) mod 2) .. + 63.
 // Three tile slots, each with 128 TMEM columns and a 32 KB activation tile,
 // rotate through the jobs (slot, layer) in the fixed order
 //   for k = 0, 1, ...: for s = 0, 1, 2: layer k % 5 of the slot's tile 3 (k / 5) + s,
@@ -1457,7 +1458,11 @@ __global__ void __launch_bounds__(kTwThreads) k_tc_wgrad(const __nv_bfloat16* __
 // the TMEM is freed.
 
 constexpr int kTpProducers = 4;  // producer warps, 32 tile rows each
-constexpr int kTpWarps = 1 + kTpProducers + 16;
+// epilogue warps: two groups of kTpEpiWarps that take alternate jobs, so that one
+// group's tensor-memory loads and hand-offs overlap the other's GELU work
+constexpr int kTpEpiWarps = 8;
+constexpr int kTpWarps = 1 + kTpProducers + 2 * kTpEpiWarps;
+static_assert(kTpEpiWarps == 8, "each epilogue group covers the four TMEM lane quadrants twice");
 constexpr int kTpThreads = kTpWarps * 32;
 constexpr int kTpSlots = 3;
 constexpr int kRing = 4;
@@ -1476,7 +1481,9 @@ static_assert(((kTpSmem + 1024) >> 4) + 7 * 16 < (1u << 14), "descriptor address
 
 struct TpBars {
   uint64_t ring_full[kRing], ring_empty[kRing];
-  uint64_t acc_full[kTpSlots], act_ready[kTpSlots];
+  // accumulator full, per slot and epilogue group (job j commits to group j % 2's
+  // barrier, so each group waits only on the phases of its own jobs, in order)
+  uint64_t acc_full[kTpSlots * 2], act_ready[kTpSlots];
   uint64_t drain;
   uint64_t wdesc[kLayers];  // weight descriptors (written and read by the issuing thread only)
 };
@@ -1563,8 +1570,9 @@ __global__ void __launch_bounds__(kTpThreads, 1)
       mbar_init(&bars.ring_empty[r], 1);
     }
     for (int s2 = 0; s2 < kTpSlots; ++s2) {
-      mbar_init(&bars.acc_full[s2], 1);
-      mbar_init(&bars.act_ready[s2], 16);
+      mbar_init(&bars.acc_full[2 * s2], 1);
+      mbar_init(&bars.acc_full[2 * s2 + 1], 1);
+      mbar_init(&bars.act_ready[s2], kTpEpiWarps);
     }
     mbar_init(&bars.drain, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -1600,11 +1608,13 @@ __global__ void __launch_bounds__(kTpThreads, 1)
 #pragma unroll
       for (int l = 0; l < kLayers; ++l) s_wdesc[l] = tc_desc(base + tc_w_off(l), dim_in(l));
       bool ok = true;
+      int job = 0;  // the jobs in order; job j goes to epilogue group j % 2
       for (int kk = 0; ok && kk < rounds * kLayers; ++kk) {
         const int rd = kk / kLayers, l = kk - rd * kLayers;
         for (int sl = 0; ok && sl < kTpSlots; ++sl) {
           const int m = kTpSlots * rd + sl;
           if (m >= my_tiles) break;
+          const int grp = (job++) & 1;
           if (kk > 0) ok = tp_wait(&bars.act_ready[sl], (uint32_t)((kk - 1) & 1), &s_abort);
           const int r = m & (kRing - 1);
           if (ok && l == 0) ok = tp_wait(&bars.ring_full[r], (uint32_t)((m / kRing) & 1), &s_abort);
@@ -1623,7 +1633,7 @@ __global__ void __launch_bounds__(kTpThreads, 1)
           // (the test hook leaves CTA 0's first job uncommitted: its epilogue's
           // bounded wait runs out and the kernel reports ST_TIMEOUT)
           if (!(P.withhold_commit && blockIdx.x == 0 && kk == 0 && sl == 0))
-            tc_commit(smem_addr(&bars.acc_full[sl]));
+            tc_commit(smem_addr(&bars.acc_full[2 * sl + grp]));
           if (l == 0) tc_commit(smem_addr(&bars.ring_empty[r]));
         }
       }
@@ -1702,42 +1712,50 @@ __global__ void __launch_bounds__(kTpThreads, 1)
   } else {
     // ---------------- epilogue ----------------
     const int quad = warp & 3;
-    const int cb = (warp - 1 - kTpProducers) >> 2;  // 32-column block 0..3
+    const int eg = (warp - 1 - kTpProducers) / kTpEpiWarps;             // group 0 or 1
+    const int half = ((warp - 1 - kTpProducers) % kTpEpiWarps) >> 2;     // 64-column half 0..1
     const int row = quad * 32 + lane;        // TMEM lane = tile row
     const float c1f = 0.0356774081f, c0f = 0.7978845608f;
     const uint64_t c1 = ((uint64_t)__float_as_uint(c1f) << 32) | __float_as_uint(c1f);
     const uint64_t c0 = ((uint64_t)__float_as_uint(c0f) << 32) | __float_as_uint(c0f);
     bool ok = true;
+    int job = 0;  // jobs in the fixed (layer round, slot) order; this group takes job % 2 == eg
+    uint32_t ph = 0;  // bit sl: phase parity of this group's accumulator barrier of slot sl
     for (int kk = 0; ok && kk < rounds * kLayers; ++kk) {
       const int rd = kk / kLayers, l = kk - rd * kLayers;
       for (int sl = 0; sl < kTpSlots; ++sl) {
         const int m = kTpSlots * rd + sl;
         if (m >= my_tiles) break;
-        ok = __all_sync(0xffffffffu, tp_wait(&bars.acc_full[sl], (uint32_t)(kk & 1), &s_abort));
+        if (((job++) & 1) != eg) continue;
+        ok = __all_sync(0xffffffffu, tp_wait(&bars.acc_full[2 * sl + eg], (ph >> sl) & 1u, &s_abort));
+        ph ^= 1u << sl;
         if (!ok) break;
         tc_fence_after();
         const uint32_t t_row = tmem + (uint32_t)(sl * kTcRows) + ((uint32_t)(quad * 32) << 16);
         if (l < kLayers - 1) {
           unsigned char* act = sm + kTpActOff + sl * kTcActBytes;
-          const int c = cb * 32;
-          uint32_t r[32];
-          tmem_ld_x32(t_row + (uint32_t)c, r);
-          tmem_wait_ld(r);
-          const float* b = sBias + b_offset(l) + c;
-          uint32_t pk[16];
+#pragma unroll 1
+          for (int cb = 0; cb < 2; ++cb) {
+            const int c = half * 64 + cb * 32;
+            uint32_t r[32];
+            tmem_ld_x32(t_row + (uint32_t)c, r);
+            tmem_wait_ld(r);
+            const float* b = sBias + b_offset(l) + c;
+            uint32_t pk[16];
 #pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const float4 bb = *reinterpret_cast<const float4*>(b + 4 * j);
-            pk[2 * j] = gelu2x_bf16(r[4 * j], r[4 * j + 1], __float_as_uint(bb.x), __float_as_uint(bb.y), c1, c0);
-            pk[2 * j + 1] =
-                gelu2x_bf16(r[4 * j + 2], r[4 * j + 3], __float_as_uint(bb.z), __float_as_uint(bb.w), c1, c0);
+            for (int j = 0; j < 8; ++j) {
+              const float4 bb = *reinterpret_cast<const float4*>(b + 4 * j);
+              pk[2 * j] = gelu2x_bf16(r[4 * j], r[4 * j + 1], __float_as_uint(bb.x), __float_as_uint(bb.y), c1, c0);
+              pk[2 * j + 1] =
+                  gelu2x_bf16(r[4 * j + 2], r[4 * j + 3], __float_as_uint(bb.z), __float_as_uint(bb.w), c1, c0);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              *reinterpret_cast<uint4*>(act + tc_canon(row, c / 8 + u, kHid)) =
+                  make_uint4(pk[4 * u], pk[4 * u + 1], pk[4 * u + 2], pk[4 * u + 3]);
           }
-#pragma unroll
-          for (int u = 0; u < 4; ++u)
-            *reinterpret_cast<uint4*>(act + tc_canon(row, c / 8 + u, kHid)) =
-                make_uint4(pk[4 * u], pk[4 * u + 1], pk[4 * u + 2], pk[4 * u + 3]);
           fence_async_smem();
-        } else if (cb == 0) {
+        } else if (half == 0) {
           uint32_t r[16];
           tmem_ld_x16(t_row, r);
           tmem_wait_ld16(r);
