@@ -830,6 +830,7 @@ def main():
                                              step_kernel=form_k) as ens:
                 ens.set_state(E.h, E.q, E.z)
                 blk, n_tiles, grid, ens_kernel = ens.info()
+                plan = ens.plan(0)
                 torch.cuda.synchronize(dev)
                 if dist is not None:
                     dist.barrier()
@@ -852,8 +853,9 @@ def main():
                           "max_steps": int(max_over_ranks(float(steps_c.max()), dist, device=dev)),
                           "min_steps": int(min_over_ranks(float(steps_c.min()), dist, device=dev)),
                           "threads_per_block": blk,
-                          ("channels" if ens_kernel == 3 else "tiles"): n_tiles, "grid": grid,
-                          "all_at_t_end": all_at}
+                          ("channels" if ens_kernel == 3 else "tiles"): n_tiles, "grid": plan["grid"],
+                          "cluster_team": plan["cluster"], "channels_on_teams": plan["teamed"],
+                          "estimated_imbalance": plan["imbalance"], "all_at_t_end": all_at}
         ensemble = {"workload": f"{n_channels} movable-bed Riemann channels, N_c log-uniform [1e3,1e5], FP32",
                     "total_cells": total_cells, "t_end": args.ensemble_t_end,
                     "ranks": ws, "sharding": "channels split over the ranks by list scheduling of "

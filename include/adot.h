@@ -282,12 +282,14 @@ typedef struct {
   int32_t steps_per_graph;  /* per-step launches captured per CUDA graph; 0 = default (48) */
   int32_t device;           /* CUDA device ordinal; -1 = current */
   int32_t step_kernel;      /* 0 = chosen at each set_state (default): persistent channel loops
-                               when the estimated list schedule of the channels onto its CTAs
+                               (one CTA per channel, or the long channels on cluster teams)
+                               when the estimated list schedule of the channels onto the CTAs
                                is within 1/0.85 of balanced, else per-step launches (4);
-                               3 = persistent channel loops; per-step launches: 1 = block
-                               kernel, 2 = persistent warp tiles (31 cells per tile, shuffle
-                               exchange, no block barrier), 4 = the faster of 1 and 2 by
-                               trial launches */
+                               3 = persistent channel loops, the better estimated plan;
+                               5 = persistent with cluster teams (block_threads 0 or 768);
+                               per-step launches: 1 = block kernel, 2 = persistent warp tiles
+                               (31 cells per tile, shuffle exchange, no block barrier), 4 = the
+                               faster of 1 and 2 by trial launches */
 } adot_ensemble_config;
 
 typedef struct adot_ensemble adot_ensemble;
@@ -330,6 +332,19 @@ adot_status adot_ensemble_query(adot_ensemble* ens, double* t_out, int64_t* step
  * 3 persistent channel loops); NULL pointers are skipped. */
 adot_status adot_ensemble_info(adot_ensemble* ens, int32_t* block_out, int64_t* tiles_out,
                                int32_t* grid_out, int32_t* step_kernel_out);
+
+/* The plan that run_to (which = 0) or step (which = 1) follows, chosen at the
+ * last set_state (no counterpart in the paper). *form_out: 3 = persistent
+ * channel loops, 1 or 2 = per-step launches (block / warp tiles);
+ * *cluster_out: 1 = one CTA per channel, 2 or 4 = the long channels stepped by
+ * teams of that many CTAs (a thread-block cluster; one exchange of the CFL
+ * maximum through distributed shared memory per step), the others one CTA
+ * each; *teamed_out: channels run by teams; *imbalance_out: the persistent
+ * form's estimated list-scheduling makespan / mean CTA load. NULL pointers are
+ * skipped. ADOT_E_INVALID_ARG for another `which`. */
+adot_status adot_ensemble_plan(adot_ensemble* ens, int32_t which, int32_t* form_out, int32_t* block_out,
+                               int32_t* cluster_out, int32_t* grid_out, int32_t* teamed_out,
+                               double* imbalance_out);
 
 /* ---- Learned surrogate of the quadrature-averaged |A| ----------------------
  * |A|_Psi = sum_k w_k |A(Psi(s_k))|, the matrix that multiplies W+ - W- in the

@@ -120,6 +120,8 @@ def lib() -> ctypes.CDLL:
             "adot_ensemble_query": ([_P, _P, _P, ctypes.POINTER(i64)], i32),
             "adot_ensemble_info": ([_P, ctypes.POINTER(i32), ctypes.POINTER(i64),
                                     ctypes.POINTER(i32), ctypes.POINTER(i32)], i32),
+            "adot_ensemble_plan": ([_P, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                    ctypes.POINTER(i32), ctypes.POINTER(i32), _D], i32),
             "adot_measure_pipe": ([i32, i32, _D, _D], i32),
             "adot_status_string": ([i32], ctypes.c_char_p),
             "adot_version": ([], ctypes.c_char_p),
@@ -345,7 +347,8 @@ def adot_step_noalloc(cfg: Config, h, q, z, n_steps: int, t0: float = 0.0, strea
 class Ensemble:
     """Owning wrapper around an adot_ensemble (batched independent channels).
 
-    step_kernel: 0 or 3 persistent channel loops (default), 1 per-step block
+    step_kernel: 0 chosen per state (default), 3 persistent channel loops,
+    5 persistent with cluster teams for the long channels, 1 per-step block
     kernel, 2 per-step warp tiles, 4 per-step, the faster of 1 and 2."""
 
     def __init__(self, n_cells, length, Ag, xi, cfl=0.9, g=9.81, precision=FP32, block_threads=0,
@@ -405,12 +408,24 @@ class Ensemble:
         return t, s, cu.value
 
     def info(self):
-        """(threads per block, tiles, resident grid, step kernel: 1 block, 2 warp tiles)."""
+        """(threads per block, tiles, resident grid, step kernel: 1 block, 2 warp tiles,
+        3 persistent channel loops)."""
         b, g, k = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
         nt = ctypes.c_int64()
         _check(lib().adot_ensemble_info(self.ptr, ctypes.byref(b), ctypes.byref(nt), ctypes.byref(g),
                                         ctypes.byref(k)), "adot_ensemble_info")
         return b.value, nt.value, g.value, k.value
+
+    def plan(self, which: int = 0) -> dict:
+        """The plan of run_to (which = 0) or step (1): form (3 persistent, 1/2
+        per-step), threads per block, cluster (1 or the team size), grid,
+        channels run by teams, estimated imbalance."""
+        v = [ctypes.c_int32() for _ in range(5)]
+        imb = ctypes.c_double()
+        _check(lib().adot_ensemble_plan(self.ptr, which, *(ctypes.byref(x) for x in v), ctypes.byref(imb)),
+               "adot_ensemble_plan")
+        return dict(zip(("form", "block", "cluster", "grid", "teamed"), (x.value for x in v)),
+                    imbalance=imb.value)
 
     def close(self):
         if getattr(self, "ptr", 0):

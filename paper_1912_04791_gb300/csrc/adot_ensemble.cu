@@ -221,7 +221,15 @@ __global__ void __launch_bounds__(B, 65536 / (B * 64))
 // and e0 + l, copies at the ends) and lanes 1..31 update cells e0 .. e0 + 30
 // with D+ of the left edge by shuffle. mode 0 steps with nu = dt/dx and folds
 // the new cells' CFL maxima into rho; mode 1 copies the cells across.
-template <typename R, int CAP>
+// State load: plain (L1-cached) or, when other SMs write the cells between
+// steps of one launch (a cluster team), at L2 only.
+template <bool CG, typename T>
+__device__ __forceinline__ T ens_ld(const T* p) {
+  if constexpr (CG) return __ldcg(p);
+  else return *p;
+}
+
+template <typename R, int CAP, bool CG = false>
 __device__ __forceinline__ void ens_subtile(const StepParams& lp, const typename Prec<R>::State& in,
                                             const typename Prec<R>::State& out, const int64_t base,
                                             const int64_t nc, const int64_t e0, const int lane,
@@ -236,12 +244,12 @@ __device__ __forceinline__ void ens_subtile(const StepParams& lp, const typename
     S wl[3], wr[3];
     const int64_t il = (e > 0) ? (e <= nc ? e - 1 : nc - 1) : 0;
     const int64_t ir = (e < nc) ? e : nc - 1;
-    wl[0] = in.h[base + il];
-    wl[1] = in.q[base + il];
-    wl[2] = in.z[base + il];
-    wr[0] = in.h[base + ir];
-    wr[1] = in.q[base + ir];
-    wr[2] = in.z[base + ir];
+    wl[0] = ens_ld<CG>(in.h + base + il);
+    wl[1] = ens_ld<CG>(in.q + base + il);
+    wl[2] = ens_ld<CG>(in.z + base + il);
+    wr[0] = ens_ld<CG>(in.h + base + ir);
+    wr[1] = ens_ld<CG>(in.q + base + ir);
+    wr[2] = ens_ld<CG>(in.z + base + ir);
     const int64_t i = e - 1;  // cell updated by this lane (lanes 1..31)
     if (mode == 1) {
       if (lane >= 1 && i < nc) {
@@ -372,6 +380,98 @@ __device__ __forceinline__ R block_max(R v, R* red) {
   return m;
 }
 
+// One CTA steps channel c of the persistent form to t_end (at most max_steps
+// steps), copies its state into the other buffer and leaves its control at
+// slot `slot` (see k_ens_run). Returns whether a non-finite value or
+// non-positive depth was met (the CTA then takes no further channel); the
+// status bits stay in flags.
+template <typename R, int B, int CAP>
+__device__ __forceinline__ bool ens_run_channel(const EnsParams& p, const typename Prec<R>::State& b0,
+                                                const typename Prec<R>::State& b1, const int c,
+                                                const double t_end, const long long max_steps,
+                                                const int slot, R* sRed, unsigned& flags) {
+  constexpr int NW = B / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int C = p.C;
+  const int64_t base = p.off[c];
+  const int64_t nc = p.off[c + 1] - base;
+  StepParams lp;
+  lp.lf = LawT<float>{p.g_f, p.K3f[c], 0.0f, 0.0f};
+  lp.ld = LawT<double>{p.g_d, p.K3d[c], 0.0, 0.0};
+  // CFL maximum of the channel's current state (as k_ens_rho)
+  R rho = R(0);
+  for (int64_t i = threadIdx.x; i < nc; i += B) {
+    const auto h = b0.h[base + i], q = b0.q[base + i], z = b0.z[base + i];
+    const R hh = Prec<R>::hi(h);
+    if (!(Prec<R>::finite(h) && Prec<R>::finite(q) && Prec<R>::finite(z))) {
+      flags |= ST_NONFINITE;
+      continue;
+    }
+    if (!(hh > R(0))) {
+      flags |= ST_DEPTH;
+      continue;
+    }
+    const R v = Prec<R>::template rho<LAW_GRASS>(lp, hh, Prec<R>::hi(q));
+    if (!(v <= R(3.0e38))) {
+      flags |= ST_NONFINITE;
+      continue;
+    }
+    rho = d_max(rho, v);
+  }
+  rho = block_max<R, NW>(rho, sRed);
+  double t = p.d.t_cur[c];
+  long long st = p.d.steps_cur[c];
+  double dt_last = p.d.dt_cur[c];
+  const double dx = p.dx[c];
+  int cur = 0;
+  bool stop = __syncthreads_or(flags != 0 || (threadIdx.x == 0 && *(volatile unsigned*)p.d.status != 0));
+  for (long long ns = 0; !stop && t < t_end && ns < max_steps; ++ns) {
+    double dt = p.cfl * dx / (double)rho;
+    double tn = t + dt;
+    if (tn >= t_end) {
+      dt = t_end - t;
+      tn = t_end;
+    }
+    const R nu = R(dt / dx);
+    const typename Prec<R>::State& in = cur ? b1 : b0;
+    const typename Prec<R>::State& out = cur ? b0 : b1;
+    R rr = R(0);
+    for (int64_t e0 = (int64_t)warp * 31; e0 < nc; e0 += NW * 31)
+      ens_subtile<R, CAP>(lp, in, out, base, nc, e0, lane, nu, 0, rr, flags);
+    rho = block_max<R, NW>(rr, sRed);
+    t = tn;
+    ++st;
+    dt_last = dt;
+    cur ^= 1;
+    stop = __syncthreads_or(flags != 0 || (threadIdx.x == 0 && *(volatile unsigned*)p.d.status != 0));
+  }
+  // both buffers hold the channel's state
+  {
+    const typename Prec<R>::State& src = cur ? b1 : b0;
+    const typename Prec<R>::State& dst = cur ? b0 : b1;
+    for (int64_t i = threadIdx.x; i < nc; i += B) {
+      dst.h[base + i] = src.h[base + i];
+      dst.q[base + i] = src.q[base + i];
+      dst.z[base + i] = src.z[base + i];
+    }
+  }
+  if (threadIdx.x == 0) {
+    const int s0 = slot, s1 = (slot + 1) % 3;
+    p.d.t[s0 * C + c] = t;
+    p.d.dt[s0 * C + c] = dt_last;
+    p.d.steps[s0 * C + c] = st;
+    p.d.rho[s0 * C + c] = rho > R(0) ? Prec<R>::bits(rho) : 0ull;
+    p.d.rho[s1 * C + c] = 0ull;
+    p.d.t_cur[c] = t;
+    p.d.steps_cur[c] = st;
+    p.d.dt_cur[c] = dt_last;
+    const bool done = !(t < t_end);
+    p.d.fin[c] = done ? p.d.gstep[s0] - 1 : 0x7fffffffffffffffLL;
+    if (!done) atomicMax(&p.d.active[s0], p.chan_tile_end[c]);
+  }
+  return stop;
+}
+
 template <typename R, int B, int CAP>
 __global__ void __launch_bounds__(B, 65536 / (B * CAP))
     k_ens_run(const EnsParams p, const typename Prec<R>::State b0, const typename Prec<R>::State b1,
@@ -379,8 +479,6 @@ __global__ void __launch_bounds__(B, 65536 / (B * CAP))
   constexpr int NW = B / 32;
   __shared__ R sRed[NW];
   __shared__ int sJ;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int C = p.C;
   unsigned flags = 0;
   bool stop = false;
   while (!stop) {
@@ -388,17 +486,170 @@ __global__ void __launch_bounds__(B, 65536 / (B * CAP))
     if (threadIdx.x == 0) sJ = atomicAdd(r.next, 1);
     __syncthreads();
     const int j = sJ;
-    if (j >= C) break;
-    const int c = r.order[j];
+    if (j >= p.C) break;
+    stop = ens_run_channel<R, B, CAP>(p, b0, b1, r.order[j], r.t_end, r.max_steps, r.slot, sRed, flags);
+    if (flags) {
+      atomicOr(p.d.status, flags);
+      flags = 0;
+    }
+  }
+}
+
+// ---- cluster teams: a long channel stepped by the CTAs of one cluster -------
+// Thread block clusters of CL CTAs (one CTA of 768 threads per SM). For each of
+// its assigned long channels a cluster steps the channel as one team: the CL x
+// 24 warps take the channel's 31-cell sub-tiles in turn, and each step ends
+// with a team exchange of the CFL maximum and an error bit. Each CTA writes its
+// value into its own shared memory (double-buffered by step parity), arrives
+// on every team member's mbarrier through distributed shared memory (release
+// at cluster scope, after a block barrier and a device fence that order the
+// step's cell writes), waits on its own (acquire; at most ~2^31 cycles, then
+// the team aborts with ST_TIMEOUT) and reads the members' values remotely.
+// A member can run at most one exchange ahead of another (it needs every
+// member's arrival to finish an exchange), so the two value buffers and the
+// barrier's phase parity suffice. Team members read cells that other SMs wrote
+// in the previous step, so their state loads bypass L1 (ld.global.cg). Every
+// decision that shapes the control flow (the channel list, t, dt, the step
+// count, the stop bit) is the same in all members, so all of them make the
+// same exchanges. After the long channels each CTA takes the short ones from
+// the dynamic queue alone (ens_run_channel), and a final cluster barrier keeps
+// every CTA's shared memory alive until no member can read it.
+
+__device__ __forceinline__ uint32_t cl_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cl_id() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t sh_addr(const void* ptr) {
+  return (uint32_t)__cvta_generic_to_shared(ptr);
+}
+// address of the same shared-memory variable in cluster CTA `rank`
+__device__ __forceinline__ uint32_t cl_map(uint32_t a, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+// all threads of every CTA of the cluster
+__device__ __forceinline__ void cl_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+struct EnsTeamRun {
+  const int* big_ptr;   // [clusters + 1]: cluster k runs big_list[big_ptr[k] .. big_ptr[k+1])
+  const int* big_list;  // the long channels, cluster by cluster
+  const int* order;     // [n_small] the other channels, largest estimated work first
+  int n_small;
+  int* next;            // queue head of those
+  double t_end;
+  long long max_steps;
+  int slot;
+};
+
+struct TeamSmem {
+  uint64_t bar;                    // CL arrivals per exchange
+  unsigned long long val[2][2];    // [parity][rho bits, stop bit] of this CTA
+  unsigned long long out_rho;      // the exchange's results, for the whole CTA
+  int out_stop;                    // 0 go on, 1 stop (an error bit), 2 timed out
+};
+
+// Thread 0: publishes (rho_bits, stop) for exchange k, arrives at every member,
+// waits for all of them and combines; false if the wait ran out.
+template <int CL>
+__device__ __forceinline__ bool team_exchange(TeamSmem& ts, int k, unsigned long long rho_bits,
+                                              unsigned long long stop, unsigned long long& rmax,
+                                              unsigned long long& sany) {
+  const int par = k & 1;
+  ts.val[par][0] = rho_bits;
+  ts.val[par][1] = stop;
+  __threadfence();
+  const uint32_t bar = sh_addr(&ts.bar);
+#pragma unroll
+  for (int q = 0; q < CL; ++q)
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cl_map(bar, (uint32_t)q))
+                 : "memory");
+  const long long t0 = clock64();
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"((uint32_t)par)
+        : "memory");
+    if (done) break;
+    if (clock64() - t0 > (1ll << 31)) return false;
+  }
+  __threadfence();
+  rmax = 0ull;
+  sany = 0ull;
+  const uint32_t va = sh_addr(&ts.val[par][0]);
+#pragma unroll
+  for (int q = 0; q < CL; ++q) {
+    const uint32_t ra = cl_map(va, (uint32_t)q);
+    unsigned long long a, b;
+    asm volatile("ld.shared::cluster.u64 %0, [%1];" : "=l"(a) : "r"(ra) : "memory");
+    asm volatile("ld.shared::cluster.u64 %0, [%1];" : "=l"(b) : "r"(ra + 8u) : "memory");
+    rmax = a > rmax ? a : rmax;
+    sany |= b;
+  }
+  return true;
+}
+
+template <typename R, int B, int CAP, int CL>
+__global__ void __launch_bounds__(B, 65536 / (B * CAP))
+    k_ens_run_team(const EnsParams p, const typename Prec<R>::State b0, const typename Prec<R>::State b1,
+                   const EnsTeamRun r) {
+  constexpr int NW = B / 32;
+  __shared__ R sRed[NW];
+  __shared__ int sJ;
+  __shared__ __align__(16) TeamSmem ts;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t rank = cl_rank();
+  const int C = p.C;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sh_addr(&ts.bar)), "r"(CL) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  cl_sync();  // every member's barrier is initialised before anyone arrives
+  unsigned flags = 0;
+  bool quit = false;
+  int xk = 0;  // exchanges so far
+  // team exchange of this CTA's (rho, error) by all threads; results in ts
+  auto exchange = [&](R rho_cta, bool err) {
+    if (threadIdx.x == 0) {
+      unsigned long long rm = 0ull, sa = 0ull;
+      const bool st_err = err || *(volatile unsigned*)p.d.status != 0;
+      if (!team_exchange<CL>(ts, xk, rho_cta > R(0) ? Prec<R>::bits(rho_cta) : 0ull, st_err ? 1ull : 0ull, rm,
+                             sa)) {
+        atomicOr(p.d.status, ST_TIMEOUT);
+        ts.out_stop = 2;
+      } else {
+        ts.out_rho = rm;
+        ts.out_stop = sa ? 1 : 0;
+      }
+    }
+    ++xk;
+    __syncthreads();
+  };
+
+  const uint32_t cid = cl_id();
+  for (int k = r.big_ptr[cid]; !quit && k < r.big_ptr[cid + 1]; ++k) {
+    const int c = r.big_list[k];
     const int64_t base = p.off[c];
     const int64_t nc = p.off[c + 1] - base;
     StepParams lp;
     lp.lf = LawT<float>{p.g_f, p.K3f[c], 0.0f, 0.0f};
     lp.ld = LawT<double>{p.g_d, p.K3d[c], 0.0, 0.0};
-    // CFL maximum of the channel's current state (as k_ens_rho)
+    // CFL maximum of the current state over this member's cells
     R rho = R(0);
-    for (int64_t i = threadIdx.x; i < nc; i += B) {
-      const auto h = b0.h[base + i], q = b0.q[base + i], z = b0.z[base + i];
+    for (int64_t i = (int64_t)rank * B + threadIdx.x; i < nc; i += (int64_t)CL * B) {
+      const auto h = ens_ld<true>(b0.h + base + i), q = ens_ld<true>(b0.q + base + i),
+                 z = ens_ld<true>(b0.z + base + i);
       const R hh = Prec<R>::hi(h);
       if (!(Prec<R>::finite(h) && Prec<R>::finite(q) && Prec<R>::finite(z))) {
         flags |= ST_NONFINITE;
@@ -416,13 +667,15 @@ __global__ void __launch_bounds__(B, 65536 / (B * CAP))
       rho = d_max(rho, v);
     }
     rho = block_max<R, NW>(rho, sRed);
+    exchange(rho, __syncthreads_or(flags != 0));
+    int stop = ts.out_stop;
+    rho = (R)Prec<R>::from_bits(ts.out_rho);
     double t = p.d.t_cur[c];
     long long st = p.d.steps_cur[c];
     double dt_last = p.d.dt_cur[c];
     const double dx = p.dx[c];
     int cur = 0;
-    stop = __syncthreads_or(flags != 0);
-    for (long long ns = 0; !stop && t < r.t_end && ns < r.max_steps; ++ns) {
+    for (long long ns = 0; stop == 0 && t < r.t_end && ns < r.max_steps; ++ns) {
       double dt = p.cfl * dx / (double)rho;
       double tn = t + dt;
       if (tn >= r.t_end) {
@@ -433,26 +686,32 @@ __global__ void __launch_bounds__(B, 65536 / (B * CAP))
       const typename Prec<R>::State& in = cur ? b1 : b0;
       const typename Prec<R>::State& out = cur ? b0 : b1;
       R rr = R(0);
-      for (int64_t e0 = (int64_t)warp * 31; e0 < nc; e0 += NW * 31)
-        ens_subtile<R, CAP>(lp, in, out, base, nc, e0, lane, nu, 0, rr, flags);
-      rho = block_max<R, NW>(rr, sRed);
+      for (int64_t e0 = ((int64_t)rank * NW + warp) * 31; e0 < nc; e0 += (int64_t)CL * NW * 31)
+        ens_subtile<R, CAP, true>(lp, in, out, base, nc, e0, lane, nu, 0, rr, flags);
+      rr = block_max<R, NW>(rr, sRed);
+      exchange(rr, __syncthreads_or(flags != 0));
+      stop = ts.out_stop;
+      rho = (R)Prec<R>::from_bits(ts.out_rho);
       t = tn;
       ++st;
       dt_last = dt;
       cur ^= 1;
-      stop = __syncthreads_or(flags != 0 || (threadIdx.x == 0 && *(volatile unsigned*)p.d.status != 0));
     }
-    // both buffers hold the channel's state
+    if (stop == 2) {
+      quit = true;
+      break;
+    }
+    // both buffers hold the channel's state (each member copies its own cells)
     {
       const typename Prec<R>::State& src = cur ? b1 : b0;
       const typename Prec<R>::State& dst = cur ? b0 : b1;
-      for (int64_t i = threadIdx.x; i < nc; i += B) {
-        dst.h[base + i] = src.h[base + i];
-        dst.q[base + i] = src.q[base + i];
-        dst.z[base + i] = src.z[base + i];
+      for (int64_t i = (int64_t)rank * B + threadIdx.x; i < nc; i += (int64_t)CL * B) {
+        dst.h[base + i] = ens_ld<true>(src.h + base + i);
+        dst.q[base + i] = ens_ld<true>(src.q + base + i);
+        dst.z[base + i] = ens_ld<true>(src.z + base + i);
       }
     }
-    if (threadIdx.x == 0) {
+    if (rank == 0 && threadIdx.x == 0) {
       const int s0 = r.slot, s1 = (r.slot + 1) % 3;
       p.d.t[s0 * C + c] = t;
       p.d.dt[s0 * C + c] = dt_last;
@@ -466,11 +725,19 @@ __global__ void __launch_bounds__(B, 65536 / (B * CAP))
       p.d.fin[c] = done ? p.d.gstep[s0] - 1 : 0x7fffffffffffffffLL;
       if (!done) atomicMax(&p.d.active[s0], p.chan_tile_end[c]);
     }
-    if (flags) {
-      atomicOr(p.d.status, flags);
-      flags = 0;
-    }
+    if (stop) quit = true;
   }
+  // the short channels, one CTA each
+  while (!quit) {
+    __syncthreads();
+    if (threadIdx.x == 0) sJ = atomicAdd(r.next, 1);
+    __syncthreads();
+    const int j = sJ;
+    if (j >= r.n_small) break;
+    quit = ens_run_channel<R, B, CAP>(p, b0, b1, r.order[j], r.t_end, r.max_steps, r.slot, sRed, flags);
+  }
+  if (flags) atomicOr(p.d.status, flags);
+  cl_sync();  // no member reads this CTA's shared memory after it exits
 }
 
 
@@ -566,11 +833,16 @@ struct adot_ensemble {
   // how run_to (plan[0]) and step (plan[1]) advance the channels
   struct Plan {
     bool persistent;
-    int block;       // threads per CTA of k_ens_run
-    int grid;        // resident CTAs (at most one per channel)
+    int block;       // threads per CTA of k_ens_run / k_ens_run_team
+    int grid;        // resident CTAs (at most one per channel without teams)
     double imbalance;  // estimated list-scheduling makespan / mean CTA load
-    int* d_order;    // [C] channel queue, largest estimated work first
+    int* d_order;    // [C] channel queue (the short channels with teams), largest estimated work first
+    int cluster;     // 1: one CTA per channel; 2 or 4: long channels stepped by cluster teams
+    int n_big;       // channels run by teams
+    int n_small;     // channels in the queue
+    int* d_team;     // [clusters + 1 + C]: big_ptr, then big_list
   } plan[2];
+  int team_clusters[2];  // resident clusters of k_ens_run_team with 2 and 4 CTAs (0: not launchable)
   int block_cfg;        // configured block_threads (0 = any)
   bool tuned;
   int steps_per_graph;
@@ -719,6 +991,36 @@ cudaError_t ens_run_dispatch(adot_ensemble* e, const EnsRun& r, int block, int g
 cudaError_t ens_run_call(adot_ensemble* e, const EnsRun& r, int block, int grid, int* per_sm = nullptr) {
   if (e->prec == ADOT_FP32) return ens_run_dispatch<float>(e, r, block, grid, per_sm);
   return ens_run_dispatch<double>(e, r, block, grid, per_sm);
+}
+
+// Launch of the cluster-team form (768 threads, 80 registers, CL CTAs per
+// cluster) on `clusters` clusters, or (clusters = 0) the resident clusters into *n.
+template <typename R, int CL>
+cudaError_t ens_team_launch_t(adot_ensemble* e, const EnsTeamRun& r, int clusters, int* n) {
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CL;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(768, 1, 1);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = e->stream;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (clusters == 0) {
+    cfg.gridDim = dim3((unsigned)((e->n_sms / CL) * CL), 1, 1);
+    return cudaOccupancyMaxActiveClusters(n, (void*)k_ens_run_team<R, 768, 80, CL>, &cfg);
+  }
+  cfg.gridDim = dim3((unsigned)(clusters * CL), 1, 1);
+  return cudaLaunchKernelEx(&cfg, k_ens_run_team<R, 768, 80, CL>, ens_params(e), ens_state<R>(e, e->cur),
+                            ens_state<R>(e, 1 - e->cur), r);
+}
+
+cudaError_t ens_team_call(adot_ensemble* e, const EnsTeamRun& r, int cl, int clusters, int* n = nullptr) {
+  if (e->prec == ADOT_FP32)
+    return cl == 2 ? ens_team_launch_t<float, 2>(e, r, clusters, n) : ens_team_launch_t<float, 4>(e, r, clusters, n);
+  return cl == 2 ? ens_team_launch_t<double, 2>(e, r, clusters, n) : ens_team_launch_t<double, 4>(e, r, clusters, n);
 }
 
 // Resident grid of a persistent shape (at most one CTA per channel).
@@ -916,13 +1218,65 @@ double lpt_imbalance(const std::vector<double>& w_sorted, int g) {
   return total > 0.0 ? mk / (total / g) : 1.0;
 }
 
+// A team plan: channels with work >= thr (the long ones, in decreasing order)
+// go to the cluster with the least team work, counted as work / (CL x
+// kTeamEff); the others to the CTA with the least load, every CTA starting at
+// its cluster's team work. Returns the makespan / (total work / CTAs); fills
+// the per-cluster lists and the short-channel order when asked.
+constexpr double kTeamEff = 0.95;  // a team of CL CTAs steps a channel ~CL x this faster than one CTA
+
+double team_plan(const std::vector<double>& ws, const std::vector<int>& ord, int n_cl, int cl, double thr,
+                 std::vector<int>* ptr, std::vector<int>* list, std::vector<int>* small, int* n_big) {
+  const int C = (int)ws.size();
+  if (n_cl < 1) return INFINITY;
+  std::vector<double> cload((size_t)n_cl, 0.0);
+  std::vector<std::vector<int>> lists((size_t)n_cl);
+  double total = 0.0;
+  int nb = 0;
+  for (int i = 0; i < C; ++i) total += ws[i];
+  for (; nb < C && ws[nb] >= thr; ++nb) {
+    int best = 0;
+    for (int k = 1; k < n_cl; ++k)
+      if (cload[k] < cload[best]) best = k;
+    cload[best] += ws[nb] / (cl * kTeamEff);
+    lists[best].push_back(ord[nb]);
+  }
+  if (nb == 0) return INFINITY;
+  const int n_cta = n_cl * cl;
+  std::vector<double> load((size_t)n_cta);
+  for (int k = 0; k < n_cta; ++k) load[k] = cload[k / cl];
+  auto cmp = [](double a, double b) { return a > b; };
+  std::make_heap(load.begin(), load.end(), cmp);
+  for (int i = nb; i < C; ++i) {
+    std::pop_heap(load.begin(), load.end(), cmp);
+    load.back() += ws[i];
+    std::push_heap(load.begin(), load.end(), cmp);
+  }
+  const double mk = *std::max_element(load.begin(), load.end());
+  if (ptr) {
+    ptr->assign(1, 0);
+    list->clear();
+    for (int k = 0; k < n_cl; ++k) {
+      list->insert(list->end(), lists[k].begin(), lists[k].end());
+      ptr->push_back((int)list->size());
+    }
+    small->assign(ord.begin() + nb, ord.end());
+    *n_big = nb;
+  }
+  return total > 0.0 ? mk / (total / n_cta) : 1.0;
+}
+
 // Plans of run_to (k = 0) and step (k = 1). A channel's work is N_c times its
 // steps: for run_to N_c rho_c / dx_c (steps per unit time, from the first CFL
 // maxima in slot 0), for step N_c. Each CTA of the persistent form steps one
 // channel at a time, so its time is that of the list schedule of the channels,
 // largest first, onto the resident CTAs; the shape with the smaller estimated
-// imbalance is taken (or the configured one), and with step_kernel = 0 the
-// per-step form instead when that imbalance exceeds 1 / kPerStepRel.
+// imbalance is taken (or the configured one). Team plans put the channels
+// above a work threshold (1/2, 1 or 2 mean CTA loads) on clusters of 2 or 4
+// CTAs and are taken when they beat the one-CTA shapes by 3 %. With
+// step_kernel = 0 the per-step form runs instead when the best imbalance
+// exceeds 1 / kPerStepRel; step_kernel 3 takes the best persistent plan, 5 the
+// best team plan.
 adot_status ens_plan(adot_ensemble* e) {
   const int C = e->C;
   std::vector<unsigned long long> bits(C);
@@ -952,9 +1306,14 @@ adot_status ens_plan(adot_ensemble* e) {
     for (int c = 0; c < C; ++c) ord[c] = c;
     std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return w[a] > w[b]; });
     std::vector<double> ws(C);
-    for (int i = 0; i < C; ++i) ws[i] = w[ord[i]];
+    double total = 0.0;
+    for (int i = 0; i < C; ++i) {
+      ws[i] = w[ord[i]];
+      total += ws[i];
+    }
     adot_ensemble::Plan& pl = e->plan[k];
     pl.imbalance = INFINITY;
+    pl.cluster = 1;
     for (int i = 0; i < kNumRunBlocks; ++i) {
       const int blk = kRunBlocks[i];
       if (e->run_block_cfg && blk != e->run_block_cfg) continue;
@@ -971,8 +1330,48 @@ adot_status ens_plan(adot_ensemble* e) {
       pl.grid = ens_run_grid(e, pl.block);
       pl.imbalance = lpt_imbalance(ws, pl.grid);
     }
-    pl.persistent = e->step_kernel_cfg == 3 || pl.imbalance * kPerStepRel <= 1.0;
-    CKE(cudaMemcpyAsync(pl.d_order, ord.data(), sizeof(int) * C, cudaMemcpyHostToDevice, e->stream));
+    // team plans (768-thread CTAs)
+    double best_team = INFINITY;
+    int team_cl = 0;
+    double team_thr = 0.0;
+    if (e->run_block_cfg == 0 || e->run_block_cfg == 768) {
+      for (int ci = 0; ci < 2; ++ci) {
+        const int cl = ci == 0 ? 2 : 4;
+        const int n_cl = e->team_clusters[ci];
+        if (n_cl < 1) continue;
+        for (double f : {0.5, 1.0, 2.0}) {
+          const double thr = f * total / (n_cl * cl);
+          const double imb = team_plan(ws, ord, n_cl, cl, thr, nullptr, nullptr, nullptr, nullptr);
+          if (imb < best_team) {
+            best_team = imb;
+            team_cl = cl;
+            team_thr = thr;
+          }
+        }
+      }
+    }
+    const bool want_team = team_cl > 0 && (e->step_kernel_cfg == 5 || best_team < 0.97 * pl.imbalance);
+    std::vector<int> small = ord;
+    pl.n_big = 0;
+    if (want_team) {
+      std::vector<int> ptr, list;
+      const int n_cl = e->team_clusters[team_cl == 2 ? 0 : 1];
+      team_plan(ws, ord, n_cl, team_cl, team_thr, &ptr, &list, &small, &pl.n_big);
+      pl.cluster = team_cl;
+      pl.block = 768;
+      pl.grid = n_cl * team_cl;
+      pl.imbalance = best_team;
+      std::vector<int> tbuf(ptr);
+      tbuf.insert(tbuf.end(), list.begin(), list.end());
+      CKE(cudaMemcpyAsync(pl.d_team, tbuf.data(), sizeof(int) * tbuf.size(), cudaMemcpyHostToDevice,
+                          e->stream));
+      CKE(cudaStreamSynchronize(e->stream));
+    }
+    pl.n_small = (int)small.size();
+    pl.persistent = e->step_kernel_cfg == 3 || e->step_kernel_cfg == 5 || pl.imbalance * kPerStepRel <= 1.0;
+    if (!small.empty())
+      CKE(cudaMemcpyAsync(pl.d_order, small.data(), sizeof(int) * small.size(), cudaMemcpyHostToDevice,
+                          e->stream));
   }
   CKE(cudaStreamSynchronize(e->stream));
   return ADOT_OK;
@@ -992,13 +1391,27 @@ adot_status ens_run(adot_ensemble* e, const adot_ensemble::Plan& pl, double t_en
     const long long m = (n_steps >= 0) ? std::min(left, kRunChunk) : kRunChunk;
     CKE(cudaMemsetAsync(e->dev.next, 0, sizeof(int), e->stream));
     CKE(cudaMemsetAsync(e->dev.active, 0, sizeof(int) * 3, e->stream));
-    EnsRun r;
-    r.order = pl.d_order;
-    r.next = e->dev.next;
-    r.t_end = t_end;
-    r.max_steps = m;
-    r.slot = e->phase % 3;
-    CKE(ens_run_call(e, r, pl.block, pl.grid));
+    const int slot = e->phase % 3;
+    if (pl.cluster > 1) {
+      EnsTeamRun r;
+      r.big_ptr = pl.d_team;
+      r.big_list = pl.d_team + pl.grid / pl.cluster + 1;
+      r.order = pl.d_order;
+      r.n_small = pl.n_small;
+      r.next = e->dev.next;
+      r.t_end = t_end;
+      r.max_steps = m;
+      r.slot = slot;
+      CKE(ens_team_call(e, r, pl.cluster, pl.grid / pl.cluster));
+    } else {
+      EnsRun r;
+      r.order = pl.d_order;
+      r.next = e->dev.next;
+      r.t_end = t_end;
+      r.max_steps = m;
+      r.slot = slot;
+      CKE(ens_run_call(e, r, pl.block, pl.grid));
+    }
     ++launches;
     left -= m;
     HostCtl hc;
@@ -1006,7 +1419,7 @@ adot_status ens_run(adot_ensemble* e, const adot_ensemble::Plan& pl, double t_en
     if (st) return st;
     st = ens_status(hc.status);
     if (st) return st;
-    if (hc.active[r.slot] == 0) break;  // every channel at t_end
+    if (hc.active[slot] == 0) break;  // every channel at t_end
   }
   if (launches_out) *launches_out = launches;
   return ADOT_OK;
@@ -1025,8 +1438,10 @@ void ens_free(adot_ensemble* e) {
   if (e->d_tile_chan) cudaFree(e->d_tile_chan);
   if (e->d_tile_e0) cudaFree(e->d_tile_e0);
   if (e->d_chan_tile_end) cudaFree(e->d_chan_tile_end);
-  for (int k = 0; k < 2; ++k)
+  for (int k = 0; k < 2; ++k) {
     if (e->plan[k].d_order) cudaFree(e->plan[k].d_order);
+    if (e->plan[k].d_team) cudaFree(e->plan[k].d_team);
+  }
   if (e->d_ctl_mem) cudaFree(e->d_ctl_mem);
   if (e->d_io) cudaFree(e->d_io);
   if (e->cap_stream) cudaStreamDestroy(e->cap_stream);
@@ -1045,8 +1460,9 @@ adot_status adot_ensemble_create(const adot_ensemble_config* cfg, void* cuda_str
   if (!cfg || cfg->n_channels < 1 || !cfg->n_cells || !cfg->length || !cfg->Ag) return ADOT_E_INVALID_ARG;
   if (!(cfg->g > 0.0) || !(cfg->xi > 0.0) || !(cfg->cfl > 0.0 && cfg->cfl <= 1.0)) return ADOT_E_INVALID_ARG;
   if (cfg->precision != ADOT_FP64 && cfg->precision != ADOT_FP32) return ADOT_E_INVALID_ARG;
-  if (cfg->step_kernel < 0 || cfg->step_kernel > 4) return ADOT_E_INVALID_ARG;
-  if (cfg->step_kernel == 0 || cfg->step_kernel == 3) {
+  if (cfg->step_kernel < 0 || cfg->step_kernel > 5) return ADOT_E_INVALID_ARG;
+  if (cfg->step_kernel == 5 && cfg->block_threads != 0 && cfg->block_threads != 768) return ADOT_E_INVALID_ARG;
+  if (cfg->step_kernel == 0 || cfg->step_kernel == 3 || cfg->step_kernel == 5) {
     if (cfg->block_threads != 0 && cfg->block_threads != 256 && cfg->block_threads != 384 &&
         cfg->block_threads != 512 && cfg->block_threads != 768)
       return ADOT_E_INVALID_ARG;
@@ -1085,7 +1501,7 @@ adot_status adot_ensemble_create(const adot_ensemble_config* cfg, void* cuda_str
   int spg = cfg->steps_per_graph ? cfg->steps_per_graph : 48;
   e->steps_per_graph = ((spg + 5) / 6) * 6;
   e->step_kernel_cfg = cfg->step_kernel;
-  const bool may_persist = cfg->step_kernel == 0 || cfg->step_kernel == 3;
+  const bool may_persist = cfg->step_kernel == 0 || cfg->step_kernel == 3 || cfg->step_kernel == 5;
   e->block_cfg = may_persist ? 0 : cfg->block_threads;
   e->run_block_cfg = may_persist ? cfg->block_threads : 0;
   e->t_end_dev = INFINITY;
@@ -1141,18 +1557,29 @@ adot_status adot_ensemble_create(const adot_ensemble_config* cfg, void* cuda_str
     e->dev.status = (unsigned*)take(sizeof(unsigned));
     e->dev.next = (int*)take(sizeof(int));
   }
+  e->n_sms = 152;
+  cudaDeviceGetAttribute(&e->n_sms, cudaDevAttrMultiProcessorCount, e->device);
   for (int k = 0; k < 2 && err == cudaSuccess; ++k) {
     err = cudaMalloc((void**)&e->plan[k].d_order, sizeof(int) * C);
+    if (err == cudaSuccess)
+      err = cudaMalloc((void**)&e->plan[k].d_team, sizeof(int) * ((size_t)e->n_sms + 1 + C));
     if (err == cudaSuccess)
       err = cudaMemcpy(e->plan[k].d_order, e->order.data(), sizeof(int) * C, cudaMemcpyHostToDevice);
     // until the first set_state: the configured form, persistent at the default shape
     e->plan[k].persistent = may_persist;
-    e->plan[k].block = e->run_block_cfg ? e->run_block_cfg : kRunBlockDefault;
+    e->plan[k].block = (e->run_block_cfg && e->run_block_cfg != 768) ? e->run_block_cfg : kRunBlockDefault;
     e->plan[k].grid = ens_run_grid(e, e->plan[k].block);
     e->plan[k].imbalance = 1.0;
+    e->plan[k].cluster = 1;
+    e->plan[k].n_big = 0;
+    e->plan[k].n_small = C;
   }
-  e->n_sms = 152;
-  cudaDeviceGetAttribute(&e->n_sms, cudaDevAttrMultiProcessorCount, e->device);
+  for (int ci = 0; ci < 2; ++ci) {
+    int n = 0;
+    if (ens_team_call(e, EnsTeamRun{}, ci == 0 ? 2 : 4, 0, &n) != cudaSuccess || n < 0) n = 0;
+    e->team_clusters[ci] = std::min(n, e->n_sms / (ci == 0 ? 2 : 4));
+  }
+  cudaGetLastError();  // an unsupported cluster query leaves no error behind
   for (int i = 0; i < kNumRunBlocks; ++i) {
     int per_sm = 0;
     if (ens_run_call(e, EnsRun{}, kRunBlocks[i], 0, &per_sm) != cudaSuccess || per_sm < 1) per_sm = 1;
@@ -1170,7 +1597,7 @@ adot_status adot_ensemble_create(const adot_ensemble_config* cfg, void* cuda_str
       v0 = kEnsVariants[i];
       ++n_cand;
     }
-  e->tuned = n_cand == 1 || cfg->step_kernel == 3;
+  e->tuned = n_cand == 1 || cfg->step_kernel == 3 || cfg->step_kernel == 5;
   if (err != cudaSuccess || build_tiles(e, v0) != ADOT_OK ||
       ens_reset_ctl(e) != ADOT_OK || ens_build_graph(e) != ADOT_OK) {
     ens_free(e);
@@ -1222,7 +1649,7 @@ adot_status adot_ensemble_set_state(adot_ensemble* e, const double* h, const dou
   st = ens_status(hc.status);
   if (st) return st;
   e->state_set = true;
-  if (e->step_kernel_cfg == 0 || e->step_kernel_cfg == 3) {
+  if (e->step_kernel_cfg == 0 || e->step_kernel_cfg == 3 || e->step_kernel_cfg == 5) {
     st = ens_plan(e);
     if (st) return st;
   }
@@ -1318,6 +1745,20 @@ adot_status adot_ensemble_info(adot_ensemble* e, int32_t* block_out, int64_t* ti
   if (block_out) *block_out = e->block;
   if (tiles_out) *tiles_out = e->n_tiles;
   if (grid_out) *grid_out = e->grid;
+  return ADOT_OK;
+}
+
+adot_status adot_ensemble_plan(adot_ensemble* e, int32_t which, int32_t* form_out, int32_t* block_out,
+                               int32_t* cluster_out, int32_t* grid_out, int32_t* teamed_out,
+                               double* imbalance_out) {
+  if (!e || which < 0 || which > 1) return ADOT_E_INVALID_ARG;
+  const adot_ensemble::Plan& pl = e->plan[which];
+  if (form_out) *form_out = pl.persistent ? 3 : (e->warp ? 2 : 1);
+  if (block_out) *block_out = pl.persistent ? pl.block : e->block;
+  if (cluster_out) *cluster_out = pl.persistent ? pl.cluster : 1;
+  if (grid_out) *grid_out = pl.persistent ? pl.grid : e->grid;
+  if (teamed_out) *teamed_out = pl.persistent ? pl.n_big : 0;
+  if (imbalance_out) *imbalance_out = pl.imbalance;
   return ADOT_OK;
 }
 

@@ -136,6 +136,7 @@ def test_null_arguments_rejected(L):
     assert L.adot_precision_stats(None, None, None) == adot.E_INVALID_ARG
     assert L.adot_mlp_apply_gradient(None, None, 1e-3, 0) == adot.E_INVALID_ARG
     assert L.adot_autotune(None, 8, None, None, None) == adot.E_INVALID_ARG
+    assert L.adot_ensemble_plan(None, 0, None, None, None, None, None, None) == adot.E_INVALID_ARG
     assert L.adot_checkpoint_size(None, None) == adot.E_INVALID_ARG
     assert L.adot_checkpoint_save(None, None, 0, 0) == adot.E_INVALID_ARG
     assert L.adot_checkpoint_load(None, None, 0, 0) == adot.E_INVALID_ARG
@@ -173,8 +174,11 @@ def test_invalid_ensemble_config_rejected(L):
     c.block_threads = 100
     assert L.adot_ensemble_create(ctypes.byref(c), None, ctypes.byref(out)) == adot.E_INVALID_ARG
     c.block_threads = 0
-    c.step_kernel = 5
+    c.step_kernel = 6
     assert L.adot_ensemble_create(ctypes.byref(c), None, ctypes.byref(out)) == adot.E_INVALID_ARG
+    c.step_kernel, c.block_threads = 5, 384  # cluster teams run 768-thread CTAs only
+    assert L.adot_ensemble_create(ctypes.byref(c), None, ctypes.byref(out)) == adot.E_INVALID_ARG
+    c.block_threads = 0
     c.step_kernel, c.block_threads = 4, 384  # 384-thread blocks: persistent channel loops only
     assert L.adot_ensemble_create(ctypes.byref(c), None, ctypes.byref(out)) == adot.E_INVALID_ARG
     c.step_kernel, c.block_threads = 3, 128

@@ -298,3 +298,84 @@ def test_form_chosen_by_estimated_balance(gpu):
         assert np.array_equal(na, nb)
         for x, y in zip(sa, sb):
             assert np.abs(x - y).max() <= 1e-14 * np.abs(y).max()
+
+
+# ---- cluster teams: long channels stepped by the CTAs of one cluster ---------
+
+def _skewed(seed, big=(30000, 22000, 9000), n_small=60):
+    rng = np.random.default_rng(seed)
+    sizes = list(big) + [int(x) for x in rng.integers(1, 3000, n_small)]
+    return _small_ensemble(sizes, seed=seed)
+
+
+def test_team_form_matches_oracle_per_channel(gpu):
+    """step_kernel 5: the long channels run on cluster teams (2 or 4 CTAs
+    exchanging the CFL maximum through distributed shared memory every step),
+    the others one CTA each; FP64 per channel against the oracle (1e-12 and the
+    same step count). (The float32 form is held to the one-CTA form below,
+    whose float32 accuracy the tests above pin against the oracle.)"""
+    E = _skewed(31)
+    with gpu.Ensemble.from_workload(E, gpu.FP64, step_kernel=5) as ens:
+        ens.set_state(E.h, E.q, E.z)
+        pl = ens.plan(0)
+        launches = ens.run_to(0.02)
+        t, steps, _ = ens.query()
+        h, q, z = ens.get_state()
+    assert pl["form"] == 3 and pl["cluster"] in (2, 4) and pl["teamed"] >= 1, pl
+    assert launches == 1 and (t == 0.02).all()
+    o = E.offsets
+    for c in range(len(E.n_cells)):
+        ho, qo, zo, to, so, _ = _oracle_channel(E, c, 0.02)
+        sl = slice(o[c], o[c + 1])
+        assert steps[c] == so, (c, steps[c], so)
+        for a, b in ((h, ho), (q, qo), (z, zo)):
+            assert np.abs(a[sl] - b).max() <= 1e-12 * max(np.abs(b).max(), 1e-300), c
+
+
+@pytest.mark.parametrize("prec", ["FP64", "FP32"])
+def test_team_form_equals_one_cta_form(gpu, prec):
+    """The team form evaluates the same edges and cells as one CTA per channel
+    (384-thread CTAs, no teams), in another kernel whose update the compiler
+    may contract into fused multiply-adds differently: states within 1e-14
+    (float64, max) and 1e-6 (float32, L1 relative), equal times and step
+    counts, after run_to, after a fixed step count and after a second run_to."""
+    E = _skewed(32)
+    out = []
+    for kern, blk in ((5, 0), (3, 384)):
+        with gpu.Ensemble.from_workload(E, getattr(gpu, prec), step_kernel=kern, block_threads=blk) as ens:
+            ens.set_state(E.h, E.q, E.z)
+            pl0, pl1 = ens.plan(0), ens.plan(1)
+            ens.step(17)
+            s17 = ens.get_state()
+            ens.set_state(E.h, E.q, E.z)
+            ens.run_to(0.01)
+            ens.run_to(0.02)
+            t, steps, cu = ens.query()
+            out.append((pl0, pl1, s17, ens.get_state(), t, steps, cu))
+    (pa0, pa1, a17, sa, ta, na, ca), (pb0, pb1, b17, sb, tb, nb, cb) = out
+    assert pa0["cluster"] > 1 and pb0["cluster"] == 1 and pb0["block"] == 384
+    assert pa1["form"] == 3 and pb1["cluster"] == 1
+    for x, y in list(zip(sa, sb)) + list(zip(a17, b17)):
+        if prec == "FP32":
+            assert np.abs(x - y).sum() <= 1e-6 * np.abs(y).sum()
+        else:
+            assert np.abs(x - y).max() <= 1e-14 * np.abs(y).max()
+    assert np.array_equal(na, nb) and ca == cb
+    assert np.array_equal(ta, tb)
+
+
+def test_team_form_reports_dry_out(gpu):
+    """The longest channel (stepped by a team) dries out: the run stops with the
+    status, every CTA leaves, and the state can still be read."""
+    E = _skewed(33, big=(30000, 9000), n_small=30)
+    P = W.dam_break(30000, hL=0.1, hR=0.1, uL=-3.0, uR=3.0)
+    o = E.offsets
+    E.h[o[0]:o[1]], E.q[o[0]:o[1]], E.z[o[0]:o[1]] = P.h, P.q, P.z
+    with gpu.Ensemble.from_workload(E, gpu.FP32, step_kernel=5) as ens:
+        ens.set_state(E.h, E.q, E.z)
+        assert ens.plan(0)["teamed"] >= 1
+        with pytest.raises(gpu.AdotError) as e:
+            ens.run_to(1.0)
+        assert e.value.status in (gpu.E_NONPOSITIVE_DEPTH, gpu.E_NONFINITE)
+        h, q, z = ens.get_state()
+        assert h.shape == (int(E.n_cells.sum()),)
