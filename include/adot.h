@@ -500,6 +500,14 @@ adot_status adot_step_noalloc(const adot_config* cfg, double* h, double* q, doub
  * ADOT_E_INVALID_ARG for another kind or a NULL rate_out. */
 adot_status adot_measure_pipe(int kind, int device, double* rate_out, double* seconds_out);
 
+/* Probe of the library's float32 device math for the tests (no counterpart in
+ * the paper): y[i] = f(x[i]) for n values in device memory, on cuda_stream
+ * (NULL = legacy stream), then waits for it. kind 0 = the step kernels'
+ * arccos(x) / 3 (a degree-7 polynomial form of Abramowitz & Stegun 4.4.46,
+ * evaluated in float32), kind 1 = CUDA's acosf(x) / 3. x in [-1, 1].
+ * ADOT_E_INVALID_ARG for another kind, n < 0 or NULL arrays with n > 0. */
+adot_status adot_math_probe(int32_t kind, const float* x, float* y, int64_t n, void* cuda_stream);
+
 /* Name of a status code (static string). */
 const char* adot_status_string(adot_status s);
 

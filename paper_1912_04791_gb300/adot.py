@@ -123,6 +123,7 @@ def lib() -> ctypes.CDLL:
             "adot_ensemble_plan": ([_P, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
                                     ctypes.POINTER(i32), ctypes.POINTER(i32), _D], i32),
             "adot_measure_pipe": ([i32, i32, _D, _D], i32),
+            "adot_math_probe": ([i32, _P, _P, i64, _P], i32),
             "adot_status_string": ([i32], ctypes.c_char_p),
             "adot_version": ([], ctypes.c_char_p),
         }
@@ -610,6 +611,18 @@ def adot_precision_stats(ctx: int):
 
 
 PIPE_FFMA, PIPE_FFMA2, PIPE_RSQ, PIPE_SIN, PIPE_DFMA, PIPE_TANH, PIPE_TANH_BF16X2 = range(7)
+
+
+def adot_math_probe(kind: int, x):
+    """The library's float32 device math on a float32 CUDA tensor x: kind 0 the
+    step kernels' arccos(x)/3, kind 1 CUDA's acosf(x)/3; returns a new tensor."""
+    import torch
+    if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.float32 and x.is_contiguous()):
+        raise ValueError("adot_math_probe takes a contiguous float32 CUDA tensor")
+    y = torch.empty_like(x)
+    _check(lib().adot_math_probe(kind, x.data_ptr(), y.data_ptr(), x.numel(),
+                                 torch.cuda.current_stream(x.device).cuda_stream), "adot_math_probe")
+    return y
 
 
 def adot_measure_pipe(kind: int, device: int = -1):

@@ -2,6 +2,7 @@
 // conversion and fixed-order conserved sums.
 #include <type_traits>
 
+#include "../../include/adot.h"
 #include "adot_step_impl.cuh"
 
 namespace adot {
@@ -289,3 +290,23 @@ cudaError_t launch_sums_f64(StateF64 st, int64_t n, double* partial, double* out
 }
 
 }  // namespace adot
+
+// Probe of the library's float32 device math for the tests (no counterpart in
+// the paper): kind 0 = acos_third (the polynomial arccos(x) / 3 of the step
+// kernels), kind 1 = CUDA's acosf(x) / 3, on n values x of device memory.
+namespace {
+__global__ void k_math_probe(int kind, const float* __restrict__ x, float* __restrict__ y, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = kind == 0 ? adot::acos_third(x[i]) : acosf(x[i]) * (float)(1.0 / 3.0);
+}
+}  // namespace
+
+extern "C" adot_status adot_math_probe(int32_t kind, const float* x, float* y, int64_t n, void* cuda_stream) {
+  if (kind < 0 || kind > 1 || n < 0 || (n > 0 && (!x || !y))) return ADOT_E_INVALID_ARG;
+  if (n == 0) return ADOT_OK;
+  const int64_t g64 = (n + 255) / 256;
+  const unsigned g = (unsigned)(g64 < 152 * 32 ? g64 : 152 * 32);
+  k_math_probe<<<g, 256, 0, (cudaStream_t)cuda_stream>>>(kind, x, y, n);
+  if (cudaGetLastError() != cudaSuccess) return ADOT_E_CUDA;
+  return cudaStreamSynchronize((cudaStream_t)cuda_stream) == cudaSuccess ? ADOT_OK : ADOT_E_CUDA;
+}

@@ -63,8 +63,22 @@ __device__ __forceinline__ void node_eig_x2(const LawT<float>& L, float2 h, floa
   const float2 arg = mul2(mul2(p2(0.5f), k2), mul2(mul2(rk, rk), rk));
   const float ax = fminf(fmaxf(arg.x, -1.0f), 1.0f), ay = fminf(fmaxf(arg.y, -1.0f), 1.0f);
   float2 S, C;
-  __sincosf(acosf(ax) * (float)(1.0 / 3.0), &S.x, &C.x);
-  __sincosf(acosf(ay) * (float)(1.0 / 3.0), &S.y, &C.y);
+#ifdef ADOT_ACOS_LIBRARY
+  __sincosf(acos_third(ax), &S.x, &C.x);
+  __sincosf(acos_third(ay), &S.y, &C.y);
+#else
+  {
+    // acos_third of both lanes with the polynomial in paired instructions
+    const float2 aa = make_float2(fabsf(ax), fabsf(ay));
+    float2 pp = p2(acos3_coef(7));
+#pragma unroll
+    for (int i = 6; i >= 0; --i) pp = fma2(pp, aa, p2(acos3_coef(i)));
+    const float2 sq = make_float2(sqrtf(1.0f - aa.x), sqrtf(1.0f - aa.y));
+    const float2 r = mul2(sq, pp);
+    __sincosf(ax >= 0.0f ? r.x : kPi3 - r.x, &S.x, &C.x);
+    __sincosf(ay >= 0.0f ? r.y : kPi3 - r.y, &S.y, &C.y);
+  }
+#endif
   const float2 k1rk = mul2(k1, rk);                               // sqrt(k1)
   const float2 m = mul2(p2((float)(2.0 / 3.0)), k1rk);            // (2/3) sqrt(k1)
   const float2 nm = mul2(p2((float)(-2.0 / 3.0)), k1rk);

@@ -147,6 +147,13 @@ def test_null_arguments_rejected(L):
     L.adot_destroy(None)
 
 
+def test_math_probe_rejects_bad_arguments(L):
+    assert L.adot_math_probe(2, None, None, 0, None) == adot.E_INVALID_ARG
+    assert L.adot_math_probe(0, None, None, 5, None) == adot.E_INVALID_ARG
+    assert L.adot_math_probe(0, None, None, -1, None) == adot.E_INVALID_ARG
+    assert L.adot_math_probe(0, None, None, 0, None) == adot.OK
+
+
 def test_measure_pipe_rejects_bad_kind(L):
     r = ctypes.c_double()
     assert L.adot_measure_pipe(7, -1, ctypes.byref(r), None) == adot.E_INVALID_ARG
