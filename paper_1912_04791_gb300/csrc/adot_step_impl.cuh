@@ -526,7 +526,9 @@ __device__ __forceinline__ void warp_step_size(const StepParams& p, int slot, in
 // share one edge (the only edge evaluated twice).
 //  - static part: with W warps and K = n / 32 chunks, each warp first takes a
 //    contiguous range of k_s = floor((6/8) K / W) chunks (none when k_s < 2),
-//    so cells [0, N_s) with N_s = W' (32 k_s - 1), W' <= W;
+//    so cells [0, N_s) with N_s = W' (32 k_s - 1), W' <= W; warp w of block b
+//    takes range w G + b (G blocks), so neighbouring ranges run on different
+//    SMs;
 //  - work pool: cells [N_s, n) in groups of 63 cells (2 chunks), handed out by
 //    an atomic counter in the control block; a warp asks for its next group
 //    before it computes the current one, so the atomic's latency is hidden.
@@ -585,10 +587,14 @@ __global__ void __launch_bounds__(B, MinBlocks<B, CAP>::value)
   int64_t eb = 0;
   int rem = -1;
   {
+    // range ri = w G + b for warp w of block b (G blocks): consecutive ranges
+    // belong to different blocks, so to different SMs, and a run of expensive
+    // cells (edges redone in float64 near critical flow) is spread over the GPU
     int64_t cs, n_s;
     static_split(cs, n_s);
-    if ((gw + 1) * cs <= n_s) {
-      eb = gw * cs;
+    const int64_t ri = (int64_t)(threadIdx.x >> 5) * gridDim.x + blockIdx.x;
+    if ((ri + 1) * cs <= n_s) {
+      eb = ri * cs;
       rem = (int)cs;
     }
   }
