@@ -346,6 +346,15 @@ adot_status adot_ensemble_plan(adot_ensemble* ens, int32_t which, int32_t* form_
                                int32_t* cluster_out, int32_t* grid_out, int32_t* teamed_out,
                                double* imbalance_out);
 
+/* Test hook of the cluster-team form's failure detection (no counterpart in
+ * the paper). kind 1: in the next launch of the team form, CTA 1 of cluster 0
+ * does not arrive at its first team exchange, so both members' bounded waits
+ * (about 2^31 clock cycles, ~1 s) run out; the kernel records ST_TIMEOUT, every
+ * CTA leaves, and run_to / step return ADOT_E_TIMEOUT with the context usable
+ * (set_state starts over). kind 0 clears it. Nothing faults or hangs.
+ * ADOT_E_INVALID_ARG for another kind. */
+adot_status adot_ensemble_inject_fault(adot_ensemble* ens, int32_t kind);
+
 /* ---- Learned surrogate of the quadrature-averaged |A| ----------------------
  * |A|_Psi = sum_k w_k |A(Psi(s_k))|, the matrix that multiplies W+ - W- in the
  * dissipative half of Eq. DOTjumpN, is approximated by a multilayer perceptron

@@ -122,6 +122,7 @@ def lib() -> ctypes.CDLL:
                                     ctypes.POINTER(i32), ctypes.POINTER(i32)], i32),
             "adot_ensemble_plan": ([_P, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
                                     ctypes.POINTER(i32), ctypes.POINTER(i32), _D], i32),
+            "adot_ensemble_inject_fault": ([_P, i32], i32),
             "adot_measure_pipe": ([i32, i32, _D, _D], i32),
             "adot_math_probe": ([i32, _P, _P, i64, _P], i32),
             "adot_status_string": ([i32], ctypes.c_char_p),
@@ -416,6 +417,11 @@ class Ensemble:
         _check(lib().adot_ensemble_info(self.ptr, ctypes.byref(b), ctypes.byref(nt), ctypes.byref(g),
                                         ctypes.byref(k)), "adot_ensemble_info")
         return b.value, nt.value, g.value, k.value
+
+    def inject_fault(self, kind: int = 1):
+        """Test hook: kind 1 withholds one team member's first arrival in the next
+        team launch (bounded waits run out, ADOT_E_TIMEOUT)."""
+        _check(lib().adot_ensemble_inject_fault(self.ptr, kind), "adot_ensemble_inject_fault")
 
     def plan(self, which: int = 0) -> dict:
         """The plan of run_to (which = 0) or step (1): form (3 persistent, 1/2

@@ -548,6 +548,7 @@ struct EnsTeamRun {
   double t_end;
   long long max_steps;
   int slot;
+  int fault;  // test hook: 1 = cluster 0's CTA 1 does not arrive at its first exchange
 };
 
 struct TeamSmem {
@@ -562,16 +563,18 @@ struct TeamSmem {
 template <int CL>
 __device__ __forceinline__ bool team_exchange(TeamSmem& ts, int k, unsigned long long rho_bits,
                                               unsigned long long stop, unsigned long long& rmax,
-                                              unsigned long long& sany) {
+                                              unsigned long long& sany, bool withhold) {
   const int par = k & 1;
   ts.val[par][0] = rho_bits;
   ts.val[par][1] = stop;
   __threadfence();
   const uint32_t bar = sh_addr(&ts.bar);
+  if (!withhold) {
 #pragma unroll
-  for (int q = 0; q < CL; ++q)
-    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cl_map(bar, (uint32_t)q))
-                 : "memory");
+    for (int q = 0; q < CL; ++q)
+      asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cl_map(bar, (uint32_t)q))
+                   : "memory");
+  }
   const long long t0 = clock64();
   for (;;) {
     uint32_t done;
@@ -619,13 +622,15 @@ __global__ void __launch_bounds__(B, 65536 / (B * CAP))
   unsigned flags = 0;
   bool quit = false;
   int xk = 0;  // exchanges so far
+  const uint32_t cid = cl_id();
   // team exchange of this CTA's (rho, error) by all threads; results in ts
   auto exchange = [&](R rho_cta, bool err) {
     if (threadIdx.x == 0) {
       unsigned long long rm = 0ull, sa = 0ull;
       const bool st_err = err || *(volatile unsigned*)p.d.status != 0;
+      const bool withhold = r.fault == 1 && cid == 0 && rank == 1 && xk == 0;
       if (!team_exchange<CL>(ts, xk, rho_cta > R(0) ? Prec<R>::bits(rho_cta) : 0ull, st_err ? 1ull : 0ull, rm,
-                             sa)) {
+                             sa, withhold)) {
         atomicOr(p.d.status, ST_TIMEOUT);
         ts.out_stop = 2;
       } else {
@@ -637,7 +642,6 @@ __global__ void __launch_bounds__(B, 65536 / (B * CAP))
     __syncthreads();
   };
 
-  const uint32_t cid = cl_id();
   for (int k = r.big_ptr[cid]; !quit && k < r.big_ptr[cid + 1]; ++k) {
     const int c = r.big_list[k];
     const int64_t base = p.off[c];
@@ -843,6 +847,7 @@ struct adot_ensemble {
     int* d_team;     // [clusters + 1 + C]: big_ptr, then big_list
   } plan[2];
   int team_clusters[2];  // resident clusters of k_ens_run_team with 2 and 4 CTAs (0: not launchable)
+  int fault;             // test hook for the next team launch (adot_ensemble_inject_fault)
   int block_cfg;        // configured block_threads (0 = any)
   bool tuned;
   int steps_per_graph;
@@ -1402,6 +1407,8 @@ adot_status ens_run(adot_ensemble* e, const adot_ensemble::Plan& pl, double t_en
       r.t_end = t_end;
       r.max_steps = m;
       r.slot = slot;
+      r.fault = e->fault;
+      e->fault = 0;
       CKE(ens_team_call(e, r, pl.cluster, pl.grid / pl.cluster));
     } else {
       EnsRun r;
@@ -1745,6 +1752,12 @@ adot_status adot_ensemble_info(adot_ensemble* e, int32_t* block_out, int64_t* ti
   if (block_out) *block_out = e->block;
   if (tiles_out) *tiles_out = e->n_tiles;
   if (grid_out) *grid_out = e->grid;
+  return ADOT_OK;
+}
+
+adot_status adot_ensemble_inject_fault(adot_ensemble* e, int32_t kind) {
+  if (!e || kind < 0 || kind > 1) return ADOT_E_INVALID_ARG;
+  e->fault = kind;
   return ADOT_OK;
 }
 

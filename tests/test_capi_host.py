@@ -137,6 +137,7 @@ def test_null_arguments_rejected(L):
     assert L.adot_mlp_apply_gradient(None, None, 1e-3, 0) == adot.E_INVALID_ARG
     assert L.adot_autotune(None, 8, None, None, None) == adot.E_INVALID_ARG
     assert L.adot_ensemble_plan(None, 0, None, None, None, None, None, None) == adot.E_INVALID_ARG
+    assert L.adot_ensemble_inject_fault(None, 1) == adot.E_INVALID_ARG
     assert L.adot_checkpoint_size(None, None) == adot.E_INVALID_ARG
     assert L.adot_checkpoint_save(None, None, 0, 0) == adot.E_INVALID_ARG
     assert L.adot_checkpoint_load(None, None, 0, 0) == adot.E_INVALID_ARG

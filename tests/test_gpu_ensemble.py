@@ -379,3 +379,29 @@ def test_team_form_reports_dry_out(gpu):
         assert e.value.status in (gpu.E_NONPOSITIVE_DEPTH, gpu.E_NONFINITE)
         h, q, z = ens.get_state()
         assert h.shape == (int(E.n_cells.sum()),)
+
+
+def test_team_exchange_wait_runs_out_and_reports(gpu):
+    """A team member withholds its first arrival (adot_ensemble_inject_fault):
+    the members' bounded waits run out (~1 s), the launch ends with
+    ADOT_E_TIMEOUT instead of hanging, and the ensemble is usable again after
+    set_state (the next run matches a fresh ensemble's)."""
+    E = _skewed(34)
+    with gpu.Ensemble.from_workload(E, gpu.FP64, step_kernel=5) as ens:
+        ens.set_state(E.h, E.q, E.z)
+        assert ens.plan(0)["teamed"] >= 1
+        ens.inject_fault(1)
+        with pytest.raises(gpu.AdotError) as e:
+            ens.run_to(0.01)
+        assert e.value.status == gpu.E_TIMEOUT
+        ens.set_state(E.h, E.q, E.z)
+        ens.run_to(0.01)
+        got = ens.get_state()
+        t, _, _ = ens.query()
+    assert (t == 0.01).all()
+    with gpu.Ensemble.from_workload(E, gpu.FP64, step_kernel=5) as ens:
+        ens.set_state(E.h, E.q, E.z)
+        ens.run_to(0.01)
+        ref = ens.get_state()
+    for a, b in zip(got, ref):
+        assert np.array_equal(a, b)
