@@ -287,6 +287,89 @@ __device__ __forceinline__ void ens_subtile(const StepParams& lp, const typename
     }
 }
 
+// A contiguous range of one channel's edges in chunks of 32 (as the
+// single-channel warp kernel): lane l of the chunk starting at edge eb
+// evaluates edge eb + l and updates cell eb + l - 1 with D+ of the previous
+// edge from lane l - 1, or in lane 0 carried over from lane 31 of the previous
+// chunk; rem = edges of the range after its first (the first edge's cell is
+// not updated). The ends copy the adjacent cell (transmissive), so the end
+// edges carry no fluctuation.
+template <typename R, int CAP, bool CG = false>
+__device__ __forceinline__ void ens_range(const StepParams& lp, const typename Prec<R>::State& in,
+                                          const typename Prec<R>::State& out, const int64_t base,
+                                          const int64_t nc, const int64_t e0, int rem, const R nu, R& rho,
+                                          unsigned& flags) {
+  using S = typename Prec<R>::S;
+  const int lane = threadIdx.x & 31;
+  R carry[3] = {R(0), R(0), R(0)};
+  bool lead = lane >= 1;
+  for (int64_t eb = e0; rem >= 0; eb += 32, rem -= 32) {
+    const int64_t e = eb + lane;
+    const bool in_range = lane <= rem;
+    S wl[3];
+    R dm[3] = {R(0), R(0), R(0)}, dp[3] = {R(0), R(0), R(0)};
+    if (in_range) {
+      S wr[3];
+      const int64_t il = (e > 0) ? e - 1 : 0;
+      const int64_t ir = (e < nc) ? e : nc - 1;
+      wl[0] = ens_ld<CG>(in.h + base + il);
+      wl[1] = ens_ld<CG>(in.q + base + il);
+      wl[2] = ens_ld<CG>(in.z + base + il);
+      wr[0] = ens_ld<CG>(in.h + base + ir);
+      wr[1] = ens_ld<CG>(in.q + base + ir);
+      wr[2] = ens_ld<CG>(in.z + base + ir);
+      if (e > 0 && e < nc) edge_fluct<R, LAW_GRASS, (CAP >= 80)>(lp, wl, wr, dm, dp, flags);
+    }
+    R dl[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const R up = __shfl_sync(0xffffffffu, dp[r], (lane + 31) & 31);
+      dl[r] = lane ? up : carry[r];
+      carry[r] = up;  // lane 0: D+ of this chunk's last edge
+    }
+    if (lead && in_range) {
+      const int64_t i = e - 1;
+      const S nh = Prec<R>::add(wl[0], -nu * (dm[0] + dl[0]));
+      const S nq = Prec<R>::add(wl[1], -nu * (dm[1] + dl[1]));
+      const S nz = Prec<R>::add(wl[2], -nu * (dm[2] + dl[2]));
+      out.h[base + i] = nh;
+      out.q[base + i] = nq;
+      out.z[base + i] = nz;
+      const R hh = Prec<R>::hi(nh);
+      if (!(hh > R(0))) flags |= ST_DEPTH;
+      if (!(Prec<R>::finite(nh) && Prec<R>::finite(nq) && Prec<R>::finite(nz))) {
+        flags |= ST_NONFINITE;
+      } else if (hh > R(0)) {
+        R v = Prec<R>::template rho<LAW_GRASS>(lp, hh, Prec<R>::hi(nq));
+        if (!(v <= R(3.0e38))) {
+          flags |= ST_NONFINITE;
+          v = R(0);
+        }
+        rho = v > rho ? v : rho;
+      }
+    }
+    lead = true;
+  }
+}
+
+// One step of a channel of nc cells by `nw` warps (warp index w): the edges
+// 0 .. nc in contiguous ranges of whole chunks, one per active warp (at least
+// 31 cells each), consecutive ranges sharing one edge.
+template <typename R, int CAP, bool CG = false>
+__device__ __forceinline__ void ens_channel_sweep(const StepParams& lp, const typename Prec<R>::State& in,
+                                                  const typename Prec<R>::State& out, const int64_t base,
+                                                  const int64_t nc, const int64_t w, const int64_t nw,
+                                                  const R nu, R& rho, unsigned& flags) {
+  const int64_t nact = (nw < (nc + 30) / 31) ? nw : (nc + 30) / 31;
+  if (w >= nact) return;
+  const int64_t K = (nc + nact + 31) / 32;
+  const int64_t kb = K / nact, kr = K % nact;
+  const int64_t kw = kb + (w < kr ? 1 : 0);
+  const int64_t e0 = 32 * (w * kb + (w < kr ? w : kr)) - w;
+  const int64_t last = (e0 + 32 * kw - 1 < nc) ? e0 + 32 * kw - 1 : nc;
+  ens_range<R, CAP, CG>(lp, in, out, base, nc, e0, (int)(last - e0), nu, rho, flags);
+}
+
 // Persistent warp tiles: each warp walks tiles of SUB x 31 cells of one
 // channel (tile list in those units, longest channel first) with a grid-wide
 // stride over the active bound. Lane 0 evaluates the channel's control once per
@@ -436,8 +519,7 @@ __device__ __forceinline__ bool ens_run_channel(const EnsParams& p, const typena
     const typename Prec<R>::State& in = cur ? b1 : b0;
     const typename Prec<R>::State& out = cur ? b0 : b1;
     R rr = R(0);
-    for (int64_t e0 = (int64_t)warp * 31; e0 < nc; e0 += NW * 31)
-      ens_subtile<R, CAP>(lp, in, out, base, nc, e0, lane, nu, 0, rr, flags);
+    ens_channel_sweep<R, CAP>(lp, in, out, base, nc, warp, NW, nu, rr, flags);
     rho = block_max<R, NW>(rr, sRed);
     t = tn;
     ++st;
@@ -690,8 +772,8 @@ __global__ void __launch_bounds__(B, 65536 / (B * CAP))
       const typename Prec<R>::State& in = cur ? b1 : b0;
       const typename Prec<R>::State& out = cur ? b0 : b1;
       R rr = R(0);
-      for (int64_t e0 = ((int64_t)rank * NW + warp) * 31; e0 < nc; e0 += (int64_t)CL * NW * 31)
-        ens_subtile<R, CAP, true>(lp, in, out, base, nc, e0, lane, nu, 0, rr, flags);
+      ens_channel_sweep<R, CAP, true>(lp, in, out, base, nc, (int64_t)rank * NW + warp, (int64_t)CL * NW, nu,
+                                      rr, flags);
       rr = block_max<R, NW>(rr, sRed);
       exchange(rr, __syncthreads_or(flags != 0));
       stop = ts.out_stop;

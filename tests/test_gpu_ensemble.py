@@ -205,10 +205,14 @@ def test_persistent_fp32_matches_oracle_per_channel(gpu):
 
 @pytest.mark.parametrize("prec", ["FP32", "FP64"])
 def test_persistent_agrees_with_per_step_warp_tiles(gpu, prec):
-    """Same sub-tile arithmetic (256 threads, 80-register cap) in both forms:
-    equal times and step counts, states within 1e-14 (float64, max; the
-    compiler may contract the update differently in the two kernels) and 1e-6
-    (float32, L1 relative), both after run_to and after a fixed step count."""
+    """The same edges (80-register cap, paired outer nodes) in both forms; the
+    persistent form walks each channel in contiguous ranges with D+ carried
+    between chunks, the per-step form in 31-cell sub-tiles, and the compiler
+    contracts their updates into fused multiply-adds differently, so float64
+    states drift apart by rounding over the ~800 steps: equal times and step
+    counts, states within 1e-13 (float64, max; both are within 1e-12 of the
+    oracle) and 1e-6 (float32, L1 relative), after run_to and after a fixed
+    step count."""
     E = _small_ensemble(SIZES + [3000, 1234, 9000], seed=6)
     out = []
     for kern, blk in ((2, 256), (3, 256)):
@@ -229,7 +233,7 @@ def test_persistent_agrees_with_per_step_warp_tiles(gpu, prec):
         if prec == "FP32":
             assert np.abs(x - y).sum() <= 1e-6 * np.abs(y).sum()
         else:
-            assert np.abs(x - y).max() <= 1e-14 * np.abs(y).max()
+            assert np.abs(x - y).max() <= 1e-13 * np.abs(y).max()
     assert np.array_equal(ta, tb) and np.array_equal(na, nb) and ca == cb
 
 
