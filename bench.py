@@ -955,7 +955,7 @@ def main():
                          "hbm_achieved_gbs": BYTES_PER_CELL_UPDATE * n / per_launch_s / 1e9,
                          "hbm_peak_gbs": measured_peaks().get("hbm_gbs", 6800.0),
                          "issue_slots": issue_roofline(kc.get("instr"), n, per_launch_s)},
-            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps, "clocks": clocks,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps * (2 if kern == 2 else 1), "clocks": clocks,
             "accuracy": accuracy, "sim_time_after_timed_steps": t_sim, "variants": variants,
             "ensemble": ensemble, "surrogate": surrogate, "friction": friction, "order2": order2,
             "price_c": price, "config3": config3, "peaks": peaks,

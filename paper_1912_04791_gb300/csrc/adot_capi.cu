@@ -39,6 +39,7 @@ struct adot_ctx {
   Ctl* d_ctl;
   Ctl* h_ctl;       // pinned mirror
   double* d_io;     // 3 * n float64 staging for conversions
+  unsigned* d_fix;  // float32: n cells left to k_fixup by a step
   double* d_partial;
   double* d_sums;
   double* h_sums;   // pinned, 3
@@ -430,6 +431,7 @@ void free_ctx(adot_ctx* c) {
   if (c->d_ctl) cudaFree(c->d_ctl);
   if (c->h_ctl) cudaFreeHost(c->h_ctl);
   if (c->d_io) cudaFree(c->d_io);
+  if (c->d_fix) cudaFree(c->d_fix);
   if (c->d_partial) cudaFree(c->d_partial);
   if (c->d_sums) cudaFree(c->d_sums);
   if (c->h_sums) cudaFreeHost(c->h_sums);
@@ -519,6 +521,8 @@ adot_status adot_create(const adot_config* cfg, void* cuda_stream, adot_ctx** ou
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_flrho, sizeof(unsigned long long) * 2);
   if (e == cudaSuccess) e = cudaHostAlloc((void**)&c->h_flrho, sizeof(unsigned long long) * 2, cudaHostAllocDefault);
   if (e == cudaSuccess && c->prec == ADOT_FP32) e = cudaMalloc((void**)&c->d_io, sizeof(double) * 3 * (size_t)n);
+  if (e == cudaSuccess && c->prec == ADOT_FP32) e = cudaMalloc((void**)&c->d_fix, sizeof(unsigned) * (size_t)n);
+  p.fix_list = c->d_fix;
   if (e == cudaSuccess) {
     memset(c->h_ctl, 0, sizeof(Ctl));
     c->h_ctl->t_end = INFINITY;

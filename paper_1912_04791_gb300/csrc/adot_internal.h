@@ -27,6 +27,11 @@ struct Ctl {
   // work-pool head of the warp-tile step kernel: 0 between launches (the warp
   // that takes the launch's last ticket puts it back)
   unsigned grab;
+  // cells the float32 warp-tile step left to k_fixup (an edge needing the
+  // float64 redo), and k_fixup's finished blocks: both 0 between steps (the
+  // last block of k_fixup puts them back)
+  unsigned fix_count;
+  unsigned fix_done;
   unsigned pad2;
 };
 
@@ -59,6 +64,7 @@ struct StepParams {
   double price_eps;         // PRICE-C: epsilon of I_eps (Eq. Im)
   Ctl* ctl;
   const float* absA;  // surrogate |A|_Psi per edge, [9][n+1] (NaN in row 0: analytic edge)
+  unsigned* fix_list; // [n] cells left to k_fixup by the float32 warp-tile step (nullptr: redo in place)
 };
 
 enum : int {

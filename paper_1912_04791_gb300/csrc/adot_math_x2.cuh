@@ -190,14 +190,14 @@ __device__ __noinline__ EdgeD edge_fluct_f64_redo(const LawT<double>& Ld, float2
   return out;
 }
 
-// D-/+ of one float32 edge (float-float states wl, wr): nodes s0 and s2 paired,
-// the midpoint node scalar. When any node has 1 - arg^2 < TAU_FP64_FALLBACK
-// (or arg not finite), i.e. two roots nearly coalesce, the whole edge is
-// redone in float64 (edge_fluct_f64_redo).
+// D-/+ of one float32 edge (float-float states wl, wr) from float32 nodes: s0
+// and s2 paired, the midpoint node scalar. Returns whether any node has
+// 1 - arg^2 < TAU_FP64_FALLBACK (or arg not finite), i.e. two roots nearly
+// coalesce and the edge must be redone in float64 (dm, dp are then the
+// float32 values, not to be used).
 template <int LAW>
-__device__ __forceinline__ void edge_fluct_f32x2(const LawT<float>& L, const LawT<double>& Ld,
-                                                 const float2 wl[3], const float2 wr[3], float dm[3],
-                                                 float dp[3], unsigned& flags) {
+__device__ __forceinline__ bool edge_fluct_f32x2_core(const LawT<float>& L, const float2 wl[3],
+                                                      const float2 wr[3], float dm[3], float dp[3]) {
   const float dh = ff_diff(wr[0], wl[0]);
   const float dq = ff_diff(wr[1], wl[1]);
   const float dz = ff_diff(wr[2], wl[2]);
@@ -218,16 +218,6 @@ __device__ __forceinline__ void edge_fluct_f32x2(const LawT<float>& L, const Law
   const bool redo = !(fmaf(-e.arg.x, e.arg.x, 1.0f) >= TAU_FP64_FALLBACK) ||
                     !(fmaf(-e.arg.y, e.arg.y, 1.0f) >= TAU_FP64_FALLBACK) ||
                     !(fmaf(-em.arg, em.arg, 1.0f) >= TAU_FP64_FALLBACK);
-  if (redo) {
-    const EdgeD d = edge_fluct_f64_redo<LAW>(Ld, wl[0], wl[1], wl[2], wr[0], wr[1], wr[2]);
-    flags |= d.flags;
-#pragma unroll
-    for (int r = 0; r < 3; ++r) {
-      dm[r] = d.dm[r];
-      dp[r] = d.dp[r];
-    }
-    return;
-  }
   const float w0 = (float)GL3_W0, w1 = (float)GL3_W1;
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
@@ -235,6 +225,24 @@ __device__ __forceinline__ void edge_fluct_f32x2(const LawT<float>& L, const Law
     const float xa = fmaf(w0, x[r].x + x[r].y, w1 * xm[r]);
     dm[r] = 0.5f * (ya - xa);
     dp[r] = 0.5f * (ya + xa);
+  }
+  return redo;
+}
+
+// The same with the float64 redo of a flagged edge done in place
+// (edge_fluct_f64_redo).
+template <int LAW>
+__device__ __forceinline__ void edge_fluct_f32x2(const LawT<float>& L, const LawT<double>& Ld,
+                                                 const float2 wl[3], const float2 wr[3], float dm[3],
+                                                 float dp[3], unsigned& flags) {
+  if (edge_fluct_f32x2_core<LAW>(L, wl, wr, dm, dp)) {
+    const EdgeD d = edge_fluct_f64_redo<LAW>(Ld, wl[0], wl[1], wl[2], wr[0], wr[1], wr[2]);
+    flags |= d.flags;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      dm[r] = d.dm[r];
+      dp[r] = d.dp[r];
+    }
   }
 }
 

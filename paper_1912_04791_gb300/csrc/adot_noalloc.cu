@@ -76,6 +76,8 @@ __global__ void k_noalloc_ctl_init(Ctl* ctl, double t0) {
   ctl->status = 0u;
   ctl->pad = 0u;
   ctl->grab = 0u;
+  ctl->fix_count = 0u;
+  ctl->fix_done = 0u;
   ctl->pad2 = 0u;
 }
 

@@ -199,6 +199,49 @@ constexpr bool kPairedNodes = true;
 // D-/+ of one edge from its two states. PAIRED: float32 edges take the
 // paired-instruction form of the two outer nodes (fewer issue slots, more
 // registers); the ensemble kernel, held to 64 registers, keeps the scalar form.
+// All-scalar float32 edge (as edge_fluct_f32x2_core with every node scalar):
+// D-/+ in float32 and whether the edge needs the float64 redo.
+template <int LAW>
+__device__ __forceinline__ bool edge_fluct_f32_scalar_core(const LawT<float>& L, const float2 wl[3],
+                                                           const float2 wr[3], float dm[3], float dp[3]) {
+  const float dh = ff_diff(wr[0], wl[0]), dq = ff_diff(wr[1], wl[1]), dz = ff_diff(wr[2], wl[2]);
+  const float h0 = wl[0].x, q0 = wl[1].x;
+  float ya[3] = {0.0f, 0.0f, 0.0f}, xa[3] = {0.0f, 0.0f, 0.0f};
+  bool redo = false;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float sk = (k == 0) ? (float)GL3_S0 : ((k == 1) ? 0.5f : (float)GL3_S2);
+    const float w = (k == 1) ? (float)GL3_W1 : (float)GL3_W0;
+    Eig<float> e;
+    node_eig<float, LAW>(L, h0 + sk * dh, q0 + sk * dq, e);
+    redo = redo || !(fmaf(-e.arg, e.arg, 1.0f) >= TAU_FP64_FALLBACK);
+    float y[3], x[3];
+    A_times(e, dh, dq, dz, y[0], y[1], y[2]);
+    abs_A_times_proj(e, dh, dq, dz, y, x);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      ya[r] += w * y[r];
+      xa[r] += w * x[r];
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    dm[r] = 0.5f * (ya[r] - xa[r]);
+    dp[r] = 0.5f * (ya[r] + xa[r]);
+  }
+  return redo;
+}
+
+// Float32 edge without the float64 redo: D-/+ from the float32 nodes and
+// whether the edge needs float64 (the step kernel then leaves the two cells of
+// the edge to k_fixup).
+template <int LAW, bool PAIRED = kPairedNodes>
+__device__ __forceinline__ bool edge_fluct_deferred(const StepParams& p, const float2 wl[3],
+                                                    const float2 wr[3], float dm[3], float dp[3]) {
+  if constexpr (PAIRED) return edge_fluct_f32x2_core<LAW>(p.lf, wl, wr, dm, dp);
+  else return edge_fluct_f32_scalar_core<LAW>(p.lf, wl, wr, dm, dp);
+}
+
 template <typename R, int LAW, bool PAIRED = kPairedNodes>
 __device__ __forceinline__ void edge_fluct(const StepParams& p, const typename Prec<R>::S wl[3],
                                            const typename Prec<R>::S wr[3], R dm[3], R dp[3],
@@ -209,27 +252,7 @@ __device__ __forceinline__ void edge_fluct(const StepParams& p, const typename P
   } else if constexpr (std::is_same<R, float>::value) {
     // all-scalar float32 nodes; as in edge_fluct_f32x2, an edge with a node
     // whose roots nearly coalesce is redone in float64 as a whole
-    const float dh = ff_diff(wr[0], wl[0]), dq = ff_diff(wr[1], wl[1]), dz = ff_diff(wr[2], wl[2]);
-    const float h0 = wl[0].x, q0 = wl[1].x;
-    float ya[3] = {0.0f, 0.0f, 0.0f}, xa[3] = {0.0f, 0.0f, 0.0f};
-    bool redo = false;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      const float sk = (k == 0) ? (float)GL3_S0 : ((k == 1) ? 0.5f : (float)GL3_S2);
-      const float w = (k == 1) ? (float)GL3_W1 : (float)GL3_W0;
-      Eig<float> e;
-      node_eig<float, LAW>(p.lf, h0 + sk * dh, q0 + sk * dq, e);
-      redo = redo || !(fmaf(-e.arg, e.arg, 1.0f) >= TAU_FP64_FALLBACK);
-      float y[3], x[3];
-      A_times(e, dh, dq, dz, y[0], y[1], y[2]);
-      abs_A_times_proj(e, dh, dq, dz, y, x);
-#pragma unroll
-      for (int r = 0; r < 3; ++r) {
-        ya[r] += w * y[r];
-        xa[r] += w * x[r];
-      }
-    }
-    if (redo) {
+    if (edge_fluct_f32_scalar_core<LAW>(p.lf, wl, wr, dm, dp)) {
       const EdgeD d = edge_fluct_f64_redo<LAW>(p.ld, wl[0], wl[1], wl[2], wr[0], wr[1], wr[2]);
       flags |= d.flags;
 #pragma unroll
@@ -237,12 +260,6 @@ __device__ __forceinline__ void edge_fluct(const StepParams& p, const typename P
         dm[r] = d.dm[r];
         dp[r] = d.dp[r];
       }
-      return;
-    }
-#pragma unroll
-    for (int r = 0; r < 3; ++r) {
-      dm[r] = 0.5f * (ya[r] - xa[r]);
-      dp[r] = 0.5f * (ya[r] + xa[r]);
     }
   } else {
     const R dh = Prec<R>::diff(wr[0], wl[0]);
@@ -544,7 +561,7 @@ __device__ __forceinline__ void warp_step_size(const StepParams& p, int slot, in
 //
 // SCHEME 0 evaluates the DOT edge of Eq. DOTjumpN; SCHEME 1 the PRICE-C edge
 // (edge_fluct_price), everything else unchanged.
-template <typename R, int LAW, int B, int CAP, bool EXT = false, int SCHEME = 0>
+template <typename R, int LAW, int B, int CAP, bool EXT = false, int SCHEME = 0, bool DEFER = false>
 __global__ void __launch_bounds__(B, MinBlocks<B, CAP>::value)
     k_step_warp(const StepParams p, const typename Prec<R>::State in,
                 const typename Prec<R>::State out, const int slot) {
@@ -574,6 +591,7 @@ __global__ void __launch_bounds__(B, MinBlocks<B, CAP>::value)
 
   unsigned flags = 0;
   R rho_run = R(0);
+  bool carry_rd = false;  // DEFER: lane 0's flag of the previous chunk's last edge
   // the split: static ranges of cs cells over cells [0, n_s), then pool groups
   auto static_split = [&](int64_t& cs, int64_t& n_s) {
     int64_t ks = (((n + 31) / 32) * ADOT_STATIC_EIGHTHS / 8) / nwarps;
@@ -629,11 +647,14 @@ __global__ void __launch_bounds__(B, MinBlocks<B, CAP>::value)
     }
     S wl[3];
     R dm[3] = {R(0), R(0), R(0)}, dp[3] = {R(0), R(0), R(0)};
+    bool rd = false;  // DEFER: this edge needs the float64 redo
     if (in_range) {
       S wr[3];
       load_edge<R, EXT>(p, in, e, slot, wl, wr);
       if constexpr (SCHEME == 1)
         edge_fluct_price<R, LAW>(p, nu, inv_nu, wl, wr, dm, dp);
+      else if constexpr (DEFER && std::is_same<R, float>::value)
+        rd = edge_fluct_deferred<LAW>(p, wl, wr, dm, dp);
       else
         edge_fluct<R, LAW>(p, wl, wr, dm, dp, flags);
       if constexpr (EXT) feed_edge<R, LAW>(p, e, wl, wr, dm, dp);
@@ -655,7 +676,24 @@ __global__ void __launch_bounds__(B, MinBlocks<B, CAP>::value)
       }
     }
     const int64_t i = e - 1;
-    if (lead && in_range) {
+    // DEFER: a cell with an edge that needs the float64 redo (its own, or the
+    // previous lane's / previous chunk's) is not written here but listed for
+    // k_fixup, which recomputes it from the same input state
+    bool fix = false;
+    if constexpr (DEFER) {
+      const bool up_rd = __shfl_sync(0xffffffffu, rd, (lane + 31) & 31);
+      const bool rd_left = lane ? up_rd : carry_rd;
+      carry_rd = up_rd;
+      fix = !done && (rd || rd_left);
+      const unsigned m = __ballot_sync(0xffffffffu, lead && in_range && fix);
+      if (m) {
+        unsigned base = 0u;
+        if (lane == 0) base = atomicAdd(&ctl->fix_count, (unsigned)__popc(m));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (lead && in_range && fix) p.fix_list[base + __popc(m & ((1u << lane) - 1u))] = (unsigned)i;
+      }
+    }
+    if (lead && in_range && !fix) {
       S nh = wl[0], nq = wl[1], nz = wl[2];
       if (!done) {
         R iq = -nu * (dm[1] + dl[1]);
@@ -693,6 +731,105 @@ __global__ void __launch_bounds__(B, MinBlocks<B, CAP>::value)
     atomicMax(&ctl->s[(slot + 1) % 3].rho_bits, Prec<R>::bits(rho_run));
   if (flags) atomicOr(&ctl->status, flags);
 }
+
+// The cells the float32 warp-tile step left (an edge of theirs needs the
+// float64 redo): each is recomputed from the step's input state, both of its
+// edges evaluated by edge_fluct (float32 nodes, or the whole edge in float64
+// when flagged) with the step's nu, and written; its CFL radius goes into the
+// next slot. Spread over the grid, the float64 edges no longer queue up in the
+// warps whose ranges cross a near-critical region. The last block to finish
+// puts the list's counters back to 0 for the next step.
+template <int LAW, bool EXT>
+__global__ void __launch_bounds__(256) k_fixup(const StepParams p, const StateF32 in, const StateF32 out,
+                                               const int slot) {
+  __shared__ float sRed[8];
+  Ctl* ctl = p.ctl;
+  const unsigned count = ctl->fix_count;
+  // nothing listed (the usual step): the counters are already 0. Otherwise every
+  // block reads the same count, since the reset below waits for all of them.
+  if (count == 0u) return;
+  // nu and done exactly as warp_step_size forms them
+  const CtlSlot cs = ctl->s[slot];
+  const double t_end = ctl->t_end;
+  const bool done = !(cs.t < t_end);
+  double dt = p.cfl * p.dx / Prec<float>::from_bits(cs.rho_bits);
+  if (cs.t + dt >= t_end) dt = t_end - cs.t;
+  const float nu = done ? 0.0f : (float)(dt / p.dx);
+  unsigned flags = 0;
+  float rho_run = 0.0f;
+  // two lanes per listed cell: the even lane evaluates the cell's left edge,
+  // the odd lane its right edge (so a cell waits for one float64 edge, not
+  // two), and the even lane updates the cell; the loop is warp-uniform
+  // warp w of block b takes the 16 cells of slot w G + b (G blocks), so that
+  // neighbouring slots, and their float64 edges, run on different SMs
+  const int lane = threadIdx.x & 31;
+  const unsigned long long n2 = done ? 0ull : 2ull * count;
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  const unsigned long long slot0 = (unsigned long long)(threadIdx.x >> 5) * gridDim.x + blockIdx.x;
+  for (unsigned long long t0 = slot0 * 32ull; t0 < n2; t0 += stride) {
+    const unsigned long long t = t0 + lane;
+    const bool active = t < n2;
+    const int side = lane & 1;
+    int64_t i = 0;
+    float2 wa[3], wb[3];
+    float dm[3] = {0.0f, 0.0f, 0.0f}, dp[3] = {0.0f, 0.0f, 0.0f};
+    if (active) {
+      i = p.fix_list[t >> 1];
+      const int64_t e = i + side;  // left edge i (cells i - 1 | i) or right edge i + 1 (cells i | i + 1)
+      load_edge<float, EXT>(p, in, e, slot, wa, wb);
+      edge_fluct<float, LAW>(p, wa, wb, dm, dp, flags);
+      if constexpr (EXT) feed_edge<float, LAW>(p, e, wa, wb, dm, dp);
+    }
+    // D- of the right edge to the even lane
+    float dmR[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) dmR[r] = __shfl_xor_sync(0xffffffffu, dm[r], 1);
+    if (active && side == 0) {
+      // the step kernel's update of cell i: state wb (the left edge's right cell),
+      // D+ of the left edge (dp) and D- of the right edge (dmR)
+      float iq = -nu * (dmR[1] + dp[1]);
+      if constexpr (EXT)
+        if (p.fric != 0.0) iq += friction_dt<float>(p, nu * float(p.dx), wb[0].x, wb[1].x);
+      const float2 nh = Prec<float>::add(wb[0], -nu * (dmR[0] + dp[0]));
+      const float2 nq = Prec<float>::add(wb[1], iq);
+      const float2 nz = Prec<float>::add(wb[2], -nu * (dmR[2] + dp[2]));
+      out.h[i] = nh;
+      out.q[i] = nq;
+      out.z[i] = nz;
+      const float hh = nh.x;
+      if (!(hh > 0.0f)) flags |= ST_DEPTH;
+      if (!(Prec<float>::finite(nh) && Prec<float>::finite(nq) && Prec<float>::finite(nz))) {
+        flags |= ST_NONFINITE;
+      } else if (hh > 0.0f) {
+        float r = Prec<float>::template rho<LAW>(p, hh, nq.x);
+        if (!(r <= 3.0e38f)) {
+          flags |= ST_NONFINITE;
+          r = 0.0f;
+        }
+        rho_run = d_max(rho_run, r);
+      }
+    }
+  }
+  rho_run = warp_max(rho_run);
+  if ((threadIdx.x & 31) == 0) sRed[threadIdx.x >> 5] = rho_run;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    float r = (threadIdx.x < 8) ? sRed[threadIdx.x] : 0.0f;
+    r = warp_max(r);
+    if (threadIdx.x == 0 && r > 0.0f) atomicMax(&ctl->s[(slot + 1) % 3].rho_bits, Prec<float>::bits(r));
+  }
+  if (flags) atomicOr(&ctl->status, flags);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&ctl->fix_done, 1u) == gridDim.x - 1) {
+      ctl->fix_count = 0u;
+      ctl->fix_done = 0u;
+      __threadfence();
+    }
+  }
+}
+constexpr unsigned kFixupBlocks = 304;
 
 // CFL maximum and admissibility of a state (grid-stride).
 template <typename R, int LAW>
@@ -750,23 +887,31 @@ cudaError_t launch_step_law(const StepParams& p, StepVariant v, typename Prec<R>
     const int64_t wpb = v.block / 32;
     int64_t gg = (tiles + wpb - 1) / wpb;
     if (gg > sms * per_sm) gg = sms * per_sm;
+    // float32: the deferred form (flagged cells listed for k_fixup, launched
+    // right after); float64 evaluates every edge in place
+    constexpr bool kDefer = std::is_same<R, float>::value;
+    if (kDefer && p.fix_list == nullptr) return cudaErrorInvalidValue;
+    cudaError_t e = cudaErrorInvalidValue;
     if (v.block == 256 && v.reg_cap == 64) {
-      k_step_warp<R, LAW, 256, 64, EXT><<<(unsigned)gg, 256, 0, s>>>(p, in, out, slot);
-      return cudaGetLastError();
+      k_step_warp<R, LAW, 256, 64, EXT, 0, kDefer><<<(unsigned)gg, 256, 0, s>>>(p, in, out, slot);
+      e = cudaGetLastError();
+    } else if (v.block == 128 && v.reg_cap == 64) {
+      k_step_warp<R, LAW, 128, 64, EXT, 0, kDefer><<<(unsigned)gg, 128, 0, s>>>(p, in, out, slot);
+      e = cudaGetLastError();
+    } else if (v.block == 128 && v.reg_cap == 72) {
+      k_step_warp<R, LAW, 128, 72, EXT, 0, kDefer><<<(unsigned)gg, 128, 0, s>>>(p, in, out, slot);
+      e = cudaGetLastError();
+    } else if (v.block == 256 && v.reg_cap == 80) {
+      k_step_warp<R, LAW, 256, 80, EXT, 0, kDefer><<<(unsigned)gg, 256, 0, s>>>(p, in, out, slot);
+      e = cudaGetLastError();
     }
-    if (v.block == 128 && v.reg_cap == 64) {
-      k_step_warp<R, LAW, 128, 64, EXT><<<(unsigned)gg, 128, 0, s>>>(p, in, out, slot);
-      return cudaGetLastError();
+    if constexpr (kDefer) {
+      if (e == cudaSuccess) {
+        k_fixup<LAW, EXT><<<kFixupBlocks, 256, 0, s>>>(p, in, out, slot);
+        e = cudaGetLastError();
+      }
     }
-    if (v.block == 128 && v.reg_cap == 72) {
-      k_step_warp<R, LAW, 128, 72, EXT><<<(unsigned)gg, 128, 0, s>>>(p, in, out, slot);
-      return cudaGetLastError();
-    }
-    if (v.block == 256 && v.reg_cap == 80) {
-      k_step_warp<R, LAW, 256, 80, EXT><<<(unsigned)gg, 256, 0, s>>>(p, in, out, slot);
-      return cudaGetLastError();
-    }
-    return cudaErrorInvalidValue;
+    return e;
   }
 #define ADOT_STEP_CASE(BB, CC)                                       \
   if (v.block == BB && v.reg_cap == CC) {                            \
