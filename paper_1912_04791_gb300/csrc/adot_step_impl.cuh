@@ -20,6 +20,7 @@
 
 #include <float.h>
 
+#include <algorithm>
 #include <type_traits>
 
 #include "adot_internal.h"
@@ -534,6 +535,26 @@ __device__ __forceinline__ void warp_step_size(const StepParams& p, int slot, in
 #define ADOT_POOL_CHUNKS 2
 #endif
 
+// The split of a warp-tile launch, the same for every warp: cells per static
+// range, the cells [0, n_s) the static ranges cover, and the pool's groups.
+// Formed on the host per launch: the kernel formed it with three 64-bit
+// divisions at every pool group (5.50 -> 5.58e10 cell-updates/s at 1e7 cells
+// when they left the kernel).
+struct WarpSplit {
+  int64_t cs, n_s, n_groups;
+};
+
+inline WarpSplit warp_split(int64_t n, int64_t nwarps) {
+  WarpSplit w;
+  int64_t ks = (((n + 31) / 32) * ADOT_STATIC_EIGHTHS / 8) / nwarps;
+  if (ks < 2) ks = 0;
+  w.cs = 32 * ks - 1;
+  w.n_s = ks ? std::min<int64_t>(nwarps, n / w.cs) * w.cs : 0;
+  constexpr int64_t kGroup = 32 * ADOT_POOL_CHUNKS - 1;
+  w.n_groups = (n - w.n_s + kGroup - 1) / kGroup;
+  return w;
+}
+
 // Persistent warp-tile variant of the time step. A warp processes ranges of
 // consecutive edges in chunks of 32 (one per lane): the edge of lane l in
 // chunk j of a range starting at edge E is E + 32 j + l, and the lane updates
@@ -564,7 +585,7 @@ __device__ __forceinline__ void warp_step_size(const StepParams& p, int slot, in
 template <typename R, int LAW, int B, int CAP, bool EXT = false, int SCHEME = 0, bool DEFER = false>
 __global__ void __launch_bounds__(B, MinBlocks<B, CAP>::value)
     k_step_warp(const StepParams p, const typename Prec<R>::State in,
-                const typename Prec<R>::State out, const int slot) {
+                const typename Prec<R>::State out, const int slot, const WarpSplit ws) {
   using S = typename Prec<R>::S;
   const int lane = threadIdx.x & 31;
   const int64_t gw = ((int64_t)blockIdx.x * B + threadIdx.x) >> 5;
@@ -592,13 +613,8 @@ __global__ void __launch_bounds__(B, MinBlocks<B, CAP>::value)
   unsigned flags = 0;
   R rho_run = R(0);
   bool carry_rd = false;  // DEFER: lane 0's flag of the previous chunk's last edge
-  // the split: static ranges of cs cells over cells [0, n_s), then pool groups
-  auto static_split = [&](int64_t& cs, int64_t& n_s) {
-    int64_t ks = (((n + 31) / 32) * ADOT_STATIC_EIGHTHS / 8) / nwarps;
-    if (ks < 2) ks = 0;
-    cs = 32 * ks - 1;                                // cells per static range
-    n_s = ks ? d_min_i64(nwarps, n / cs) * cs : 0;    // cells [0, n_s)
-  };
+  // the split (warp_split): static ranges of ws.cs cells over cells [0, ws.n_s),
+  // then ws.n_groups pool groups
   constexpr int64_t kGroup = 32 * ADOT_POOL_CHUNKS - 1;  // cells per pool group
   // current range: next chunk's first edge eb, rem = edges after it (< 2^31;
   // negative when the range is finished)
@@ -608,29 +624,24 @@ __global__ void __launch_bounds__(B, MinBlocks<B, CAP>::value)
     // range ri = w G + b for warp w of block b (G blocks): consecutive ranges
     // belong to different blocks, so to different SMs, and a run of expensive
     // cells (edges redone in float64 near critical flow) is spread over the GPU
-    int64_t cs, n_s;
-    static_split(cs, n_s);
     const int64_t ri = (int64_t)(threadIdx.x >> 5) * gridDim.x + blockIdx.x;
-    if ((ri + 1) * cs <= n_s) {
-      eb = ri * cs;
-      rem = (int)cs;
+    if ((ri + 1) * ws.cs <= ws.n_s) {
+      eb = ri * ws.cs;
+      rem = (int)ws.cs;
     }
   }
   bool lead = lane >= 1;  // the lane's cell is in the range (all lanes after the first chunk)
   for (;;) {
     if (rem < 0) {
       // next range from the pool
-      int64_t cs, n_s;
-      static_split(cs, n_s);
-      const int64_t n_groups = (n - n_s + kGroup - 1) / kGroup;
       const int64_t g = (int64_t)__shfl_sync(0xffffffffu, ticket, 0);
-      if (g >= n_groups) {
+      if (g >= ws.n_groups) {
         // the launch's last ticket: every other request has been served
-        if (lane == 0 && g == n_groups + nwarps - 1) atomicExch(&ctl->grab, 0u);
+        if (lane == 0 && g == ws.n_groups + nwarps - 1) atomicExch(&ctl->grab, 0u);
         break;
       }
       if (lane == 0) ticket = atomicAdd(&ctl->grab, 1u);
-      eb = n_s + g * kGroup;
+      eb = ws.n_s + g * kGroup;
       rem = (int)d_min_i64(kGroup, n - eb);
       lead = lane >= 1;
     }
@@ -640,6 +651,8 @@ __global__ void __launch_bounds__(B, MinBlocks<B, CAP>::value)
       // the range's next chunk into L2 while this one is computed
       const int64_t cn = e + 31;
       if (rem >= 32 && cn < n) {
+        // (into L1 instead, or also the next pool group's first chunk at a
+        // range's last one: no gain, or 0.5 % and 2 % (PRICE-C) slower at 1e7 cells)
         asm volatile("prefetch.global.L2 [%0];" ::"l"(in.h + cn));
         asm volatile("prefetch.global.L2 [%0];" ::"l"(in.q + cn));
         asm volatile("prefetch.global.L2 [%0];" ::"l"(in.z + cn));
@@ -891,18 +904,19 @@ cudaError_t launch_step_law(const StepParams& p, StepVariant v, typename Prec<R>
     // right after); float64 evaluates every edge in place
     constexpr bool kDefer = std::is_same<R, float>::value;
     if (kDefer && p.fix_list == nullptr) return cudaErrorInvalidValue;
+    const WarpSplit ws = warp_split(p.n, gg * (v.block / 32));
     cudaError_t e = cudaErrorInvalidValue;
     if (v.block == 256 && v.reg_cap == 64) {
-      k_step_warp<R, LAW, 256, 64, EXT, 0, kDefer><<<(unsigned)gg, 256, 0, s>>>(p, in, out, slot);
+      k_step_warp<R, LAW, 256, 64, EXT, 0, kDefer><<<(unsigned)gg, 256, 0, s>>>(p, in, out, slot, ws);
       e = cudaGetLastError();
     } else if (v.block == 128 && v.reg_cap == 64) {
-      k_step_warp<R, LAW, 128, 64, EXT, 0, kDefer><<<(unsigned)gg, 128, 0, s>>>(p, in, out, slot);
+      k_step_warp<R, LAW, 128, 64, EXT, 0, kDefer><<<(unsigned)gg, 128, 0, s>>>(p, in, out, slot, ws);
       e = cudaGetLastError();
     } else if (v.block == 128 && v.reg_cap == 72) {
-      k_step_warp<R, LAW, 128, 72, EXT, 0, kDefer><<<(unsigned)gg, 128, 0, s>>>(p, in, out, slot);
+      k_step_warp<R, LAW, 128, 72, EXT, 0, kDefer><<<(unsigned)gg, 128, 0, s>>>(p, in, out, slot, ws);
       e = cudaGetLastError();
     } else if (v.block == 256 && v.reg_cap == 80) {
-      k_step_warp<R, LAW, 256, 80, EXT, 0, kDefer><<<(unsigned)gg, 256, 0, s>>>(p, in, out, slot);
+      k_step_warp<R, LAW, 256, 80, EXT, 0, kDefer><<<(unsigned)gg, 256, 0, s>>>(p, in, out, slot, ws);
       e = cudaGetLastError();
     }
     if constexpr (kDefer) {
