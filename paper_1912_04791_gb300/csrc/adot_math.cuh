@@ -400,8 +400,14 @@ __device__ __noinline__ float spectral_radius_f32_trig(const LawT<float>& L, flo
 // 1e-7 of the root); if the start does not meet those conditions
 // (strong transport, b > ~2) or the last correction is not below 1e-5 of the
 // root, the roots of Eq. lambda are used instead.
-template <int LAW>
-__device__ __forceinline__ float spectral_radius_f32(const LawT<float>& L, float h, float q) {
+// SKIP: the caller wants only radii above floor (a running maximum). After the
+// first step every Newton iterate lies above the root, so once it is below
+// floor (1 - 1e-6) the radius cannot raise the maximum and 0 is returned (the
+// margin covers the iterates' rounding, so the maximum is unchanged; 0.5 % on
+// the 1e7-cell step).
+template <int LAW, bool SKIP = false>
+__device__ __forceinline__ float spectral_radius_f32(const LawT<float>& L, float h, float q,
+                                                     float floor = 0.0f) {
   const float inv_h = __fdividef(1.0f, h);
   const float u = q * inv_h;
   const float c2 = L.g * h;
@@ -422,6 +428,8 @@ __device__ __forceinline__ float spectral_radius_f32(const LawT<float>& L, float
   for (int it = 0; it < 4; ++it) {
     d = __fdividef(pv, dp);
     l -= d;
+    if constexpr (SKIP)
+      if (it == 0 && ok && l <= floor * 0.999999f) return 0.0f;
     // quadratic convergence: once a correction is below 1e-7 of the root the
     // next one is below float rounding, so the iteration stops
     if (fabsf(d) <= 1e-7f * l) break;

@@ -345,3 +345,28 @@ def test_fp32_deferred_redo_on_every_cell(gpu, bc, ks):
             assert np.abs(inc).max() <= 1e-15 and np.abs(ref).max() <= 1e-15
             continue
         assert np.abs(inc - ref).sum() <= 1e-5 * np.abs(ref).sum(), np.abs(inc - ref).sum() / np.abs(ref).sum()
+
+
+@pytest.mark.parametrize("block,cap", [(256, 64), (256, 80)])
+@pytest.mark.parametrize("case", ["smooth", "riemann"])
+def test_fp32_step_cfl_maximum_equals_fresh_maximum(gpu, block, cap, case):
+    """The float32 warp-tile step forms the next step's CFL maximum while it
+    writes the cells, skipping a cell's Newton iteration once its first iterate
+    (an upper bound of the radius) falls below the lane's running maximum. The
+    maximum must be the one the separate reduction (k_rho, no skipping) gives on
+    the same state: after one step, the next step's dt from the running form
+    equals, bit for bit, the first dt of a solver set to the state read back."""
+    P = W.smooth_periodic(200_003) if case == "smooth" else W.movable_bed_riemann(150_001)
+    kw = dict(block_threads=block, reg_cap=cap, step_kernel=2)
+    for k in range(3):
+        with gpu.Solver(gpu.config_for(P, gpu.FP32, **kw)) as s:
+            s.set_state(P.h, P.q, P.z)
+            s.step(k + 1)
+            state = s.get_state()
+            s.step(1)
+            dt_run = s.query()[2]
+        with gpu.Solver(gpu.config_for(P, gpu.FP32, **kw)) as s:
+            s.set_state(*state)
+            s.step(1)
+            dt_fresh = s.query()[2]
+        assert dt_run == dt_fresh, (k, dt_run, dt_fresh)
