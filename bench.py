@@ -40,16 +40,17 @@ UNIT = "cell-updates/s"
 #  xu:    XU-pipe thread instructions per cell-update (sm__inst_executed_pipe_xu x 32 / cells);
 #  dram:  dram__bytes_read.sum + dram__bytes_write.sum per cell-update.
 KERNEL_COUNTS = {
-    # static ranges over 6/8 of the chunks (assigned across blocks) plus the 63-cell work
-    # pool: at 4e6 cells and 3648 warps, 4,020,875 edges evaluated for 4,000,001 (20,874
-    # evaluated twice, removed); arccos(x)/3 by the library's polynomial form; float64 redo
-    # deferred to k_fixup (which the smooth workload never calls)
-    ("warp", 256, 80): {"flops": (2 * 466.011296e6 + 345.064625e6 + 559.188189e6) / 4e6
+    # static ranges over 6/8 of the chunks (assigned across blocks, the split formed on the
+    # host) plus the 63-cell work pool: at 4e6 cells and 3648 warps, 4,020,875 edges
+    # evaluated for 4,000,001 (20,874 evaluated twice, removed); arccos(x)/3 by the library's
+    # polynomial form; float64 redo deferred to k_fixup (which the smooth workload never
+    # calls); CFL Newton steps skipped below the lane's running maximum
+    ("warp", 256, 80): {"flops": (2 * 445.41752e6 + 334.767737e6 + 547.742857e6) / 4e6
                         * (1 - 20874 / 4e6),
-                        "instr": 70.868425e6 * 32 / 4e6, "xu": 3.672718e6 * 32 / 4e6,
-                        "dram": (97.702656e6 + 51.950336e6) / 4e6},
-    ("warp", 256, 64): {"flops": None, "instr": 71.450227e6 * 32 / 4e6, "xu": 3.68668e6 * 32 / 4e6,
-                        "dram": (98.028544e6 + 51.718144e6) / 4e6},
+                        "instr": 66.955724e6 * 32 / 4e6, "xu": 3.351343e6 * 32 / 4e6,
+                        "dram": (97.698304e6 + 51.847424e6) / 4e6},
+    ("warp", 256, 64): {"flops": None, "instr": 67.514271e6 * 32 / 4e6, "xu": 3.36922e6 * 32 / 4e6,
+                        "dram": (98.000640e6 + 51.617024e6) / 4e6},
     ("order2", 256, 64): {"flops": None, "instr": None, "xu": None, "dram": None},
 }
 # The block kernel's all-scalar count (1 edge in 256 evaluated twice, removed).
