@@ -1734,26 +1734,39 @@ __global__ void __launch_bounds__(kTpThreads, 1)
         const uint32_t t_row = tmem + (uint32_t)(sl * kTcRows) + ((uint32_t)(quad * 32) << 16);
         if (l < kLayers - 1) {
           unsigned char* act = sm + kTpActOff + sl * kTcActBytes;
-#pragma unroll 1
-          for (int cb = 0; cb < 2; ++cb) {
-            const int c = half * 64 + cb * 32;
-            uint32_t r[32];
-            tmem_ld_x32(t_row + (uint32_t)c, r);
-            tmem_wait_ld(r);
+          // the warp's 64 columns in four 16-column blocks: the tensor-memory
+          // load of the next block is in flight while the current one is
+          // computed (two register buffers, used in turn)
+          auto emit = [&](const uint32_t r[16], int cb) {
+            const int c = half * 64 + cb * 16;
             const float* b = sBias + b_offset(l) + c;
-            uint32_t pk[16];
+            uint32_t pk[8];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
+            for (int j = 0; j < 4; ++j) {
               const float4 bb = *reinterpret_cast<const float4*>(b + 4 * j);
               pk[2 * j] = gelu2x_bf16(r[4 * j], r[4 * j + 1], __float_as_uint(bb.x), __float_as_uint(bb.y), c1, c0);
               pk[2 * j + 1] =
                   gelu2x_bf16(r[4 * j + 2], r[4 * j + 3], __float_as_uint(bb.z), __float_as_uint(bb.w), c1, c0);
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
+            for (int u = 0; u < 2; ++u)
               *reinterpret_cast<uint4*>(act + tc_canon(row, c / 8 + u, kHid)) =
                   make_uint4(pk[4 * u], pk[4 * u + 1], pk[4 * u + 2], pk[4 * u + 3]);
-          }
+          };
+          const uint32_t tc0 = t_row + (uint32_t)(half * 64);
+          uint32_t ra[16], rb[16];
+          tmem_ld_x16(tc0, ra);
+          tmem_wait_ld16(ra);
+          tmem_ld_x16(tc0 + 16u, rb);
+          emit(ra, 0);
+          tmem_wait_ld16(rb);
+          tmem_ld_x16(tc0 + 32u, ra);
+          emit(rb, 1);
+          tmem_wait_ld16(ra);
+          tmem_ld_x16(tc0 + 48u, rb);
+          emit(ra, 2);
+          tmem_wait_ld16(rb);
+          emit(rb, 3);
           fence_async_smem();
         } else if (half == 0) {
           uint32_t r[16];
