@@ -194,7 +194,11 @@ __global__ void __launch_bounds__(B, MinBlocks<B, CAP>::value)
         if (!(Prec<R>::finite(nh) && Prec<R>::finite(nq) && Prec<R>::finite(nz))) {
           flags |= ST_NONFINITE;
         } else if (hh > R(0)) {
-          R r = Prec<R>::template rho<LAW>(p, hh, Prec<R>::hi(nq));
+          R r;
+          if constexpr (std::is_same<R, float>::value)
+            r = spectral_radius_f32<LAW, true>(p.lf, hh, Prec<R>::hi(nq), rho_run);  // 0: below rho_run
+          else
+            r = Prec<R>::template rho<LAW>(p, hh, Prec<R>::hi(nq));
           if (!(r <= R(3.0e38))) {
             flags |= ST_NONFINITE;
             r = R(0);

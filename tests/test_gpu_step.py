@@ -347,17 +347,18 @@ def test_fp32_deferred_redo_on_every_cell(gpu, bc, ks):
         assert np.abs(inc - ref).sum() <= 1e-5 * np.abs(ref).sum(), np.abs(inc - ref).sum() / np.abs(ref).sum()
 
 
-@pytest.mark.parametrize("block,cap", [(256, 64), (256, 80)])
+@pytest.mark.parametrize("block,cap,order", [(256, 64, 1), (256, 80, 1), (256, 80, 2)])
 @pytest.mark.parametrize("case", ["smooth", "riemann"])
-def test_fp32_step_cfl_maximum_equals_fresh_maximum(gpu, block, cap, case):
-    """The float32 warp-tile step forms the next step's CFL maximum while it
-    writes the cells, skipping a cell's Newton iteration once its first iterate
-    (an upper bound of the radius) falls below the lane's running maximum. The
-    maximum must be the one the separate reduction (k_rho, no skipping) gives on
-    the same state: after one step, the next step's dt from the running form
-    equals, bit for bit, the first dt of a solver set to the state read back."""
+def test_fp32_step_cfl_maximum_equals_fresh_maximum(gpu, block, cap, order, case):
+    """The float32 warp-tile steps (first order, and the second-order
+    variant) form the next step's CFL maximum while they write the cells,
+    skipping a cell's Newton iteration once its first iterate (an upper bound of
+    the radius) falls below the lane's running maximum. The maximum must be the
+    one the separate reduction (k_rho, no skipping) gives on the same state:
+    after one step, the next step's dt from the running form equals, bit for
+    bit, the first dt of a solver set to the state read back."""
     P = W.smooth_periodic(200_003) if case == "smooth" else W.movable_bed_riemann(150_001)
-    kw = dict(block_threads=block, reg_cap=cap, step_kernel=2)
+    kw = dict(block_threads=block, reg_cap=cap, step_kernel=2, order=order)
     for k in range(3):
         with gpu.Solver(gpu.config_for(P, gpu.FP32, **kw)) as s:
             s.set_state(P.h, P.q, P.z)
