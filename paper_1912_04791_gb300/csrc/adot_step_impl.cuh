@@ -535,6 +535,42 @@ __device__ __forceinline__ void warp_step_size(const StepParams& p, int slot, in
 #define ADOT_POOL_CHUNKS 2
 #endif
 
+// Programmatic dependent launch: the float32 warp-tile step and k_fixup are
+// launched with programmatic stream serialisation, so that each can be
+// scheduled while the kernel before it drains. griddep_wait() blocks until the
+// kernel before has completed and its writes are visible (a no-op for a normal
+// launch), and comes before a kernel's first read of the control block or the
+// state; griddep_launch() lets the next kernel be scheduled.
+#ifndef ADOT_PDL
+#define ADOT_PDL 1
+#endif
+__device__ __forceinline__ void griddep_wait() {
+#if ADOT_PDL
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+#endif
+}
+__device__ __forceinline__ void griddep_launch() {
+#if ADOT_PDL
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+#endif
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), unsigned grid, unsigned block, cudaStream_t s,
+                       Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = ADOT_PDL;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // The split of a warp-tile launch, the same for every warp: cells per static
 // range, the cells [0, n_s) the static ranges cover, and the pool's groups.
 // Formed on the host per launch: the kernel formed it with three 64-bit
@@ -593,6 +629,7 @@ __global__ void __launch_bounds__(B, MinBlocks<B, CAP>::value)
   const int64_t n = p.n;
   Ctl* ctl = p.ctl;
 
+  griddep_wait();  // the previous kernel's state, control slot and counters
   // first pool ticket, asked for before anything else (used after the static range)
   unsigned ticket = 0u;
   if (lane == 0) ticket = atomicAdd(&ctl->grab, 1u);
@@ -743,6 +780,7 @@ __global__ void __launch_bounds__(B, MinBlocks<B, CAP>::value)
     eb += 32;
     rem -= 32;
   }
+  griddep_launch();  // k_fixup may be scheduled (it waits for this grid to complete)
   rho_run = warp_max(rho_run);
   if (lane == 0 && !done && rho_run > R(0))
     atomicMax(&ctl->s[(slot + 1) % 3].rho_bits, Prec<R>::bits(rho_run));
@@ -761,6 +799,8 @@ __global__ void __launch_bounds__(256) k_fixup(const StepParams p, const StateF3
                                                const int slot) {
   __shared__ float sRed[8];
   Ctl* ctl = p.ctl;
+  griddep_wait();    // the step kernel has completed: its list and counters are visible
+  griddep_launch();  // the next step may be scheduled (it waits for this grid to complete)
   const unsigned count = ctl->fix_count;
   // nothing listed (the usual step): the counters are already 0. Otherwise every
   // block reads the same count, since the reset below waits for all of them.
@@ -911,22 +951,17 @@ cudaError_t launch_step_law(const StepParams& p, StepVariant v, typename Prec<R>
     const WarpSplit ws = warp_split(p.n, gg * (v.block / 32));
     cudaError_t e = cudaErrorInvalidValue;
     if (v.block == 256 && v.reg_cap == 64) {
-      k_step_warp<R, LAW, 256, 64, EXT, 0, kDefer><<<(unsigned)gg, 256, 0, s>>>(p, in, out, slot, ws);
-      e = cudaGetLastError();
+      e = launch_pdl(k_step_warp<R, LAW, 256, 64, EXT, 0, kDefer>, (unsigned)gg, 256u, s, p, in, out, slot, ws);
     } else if (v.block == 128 && v.reg_cap == 64) {
-      k_step_warp<R, LAW, 128, 64, EXT, 0, kDefer><<<(unsigned)gg, 128, 0, s>>>(p, in, out, slot, ws);
-      e = cudaGetLastError();
+      e = launch_pdl(k_step_warp<R, LAW, 128, 64, EXT, 0, kDefer>, (unsigned)gg, 128u, s, p, in, out, slot, ws);
     } else if (v.block == 128 && v.reg_cap == 72) {
-      k_step_warp<R, LAW, 128, 72, EXT, 0, kDefer><<<(unsigned)gg, 128, 0, s>>>(p, in, out, slot, ws);
-      e = cudaGetLastError();
+      e = launch_pdl(k_step_warp<R, LAW, 128, 72, EXT, 0, kDefer>, (unsigned)gg, 128u, s, p, in, out, slot, ws);
     } else if (v.block == 256 && v.reg_cap == 80) {
-      k_step_warp<R, LAW, 256, 80, EXT, 0, kDefer><<<(unsigned)gg, 256, 0, s>>>(p, in, out, slot, ws);
-      e = cudaGetLastError();
+      e = launch_pdl(k_step_warp<R, LAW, 256, 80, EXT, 0, kDefer>, (unsigned)gg, 256u, s, p, in, out, slot, ws);
     }
     if constexpr (kDefer) {
       if (e == cudaSuccess) {
-        k_fixup<LAW, EXT><<<kFixupBlocks, 256, 0, s>>>(p, in, out, slot);
-        e = cudaGetLastError();
+        e = launch_pdl(k_fixup<LAW, EXT>, kFixupBlocks, 256u, s, p, in, out, slot);
       }
     }
     return e;
