@@ -814,34 +814,73 @@ __global__ void __launch_bounds__(256) k_fixup(const StepParams p, const StateF3
   const float nu = done ? 0.0f : (float)(dt / p.dx);
   unsigned flags = 0;
   float rho_run = 0.0f;
-  // two lanes per listed cell: the even lane evaluates the cell's left edge,
-  // the odd lane its right edge (so a cell waits for one float64 edge, not
-  // two), and the even lane updates the cell; the loop is warp-uniform
-  // warp w of block b takes the 16 cells of slot w G + b (G blocks), so that
-  // neighbouring slots, and their float64 edges, run on different SMs
+  // six lanes per listed cell (five cells per warp, lanes 30 and 31 idle): lane
+  // 6 c + 3 side + k takes edge i + side of cell c (the left edge i, or the right
+  // edge i + 1) and Gauss-Legendre node k. The three lanes of an edge each
+  // evaluate its float32 nodes; when the edge needs the float64 redo, each
+  // evaluates its own node in float64 and the first gathers the three (the
+  // accumulation of edge_fluct_f64_redo, in the same order), so a cell waits
+  // for one float64 node, not an edge's three in turn. Lane 6 c updates the
+  // cell. The loop is warp-uniform; warp w of block b takes the cells of slot
+  // w G + b (G blocks), so neighbouring slots run on different SMs.
   const int lane = threadIdx.x & 31;
-  const unsigned long long n2 = done ? 0ull : 2ull * count;
-  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  const int cl = lane / 6, side = (lane % 6) / 3, k = lane % 3;
+  const unsigned long long n_c = done ? 0ull : (unsigned long long)count;
+  const unsigned long long stride = (unsigned long long)gridDim.x * (blockDim.x >> 5) * 5ull;
   const unsigned long long slot0 = (unsigned long long)(threadIdx.x >> 5) * gridDim.x + blockIdx.x;
-  for (unsigned long long t0 = slot0 * 32ull; t0 < n2; t0 += stride) {
-    const unsigned long long t = t0 + lane;
-    const bool active = t < n2;
-    const int side = lane & 1;
+  for (unsigned long long c0 = slot0 * 5ull; c0 < n_c; c0 += stride) {
+    const unsigned long long c = c0 + (unsigned long long)cl;
+    const bool active = lane < 30 && c < n_c;
     int64_t i = 0;
     float2 wa[3], wb[3];
     float dm[3] = {0.0f, 0.0f, 0.0f}, dp[3] = {0.0f, 0.0f, 0.0f};
+    bool rd = false;
+    int64_t e = 0;
     if (active) {
-      i = p.fix_list[t >> 1];
-      const int64_t e = i + side;  // left edge i (cells i - 1 | i) or right edge i + 1 (cells i | i + 1)
+      i = p.fix_list[c];
+      e = i + side;  // left edge i (cells i - 1 | i) or right edge i + 1 (cells i | i + 1)
       load_edge<float, EXT>(p, in, e, slot, wa, wb);
-      edge_fluct<float, LAW>(p, wa, wb, dm, dp, flags);
-      if constexpr (EXT) feed_edge<float, LAW>(p, e, wa, wb, dm, dp);
+      rd = edge_fluct_deferred<LAW>(p, wa, wb, dm, dp);
     }
-    // D- of the right edge to the even lane
+    if (__any_sync(0xffffffffu, rd)) {
+      double y[3] = {0.0, 0.0, 0.0}, x[3] = {0.0, 0.0, 0.0};
+      if (rd) {
+        const double hl = ff_to_double(wa[0]), ql = ff_to_double(wa[1]), zl = ff_to_double(wa[2]);
+        const double dh = ff_to_double(wb[0]) - hl, dq = ff_to_double(wb[1]) - ql,
+                     dz = ff_to_double(wb[2]) - zl;
+        const double sk = (k == 0) ? GL3_S0 : ((k == 1) ? 0.5 : GL3_S2);
+        node_f64<LAW>(p.ld, hl + sk * dh, ql + sk * dq, dh, dq, dz, y, x, flags);
+      }
+      double y1[3], y2[3], x1[3], x2[3];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        y1[r] = __shfl_down_sync(0xffffffffu, y[r], 1);
+        y2[r] = __shfl_down_sync(0xffffffffu, y[r], 2);
+        x1[r] = __shfl_down_sync(0xffffffffu, x[r], 1);
+        x2[r] = __shfl_down_sync(0xffffffffu, x[r], 2);
+      }
+      if (rd && k == 0) {
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          double ya = 0.0, xa = 0.0;
+          ya += GL3_W0 * y[r];
+          xa += GL3_W0 * x[r];
+          ya += GL3_W1 * y1[r];
+          xa += GL3_W1 * x1[r];
+          ya += GL3_W0 * y2[r];
+          xa += GL3_W0 * x2[r];
+          dm[r] = (float)(0.5 * (ya - xa));
+          dp[r] = (float)(0.5 * (ya + xa));
+        }
+      }
+    }
+    if constexpr (EXT)
+      if (active) feed_edge<float, LAW>(p, e, wa, wb, dm, dp);
+    // D- of the right edge (lane 6 c + 3) to the cell's lane 6 c
     float dmR[3];
 #pragma unroll
-    for (int r = 0; r < 3; ++r) dmR[r] = __shfl_xor_sync(0xffffffffu, dm[r], 1);
-    if (active && side == 0) {
+    for (int r = 0; r < 3; ++r) dmR[r] = __shfl_down_sync(0xffffffffu, dm[r], 3);
+    if (active && side == 0 && k == 0) {
       // the step kernel's update of cell i: state wb (the left edge's right cell),
       // D+ of the left edge (dp) and D- of the right edge (dmR)
       float iq = -nu * (dmR[1] + dp[1]);
