@@ -789,11 +789,12 @@ __global__ void __launch_bounds__(B, MinBlocks<B, CAP>::value)
 
 // The cells the float32 warp-tile step left (an edge of theirs needs the
 // float64 redo): each is recomputed from the step's input state, both of its
-// edges evaluated by edge_fluct (float32 nodes, or the whole edge in float64
-// when flagged) with the step's nu, and written; its CFL radius goes into the
-// next slot. Spread over the grid, the float64 edges no longer queue up in the
-// warps whose ranges cross a near-critical region. The last block to finish
-// puts the list's counters back to 0 for the next step.
+// edges evaluated as the step evaluates an edge (float32 nodes, or, when
+// flagged, the three nodes in float64 as edge_fluct_f64_redo forms them) with
+// the step's nu, and written; its CFL radius goes into the next slot. Spread
+// over the grid and over one lane per node, the float64 work no longer queues
+// up in the warps whose ranges cross a near-critical region. The last block to
+// finish puts the list's counters back to 0 for the next step.
 template <int LAW, bool EXT>
 __global__ void __launch_bounds__(256) k_fixup(const StepParams p, const StateF32 in, const StateF32 out,
                                                const int slot) {
