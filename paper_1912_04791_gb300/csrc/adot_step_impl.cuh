@@ -521,19 +521,35 @@ __device__ __forceinline__ void warp_step_size(const StepParams& p, int slot, in
 }
 
 // Share of a warp's chunks taken as one static contiguous range (in eighths)
-// and the chunks per pool group. On the 1e7-cell smooth workload (cell-updates/s,
-// A-DOT / PRICE-C): 8/8 4.71e10 / 7.9e10, 7/8 4.81e10 / 8.2e10, 6/8 5.04-5.07e10 /
-// 8.5-8.6e10, 5/8 5.02e10 / 8.4e10, 4/8 4.92e10 / 8.1e10, all pool 5.04e10 /
-// 6.3e10 (contention on the counter at PRICE-C's rate); groups of 1 or 4 chunks
-// at 6/8: 4.92e10 and 5.02e10; static groups interleaved over the warps instead
-// of contiguous ranges: at most 4.97e10. Measurement builds may set other values
-// (-DADOT_STATIC_EIGHTHS=k, -DADOT_POOL_CHUNKS=c).
+// and the chunks per pool group, per jump function. Measured on the 1e7-cell
+// smooth workload with the split formed on the host (cell-updates/s):
+//  DOT: 3/8 6.01e10, 4/8 6.03e10, 5/8 5.81e10, 6/8 5.61e10, 7/8 5.28e10 (groups
+//  of 2 chunks); at 5/8 groups of 1, 2, 4 chunks 5.54, 5.81, 5.84e10; 4/8 with 4
+//  chunks 5.96e10.
+//  PRICE-C: 4/8 with groups of 2 or 4 chunks 8.19e10 or 9.64e10, 5/8 8.62e10 or
+//  9.32e10, 6/8 8.56e10 (2 chunks); a pool of single chunks loses to
+//  contention on the counter at PRICE-C's rate (6.6e10 at 5/8).
+// Static groups interleaved over the warps instead of contiguous ranges
+// measured at most 4.97e10 (DOT, before the host-side split). Measurement
+// builds may set other values (-DADOT_STATIC_EIGHTHS=k, -DADOT_POOL_CHUNKS=c,
+// -DADOT_PRICE_STATIC_EIGHTHS=k, -DADOT_PRICE_POOL_CHUNKS=c).
 #ifndef ADOT_STATIC_EIGHTHS
-#define ADOT_STATIC_EIGHTHS 6
+#define ADOT_STATIC_EIGHTHS 4
 #endif
 #ifndef ADOT_POOL_CHUNKS
 #define ADOT_POOL_CHUNKS 2
 #endif
+#ifndef ADOT_PRICE_STATIC_EIGHTHS
+#define ADOT_PRICE_STATIC_EIGHTHS 4
+#endif
+#ifndef ADOT_PRICE_POOL_CHUNKS
+#define ADOT_PRICE_POOL_CHUNKS 4
+#endif
+template <int SCHEME>
+struct SplitShape {
+  static constexpr int eighths = SCHEME == 1 ? ADOT_PRICE_STATIC_EIGHTHS : ADOT_STATIC_EIGHTHS;
+  static constexpr int pool_chunks = SCHEME == 1 ? ADOT_PRICE_POOL_CHUNKS : ADOT_POOL_CHUNKS;
+};
 
 // Programmatic dependent launch: the float32 warp-tile step and k_fixup are
 // launched with programmatic stream serialisation, so that each can be
@@ -580,13 +596,14 @@ struct WarpSplit {
   int64_t cs, n_s, n_groups;
 };
 
+template <int SCHEME>
 inline WarpSplit warp_split(int64_t n, int64_t nwarps) {
   WarpSplit w;
-  int64_t ks = (((n + 31) / 32) * ADOT_STATIC_EIGHTHS / 8) / nwarps;
+  int64_t ks = (((n + 31) / 32) * SplitShape<SCHEME>::eighths / 8) / nwarps;
   if (ks < 2) ks = 0;
   w.cs = 32 * ks - 1;
   w.n_s = ks ? std::min<int64_t>(nwarps, n / w.cs) * w.cs : 0;
-  constexpr int64_t kGroup = 32 * ADOT_POOL_CHUNKS - 1;
+  constexpr int64_t kGroup = 32 * SplitShape<SCHEME>::pool_chunks - 1;
   w.n_groups = (n - w.n_s + kGroup - 1) / kGroup;
   return w;
 }
@@ -599,11 +616,13 @@ inline WarpSplit warp_split(int64_t n, int64_t nwarps) {
 // chunk. A range of k chunks updates 32 k - 1 cells, and consecutive ranges
 // share one edge (the only edge evaluated twice).
 //  - static part: with W warps and K = n / 32 chunks, each warp first takes a
-//    contiguous range of k_s = floor((6/8) K / W) chunks (none when k_s < 2),
+//    contiguous range of k_s = floor((e/8) K / W) chunks (none when k_s < 2;
+//    e = SplitShape<SCHEME>::eighths, 4 for both jump functions),
 //    so cells [0, N_s) with N_s = W' (32 k_s - 1), W' <= W; warp w of block b
 //    takes range w G + b (G blocks), so neighbouring ranges run on different
 //    SMs;
-//  - work pool: cells [N_s, n) in groups of 63 cells (2 chunks), handed out by
+//  - work pool: cells [N_s, n) in groups of 32 c - 1 cells (c chunks: 2 for the
+//    DOT edge, 4 for PRICE-C's cheaper one), handed out by
 //    an atomic counter in the control block; a warp asks for its next group
 //    before it computes the current one, so the atomic's latency is hidden.
 // The pool evens out the warps' finishing times: with static ranges alone the
@@ -652,7 +671,7 @@ __global__ void __launch_bounds__(B, MinBlocks<B, CAP>::value)
   bool carry_rd = false;  // DEFER: lane 0's flag of the previous chunk's last edge
   // the split (warp_split): static ranges of ws.cs cells over cells [0, ws.n_s),
   // then ws.n_groups pool groups
-  constexpr int64_t kGroup = 32 * ADOT_POOL_CHUNKS - 1;  // cells per pool group
+  constexpr int64_t kGroup = 32 * SplitShape<SCHEME>::pool_chunks - 1;  // cells per pool group
   // current range: next chunk's first edge eb, rem = edges after it (< 2^31;
   // negative when the range is finished)
   int64_t eb = 0;
@@ -926,7 +945,11 @@ __global__ void __launch_bounds__(256) k_fixup(const StepParams p, const StateF3
     }
   }
 }
-constexpr unsigned kFixupBlocks = 304;
+#ifndef ADOT_FIXUP_BLOCKS
+#define ADOT_FIXUP_BLOCKS 304
+#endif
+// k_fixup blocks: 2 per SM (measurement builds: -DADOT_FIXUP_BLOCKS=n)
+constexpr unsigned kFixupBlocks = ADOT_FIXUP_BLOCKS;
 
 // CFL maximum and admissibility of a state (grid-stride).
 template <typename R, int LAW>
@@ -988,7 +1011,7 @@ cudaError_t launch_step_law(const StepParams& p, StepVariant v, typename Prec<R>
     // right after); float64 evaluates every edge in place
     constexpr bool kDefer = std::is_same<R, float>::value;
     if (kDefer && p.fix_list == nullptr) return cudaErrorInvalidValue;
-    const WarpSplit ws = warp_split(p.n, gg * (v.block / 32));
+    const WarpSplit ws = warp_split<0>(p.n, gg * (v.block / 32));
     cudaError_t e = cudaErrorInvalidValue;
     if (v.block == 256 && v.reg_cap == 64) {
       e = launch_pdl(k_step_warp<R, LAW, 256, 64, EXT, 0, kDefer>, (unsigned)gg, 256u, s, p, in, out, slot, ws);

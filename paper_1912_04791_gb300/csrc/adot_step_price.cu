@@ -28,7 +28,7 @@ cudaError_t launch_shape(const StepParams& p, typename Prec<R>::State in,
   int64_t g = (tiles + wpb - 1) / wpb;
   if (g > sms * per_sm) g = sms * per_sm;
   k_step_warp<R, LAW, B, CAP, EXT, 1><<<(unsigned)g, B, 0, s>>>(p, in, out, slot,
-                                                               warp_split(p.n, g * (B / 32)));
+                                                               warp_split<1>(p.n, g * (B / 32)));
   return cudaGetLastError();
 }
 
