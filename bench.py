@@ -40,17 +40,20 @@ UNIT = "cell-updates/s"
 #  xu:    XU-pipe thread instructions per cell-update (sm__inst_executed_pipe_xu x 32 / cells);
 #  dram:  dram__bytes_read.sum + dram__bytes_write.sum per cell-update.
 KERNEL_COUNTS = {
-    # static ranges over 6/8 of the chunks (assigned across blocks, the split formed on the
-    # host) plus the 63-cell work pool: at 4e6 cells and 3648 warps, 4,020,875 edges
-    # evaluated for 4,000,001 (20,874 evaluated twice, removed); arccos(x)/3 by the library's
+    # static ranges over 4/8 of the chunks (assigned across blocks, the split formed on the
+    # host) plus the 63-cell work pool: at 4e6 cells and 3648 warps (cap 80), 4,035,698 edges
+    # evaluated for 4,000,001 (35,697 evaluated twice, removed); arccos(x)/3 by the library's
     # polynomial form; float64 redo deferred to k_fixup (which the smooth workload never
-    # calls); CFL Newton steps skipped below the lane's running maximum
-    ("warp", 256, 80): {"flops": (2 * 445.41752e6 + 334.767737e6 + 547.742857e6) / 4e6
-                        * (1 - 20874 / 4e6),
-                        "instr": 66.955724e6 * 32 / 4e6, "xu": 3.351343e6 * 32 / 4e6,
-                        "dram": (97.698304e6 + 51.847424e6) / 4e6},
-    ("warp", 256, 64): {"flops": None, "instr": 67.514271e6 * 32 / 4e6, "xu": 3.36922e6 * 32 / 4e6,
-                        "dram": (98.000640e6 + 51.617024e6) / 4e6},
+    # calls); CFL Newton steps skipped below the lane's running maximum. The flop count is the
+    # all-scalar build's (the same arithmetic at either register cap).
+    ("warp", 256, 80): {"flops": (2 * 443.619368e6 + 333.91313e6 + 547.090924e6) / 4e6
+                        * (1 - 35697 / 4e6),
+                        "instr": 67.00175e6 * 32 / 4e6, "xu": 3.369332e6 * 32 / 4e6,
+                        "dram": (96.802816e6 + 51.708416e6) / 4e6},
+    ("warp", 256, 64): {"flops": (2 * 443.619368e6 + 333.91313e6 + 547.090924e6) / 4e6
+                        * (1 - 35697 / 4e6),
+                        "instr": 67.596198e6 * 32 / 4e6, "xu": 3.388325e6 * 32 / 4e6,
+                        "dram": (97.00864e6 + 51.615488e6) / 4e6},
     ("order2", 256, 64): {"flops": None, "instr": None, "xu": None, "dram": None},
 }
 # The block kernel's all-scalar count (1 edge in 256 evaluated twice, removed).
