@@ -524,8 +524,9 @@ __device__ __forceinline__ void warp_step_size(const StepParams& p, int slot, in
 // and the chunks per pool group, per jump function. Measured on the 1e7-cell
 // smooth workload with the split formed on the host (cell-updates/s):
 //  DOT: 3/8 6.01e10, 4/8 6.03e10, 5/8 5.81e10, 6/8 5.61e10, 7/8 5.28e10 (groups
-//  of 2 chunks); at 5/8 groups of 1, 2, 4 chunks 5.54, 5.81, 5.84e10; 4/8 with 4
-//  chunks 5.96e10.
+//  of 2 chunks); at 5/8 groups of 1, 2, 4 chunks 5.54, 5.81, 5.84e10; 4/8 with 3
+//  or 4 chunks 6.00e10 or 5.96e10; 3/8 with 3 chunks 6.03e10 (4/8 with 2 chunks
+//  measured 6.02-6.03e10 in the same runs).
 //  PRICE-C: 4/8 with groups of 2 or 4 chunks 8.19e10 or 9.64e10, 5/8 8.62e10 or
 //  9.32e10, 6/8 8.56e10 (2 chunks); a pool of single chunks loses to
 //  contention on the counter at PRICE-C's rate (6.6e10 at 5/8).
