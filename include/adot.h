@@ -24,7 +24,11 @@
  *    device status word and returned by the next synchronising call; the
  *    context stays valid so that adot_get_state can still read the state.
  *  - Work is ordered on the CUDA stream given at creation (NULL: a stream the
- *    library creates). A context is not thread-safe.
+ *    library creates). A context is not thread-safe. The warp-tile step
+ *    kernels are launched with programmatic dependent launch: each may be
+ *    scheduled while the kernel before it on the stream drains, but it reads
+ *    nothing until that kernel has completed, so work the caller puts on the
+ *    same stream is ordered as with ordinary launches.
  *  - There is no CPU fallback: without a usable CUDA device adot_create fails
  *    with ADOT_E_CUDA.
  */
